@@ -1,0 +1,346 @@
+"""Benchmark of the adaptive pseudo-spectral BDF2 step for the 2D FCH flow.
+
+Workload: 1024^2 grid, mixed precision (single-precision transforms and pointwise
+stages, double-precision norms, energy, mass and controller), adaptive IMEX-BDF2
+with sigma_tol = 1e-5, critical-case parameters (q = 0, eta1 = 1.45 eps,
+eta2 = 1.5 eps, d = 0.75), seeded random bilayer network initial data.
+
+One step = one trial of the adaptive algorithm (Sec. 3.2): the IMEX-BDF2 trial
+(eq. IMEX-eq, 4 real 2D transforms), F of the trial (4 transforms), the AM3
+predictor and relative-L2 error, and the accept/reject + next-step decision, all
+on the device. L2 is flushed (a 512 MiB write) before every timed step; each
+step is timed with CUDA events on the library's stream.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+
+Under torchrun each rank runs an independent replica on its own GPU (the path
+has no exchange step); value = steps of all ranks / max-over-ranks time.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+N_GRID = 1024
+SIGMA = 1e-5
+T_FINAL = 10.0
+METRIC = "BDF2 steps/s (adaptive IMEX-BDF2 trials, 1024^2, mixed precision)"
+CONFIG = {"workload": "adaptive IMEX-BDF2, 1024x1024 periodic grid on [-2pi,2pi)^2, mixed "
+                      "precision (FP32 transforms/pointwise, FP64 reductions/controller), "
+                      "sigma_tol=1e-5, critical eta1/eta2 (pearling regime), seeded random "
+                      "bilayer network init",
+          "n": N_GRID, "scheme": "imex", "precision": "mixed", "sigma_tol": SIGMA,
+          "l2": "flushed before every timed step (512 MiB write)"}
+
+
+def rank_info():
+    return (int(os.environ.get("RANK", 0)), int(os.environ.get("WORLD_SIZE", 1)),
+            int(os.environ.get("LOCAL_RANK", 0)))
+
+
+def measured_peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        return {}
+
+
+class Clocks:
+    """nvidia-smi sampling during the timed region."""
+
+    def __init__(self, gpu: int):
+        self.gpu, self.proc, self.lines = gpu, None, []
+
+    def __enter__(self):
+        q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+             "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+             "clocks_event_reasons.sw_power_cap")
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={q}", "--format=csv,noheader,nounits",
+                 "-lms", "100"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], 0.0, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 7:
+                continue
+            try:
+                sm.append(float(f[0]))
+                mx = max(mx, float(f[1]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[3:7]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        sm.sort()
+        return {"sm_mhz": sm[len(sm) // 2] if sm else None, "sm_max_mhz": mx or None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def pass_bytes(name: str, n: int, csz: int) -> int:
+    """Algorithmic bytes of one launch of a pass: each array it must read or
+    write, once. H = one half spectrum (n/2+1)*n complex; Z = the n*n complex
+    work array between the column and row passes."""
+    H = (n // 2 + 1) * n * csz
+    Z = n * n * csz
+    table = {
+        "col_start": H * 2 + Z,            # u^n, u^{n-1} -> u*, packed Z
+        "row_nimex": 2 * Z,                # Z in, Z out
+        "row_f": 2 * Z,
+        "col_imex_solve": Z + 2 * H + H + Z,  # Z, u^n, u^{n-1} in; u^{n+1}, Z out
+        "col_f_finish": Z + H + H + 3 * H,    # Z, u~ in; F~ out; u^n, F^n, F^{n-1} in (AM3)
+    }
+    return table.get(name, 0)
+
+
+def run_gb300(args):
+    import numpy as np
+    import torch
+
+    rank, world, local = rank_info()
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+
+    from paper_2006_04784_gb300 import build as B
+    if rank == 0 or world == 1:
+        B.build()
+    if world > 1:
+        torch.distributed.barrier()
+    from paper_2006_04784_gb300 import fch
+    from paper_2006_04784_gb300 import inputs as I
+
+    n = N_GRID
+    p = fch.params_default(0.0, eta2=1.5 * 0.1, prec=fch.FCH_MIXED, sync_every=64)
+    u0 = I.random_network(n, d=0.75, seed=3 + rank)
+    stream = torch.cuda.Stream(device=dev)
+    ctx = fch.Context(n, p, stream=stream)
+    ctx.set_state(u0)
+    ctx.adaptive_begin("imex", SIGMA, T_FINAL)
+    ctx.adaptive_enqueue(max(args.warmup, 3))
+    ctx.synchronize()
+    st0 = ctx.stats()
+
+    flush = torch.empty(512 * 2 ** 20 // 4, dtype=torch.float32, device=dev)
+    K = args.steps
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+           for _ in range(K)]
+    ctx.pass_timing(True)
+    ctx.pass_times()  # clear
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    with Clocks(local) as clk:
+        with torch.cuda.stream(stream):
+            for i in range(K):
+                flush.fill_(float(i))
+                evs[i][0].record(stream)
+                ctx.adaptive_enqueue(1)
+                evs[i][1].record(stream)
+        torch.cuda.synchronize()
+    times = ctx.pass_times()
+    ctx.pass_timing(False)
+    st1 = ctx.adaptive_end()
+    step_ms = [a.elapsed_time(b) for a, b in evs]
+    tot_ms = sum(step_ms)
+    if world > 1:
+        t = torch.tensor([tot_ms], device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        tot_ms = float(t.item())
+        torch.distributed.barrier()
+    ms_per_step = tot_ms / K
+    value = world * K / (tot_ms / 1e3)
+    nfft = st1["n_fft"] - st0["n_fft"]
+
+    # dominant kernel and its roofline
+    peaks = measured_peaks()
+    hbm = peaks.get("hbm_gbs")
+    dom = max((k for k in times if k != "ctrl"), key=lambda k: times[k][0])
+    dms, dn = times[dom]
+    csz = 8  # complex64 in mixed precision
+    ab = pass_bytes(dom, n, csz)
+    achieved = ab / (dms / dn / 1e3) / 1e9 if ab else None
+    roof = {"kernel": dom, "bound": "hbm", "achieved": achieved, "peak": hbm,
+            "peak_source": "MEASURED_PEAKS.json hbm_gbs (measured)" if hbm else "fallback 6800",
+            "unit": "GB/s", "frac": (achieved / (hbm or 6800.0)) if achieved else None,
+            "traffic": traffic_from_profiles(dom, n), "algorithmic_bytes_per_launch": ab,
+            "avg_launch_us": dms / dn * 1e3}
+    kernels = {k: {"ms_total": round(v[0], 4), "launches": v[1],
+                   "share": round(v[0] / sum(x[0] for x in times.values()), 4)}
+               for k, v in sorted(times.items(), key=lambda kv: -kv[1][0])}
+
+    out = None
+    if rank == 0:
+        e2e = e2e_measure(fch, I, p, n, dev, min(K, 200))
+        out = {"metric": METRIC, "value": value, "unit": "steps/s", "n_gpus": world, "steps": K,
+               "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
+               "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64",
+               "data": "synthetic (seeded random bilayer network, no dataset)",
+               "config": dict(CONFIG, parallelism="replicas" if world > 1 else "single"),
+               "ffts_per_s": world * nfft / (tot_ms / 1e3),
+               "ffts_per_step": nfft / K,
+               "accepted": st1["n_steps"] - st0["n_steps"], "rejected": st1["n_rejects"] - st0["n_rejects"],
+               "t_reached": st1["t"],
+               "gpu_launches": sum(v[1] for v in times.values()),
+               "kernels": kernels, "roofline": roof, "clocks": clk.summary(), "e2e": e2e}
+        if not args.no_cpu_baseline and world == 1:
+            out["cpu_baseline"] = cpu_baseline(args)
+    ctx.close()
+    if world > 1:
+        torch.distributed.barrier()
+        torch.distributed.destroy_process_group()
+    return out
+
+
+def e2e_measure(fch, I, p, n, dev, K):
+    """The same metric through the public C ABI with host arrays: set_state from
+    a host array, K adaptive trials by fch_run_adaptive (one call per step, each
+    pushes the step's scalars and reads back the control block), get_state to a
+    host array at the end. Host copies are inside the timed region."""
+    import numpy as np
+    import torch
+
+    u0 = np.ascontiguousarray(I.random_network(n, d=0.75, seed=3))
+    out = np.empty_like(u0)
+    ctx = fch.Context(n, p)
+    ctx.set_state(u0)
+    ctx.run_adaptive("imex", SIGMA, T_FINAL, max_attempts=4, raise_on_timeout=False)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    ctx.set_state(u0)
+    for _ in range(K):
+        ctx.run_adaptive("imex", SIGMA, T_FINAL, max_attempts=1, raise_on_timeout=False)
+    ctx.get_state_into = None
+    res = ctx.get_state()
+    t1 = time.perf_counter()
+    ctx.close()
+    ctrl_bytes = fch.geometry(n)["ctrl_bytes"]
+    return {"value": K / (t1 - t0), "unit": "steps/s",
+            "h2d_bytes_per_step": (8 * n * n) / K + 2 * ctrl_bytes,
+            "d2h_bytes_per_step": (8 * n * n) / K + 3 * ctrl_bytes,
+            "note": "public API with host arrays: fch_set_state (host u0), one fch_run_adaptive "
+                    "call per step (control block in and out), fch_get_state (host) at the end; "
+                    "includes the backward-Euler restart of set_state"}
+
+
+def cpu_baseline(args):
+    """The oracle as it stands (single-threaded FP64 C) on a bounded sample of
+    the workload: two adaptive IMEX trials at 1024^2."""
+    import numpy as np
+
+    from oracle import oracle as O
+    from paper_2006_04784_gb300 import inputs as I
+
+    n = N_GRID
+    u0 = I.random_network(n, d=0.75, seed=3)
+    L = 4 * math.pi
+    p = O.params(eta2=0.15, zeta=1.1, D0=170.0)
+    s = O.Stepper(n, L, p)
+    s.set_history(u0, u0, 1e-6)
+    s.run_adaptive("imex", SIGMA, T_FINAL, max_attempts=1)  # F history + one trial
+    t0 = time.perf_counter()
+    s.run_adaptive("imex", SIGMA, T_FINAL, max_attempts=2)
+    dt = time.perf_counter() - t0
+    return {"value": 2 / dt, "unit": "steps/s", "cores": 1, "kind": "oracle",
+            "sample": "2 adaptive IMEX-BDF2 trials at 1024^2 (FP64 oracle, after its F history "
+                      f"was built), {dt:.1f} s"}
+
+
+def traffic_from_profiles(kernel: str, n: int):
+    """dram bytes per launch recorded by an ncu capture summarised in profiles/."""
+    path = os.path.join(ROOT, "profiles", "dram_traffic.txt")
+    try:
+        for line in open(path):
+            f = line.split("#")[0].split()
+            if len(f) >= 3 and f[0] == kernel and int(f[1]) == n:
+                return float(f[2])
+    except OSError:
+        pass
+    return None
+
+
+def run_reference(args):
+    """The oracle as the reference arm: adaptive IMEX trials at 1024^2 on the host
+    cores, each step one trial (bounded: at most ~150 s of timed work)."""
+    rank, world, _ = rank_info()
+    if rank != 0:
+        return None
+    import numpy as np
+
+    from oracle import oracle as O
+    from paper_2006_04784_gb300 import inputs as I
+
+    O.build()
+    n = N_GRID
+    L = 4 * math.pi
+    u0 = I.random_network(n, d=0.75, seed=3)
+    s = O.Stepper(n, L, O.params(eta2=0.15, zeta=1.1, D0=170.0))
+    s.set_history(u0, u0, 1e-6)
+    s.run_adaptive("imex", SIGMA, T_FINAL, max_attempts=max(1, min(args.warmup, 2)))
+    K = args.steps
+    t0 = time.perf_counter()
+    done = 0
+    while done < K:
+        s.run_adaptive("imex", SIGMA, T_FINAL, max_attempts=1)
+        done += 1
+        if time.perf_counter() - t0 > 150:
+            break
+    dt = time.perf_counter() - t0
+    v = done / dt
+    return {"impl": "reference", "metric": METRIC, "value": v, "unit": "steps/s", "n_gpus": world,
+            "steps": done, "warmup": args.warmup, "ms_per_step": 1e3 * dt / done,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic (seeded random bilayer network, no dataset)",
+            "config": dict(CONFIG, parallelism="single"),
+            "cpu_baseline": {"value": v, "unit": "steps/s", "cores": 1, "kind": "oracle",
+                             "sample": f"{done} adaptive IMEX trials at 1024^2 (of {K} asked; "
+                                       "capped at 150 s)"},
+            "e2e": {"value": v, "unit": "steps/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=1000)
+    ap.add_argument("--warmup", type=int, default=20)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    out = run_reference(args) if args.impl == "reference" else run_gb300(args)
+    if out is not None:
+        print(json.dumps(out))
+
+
+if __name__ == "__main__":
+    main()

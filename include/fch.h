@@ -1,0 +1,211 @@
+/*
+ * fch.h -- C ABI of the GB300 (sm_103a) Fourier pseudo-spectral steppers for the
+ * functionalized Cahn-Hilliard (FCH) gradient flow of
+ *   A. Christlieb, K. Promislow, Z. Tan, S. Wang, B. Wetton, S. Wise,
+ *   "Benchmark computation of morphological complexity in the functionalized
+ *    Cahn-Hilliard gradient flow", arXiv 2006.04784.
+ *
+ * Conventions (all entry points):
+ *  - Every function returns an fch_status; nothing throws across the ABI.
+ *  - Grid: N x N points on the periodic square [x0, x0+L)^2, N a power of two,
+ *    16 <= N <= 2048. A real field is a row-major N x N array, row index y,
+ *    column index x: u[y*N + x] is the value at (x0 + x h, x0 + y h), h = L/N.
+ *  - Spectra (the standalone transforms) are half spectra stored kx-major:
+ *    X[kx*N + ky], kx = 0..N/2, ky = 0..N-1, interleaved complex (re, im),
+ *    X(kx,ky) = sum_{x,y} u[y*N+x] exp(-2 pi i (kx x + ky y)/N)  (unnormalised);
+ *    the inverse transform divides by N^2.
+ *  - Host pointers are read or written during the call only and stay owned by the
+ *    caller. Device pointers passed in must be device memory of the context's
+ *    device; they are used in stream order on the context's stream (the caller
+ *    makes their contents ready with respect to that stream) and are not
+ *    retained after the work of the call has run.
+ *  - Calls on one context are not thread safe; different contexts are independent.
+ *  - Work is enqueued on the context's stream. fch_step, fch_set_state_device and
+ *    fch_get_state_device return without waiting; an error raised on the device
+ *    inside them (non-convergence, non-finite values) is reported by the next call
+ *    that waits for the stream (fch_get_state, fch_energy, fch_mass,
+ *    fch_get_stats, fch_run_adaptive, fch_synchronize). After a failed step every
+ *    stepping call returns FCH_ESTATE until a new state is set.
+ */
+#ifndef FCH_H
+#define FCH_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    FCH_OK = 0,
+    FCH_EINVAL = 1,      /* bad argument (N not a power of two, dt <= 0, NULL ...) */
+    FCH_ENOMEM = 2,      /* device or host allocation failed */
+    FCH_ECUDA = 3,       /* a CUDA runtime call failed (see fch_last_cuda_error) */
+    FCH_ENOCONV = 4,     /* PSD iteration reached psd_max_iter without meeting i_tol */
+    FCH_ENONFINITE = 5,  /* a norm, energy or error estimate was not finite */
+    FCH_ETIMEOUT = 6,    /* an attempt budget (max_attempts) ran out before t_final */
+    FCH_ESTATE = 7       /* stepping after a failure, or before a state was set */
+} fch_status;
+
+/* The time integrators of Secs. 3.3-3.6 of the paper. */
+typedef enum { FCH_IMEX = 0, FCH_SAV = 1, FCH_PSD = 2, FCH_ETD = 3 } fch_scheme;
+
+/* FCH_FP64: every stage in double precision.
+ * FCH_MIXED: transforms and pointwise stages in single precision; the mass,
+ * energy, SAV inner products and auxiliary scalar, the LTE norms and the
+ * step-size controller stay in double precision. */
+typedef enum { FCH_FP64 = 0, FCH_MIXED = 1 } fch_precision;
+
+typedef struct {
+    int n;       /* grid points per side, power of two in [16, 2048] */
+    double L;    /* period (paper: 4 pi) */
+    double x0;   /* origin of the square (only used to document the input grid) */
+} fch_grid;
+
+typedef struct {
+    /* model: regularised well W_q, eq. (e:Wq-def); energy, eq. (Functional) */
+    double eps, q, gamma, b_minus, b_plus, eta1, eta2;
+    /* SAV, eqs. (4.1)-(4.8): stabilisers beta1, beta2; zeta; energy shift D0 */
+    double beta1, beta2, zeta, D0;
+    /* ETDRK2 stabilisers, eq. (ETD-L) */
+    double kappa0, kappa2;
+    /* step-size controller, Sec. 3.2: safety rho_s, bounds k_min, k_max
+     * (k_max applies to IMEX, SAV, ETD; PSD uses min(k_max, psd_k_max)) */
+    double rho_s, k_min, k_max;
+    int zero_stab_cap;   /* 1: cap A_dp at (1 + sqrt 2) k (Sec. 3.2) */
+    /* PSD, Sec. 3.3: i_tol = psd_nu * sigma_tol in adaptive runs, psd_itol for
+     * fixed steps; lambda from Table SearchSize unless psd_lambda > 0 */
+    double psd_nu, psd_itol, psd_lambda, psd_k_max;
+    int psd_max_iter;
+    int prec;            /* fch_precision */
+    int sync_every;      /* adaptive runs: trial steps enqueued between host checks */
+} fch_params;
+
+typedef struct {
+    long long n_steps;     /* accepted steps since the state was set */
+    long long n_rejects;   /* rejected trial steps */
+    long long n_attempts;  /* trial steps */
+    long long n_psd_iter;  /* PSD iterations */
+    long long n_fft;       /* 2D real transforms (one field, R2C or C2R) */
+    double t;              /* current time */
+    double k_last;         /* last accepted step size */
+    double e_last;         /* last relative LTE estimate */
+    int last_psd_iter;     /* PSD iterations of the last solve */
+} fch_stats;
+
+typedef struct fch_ctx fch_ctx;
+typedef struct fch_fft_plan fch_fft_plan;
+
+/* Human-readable name of a status code (static string). */
+const char *fch_status_string(fch_status s);
+
+/* Text of the last CUDA error seen by this context; with ctx = NULL, the last
+ * error of a standalone-transform call on the calling thread. */
+const char *fch_last_cuda_error(const fch_ctx *ctx);
+
+/* Fill *p with the paper's constants for well parameter q (Table t:Benchmark,
+ * sub-critical row: eps = 0.1, gamma = 0.3, b_-/+ = -1/+1, eta1 = 1.45 eps,
+ * eta2 = 3 eps; beta1 = 2, beta2 = 1 (Sec. 3.5); kappa0 = 1e-2, kappa2 = 15
+ * (Sec. 3.6); rho_s = 0.9, k_min = 1e-9, k_max = infinity (Sec. 3.2);
+ * psd_nu and psd_k_max from Table tolPSD for q = 0, 0.2, 0.5). zeta exceeds
+ * -min W_q'' and D0 bounds -E1 from below as Sec. 3.5 requires; both are
+ * computed here by sampling W_q. prec = FCH_FP64. */
+fch_status fch_params_default(fch_params *p, double q);
+
+/* Create a context: allocates all device buffers for grid g on the current
+ * device. stream: a cudaStream_t to run on, or NULL for a stream the context
+ * creates and owns. The grid and params are copied. */
+fch_status fch_create(const fch_grid *g, const fch_params *p, void *stream, fch_ctx **out);
+fch_status fch_destroy(fch_ctx *ctx);
+
+/* Wait for all work enqueued on the context's stream; report device errors. */
+fch_status fch_synchronize(fch_ctx *ctx);
+
+/* Set u^0 from a host array of n_elems = N*N doubles. Clears the step history:
+ * the next step is a backward-Euler start (the k_{n-1} -> infinity limit of the
+ * variable-step BDF2, eq. (BDF2Coef)); SAV r^0 = sqrt(E1(u^0) + D0). */
+fch_status fch_set_state(fch_ctx *ctx, const double *u_host, size_t n_elems);
+
+/* Same from device memory; dtype 0 = float64, 1 = float32. */
+fch_status fch_set_state_device(fch_ctx *ctx, const void *u_dev, int dtype);
+
+/* Set (u^n, u^{n-1}, k_n): the next step is a full variable-step BDF2 step.
+ * SAV takes r^n = sqrt(E1(u^n)+D0), r^{n-1} = sqrt(E1(u^{n-1})+D0). */
+fch_status fch_set_history(fch_ctx *ctx, const double *un_host, const double *unm1_host,
+                           size_t n_elems, double kn);
+
+/* Copy u^n to the host (N*N doubles) / to device memory (dtype as above). */
+fch_status fch_get_state(fch_ctx *ctx, double *u_host, size_t n_elems);
+fch_status fch_get_state_device(fch_ctx *ctx, void *u_dev, int dtype);
+
+/* One step of size dt with the given scheme (Secs. 3.3-3.6):
+ * IMEX eq. (IMEX-eq); SAV eqs. (4.7)-(4.8); PSD eqs. (residual), (recurrence)
+ * with i_tol = psd_itol; ETDRK2 eqs. (ETDRK2), (ETD-L). Enqueued without waiting;
+ * PSD waits after every few iterations to test convergence. */
+fch_status fch_step(fch_ctx *ctx, fch_scheme scheme, double dt);
+
+/* E(u^n) of eq. (Functional), FP64 accumulation (waits for the stream). */
+fch_status fch_energy(fch_ctx *ctx, double *E);
+
+/* m(u^n) = 1/2 int (u+1) dx (Sec. 2.3), read from the k = 0 mode. */
+fch_status fch_mass(fch_ctx *ctx, double *m);
+
+/* F(u) = Lap dE/du (eq. sFCH) of a device field u (dtype as above) into F. */
+fch_status fch_rhs_device(fch_ctx *ctx, const void *u_dev, void *F_dev, int dtype);
+
+/* SAV auxiliary variables r^n, r^{n-1} (waits for the stream). */
+fch_status fch_get_sav_r(fch_ctx *ctx, double *r_n, double *r_nm1);
+
+/* Adaptive integration to t_final with the algorithm of Sec. 3.2 (AM3
+ * predictor, eq. (Predictor); relative L2 error; A_dp controller). The
+ * controller runs on the device; the host waits every sync_every trial steps.
+ * max_attempts bounds the number of trial steps of this call (<= 0: no bound);
+ * running out returns FCH_ETIMEOUT with the state valid at the time reached.
+ * stats may be NULL. */
+fch_status fch_run_adaptive(fch_ctx *ctx, fch_scheme scheme, double sigma_tol, double t_final,
+                            long long max_attempts, fch_stats *stats);
+
+fch_status fch_get_stats(fch_ctx *ctx, fch_stats *stats);
+
+/* fch_run_adaptive in three parts, for callers that enqueue trial steps without
+ * waiting (the controller of Sec. 3.2 runs on the device, so no host decision
+ * is needed between trials):
+ *  begin   -- sets sigma_tol and t_final, takes the backward-Euler start if the
+ *             history is empty and evaluates the F history; does not wait;
+ *  enqueue -- enqueues n trial steps (IMEX, SAV, ETD: no wait; PSD waits inside
+ *             each solve to test convergence); trials past t_final do nothing;
+ *  end     -- waits, reports device errors, fills stats (may be NULL). */
+fch_status fch_adaptive_begin(fch_ctx *ctx, fch_scheme scheme, double sigma_tol, double t_final);
+fch_status fch_adaptive_enqueue(fch_ctx *ctx, int n_trials);
+fch_status fch_adaptive_end(fch_ctx *ctx, fch_stats *stats);
+
+/* Device timing of the passes: with on = 1 every pass launch of this context is
+ * bracketed by CUDA events recorded on the context's stream. fch_pass_times waits
+ * for the stream, then returns and clears the accumulated milliseconds and launch
+ * counts per pass kind: index m < FCH_NCOL is the column pass in mode m, then
+ * FCH_NROW row-pass modes, then the control kernel (n >= FCH_NPASS entries). */
+#define FCH_NCOL 10
+#define FCH_NROW 6
+#define FCH_NPASS (FCH_NCOL + FCH_NROW + 1)
+fch_status fch_pass_timing(fch_ctx *ctx, int on);
+fch_status fch_pass_times(fch_ctx *ctx, double *ms, long long *launches, int n);
+
+/* ---- standalone 2D real transforms (the paper's cost unit, Sec. 1) ---- */
+
+/* Plan for N x N real transforms in precision prec on the given stream (NULL:
+ * the legacy default stream). Allocates one N x N complex work array. */
+fch_status fch_fft_plan_create(int n, int prec, void *stream, fch_fft_plan **out);
+fch_status fch_fft_plan_destroy(fch_fft_plan *plan);
+
+/* batch real fields x[b][N][N] -> half spectra X[b][N/2+1][N] (layout above);
+ * elements are double (FCH_FP64) or float (FCH_MIXED). Enqueued, no wait. */
+fch_status fch_fft_r2c(fch_fft_plan *plan, const void *x_dev, void *X_dev, int batch);
+
+/* inverse of fch_fft_r2c (divides by N^2); X is not modified. */
+fch_status fch_fft_c2r(fch_fft_plan *plan, const void *X_dev, void *x_dev, int batch);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* FCH_H */

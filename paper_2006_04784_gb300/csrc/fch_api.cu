@@ -1,0 +1,1150 @@
+// fch_api.cu -- host side of libfch: contexts, the scheme pipelines, the adaptive
+// driver, the control kernel (FP64 reductions and the step-size controller) and
+// the standalone transforms. The C ABI is declared in include/fch.h.
+#include <math.h>
+#include <stdio.h>
+#include <stdlib.h>
+#include <string.h>
+
+#include "../../include/fch.h"
+#include "fch_internal.h"
+
+// ---------------------------------------------------------------------------
+// geometry
+fch_geom fch_geometry(int N, int prec)
+{
+    fch_geom g;
+    const int csz = prec ? 8 : 16; // bytes per complex element
+    int P = 1024 / N;
+    if (P < 2) P = 2;
+    if (P > N / 2) P = N / 2;
+    g.P = P;
+    g.col_threads = P * N / 4; // 2P sequences x N/8 threads
+    g.col_blocks = N / (2 * P);
+    g.col_smem = (N + 2 * P * N) * csz;
+    const int tps = N / 8;
+    int rpb = 256 / tps;
+    if (rpb < 1) rpb = 1;
+    if (rpb > N) rpb = N;
+    g.rpb = rpb;
+    g.row_threads = rpb * tps;
+    g.row_blocks = N / rpb;
+    g.row_smem = (N + rpb * N) * csz;
+    return g;
+}
+
+// ---------------------------------------------------------------------------
+// control kernel: one block of 256 threads; deterministic FP64 sums of the
+// per-block partials (fixed thread assignment, fixed tree), then thread 0 acts.
+__global__ void __launch_bounds__(256) fch_ctrl_kernel(const fch_kparams kp, int op, int na, double arg0)
+{
+    __shared__ double sh[2][256];
+    fch_ctrl *c = kp.ctrl;
+    if (c->done && !(kp.flags & FCH_FL_NOSKIP)) return;
+    if (op == OP_PSD_CHECK && c->psd_conv) return;
+    double s0 = 0, s1 = 0;
+    for (int i = threadIdx.x; i < na; i += 256) {
+        s0 += kp.part[i];
+        s1 += kp.part[FCH_MAXBLK + i];
+    }
+    sh[0][threadIdx.x] = s0;
+    sh[1][threadIdx.x] = s1;
+    __syncthreads();
+    for (int w = 128; w > 0; w >>= 1) {
+        if (threadIdx.x < w) {
+            sh[0][threadIdx.x] += sh[0][threadIdx.x + w];
+            sh[1][threadIdx.x] += sh[1][threadIdx.x + w];
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x != 0) return;
+    const double S0 = sh[0][0], S1 = sh[1][0];
+
+    switch (op) {
+    case OP_INIT_TRIAL: {
+        double k1;
+        if (arg0 > 0) {
+            k1 = arg0; // fixed step
+        } else {
+            const double rem = c->t_final - c->t;
+            if (rem <= 1e-12 * fmax(1.0, fabs(c->t_final))) {
+                c->done = 1;
+                return;
+            }
+            k1 = fmin(c->ktrial, rem); // the run ends exactly at t_final
+        }
+        c->k1 = k1;
+        if (c->kn <= 0) { // backward-Euler start: k_{n-1} -> infinity in eq. (BDF2Coef)
+            c->a = 1.0 / k1;
+            c->b = -1.0 / k1;
+            c->c = 0.0;
+            c->gam = 0.0;
+        } else { // eq. (BDF2Coef)
+            const double kn = c->kn;
+            c->a = 1.0 / k1 + 1.0 / (k1 + kn);
+            c->b = -1.0 / k1 - 1.0 / kn;
+            c->c = 1.0 / kn - 1.0 / (k1 + kn);
+            c->gam = k1 / kn;
+            const double g = c->gam; // eq. (Predictor) weights
+            c->w1 = k1 / 6.0 * (3.0 + 2.0 * g) / (1.0 + g);
+            c->w2 = k1 / 6.0 * (3.0 + g);
+            c->w3 = -k1 / 6.0 * g * g / (1.0 + g);
+        }
+        // PSD search step: Table SearchSize row, linear in k, clamped
+        if (c->lam_k[0] < 0) {
+            c->lam = c->lam_tab[0]; // fixed lambda
+        } else if (k1 <= c->lam_k[0]) {
+            c->lam = c->lam_tab[0];
+        } else if (k1 >= c->lam_k[9]) {
+            c->lam = c->lam_tab[9];
+        } else {
+            int j = 0;
+            while (j < 8 && k1 > c->lam_k[j + 1]) j++;
+            const double th = (k1 - c->lam_k[j]) / (c->lam_k[j + 1] - c->lam_k[j]);
+            c->lam = c->lam_tab[j] + th * (c->lam_tab[j + 1] - c->lam_tab[j]);
+        }
+        c->psd_conv = 0;
+        c->psd_iter = 0;
+        break;
+    }
+    case OP_SAV_E1: {
+        const double e1 = kp.h2 * S0;
+        const double v = e1 + kp.D0;
+        if (!isfinite(v) || v <= 0) {
+            c->status = FCH_ENONFINITE;
+            c->done = 1;
+            return;
+        }
+        c->e1 = e1;
+        c->inv_sqrt_e1 = 1.0 / sqrt(v);
+        if (arg0 == 1.0) c->r_n = sqrt(v);
+        if (arg0 == 2.0) c->r_m = sqrt(v);
+        break;
+    }
+    case OP_SAV_R: {
+        // eq. (4.8) with u^{n+1} = p + r q:
+        // r (a - a (X, q)/2) = -b r^n - c r^{n-1} + (X, a p + b u^n + c u^{n-1})/2
+        const double sc = kp.h2 * kp.inv_n2; // Parseval on the unnormalised half spectra
+        const double xr = sc * S0, xq = sc * S1;
+        const double r = (-c->b * c->r_n - c->c * c->r_m + 0.5 * xr) / (c->a * (1.0 - 0.5 * xq));
+        if (!isfinite(r)) {
+            c->status = FCH_ENONFINITE;
+            c->done = 1;
+            return;
+        }
+        c->r_new = r;
+        break;
+    }
+    case OP_PSD_CHECK: {
+        const double ratio = sqrt(S0) / sqrt(S1); // ||d|| / ||v_{s+1}||, h cancels
+        c->psd_iter++;
+        c->n_psd_iter++;
+        c->psd_ratio = ratio;
+        if (!isfinite(ratio)) {
+            c->status = FCH_ENONFINITE;
+            c->done = 1;
+        } else if (ratio < c->itol) {
+            c->psd_conv = 1;
+            c->last_psd_iter = c->psd_iter;
+        } else if (c->psd_iter >= c->psd_max_iter) {
+            c->status = FCH_ENOCONV;
+            c->done = 1;
+            c->last_psd_iter = c->psd_iter;
+        }
+        break;
+    }
+    case OP_DECIDE: {
+        // Steps 3-4 of the adaptive algorithm, Sec. 3.2
+        const double e = sqrt(S0) / sqrt(S1);
+        c->n_attempts++;
+        if (!isfinite(e)) {
+            c->status = FCH_ENONFINITE;
+            c->done = 1;
+            return;
+        }
+        c->e_last = e;
+        const double k1 = c->k1;
+        double kn = c->rho_s * cbrt(c->sigma / fmax(e, 1e-16)) * k1; // A_dp(e, k)
+        if (c->cap) kn = fmin(kn, (1.0 + sqrt(2.0)) * k1);
+        kn = fmax(c->kmin, fmin(kn, c->kmax));
+        if (e <= c->sigma || k1 <= c->kmin) {
+            const int un = c->iu_n, um = c->iu_m, fn = c->if_n, fm = c->if_m;
+            c->iu_m = un;
+            c->iu_n = c->iu_new;
+            c->iu_new = um;
+            c->if_m = fn;
+            c->if_n = c->if_new;
+            c->if_new = fm;
+            c->r_m = c->r_n;
+            c->r_n = c->r_new;
+            c->kn = k1;
+            c->t += k1;
+            c->n_steps++;
+            c->accepted_last = 1;
+        } else {
+            c->n_rejects++;
+            c->accepted_last = 0;
+        }
+        c->ktrial = kn;
+        break;
+    }
+    case OP_ACCEPT: {
+        const int un = c->iu_n, um = c->iu_m;
+        c->iu_m = un;
+        c->iu_n = c->iu_new;
+        c->iu_new = um;
+        if (arg0 == 1.0) { // also rotate the F history (adaptive start)
+            const int fn = c->if_n, fm = c->if_m;
+            c->if_m = fn;
+            c->if_n = c->if_new;
+            c->if_new = fm;
+        }
+        c->r_m = c->r_n;
+        c->r_n = c->r_new;
+        c->kn = c->k1;
+        c->ktrial = c->k1;
+        c->t += c->k1;
+        c->n_steps++;
+        c->n_attempts++;
+        break;
+    }
+    case OP_ENERGY: {
+        c->energy = kp.h2 * S0;
+        break;
+    }
+    }
+}
+
+cudaError_t fch_launch_ctrl(int op, const fch_kparams &kp, int na, int, double arg0, cudaStream_t s)
+{
+    fch_ctrl_kernel<<<1, 256, 0, s>>>(kp, op, na, arg0);
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// host-side model constants (product side; the test oracle has its own)
+static void host_well(const fch_params &p, double u, double *W, double *W1, double *W2)
+{
+    const double v = u - p.b_minus;
+    double A = 0.5 * v * v, A1 = v, A2 = 1.0;
+    if (p.q != 0.0) {
+        const double x = v / p.eps;
+        const double e = exp(-fabs(x));
+        const double sech = 2.0 * e / (1.0 + e * e);
+        const double th = copysign((1.0 - e * e) / (1.0 + e * e), x);
+        A += p.q * p.eps * (1.0 - sech);
+        A1 += p.q * sech * th;
+        A2 += (p.q / p.eps) * sech * (2.0 * sech * sech - 1.0);
+    }
+    const double w = u - p.b_plus;
+    const double B = 0.5 * w * w + p.gamma / 3.0 * (u - 0.5 * (3.0 * p.b_plus - p.b_minus));
+    const double B1 = w + p.gamma / 3.0;
+    *W = A * B;
+    *W1 = A1 * B + A * B1;
+    *W2 = A2 * B + 2.0 * A1 * B1 + A;
+}
+
+// zeta > -min W_q'' and D0 >= -|Omega| min (W'^2/2 - eta2 W) + |Omega|, Sec. 3.5
+static void sav_constants(const fch_params &p, double area, double *zeta, double *D0)
+{
+    double minW2 = 1e300, minG = 1e300;
+    for (int i = 0; i <= 600000; i++) {
+        const double u = -4.0 + 8.0 * i / 600000.0;
+        double W, W1, W2;
+        host_well(p, u, &W, &W1, &W2);
+        if (W2 < minW2) minW2 = W2;
+        const double g = 0.5 * W1 * W1 - p.eta2 * W;
+        if (g < minG) minG = g;
+    }
+    *zeta = -minW2 + 0.1;
+    *D0 = area * (fmax(0.0, -minG) + 1.0);
+}
+
+static int psd_row(double q) { return q < 0.1 ? 0 : (q < 0.35 ? 1 : 2); }
+
+static const double kLamK[10] = {1e-6, 1e-5, 5e-5, 1e-4, 5e-4, 1e-3, 5e-3, 1e-2, 2e-2, 3e-2};
+static const double kLamTab[3][10] = { // Table SearchSize
+    {1, 1.07, 1.11, 1.14, 1.24, 1.34, 1.60, 1.738, 1.804, 1.855},
+    {1, 1.04, 1.15, 1.28, 1.50, 1.70, 1.87, 1.92, 1.95, 1.97},
+    {1, 1.20, 1.32, 1.45, 1.72, 1.83, 1.965, 1.97, 1.985, 1.99},
+};
+
+extern "C" fch_status fch_params_default(fch_params *p, double q)
+{
+    if (!p) return FCH_EINVAL;
+    memset(p, 0, sizeof(*p));
+    p->eps = 0.1;
+    p->q = q;
+    p->gamma = 0.3;
+    p->b_minus = -1.0;
+    p->b_plus = 1.0;
+    p->eta1 = 1.45 * p->eps;
+    p->eta2 = 3.0 * p->eps;
+    p->beta1 = 2.0;
+    p->beta2 = 1.0;
+    p->zeta = 0.0; // 0: computed at fch_create from the well
+    p->D0 = 0.0;   // 0: computed at fch_create for the grid's area
+    p->kappa0 = 1e-2;
+    p->kappa2 = 15.0;
+    p->rho_s = 0.9;
+    p->k_min = 1e-9;
+    p->k_max = INFINITY;
+    p->zero_stab_cap = 0;
+    const int row = psd_row(q); // Table tolPSD: nu(q) and the optimal k_max
+    const double nu[3] = {1e-3, 2e-5, 1e-6}, km[3] = {0.05, 0.02, 0.01};
+    p->psd_nu = nu[row];
+    p->psd_k_max = km[row];
+    p->psd_itol = 1e-10;
+    p->psd_lambda = 0.0;
+    p->psd_max_iter = 1000;
+    p->prec = FCH_FP64;
+    p->sync_every = 16;
+    return FCH_OK;
+}
+
+extern "C" const char *fch_status_string(fch_status s)
+{
+    switch (s) {
+    case FCH_OK: return "ok";
+    case FCH_EINVAL: return "invalid argument";
+    case FCH_ENOMEM: return "out of memory";
+    case FCH_ECUDA: return "CUDA error";
+    case FCH_ENOCONV: return "PSD iteration did not converge";
+    case FCH_ENONFINITE: return "non-finite value";
+    case FCH_ETIMEOUT: return "attempt budget exhausted";
+    case FCH_ESTATE: return "invalid state (failed step or no state set)";
+    }
+    return "unknown status";
+}
+
+// ---------------------------------------------------------------------------
+// context
+struct fch_ctx {
+    int N, prec;
+    fch_grid grid;
+    fch_params p;
+    cudaStream_t stream;
+    bool own_stream;
+    fch_geom geom;
+    fch_kparams kp;      // base parameters; passes copy and adjust
+    fch_ctrl hc;         // host mirror of the control block
+    fch_ctrl *dctrl;
+    double *part;
+    void *U[3], *F[3], *Pb, *Qb, *Vb, *Nb, *Z, *tw;
+    double *staging;     // N*N doubles for host io
+    long long *nfft_dev;
+    long long nfft_base;
+    bool have_state, failed, have_F;
+    fch_scheme ad_scheme;           // scheme of the adaptive run begun last
+    bool ad_open;
+    // per-pass event timing
+    bool timing;
+    int nev;
+    cudaEvent_t ev[2 * 2048];
+    int ev_kind[2048];
+    double t_ms[FCH_NPASS];
+    long long t_n[FCH_NPASS];
+    char errbuf[256];
+};
+
+static void timing_flush(fch_ctx *ctx)
+{
+    if (!ctx->nev) return;
+    cudaStreamSynchronize(ctx->stream);
+    for (int i = 0; i < ctx->nev; i++) {
+        float ms = 0;
+        cudaEventElapsedTime(&ms, ctx->ev[2 * i], ctx->ev[2 * i + 1]);
+        ctx->t_ms[ctx->ev_kind[i]] += ms;
+        ctx->t_n[ctx->ev_kind[i]]++;
+    }
+    ctx->nev = 0;
+}
+
+static void timing_begin(fch_ctx *ctx)
+{
+    if (!ctx->timing) return;
+    if (ctx->nev == 2048) timing_flush(ctx);
+    cudaEventRecord(ctx->ev[2 * ctx->nev], ctx->stream);
+}
+
+static void timing_end(fch_ctx *ctx, int kind)
+{
+    if (!ctx->timing) return;
+    cudaEventRecord(ctx->ev[2 * ctx->nev + 1], ctx->stream);
+    ctx->ev_kind[ctx->nev++] = kind;
+}
+
+#define CKC(ctx, call)                                                                    \
+    do {                                                                                  \
+        cudaError_t e_ = (call);                                                          \
+        if (e_ != cudaSuccess) {                                                          \
+            snprintf((ctx)->errbuf, sizeof((ctx)->errbuf), "%s: %s", #call,               \
+                     cudaGetErrorString(e_));                                             \
+            return FCH_ECUDA;                                                             \
+        }                                                                                 \
+    } while (0)
+
+static thread_local char g_plan_err[256];
+
+extern "C" const char *fch_last_cuda_error(const fch_ctx *ctx) { return ctx ? ctx->errbuf : g_plan_err; }
+
+static bool pow2_in_range(int n) { return n >= FCH_MIN_N && n <= FCH_MAX_N && (n & (n - 1)) == 0; }
+
+static int ilog2(int n)
+{
+    int l = 0;
+    while ((1 << l) < n) l++;
+    return l;
+}
+
+template <typename T> static void make_twiddles(int N, T *out)
+{
+    for (int m = 0; m < N; m++) {
+        const double a = -2.0 * M_PI * (double)m / (double)N;
+        out[2 * m] = (T)cos(a);
+        out[2 * m + 1] = (T)sin(a);
+    }
+}
+
+static fch_status upload_twiddles(fch_ctx *ctx, int N, int prec, void *dst, cudaStream_t s)
+{
+    if (prec) {
+        float *h = (float *)malloc(sizeof(float) * 2 * N);
+        make_twiddles(N, h);
+        cudaError_t e = cudaMemcpyAsync(dst, h, sizeof(float) * 2 * N, cudaMemcpyHostToDevice, s);
+        cudaStreamSynchronize(s);
+        free(h);
+        if (e != cudaSuccess) return FCH_ECUDA;
+    } else {
+        double *h = (double *)malloc(sizeof(double) * 2 * N);
+        make_twiddles(N, h);
+        cudaError_t e = cudaMemcpyAsync(dst, h, sizeof(double) * 2 * N, cudaMemcpyHostToDevice, s);
+        cudaStreamSynchronize(s);
+        free(h);
+        if (e != cudaSuccess) return FCH_ECUDA;
+    }
+    (void)ctx;
+    return FCH_OK;
+}
+
+static void fill_kparams_model(fch_kparams &kp, const fch_params &p, int N, double L)
+{
+    kp.N = N;
+    kp.logN = ilog2(N);
+    kp.L = L;
+    kp.kf = 2.0 * M_PI / L;
+    kp.inv_n2 = 1.0 / ((double)N * N);
+    kp.h2 = (L / N) * (L / N);
+    kp.eps = p.eps;
+    kp.eps2 = p.eps * p.eps;
+    kp.q = p.q;
+    kp.gamma = p.gamma;
+    kp.bm = p.b_minus;
+    kp.bp = p.b_plus;
+    kp.eta1 = p.eta1;
+    kp.eta2 = p.eta2;
+    double W, W1, W2;
+    host_well(p, p.b_minus, &W, &W1, &W2);
+    kp.am = W2; // alpha_m = W_q''(b_-)
+    kp.beta1 = p.beta1;
+    kp.beta2 = p.beta2;
+    kp.zeta = p.zeta;
+    kp.D0 = p.D0;
+    kp.kappa0 = p.kappa0;
+    kp.kappa2 = p.kappa2;
+}
+
+static void reset_ctrl(fch_ctx *ctx)
+{
+    fch_ctrl &c = ctx->hc;
+    memset(&c, 0, sizeof(c));
+    c.iu_n = 0;
+    c.iu_m = 1;
+    c.iu_new = 2;
+    c.if_n = 0;
+    c.if_m = 1;
+    c.if_new = 2;
+    c.rho_s = ctx->p.rho_s;
+    c.kmin = ctx->p.k_min;
+    c.kmax = ctx->p.k_max;
+    c.cap = ctx->p.zero_stab_cap;
+    c.psd_max_iter = ctx->p.psd_max_iter;
+    c.itol = ctx->p.psd_itol;
+    if (ctx->p.psd_lambda > 0) {
+        c.lam_k[0] = -1.0;
+        c.lam_tab[0] = ctx->p.psd_lambda;
+    } else {
+        const int row = psd_row(ctx->p.q);
+        for (int j = 0; j < 10; j++) {
+            c.lam_k[j] = kLamK[j];
+            c.lam_tab[j] = kLamTab[row][j];
+        }
+    }
+}
+
+static fch_status push_ctrl(fch_ctx *ctx)
+{
+    CKC(ctx, cudaMemcpyAsync(ctx->dctrl, &ctx->hc, sizeof(fch_ctrl), cudaMemcpyHostToDevice, ctx->stream));
+    return FCH_OK;
+}
+
+static fch_status pull_ctrl(fch_ctx *ctx)
+{
+    CKC(ctx, cudaMemcpyAsync(&ctx->hc, ctx->dctrl, sizeof(fch_ctrl), cudaMemcpyDeviceToHost, ctx->stream));
+    CKC(ctx, cudaStreamSynchronize(ctx->stream));
+    return FCH_OK;
+}
+
+// pass launchers
+static fch_status col(fch_ctx *ctx, int mode, int src = 0, int flags = 0, const void *in0 = nullptr,
+                      const void *in1 = nullptr, void *out0 = nullptr, void *out1 = nullptr)
+{
+    fch_kparams kp = ctx->kp;
+    kp.src = src;
+    kp.flags = flags;
+    kp.in0 = in0;
+    kp.in1 = in1;
+    kp.out0 = out0;
+    kp.out1 = out1;
+    timing_begin(ctx);
+    cudaError_t e = ctx->prec ? fch_launch_col_f32(mode, kp, ctx->stream)
+                              : fch_launch_col_f64(mode, kp, ctx->stream);
+    timing_end(ctx, mode);
+    CKC(ctx, e);
+    return FCH_OK;
+}
+
+static fch_status row(fch_ctx *ctx, int mode, int flags = 0, const void *in0 = nullptr,
+                      void *out0 = nullptr)
+{
+    fch_kparams kp = ctx->kp;
+    kp.flags = flags;
+    kp.in0 = in0;
+    kp.out0 = out0;
+    timing_begin(ctx);
+    cudaError_t e = ctx->prec ? fch_launch_row_f32(mode, kp, ctx->stream)
+                              : fch_launch_row_f64(mode, kp, ctx->stream);
+    timing_end(ctx, FCH_NCOL + mode);
+    CKC(ctx, e);
+    return FCH_OK;
+}
+
+static fch_status ctl(fch_ctx *ctx, int op, int na, double arg0 = 0.0, int flags = 0)
+{
+    fch_kparams kp = ctx->kp;
+    kp.flags = flags;
+    timing_begin(ctx);
+    cudaError_t e = fch_launch_ctrl(op, kp, na, 0, arg0, ctx->stream);
+    timing_end(ctx, FCH_NCOL + FCH_NROW);
+    CKC(ctx, e);
+    return FCH_OK;
+}
+
+#define TRY(x)                                                                            \
+    do {                                                                                  \
+        fch_status s_ = (x);                                                              \
+        if (s_ != FCH_OK) return s_;                                                      \
+    } while (0)
+
+extern "C" fch_status fch_create(const fch_grid *g, const fch_params *p, void *stream, fch_ctx **out)
+{
+    if (!g || !p || !out) return FCH_EINVAL;
+    *out = nullptr;
+    if (!pow2_in_range(g->n) || !(g->L > 0) || !(p->eps > 0) || (p->prec != 0 && p->prec != 1) ||
+        !(p->k_min > 0) || !(p->rho_s > 0) || p->psd_max_iter < 1)
+        return FCH_EINVAL;
+    fch_ctx *ctx = (fch_ctx *)calloc(1, sizeof(fch_ctx));
+    if (!ctx) return FCH_ENOMEM;
+    ctx->N = g->n;
+    ctx->prec = p->prec;
+    ctx->grid = *g;
+    ctx->p = *p;
+    if (ctx->p.sync_every < 1) ctx->p.sync_every = 16;
+    if (ctx->p.zeta <= 0 || ctx->p.D0 <= 0) {
+        double z, d;
+        sav_constants(ctx->p, g->L * g->L, &z, &d);
+        if (ctx->p.zeta <= 0) ctx->p.zeta = z;
+        if (ctx->p.D0 <= 0) ctx->p.D0 = d;
+    }
+    ctx->geom = fch_geometry(ctx->N, ctx->prec);
+    const int N = ctx->N;
+    const size_t csz = ctx->prec ? 8 : 16;
+    const size_t hs = (size_t)(N / 2 + 1) * N * csz;
+    cudaError_t e = cudaSuccess;
+    if (stream) {
+        ctx->stream = (cudaStream_t)stream;
+    } else {
+        e = cudaStreamCreateWithFlags(&ctx->stream, cudaStreamNonBlocking);
+        ctx->own_stream = true;
+    }
+    void **bufs[] = {&ctx->U[0], &ctx->U[1], &ctx->U[2], &ctx->F[0], &ctx->F[1], &ctx->F[2],
+                     &ctx->Pb, &ctx->Qb, &ctx->Vb, &ctx->Nb};
+    for (void **b : bufs)
+        if (e == cudaSuccess) e = cudaMalloc(b, hs);
+    if (e == cudaSuccess) e = cudaMalloc(&ctx->Z, (size_t)N * N * csz);
+    if (e == cudaSuccess) e = cudaMalloc(&ctx->tw, (size_t)N * csz);
+    if (e == cudaSuccess) e = cudaMalloc((void **)&ctx->part, sizeof(double) * FCH_NRED * FCH_MAXBLK);
+    if (e == cudaSuccess) e = cudaMalloc((void **)&ctx->dctrl, sizeof(fch_ctrl));
+    if (e == cudaSuccess) e = cudaMalloc((void **)&ctx->staging, sizeof(double) * N * N * 2);
+    if (e == cudaSuccess) e = cudaMalloc((void **)&ctx->nfft_dev, sizeof(long long));
+    if (e == cudaSuccess) e = cudaMemsetAsync(ctx->nfft_dev, 0, sizeof(long long), ctx->stream);
+    if (e != cudaSuccess) {
+        snprintf(ctx->errbuf, sizeof(ctx->errbuf), "fch_create: %s", cudaGetErrorString(e));
+        fch_destroy(ctx);
+        return e == cudaErrorMemoryAllocation ? FCH_ENOMEM : FCH_ECUDA;
+    }
+    fill_kparams_model(ctx->kp, ctx->p, N, g->L);
+    ctx->kp.P = ctx->geom.P;
+    for (int i = 0; i < 3; i++) {
+        ctx->kp.U[i] = ctx->U[i];
+        ctx->kp.F[i] = ctx->F[i];
+    }
+    ctx->kp.Pb = ctx->Pb;
+    ctx->kp.Qb = ctx->Qb;
+    ctx->kp.Vb = ctx->Vb;
+    ctx->kp.Nb = ctx->Nb;
+    ctx->kp.Z = ctx->Z;
+    ctx->kp.tw = ctx->tw;
+    ctx->kp.part = ctx->part;
+    ctx->kp.ctrl = ctx->dctrl;
+    ctx->kp.nfft = (unsigned long long *)ctx->nfft_dev;
+    fch_status s = upload_twiddles(ctx, N, ctx->prec, ctx->tw, ctx->stream);
+    if (s != FCH_OK) {
+        fch_destroy(ctx);
+        return s;
+    }
+    reset_ctrl(ctx);
+    s = push_ctrl(ctx);
+    if (s != FCH_OK) {
+        fch_destroy(ctx);
+        return s;
+    }
+    *out = ctx;
+    return FCH_OK;
+}
+
+extern "C" fch_status fch_destroy(fch_ctx *ctx)
+{
+    if (!ctx) return FCH_OK;
+    if (ctx->stream) cudaStreamSynchronize(ctx->stream);
+    void *bufs[] = {ctx->U[0], ctx->U[1], ctx->U[2], ctx->F[0], ctx->F[1], ctx->F[2], ctx->Pb,
+                    ctx->Qb, ctx->Vb, ctx->Nb, ctx->Z, ctx->tw, ctx->part, ctx->dctrl,
+                    ctx->staging, ctx->nfft_dev};
+    for (void *b : bufs)
+        if (b) cudaFree(b);
+    if (ctx->timing)
+        for (int i = 0; i < 2 * 2048; i++) cudaEventDestroy(ctx->ev[i]);
+    if (ctx->own_stream && ctx->stream) cudaStreamDestroy(ctx->stream);
+    free(ctx);
+    return FCH_OK;
+}
+
+extern "C" fch_status fch_synchronize(fch_ctx *ctx)
+{
+    if (!ctx) return FCH_EINVAL;
+    TRY(pull_ctrl(ctx));
+    if (ctx->hc.status) {
+        ctx->failed = true;
+        return (fch_status)ctx->hc.status;
+    }
+    return FCH_OK;
+}
+
+// real field (device; f64 when io64) -> U[slot]
+static fch_status load_field(fch_ctx *ctx, const void *u_dev, bool io64, void *dst)
+{
+    TRY(row(ctx, RM_R2C_LOAD, FCH_FL_NOSKIP | (io64 ? FCH_FL_F64IO : 0), u_dev));
+    TRY(col(ctx, CM_FWD_STORE, 0, FCH_FL_NOSKIP, nullptr, nullptr, dst, nullptr));
+    return FCH_OK;
+}
+
+// SAV r from E1 of the state in slot src (4 = u^n via USTAR with gam 0? use explicit srcs)
+static fch_status sav_r_init(fch_ctx *ctx, int src, double which)
+{
+    TRY(col(ctx, CM_START, src, FCH_FL_NOSKIP));
+    TRY(row(ctx, RM_SAV, FCH_FL_NOSKIP));
+    TRY(ctl(ctx, OP_SAV_E1, ctx->geom.row_blocks, which, FCH_FL_NOSKIP));
+    return FCH_OK;
+}
+
+static fch_status set_state_common(fch_ctx *ctx, const void *u_dev, bool io64)
+{
+    reset_ctrl(ctx);
+    TRY(push_ctrl(ctx));
+    TRY(load_field(ctx, u_dev, io64, ctx->U[0]));
+    TRY(sav_r_init(ctx, FCH_SRC_UN, 1.0));
+    ctx->have_state = true;
+    ctx->failed = false;
+    ctx->have_F = false;
+    return FCH_OK;
+}
+
+extern "C" fch_status fch_set_state(fch_ctx *ctx, const double *u_host, size_t n)
+{
+    if (!ctx || !u_host || n != (size_t)ctx->N * ctx->N) return FCH_EINVAL;
+    CKC(ctx, cudaMemcpyAsync(ctx->staging, u_host, sizeof(double) * n, cudaMemcpyHostToDevice, ctx->stream));
+    TRY(set_state_common(ctx, ctx->staging, true));
+    return fch_synchronize(ctx);
+}
+
+extern "C" fch_status fch_set_state_device(fch_ctx *ctx, const void *u_dev, int dtype)
+{
+    if (!ctx || !u_dev || (dtype != 0 && dtype != 1)) return FCH_EINVAL;
+    return set_state_common(ctx, u_dev, dtype == 0);
+}
+
+extern "C" fch_status fch_set_history(fch_ctx *ctx, const double *un, const double *unm1, size_t n,
+                                      double kn)
+{
+    if (!ctx || !un || !unm1 || n != (size_t)ctx->N * ctx->N || !(kn > 0)) return FCH_EINVAL;
+    reset_ctrl(ctx);
+    ctx->hc.kn = kn;
+    ctx->hc.ktrial = kn;
+    TRY(push_ctrl(ctx));
+    CKC(ctx, cudaMemcpyAsync(ctx->staging, un, sizeof(double) * n, cudaMemcpyHostToDevice, ctx->stream));
+    CKC(ctx, cudaMemcpyAsync(ctx->staging + n, unm1, sizeof(double) * n, cudaMemcpyHostToDevice,
+                             ctx->stream));
+    TRY(load_field(ctx, ctx->staging, true, ctx->U[0]));
+    TRY(load_field(ctx, ctx->staging + n, true, ctx->U[1]));
+    TRY(sav_r_init(ctx, FCH_SRC_UN, 1.0));
+    TRY(sav_r_init(ctx, 5, 2.0));
+    ctx->have_state = true;
+    ctx->failed = false;
+    ctx->have_F = false;
+    return fch_synchronize(ctx);
+}
+
+// u^n -> real field (device; f64 when io64)
+static fch_status store_state(fch_ctx *ctx, void *u_dev, bool io64)
+{
+    TRY(col(ctx, CM_START, FCH_SRC_UN, FCH_FL_NOSKIP));
+    TRY(row(ctx, RM_C2R_STORE, FCH_FL_NOSKIP | (io64 ? FCH_FL_F64IO : 0), nullptr, u_dev));
+    return FCH_OK;
+}
+
+extern "C" fch_status fch_get_state(fch_ctx *ctx, double *u_host, size_t n)
+{
+    if (!ctx || !u_host || n != (size_t)ctx->N * ctx->N) return FCH_EINVAL;
+    if (!ctx->have_state) return FCH_ESTATE;
+    TRY(store_state(ctx, ctx->staging, true));
+    CKC(ctx, cudaMemcpyAsync(u_host, ctx->staging, sizeof(double) * n, cudaMemcpyDeviceToHost, ctx->stream));
+    return fch_synchronize(ctx);
+}
+
+extern "C" fch_status fch_get_state_device(fch_ctx *ctx, void *u_dev, int dtype)
+{
+    if (!ctx || !u_dev || (dtype != 0 && dtype != 1)) return FCH_EINVAL;
+    if (!ctx->have_state) return FCH_ESTATE;
+    return store_state(ctx, u_dev, dtype == 0);
+}
+
+// one trial step from the current history into the trial slot (parameters already
+// in the control block). pack_f: leave (u_new, Lap u_new) packed for F(u_new).
+static fch_status enqueue_trial(fch_ctx *ctx, fch_scheme scheme, bool pack_f)
+{
+    const int pf = pack_f ? FCH_FL_PACK_F : 0;
+    const fch_geom &g = ctx->geom;
+    switch (scheme) {
+    case FCH_IMEX:
+        TRY(col(ctx, CM_START, 4));
+        TRY(row(ctx, RM_NIMEX));
+        TRY(col(ctx, CM_IMEX_SOLVE, 0, pf));
+        return FCH_OK;
+    case FCH_SAV:
+        TRY(col(ctx, CM_START, 4));
+        TRY(row(ctx, RM_SAV));
+        TRY(ctl(ctx, OP_SAV_E1, g.row_blocks, 0.0));
+        TRY(col(ctx, CM_SAV_PQ));
+        TRY(ctl(ctx, OP_SAV_R, g.col_blocks));
+        TRY(col(ctx, CM_SAV_COMBINE, 0, pf));
+        return FCH_OK;
+    case FCH_ETD:
+        TRY(col(ctx, CM_START, FCH_SRC_UN));
+        TRY(row(ctx, RM_NIMEX));
+        TRY(col(ctx, CM_ETD_STAGE1));
+        TRY(row(ctx, RM_NIMEX));
+        TRY(col(ctx, CM_ETD_STAGE2, 0, pf));
+        return FCH_OK;
+    case FCH_PSD: {
+        TRY(col(ctx, CM_START, 4, 128));
+        const int chunk = 4;
+        for (int guard = 0;; guard++) {
+            if (guard * chunk > ctx->p.psd_max_iter + 2 * chunk) return FCH_ENOCONV;
+            for (int i = 0; i < chunk; i++) {
+                TRY(row(ctx, RM_F, FCH_FL_PSDSKIP));
+                TRY(col(ctx, CM_PSD_ITER, 0, FCH_FL_PSDSKIP));
+                TRY(ctl(ctx, OP_PSD_CHECK, g.col_blocks));
+            }
+            TRY(pull_ctrl(ctx));
+            if (ctx->hc.status || ctx->hc.done || ctx->hc.psd_conv) break;
+        }
+        if (ctx->hc.status) return (fch_status)ctx->hc.status;
+        // trial = converged iterate
+        TRY(col(ctx, CM_START, FCH_SRC_V, FCH_FL_COPYV));
+        return FCH_OK;
+    }
+    }
+    return FCH_EINVAL;
+}
+
+extern "C" fch_status fch_step(fch_ctx *ctx, fch_scheme scheme, double dt)
+{
+    if (!ctx || !(dt > 0) || scheme < FCH_IMEX || scheme > FCH_ETD) return FCH_EINVAL;
+    if (!ctx->have_state || ctx->failed) return FCH_ESTATE;
+    TRY(ctl(ctx, OP_INIT_TRIAL, 0, dt));
+    fch_status s = enqueue_trial(ctx, scheme, false);
+    if (s != FCH_OK) {
+        ctx->failed = true;
+        return s;
+    }
+    TRY(ctl(ctx, OP_ACCEPT, 0, 0.0));
+    ctx->have_F = false;
+    return FCH_OK;
+}
+
+// F of the state in slot src into its F slot (src: FCH_SRC_UN -> F(u^n), 5 -> F(u^{n-1}))
+static fch_status eval_F(fch_ctx *ctx, int src)
+{
+    TRY(col(ctx, CM_START, src));
+    TRY(row(ctx, RM_F));
+    TRY(col(ctx, CM_F_FINISH, src));
+    return FCH_OK;
+}
+
+static void fill_stats(fch_ctx *ctx, fch_stats *st)
+{
+    st->n_steps = ctx->hc.n_steps;
+    st->n_rejects = ctx->hc.n_rejects;
+    st->n_attempts = ctx->hc.n_attempts;
+    st->n_psd_iter = ctx->hc.n_psd_iter;
+    long long nf = 0;
+    cudaMemcpy(&nf, ctx->nfft_dev, sizeof(long long), cudaMemcpyDeviceToHost);
+    st->n_fft = nf;
+    st->t = ctx->hc.t;
+    st->k_last = ctx->hc.kn;
+    st->e_last = ctx->hc.e_last;
+    st->last_psd_iter = ctx->hc.last_psd_iter;
+}
+
+extern "C" fch_status fch_adaptive_begin(fch_ctx *ctx, fch_scheme scheme, double sigma,
+                                         double t_final)
+{
+    if (!ctx || !(sigma > 0) || scheme < FCH_IMEX || scheme > FCH_ETD) return FCH_EINVAL;
+    if (!ctx->have_state || ctx->failed) return FCH_ESTATE;
+    TRY(pull_ctrl(ctx));
+    if (ctx->hc.status) {
+        ctx->failed = true;
+        return (fch_status)ctx->hc.status;
+    }
+    if (!(t_final >= ctx->hc.t)) return FCH_EINVAL;
+    fch_ctrl &c = ctx->hc;
+    c.sigma = sigma;
+    c.t_final = t_final;
+    c.kmax = scheme == FCH_PSD ? fmin(ctx->p.k_max, ctx->p.psd_k_max) : ctx->p.k_max;
+    c.itol = ctx->p.psd_nu * sigma;
+    c.done = 0;
+    c.adaptive = 1;
+    TRY(push_ctrl(ctx));
+    ctx->ad_scheme = scheme;
+    ctx->ad_open = true;
+    if (c.kn <= 0) {
+        // first step k_1 = k_min by the backward-Euler start (Sec. 3.2)
+        TRY(eval_F(ctx, FCH_SRC_UN));
+        TRY(ctl(ctx, OP_INIT_TRIAL, 0, ctx->p.k_min));
+        fch_status s = enqueue_trial(ctx, scheme, true);
+        if (s != FCH_OK) {
+            ctx->failed = true;
+            return s;
+        }
+        TRY(row(ctx, RM_F));
+        TRY(col(ctx, CM_F_FINISH, FCH_SRC_UNEW));
+        TRY(ctl(ctx, OP_ACCEPT, 0, 1.0));
+    } else if (!ctx->have_F) {
+        TRY(eval_F(ctx, FCH_SRC_UN));
+        TRY(eval_F(ctx, 5));
+    }
+    ctx->have_F = true;
+    return FCH_OK;
+}
+
+extern "C" fch_status fch_adaptive_enqueue(fch_ctx *ctx, int n)
+{
+    if (!ctx || n < 0) return FCH_EINVAL;
+    if (!ctx->ad_open || ctx->failed) return FCH_ESTATE;
+    for (int i = 0; i < n; i++) {
+        TRY(ctl(ctx, OP_INIT_TRIAL, 0, -1.0));
+        fch_status s = enqueue_trial(ctx, ctx->ad_scheme, true);
+        if (s != FCH_OK) {
+            ctx->failed = true;
+            return s;
+        }
+        TRY(row(ctx, RM_F));
+        TRY(col(ctx, CM_F_FINISH, FCH_SRC_UNEW, FCH_FL_AM3));
+        TRY(ctl(ctx, OP_DECIDE, ctx->geom.col_blocks));
+    }
+    return FCH_OK;
+}
+
+extern "C" fch_status fch_adaptive_end(fch_ctx *ctx, fch_stats *stats)
+{
+    if (!ctx) return FCH_EINVAL;
+    TRY(pull_ctrl(ctx));
+    fch_status result = FCH_OK;
+    if (ctx->hc.status) {
+        ctx->failed = true;
+        result = (fch_status)ctx->hc.status;
+    }
+    // leave the control block ready for further calls
+    fch_ctrl &c = ctx->hc;
+    c.done = 0;
+    c.adaptive = 0;
+    c.itol = ctx->p.psd_itol;
+    c.kmax = ctx->p.k_max;
+    TRY(push_ctrl(ctx));
+    TRY(pull_ctrl(ctx));
+    ctx->ad_open = false;
+    if (stats) fill_stats(ctx, stats);
+    return result;
+}
+
+extern "C" fch_status fch_run_adaptive(fch_ctx *ctx, fch_scheme scheme, double sigma, double t_final,
+                                       long long max_attempts, fch_stats *stats)
+{
+    const long long att0 = ctx && ctx->have_state ? (pull_ctrl(ctx), ctx->hc.n_attempts) : 0;
+    TRY(fch_adaptive_begin(ctx, scheme, sigma, t_final));
+    fch_status result = FCH_OK;
+    for (;;) {
+        fch_status s = pull_ctrl(ctx);
+        if (s != FCH_OK) return s;
+        const fch_ctrl &c = ctx->hc;
+        if (c.status || c.done) break;
+        const long long used = c.n_attempts - att0;
+        if (max_attempts > 0 && used >= max_attempts) {
+            result = FCH_ETIMEOUT;
+            break;
+        }
+        long long nb = scheme == FCH_PSD ? 1 : ctx->p.sync_every;
+        if (max_attempts > 0 && nb > max_attempts - used) nb = max_attempts - used;
+        s = fch_adaptive_enqueue(ctx, (int)nb);
+        if (s != FCH_OK) {
+            ctx->ad_open = false;
+            return s;
+        }
+    }
+    fch_status e = fch_adaptive_end(ctx, stats);
+    return e != FCH_OK ? e : result;
+}
+
+extern "C" fch_status fch_pass_timing(fch_ctx *ctx, int on)
+{
+    if (!ctx) return FCH_EINVAL;
+    if (on && !ctx->timing) {
+        for (int i = 0; i < 2 * 2048; i++)
+            CKC(ctx, cudaEventCreate(&ctx->ev[i]));
+        ctx->nev = 0;
+        memset(ctx->t_ms, 0, sizeof(ctx->t_ms));
+        memset(ctx->t_n, 0, sizeof(ctx->t_n));
+        ctx->timing = true;
+    } else if (!on && ctx->timing) {
+        timing_flush(ctx);
+        for (int i = 0; i < 2 * 2048; i++) cudaEventDestroy(ctx->ev[i]);
+        ctx->timing = false;
+    }
+    return FCH_OK;
+}
+
+extern "C" fch_status fch_pass_times(fch_ctx *ctx, double *ms, long long *launches, int n)
+{
+    if (!ctx || !ms || !launches || n < FCH_NPASS) return FCH_EINVAL;
+    timing_flush(ctx);
+    for (int i = 0; i < FCH_NPASS; i++) {
+        ms[i] = ctx->t_ms[i];
+        launches[i] = ctx->t_n[i];
+        ctx->t_ms[i] = 0;
+        ctx->t_n[i] = 0;
+    }
+    return FCH_OK;
+}
+
+extern "C" fch_status fch_get_stats(fch_ctx *ctx, fch_stats *st)
+{
+    if (!ctx || !st) return FCH_EINVAL;
+    TRY(pull_ctrl(ctx));
+    fill_stats(ctx, st);
+    return FCH_OK;
+}
+
+extern "C" fch_status fch_energy(fch_ctx *ctx, double *E)
+{
+    if (!ctx || !E) return FCH_EINVAL;
+    if (!ctx->have_state) return FCH_ESTATE;
+    TRY(col(ctx, CM_START, FCH_SRC_UN, FCH_FL_NOSKIP));
+    TRY(row(ctx, RM_ENERGY, FCH_FL_NOSKIP));
+    TRY(ctl(ctx, OP_ENERGY, ctx->geom.row_blocks, 0.0, FCH_FL_NOSKIP));
+    TRY(fch_synchronize(ctx));
+    *E = ctx->hc.energy;
+    return FCH_OK;
+}
+
+extern "C" fch_status fch_mass(fch_ctx *ctx, double *m)
+{
+    if (!ctx || !m) return FCH_EINVAL;
+    if (!ctx->have_state) return FCH_ESTATE;
+    TRY(fch_synchronize(ctx));
+    double re;
+    const void *u0 = ctx->U[ctx->hc.iu_n];
+    if (ctx->prec) {
+        float v[2];
+        CKC(ctx, cudaMemcpy(v, u0, sizeof(v), cudaMemcpyDeviceToHost));
+        re = v[0];
+    } else {
+        double v[2];
+        CKC(ctx, cudaMemcpy(v, u0, sizeof(v), cudaMemcpyDeviceToHost));
+        re = v[0];
+    }
+    // m = 1/2 int (u + 1) = 1/2 (h^2 sum u + L^2), sum u = the k = 0 coefficient
+    const double L = ctx->grid.L;
+    *m = 0.5 * (ctx->kp.h2 * re + L * L);
+    return FCH_OK;
+}
+
+extern "C" fch_status fch_rhs_device(fch_ctx *ctx, const void *u_dev, void *F_dev, int dtype)
+{
+    if (!ctx || !u_dev || !F_dev || (dtype != 0 && dtype != 1)) return FCH_EINVAL;
+    const int io = (dtype == 0 ? FCH_FL_F64IO : 0) | FCH_FL_NOSKIP;
+    TRY(row(ctx, RM_R2C_LOAD, io, u_dev));
+    TRY(col(ctx, CM_FWD_STORE, 0, FCH_FL_NOSKIP, nullptr, nullptr, ctx->Pb, nullptr));
+    TRY(col(ctx, CM_START, FCH_SRC_IN0, FCH_FL_NOSKIP, ctx->Pb));
+    TRY(row(ctx, RM_F, FCH_FL_NOSKIP));
+    TRY(col(ctx, CM_F_FINISH, FCH_SRC_IN0, FCH_FL_NOSKIP, ctx->Pb, nullptr, ctx->Qb));
+    TRY(col(ctx, CM_INV_LOAD, 0, FCH_FL_NOSKIP, ctx->Qb));
+    TRY(row(ctx, RM_C2R_STORE, io, nullptr, F_dev));
+    return FCH_OK;
+}
+
+extern "C" fch_status fch_get_sav_r(fch_ctx *ctx, double *r_n, double *r_nm1)
+{
+    if (!ctx || !r_n || !r_nm1) return FCH_EINVAL;
+    TRY(fch_synchronize(ctx));
+    *r_n = ctx->hc.r_n;
+    *r_nm1 = ctx->hc.r_m;
+    return FCH_OK;
+}
+
+// ---------------------------------------------------------------------------
+// standalone transforms
+struct fch_fft_plan {
+    int N, prec;
+    cudaStream_t stream;
+    fch_geom geom;
+    fch_kparams kp;
+    void *Z, *tw;
+};
+
+extern "C" fch_status fch_fft_plan_create(int n, int prec, void *stream, fch_fft_plan **out)
+{
+    if (!out || !pow2_in_range(n) || (prec != 0 && prec != 1)) return FCH_EINVAL;
+    fch_fft_plan *pl = (fch_fft_plan *)calloc(1, sizeof(fch_fft_plan));
+    if (!pl) return FCH_ENOMEM;
+    pl->N = n;
+    pl->prec = prec;
+    pl->stream = (cudaStream_t)stream;
+    pl->geom = fch_geometry(n, prec);
+    const size_t csz = prec ? 8 : 16;
+    cudaError_t e = cudaMalloc(&pl->Z, (size_t)n * n * csz);
+    if (e == cudaSuccess) e = cudaMalloc(&pl->tw, (size_t)n * csz);
+    if (e != cudaSuccess) {
+        fch_fft_plan_destroy(pl);
+        return e == cudaErrorMemoryAllocation ? FCH_ENOMEM : FCH_ECUDA;
+    }
+    fch_ctx dummy;
+    if (upload_twiddles(&dummy, n, prec, pl->tw, pl->stream) != FCH_OK) {
+        fch_fft_plan_destroy(pl);
+        return FCH_ECUDA;
+    }
+    memset(&pl->kp, 0, sizeof(pl->kp));
+    pl->kp.N = n;
+    pl->kp.logN = ilog2(n);
+    pl->kp.P = pl->geom.P;
+    pl->kp.inv_n2 = 1.0 / ((double)n * n);
+    pl->kp.Z = pl->Z;
+    pl->kp.tw = pl->tw;
+    *out = pl;
+    return FCH_OK;
+}
+
+extern "C" fch_status fch_fft_plan_destroy(fch_fft_plan *pl)
+{
+    if (!pl) return FCH_OK;
+    if (pl->Z) cudaFree(pl->Z);
+    if (pl->tw) cudaFree(pl->tw);
+    free(pl);
+    return FCH_OK;
+}
+
+static cudaError_t plan_pass(fch_fft_plan *pl, bool is_col, int mode, const void *in0, const void *in1,
+                             void *out0, void *out1)
+{
+    fch_kparams kp = pl->kp;
+    kp.flags = FCH_FL_NOSKIP | (pl->prec ? 0 : FCH_FL_F64IO);
+    kp.in0 = in0;
+    kp.in1 = in1;
+    kp.out0 = out0;
+    kp.out1 = out1;
+    cudaError_t e;
+    if (is_col)
+        e = pl->prec ? fch_launch_col_f32(mode, kp, pl->stream) : fch_launch_col_f64(mode, kp, pl->stream);
+    else
+        e = pl->prec ? fch_launch_row_f32(mode, kp, pl->stream) : fch_launch_row_f64(mode, kp, pl->stream);
+    if (e != cudaSuccess)
+        snprintf(g_plan_err, sizeof(g_plan_err), "%s pass %d: %s", is_col ? "column" : "row", mode,
+                 cudaGetErrorString(e));
+    return e;
+}
+
+extern "C" fch_status fch_fft_r2c(fch_fft_plan *pl, const void *x, void *X, int batch)
+{
+    if (!pl || !x || !X || batch < 0) return FCH_EINVAL;
+    const size_t N = pl->N, rb = N * N * (pl->prec ? 4 : 8), cb = (N / 2 + 1) * N * (pl->prec ? 8 : 16);
+    for (int b = 0; b < batch; b += 2) {
+        const char *x0 = (const char *)x + b * rb;
+        const char *x1 = b + 1 < batch ? x0 + rb : nullptr;
+        char *X0 = (char *)X + b * cb;
+        char *X1 = b + 1 < batch ? X0 + cb : nullptr;
+        if (plan_pass(pl, false, RM_R2C_LOAD, x0, x1, nullptr, nullptr) != cudaSuccess) return FCH_ECUDA;
+        if (plan_pass(pl, true, CM_FWD_STORE, nullptr, nullptr, X0, X1) != cudaSuccess) return FCH_ECUDA;
+    }
+    return FCH_OK;
+}
+
+extern "C" fch_status fch_fft_c2r(fch_fft_plan *pl, const void *X, void *x, int batch)
+{
+    if (!pl || !x || !X || batch < 0) return FCH_EINVAL;
+    const size_t N = pl->N, rb = N * N * (pl->prec ? 4 : 8), cb = (N / 2 + 1) * N * (pl->prec ? 8 : 16);
+    for (int b = 0; b < batch; b += 2) {
+        const char *X0 = (const char *)X + b * cb;
+        const char *X1 = b + 1 < batch ? X0 + cb : nullptr;
+        char *x0 = (char *)x + b * rb;
+        char *x1 = b + 1 < batch ? x0 + rb : nullptr;
+        if (plan_pass(pl, true, CM_INV_LOAD, X0, X1, nullptr, nullptr) != cudaSuccess) return FCH_ECUDA;
+        if (plan_pass(pl, false, RM_C2R_STORE, nullptr, nullptr, x0, x1) != cudaSuccess) return FCH_ECUDA;
+    }
+    return FCH_OK;
+}
+
+// host-side geometry query (used by the CPU tests of the launch configuration)
+extern "C" int fch_debug_geometry(int n, int prec, int *out)
+{
+    if (!pow2_in_range(n) || !out) return 1;
+    const fch_geom g = fch_geometry(n, prec);
+    out[0] = g.col_blocks;
+    out[1] = g.col_threads;
+    out[2] = g.col_smem;
+    out[3] = g.row_blocks;
+    out[4] = g.row_threads;
+    out[5] = g.row_smem;
+    out[6] = g.rpb;
+    out[7] = g.P;
+    out[8] = (int)sizeof(fch_ctrl);
+    return 0;
+}

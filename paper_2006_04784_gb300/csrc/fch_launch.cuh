@@ -1,0 +1,74 @@
+// fch_launch.cuh -- host launchers of the column and row passes for one precision.
+// Included once per precision by fch_f64.cu / fch_f32.cu with FCH_T and FCH_SUFFIX set.
+#include "fch_kernels.cuh"
+
+namespace {
+
+typedef void (*pass_fn)(const fch_kparams);
+
+// Raise the kernel's dynamic shared-memory limit once, to what the largest grid
+// (FCH_MAX_N) needs, so every smaller launch fits under it.
+template <typename T, int M> cudaError_t set_smem(pass_fn f, int bytes, bool &done)
+{
+    if (done) return cudaSuccess;
+    cudaError_t e = cudaFuncSetAttribute((const void *)f, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    if (e == cudaSuccess) done = true;
+    return e;
+}
+
+template <typename T, int M> cudaError_t launch_col(const fch_kparams &kp, cudaStream_t s)
+{
+    static bool attr = false;
+    const fch_geom g = fch_geometry(kp.N, sizeof(T) == 4);
+    pass_fn f = fch::col_pass<T, M>;
+    cudaError_t e = set_smem<T, M>(f, fch_geometry(FCH_MAX_N, sizeof(T) == 4).col_smem, attr);
+    if (e != cudaSuccess) return e;
+    f<<<g.col_blocks, g.col_threads, g.col_smem, s>>>(kp);
+    return cudaGetLastError();
+}
+
+template <typename T, int M> cudaError_t launch_row(const fch_kparams &kp, cudaStream_t s)
+{
+    static bool attr = false;
+    const fch_geom g = fch_geometry(kp.N, sizeof(T) == 4);
+    pass_fn f = fch::row_pass<T, M>;
+    cudaError_t e = set_smem<T, M>(f, fch_geometry(FCH_MAX_N, sizeof(T) == 4).row_smem, attr);
+    if (e != cudaSuccess) return e;
+    f<<<g.row_blocks, g.row_threads, g.row_smem, s>>>(kp);
+    return cudaGetLastError();
+}
+
+} // namespace
+
+#define FCH_CAT2(a, b) a##b
+#define FCH_CAT(a, b) FCH_CAT2(a, b)
+
+cudaError_t FCH_CAT(fch_launch_col_, FCH_SUFFIX)(int mode, const fch_kparams &kp, cudaStream_t s)
+{
+    switch (mode) {
+    case CM_FWD_STORE: return launch_col<FCH_T, CM_FWD_STORE>(kp, s);
+    case CM_INV_LOAD: return launch_col<FCH_T, CM_INV_LOAD>(kp, s);
+    case CM_START: return launch_col<FCH_T, CM_START>(kp, s);
+    case CM_IMEX_SOLVE: return launch_col<FCH_T, CM_IMEX_SOLVE>(kp, s);
+    case CM_F_FINISH: return launch_col<FCH_T, CM_F_FINISH>(kp, s);
+    case CM_SAV_PQ: return launch_col<FCH_T, CM_SAV_PQ>(kp, s);
+    case CM_SAV_COMBINE: return launch_col<FCH_T, CM_SAV_COMBINE>(kp, s);
+    case CM_PSD_ITER: return launch_col<FCH_T, CM_PSD_ITER>(kp, s);
+    case CM_ETD_STAGE1: return launch_col<FCH_T, CM_ETD_STAGE1>(kp, s);
+    case CM_ETD_STAGE2: return launch_col<FCH_T, CM_ETD_STAGE2>(kp, s);
+    }
+    return cudaErrorInvalidValue;
+}
+
+cudaError_t FCH_CAT(fch_launch_row_, FCH_SUFFIX)(int mode, const fch_kparams &kp, cudaStream_t s)
+{
+    switch (mode) {
+    case RM_R2C_LOAD: return launch_row<FCH_T, RM_R2C_LOAD>(kp, s);
+    case RM_C2R_STORE: return launch_row<FCH_T, RM_C2R_STORE>(kp, s);
+    case RM_NIMEX: return launch_row<FCH_T, RM_NIMEX>(kp, s);
+    case RM_F: return launch_row<FCH_T, RM_F>(kp, s);
+    case RM_SAV: return launch_row<FCH_T, RM_SAV>(kp, s);
+    case RM_ENERGY: return launch_row<FCH_T, RM_ENERGY>(kp, s);
+    }
+    return cudaErrorInvalidValue;
+}

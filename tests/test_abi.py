@@ -1,0 +1,107 @@
+"""CPU checks of the C ABI: the library builds, loads and exports every symbol
+include/fch.h declares; launch geometry fits its buffers; argument checks that
+return before any device work."""
+import ctypes as C
+import os
+import re
+
+import pytest
+
+from paper_2006_04784_gb300 import build as B
+from paper_2006_04784_gb300 import fch
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    B.build()
+
+
+def declared_symbols():
+    src = open(os.path.join(ROOT, "include", "fch.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(fch_[a-z0-9_]+)\s*\(", src)))
+
+
+def test_every_declared_symbol_is_exported():
+    syms = declared_symbols()
+    assert len(syms) >= 20
+    L = C.CDLL(fch.LIB_PATH)
+    for s in syms:
+        assert hasattr(L, s), s
+    assert sorted(fch.EXPORTS) == syms
+
+
+def test_status_strings():
+    L = fch.lib()
+    for s in range(8):
+        assert L.fch_status_string(s)
+    assert L.fch_status_string(99) == b"unknown status"
+
+
+@pytest.mark.parametrize("n", [16, 32, 64, 128, 256, 512, 1024, 2048])
+@pytest.mark.parametrize("prec", [0, 1])
+def test_geometry_covers_grid(n, prec):
+    g = fch.geometry(n, prec)
+    csz = 8 if prec else 16
+    # column pass: P pairs per block, 2P sequences of N/8 threads, all N/2 pairs covered
+    assert g["col_blocks"] * g["P"] == n // 2
+    assert g["col_threads"] == 2 * g["P"] * (n // 8) and g["col_threads"] <= 1024
+    assert g["col_threads"] % 32 == 0
+    assert g["col_smem"] == (n + 2 * g["P"] * n) * csz and g["col_smem"] <= 227 * 1024
+    # row pass: rpb rows of N/8 threads, all N rows covered
+    assert g["row_blocks"] * g["rpb"] == n
+    assert g["row_threads"] == g["rpb"] * (n // 8) and g["row_threads"] <= 256
+    assert g["row_threads"] % 32 == 0
+    assert g["row_smem"] == (n + g["rpb"] * n) * csz and g["row_smem"] <= 227 * 1024
+    # per-block partial sums fit their slots (FCH_MAXBLK = 4096)
+    assert max(g["row_blocks"], g["col_blocks"]) <= 4096
+
+
+def test_stockham_index_map_is_a_permutation():
+    # the store index of every Stockham stage (fft_smem) is a bijection on [0, N)
+    for logn in range(4, 12):
+        n = 1 << logn
+        tps = n // 8
+        ns, lns, rem = 1, 0, logn
+        while rem > 0:
+            lr = 3 if rem >= 3 else rem
+            r_ = 1 << lr
+            seen = set()
+            for t in range(tps):
+                for i in range(8):
+                    b, r = i >> lr, i & (r_ - 1)
+                    j = t + b * tps
+                    assert j + r * (n >> lr) < n  # load index in range
+                    idx = ((j >> lns) << (lns + lr)) + (j & (ns - 1)) + r * ns
+                    assert 0 <= idx < n
+                    seen.add(idx)
+            assert len(seen) == n
+            ns <<= lr
+            lns += lr
+            rem -= lr
+
+
+def test_params_default_paper_constants():
+    p = fch.params_default(0.2)
+    assert p.eps == 0.1 and p.gamma == 0.3 and p.b_minus == -1 and p.b_plus == 1
+    assert p.eta1 == pytest.approx(0.145) and p.eta2 == pytest.approx(0.3)
+    assert (p.beta1, p.beta2, p.kappa0, p.kappa2, p.rho_s, p.k_min) == (2, 1, 1e-2, 15, 0.9, 1e-9)
+    assert p.psd_nu == 2e-5 and p.psd_k_max == 0.02
+
+
+def test_create_rejects_bad_arguments_before_device_work():
+    L = fch.lib()
+    p = fch.params_default(0.0)
+    h = C.c_void_p()
+    for n in (0, 8, 100, 4096, 3000):
+        g = fch.Grid(n, 4.0, 0.0)
+        assert L.fch_create(C.byref(g), C.byref(p), None, C.byref(h)) == 1
+    g = fch.Grid(64, -1.0, 0.0)
+    assert L.fch_create(C.byref(g), C.byref(p), None, C.byref(h)) == 1
+    bad = fch.params_default(0.0, eps=0.0)
+    g = fch.Grid(64, 4.0, 0.0)
+    assert L.fch_create(C.byref(g), C.byref(bad), None, C.byref(h)) == 1
+    assert L.fch_step(None, 0, 1e-3) == 1
+    assert L.fch_fft_plan_create(100, 0, None, C.byref(h)) == 1

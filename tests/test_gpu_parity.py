@@ -1,0 +1,268 @@
+"""GPU parity: the CUDA path (through the C ABI) against the FP64 CPU oracle.
+
+Tolerances: FP64 1e-10 relative L2 per step (1e-12 for one step from identical
+history), mixed precision 3e-5 relative L2 per step (single-precision transforms
+of fields with ~1e2 dynamic range in the symbols), transforms 1e-13 (FP64) and
+2e-6 (FP32) relative to the field norm.
+"""
+import math
+
+import numpy as np
+import pytest
+
+from oracle import oracle as O
+from paper_2006_04784_gb300 import inputs as I
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():  # pragma: no cover
+    pytest.skip("needs a CUDA device", allow_module_level=True)
+
+from paper_2006_04784_gb300 import build as B  # noqa: E402
+
+B.build()
+from paper_2006_04784_gb300 import fch  # noqa: E402
+
+L = 4 * math.pi
+DEV = torch.device("cuda:0")
+
+
+def rel(a, b):
+    return float(np.linalg.norm(a - b) / np.linalg.norm(b))
+
+
+def oparams(fp, **kw):
+    """oracle parameters equal to the library's effective fch_params"""
+    d = dict(eps=fp.eps, q=fp.q, gamma=fp.gamma, b_minus=fp.b_minus, b_plus=fp.b_plus,
+             eta1=fp.eta1, eta2=fp.eta2, beta1=fp.beta1, beta2=fp.beta2, zeta=fp.zeta, D0=fp.D0,
+             kappa0=fp.kappa0, kappa2=fp.kappa2, rho_s=fp.rho_s, k_min=fp.k_min, k_max=fp.k_max,
+             zero_stab_cap=fp.zero_stab_cap, well=0, psd_nu=fp.psd_nu, psd_itol=fp.psd_itol,
+             psd_lambda=fp.psd_lambda, psd_max_iter=fp.psd_max_iter)
+    d.update(kw)
+    return O.params(**d)
+
+
+def lib_params(q=0.0, **kw):
+    p = fch.params_default(q, **kw)
+    if p.zeta <= 0:
+        p.zeta = 1.1 if q < 0.35 else 1.8
+    if p.D0 <= 0:
+        p.D0 = 170.0
+    return p
+
+
+# --------------------------------------------------------------------------- transforms
+@pytest.mark.parametrize("n", [16, 32, 64, 128, 256])
+@pytest.mark.parametrize("prec", [0, 1])
+def test_fft_r2c_c2r_vs_oracle(n, prec):
+    batch = 3  # odd: the last pair carries one field
+    rng = np.random.default_rng(n + prec)
+    x = rng.standard_normal((batch, n, n))
+    dt = torch.float64 if prec == 0 else torch.float32
+    cdt = torch.complex128 if prec == 0 else torch.complex64
+    xt = torch.tensor(x, dtype=dt, device=DEV)
+    X = torch.empty((batch, n // 2 + 1, n), dtype=cdt, device=DEV)
+    plan = fch.FFTPlan(n, prec)
+    plan.r2c(xt, X)
+    back = torch.empty_like(xt)
+    plan.c2r(X, back)
+    torch.cuda.synchronize()
+    Xh = X.cpu().numpy()
+    tol = 1e-13 if prec == 0 else 2e-6
+    for b in range(batch):
+        ref = O.fft2(x[b], -1)[:, : n // 2 + 1].T  # kx-major half spectrum
+        assert np.abs(Xh[b] - ref).max() <= tol * np.abs(ref).max() * math.log2(n)
+    assert np.abs(back.cpu().numpy() - x).max() <= tol * 10 * np.abs(x).max()
+
+
+@pytest.mark.parametrize("n,prec", [(1024, 0), (2048, 0), (1024, 1), (2048, 1)])
+def test_fft_full_size_sampled_outputs(n, prec):
+    rng = np.random.default_rng(7)
+    x = rng.standard_normal((n, n))
+    dt = torch.float64 if prec == 0 else torch.float32
+    cdt = torch.complex128 if prec == 0 else torch.complex64
+    xt = torch.tensor(x, dtype=dt, device=DEV)
+    X = torch.empty((1, n // 2 + 1, n), dtype=cdt, device=DEV)
+    plan = fch.FFTPlan(n, prec)
+    plan.r2c(xt[None], X)
+    torch.cuda.synchronize()
+    Xh = X[0].cpu().numpy()
+    idx = np.arange(n)
+    scale = math.sqrt(n * n)  # typical |X| of unit white noise
+    for kx, ky in [(0, 0), (1, 0), (0, 1), (n // 2, 0), (n // 2, n // 2), (3, n - 5),
+                   (n // 2 - 1, 17), (200, 999 % n)]:
+        ex = np.exp(-2j * np.pi * kx * idx / n)
+        ey = np.exp(-2j * np.pi * ky * idx / n)
+        ref = ey @ x @ ex  # direct DFT of one output
+        tol = 1e-12 if prec == 0 else 3e-6
+        assert abs(Xh[kx, ky] - ref) <= tol * scale * math.log2(n)
+    back = torch.empty_like(xt)
+    plan.c2r(X, back[None])
+    torch.cuda.synchronize()
+    assert np.abs(back.cpu().numpy() - x).max() <= (1e-12 if prec == 0 else 3e-5)
+
+
+# --------------------------------------------------------------------------- F(u)
+@pytest.mark.parametrize("q", [0.0, 0.5])
+def test_rhs_vs_oracle(q):
+    n = 64
+    p = lib_params(q)
+    u = I.circle_bilayer(n, noise=1e-2)
+    with fch.Context(n, p) as ctx:
+        ut = torch.tensor(u, device=DEV)
+        F = torch.empty_like(ut)
+        torch.cuda.synchronize()  # the context runs on its own stream
+        ctx.rhs_device(ut, F)
+        ctx.synchronize()
+        ref = O.rhs(oparams(p), u, L)
+        assert rel(F.cpu().numpy(), ref) < 1e-11
+
+
+# --------------------------------------------------------------------------- state io, energy, mass
+def test_state_roundtrip_energy_mass():
+    n = 128
+    p = lib_params(0.2)
+    u = I.circle_bilayer(n)
+    with fch.Context(n, p) as ctx:
+        ctx.set_state(u)
+        assert np.abs(ctx.get_state() - u).max() < 1e-13
+        op = oparams(p)
+        assert ctx.energy() == pytest.approx(O.energy(op, u, L), rel=1e-11)
+        assert ctx.mass() == pytest.approx(O.mass(u, L), rel=1e-13)
+        t = torch.tensor(u, device=DEV, dtype=torch.float32)
+        torch.cuda.synchronize()  # the context runs on its own stream
+        ctx.set_state_device(t)
+        out = torch.empty((n, n), device=DEV, dtype=torch.float64)
+        ctx.get_state_device(out)
+        ctx.synchronize()
+        assert np.abs(out.cpu().numpy() - t.double().cpu().numpy()).max() < 1e-13
+
+
+# --------------------------------------------------------------------------- fixed steps
+@pytest.mark.parametrize("scheme", ["imex", "sav", "psd", "etd"])
+def test_fixed_steps_fp64_vs_oracle(scheme):
+    n = 64
+    p = lib_params(0.0, psd_itol=1e-12)
+    u0 = I.circle_bilayer(n, noise=1e-3)
+    s = O.Stepper(n, L, oparams(p))
+    s.set_state(u0)
+    with fch.Context(n, p) as ctx:
+        ctx.set_state(u0)
+        for k in range(6):
+            dt = 1e-3 if k < 4 else 2e-3
+            s.step(scheme, dt)
+            ctx.step(scheme, dt)
+            got = ctx.get_state()
+            assert rel(got, s.state()) < 1e-10, (k, rel(got, s.state()))
+        if scheme == "sav":
+            rn, rm = ctx.sav_r()
+            assert rn == pytest.approx(s.r(0), rel=1e-11) and rm == pytest.approx(s.r(1), rel=1e-11)
+        if scheme == "psd":
+            assert ctx.stats()["last_psd_iter"] == s.counts()["last_psd_iter"]
+
+
+@pytest.mark.parametrize("scheme", ["imex", "sav", "psd", "etd"])
+def test_one_step_from_identical_history(scheme):
+    n = 32
+    p = lib_params(0.2, psd_itol=1e-13)
+    un = I.smooth_random(n, seed=3)
+    um = I.smooth_random(n, seed=4, amp=0.49)
+    s = O.Stepper(n, L, oparams(p))
+    s.set_history(un, um, 1e-3)
+    s.step(scheme, 1.5e-3)
+    with fch.Context(n, p) as ctx:
+        ctx.set_history(un, um, 1e-3)
+        ctx.step(scheme, 1.5e-3)
+        assert rel(ctx.get_state(), s.state()) < 1e-12
+
+
+def test_imex_128_fixed_dt_400_steps():
+    # the 128^2 fixed-step workload: circle of radius 2, d = 0.2, noise 1e-3 (seed 1)
+    n = 128
+    p = lib_params(0.0)
+    u0 = I.circle_bilayer(n)
+    s = O.Stepper(n, L, oparams(p))
+    s.set_state(u0)
+    with fch.Context(n, p) as ctx:
+        ctx.set_state(u0)
+        for k in range(400):
+            s.step("imex", 1e-3)
+            ctx.step("imex", 1e-3)
+            if k % 50 == 0 or k == 399:
+                assert rel(ctx.get_state(), s.state()) < 1e-10, k
+        assert ctx.mass() == pytest.approx(O.mass(u0, L), rel=1e-12)
+
+
+@pytest.mark.parametrize("scheme", ["imex", "etd"])
+def test_fixed_steps_mixed_precision(scheme):
+    n = 128
+    p = lib_params(0.0, prec=1)
+    u0 = I.circle_bilayer(n)
+    s = O.Stepper(n, L, oparams(p))
+    s.set_state(u0)
+    with fch.Context(n, p) as ctx:
+        ctx.set_state(u0)
+        for k in range(10):
+            s.step(scheme, 1e-3)
+            ctx.step(scheme, 1e-3)
+        assert rel(ctx.get_state(), s.state()) < 3e-5
+
+
+# --------------------------------------------------------------------------- adaptive
+@pytest.mark.parametrize("scheme", ["imex", "sav", "etd", "psd"])
+def test_adaptive_vs_oracle(scheme):
+    n = 64
+    p = lib_params(0.0, zero_stab_cap=1, k_max=0.05 if scheme == "psd" else float("inf"))
+    p.sync_every = 4
+    u0 = I.circle_bilayer(n, noise=1e-3)
+    tf = 0.01
+    s = O.Stepper(n, L, oparams(p))
+    s.set_state(u0)
+    rc = s.run_adaptive(scheme, 1e-5, tf)
+    assert rc == 0
+    with fch.Context(n, p) as ctx:
+        ctx.set_state(u0)
+        st = ctx.run_adaptive(scheme, 1e-5, tf)
+        c = s.counts()
+        assert st["n_steps"] == c["steps"] and st["n_rejects"] == c["rejects"]
+        assert st["t"] == pytest.approx(tf, rel=1e-14)
+        assert rel(ctx.get_state(), s.state()) < 1e-9
+
+
+def test_adaptive_attempt_budget_and_resume():
+    n = 32
+    p = lib_params(0.0)
+    u0 = I.circle_bilayer(n)
+    with fch.Context(n, p) as ctx:
+        ctx.set_state(u0)
+        st = ctx.run_adaptive("imex", 1e-5, 1.0, max_attempts=7, raise_on_timeout=False)
+        assert st["n_attempts"] == 7  # the backward-Euler start + 6 trials
+        st2 = ctx.run_adaptive("imex", 1e-5, st["t"] + 1e-3)
+        assert st2["t"] == pytest.approx(st["t"] + 1e-3, rel=1e-13)
+
+
+def test_errors_are_reported():
+    n = 32
+    p = lib_params(0.0, psd_max_iter=2, psd_itol=1e-14)
+    with fch.Context(n, p) as ctx:
+        with pytest.raises(fch.FchError) as e:
+            ctx.step("imex", 1e-3)
+        assert e.value.status == 7  # no state yet
+        ctx.set_state(I.circle_bilayer(n))
+        with pytest.raises(fch.FchError) as e:
+            ctx.step("psd", 1e-3)
+        assert e.value.status == 4  # PSD did not converge in 2 iterations
+        with pytest.raises(fch.FchError) as e:
+            ctx.step("imex", 1e-3)
+        assert e.value.status == 7  # failed context until a new state is set
+        ctx.set_state(I.circle_bilayer(n))
+        ctx.step("imex", 1e-3)
+        bad = I.circle_bilayer(n)
+        bad[3, 4] = np.nan
+        with pytest.raises(fch.FchError) as e:
+            ctx.set_state(bad)  # the SAV energy E1(u^0) is not finite
+        assert e.value.status == 5
+        with pytest.raises(fch.FchError) as e:
+            ctx.run_adaptive("imex", 1e-5, 1e-3)
+        assert e.value.status == 7
