@@ -21,7 +21,8 @@ fch_geom fch_geometry(int N, int prec)
     g.P = P;
     g.col_threads = P * N / 4; // 2P sequences x N/8 threads
     g.col_blocks = N / (2 * P);
-    g.col_smem = (N + 2 * P * N) * csz;
+    const int SL = N + N / 8; // skewed sequence length in shared memory
+    g.col_smem = (N + 2 * P * SL) * csz;
     const int tps = N / 8;
     int rpb = 256 / tps;
     if (rpb < 1) rpb = 1;
@@ -29,37 +30,15 @@ fch_geom fch_geometry(int N, int prec)
     g.rpb = rpb;
     g.row_threads = rpb * tps;
     g.row_blocks = N / rpb;
-    g.row_smem = (N + rpb * N) * csz;
+    g.row_smem = (N + rpb * SL) * csz;
     return g;
 }
 
 // ---------------------------------------------------------------------------
-// control kernel: one block of 256 threads; deterministic FP64 sums of the
-// per-block partials (fixed thread assignment, fixed tree), then thread 0 acts.
-__global__ void __launch_bounds__(256) fch_ctrl_kernel(const fch_kparams kp, int op, int na, double arg0)
+// one control operation; returns false when the run stopped (done or failure)
+__device__ static bool ctrl_op(fch_ctrl *c, const fch_kparams &kp, int op, double S0, double S1,
+                               double arg0)
 {
-    __shared__ double sh[2][256];
-    fch_ctrl *c = kp.ctrl;
-    if (c->done && !(kp.flags & FCH_FL_NOSKIP)) return;
-    if (op == OP_PSD_CHECK && c->psd_conv) return;
-    double s0 = 0, s1 = 0;
-    for (int i = threadIdx.x; i < na; i += 256) {
-        s0 += kp.part[i];
-        s1 += kp.part[FCH_MAXBLK + i];
-    }
-    sh[0][threadIdx.x] = s0;
-    sh[1][threadIdx.x] = s1;
-    __syncthreads();
-    for (int w = 128; w > 0; w >>= 1) {
-        if (threadIdx.x < w) {
-            sh[0][threadIdx.x] += sh[0][threadIdx.x + w];
-            sh[1][threadIdx.x] += sh[1][threadIdx.x + w];
-        }
-        __syncthreads();
-    }
-    if (threadIdx.x != 0) return;
-    const double S0 = sh[0][0], S1 = sh[1][0];
-
     switch (op) {
     case OP_INIT_TRIAL: {
         double k1;
@@ -69,7 +48,7 @@ __global__ void __launch_bounds__(256) fch_ctrl_kernel(const fch_kparams kp, int
             const double rem = c->t_final - c->t;
             if (rem <= 1e-12 * fmax(1.0, fabs(c->t_final))) {
                 c->done = 1;
-                return;
+                return false;
             }
             k1 = fmin(c->ktrial, rem); // the run ends exactly at t_final
         }
@@ -113,7 +92,7 @@ __global__ void __launch_bounds__(256) fch_ctrl_kernel(const fch_kparams kp, int
         if (!isfinite(v) || v <= 0) {
             c->status = FCH_ENONFINITE;
             c->done = 1;
-            return;
+            return false;
         }
         c->e1 = e1;
         c->inv_sqrt_e1 = 1.0 / sqrt(v);
@@ -130,7 +109,7 @@ __global__ void __launch_bounds__(256) fch_ctrl_kernel(const fch_kparams kp, int
         if (!isfinite(r)) {
             c->status = FCH_ENONFINITE;
             c->done = 1;
-            return;
+            return false;
         }
         c->r_new = r;
         break;
@@ -160,7 +139,7 @@ __global__ void __launch_bounds__(256) fch_ctrl_kernel(const fch_kparams kp, int
         if (!isfinite(e)) {
             c->status = FCH_ENONFINITE;
             c->done = 1;
-            return;
+            return false;
         }
         c->e_last = e;
         const double k1 = c->k1;
@@ -213,6 +192,75 @@ __global__ void __launch_bounds__(256) fch_ctrl_kernel(const fch_kparams kp, int
         break;
     }
     }
+    return !c->done;
+}
+
+// float and double mirrors of the per-trial coefficients read by the passes
+__device__ static void sync_coef(fch_ctrl *c)
+{
+    c->cod.a = c->a;
+    c->cod.b = c->b;
+    c->cod.c = c->c;
+    c->cod.gam = c->gam;
+    c->cod.w1 = c->w1;
+    c->cod.w2 = c->w2;
+    c->cod.w3 = c->w3;
+    c->cod.lam = c->lam;
+    c->cod.k1 = c->k1;
+    c->cod.r_new = c->r_new;
+    c->cod.isq = c->inv_sqrt_e1;
+    c->cof.a = (float)c->a;
+    c->cof.b = (float)c->b;
+    c->cof.c = (float)c->c;
+    c->cof.gam = (float)c->gam;
+    c->cof.w1 = (float)c->w1;
+    c->cof.w2 = (float)c->w2;
+    c->cof.w3 = (float)c->w3;
+    c->cof.lam = (float)c->lam;
+    c->cof.k1 = (float)c->k1;
+    c->cof.r_new = (float)c->r_new;
+    c->cof.isq = (float)c->inv_sqrt_e1;
+}
+
+// control kernel: one block of 256 threads; deterministic FP64 sums of the
+// per-block partials (fixed thread assignment, fixed tree), then thread 0 acts.
+__global__ void __launch_bounds__(256) fch_ctrl_kernel(const fch_kparams kp, int op, int na, double arg0)
+{
+    __shared__ double sh[2][256];
+    fch_ctrl *c = kp.ctrl;
+    if (c->done && !(kp.flags & FCH_FL_NOSKIP)) return;
+    if (op == OP_PSD_CHECK && c->psd_conv) return;
+    double s0 = 0, s1 = 0;
+    for (int i = threadIdx.x; i < na; i += 256) {
+        s0 += kp.part[i];
+        s1 += kp.part[FCH_MAXBLK + i];
+    }
+    sh[0][threadIdx.x] = s0;
+    sh[1][threadIdx.x] = s1;
+    __syncthreads();
+    for (int w = 128; w > 0; w >>= 1) {
+        if (threadIdx.x < w) {
+            sh[0][threadIdx.x] += sh[0][threadIdx.x + w];
+            sh[1][threadIdx.x] += sh[1][threadIdx.x + w];
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x != 0) return;
+    const double S0 = sh[0][0], S1 = sh[1][0];
+
+    bool again = false;
+    if (op == OP_DECIDE_INIT) {
+        op = OP_DECIDE;
+        again = true;
+    }
+    for (;;) {
+        if (!ctrl_op(c, kp, op, S0, S1, arg0)) break;
+        if (!again) break;
+        again = false;
+        op = OP_INIT_TRIAL;
+        arg0 = -1.0;
+    }
+    sync_coef(c);
 }
 
 cudaError_t fch_launch_ctrl(int op, const fch_kparams &kp, int na, int, double arg0, cudaStream_t s)
@@ -427,6 +475,34 @@ static fch_status upload_twiddles(fch_ctx *ctx, int N, int prec, void *dst, cuda
     return FCH_OK;
 }
 
+template <typename T>
+static void fill_consts(fch_consts<T> &k, const fch_params &p, double kf, double am, double inv_n2)
+{
+    const double e2 = p.eps * p.eps;
+    k.kf2 = (T)(kf * kf);
+    k.e2 = (T)e2;
+    k.e4 = (T)(e2 * e2);
+    k.am = (T)am;
+    k.am2 = (T)(am * am);
+    k.eta1 = (T)p.eta1;
+    k.eta2 = (T)p.eta2;
+    k.zeta = (T)p.zeta;
+    k.b1am_e2 = (T)(p.beta1 * am * e2);
+    k.b2am2 = (T)(p.beta2 * am * am);
+    k.l1c = (T)(e2 * (p.eta1 + 2.0 * p.zeta));
+    k.kappa0 = (T)p.kappa0;
+    k.k2e2 = (T)(p.kappa2 * e2);
+    k.inv_n2 = (T)inv_n2;
+    k.bm = (T)p.b_minus;
+    k.bp = (T)p.b_plus;
+    k.eps = (T)p.eps;
+    k.q = (T)p.q;
+    k.qeps = (T)(p.q * p.eps);
+    k.qoe = (T)(p.q / p.eps);
+    k.g3 = (T)(p.gamma / 3.0);
+    k.c3 = (T)(0.5 * (3.0 * p.b_plus - p.b_minus));
+}
+
 static void fill_kparams_model(fch_kparams &kp, const fch_params &p, int N, double L)
 {
     kp.N = N;
@@ -452,6 +528,8 @@ static void fill_kparams_model(fch_kparams &kp, const fch_params &p, int N, doub
     kp.D0 = p.D0;
     kp.kappa0 = p.kappa0;
     kp.kappa2 = p.kappa2;
+    fill_consts(kp.cf, p, kp.kf, kp.am, kp.inv_n2);
+    fill_consts(kp.cd, p, kp.kf, kp.am, kp.inv_n2);
 }
 
 static void reset_ctrl(fch_ctx *ctx)
@@ -864,6 +942,7 @@ extern "C" fch_status fch_adaptive_begin(fch_ctx *ctx, fch_scheme scheme, double
         TRY(eval_F(ctx, 5));
     }
     ctx->have_F = true;
+    TRY(ctl(ctx, OP_INIT_TRIAL, 0, -1.0)); // the first trial of this run
     return FCH_OK;
 }
 
@@ -872,7 +951,6 @@ extern "C" fch_status fch_adaptive_enqueue(fch_ctx *ctx, int n)
     if (!ctx || n < 0) return FCH_EINVAL;
     if (!ctx->ad_open || ctx->failed) return FCH_ESTATE;
     for (int i = 0; i < n; i++) {
-        TRY(ctl(ctx, OP_INIT_TRIAL, 0, -1.0));
         fch_status s = enqueue_trial(ctx, ctx->ad_scheme, true);
         if (s != FCH_OK) {
             ctx->failed = true;
@@ -880,7 +958,7 @@ extern "C" fch_status fch_adaptive_enqueue(fch_ctx *ctx, int n)
         }
         TRY(row(ctx, RM_F));
         TRY(col(ctx, CM_F_FINISH, FCH_SRC_UNEW, FCH_FL_AM3));
-        TRY(ctl(ctx, OP_DECIDE, ctx->geom.col_blocks));
+        TRY(ctl(ctx, OP_DECIDE_INIT, ctx->geom.col_blocks)); // decide, then set up the next trial
     }
     return FCH_OK;
 }
@@ -1067,6 +1145,8 @@ extern "C" fch_status fch_fft_plan_create(int n, int prec, void *stream, fch_fft
     pl->kp.logN = ilog2(n);
     pl->kp.P = pl->geom.P;
     pl->kp.inv_n2 = 1.0 / ((double)n * n);
+    pl->kp.cf.inv_n2 = (float)pl->kp.inv_n2;
+    pl->kp.cd.inv_n2 = pl->kp.inv_n2;
     pl->kp.Z = pl->Z;
     pl->kp.tw = pl->tw;
     *out = pl;

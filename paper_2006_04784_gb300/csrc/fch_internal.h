@@ -8,6 +8,28 @@
 #define FCH_NRED 4        // reduction slots per pass
 #define FCH_MAXBLK 4096   // partial sums per slot (>= the largest grid of a pass)
 
+// Model and grid constants in the precision of a pass (filled on the host, so a
+// single-precision pass does no double-precision arithmetic per element).
+template <typename T> struct fch_consts {
+    T kf2;            // (2 pi / L)^2
+    T e2, e4;         // eps^2, eps^4
+    T am, am2;        // alpha_m, alpha_m^2
+    T eta1, eta2, zeta;
+    T b1am_e2, b2am2; // beta1 alpha_m eps^2, beta2 alpha_m^2 (SAV L0, L1)
+    T l1c;            // eps^2 (eta1 + 2 zeta) (SAV L1)
+    T kappa0, k2e2;   // kappa0, kappa2 eps^2 (ETD)
+    T inv_n2;         // 1 / N^2
+    T bm, bp, eps, q, qeps, qoe, g3, c3; // well: b_-, b_+, eps, q, q eps, q/eps, gamma/3, (3 b_+ - b_-)/2
+};
+
+// Per-trial coefficients, mirrored in both precisions by the control kernel.
+template <typename T> struct fch_coef {
+    T a, b, c, gam;   // eq. (BDF2Coef) and k_{n+1}/k_n
+    T w1, w2, w3;     // eq. (Predictor) weights
+    T lam, k1;        // PSD search step, trial step
+    T r_new, isq;     // SAV r^{n+1}, 1/sqrt(E1 + D0)
+};
+
 // Device-resident stepping state: step sizes, BDF2/AM3 coefficients, SAV
 // scalars, controller decisions and counters. Written only by fch_ctrl_kernel
 // (one thread) and by the host between runs; read by every pass.
@@ -29,6 +51,8 @@ struct fch_ctrl {
     int accepted_last, adaptive, first_step;
     long long n_steps, n_rejects, n_attempts, n_psd_iter;
     double lam_tab[10], lam_k[10];  // PSD search step table row for q
+    fch_coef<float> cof;            // float mirror of the coefficients above
+    fch_coef<double> cod;           // double copy, read by the double-precision passes
 };
 
 // Everything a pass needs, passed by value.
@@ -47,6 +71,8 @@ struct fch_kparams {
     void *out0, *out1;              // explicit outputs
     int src;                        // spectrum a start pass reads (FCH_SRC_*)
     int flags;                      // FCH_FL_*
+    fch_consts<float> cf;
+    fch_consts<double> cd;
 };
 
 enum { FCH_SRC_UN = 0, FCH_SRC_UNEW = 1, FCH_SRC_V = 2, FCH_SRC_IN0 = 3 };
@@ -95,7 +121,7 @@ enum {
     OP_DECIDE,         // adaptive accept / reject and next trial size
     OP_ACCEPT,         // fixed step: accept unconditionally
     OP_ENERGY,         // energy from partials
-    OP_SAV_RM          // arg0 = 1: r_m = sqrt(E1 + D0) for set_history
+    OP_DECIDE_INIT     // OP_DECIDE, then OP_INIT_TRIAL (adaptive) for the next trial
 };
 
 // pass geometry for grid N and precision (0 = f64, 1 = f32)

@@ -3,8 +3,8 @@
 // A 2D transform of two real fields a, b is one complex N x N transform of
 // z = a + i b, done as two passes over HBM/L2:
 //   row pass:    one block owns rpb rows; each row is transformed along x in
-//                shared memory (mixed radix-8/4/2 Stockham, E = 8 elements per
-//                thread per stage);
+//                shared memory (Stockham, radix-8 stages then one radix-4 or
+//                radix-2 stage, 8 elements per thread per stage);
 //   column pass: one block owns P column pairs (kx, N-kx); they are transformed
 //                along y in shared memory, and the Hermitian split
 //                A(k) = (Z(k) + conj Z(-k))/2, B(k) = (Z(k) - conj Z(-k))/(2i)
@@ -16,6 +16,10 @@
 // diagonal Fourier-space operations of Secs. 3.3-3.6 (and the AM3 predictor of
 // Sec. 3.2), the row pass the pointwise chemical-potential pieces of eq. (FCH).
 // Half spectra of the state live kx-major: S[kx*N + ky].
+//
+// Single-precision passes do no double-precision arithmetic per element: the
+// double pipe of this GPU runs at a small fraction of the float rate, so every
+// constant arrives precomputed in the pass precision (fch_consts, fch_coef).
 #pragma once
 #include <math.h>
 #include "fch_internal.h"
@@ -25,6 +29,14 @@ namespace fch {
 template <typename T> struct CT;
 template <> struct CT<double> { typedef double2 t; };
 template <> struct CT<float> { typedef float2 t; };
+
+template <typename T> __device__ __forceinline__ const fch_consts<T> &consts(const fch_kparams &kp);
+template <> __device__ __forceinline__ const fch_consts<float> &consts<float>(const fch_kparams &kp) { return kp.cf; }
+template <> __device__ __forceinline__ const fch_consts<double> &consts<double>(const fch_kparams &kp) { return kp.cd; }
+
+template <typename T> __device__ __forceinline__ fch_coef<T> load_coef(const fch_ctrl *c);
+template <> __device__ __forceinline__ fch_coef<float> load_coef<float>(const fch_ctrl *c) { return c->cof; }
+template <> __device__ __forceinline__ fch_coef<double> load_coef<double>(const fch_ctrl *c) { return c->cod; }
 
 template <typename C> __device__ __forceinline__ C mk(decltype(C().x) x, decltype(C().x) y)
 {
@@ -87,64 +99,75 @@ template <int DIR, typename C> __device__ __forceinline__ void bfly8(C *v)
     v[7] = csub(e3, o3);
 }
 
-// In-place Stockham transform of one length-N sequence held in shared memory at
-// s[n*stride + off], by tps = N/8 threads (t = 0..tps-1), 8 elements per
-// thread per stage. tw[m] = exp(-2 pi i m/N). Starts and ends with a barrier of
-// the whole block (all sequences of a block run in lockstep).
+// Shared-memory skew: element n of a sequence is stored at n + n/8, which spreads
+// the stride-R stores of the first Stockham stages over the banks.
+__device__ __forceinline__ int skew(int n) { return n + (n >> 3); }
+__host__ __device__ inline int skewed_len(int n) { return n + (n >> 3); }
+
+// One Stockham stage of radix R = 2^LR on a length-N sequence at
+// s[skew(n)*stride + off]; thread t of tps = N/8 owns 8/R butterflies.
+template <int DIR, int LR, typename C>
+__device__ __forceinline__ void fft_stage(C *s, int N, int logN, int stride, int off, const C *tw,
+                                          int t, int Ns, int lNs)
+{
+    constexpr int R = 1 << LR;
+    constexpr int NB = 8 / R;
+    const int tps = N >> 3, nb = N >> LR;
+    C v[8];
+#pragma unroll
+    for (int b = 0; b < NB; b++) {
+        const int j = t + b * tps;
+#pragma unroll
+        for (int r = 0; r < R; r++) v[b * R + r] = s[skew(j + r * nb) * stride + off];
+    }
+#pragma unroll
+    for (int b = 0; b < NB; b++) {
+        const int j = t + b * tps;
+        if (Ns > 1) {
+            // twiddle w^(r * (j mod Ns)), w = exp(DIR 2 pi i / (Ns R)) = tw[N / (Ns R)]
+            const int step = (j & (Ns - 1)) << (logN - lNs - LR);
+#pragma unroll
+            for (int r = 1; r < R; r++) {
+                C tv = tw[(r * step) & (N - 1)];
+                if (DIR > 0) tv = cconj(tv);
+                v[b * R + r] = cmul(v[b * R + r], tv);
+            }
+        }
+        if (LR == 3)
+            bfly8<DIR>(v + b * R);
+        else if (LR == 2)
+            bfly4<DIR>(v[b * R], v[b * R + 1], v[b * R + 2], v[b * R + 3]);
+        else
+            bfly2<DIR>(v[b * R], v[b * R + 1]);
+    }
+    __syncthreads();
+#pragma unroll
+    for (int b = 0; b < NB; b++) {
+        const int j = t + b * tps;
+        const int idxD = ((j >> lNs) << (lNs + LR)) + (j & (Ns - 1));
+#pragma unroll
+        for (int r = 0; r < R; r++) s[skew(idxD + r * Ns) * stride + off] = v[b * R + r];
+    }
+    __syncthreads();
+}
+
+// In-place transform of one sequence (all sequences of a block in lockstep);
+// starts and ends with a barrier of the whole block. tw[m] = exp(-2 pi i m/N).
 template <int DIR, typename C>
 __device__ void fft_smem(C *s, int N, int logN, int stride, int off, const C *tw, int t)
 {
-    const int tps = N >> 3;
     int Ns = 1, lNs = 0, rem = logN;
     __syncthreads();
-    while (rem > 0) {
-        const int lR = rem >= 3 ? 3 : rem;
-        const int R = 1 << lR;
-        const int nb = N >> lR;
-        C v[8];
-#pragma unroll
-        for (int i = 0; i < 8; i++) {
-            const int b = i >> lR, r = i & (R - 1);
-            const int j = t + b * tps;
-            v[i] = s[(j + r * nb) * stride + off];
-        }
-        const int nbt = 8 >> lR; // butterflies per thread
-#pragma unroll
-        for (int b = 0; b < 8; b++) {
-            if (b >= nbt) break;
-            const int j = t + b * tps;
-            const int jj = j & (Ns - 1);
-            // twiddle index r * jj * N / (Ns R)
-            const int step = (jj << (logN - lNs - lR));
-            C *w = v + b * R;
-#pragma unroll
-            for (int r = 1; r < 8; r++) {
-                if (r >= R) break;
-                C tv = tw[(r * step) & (N - 1)];
-                if (DIR > 0) tv = cconj(tv);
-                w[r] = cmul(w[r], tv);
-            }
-            if (R == 8)
-                bfly8<DIR>(w);
-            else if (R == 4)
-                bfly4<DIR>(w[0], w[1], w[2], w[3]);
-            else
-                bfly2<DIR>(w[0], w[1]);
-        }
-        __syncthreads();
-#pragma unroll
-        for (int i = 0; i < 8; i++) {
-            const int b = i >> lR, r = i & (R - 1);
-            const int j = t + b * tps;
-            const int jj = j & (Ns - 1);
-            const int idxD = ((j >> lNs) << (lNs + lR)) + jj;
-            s[(idxD + r * Ns) * stride + off] = v[i];
-        }
-        __syncthreads();
-        Ns <<= lR;
-        lNs += lR;
-        rem -= lR;
+    while (rem >= 3) {
+        fft_stage<DIR, 3>(s, N, logN, stride, off, tw, t, Ns, lNs);
+        Ns <<= 3;
+        lNs += 3;
+        rem -= 3;
     }
+    if (rem == 2)
+        fft_stage<DIR, 2>(s, N, logN, stride, off, tw, t, Ns, lNs);
+    else if (rem == 1)
+        fft_stage<DIR, 1>(s, N, logN, stride, off, tw, t, Ns, lNs);
 }
 
 // natural kx of slot q of a pair-layout row
@@ -158,40 +181,40 @@ __device__ __forceinline__ int pair_kx(int q, int N)
 // ---------------------------------------------------------------------------
 // the regularised well W_q, eq. (e:Wq-def), with an overflow-free sech/tanh
 template <typename T>
-__device__ __forceinline__ void well(const fch_kparams &kp, T u, T &W, T &W1, T &W2)
+__device__ __forceinline__ void well(const fch_consts<T> &k, T u, T &W, T &W1, T &W2)
 {
-    const T bm = (T)kp.bm, bp = (T)kp.bp, eps = (T)kp.eps, q = (T)kp.q, g3 = (T)(kp.gamma / 3.0);
-    const T v = u - bm;
+    const T v = u - k.bm;
     T A = (T)0.5 * v * v, A1 = v, A2 = (T)1;
-    if (kp.q != 0.0) {
-        const T x = v / eps;
-        const T e = exp(-fabs(x));           // e^{-|x|} in (0, 1]
-        const T den = (T)1 + e * e;
-        const T sech = (T)2 * e / den;
-        const T th = copysign(((T)1 - e * e) / den, x);
-        A += q * eps * ((T)1 - sech);
-        A1 += q * sech * th;
-        A2 += (q / eps) * sech * ((T)2 * sech * sech - (T)1);
+    if (k.q != (T)0) {
+        const T x = v / k.eps;
+        const T e = exp(-fabs(x)); // e^{-|x|} in (0, 1]
+        const T id = (T)1 / ((T)1 + e * e);
+        const T sech = (T)2 * e * id;
+        const T th = copysign(((T)1 - e * e) * id, x);
+        A += k.qeps * ((T)1 - sech);
+        A1 += k.q * sech * th;
+        A2 += k.qoe * sech * ((T)2 * sech * sech - (T)1);
     }
-    const T w = u - bp;
-    const T B = (T)0.5 * w * w + g3 * (u - (T)0.5 * ((T)3 * bp - bm));
-    const T B1 = w + g3;
+    const T w = u - k.bp;
+    const T B = (T)0.5 * w * w + k.g3 * (u - k.c3);
+    const T B1 = w + k.g3;
     W = A * B;
     W1 = A1 * B + A * B1;
     W2 = A2 * B + (T)2 * A1 * B1 + A;
 }
 
 // ---------------------------------------------------------------------------
-// block reduction of up to FCH_NRED doubles into part[slot][blockIdx.x]
+// block reduction of NR per-thread partials into part[slot][blockIdx.x]:
+// warp sums in the pass precision, the per-block sum of warp sums in double.
 template <int NR, typename T>
 __device__ void block_partials(const T *red, double *part, double *scratch)
 {
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
 #pragma unroll
     for (int r = 0; r < NR; r++) {
-        double v = (double)red[r];
+        T v = red[r];
         for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
-        if (lane == 0) scratch[r * 32 + wid] = v;
+        if (lane == 0) scratch[r * 32 + wid] = (double)v;
     }
     __syncthreads();
     if (threadIdx.x < NR) {
@@ -211,25 +234,29 @@ __device__ __forceinline__ bool pass_skipped(const fch_kparams &kp)
 }
 
 // ---------------------------------------------------------------------------
-// ETD phi functions: phi1 = (e^z - 1)/z, phi2 = (e^z - 1 - z)/z^2, in double
-__device__ __forceinline__ void etd_phi(double z, double &ez, double &p1, double &p2)
+// ETD phi functions in precision T: phi1 = (e^z - 1)/z, phi2 = (e^z - 1 - z)/z^2.
+// Below a threshold (1e-2 in double, 0.1 in float, where the direct forms lose
+// digits to cancellation) the Taylor series sum_j z^j/(j+1)!, sum_j z^j/(j+2)!
+// in Horner form, j < 10; the direct forms above.
+template <typename T> __device__ __forceinline__ void etd_phi(T z, T &ez, T &p1, T &p2)
 {
     ez = exp(z);
-    if (fabs(z) < 1e-2) {
-        // Horner forms of sum z^j/(j+1)! and sum z^j/(j+2)!, j < 9
-        const double f1[9] = {1.0, 1.0 / 2, 1.0 / 6, 1.0 / 24, 1.0 / 120, 1.0 / 720, 1.0 / 5040,
-                              1.0 / 40320, 1.0 / 362880};
-        const double f2[9] = {1.0 / 2, 1.0 / 6, 1.0 / 24, 1.0 / 120, 1.0 / 720, 1.0 / 5040,
-                              1.0 / 40320, 1.0 / 362880, 1.0 / 3628800};
-        double a = f1[8], b = f2[8];
-        for (int j = 7; j >= 0; j--) {
-            a = a * z + f1[j];
-            b = b * z + f2[j];
+    const T thr = sizeof(T) == 8 ? (T)1e-2 : (T)0.1;
+    if (fabs(z) < thr) {
+        // inverse factorials 1/1! .. 1/11!
+        const T f[11] = {(T)1.0, (T)(1.0 / 2), (T)(1.0 / 6), (T)(1.0 / 24), (T)(1.0 / 120),
+                         (T)(1.0 / 720), (T)(1.0 / 5040), (T)(1.0 / 40320), (T)(1.0 / 362880),
+                         (T)(1.0 / 3628800), (T)(1.0 / 39916800)};
+        T a = f[9], b = f[10];
+#pragma unroll
+        for (int j = 8; j >= 0; j--) {
+            a = a * z + f[j];
+            b = b * z + f[j + 1];
         }
         p1 = a;
         p2 = b;
     } else {
-        const double em = expm1(z);
+        const T em = expm1(z);
         p1 = em / z;
         p2 = (em - z) / (z * z);
     }
@@ -238,7 +265,7 @@ __device__ __forceinline__ void etd_phi(double z, double &ez, double &p1, double
 // ---------------------------------------------------------------------------
 // column pass: [forward columns + Hermitian split] -> spectral stage ->
 //              [Hermitian pack + inverse columns]
-template <typename T, int MODE> struct ColTraits {
+template <int MODE> struct ColTraits {
     static const bool FWD = MODE != CM_INV_LOAD && MODE != CM_START && MODE != CM_SAV_COMBINE;
     static const bool INV_ALWAYS = MODE == CM_INV_LOAD || MODE == CM_START || MODE == CM_PSD_ITER ||
                                    MODE == CM_ETD_STAGE1;
@@ -246,20 +273,26 @@ template <typename T, int MODE> struct ColTraits {
                                 MODE == CM_ETD_STAGE2;
 };
 
+// buffers a column pass works on, resolved once per block from the control block
+template <typename C> struct ColBufs {
+    const C *Un, *Um, *src, *Fn, *Fm;
+    C *Unew, *dst;
+};
+
 template <typename T, int MODE>
-__device__ __forceinline__ void spec_elem(const fch_kparams &kp, const fch_ctrl *cs, int kx, int ky,
-                                          typename CT<T>::t A, typename CT<T>::t B,
+__device__ __forceinline__ void spec_elem(const fch_kparams &kp, const fch_consts<T> &K,
+                                          const fch_coef<T> &co, const ColBufs<typename CT<T>::t> &bf,
+                                          int kx, int ky, typename CT<T>::t A, typename CT<T>::t B,
                                           typename CT<T>::t &Co, typename CT<T>::t &Do, T *red)
 {
     typedef typename CT<T>::t C;
     const int N = kp.N;
     const long idx = (long)kx * N + ky;
     const int my = ky < (N >> 1) ? ky : ky - N;
-    const T k2 = (T)(kp.kf * kp.kf) * (T)(kx * kx + my * my);
-    const T e2 = (T)kp.eps2, am = (T)kp.am;
-    const T sk = (e2 * k2 + am) * (e2 * k2 + am); // symbol of L_IMEX, eq. (e:IMEX-op)
+    const T k2 = K.kf2 * (T)(kx * kx + my * my);
+    const T sq = K.e2 * k2 + K.am;
+    const T sk = sq * sq; // symbol of L_IMEX, eq. (e:IMEX-op)
     const T wgt = (kx == 0 || kx == (N >> 1)) ? (T)1 : (T)2;
-    const T in2 = (T)kp.inv_n2;
     C v = mk<C>(0, 0);
     bool pack = false;
 
@@ -269,61 +302,37 @@ __device__ __forceinline__ void spec_elem(const fch_kparams &kp, const fch_ctrl 
         return;
     }
     if (MODE == CM_INV_LOAD) {
-        Co = cscale(((const C *)kp.in0)[idx], in2);
-        Do = kp.in1 ? cscale(((const C *)kp.in1)[idx], in2) : mk<C>(0, 0);
+        Co = cscale(((const C *)kp.in0)[idx], K.inv_n2);
+        Do = kp.in1 ? cscale(((const C *)kp.in1)[idx], K.inv_n2) : mk<C>(0, 0);
         return;
     }
-    const C *Un = (const C *)kp.U[cs->iu_n];
-    const C *Um = (const C *)kp.U[cs->iu_m];
-    C *Unew = (C *)kp.U[cs->iu_new];
     if (MODE == CM_START) {
-        switch (kp.src) {
-        case FCH_SRC_UN: v = Un[idx]; break;
-        case FCH_SRC_UNEW: v = Unew[idx]; break;
-        case FCH_SRC_V:
-            v = ((const C *)kp.Vb)[idx];
-            if (kp.flags & FCH_FL_COPYV) Unew[idx] = v;
-            break;
-        case FCH_SRC_IN0: v = ((const C *)kp.in0)[idx]; break;
-        case 4: { // u* = u^n + gam (u^n - u^{n-1}), eq. (Richardson); gam = 0 at the start
-            const T g = (T)cs->gam;
-            const C un = Un[idx];
-            v = g != (T)0 ? cadd(un, cscale(csub(un, Um[idx]), g)) : un;
+        if (kp.src == 4) { // u* = u^n + gam (u^n - u^{n-1}), eq. (Richardson); gam = 0 at the start
+            const C un = bf.Un[idx];
+            v = co.gam != (T)0 ? cadd(un, cscale(csub(un, bf.Um[idx]), co.gam)) : un;
             if (kp.flags & 128) ((C *)kp.Vb)[idx] = v; // PSD: v_0 = u*, eq. (recurrence)
-            break;
-        }
-        case 5: v = Um[idx]; break;
+        } else {
+            v = bf.src[idx];
+            if (kp.flags & FCH_FL_COPYV) bf.Unew[idx] = v;
         }
         pack = true;
     } else if (MODE == CM_IMEX_SOLVE) {
         // eq. (IMEX-eq): (a + |k|^2 s) u^{n+1} = -b u^n - c u^{n-1} - |k|^2 N_IMEX(u*)^
-        const C Nh = csub(A, cscale(B, e2 * k2));
-        const T a = (T)cs->a, b = (T)cs->b, c = (T)cs->c;
-        const C rhs = csub(cscale(Un[idx], -b), cadd(cscale(Um[idx], c), cscale(Nh, k2)));
-        v = cscale(rhs, (T)1 / (a + k2 * sk));
-        Unew[idx] = v;
+        const C Nh = csub(A, cscale(B, K.e2 * k2));
+        const C rhs = csub(cscale(bf.Un[idx], -co.b), cadd(cscale(bf.Um[idx], co.c), cscale(Nh, k2)));
+        v = cscale(rhs, (T)1 / (co.a + k2 * sk));
+        bf.Unew[idx] = v;
         pack = kp.flags & FCH_FL_PACK_F;
     } else if (MODE == CM_F_FINISH) {
         // mu^ = eps^4 |k|^4 u^ + eps^2 |k|^2 W'^ + (rest)^ ; F^ = -|k|^2 mu^ (eq. sFCH)
-        const C *src;
-        C *dst;
-        switch (kp.src) {
-        case FCH_SRC_UN: src = Un; dst = (C *)kp.F[cs->if_n]; break;
-        case 5: src = Um; dst = (C *)kp.F[cs->if_m]; break;
-        case FCH_SRC_UNEW: src = Unew; dst = (C *)kp.F[cs->if_new]; break;
-        default: src = (const C *)kp.in0; dst = (C *)kp.out0; break;
-        }
-        const C u = src[idx];
-        const C mu = cadd(cadd(cscale(u, e2 * e2 * k2 * k2), cscale(A, e2 * k2)), B);
+        const C u = bf.src[idx];
+        const C mu = cadd(cadd(cscale(u, K.e4 * k2 * k2), cscale(A, K.e2 * k2)), B);
         const C F = cscale(mu, -k2);
-        dst[idx] = F;
+        bf.dst[idx] = F;
         if (kp.flags & FCH_FL_AM3) {
             // eq. (Predictor): u_p = u^n + w1 F(u~) + w2 F(u^n) + w3 F(u^{n-1})
-            const C Fn = ((const C *)kp.F[cs->if_n])[idx];
-            const C Fm = ((const C *)kp.F[cs->if_m])[idx];
-            const T w1 = (T)cs->w1, w2 = (T)cs->w2, w3 = (T)cs->w3;
-            const C un = Un[idx];
-            const C up = cadd(cadd(un, cscale(F, w1)), cadd(cscale(Fn, w2), cscale(Fm, w3)));
+            const C up = cadd(cadd(bf.Un[idx], cscale(F, co.w1)),
+                              cadd(cscale(bf.Fn[idx], co.w2), cscale(bf.Fm[idx], co.w3)));
             const C df = csub(u, up);
             red[0] += wgt * (df.x * df.x + df.y * df.y);
             red[1] += wgt * (up.x * up.x + up.y * up.y);
@@ -332,28 +341,23 @@ __device__ __forceinline__ void spec_elem(const fch_kparams &kp, const fch_ctrl 
     } else if (MODE == CM_SAV_PQ) {
         // eqs. (4.7)-(4.8): (a + |k|^2 l0) p = -b u^n - c u^{n-1} - |k|^2 l1 u*,
         //                   (a + |k|^2 l0) q = -|k|^2 X,  X = V[u*]/sqrt(E1(u*) + D0)
-        const T isq = (T)cs->inv_sqrt_e1;
-        const C X = cscale(cadd(cscale(A, e2 * k2), B), isq);
-        const T g = (T)cs->gam;
-        const C un = Un[idx], um = Um[idx];
-        const C us = g != (T)0 ? cadd(un, cscale(csub(un, um), g)) : un;
-        const T b1 = (T)kp.beta1, b2 = (T)kp.beta2;
-        const T l0 = e2 * e2 * k2 * k2 + b1 * am * e2 * k2 + b2 * am * am;
-        const T l1 = -e2 * (T)(kp.eta1 + 2.0 * kp.zeta) * k2 - b1 * am * e2 * k2 - b2 * am * am;
-        const T a = (T)cs->a, b = (T)cs->b, c = (T)cs->c;
-        const T iden = (T)1 / (a + k2 * l0);
-        const C p = cscale(csub(cscale(un, -b), cadd(cscale(um, c), cscale(us, k2 * l1))), iden);
+        const C X = cscale(cadd(cscale(A, K.e2 * k2), B), co.isq);
+        const C un = bf.Un[idx], um = bf.Um[idx];
+        const C us = co.gam != (T)0 ? cadd(un, cscale(csub(un, um), co.gam)) : un;
+        const T l0 = K.e4 * k2 * k2 + K.b1am_e2 * k2 + K.b2am2;
+        const T l1 = -K.l1c * k2 - K.b1am_e2 * k2 - K.b2am2;
+        const T iden = (T)1 / (co.a + k2 * l0);
+        const C p = cscale(csub(cscale(un, -co.b), cadd(cscale(um, co.c), cscale(us, k2 * l1))), iden);
         const C q = cscale(X, -k2 * iden);
         ((C *)kp.Pb)[idx] = p;
         ((C *)kp.Qb)[idx] = q;
-        const C rr = cadd(cscale(p, a), cadd(cscale(un, b), cscale(um, c)));
+        const C rr = cadd(cscale(p, co.a), cadd(cscale(un, co.b), cscale(um, co.c)));
         red[0] += wgt * (X.x * rr.x + X.y * rr.y);
         red[1] += wgt * (X.x * q.x + X.y * q.y);
         return;
     } else if (MODE == CM_SAV_COMBINE) {
-        const T r = (T)cs->r_new;
-        v = cadd(((const C *)kp.Pb)[idx], cscale(((const C *)kp.Qb)[idx], r));
-        Unew[idx] = v;
+        v = cadd(((const C *)kp.Pb)[idx], cscale(((const C *)kp.Qb)[idx], co.r_new));
+        bf.Unew[idx] = v;
         pack = kp.flags & FCH_FL_PACK_F;
     } else if (MODE == CM_PSD_ITER) {
         // R = mu(v) + (a v + b u^n + c u^{n-1}) / |k|^2,  d = -R / (s + a/|k|^2)  (k != 0),
@@ -362,44 +366,42 @@ __device__ __forceinline__ void spec_elem(const fch_kparams &kp, const fch_ctrl 
         const C vv = Vb[idx];
         C d = mk<C>(0, 0);
         if (k2 > (T)0) {
-            const C mu = cadd(cadd(cscale(vv, e2 * e2 * k2 * k2), cscale(A, e2 * k2)), B);
-            const T a = (T)cs->a, b = (T)cs->b, c = (T)cs->c;
+            const C mu = cadd(cadd(cscale(vv, K.e4 * k2 * k2), cscale(A, K.e2 * k2)), B);
             const T ik2 = (T)1 / k2;
-            const C R = cadd(mu, cscale(cadd(cscale(vv, a), cadd(cscale(Un[idx], b), cscale(Um[idx], c))), ik2));
-            d = cscale(R, (T)-1 / (sk + a * ik2));
+            const C R = cadd(mu, cscale(cadd(cscale(vv, co.a), cadd(cscale(bf.Un[idx], co.b),
+                                                                    cscale(bf.Um[idx], co.c))), ik2));
+            d = cscale(R, (T)-1 / (sk + co.a * ik2));
         }
-        v = cadd(vv, cscale(d, (T)cs->lam));
+        v = cadd(vv, cscale(d, co.lam));
         Vb[idx] = v;
         red[0] += wgt * (d.x * d.x + d.y * d.y);
         red[1] += wgt * (v.x * v.x + v.y * v.y);
         pack = true;
     } else if (MODE == CM_ETD_STAGE1 || MODE == CM_ETD_STAGE2) {
         // eqs. (ETDRK2), (ETD-L): l = -|k|^2 s - kappa0 - kappa2 eps^2 |k|^2, z = l k
-        const T k0 = (T)kp.kappa0, kk2 = (T)kp.kappa2;
-        const C Nim = csub(A, cscale(B, e2 * k2));
-        const double ell = -(double)k2 * (double)sk - kp.kappa0 - kp.kappa2 * kp.eps2 * (double)k2;
-        double ez, p1, p2;
-        etd_phi(ell * cs->k1, ez, p1, p2);
-        const T k1 = (T)cs->k1;
+        const C Nim = csub(A, cscale(B, K.e2 * k2));
+        const T ell = -k2 * sk - K.kappa0 - K.k2e2 * k2;
+        T ez, p1, p2;
+        etd_phi<T>(ell * co.k1, ez, p1, p2);
         C *Nb = (C *)kp.Nb;
         if (MODE == CM_ETD_STAGE1) {
-            const C un = Un[idx];
-            const C N0 = cadd(cscale(Nim, -k2), cscale(un, k0 + kk2 * e2 * k2));
+            const C un = bf.Un[idx];
+            const C N0 = cadd(cscale(Nim, -k2), cscale(un, K.kappa0 + K.k2e2 * k2));
             Nb[idx] = N0;
-            v = cadd(cscale(un, (T)ez), cscale(N0, k1 * (T)p1));
-            Unew[idx] = v;
+            v = cadd(cscale(un, ez), cscale(N0, co.k1 * p1));
+            bf.Unew[idx] = v;
             pack = true;
         } else {
-            const C ut = Unew[idx];
-            const C N1 = cadd(cscale(Nim, -k2), cscale(ut, k0 + kk2 * e2 * k2));
-            v = cadd(ut, cscale(csub(N1, Nb[idx]), k1 * (T)p2));
-            Unew[idx] = v;
+            const C ut = bf.Unew[idx];
+            const C N1 = cadd(cscale(Nim, -k2), cscale(ut, K.kappa0 + K.k2e2 * k2));
+            v = cadd(ut, cscale(csub(N1, Nb[idx]), co.k1 * p2));
+            bf.Unew[idx] = v;
             pack = kp.flags & FCH_FL_PACK_F;
         }
     }
     if (pack) {
-        Co = cscale(v, in2);
-        Do = cscale(v, -k2 * in2);
+        Co = cscale(v, K.inv_n2);
+        Do = cscale(v, -k2 * K.inv_n2);
     }
 }
 
@@ -407,7 +409,7 @@ template <typename T, int MODE>
 __global__ void __launch_bounds__(1024) col_pass(const fch_kparams kp)
 {
     typedef typename CT<T>::t C;
-    typedef ColTraits<T, MODE> TR;
+    typedef ColTraits<MODE> TR;
     if (pass_skipped(kp)) return;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ double red_scratch[FCH_NRED * 32];
@@ -416,17 +418,41 @@ __global__ void __launch_bounds__(1024) col_pass(const fch_kparams kp)
     C *tile = tw + N;
     const int c = threadIdx.x % nc, t = threadIdx.x / nc;
     const int p0 = blockIdx.x * P;
-    const fch_ctrl *cs = kp.ctrl;
+    const fch_consts<T> &K = consts<T>(kp);
     const bool inv = TR::INV_ALWAYS || (TR::INV_OPT && (kp.flags & FCH_FL_PACK_F));
     const bool has_red = MODE == CM_SAV_PQ || MODE == CM_PSD_ITER ||
                          (MODE == CM_F_FINISH && (kp.flags & FCH_FL_AM3));
     C *Z = (C *)kp.Z;
 
+    // per-block constants from the control block
+    fch_coef<T> co;
+    ColBufs<C> bf;
+    if (kp.ctrl) {
+        const fch_ctrl *cs = kp.ctrl;
+        co = load_coef<T>(cs);
+        bf.Un = (const C *)kp.U[cs->iu_n];
+        bf.Um = (const C *)kp.U[cs->iu_m];
+        bf.Unew = (C *)kp.U[cs->iu_new];
+        bf.Fn = (const C *)kp.F[cs->if_n];
+        bf.Fm = (const C *)kp.F[cs->if_m];
+        switch (kp.src) {
+        case FCH_SRC_UN: bf.src = bf.Un; bf.dst = (C *)kp.F[cs->if_n]; break;
+        case 5: bf.src = bf.Um; bf.dst = (C *)kp.F[cs->if_m]; break;
+        case FCH_SRC_UNEW: bf.src = bf.Unew; bf.dst = (C *)kp.F[cs->if_new]; break;
+        case FCH_SRC_V: bf.src = (const C *)kp.Vb; bf.dst = nullptr; break;
+        default: bf.src = (const C *)kp.in0; bf.dst = (C *)kp.out0; break;
+        }
+    } else {
+        bf.Un = bf.Um = bf.src = bf.Fn = bf.Fm = nullptr;
+        bf.Unew = bf.dst = nullptr;
+        co = fch_coef<T>();
+    }
+
     for (int i = threadIdx.x; i < N; i += blockDim.x) tw[i] = ((const C *)kp.tw)[i];
     if (TR::FWD) {
         for (int i = threadIdx.x; i < N * nc; i += blockDim.x) {
             const int n = i / nc, cc = i - n * nc;
-            tile[i] = Z[(long)n * N + 2 * p0 + cc];
+            tile[skew(n) * nc + cc] = Z[(long)n * N + 2 * p0 + cc];
         }
         fft_smem<-1>(tile, N, kp.logN, nc, c, tw, t);
     } else {
@@ -440,55 +466,62 @@ __global__ void __launch_bounds__(1024) col_pass(const fch_kparams kp)
         const int p = p0 + pp;
         const int s0 = 2 * pp, s1 = 2 * pp + 1;
         const int mky = (N - ky) & (N - 1);
+        const int rk = skew(ky) * nc, rm = skew(mky) * nc;
         if (p > 0) {
             C A = mk<C>(0, 0), B = mk<C>(0, 0);
             if (TR::FWD) {
-                const C z0 = tile[ky * nc + s0], z1 = cconj(tile[mky * nc + s1]);
+                const C z0 = tile[rk + s0], z1 = cconj(tile[rm + s1]);
                 A = cscale(cadd(z0, z1), (T)0.5);
                 const C dm = csub(z0, z1);
                 B = mk<C>((T)0.5 * dm.y, (T)-0.5 * dm.x);
             }
             C Co = mk<C>(0, 0), Do = mk<C>(0, 0);
-            spec_elem<T, MODE>(kp, cs, p, ky, A, B, Co, Do, red);
+            spec_elem<T, MODE>(kp, K, co, bf, p, ky, A, B, Co, Do, red);
             if (inv) {
-                tile[ky * nc + s0] = mk<C>(Co.x - Do.y, Co.y + Do.x);
-                tile[mky * nc + s1] = mk<C>(Co.x + Do.y, Do.x - Co.y);
+                tile[rk + s0] = mk<C>(Co.x - Do.y, Co.y + Do.x);
+                tile[rm + s1] = mk<C>(Co.x + Do.y, Do.x - Co.y);
             }
         } else {
             if (ky > (N >> 1)) continue;
             // columns kx = 0 (slot s0) and kx = N/2 (slot s1), rows ky and -ky
             const int nrow = (ky == 0 || ky == (N >> 1)) ? 1 : 2;
             C za[2], zb[2];
-            za[0] = tile[ky * nc + s0];
-            za[1] = tile[mky * nc + s0];
-            zb[0] = tile[ky * nc + s1];
-            zb[1] = tile[mky * nc + s1];
+            za[0] = tile[rk + s0];
+            za[1] = tile[rm + s0];
+            zb[0] = tile[rk + s1];
+            zb[1] = tile[rm + s1];
             C outa[2], outb[2];
 #pragma unroll
             for (int side = 0; side < 2; side++) {
-                const C *zz = side ? zb : za;
-                C *oo = side ? outb : outa;
                 const int kx = side ? (N >> 1) : 0;
-                for (int rr = 0; rr < nrow; rr++) {
+#pragma unroll
+                for (int rr = 0; rr < 2; rr++) {
+                    if (rr >= nrow) break;
                     const int kyy = rr ? mky : ky;
+                    const C zr = side ? zb[rr] : za[rr];
+                    const C zo = side ? zb[rr ^ 1] : za[rr ^ 1];
                     C A = mk<C>(0, 0), B = mk<C>(0, 0);
                     if (TR::FWD) {
-                        const C z0 = zz[rr], z1 = cconj(zz[rr ^ 1]);
-                        A = cscale(cadd(z0, z1), (T)0.5);
-                        const C dm = csub(z0, z1);
+                        const C z1 = cconj(zo);
+                        A = cscale(cadd(zr, z1), (T)0.5);
+                        const C dm = csub(zr, z1);
                         B = mk<C>((T)0.5 * dm.y, (T)-0.5 * dm.x);
                     }
                     C Co = mk<C>(0, 0), Do = mk<C>(0, 0);
-                    spec_elem<T, MODE>(kp, cs, kx, kyy, A, B, Co, Do, red);
-                    oo[rr] = mk<C>(Co.x - Do.y, Co.y + Do.x);
+                    spec_elem<T, MODE>(kp, K, co, bf, kx, kyy, A, B, Co, Do, red);
+                    const C o = mk<C>(Co.x - Do.y, Co.y + Do.x);
+                    if (side)
+                        outb[rr] = o;
+                    else
+                        outa[rr] = o;
                 }
             }
             if (inv) {
-                tile[ky * nc + s0] = outa[0];
-                tile[ky * nc + s1] = outb[0];
+                tile[rk + s0] = outa[0];
+                tile[rk + s1] = outb[0];
                 if (nrow == 2) {
-                    tile[mky * nc + s0] = outa[1];
-                    tile[mky * nc + s1] = outb[1];
+                    tile[rm + s0] = outa[1];
+                    tile[rm + s1] = outb[1];
                 }
             }
         }
@@ -498,7 +531,7 @@ __global__ void __launch_bounds__(1024) col_pass(const fch_kparams kp)
         fft_smem<+1>(tile, N, kp.logN, nc, c, tw, t);
         for (int i = threadIdx.x; i < N * nc; i += blockDim.x) {
             const int n = i / nc, cc = i - n * nc;
-            Z[(long)n * N + 2 * p0 + cc] = tile[i];
+            Z[(long)n * N + 2 * p0 + cc] = tile[skew(n) * nc + cc];
         }
     }
 }
@@ -512,7 +545,7 @@ __global__ void __launch_bounds__(256) row_pass(const fch_kparams kp)
     if (pass_skipped(kp)) return;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ double red_scratch[FCH_NRED * 32];
-    const int N = kp.N, tps = N >> 3;
+    const int N = kp.N, tps = N >> 3, SL = skewed_len(N);
     if (kp.nfft && blockIdx.x == 0 && threadIdx.x == 0)
         atomicAdd(kp.nfft, (MODE == RM_R2C_LOAD || MODE == RM_C2R_STORE || MODE == RM_ENERGY) ? 2ull : 4ull);
     C *tw = (C *)smem_raw;
@@ -522,10 +555,12 @@ __global__ void __launch_bounds__(256) row_pass(const fch_kparams kp)
     const int y0 = blockIdx.x * rpb;
     C *Z = (C *)kp.Z;
     const bool f64io = kp.flags & FCH_FL_F64IO;
+    const fch_consts<T> &K = consts<T>(kp);
 
     for (int i = threadIdx.x; i < N; i += blockDim.x) tw[i] = ((const C *)kp.tw)[i];
     if (MODE == RM_R2C_LOAD) {
         for (int i = threadIdx.x; i < rpb * N; i += blockDim.x) {
+            const int r = i / N, x = i - r * N;
             const long g = (long)y0 * N + i;
             T a, b = 0;
             if (f64io) {
@@ -535,24 +570,22 @@ __global__ void __launch_bounds__(256) row_pass(const fch_kparams kp)
                 a = (T)((const float *)kp.in0)[g];
                 if (kp.in1) b = (T)((const float *)kp.in1)[g];
             }
-            rows[i] = mk<C>(a, b);
+            rows[r * SL + skew(x)] = mk<C>(a, b);
         }
     } else {
         for (int i = threadIdx.x; i < rpb * N; i += blockDim.x) {
             const int r = i / N, q = i - r * N;
-            rows[r * N + pair_kx(q, N)] = Z[(long)(y0 + r) * N + q];
+            rows[r * SL + skew(pair_kx(q, N))] = Z[(long)(y0 + r) * N + q];
         }
-        fft_smem<+1>(rows + rr * N, N, kp.logN, 1, 0, tw, t);
+        fft_smem<+1>(rows + rr * SL, N, kp.logN, 1, 0, tw, t);
     }
 
     T red[FCH_NRED] = {0, 0, 0, 0};
-    C *s = rows + rr * N;
+    C *s = rows + rr * SL;
     const int y = y0 + rr;
     if (MODE != RM_R2C_LOAD) {
-        const T e2 = (T)kp.eps2, am = (T)kp.am, eta1 = (T)kp.eta1, eta2 = (T)kp.eta2,
-                zeta = (T)kp.zeta;
         for (int x = t; x < N; x += tps) {
-            const C z = s[x];
+            const C z = s[skew(x)];
             const T u = z.x, lu = z.y; // u and Lap u
             if (MODE == RM_C2R_STORE) {
                 const long g = (long)y * N + x;
@@ -566,36 +599,36 @@ __global__ void __launch_bounds__(256) row_pass(const fch_kparams kp)
                 continue;
             }
             T W, W1, W2;
-            well<T>(kp, u, W, W1, W2);
+            well<T>(K, u, W, W1, W2);
             C o = mk<C>(0, 0);
             if (MODE == RM_NIMEX) {
                 // N_IMEX = [eps^2 (am - W'' + eta1) Lap u + W''W' - am^2 u - eta2 W'] + eps^2 Lap (am u - W')
-                o.x = e2 * (am - W2 + eta1) * lu + W2 * W1 - am * am * u - eta2 * W1;
-                o.y = am * u - W1;
+                o.x = K.e2 * (K.am - W2 + K.eta1) * lu + W2 * W1 - K.am2 * u - K.eta2 * W1;
+                o.y = K.am * u - W1;
             } else if (MODE == RM_F || MODE == RM_ENERGY) {
                 // mu = eps^2 Lap w - W'' w + eps^2 eta1 Lap u - eta2 W', w = eps^2 Lap u - W'
-                const T w = e2 * lu - W1;
+                const T w = K.e2 * lu - W1;
                 o.x = W1;
-                o.y = -W2 * w - eta2 * W1 + e2 * eta1 * lu;
+                o.y = -W2 * w - K.eta2 * W1 + K.e2 * K.eta1 * lu;
                 if (MODE == RM_ENERGY || (kp.flags & FCH_FL_ENERGY))
-                    red[0] += (T)0.5 * w * w - eta2 * W + (T)0.5 * e2 * eta1 * u * lu;
+                    red[0] += (T)0.5 * w * w - K.eta2 * W + (T)0.5 * K.e2 * K.eta1 * u * lu;
             } else if (MODE == RM_SAV) {
                 // V = -eps^2 Lap (W' + zeta u) + [-eps^2 (W'' + zeta) Lap u + W' W'' - eta2 W']
-                o.x = W1 + zeta * u;
-                o.y = -e2 * (W2 + zeta) * lu + W1 * W2 - eta2 * W1;
-                red[0] += -e2 * lu * (W1 + zeta * u) + (T)0.5 * W1 * W1 - eta2 * W;
+                o.x = W1 + K.zeta * u;
+                o.y = -K.e2 * (W2 + K.zeta) * lu + W1 * W2 - K.eta2 * W1;
+                red[0] += -K.e2 * lu * (W1 + K.zeta * u) + (T)0.5 * W1 * W1 - K.eta2 * W;
             }
-            s[x] = o;
+            s[skew(x)] = o;
         }
     }
     const bool has_red = MODE == RM_SAV || MODE == RM_ENERGY || (MODE == RM_F && (kp.flags & FCH_FL_ENERGY));
     if (has_red) block_partials<1>(red, kp.part, red_scratch);
     if (MODE == RM_C2R_STORE || MODE == RM_ENERGY) return;
 
-    fft_smem<-1>(rows + rr * N, N, kp.logN, 1, 0, tw, t);
+    fft_smem<-1>(rows + rr * SL, N, kp.logN, 1, 0, tw, t);
     for (int i = threadIdx.x; i < rpb * N; i += blockDim.x) {
         const int r = i / N, q = i - r * N;
-        Z[(long)(y0 + r) * N + q] = rows[r * N + pair_kx(q, N)];
+        Z[(long)(y0 + r) * N + q] = rows[r * SL + skew(pair_kx(q, N))];
     }
 }
 

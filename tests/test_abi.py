@@ -49,12 +49,13 @@ def test_geometry_covers_grid(n, prec):
     assert g["col_blocks"] * g["P"] == n // 2
     assert g["col_threads"] == 2 * g["P"] * (n // 8) and g["col_threads"] <= 1024
     assert g["col_threads"] % 32 == 0
-    assert g["col_smem"] == (n + 2 * g["P"] * n) * csz and g["col_smem"] <= 227 * 1024
+    sl = n + n // 8  # skewed sequence length
+    assert g["col_smem"] == (n + 2 * g["P"] * sl) * csz and g["col_smem"] <= 227 * 1024
     # row pass: rpb rows of N/8 threads, all N rows covered
     assert g["row_blocks"] * g["rpb"] == n
     assert g["row_threads"] == g["rpb"] * (n // 8) and g["row_threads"] <= 256
     assert g["row_threads"] % 32 == 0
-    assert g["row_smem"] == (n + g["rpb"] * n) * csz and g["row_smem"] <= 227 * 1024
+    assert g["row_smem"] == (n + g["rpb"] * sl) * csz and g["row_smem"] <= 227 * 1024
     # per-block partial sums fit their slots (FCH_MAXBLK = 4096)
     assert max(g["row_blocks"], g["col_blocks"]) <= 4096
 
@@ -76,6 +77,7 @@ def test_stockham_index_map_is_a_permutation():
                     assert j + r * (n >> lr) < n  # load index in range
                     idx = ((j >> lns) << (lns + lr)) + (j & (ns - 1)) + r * ns
                     assert 0 <= idx < n
+                    assert idx + (idx >> 3) < n + n // 8  # skewed slot inside the sequence
                     seen.add(idx)
             assert len(seen) == n
             ns <<= lr
