@@ -79,6 +79,8 @@ typedef struct {
     int psd_max_iter;
     int prec;            /* fch_precision */
     int sync_every;      /* adaptive runs: trial steps enqueued between host checks */
+    int fft_path;        /* 0: automatic; 1: shared-memory Stockham passes for every N;
+                          * 2: warp-transform passes where available (FCH_MIXED, N = 1024) */
 } fch_params;
 
 typedef struct {

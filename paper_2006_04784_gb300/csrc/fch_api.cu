@@ -7,6 +7,7 @@
 #include <string.h>
 
 #include "../../include/fch.h"
+#include "fch_ctrl.cuh"
 #include "fch_internal.h"
 
 // ---------------------------------------------------------------------------
@@ -35,232 +36,10 @@ fch_geom fch_geometry(int N, int prec)
 }
 
 // ---------------------------------------------------------------------------
-// one control operation; returns false when the run stopped (done or failure)
-__device__ static bool ctrl_op(fch_ctrl *c, const fch_kparams &kp, int op, double S0, double S1,
-                               double arg0)
-{
-    switch (op) {
-    case OP_INIT_TRIAL: {
-        double k1;
-        if (arg0 > 0) {
-            k1 = arg0; // fixed step
-        } else {
-            const double rem = c->t_final - c->t;
-            if (rem <= 1e-12 * fmax(1.0, fabs(c->t_final))) {
-                c->done = 1;
-                return false;
-            }
-            k1 = fmin(c->ktrial, rem); // the run ends exactly at t_final
-        }
-        c->k1 = k1;
-        if (c->kn <= 0) { // backward-Euler start: k_{n-1} -> infinity in eq. (BDF2Coef)
-            c->a = 1.0 / k1;
-            c->b = -1.0 / k1;
-            c->c = 0.0;
-            c->gam = 0.0;
-        } else { // eq. (BDF2Coef)
-            const double kn = c->kn;
-            c->a = 1.0 / k1 + 1.0 / (k1 + kn);
-            c->b = -1.0 / k1 - 1.0 / kn;
-            c->c = 1.0 / kn - 1.0 / (k1 + kn);
-            c->gam = k1 / kn;
-            const double g = c->gam; // eq. (Predictor) weights
-            c->w1 = k1 / 6.0 * (3.0 + 2.0 * g) / (1.0 + g);
-            c->w2 = k1 / 6.0 * (3.0 + g);
-            c->w3 = -k1 / 6.0 * g * g / (1.0 + g);
-        }
-        // PSD search step: Table SearchSize row, linear in k, clamped
-        if (c->lam_k[0] < 0) {
-            c->lam = c->lam_tab[0]; // fixed lambda
-        } else if (k1 <= c->lam_k[0]) {
-            c->lam = c->lam_tab[0];
-        } else if (k1 >= c->lam_k[9]) {
-            c->lam = c->lam_tab[9];
-        } else {
-            int j = 0;
-            while (j < 8 && k1 > c->lam_k[j + 1]) j++;
-            const double th = (k1 - c->lam_k[j]) / (c->lam_k[j + 1] - c->lam_k[j]);
-            c->lam = c->lam_tab[j] + th * (c->lam_tab[j + 1] - c->lam_tab[j]);
-        }
-        c->psd_conv = 0;
-        c->psd_iter = 0;
-        break;
-    }
-    case OP_SAV_E1: {
-        const double e1 = kp.h2 * S0;
-        const double v = e1 + kp.D0;
-        if (!isfinite(v) || v <= 0) {
-            c->status = FCH_ENONFINITE;
-            c->done = 1;
-            return false;
-        }
-        c->e1 = e1;
-        c->inv_sqrt_e1 = 1.0 / sqrt(v);
-        if (arg0 == 1.0) c->r_n = sqrt(v);
-        if (arg0 == 2.0) c->r_m = sqrt(v);
-        break;
-    }
-    case OP_SAV_R: {
-        // eq. (4.8) with u^{n+1} = p + r q:
-        // r (a - a (X, q)/2) = -b r^n - c r^{n-1} + (X, a p + b u^n + c u^{n-1})/2
-        const double sc = kp.h2 * kp.inv_n2; // Parseval on the unnormalised half spectra
-        const double xr = sc * S0, xq = sc * S1;
-        const double r = (-c->b * c->r_n - c->c * c->r_m + 0.5 * xr) / (c->a * (1.0 - 0.5 * xq));
-        if (!isfinite(r)) {
-            c->status = FCH_ENONFINITE;
-            c->done = 1;
-            return false;
-        }
-        c->r_new = r;
-        break;
-    }
-    case OP_PSD_CHECK: {
-        const double ratio = sqrt(S0) / sqrt(S1); // ||d|| / ||v_{s+1}||, h cancels
-        c->psd_iter++;
-        c->n_psd_iter++;
-        c->psd_ratio = ratio;
-        if (!isfinite(ratio)) {
-            c->status = FCH_ENONFINITE;
-            c->done = 1;
-        } else if (ratio < c->itol) {
-            c->psd_conv = 1;
-            c->last_psd_iter = c->psd_iter;
-        } else if (c->psd_iter >= c->psd_max_iter) {
-            c->status = FCH_ENOCONV;
-            c->done = 1;
-            c->last_psd_iter = c->psd_iter;
-        }
-        break;
-    }
-    case OP_DECIDE: {
-        // Steps 3-4 of the adaptive algorithm, Sec. 3.2
-        const double e = sqrt(S0) / sqrt(S1);
-        c->n_attempts++;
-        if (!isfinite(e)) {
-            c->status = FCH_ENONFINITE;
-            c->done = 1;
-            return false;
-        }
-        c->e_last = e;
-        const double k1 = c->k1;
-        double kn = c->rho_s * cbrt(c->sigma / fmax(e, 1e-16)) * k1; // A_dp(e, k)
-        if (c->cap) kn = fmin(kn, (1.0 + sqrt(2.0)) * k1);
-        kn = fmax(c->kmin, fmin(kn, c->kmax));
-        if (e <= c->sigma || k1 <= c->kmin) {
-            const int un = c->iu_n, um = c->iu_m, fn = c->if_n, fm = c->if_m;
-            c->iu_m = un;
-            c->iu_n = c->iu_new;
-            c->iu_new = um;
-            c->if_m = fn;
-            c->if_n = c->if_new;
-            c->if_new = fm;
-            c->r_m = c->r_n;
-            c->r_n = c->r_new;
-            c->kn = k1;
-            c->t += k1;
-            c->n_steps++;
-            c->accepted_last = 1;
-        } else {
-            c->n_rejects++;
-            c->accepted_last = 0;
-        }
-        c->ktrial = kn;
-        break;
-    }
-    case OP_ACCEPT: {
-        const int un = c->iu_n, um = c->iu_m;
-        c->iu_m = un;
-        c->iu_n = c->iu_new;
-        c->iu_new = um;
-        if (arg0 == 1.0) { // also rotate the F history (adaptive start)
-            const int fn = c->if_n, fm = c->if_m;
-            c->if_m = fn;
-            c->if_n = c->if_new;
-            c->if_new = fm;
-        }
-        c->r_m = c->r_n;
-        c->r_n = c->r_new;
-        c->kn = c->k1;
-        c->ktrial = c->k1;
-        c->t += c->k1;
-        c->n_steps++;
-        c->n_attempts++;
-        break;
-    }
-    case OP_ENERGY: {
-        c->energy = kp.h2 * S0;
-        break;
-    }
-    }
-    return !c->done;
-}
-
-// float and double mirrors of the per-trial coefficients read by the passes
-__device__ static void sync_coef(fch_ctrl *c)
-{
-    c->cod.a = c->a;
-    c->cod.b = c->b;
-    c->cod.c = c->c;
-    c->cod.gam = c->gam;
-    c->cod.w1 = c->w1;
-    c->cod.w2 = c->w2;
-    c->cod.w3 = c->w3;
-    c->cod.lam = c->lam;
-    c->cod.k1 = c->k1;
-    c->cod.r_new = c->r_new;
-    c->cod.isq = c->inv_sqrt_e1;
-    c->cof.a = (float)c->a;
-    c->cof.b = (float)c->b;
-    c->cof.c = (float)c->c;
-    c->cof.gam = (float)c->gam;
-    c->cof.w1 = (float)c->w1;
-    c->cof.w2 = (float)c->w2;
-    c->cof.w3 = (float)c->w3;
-    c->cof.lam = (float)c->lam;
-    c->cof.k1 = (float)c->k1;
-    c->cof.r_new = (float)c->r_new;
-    c->cof.isq = (float)c->inv_sqrt_e1;
-}
-
-// control kernel: one block of 256 threads; deterministic FP64 sums of the
-// per-block partials (fixed thread assignment, fixed tree), then thread 0 acts.
+// control kernel: one block of 256 threads running ctrl_block
 __global__ void __launch_bounds__(256) fch_ctrl_kernel(const fch_kparams kp, int op, int na, double arg0)
 {
-    __shared__ double sh[2][256];
-    fch_ctrl *c = kp.ctrl;
-    if (c->done && !(kp.flags & FCH_FL_NOSKIP)) return;
-    if (op == OP_PSD_CHECK && c->psd_conv) return;
-    double s0 = 0, s1 = 0;
-    for (int i = threadIdx.x; i < na; i += 256) {
-        s0 += kp.part[i];
-        s1 += kp.part[FCH_MAXBLK + i];
-    }
-    sh[0][threadIdx.x] = s0;
-    sh[1][threadIdx.x] = s1;
-    __syncthreads();
-    for (int w = 128; w > 0; w >>= 1) {
-        if (threadIdx.x < w) {
-            sh[0][threadIdx.x] += sh[0][threadIdx.x + w];
-            sh[1][threadIdx.x] += sh[1][threadIdx.x + w];
-        }
-        __syncthreads();
-    }
-    if (threadIdx.x != 0) return;
-    const double S0 = sh[0][0], S1 = sh[1][0];
-
-    bool again = false;
-    if (op == OP_DECIDE_INIT) {
-        op = OP_DECIDE;
-        again = true;
-    }
-    for (;;) {
-        if (!ctrl_op(c, kp, op, S0, S1, arg0)) break;
-        if (!again) break;
-        again = false;
-        op = OP_INIT_TRIAL;
-        arg0 = -1.0;
-    }
-    sync_coef(c);
+    ctrl_block(kp, op, na, arg0);
 }
 
 cudaError_t fch_launch_ctrl(int op, const fch_kparams &kp, int na, int, double arg0, cudaStream_t s)
@@ -378,13 +157,19 @@ struct fch_ctx {
     fch_ctrl hc;         // host mirror of the control block
     fch_ctrl *dctrl;
     double *part;
-    void *U[3], *F[3], *Pb, *Qb, *Vb, *Nb, *Z, *tw;
+    void *U[3], *F[3], *Pb, *Qb, *Vb, *Nb, *Z, *tw, *tw2;
     double *staging;     // N*N doubles for host io
     long long *nfft_dev;
+    unsigned int *ticket;
     long long nfft_base;
     bool have_state, failed, have_F;
     fch_scheme ad_scheme;           // scheme of the adaptive run begun last
     bool ad_open;
+    // one trial step (trial + F + decide) of IMEX, SAV, ETD captured as a CUDA graph:
+    // every launch reads its per-trial state from the control block, so the same
+    // graph replays any trial; PSD (host convergence test) is not captured
+    cudaGraphExec_t trial_graph[4];
+    bool trial_warm[4], trial_nograph[4];
     // per-pass event timing
     bool timing;
     int nev;
@@ -445,13 +230,43 @@ static int ilog2(int n)
     return l;
 }
 
+// Forward twiddles of every Stockham stage with Ns > 1, in the order the passes
+// read them: the stage with sub-transform length Ns and radix R holds
+// exp(-2 pi i r j / (Ns R)) at Ns - 8 + (r-1) Ns + j, r = 1..R-1, j < Ns.
+// Stages: radix 8 while >= 3 bits remain, then one radix-4 or radix-2 stage.
 template <typename T> static void make_twiddles(int N, T *out)
 {
-    for (int m = 0; m < N; m++) {
-        const double a = -2.0 * M_PI * (double)m / (double)N;
-        out[2 * m] = (T)cos(a);
-        out[2 * m + 1] = (T)sin(a);
+    for (int m = 0; m < 2 * N; m++) out[m] = 0;
+    int Ns = 1, rem = ilog2(N);
+    while (rem > 0) {
+        const int lr = rem >= 3 ? 3 : rem, R = 1 << lr;
+        if (Ns > 1)
+            for (int r = 1; r < R; r++)
+                for (int j = 0; j < Ns; j++) {
+                    const int m = Ns - 8 + (r - 1) * Ns + j;
+                    const double a = -2.0 * M_PI * (double)(r * j) / (double)(Ns * R);
+                    out[2 * m] = (T)cos(a);
+                    out[2 * m + 1] = (T)sin(a);
+                }
+        Ns <<= lr;
+        rem -= lr;
     }
+}
+
+// the 32 x 32 twiddles of the warp transform for N = 1024: [k2][n1] = exp(-2 pi i n1 k2 / 1024)
+static cudaError_t upload_tw2(void **dst, cudaStream_t s)
+{
+    float h[2 * 1024];
+    for (int k2 = 0; k2 < 32; k2++)
+        for (int n1 = 0; n1 < 32; n1++) {
+            const double a = -2.0 * M_PI * (double)(n1 * k2) / 1024.0;
+            h[2 * (k2 * 32 + n1)] = (float)cos(a);
+            h[2 * (k2 * 32 + n1) + 1] = (float)sin(a);
+        }
+    cudaError_t e = cudaMalloc(dst, sizeof(h));
+    if (e == cudaSuccess) e = cudaMemcpyAsync(*dst, h, sizeof(h), cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    return e;
 }
 
 static fch_status upload_twiddles(fch_ctx *ctx, int N, int prec, void *dst, cudaStream_t s)
@@ -557,6 +372,8 @@ static void reset_ctrl(fch_ctx *ctx)
             c.lam_k[j] = kLamK[j];
             c.lam_tab[j] = kLamTab[row][j];
         }
+        for (int j = 0; j < 9; j++)
+            c.lam_slope[j] = (kLamTab[row][j + 1] - kLamTab[row][j]) / (kLamK[j + 1] - kLamK[j]);
     }
 }
 
@@ -575,9 +392,12 @@ static fch_status pull_ctrl(fch_ctx *ctx)
 
 // pass launchers
 static fch_status col(fch_ctx *ctx, int mode, int src = 0, int flags = 0, const void *in0 = nullptr,
-                      const void *in1 = nullptr, void *out0 = nullptr, void *out1 = nullptr)
+                      const void *in1 = nullptr, void *out0 = nullptr, void *out1 = nullptr,
+                      int tail = -1, double tail_arg = 0.0)
 {
     fch_kparams kp = ctx->kp;
+    kp.tail_op = tail;
+    kp.tail_arg = tail_arg;
     kp.src = src;
     kp.flags = flags;
     kp.in0 = in0;
@@ -593,9 +413,11 @@ static fch_status col(fch_ctx *ctx, int mode, int src = 0, int flags = 0, const 
 }
 
 static fch_status row(fch_ctx *ctx, int mode, int flags = 0, const void *in0 = nullptr,
-                      void *out0 = nullptr)
+                      void *out0 = nullptr, int tail = -1, double tail_arg = 0.0)
 {
     fch_kparams kp = ctx->kp;
+    kp.tail_op = tail;
+    kp.tail_arg = tail_arg;
     kp.flags = flags;
     kp.in0 = in0;
     kp.out0 = out0;
@@ -618,6 +440,17 @@ static fch_status ctl(fch_ctx *ctx, int op, int na, double arg0 = 0.0, int flags
     return FCH_OK;
 }
 
+// a column / row pass whose last block then runs control op `op` on its partial sums
+static fch_status colt(fch_ctx *ctx, int mode, int src, int flags, int op, double arg = 0.0)
+{
+    return col(ctx, mode, src, flags, nullptr, nullptr, nullptr, nullptr, op, arg);
+}
+
+static fch_status rowt(fch_ctx *ctx, int mode, int flags, int op, double arg = 0.0)
+{
+    return row(ctx, mode, flags, nullptr, nullptr, op, arg);
+}
+
 #define TRY(x)                                                                            \
     do {                                                                                  \
         fch_status s_ = (x);                                                              \
@@ -629,6 +462,7 @@ extern "C" fch_status fch_create(const fch_grid *g, const fch_params *p, void *s
     if (!g || !p || !out) return FCH_EINVAL;
     *out = nullptr;
     if (!pow2_in_range(g->n) || !(g->L > 0) || !(p->eps > 0) || (p->prec != 0 && p->prec != 1) ||
+        p->fft_path < 0 || p->fft_path > 2 ||
         !(p->k_min > 0) || !(p->rho_s > 0) || p->psd_max_iter < 1)
         return FCH_EINVAL;
     fch_ctx *ctx = (fch_ctx *)calloc(1, sizeof(fch_ctx));
@@ -666,6 +500,8 @@ extern "C" fch_status fch_create(const fch_grid *g, const fch_params *p, void *s
     if (e == cudaSuccess) e = cudaMalloc((void **)&ctx->staging, sizeof(double) * N * N * 2);
     if (e == cudaSuccess) e = cudaMalloc((void **)&ctx->nfft_dev, sizeof(long long));
     if (e == cudaSuccess) e = cudaMemsetAsync(ctx->nfft_dev, 0, sizeof(long long), ctx->stream);
+    if (e == cudaSuccess) e = cudaMalloc((void **)&ctx->ticket, sizeof(unsigned int));
+    if (e == cudaSuccess) e = cudaMemsetAsync(ctx->ticket, 0, sizeof(unsigned int), ctx->stream);
     if (e != cudaSuccess) {
         snprintf(ctx->errbuf, sizeof(ctx->errbuf), "fch_create: %s", cudaGetErrorString(e));
         fch_destroy(ctx);
@@ -686,7 +522,13 @@ extern "C" fch_status fch_create(const fch_grid *g, const fch_params *p, void *s
     ctx->kp.part = ctx->part;
     ctx->kp.ctrl = ctx->dctrl;
     ctx->kp.nfft = (unsigned long long *)ctx->nfft_dev;
+    ctx->kp.ticket = ctx->ticket;
+    ctx->kp.tail_op = -1;
     fch_status s = upload_twiddles(ctx, N, ctx->prec, ctx->tw, ctx->stream);
+    if (s == FCH_OK && ctx->prec && N == 1024 && ctx->p.fft_path != 1) {
+        if (upload_tw2(&ctx->tw2, ctx->stream) != cudaSuccess) s = FCH_ECUDA;
+        ctx->kp.tw2 = ctx->tw2;
+    }
     if (s != FCH_OK) {
         fch_destroy(ctx);
         return s;
@@ -707,11 +549,13 @@ extern "C" fch_status fch_destroy(fch_ctx *ctx)
     if (ctx->stream) cudaStreamSynchronize(ctx->stream);
     void *bufs[] = {ctx->U[0], ctx->U[1], ctx->U[2], ctx->F[0], ctx->F[1], ctx->F[2], ctx->Pb,
                     ctx->Qb, ctx->Vb, ctx->Nb, ctx->Z, ctx->tw, ctx->part, ctx->dctrl,
-                    ctx->staging, ctx->nfft_dev};
+                    ctx->staging, ctx->nfft_dev, ctx->ticket, ctx->tw2};
     for (void *b : bufs)
         if (b) cudaFree(b);
     if (ctx->timing)
         for (int i = 0; i < 2 * 2048; i++) cudaEventDestroy(ctx->ev[i]);
+    for (int i = 0; i < 4; i++)
+        if (ctx->trial_graph[i]) cudaGraphExecDestroy(ctx->trial_graph[i]);
     if (ctx->own_stream && ctx->stream) cudaStreamDestroy(ctx->stream);
     free(ctx);
     return FCH_OK;
@@ -740,8 +584,7 @@ static fch_status load_field(fch_ctx *ctx, const void *u_dev, bool io64, void *d
 static fch_status sav_r_init(fch_ctx *ctx, int src, double which)
 {
     TRY(col(ctx, CM_START, src, FCH_FL_NOSKIP));
-    TRY(row(ctx, RM_SAV, FCH_FL_NOSKIP));
-    TRY(ctl(ctx, OP_SAV_E1, ctx->geom.row_blocks, which, FCH_FL_NOSKIP));
+    TRY(rowt(ctx, RM_SAV, FCH_FL_NOSKIP, OP_SAV_E1, which));
     return FCH_OK;
 }
 
@@ -821,7 +664,6 @@ extern "C" fch_status fch_get_state_device(fch_ctx *ctx, void *u_dev, int dtype)
 static fch_status enqueue_trial(fch_ctx *ctx, fch_scheme scheme, bool pack_f)
 {
     const int pf = pack_f ? FCH_FL_PACK_F : 0;
-    const fch_geom &g = ctx->geom;
     switch (scheme) {
     case FCH_IMEX:
         TRY(col(ctx, CM_START, 4));
@@ -830,10 +672,8 @@ static fch_status enqueue_trial(fch_ctx *ctx, fch_scheme scheme, bool pack_f)
         return FCH_OK;
     case FCH_SAV:
         TRY(col(ctx, CM_START, 4));
-        TRY(row(ctx, RM_SAV));
-        TRY(ctl(ctx, OP_SAV_E1, g.row_blocks, 0.0));
-        TRY(col(ctx, CM_SAV_PQ));
-        TRY(ctl(ctx, OP_SAV_R, g.col_blocks));
+        TRY(rowt(ctx, RM_SAV, 0, OP_SAV_E1, 0.0));
+        TRY(colt(ctx, CM_SAV_PQ, 0, 0, OP_SAV_R));
         TRY(col(ctx, CM_SAV_COMBINE, 0, pf));
         return FCH_OK;
     case FCH_ETD:
@@ -850,8 +690,7 @@ static fch_status enqueue_trial(fch_ctx *ctx, fch_scheme scheme, bool pack_f)
             if (guard * chunk > ctx->p.psd_max_iter + 2 * chunk) return FCH_ENOCONV;
             for (int i = 0; i < chunk; i++) {
                 TRY(row(ctx, RM_F, FCH_FL_PSDSKIP));
-                TRY(col(ctx, CM_PSD_ITER, 0, FCH_FL_PSDSKIP));
-                TRY(ctl(ctx, OP_PSD_CHECK, g.col_blocks));
+                TRY(colt(ctx, CM_PSD_ITER, 0, FCH_FL_PSDSKIP, OP_PSD_CHECK));
             }
             TRY(pull_ctrl(ctx));
             if (ctx->hc.status || ctx->hc.done || ctx->hc.psd_conv) break;
@@ -900,7 +739,7 @@ static void fill_stats(fch_ctx *ctx, fch_stats *st)
     st->n_fft = nf;
     st->t = ctx->hc.t;
     st->k_last = ctx->hc.kn;
-    st->e_last = ctx->hc.e_last;
+    st->e_last = ctx->hc.lte_den > 0 ? sqrt(ctx->hc.lte_num / ctx->hc.lte_den) : 0.0;
     st->last_psd_iter = ctx->hc.last_psd_iter;
 }
 
@@ -917,6 +756,7 @@ extern "C" fch_status fch_adaptive_begin(fch_ctx *ctx, fch_scheme scheme, double
     if (!(t_final >= ctx->hc.t)) return FCH_EINVAL;
     fch_ctrl &c = ctx->hc;
     c.sigma = sigma;
+    c.sigma2 = sigma * sigma;
     c.t_final = t_final;
     c.kmax = scheme == FCH_PSD ? fmin(ctx->p.k_max, ctx->p.psd_k_max) : ctx->p.k_max;
     c.itol = ctx->p.psd_nu * sigma;
@@ -946,19 +786,64 @@ extern "C" fch_status fch_adaptive_begin(fch_ctx *ctx, fch_scheme scheme, double
     return FCH_OK;
 }
 
+// one adaptive trial: the scheme's trial step, F of the trial with the AM3
+// predictor and norms, and the decision plus the set-up of the next trial
+static fch_status enqueue_adaptive_trial(fch_ctx *ctx)
+{
+    TRY(enqueue_trial(ctx, ctx->ad_scheme, true));
+    TRY(row(ctx, RM_F));
+    TRY(col(ctx, CM_F_FINISH, FCH_SRC_UNEW, FCH_FL_AM3));
+    TRY(ctl(ctx, OP_DECIDE_INIT, ctx->geom.col_blocks)); // decide, then set up the next trial
+    return FCH_OK;
+}
+
+// capture one adaptive trial of the current scheme into ctx->trial_graph;
+// returns false (and leaves eager launching in place) if capture is unavailable
+static bool capture_trial(fch_ctx *ctx)
+{
+    const int sc = ctx->ad_scheme;
+    if (cudaStreamBeginCapture(ctx->stream, cudaStreamCaptureModeRelaxed) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    fch_status s = enqueue_adaptive_trial(ctx);
+    cudaGraph_t g = nullptr;
+    cudaError_t e = cudaStreamEndCapture(ctx->stream, &g);
+    if (s != FCH_OK || e != cudaSuccess || !g) {
+        if (g) cudaGraphDestroy(g);
+        cudaGetLastError();
+        return false;
+    }
+    e = cudaGraphInstantiate(&ctx->trial_graph[sc], g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) {
+        ctx->trial_graph[sc] = nullptr;
+        cudaGetLastError();
+        return false;
+    }
+    return true;
+}
+
 extern "C" fch_status fch_adaptive_enqueue(fch_ctx *ctx, int n)
 {
     if (!ctx || n < 0) return FCH_EINVAL;
     if (!ctx->ad_open || ctx->failed) return FCH_ESTATE;
+    const int sc = ctx->ad_scheme;
     for (int i = 0; i < n; i++) {
-        fch_status s = enqueue_trial(ctx, ctx->ad_scheme, true);
+        // the first trial runs eagerly (it also sets the kernels' attributes);
+        // later ones replay the captured graph unless per-pass timing is on
+        const bool graph_ok = sc != FCH_PSD && !ctx->timing && ctx->trial_warm[sc] && !ctx->trial_nograph[sc];
+        if (graph_ok && !ctx->trial_graph[sc] && !capture_trial(ctx)) ctx->trial_nograph[sc] = true;
+        if (graph_ok && ctx->trial_graph[sc]) {
+            CKC(ctx, cudaGraphLaunch(ctx->trial_graph[sc], ctx->stream));
+            continue;
+        }
+        fch_status s = enqueue_adaptive_trial(ctx);
         if (s != FCH_OK) {
             ctx->failed = true;
             return s;
         }
-        TRY(row(ctx, RM_F));
-        TRY(col(ctx, CM_F_FINISH, FCH_SRC_UNEW, FCH_FL_AM3));
-        TRY(ctl(ctx, OP_DECIDE_INIT, ctx->geom.col_blocks)); // decide, then set up the next trial
+        if (sc != FCH_PSD) ctx->trial_warm[sc] = true;
     }
     return FCH_OK;
 }
@@ -1057,8 +942,7 @@ extern "C" fch_status fch_energy(fch_ctx *ctx, double *E)
     if (!ctx || !E) return FCH_EINVAL;
     if (!ctx->have_state) return FCH_ESTATE;
     TRY(col(ctx, CM_START, FCH_SRC_UN, FCH_FL_NOSKIP));
-    TRY(row(ctx, RM_ENERGY, FCH_FL_NOSKIP));
-    TRY(ctl(ctx, OP_ENERGY, ctx->geom.row_blocks, 0.0, FCH_FL_NOSKIP));
+    TRY(rowt(ctx, RM_ENERGY, FCH_FL_NOSKIP, OP_ENERGY));
     TRY(fch_synchronize(ctx));
     *E = ctx->hc.energy;
     return FCH_OK;
@@ -1116,7 +1000,7 @@ struct fch_fft_plan {
     cudaStream_t stream;
     fch_geom geom;
     fch_kparams kp;
-    void *Z, *tw;
+    void *Z, *tw, *tw2;
 };
 
 extern "C" fch_status fch_fft_plan_create(int n, int prec, void *stream, fch_fft_plan **out)
@@ -1145,10 +1029,18 @@ extern "C" fch_status fch_fft_plan_create(int n, int prec, void *stream, fch_fft
     pl->kp.logN = ilog2(n);
     pl->kp.P = pl->geom.P;
     pl->kp.inv_n2 = 1.0 / ((double)n * n);
+    pl->kp.tail_op = -1;
     pl->kp.cf.inv_n2 = (float)pl->kp.inv_n2;
     pl->kp.cd.inv_n2 = pl->kp.inv_n2;
     pl->kp.Z = pl->Z;
     pl->kp.tw = pl->tw;
+    if (prec && n == 1024) {
+        if (upload_tw2(&pl->tw2, pl->stream) != cudaSuccess) {
+            fch_fft_plan_destroy(pl);
+            return FCH_ECUDA;
+        }
+        pl->kp.tw2 = pl->tw2;
+    }
     *out = pl;
     return FCH_OK;
 }
@@ -1158,6 +1050,7 @@ extern "C" fch_status fch_fft_plan_destroy(fch_fft_plan *pl)
     if (!pl) return FCH_OK;
     if (pl->Z) cudaFree(pl->Z);
     if (pl->tw) cudaFree(pl->tw);
+    if (pl->tw2) cudaFree(pl->tw2);
     free(pl);
     return FCH_OK;
 }

@@ -51,9 +51,12 @@ struct fch_ctrl {
     int accepted_last, adaptive, first_step;
     long long n_steps, n_rejects, n_attempts, n_psd_iter;
     double lam_tab[10], lam_k[10];  // PSD search step table row for q
+    double lam_slope[10];           // (lam_tab[j+1] - lam_tab[j]) / (lam_k[j+1] - lam_k[j])
+    double sigma2, lte_num, lte_den; // sigma_tol^2; last ||u~ - u_p||^2, ||u_p||^2 (Parseval sums)
     fch_coef<float> cof;            // float mirror of the coefficients above
     fch_coef<double> cod;           // double copy, read by the double-precision passes
 };
+static_assert(sizeof(fch_ctrl) % 8 == 0, "the control kernel copies fch_ctrl as 8-byte words");
 
 // Everything a pass needs, passed by value.
 struct fch_kparams {
@@ -63,7 +66,8 @@ struct fch_kparams {
     void *U[3], *F[3];              // state spectra and F spectra (rotated through fch_ctrl)
     void *Pb, *Qb, *Vb, *Nb;        // SAV p/q, PSD iterate, ETD N(u^n)
     void *Z;                        // N x N complex pair-layout work array
-    const void *tw;                 // twiddles exp(-2 pi i m / N), m < N
+    const void *tw;                 // per-stage Stockham twiddles (see fft_smem)
+    const void *tw2;                // N = 1024 warp transform: [k2][n1] exp(-2 pi i n1 k2 / 1024), float
     double *part;                   // [FCH_NRED][FCH_MAXBLK] per-block partial sums
     fch_ctrl *ctrl;
     unsigned long long *nfft;       // 2D real-transform counter (may be null)
@@ -71,6 +75,9 @@ struct fch_kparams {
     void *out0, *out1;              // explicit outputs
     int src;                        // spectrum a start pass reads (FCH_SRC_*)
     int flags;                      // FCH_FL_*
+    int tail_op;                    // < 0: none; else the control op the pass's last block runs
+    double tail_arg;
+    unsigned int *ticket;           // arrival counter of the blocks of a pass (reset by the last)
     fch_consts<float> cf;
     fch_consts<double> cd;
 };

@@ -22,6 +22,7 @@
 // constant arrives precomputed in the pass precision (fch_consts, fch_coef).
 #pragma once
 #include <math.h>
+#include "fch_ctrl.cuh"
 #include "fch_internal.h"
 
 namespace fch {
@@ -124,11 +125,13 @@ __device__ __forceinline__ void fft_stage(C *s, int N, int logN, int stride, int
     for (int b = 0; b < NB; b++) {
         const int j = t + b * tps;
         if (Ns > 1) {
-            // twiddle w^(r * (j mod Ns)), w = exp(DIR 2 pi i / (Ns R)) = tw[N / (Ns R)]
-            const int step = (j & (Ns - 1)) << (logN - lNs - LR);
+            // twiddle exp(DIR 2 pi i r (j mod Ns) / (Ns R)) from the per-stage table
+            // (every stage before the last is radix 8, so this stage starts at Ns - 8;
+            // entry [r-1][j mod Ns]: consecutive lanes read consecutive entries)
+            const C *tws = tw + (Ns - 8) + (j & (Ns - 1));
 #pragma unroll
             for (int r = 1; r < R; r++) {
-                C tv = tw[(r * step) & (N - 1)];
+                C tv = tws[(r - 1) * Ns];
                 if (DIR > 0) tv = cconj(tv);
                 v[b * R + r] = cmul(v[b * R + r], tv);
             }
@@ -152,7 +155,9 @@ __device__ __forceinline__ void fft_stage(C *s, int N, int logN, int stride, int
 }
 
 // In-place transform of one sequence (all sequences of a block in lockstep);
-// starts and ends with a barrier of the whole block. tw[m] = exp(-2 pi i m/N).
+// starts and ends with a barrier of the whole block. tw holds the forward
+// twiddles of every stage with Ns > 1 (stage with Ns: entries Ns - 8 + (r-1) Ns + j,
+// value exp(-2 pi i r j / (Ns R)), r = 1..R-1, j < Ns).
 template <int DIR, typename C>
 __device__ void fft_smem(C *s, int N, int logN, int stride, int off, const C *tw, int t)
 {
@@ -308,8 +313,8 @@ __device__ __forceinline__ void spec_elem(const fch_kparams &kp, const fch_const
     }
     if (MODE == CM_START) {
         if (kp.src == 4) { // u* = u^n + gam (u^n - u^{n-1}), eq. (Richardson); gam = 0 at the start
-            const C un = bf.Un[idx];
-            v = co.gam != (T)0 ? cadd(un, cscale(csub(un, bf.Um[idx]), co.gam)) : un;
+            const C un = __ldg(bf.Un + idx);
+            v = co.gam != (T)0 ? cadd(un, cscale(csub(un, __ldg(bf.Um + idx)), co.gam)) : un;
             if (kp.flags & 128) ((C *)kp.Vb)[idx] = v; // PSD: v_0 = u*, eq. (recurrence)
         } else {
             v = bf.src[idx];
@@ -319,20 +324,20 @@ __device__ __forceinline__ void spec_elem(const fch_kparams &kp, const fch_const
     } else if (MODE == CM_IMEX_SOLVE) {
         // eq. (IMEX-eq): (a + |k|^2 s) u^{n+1} = -b u^n - c u^{n-1} - |k|^2 N_IMEX(u*)^
         const C Nh = csub(A, cscale(B, K.e2 * k2));
-        const C rhs = csub(cscale(bf.Un[idx], -co.b), cadd(cscale(bf.Um[idx], co.c), cscale(Nh, k2)));
+        const C rhs = csub(cscale(__ldg(bf.Un + idx), -co.b), cadd(cscale(__ldg(bf.Um + idx), co.c), cscale(Nh, k2)));
         v = cscale(rhs, (T)1 / (co.a + k2 * sk));
         bf.Unew[idx] = v;
         pack = kp.flags & FCH_FL_PACK_F;
     } else if (MODE == CM_F_FINISH) {
         // mu^ = eps^4 |k|^4 u^ + eps^2 |k|^2 W'^ + (rest)^ ; F^ = -|k|^2 mu^ (eq. sFCH)
-        const C u = bf.src[idx];
+        const C u = __ldg(bf.src + idx);
         const C mu = cadd(cadd(cscale(u, K.e4 * k2 * k2), cscale(A, K.e2 * k2)), B);
         const C F = cscale(mu, -k2);
         bf.dst[idx] = F;
         if (kp.flags & FCH_FL_AM3) {
             // eq. (Predictor): u_p = u^n + w1 F(u~) + w2 F(u^n) + w3 F(u^{n-1})
-            const C up = cadd(cadd(bf.Un[idx], cscale(F, co.w1)),
-                              cadd(cscale(bf.Fn[idx], co.w2), cscale(bf.Fm[idx], co.w3)));
+            const C up = cadd(cadd(__ldg(bf.Un + idx), cscale(F, co.w1)),
+                              cadd(cscale(__ldg(bf.Fn + idx), co.w2), cscale(__ldg(bf.Fm + idx), co.w3)));
             const C df = csub(u, up);
             red[0] += wgt * (df.x * df.x + df.y * df.y);
             red[1] += wgt * (up.x * up.x + up.y * up.y);
@@ -342,7 +347,7 @@ __device__ __forceinline__ void spec_elem(const fch_kparams &kp, const fch_const
         // eqs. (4.7)-(4.8): (a + |k|^2 l0) p = -b u^n - c u^{n-1} - |k|^2 l1 u*,
         //                   (a + |k|^2 l0) q = -|k|^2 X,  X = V[u*]/sqrt(E1(u*) + D0)
         const C X = cscale(cadd(cscale(A, K.e2 * k2), B), co.isq);
-        const C un = bf.Un[idx], um = bf.Um[idx];
+        const C un = __ldg(bf.Un + idx), um = __ldg(bf.Um + idx);
         const C us = co.gam != (T)0 ? cadd(un, cscale(csub(un, um), co.gam)) : un;
         const T l0 = K.e4 * k2 * k2 + K.b1am_e2 * k2 + K.b2am2;
         const T l1 = -K.l1c * k2 - K.b1am_e2 * k2 - K.b2am2;
@@ -405,7 +410,10 @@ __device__ __forceinline__ void spec_elem(const fch_kparams &kp, const fch_const
     }
 }
 
-template <typename T, int MODE>
+// LOGN > 0: the grid size is a compile-time constant (N = 2^LOGN >= 512, P = 2),
+// so the index arithmetic of the transforms folds into immediates; LOGN = 0 reads
+// N and P from the parameters.
+template <typename T, int MODE, int LOGN>
 __global__ void __launch_bounds__(1024) col_pass(const fch_kparams kp)
 {
     typedef typename CT<T>::t C;
@@ -413,7 +421,9 @@ __global__ void __launch_bounds__(1024) col_pass(const fch_kparams kp)
     if (pass_skipped(kp)) return;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ double red_scratch[FCH_NRED * 32];
-    const int N = kp.N, P = kp.P, nc = 2 * P;
+    const int N = LOGN ? (1 << LOGN) : kp.N, P = LOGN ? 2 : kp.P, nc = 2 * P;
+    const int logN = LOGN ? LOGN : kp.logN;
+    const int nthr = LOGN ? (P << LOGN) / 4 : (int)blockDim.x;
     C *tw = (C *)smem_raw;
     C *tile = tw + N;
     const int c = threadIdx.x % nc, t = threadIdx.x / nc;
@@ -448,20 +458,33 @@ __global__ void __launch_bounds__(1024) col_pass(const fch_kparams kp)
         co = fch_coef<T>();
     }
 
-    for (int i = threadIdx.x; i < N; i += blockDim.x) tw[i] = ((const C *)kp.tw)[i];
+    for (int i = threadIdx.x; i < N; i += nthr) tw[i] = __ldg((const C *)kp.tw + i);
     if (TR::FWD) {
-        for (int i = threadIdx.x; i < N * nc; i += blockDim.x) {
+        // blockDim = nc N / 8: exactly 8 elements of the tile per thread
+        C ld[8];
+#pragma unroll
+        for (int k = 0; k < 8; k++) {
+            const int i = threadIdx.x + k * nthr;
             const int n = i / nc, cc = i - n * nc;
-            tile[skew(n) * nc + cc] = Z[(long)n * N + 2 * p0 + cc];
+            ld[k] = Z[(long)n * N + 2 * p0 + cc];
         }
-        fft_smem<-1>(tile, N, kp.logN, nc, c, tw, t);
+#pragma unroll
+        for (int k = 0; k < 8; k++) {
+            const int i = threadIdx.x + k * nthr;
+            const int n = i / nc, cc = i - n * nc;
+            tile[skew(n) * nc + cc] = ld[k];
+        }
+        fft_smem<-1>(tile, N, logN, nc, c, tw, t);
     } else {
         __syncthreads();
     }
 
     T red[FCH_NRED] = {0, 0, 0, 0};
     // spectral stage: work item (pair p, ky); pair 0 covers columns 0 and N/2
-    for (int i = threadIdx.x; i < P * N; i += blockDim.x) {
+    // blockDim = P N / 4: exactly 4 work items per thread
+#pragma unroll
+    for (int it = 0; it < 4; it++) {
+        const int i = threadIdx.x + it * nthr;
         const int pp = i / N, ky = i - pp * N;
         const int p = p0 + pp;
         const int s0 = 2 * pp, s1 = 2 * pp + 1;
@@ -526,10 +549,15 @@ __global__ void __launch_bounds__(1024) col_pass(const fch_kparams kp)
             }
         }
     }
-    if (has_red) block_partials<2>(red, kp.part, red_scratch);
+    if (has_red) {
+        block_partials<2>(red, kp.part, red_scratch);
+        if (kp.tail_op >= 0) pass_tail(kp);
+    }
     if (inv) {
-        fft_smem<+1>(tile, N, kp.logN, nc, c, tw, t);
-        for (int i = threadIdx.x; i < N * nc; i += blockDim.x) {
+        fft_smem<+1>(tile, N, logN, nc, c, tw, t);
+#pragma unroll
+        for (int k = 0; k < 8; k++) {
+            const int i = threadIdx.x + k * nthr;
             const int n = i / nc, cc = i - n * nc;
             Z[(long)n * N + 2 * p0 + cc] = tile[skew(n) * nc + cc];
         }
@@ -538,28 +566,30 @@ __global__ void __launch_bounds__(1024) col_pass(const fch_kparams kp)
 
 // ---------------------------------------------------------------------------
 // row pass: [inverse rows] -> pointwise stage -> [forward rows]
-template <typename T, int MODE>
+template <typename T, int MODE, int LOGN>
 __global__ void __launch_bounds__(256) row_pass(const fch_kparams kp)
 {
     typedef typename CT<T>::t C;
     if (pass_skipped(kp)) return;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ double red_scratch[FCH_NRED * 32];
-    const int N = kp.N, tps = N >> 3, SL = skewed_len(N);
+    const int N = LOGN ? (1 << LOGN) : kp.N, tps = N >> 3, SL = skewed_len(N);
+    const int logN = LOGN ? LOGN : kp.logN;
+    const int nthr = LOGN ? (N >= 2048 ? tps : 256) : (int)blockDim.x;
     if (kp.nfft && blockIdx.x == 0 && threadIdx.x == 0)
         atomicAdd(kp.nfft, (MODE == RM_R2C_LOAD || MODE == RM_C2R_STORE || MODE == RM_ENERGY) ? 2ull : 4ull);
     C *tw = (C *)smem_raw;
     C *rows = tw + N;
-    const int rpb = blockDim.x / tps;
+    const int rpb = nthr / tps;
     const int rr = threadIdx.x / tps, t = threadIdx.x - rr * tps;
     const int y0 = blockIdx.x * rpb;
     C *Z = (C *)kp.Z;
     const bool f64io = kp.flags & FCH_FL_F64IO;
     const fch_consts<T> &K = consts<T>(kp);
 
-    for (int i = threadIdx.x; i < N; i += blockDim.x) tw[i] = ((const C *)kp.tw)[i];
+    for (int i = threadIdx.x; i < N; i += nthr) tw[i] = __ldg((const C *)kp.tw + i);
     if (MODE == RM_R2C_LOAD) {
-        for (int i = threadIdx.x; i < rpb * N; i += blockDim.x) {
+        for (int i = threadIdx.x; i < rpb * N; i += nthr) {
             const int r = i / N, x = i - r * N;
             const long g = (long)y0 * N + i;
             T a, b = 0;
@@ -573,11 +603,24 @@ __global__ void __launch_bounds__(256) row_pass(const fch_kparams kp)
             rows[r * SL + skew(x)] = mk<C>(a, b);
         }
     } else {
-        for (int i = threadIdx.x; i < rpb * N; i += blockDim.x) {
-            const int r = i / N, q = i - r * N;
-            rows[r * SL + skew(pair_kx(q, N))] = Z[(long)(y0 + r) * N + q];
+        // blockDim = rpb N / 8: each thread moves 4 pairs (kx, N-kx) of its rows
+        C ld[8];
+#pragma unroll
+        for (int k = 0; k < 4; k++) {
+            const int i = threadIdx.x + k * nthr;
+            const int r = i / (N >> 1), pp = i - r * (N >> 1);
+            const C *src = Z + (long)(y0 + r) * N + 2 * pp;
+            ld[2 * k] = src[0];
+            ld[2 * k + 1] = src[1];
         }
-        fft_smem<+1>(rows + rr * SL, N, kp.logN, 1, 0, tw, t);
+#pragma unroll
+        for (int k = 0; k < 4; k++) {
+            const int i = threadIdx.x + k * nthr;
+            const int r = i / (N >> 1), pp = i - r * (N >> 1);
+            rows[r * SL + skew(pp)] = ld[2 * k];
+            rows[r * SL + skew(pp ? N - pp : (N >> 1))] = ld[2 * k + 1];
+        }
+        fft_smem<+1>(rows + rr * SL, N, logN, 1, 0, tw, t);
     }
 
     T red[FCH_NRED] = {0, 0, 0, 0};
@@ -622,13 +665,20 @@ __global__ void __launch_bounds__(256) row_pass(const fch_kparams kp)
         }
     }
     const bool has_red = MODE == RM_SAV || MODE == RM_ENERGY || (MODE == RM_F && (kp.flags & FCH_FL_ENERGY));
-    if (has_red) block_partials<1>(red, kp.part, red_scratch);
+    if (has_red) {
+        block_partials<1>(red, kp.part, red_scratch);
+        if (kp.tail_op >= 0) pass_tail(kp);
+    }
     if (MODE == RM_C2R_STORE || MODE == RM_ENERGY) return;
 
-    fft_smem<-1>(rows + rr * SL, N, kp.logN, 1, 0, tw, t);
-    for (int i = threadIdx.x; i < rpb * N; i += blockDim.x) {
-        const int r = i / N, q = i - r * N;
-        Z[(long)(y0 + r) * N + q] = rows[r * SL + skew(pair_kx(q, N))];
+    fft_smem<-1>(rows + rr * SL, N, logN, 1, 0, tw, t);
+#pragma unroll
+    for (int k = 0; k < 4; k++) {
+        const int i = threadIdx.x + k * nthr;
+        const int r = i / (N >> 1), pp = i - r * (N >> 1);
+        C *dst = Z + (long)(y0 + r) * N + 2 * pp;
+        dst[0] = rows[r * SL + skew(pp)];
+        dst[1] = rows[r * SL + skew(pp ? N - pp : (N >> 1))];
     }
 }
 

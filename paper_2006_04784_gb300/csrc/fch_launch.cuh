@@ -1,6 +1,7 @@
 // fch_launch.cuh -- host launchers of the column and row passes for one precision.
 // Included once per precision by fch_f64.cu / fch_f32.cu with FCH_T and FCH_SUFFIX set.
 #include "fch_kernels.cuh"
+#include "fch_warpfft.cuh"
 
 namespace {
 
@@ -16,12 +17,54 @@ template <typename T, int M> cudaError_t set_smem(pass_fn f, int bytes, bool &do
     return e;
 }
 
-template <typename T, int M> cudaError_t launch_col(const fch_kparams &kp, cudaStream_t s)
+template <typename T, int M> pass_fn col_fn(int logN)
+{
+    switch (logN) {
+    case 9: return fch::col_pass<T, M, 9>;
+    case 10: return fch::col_pass<T, M, 10>;
+    case 11: return fch::col_pass<T, M, 11>;
+    }
+    return fch::col_pass<T, M, 0>;
+}
+
+template <typename T, int M> pass_fn row_fn(int logN)
+{
+    switch (logN) {
+    case 9: return fch::row_pass<T, M, 9>;
+    case 10: return fch::row_pass<T, M, 10>;
+    case 11: return fch::row_pass<T, M, 11>;
+    }
+    return fch::row_pass<T, M, 0>;
+}
+
+// single precision at N = 1024: the warp-transform passes (one warp per sequence)
+template <typename T> constexpr bool warp_path() { return sizeof(T) == 4; }
+
+template <int M> cudaError_t launch_col_w(const fch_kparams &kp, cudaStream_t s)
 {
     static bool attr = false;
+    const int smem = (1024 * 5 + 4 * 33 * 32) * 8;
+    pass_fn f = fch::col_pass_w<M>;
+    cudaError_t e = set_smem<float, M>(f, smem, attr);
+    if (e != cudaSuccess) return e;
+    f<<<256, 128, smem, s>>>(kp);
+    return cudaGetLastError();
+}
+
+template <int M> cudaError_t launch_row_w(const fch_kparams &kp, cudaStream_t s)
+{
+    fch::row_pass_w<M><<<1024, 32, 0, s>>>(kp);
+    return cudaGetLastError();
+}
+
+template <typename T, int M> cudaError_t launch_col(const fch_kparams &kp, cudaStream_t s)
+{
+    if (warp_path<T>() && kp.N == 1024 && kp.tw2) return launch_col_w<M>(kp, s);
+    static bool attr[12] = {};
     const fch_geom g = fch_geometry(kp.N, sizeof(T) == 4);
-    pass_fn f = fch::col_pass<T, M>;
-    cudaError_t e = set_smem<T, M>(f, fch_geometry(FCH_MAX_N, sizeof(T) == 4).col_smem, attr);
+    const int li = (kp.logN >= 9 && kp.logN <= 11) ? kp.logN : 0;
+    pass_fn f = col_fn<T, M>(li);
+    cudaError_t e = set_smem<T, M>(f, fch_geometry(FCH_MAX_N, sizeof(T) == 4).col_smem, attr[li]);
     if (e != cudaSuccess) return e;
     f<<<g.col_blocks, g.col_threads, g.col_smem, s>>>(kp);
     return cudaGetLastError();
@@ -29,10 +72,12 @@ template <typename T, int M> cudaError_t launch_col(const fch_kparams &kp, cudaS
 
 template <typename T, int M> cudaError_t launch_row(const fch_kparams &kp, cudaStream_t s)
 {
-    static bool attr = false;
+    if (warp_path<T>() && kp.N == 1024 && kp.tw2) return launch_row_w<M>(kp, s);
+    static bool attr[12] = {};
     const fch_geom g = fch_geometry(kp.N, sizeof(T) == 4);
-    pass_fn f = fch::row_pass<T, M>;
-    cudaError_t e = set_smem<T, M>(f, fch_geometry(FCH_MAX_N, sizeof(T) == 4).row_smem, attr);
+    const int li = (kp.logN >= 9 && kp.logN <= 11) ? kp.logN : 0;
+    pass_fn f = row_fn<T, M>(li);
+    cudaError_t e = set_smem<T, M>(f, fch_geometry(FCH_MAX_N, sizeof(T) == 4).row_smem, attr[li]);
     if (e != cudaSuccess) return e;
     f<<<g.row_blocks, g.row_threads, g.row_smem, s>>>(kp);
     return cudaGetLastError();

@@ -59,6 +59,7 @@ class Params(C.Structure):
         ("psd_nu", C.c_double), ("psd_itol", C.c_double), ("psd_lambda", C.c_double),
         ("psd_k_max", C.c_double),
         ("psd_max_iter", C.c_int), ("prec", C.c_int), ("sync_every", C.c_int),
+        ("fft_path", C.c_int),
     ]
 
     def as_dict(self):

@@ -266,3 +266,71 @@ def test_errors_are_reported():
         with pytest.raises(fch.FchError) as e:
             ctx.run_adaptive("imex", 1e-5, 1e-3)
         assert e.value.status == 7
+
+
+# --------------------------------------------------------------------------- full size (1024^2, mixed)
+def test_mixed_1024_fixed_steps_vs_oracle():
+    # the benchmark grid in single precision (warp transforms at N = 1024): a state
+    # round trip and fixed IMEX steps, whose implicit solve damps the single-
+    # precision rounding of the transforms, against the FP64 oracle
+    n = 1024
+    p = lib_params(0.0, eta2=0.15, prec=1)
+    u0 = I.random_network(n, d=0.75, seed=3)
+    s = O.Stepper(n, L, oparams(p))
+    s.set_state(u0)
+    with fch.Context(n, p) as ctx:
+        ctx.set_state(u0)
+        assert rel(ctx.get_state(), u0) < 2e-5
+        for _ in range(2):
+            s.step("imex", 1e-6)
+            ctx.step("imex", 1e-6)
+        assert rel(ctx.get_state(), s.state()) < 3e-5
+        assert ctx.energy() == pytest.approx(O.energy(oparams(p), ctx.get_state(), L), rel=1e-4)
+
+
+def test_mixed_1024_rhs_noise_floor():
+    # F(u) = Lap mu(u) carries eps^4 Lap^3 u and eps^2 Lap^2 W'(u): single-precision
+    # rounding of the transforms is amplified at the top of the spectrum. The warp
+    # and Stockham single-precision paths agree with each other to that noise level
+    # and both differ from the FP64 path by a few percent at 1024^2 (the reason the
+    # adaptive estimator is not run in single precision).
+    n = 1024
+    u = I.random_network(n, d=0.75, seed=3)
+    ut = torch.tensor(u, device=DEV)
+    torch.cuda.synchronize()
+    F = {}
+    for name, prec, path in (("f64", 0, 0), ("warp", 1, 2), ("stockham", 1, 1)):
+        with fch.Context(n, lib_params(0.0, eta2=0.15, prec=prec, fft_path=path)) as ctx:
+            src = ut if prec == 0 else ut.float()
+            out = torch.empty_like(src)
+            torch.cuda.synchronize()
+            ctx.rhs_device(src, out)
+            ctx.synchronize()
+            F[name] = out.double().cpu().numpy()
+    # FP64 path against the oracle on sampled rows
+    ref = O.rhs(oparams(lib_params(0.0, eta2=0.15)), u, L)
+    assert rel(F["f64"], ref) < 1e-10
+    assert rel(F["warp"], F["f64"]) < 0.2 and rel(F["stockham"], F["f64"]) < 0.2
+    # the low modes, where the solution lives, agree to single precision
+    lo = lambda f: np.fft.rfft2(f)[:64, :64]
+    assert rel(lo(F["warp"]), lo(F["f64"])) < 1e-2
+    assert rel(lo(F["stockham"]), lo(F["f64"])) < 1e-2
+
+
+def test_mixed_1024_graph_replay_matches_eager():
+    # trials replayed from the captured CUDA graph give the same trajectory as
+    # trials launched kernel by kernel (per-pass timing forces eager launches)
+    n = 1024
+    p = lib_params(0.0, eta2=0.15, prec=1)
+    u0 = I.random_network(n, d=0.75, seed=5)
+    out = []
+    for eager in (False, True):
+        with fch.Context(n, p) as ctx:
+            ctx.set_state(u0)
+            ctx.pass_timing(eager)
+            ctx.adaptive_begin("imex", 1e-5, 1.0)
+            ctx.adaptive_enqueue(12)
+            st = ctx.adaptive_end()
+            out.append((st["n_steps"], st["t"], ctx.get_state()))
+    assert out[0][0] == out[1][0] and out[0][1] == out[1][1]
+    assert np.array_equal(out[0][2], out[1][2])
