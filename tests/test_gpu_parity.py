@@ -307,9 +307,10 @@ def test_mixed_1024_rhs_noise_floor():
             ctx.rhs_device(src, out)
             ctx.synchronize()
             F[name] = out.double().cpu().numpy()
-    # FP64 path against the oracle on sampled rows
+    # FP64 path against the oracle; F carries six derivatives, so rounding at 1e-16
+    # is amplified about 1e6 at the top of a 1024^2 spectrum
     ref = O.rhs(oparams(lib_params(0.0, eta2=0.15)), u, L)
-    assert rel(F["f64"], ref) < 1e-10
+    assert rel(F["f64"], ref) < 1e-9
     assert rel(F["warp"], F["f64"]) < 0.2 and rel(F["stockham"], F["f64"]) < 0.2
     # the low modes, where the solution lives, agree to single precision
     lo = lambda f: np.fft.rfft2(f)[:64, :64]
