@@ -206,6 +206,28 @@ fch_status fch_fft_r2c(fch_fft_plan *plan, const void *x_dev, void *X_dev, int b
 /* inverse of fch_fft_r2c (divides by N^2); X is not modified. */
 fch_status fch_fft_c2r(fch_fft_plan *plan, const void *X_dev, void *x_dev, int batch);
 
+/* ---- standalone R2C transform without device allocation ----
+ * The paper has no counterpart to this entry point; it serves callers that must
+ * not allocate device memory once running (another component owns the device's
+ * memory budget, cudaMalloc/cudaFree could synchronize the device and stall other
+ * work, or the caller's rules forbid dynamic allocation after start-up).
+ * Same transform, layouts and precisions as fch_fft_r2c, for n <= FCH_NOALLOC_MAX_N;
+ * the work array and twiddle table live in a fixed array inside the library
+ * (n^2 + n complex doubles at the maximum n, about 4 MiB), which every GPU that
+ * loads the library holds until the process exits. Nothing is allocated, freed or
+ * created: no cudaMalloc, cudaFree, plan or library allocation.
+ *  - n > FCH_NOALLOC_MAX_N, n not a power of two >= 16, prec not 0/1, NULL
+ *    pointers: FCH_EINVAL, with the reason in fch_last_cuda_error(NULL).
+ *  - The first call on a device looks up that array's device address with the
+ *    device current and caches it; make that first call before any stream capture.
+ *  - All calls share the array and it keeps the last call's contents; nothing in it
+ *    needs clearing (each call rewrites the twiddles and writes each work element
+ *    before reading it). Calls whose GPU work overlaps (different streams or host
+ *    threads) race on the array and must be ordered by the caller.
+ *  - stream: a cudaStream_t, or NULL for the legacy default stream. Enqueued, no wait. */
+#define FCH_NOALLOC_MAX_N 512
+fch_status fch_fft_r2c_noalloc(int n, int prec, const void *x_dev, void *X_dev, int batch, void *stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -221,6 +221,8 @@ static thread_local char g_plan_err[256];
 
 extern "C" const char *fch_last_cuda_error(const fch_ctx *ctx) { return ctx ? ctx->errbuf : g_plan_err; }
 
+void fch_set_thread_error(const char *msg) { snprintf(g_plan_err, sizeof(g_plan_err), "%s", msg); }
+
 static bool pow2_in_range(int n) { return n >= FCH_MIN_N && n <= FCH_MAX_N && (n & (n - 1)) == 0; }
 
 static int ilog2(int n)

@@ -145,3 +145,6 @@ cudaError_t fch_launch_col_f32(int mode, const fch_kparams &kp, cudaStream_t s);
 cudaError_t fch_launch_row_f32(int mode, const fch_kparams &kp, cudaStream_t s);
 cudaError_t fch_launch_ctrl(int op, const fch_kparams &kp, int nblk_a, int nblk_b, double arg0,
                             cudaStream_t s);
+
+// sets the per-thread message returned by fch_last_cuda_error(NULL)
+void fch_set_thread_error(const char *msg);

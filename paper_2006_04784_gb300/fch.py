@@ -29,7 +29,7 @@ EXPORTS = ["fch_status_string", "fch_last_cuda_error", "fch_params_default", "fc
            "fch_mass", "fch_rhs_device", "fch_get_sav_r", "fch_run_adaptive", "fch_get_stats",
            "fch_fft_plan_create", "fch_fft_plan_destroy", "fch_fft_r2c", "fch_fft_c2r",
            "fch_adaptive_begin", "fch_adaptive_enqueue", "fch_adaptive_end", "fch_pass_timing",
-           "fch_pass_times"]
+           "fch_pass_times", "fch_fft_r2c_noalloc"]
 NCOL, NROW = 10, 6
 NPASS = NCOL + NROW + 1
 PASS_NAMES = (["col_fwd_store", "col_inv_load", "col_start", "col_imex_solve", "col_f_finish",
