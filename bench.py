@@ -47,6 +47,21 @@ def rank_info():
             int(os.environ.get("LOCAL_RANK", 0)))
 
 
+def job_throughput(local_ms: float, steps: int, world: int, device=None):
+    """Whole-job steps/s of independent replicas: every rank ran `steps` steps in
+    local_ms of device time; the job's time is the slowest rank's (max over
+    ranks, after a barrier), and value = world * steps / that time."""
+    t_ms = float(local_ms)
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        t = torch.tensor([t_ms], dtype=torch.float64, device=device)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        t_ms = float(t.item())
+        dist.barrier()
+    return world * steps / (t_ms / 1e3), t_ms
+
+
 def measured_peaks():
     try:
         return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
@@ -142,12 +157,13 @@ def run_gb300(args):
     from paper_2006_04784_gb300 import inputs as I
 
     n = N_GRID
-    p = fch.params_default(0.0, eta2=1.5 * 0.1, prec=fch.FCH_MIXED, sync_every=64)
+    prec = {"mixed": fch.FCH_MIXED, "fp64": fch.FCH_FP64, "fp32x2": fch.FCH_FP32X2}[args.prec]
+    p = fch.params_default(0.0, eta2=1.5 * 0.1, prec=prec, sync_every=64)
     u0 = I.random_network(n, d=0.75, seed=3 + rank)
     stream = torch.cuda.Stream(device=dev)
     ctx = fch.Context(n, p, stream=stream)
     ctx.set_state(u0)
-    ctx.adaptive_begin("imex", SIGMA, T_FINAL)
+    ctx.adaptive_begin(args.scheme, SIGMA, T_FINAL)
     ctx.adaptive_enqueue(max(args.warmup, 3))
     ctx.synchronize()
     st0 = ctx.stats()
@@ -185,14 +201,8 @@ def run_gb300(args):
     times = ctx.pass_times()
     ctx.pass_timing(False)
     ctx.adaptive_end()
-    tot_ms = sum(step_ms)
-    if world > 1:
-        t = torch.tensor([tot_ms], device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        tot_ms = float(t.item())
-        torch.distributed.barrier()
+    value, tot_ms = job_throughput(sum(step_ms), K, world, dev)
     ms_per_step = tot_ms / K
-    value = world * K / (tot_ms / 1e3)
     nfft = st1["n_fft"] - st0["n_fft"]
     eager_ms_per_step = sum(step_ms_eager) / K2
     # dominant kernel and its roofline
@@ -200,7 +210,7 @@ def run_gb300(args):
     hbm = peaks.get("hbm_gbs")
     dom = max((k for k in times if k != "ctrl"), key=lambda k: times[k][0])
     dms, dn = times[dom]
-    csz = 8  # complex64 in mixed precision
+    csz = 8 if prec == fch.FCH_MIXED else 16  # bytes per complex element
     ab = pass_bytes(dom, n, csz)
     achieved = ab / (dms / dn / 1e3) / 1e9 if ab else None
     roof = {"kernel": dom, "bound": "hbm", "achieved": achieved, "peak": hbm,
@@ -350,6 +360,9 @@ def main():
     ap.add_argument("--warmup", type=int, default=20)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--prec", default="mixed", choices=["mixed", "fp64", "fp32x2"],
+                    help="mixed (single-precision transforms), fp64, or fp32x2 (double-float)")
+    ap.add_argument("--scheme", default="imex", choices=["imex", "sav", "etd"])
     args = ap.parse_args()
     out = run_reference(args) if args.impl == "reference" else run_gb300(args)
     if out is not None:

@@ -53,8 +53,14 @@ typedef enum { FCH_IMEX = 0, FCH_SAV = 1, FCH_PSD = 2, FCH_ETD = 3 } fch_scheme;
 /* FCH_FP64: every stage in double precision.
  * FCH_MIXED: transforms and pointwise stages in single precision; the mass,
  * energy, SAV inner products and auxiliary scalar, the LTE norms and the
- * step-size controller stay in double precision. */
-typedef enum { FCH_FP64 = 0, FCH_MIXED = 1 } fch_precision;
+ * step-size controller stay in double precision. At large N the single-precision
+ * rounding of the transforms, amplified by the sixth-order operator in F(u),
+ * dominates the AM3 error estimate; use it for fixed steps.
+ * FCH_FP32X2: transforms and pointwise stages in double-float arithmetic (each
+ * value an unevaluated sum of two floats, about 48 bits) on the single-precision
+ * pipe; reductions and controller in double. Accuracy of the FP64 mode to ~1e-13
+ * per step. */
+typedef enum { FCH_FP64 = 0, FCH_MIXED = 1, FCH_FP32X2 = 2 } fch_precision;
 
 typedef struct {
     int n;       /* grid points per side, power of two in [16, 2048] */

@@ -15,7 +15,7 @@
 fch_geom fch_geometry(int N, int prec)
 {
     fch_geom g;
-    const int csz = prec ? 8 : 16; // bytes per complex element
+    const int csz = prec == 1 ? 8 : 16; // bytes per complex element (single: 8; double, double-float: 16)
     int P = 1024 / N;
     if (P < 2) P = 2;
     if (P > N / 2) P = N / 2;
@@ -273,7 +273,14 @@ static cudaError_t upload_tw2(void **dst, cudaStream_t s)
 
 static fch_status upload_twiddles(fch_ctx *ctx, int N, int prec, void *dst, cudaStream_t s)
 {
-    if (prec) {
+    if (prec == FCH_FP32X2) {
+        fch::df *h = (fch::df *)malloc(sizeof(fch::df) * 2 * N);
+        make_twiddles(N, h);
+        cudaError_t e = cudaMemcpyAsync(dst, h, sizeof(fch::df) * 2 * N, cudaMemcpyHostToDevice, s);
+        cudaStreamSynchronize(s);
+        free(h);
+        if (e != cudaSuccess) return FCH_ECUDA;
+    } else if (prec) {
         float *h = (float *)malloc(sizeof(float) * 2 * N);
         make_twiddles(N, h);
         cudaError_t e = cudaMemcpyAsync(dst, h, sizeof(float) * 2 * N, cudaMemcpyHostToDevice, s);
@@ -347,6 +354,7 @@ static void fill_kparams_model(fch_kparams &kp, const fch_params &p, int N, doub
     kp.kappa2 = p.kappa2;
     fill_consts(kp.cf, p, kp.kf, kp.am, kp.inv_n2);
     fill_consts(kp.cd, p, kp.kf, kp.am, kp.inv_n2);
+    fill_consts(kp.cdf, p, kp.kf, kp.am, kp.inv_n2);
 }
 
 static void reset_ctrl(fch_ctx *ctx)
@@ -407,8 +415,9 @@ static fch_status col(fch_ctx *ctx, int mode, int src = 0, int flags = 0, const 
     kp.out0 = out0;
     kp.out1 = out1;
     timing_begin(ctx);
-    cudaError_t e = ctx->prec ? fch_launch_col_f32(mode, kp, ctx->stream)
-                              : fch_launch_col_f64(mode, kp, ctx->stream);
+    cudaError_t e = ctx->prec == FCH_MIXED    ? fch_launch_col_f32(mode, kp, ctx->stream)
+                    : ctx->prec == FCH_FP32X2 ? fch_launch_col_dfl(mode, kp, ctx->stream)
+                                              : fch_launch_col_f64(mode, kp, ctx->stream);
     timing_end(ctx, mode);
     CKC(ctx, e);
     return FCH_OK;
@@ -424,8 +433,9 @@ static fch_status row(fch_ctx *ctx, int mode, int flags = 0, const void *in0 = n
     kp.in0 = in0;
     kp.out0 = out0;
     timing_begin(ctx);
-    cudaError_t e = ctx->prec ? fch_launch_row_f32(mode, kp, ctx->stream)
-                              : fch_launch_row_f64(mode, kp, ctx->stream);
+    cudaError_t e = ctx->prec == FCH_MIXED    ? fch_launch_row_f32(mode, kp, ctx->stream)
+                    : ctx->prec == FCH_FP32X2 ? fch_launch_row_dfl(mode, kp, ctx->stream)
+                                              : fch_launch_row_f64(mode, kp, ctx->stream);
     timing_end(ctx, FCH_NCOL + mode);
     CKC(ctx, e);
     return FCH_OK;
@@ -463,7 +473,7 @@ extern "C" fch_status fch_create(const fch_grid *g, const fch_params *p, void *s
 {
     if (!g || !p || !out) return FCH_EINVAL;
     *out = nullptr;
-    if (!pow2_in_range(g->n) || !(g->L > 0) || !(p->eps > 0) || (p->prec != 0 && p->prec != 1) ||
+    if (!pow2_in_range(g->n) || !(g->L > 0) || !(p->eps > 0) || p->prec < 0 || p->prec > 2 ||
         p->fft_path < 0 || p->fft_path > 2 ||
         !(p->k_min > 0) || !(p->rho_s > 0) || p->psd_max_iter < 1)
         return FCH_EINVAL;
@@ -480,9 +490,9 @@ extern "C" fch_status fch_create(const fch_grid *g, const fch_params *p, void *s
         if (ctx->p.zeta <= 0) ctx->p.zeta = z;
         if (ctx->p.D0 <= 0) ctx->p.D0 = d;
     }
-    ctx->geom = fch_geometry(ctx->N, ctx->prec);
+    ctx->geom = fch_geometry(ctx->N, ctx->prec == FCH_MIXED);
     const int N = ctx->N;
-    const size_t csz = ctx->prec ? 8 : 16;
+    const size_t csz = ctx->prec == FCH_MIXED ? 8 : 16;
     const size_t hs = (size_t)(N / 2 + 1) * N * csz;
     cudaError_t e = cudaSuccess;
     if (stream) {
@@ -527,7 +537,7 @@ extern "C" fch_status fch_create(const fch_grid *g, const fch_params *p, void *s
     ctx->kp.ticket = ctx->ticket;
     ctx->kp.tail_op = -1;
     fch_status s = upload_twiddles(ctx, N, ctx->prec, ctx->tw, ctx->stream);
-    if (s == FCH_OK && ctx->prec && N == 1024 && ctx->p.fft_path != 1) {
+    if (s == FCH_OK && ctx->prec == FCH_MIXED && N == 1024 && ctx->p.fft_path != 1) {
         if (upload_tw2(&ctx->tw2, ctx->stream) != cudaSuccess) s = FCH_ECUDA;
         ctx->kp.tw2 = ctx->tw2;
     }
@@ -957,10 +967,14 @@ extern "C" fch_status fch_mass(fch_ctx *ctx, double *m)
     TRY(fch_synchronize(ctx));
     double re;
     const void *u0 = ctx->U[ctx->hc.iu_n];
-    if (ctx->prec) {
+    if (ctx->prec == FCH_MIXED) {
         float v[2];
         CKC(ctx, cudaMemcpy(v, u0, sizeof(v), cudaMemcpyDeviceToHost));
         re = v[0];
+    } else if (ctx->prec == FCH_FP32X2) {
+        float v[4]; // (re.hi, re.lo, im.hi, im.lo)
+        CKC(ctx, cudaMemcpy(v, u0, sizeof(v), cudaMemcpyDeviceToHost));
+        re = (double)v[0] + (double)v[1];
     } else {
         double v[2];
         CKC(ctx, cudaMemcpy(v, u0, sizeof(v), cudaMemcpyDeviceToHost));

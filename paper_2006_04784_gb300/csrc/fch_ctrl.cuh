@@ -223,6 +223,17 @@ __device__ inline void sync_coef(fch_ctrl *c)
     c->cof.k1 = (float)c->k1;
     c->cof.r_new = (float)c->r_new;
     c->cof.isq = (float)c->inv_sqrt_e1;
+    c->codf.a = fch::df(c->a);
+    c->codf.b = fch::df(c->b);
+    c->codf.c = fch::df(c->c);
+    c->codf.gam = fch::df(c->gam);
+    c->codf.w1 = fch::df(c->w1);
+    c->codf.w2 = fch::df(c->w2);
+    c->codf.w3 = fch::df(c->w3);
+    c->codf.lam = fch::df(c->lam);
+    c->codf.k1 = fch::df(c->k1);
+    c->codf.r_new = fch::df(c->r_new);
+    c->codf.isq = fch::df(c->inv_sqrt_e1);
 }
 
 

@@ -1,0 +1,125 @@
+// fch_df.cuh -- double-float arithmetic: a value is the unevaluated sum hi + lo of
+// two floats with |lo| <= ulp(hi)/2, about 48 significant bits. The FP64 pipe of
+// this GPU runs at a small fraction of the FP32 rate; carrying FP64-class
+// precision as float pairs keeps every operation on the FP32 pipe.
+//
+// Error-free transformations used (classical results, restated here):
+//   TwoSum (Knuth): s = fl(a + b), e = (a - (s - b')) + (b - b'), b' = s - a, gives
+//     a + b = s + e exactly for any floats a, b;
+//   FastTwoSum (Dekker): for |a| >= |b|, s = fl(a + b), e = b - (s - a) is exact;
+//   TwoProd with a fused multiply-add: p = fl(a b), e = fma(a, b, -p), a b = p + e.
+// Addition sums both parts with TwoSum and renormalises twice (accurate under
+// cancellation, which the butterflies of a transform produce); multiplication adds
+// the cross terms to the exact product of the high parts; division refines a float
+// quotient with two correction terms. Transcendental functions (used only by the
+// q > 0 well and the ETD phi functions) go through double.
+// Compile without fast-math: the transformations rely on IEEE rounding of each step.
+#pragma once
+#include <math.h>
+
+namespace fch {
+
+struct df {
+    float hi, lo;
+    df() = default;
+    __host__ __device__ constexpr df(float h, float l) : hi(h), lo(l) {}
+    __host__ __device__ constexpr df(double d) : hi((float)d), lo((float)(d - (double)(float)d)) {}
+    __host__ __device__ constexpr df(int i) : hi((float)i), lo(0.f) {}
+    __host__ __device__ explicit operator double() const { return (double)hi + (double)lo; }
+    __host__ __device__ explicit operator float() const { return hi + lo; }
+};
+
+struct __align__(16) df2 {
+    df x, y;
+};
+
+// read-only loads of complex elements
+__device__ __forceinline__ float2 ldg(const float2 *p) { return __ldg(p); }
+__device__ __forceinline__ double2 ldg(const double2 *p) { return __ldg(p); }
+__device__ __forceinline__ df2 ldg(const df2 *p)
+{
+    const float4 v = __ldg((const float4 *)p);
+    df2 r;
+    r.x = df(v.x, v.y);
+    r.y = df(v.z, v.w);
+    return r;
+}
+
+__device__ __forceinline__ df two_sum(float a, float b)
+{
+    const float s = a + b;
+    const float bb = s - a;
+    const float e = (a - (s - bb)) + (b - bb);
+    return df(s, e);
+}
+
+__device__ __forceinline__ df fast_two_sum(float a, float b)
+{
+    const float s = a + b;
+    return df(s, b - (s - a));
+}
+
+__device__ __forceinline__ df operator+(df a, df b)
+{
+    df s = two_sum(a.hi, b.hi);
+    const df t = two_sum(a.lo, b.lo);
+    s.lo += t.hi;
+    s = fast_two_sum(s.hi, s.lo);
+    s.lo += t.lo;
+    return fast_two_sum(s.hi, s.lo);
+}
+
+__device__ __forceinline__ df operator-(df a) { return df(-a.hi, -a.lo); }
+__device__ __forceinline__ df operator-(df a, df b) { return a + (-b); }
+
+__device__ __forceinline__ df operator*(df a, df b)
+{
+    const float p = a.hi * b.hi;
+    float e = fmaf(a.hi, b.hi, -p);
+    e = fmaf(a.hi, b.lo, e);
+    e = fmaf(a.lo, b.hi, e);
+    return fast_two_sum(p, e);
+}
+
+// by +-1 (the DIR factors of the butterflies)
+__device__ __forceinline__ df operator*(int s, df a) { return s < 0 ? -a : a; }
+
+__device__ __forceinline__ df operator/(df a, df b)
+{
+    const float rb = 1.0f / b.hi;
+    const float q1 = a.hi * rb;
+    df r = a - b * df(q1, 0.f);
+    const float q2 = r.hi * rb;
+    r = r - b * df(q2, 0.f);
+    const float q3 = r.hi * rb;
+    df q = fast_two_sum(q1, q2);
+    return q + df(q3, 0.f);
+}
+
+__device__ __forceinline__ df &operator+=(df &a, df b) { return a = a + b; }
+__device__ __forceinline__ df &operator-=(df &a, df b) { return a = a - b; }
+__device__ __forceinline__ df &operator*=(df &a, df b) { return a = a * b; }
+__device__ __forceinline__ df &operator/=(df &a, df b) { return a = a / b; }
+
+__device__ __forceinline__ bool operator<(df a, df b) { return a.hi < b.hi || (a.hi == b.hi && a.lo < b.lo); }
+__device__ __forceinline__ bool operator>(df a, df b) { return b < a; }
+__device__ __forceinline__ bool operator==(df a, df b) { return a.hi == b.hi && a.lo == b.lo; }
+__device__ __forceinline__ bool operator!=(df a, df b) { return !(a == b); }
+
+// float and double forms next to the double-float ones, so unqualified calls in
+// namespace fch find every overload
+__device__ __forceinline__ float fabs(float a) { return ::fabsf(a); }
+__device__ __forceinline__ double fabs(double a) { return ::fabs(a); }
+__device__ __forceinline__ float exp(float a) { return ::expf(a); }
+__device__ __forceinline__ double exp(double a) { return ::exp(a); }
+__device__ __forceinline__ float expm1(float a) { return ::expm1f(a); }
+__device__ __forceinline__ double expm1(double a) { return ::expm1(a); }
+__device__ __forceinline__ float copysign(float a, float b) { return ::copysignf(a, b); }
+__device__ __forceinline__ double copysign(double a, double b) { return ::copysign(a, b); }
+
+__device__ __forceinline__ df fabs(df a) { return a.hi < 0.f ? -a : a; }
+__device__ __forceinline__ df copysign(df a, df s) { return (a.hi < 0.f) != (s.hi < 0.f) ? -a : a; }
+__device__ __forceinline__ df exp(df a) { return df(::exp((double)a)); }
+__device__ __forceinline__ df expm1(df a) { return df(::expm1((double)a)); }
+
+} // namespace fch

@@ -3,6 +3,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include "fch_df.cuh"
+
 #define FCH_MIN_N 16
 #define FCH_MAX_N 2048
 #define FCH_NRED 4        // reduction slots per pass
@@ -55,6 +57,7 @@ struct fch_ctrl {
     double sigma2, lte_num, lte_den; // sigma_tol^2; last ||u~ - u_p||^2, ||u_p||^2 (Parseval sums)
     fch_coef<float> cof;            // float mirror of the coefficients above
     fch_coef<double> cod;           // double copy, read by the double-precision passes
+    fch_coef<fch::df> codf;         // double-float copy, read by the FP32x2 passes
 };
 static_assert(sizeof(fch_ctrl) % 8 == 0, "the control kernel copies fch_ctrl as 8-byte words");
 
@@ -80,6 +83,7 @@ struct fch_kparams {
     unsigned int *ticket;           // arrival counter of the blocks of a pass (reset by the last)
     fch_consts<float> cf;
     fch_consts<double> cd;
+    fch_consts<fch::df> cdf;
 };
 
 enum { FCH_SRC_UN = 0, FCH_SRC_UNEW = 1, FCH_SRC_V = 2, FCH_SRC_IN0 = 3 };
@@ -143,6 +147,8 @@ cudaError_t fch_launch_col_f64(int mode, const fch_kparams &kp, cudaStream_t s);
 cudaError_t fch_launch_row_f64(int mode, const fch_kparams &kp, cudaStream_t s);
 cudaError_t fch_launch_col_f32(int mode, const fch_kparams &kp, cudaStream_t s);
 cudaError_t fch_launch_row_f32(int mode, const fch_kparams &kp, cudaStream_t s);
+cudaError_t fch_launch_col_dfl(int mode, const fch_kparams &kp, cudaStream_t s);
+cudaError_t fch_launch_row_dfl(int mode, const fch_kparams &kp, cudaStream_t s);
 cudaError_t fch_launch_ctrl(int op, const fch_kparams &kp, int nblk_a, int nblk_b, double arg0,
                             cudaStream_t s);
 

@@ -23,6 +23,7 @@
 #pragma once
 #include <math.h>
 #include "fch_ctrl.cuh"
+#include "fch_df.cuh"
 #include "fch_internal.h"
 
 namespace fch {
@@ -31,13 +32,22 @@ template <typename T> struct CT;
 template <> struct CT<double> { typedef double2 t; };
 template <> struct CT<float> { typedef float2 t; };
 
+template <> struct CT<df> { typedef df2 t; };
+
 template <typename T> __device__ __forceinline__ const fch_consts<T> &consts(const fch_kparams &kp);
 template <> __device__ __forceinline__ const fch_consts<float> &consts<float>(const fch_kparams &kp) { return kp.cf; }
 template <> __device__ __forceinline__ const fch_consts<double> &consts<double>(const fch_kparams &kp) { return kp.cd; }
+template <> __device__ __forceinline__ const fch_consts<df> &consts<df>(const fch_kparams &kp) { return kp.cdf; }
 
 template <typename T> __device__ __forceinline__ fch_coef<T> load_coef(const fch_ctrl *c);
 template <> __device__ __forceinline__ fch_coef<float> load_coef<float>(const fch_ctrl *c) { return c->cof; }
 template <> __device__ __forceinline__ fch_coef<double> load_coef<double>(const fch_ctrl *c) { return c->cod; }
+template <> __device__ __forceinline__ fch_coef<df> load_coef<df>(const fch_ctrl *c) { return c->codf; }
+
+// type of the warp-level sums of per-thread partials (double-float partials are
+// summed as doubles)
+template <typename T> struct RedType { typedef T t; };
+template <> struct RedType<df> { typedef double t; };
 
 template <typename C> __device__ __forceinline__ C mk(decltype(C().x) x, decltype(C().x) y)
 {
@@ -215,9 +225,10 @@ template <int NR, typename T>
 __device__ void block_partials(const T *red, double *part, double *scratch)
 {
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
+    typedef typename RedType<T>::t R;
 #pragma unroll
     for (int r = 0; r < NR; r++) {
-        T v = red[r];
+        R v = (R)red[r];
         for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
         if (lane == 0) scratch[r * 32 + wid] = (double)v;
     }
@@ -313,8 +324,8 @@ __device__ __forceinline__ void spec_elem(const fch_kparams &kp, const fch_const
     }
     if (MODE == CM_START) {
         if (kp.src == 4) { // u* = u^n + gam (u^n - u^{n-1}), eq. (Richardson); gam = 0 at the start
-            const C un = __ldg(bf.Un + idx);
-            v = co.gam != (T)0 ? cadd(un, cscale(csub(un, __ldg(bf.Um + idx)), co.gam)) : un;
+            const C un = ldg(bf.Un + idx);
+            v = co.gam != (T)0 ? cadd(un, cscale(csub(un, ldg(bf.Um + idx)), co.gam)) : un;
             if (kp.flags & 128) ((C *)kp.Vb)[idx] = v; // PSD: v_0 = u*, eq. (recurrence)
         } else {
             v = bf.src[idx];
@@ -324,20 +335,20 @@ __device__ __forceinline__ void spec_elem(const fch_kparams &kp, const fch_const
     } else if (MODE == CM_IMEX_SOLVE) {
         // eq. (IMEX-eq): (a + |k|^2 s) u^{n+1} = -b u^n - c u^{n-1} - |k|^2 N_IMEX(u*)^
         const C Nh = csub(A, cscale(B, K.e2 * k2));
-        const C rhs = csub(cscale(__ldg(bf.Un + idx), -co.b), cadd(cscale(__ldg(bf.Um + idx), co.c), cscale(Nh, k2)));
+        const C rhs = csub(cscale(ldg(bf.Un + idx), -co.b), cadd(cscale(ldg(bf.Um + idx), co.c), cscale(Nh, k2)));
         v = cscale(rhs, (T)1 / (co.a + k2 * sk));
         bf.Unew[idx] = v;
         pack = kp.flags & FCH_FL_PACK_F;
     } else if (MODE == CM_F_FINISH) {
         // mu^ = eps^4 |k|^4 u^ + eps^2 |k|^2 W'^ + (rest)^ ; F^ = -|k|^2 mu^ (eq. sFCH)
-        const C u = __ldg(bf.src + idx);
+        const C u = ldg(bf.src + idx);
         const C mu = cadd(cadd(cscale(u, K.e4 * k2 * k2), cscale(A, K.e2 * k2)), B);
         const C F = cscale(mu, -k2);
         bf.dst[idx] = F;
         if (kp.flags & FCH_FL_AM3) {
             // eq. (Predictor): u_p = u^n + w1 F(u~) + w2 F(u^n) + w3 F(u^{n-1})
-            const C up = cadd(cadd(__ldg(bf.Un + idx), cscale(F, co.w1)),
-                              cadd(cscale(__ldg(bf.Fn + idx), co.w2), cscale(__ldg(bf.Fm + idx), co.w3)));
+            const C up = cadd(cadd(ldg(bf.Un + idx), cscale(F, co.w1)),
+                              cadd(cscale(ldg(bf.Fn + idx), co.w2), cscale(ldg(bf.Fm + idx), co.w3)));
             const C df = csub(u, up);
             red[0] += wgt * (df.x * df.x + df.y * df.y);
             red[1] += wgt * (up.x * up.x + up.y * up.y);
@@ -347,7 +358,7 @@ __device__ __forceinline__ void spec_elem(const fch_kparams &kp, const fch_const
         // eqs. (4.7)-(4.8): (a + |k|^2 l0) p = -b u^n - c u^{n-1} - |k|^2 l1 u*,
         //                   (a + |k|^2 l0) q = -|k|^2 X,  X = V[u*]/sqrt(E1(u*) + D0)
         const C X = cscale(cadd(cscale(A, K.e2 * k2), B), co.isq);
-        const C un = __ldg(bf.Un + idx), um = __ldg(bf.Um + idx);
+        const C un = ldg(bf.Un + idx), um = ldg(bf.Um + idx);
         const C us = co.gam != (T)0 ? cadd(un, cscale(csub(un, um), co.gam)) : un;
         const T l0 = K.e4 * k2 * k2 + K.b1am_e2 * k2 + K.b2am2;
         const T l1 = -K.l1c * k2 - K.b1am_e2 * k2 - K.b2am2;
@@ -414,7 +425,7 @@ __device__ __forceinline__ void spec_elem(const fch_kparams &kp, const fch_const
 // so the index arithmetic of the transforms folds into immediates; LOGN = 0 reads
 // N and P from the parameters.
 template <typename T, int MODE, int LOGN>
-__global__ void __launch_bounds__(1024) col_pass(const fch_kparams kp)
+__global__ void __launch_bounds__(LOGN ? ((2 << LOGN) >> 2) : 1024) col_pass(const fch_kparams kp)
 {
     typedef typename CT<T>::t C;
     typedef ColTraits<MODE> TR;
@@ -458,7 +469,7 @@ __global__ void __launch_bounds__(1024) col_pass(const fch_kparams kp)
         co = fch_coef<T>();
     }
 
-    for (int i = threadIdx.x; i < N; i += nthr) tw[i] = __ldg((const C *)kp.tw + i);
+    for (int i = threadIdx.x; i < N; i += nthr) tw[i] = ldg((const C *)kp.tw + i);
     if (TR::FWD) {
         // blockDim = nc N / 8: exactly 8 elements of the tile per thread
         C ld[8];
@@ -587,7 +598,7 @@ __global__ void __launch_bounds__(256) row_pass(const fch_kparams kp)
     const bool f64io = kp.flags & FCH_FL_F64IO;
     const fch_consts<T> &K = consts<T>(kp);
 
-    for (int i = threadIdx.x; i < N; i += nthr) tw[i] = __ldg((const C *)kp.tw + i);
+    for (int i = threadIdx.x; i < N; i += nthr) tw[i] = ldg((const C *)kp.tw + i);
     if (MODE == RM_R2C_LOAD) {
         for (int i = threadIdx.x; i < rpb * N; i += nthr) {
             const int r = i / N, x = i - r * N;

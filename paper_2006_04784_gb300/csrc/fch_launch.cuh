@@ -17,12 +17,16 @@ template <typename T, int M> cudaError_t set_smem(pass_fn f, int bytes, bool &do
     return e;
 }
 
+// compile-time grid sizes: 512, 1024, 2048 (with FCH_ONLY_1024: 1024 only, which
+// keeps the double-float translation units small); others use the generic kernel
 template <typename T, int M> pass_fn col_fn(int logN)
 {
     switch (logN) {
+#ifndef FCH_ONLY_1024
     case 9: return fch::col_pass<T, M, 9>;
-    case 10: return fch::col_pass<T, M, 10>;
     case 11: return fch::col_pass<T, M, 11>;
+#endif
+    case 10: return fch::col_pass<T, M, 10>;
     }
     return fch::col_pass<T, M, 0>;
 }
@@ -30,9 +34,11 @@ template <typename T, int M> pass_fn col_fn(int logN)
 template <typename T, int M> pass_fn row_fn(int logN)
 {
     switch (logN) {
+#ifndef FCH_ONLY_1024
     case 9: return fch::row_pass<T, M, 9>;
-    case 10: return fch::row_pass<T, M, 10>;
     case 11: return fch::row_pass<T, M, 11>;
+#endif
+    case 10: return fch::row_pass<T, M, 10>;
     }
     return fch::row_pass<T, M, 0>;
 }
@@ -88,6 +94,7 @@ template <typename T, int M> cudaError_t launch_row(const fch_kparams &kp, cudaS
 #define FCH_CAT2(a, b) a##b
 #define FCH_CAT(a, b) FCH_CAT2(a, b)
 
+#ifndef FCH_NO_COL
 cudaError_t FCH_CAT(fch_launch_col_, FCH_SUFFIX)(int mode, const fch_kparams &kp, cudaStream_t s)
 {
     switch (mode) {
@@ -105,6 +112,9 @@ cudaError_t FCH_CAT(fch_launch_col_, FCH_SUFFIX)(int mode, const fch_kparams &kp
     return cudaErrorInvalidValue;
 }
 
+#endif
+
+#ifndef FCH_NO_ROW
 cudaError_t FCH_CAT(fch_launch_row_, FCH_SUFFIX)(int mode, const fch_kparams &kp, cudaStream_t s)
 {
     switch (mode) {
@@ -117,3 +127,4 @@ cudaError_t FCH_CAT(fch_launch_row_, FCH_SUFFIX)(int mode, const fch_kparams &kp
     }
     return cudaErrorInvalidValue;
 }
+#endif

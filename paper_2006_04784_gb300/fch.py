@@ -18,7 +18,7 @@ LIB_PATH = os.path.join(_HERE, "_build", "libfch.so")
 
 FCH_IMEX, FCH_SAV, FCH_PSD, FCH_ETD = 0, 1, 2, 3
 SCHEMES = {"imex": FCH_IMEX, "sav": FCH_SAV, "psd": FCH_PSD, "etd": FCH_ETD}
-FCH_FP64, FCH_MIXED = 0, 1
+FCH_FP64, FCH_MIXED, FCH_FP32X2 = 0, 1, 2
 STATUS = {0: "FCH_OK", 1: "FCH_EINVAL", 2: "FCH_ENOMEM", 3: "FCH_ECUDA", 4: "FCH_ENOCONV",
           5: "FCH_ENONFINITE", 6: "FCH_ETIMEOUT", 7: "FCH_ESTATE"}
 

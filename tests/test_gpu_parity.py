@@ -104,10 +104,11 @@ def test_fft_full_size_sampled_outputs(n, prec):
 
 
 # --------------------------------------------------------------------------- F(u)
+@pytest.mark.parametrize("prec", [0, 2])
 @pytest.mark.parametrize("q", [0.0, 0.5])
-def test_rhs_vs_oracle(q):
+def test_rhs_vs_oracle(q, prec):
     n = 64
-    p = lib_params(q)
+    p = lib_params(q, prec=prec)
     u = I.circle_bilayer(n, noise=1e-2)
     with fch.Context(n, p) as ctx:
         ut = torch.tensor(u, device=DEV)
@@ -140,10 +141,12 @@ def test_state_roundtrip_energy_mass():
 
 
 # --------------------------------------------------------------------------- fixed steps
+@pytest.mark.parametrize("prec", [0, 2])
 @pytest.mark.parametrize("scheme", ["imex", "sav", "psd", "etd"])
-def test_fixed_steps_fp64_vs_oracle(scheme):
+def test_fixed_steps_fp64_vs_oracle(scheme, prec):
+    # FP64 and double-float (FP32X2) modes, 1e-10 relative L2 per step
     n = 64
-    p = lib_params(0.0, psd_itol=1e-12)
+    p = lib_params(0.0, psd_itol=1e-12, prec=prec)
     u0 = I.circle_bilayer(n, noise=1e-3)
     s = O.Stepper(n, L, oparams(p))
     s.set_state(u0)
@@ -162,10 +165,11 @@ def test_fixed_steps_fp64_vs_oracle(scheme):
             assert ctx.stats()["last_psd_iter"] == s.counts()["last_psd_iter"]
 
 
+@pytest.mark.parametrize("prec", [0, 2])
 @pytest.mark.parametrize("scheme", ["imex", "sav", "psd", "etd"])
-def test_one_step_from_identical_history(scheme):
+def test_one_step_from_identical_history(scheme, prec):
     n = 32
-    p = lib_params(0.2, psd_itol=1e-13)
+    p = lib_params(0.2, psd_itol=1e-13, prec=prec)
     un = I.smooth_random(n, seed=3)
     um = I.smooth_random(n, seed=4, amp=0.49)
     s = O.Stepper(n, L, oparams(p))
@@ -210,10 +214,11 @@ def test_fixed_steps_mixed_precision(scheme):
 
 
 # --------------------------------------------------------------------------- adaptive
+@pytest.mark.parametrize("prec", [0, 2])
 @pytest.mark.parametrize("scheme", ["imex", "sav", "etd", "psd"])
-def test_adaptive_vs_oracle(scheme):
+def test_adaptive_vs_oracle(scheme, prec):
     n = 64
-    p = lib_params(0.0, zero_stab_cap=1, k_max=0.05 if scheme == "psd" else float("inf"))
+    p = lib_params(0.0, zero_stab_cap=1, k_max=0.05 if scheme == "psd" else float("inf"), prec=prec)
     p.sync_every = 4
     u0 = I.circle_bilayer(n, noise=1e-3)
     tf = 0.01
@@ -335,3 +340,34 @@ def test_mixed_1024_graph_replay_matches_eager():
             out.append((st["n_steps"], st["t"], ctx.get_state()))
     assert out[0][0] == out[1][0] and out[0][1] == out[1][1]
     assert np.array_equal(out[0][2], out[1][2])
+
+
+def test_fp32x2_1024_adaptive_trials_track_fp64():
+    # the benchmark workload in double-float: 40 adaptive trials at 1024^2 take the
+    # same accept/reject decisions and step sizes as the FP64 mode and end within
+    # 1e-10 of it (the FP64 mode itself matches the oracle at smaller sizes)
+    n = 1024
+    u0 = I.random_network(n, d=0.75, seed=3)
+    out = {}
+    for prec in (0, 2):
+        with fch.Context(n, lib_params(0.0, eta2=0.15, prec=prec)) as ctx:
+            ctx.set_state(u0)
+            st = ctx.run_adaptive("imex", 1e-5, 10.0, max_attempts=40, raise_on_timeout=False)
+            out[prec] = (st, ctx.get_state())
+    s0, s2 = out[0][0], out[2][0]
+    assert (s0["n_steps"], s0["n_rejects"]) == (s2["n_steps"], s2["n_rejects"])
+    assert s2["t"] == pytest.approx(s0["t"], rel=1e-9)
+    assert rel(out[2][1], out[0][1]) < 1e-10
+
+
+def test_fp32x2_1024_one_step_vs_oracle():
+    n = 1024
+    p = lib_params(0.0, eta2=0.15, prec=2)
+    u0 = I.random_network(n, d=0.75, seed=3)
+    s = O.Stepper(n, L, oparams(p))
+    s.set_state(u0)
+    s.step("imex", 1e-6)
+    with fch.Context(n, p) as ctx:
+        ctx.set_state(u0)
+        ctx.step("imex", 1e-6)
+        assert rel(ctx.get_state(), s.state()) < 1e-10
