@@ -1,9 +1,11 @@
 """Benchmark of the adaptive pseudo-spectral BDF2 step for the 2D FCH flow.
 
-Workload: 1024^2 grid, mixed precision (single-precision transforms and pointwise
-stages, double-precision norms, energy, mass and controller), adaptive IMEX-BDF2
-with sigma_tol = 1e-5, critical-case parameters (q = 0, eta1 = 1.45 eps,
-eta2 = 1.5 eps, d = 0.75), seeded random bilayer network initial data.
+Workload: 1024^2 grid, adaptive IMEX-BDF2 with sigma_tol = 1e-5, critical-case
+parameters (q = 0, eta1 = 1.45 eps, eta2 = 1.5 eps, d = 0.75), seeded random
+bilayer network initial data. Precision (default fp32x2): transforms and pointwise
+stages in double-float arithmetic (pairs of floats, FP64-class accuracy on the
+FP32 pipe), norms, energy, mass and controller in double; --prec fp64 runs every
+stage in double, --prec mixed in single precision.
 
 One step = one trial of the adaptive algorithm (Sec. 3.2): the IMEX-BDF2 trial
 (eq. IMEX-eq, 4 real 2D transforms), F of the trial (4 transforms), the AM3
@@ -33,13 +35,20 @@ sys.path.insert(0, ROOT)
 N_GRID = 1024
 SIGMA = 1e-5
 T_FINAL = 10.0
-METRIC = "BDF2 steps/s (adaptive IMEX-BDF2 trials, 1024^2, mixed precision)"
-CONFIG = {"workload": "adaptive IMEX-BDF2, 1024x1024 periodic grid on [-2pi,2pi)^2, mixed "
-                      "precision (FP32 transforms/pointwise, FP64 reductions/controller), "
-                      "sigma_tol=1e-5, critical eta1/eta2 (pearling regime), seeded random "
-                      "bilayer network init",
-          "n": N_GRID, "scheme": "imex", "precision": "mixed", "sigma_tol": SIGMA,
-          "l2": "flushed before every timed step (512 MiB write)"}
+METRIC = "BDF2 steps/s (adaptive IMEX-BDF2 trial steps at 1024^2)"
+PREC_TEXT = {
+    "fp32x2": "double-float (FP32-pair) transforms/pointwise, FP64 reductions/controller",
+    "fp64": "FP64 transforms/pointwise/reductions/controller",
+    "mixed": "FP32 transforms/pointwise, FP64 reductions/controller",
+}
+
+
+def config(prec: str):
+    return {"workload": "adaptive IMEX-BDF2, 1024x1024 periodic grid on [-2pi,2pi)^2, "
+                        f"{PREC_TEXT[prec]}, sigma_tol=1e-5, critical eta1/eta2 (pearling "
+                        "regime), seeded random bilayer network init",
+            "n": N_GRID, "scheme": "imex", "precision": prec, "sigma_tol": SIGMA,
+            "l2": "flushed before every timed step (512 MiB write)"}
 
 
 def rank_info():
@@ -119,6 +128,62 @@ class Clocks:
         sm.sort()
         return {"sm_mhz": sm[len(sm) // 2] if sm else None, "sm_max_mhz": mx or None,
                 "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# FP32 peak from unit counts: 152 SMs x 128 FP32 lanes x 2 flops (FMA) x 2.07 GHz
+FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
+# FP64 peak of this GPU: the nominal 1.25 TFLOP/s figure
+FP64_PEAK_TFLOPS = 1.25
+
+
+def profile_table(name: str):
+    """rows of a whitespace table in profiles/<name> (ncu-derived figures)"""
+    rows = []
+    try:
+        for line in open(os.path.join(ROOT, "profiles", name)):
+            f = line.split("#")[0].split()
+            if f:
+                rows.append(f)
+    except OSError:
+        pass
+    return rows
+
+
+def roofline(prec: str, kernel: str, n: int, launch_s_ms: float):
+    """Roofline of the dominant pass. fp32x2 and fp64 passes are bound by the FP32 /
+    FP64 pipes: achieved = floating-point operations per launch (counted by ncu for
+    this kernel and size, profiles/flops_per_launch.txt) / the live mean launch time.
+    mixed passes stream memory: achieved = algorithmic bytes per launch / time. The
+    HBM view of the same launch is reported beside the ALU one."""
+    peaks = measured_peaks()
+    hbm = peaks.get("hbm_gbs") or 6800.0
+    t = launch_s_ms / 1e3
+    csz = 8 if prec == "mixed" else 16
+    ab = pass_bytes(kernel, n, csz)
+    hbm_view = {"achieved_gbs": ab / t / 1e9 if ab else None, "peak_gbs": hbm,
+                "frac": (ab / t / 1e9) / hbm if ab else None, "algorithmic_bytes_per_launch": ab}
+    traffic = None
+    for r in profile_table("dram_traffic.txt"):
+        if len(r) >= 4 and r[0] == prec and r[1] == kernel and int(r[2]) == n:
+            traffic = float(r[3])
+    if prec == "mixed":
+        return {"kernel": kernel, "bound": "hbm", "achieved": hbm_view["achieved_gbs"], "peak": hbm,
+                "unit": "GB/s", "frac": hbm_view["frac"], "traffic": traffic,
+                "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)" if peaks.get("hbm_gbs")
+                else "fallback 6800 GB/s", "algorithmic_bytes_per_launch": ab,
+                "avg_launch_us": launch_s_ms * 1e3}
+    flops = None
+    for r in profile_table("flops_per_launch.txt"):
+        if len(r) >= 4 and r[0] == prec and r[1] == kernel and int(r[2]) == n:
+            flops = float(r[3])
+    peak = FP32_PEAK_TFLOPS if prec == "fp32x2" else FP64_PEAK_TFLOPS
+    ach = flops / t / 1e12 if flops else None
+    return {"kernel": kernel, "bound": "alu", "achieved": ach, "peak": peak, "unit": "TFLOP/s",
+            "frac": ach / peak if ach else None, "traffic": traffic,
+            "peak_source": ("FP32 pipe from unit counts: 152 SM x 128 lanes x 2 x 2.07 GHz"
+                            if prec == "fp32x2" else "FP64 nominal 1.25 TFLOP/s"),
+            "flops_per_launch": flops, "flops_source": "ncu sass op counts (profiles/flops_per_launch.txt)",
+            "avg_launch_us": launch_s_ms * 1e3, "hbm_view": hbm_view}
 
 
 def pass_bytes(name: str, n: int, csz: int) -> int:
@@ -206,18 +271,9 @@ def run_gb300(args):
     nfft = st1["n_fft"] - st0["n_fft"]
     eager_ms_per_step = sum(step_ms_eager) / K2
     # dominant kernel and its roofline
-    peaks = measured_peaks()
-    hbm = peaks.get("hbm_gbs")
     dom = max((k for k in times if k != "ctrl"), key=lambda k: times[k][0])
     dms, dn = times[dom]
-    csz = 8 if prec == fch.FCH_MIXED else 16  # bytes per complex element
-    ab = pass_bytes(dom, n, csz)
-    achieved = ab / (dms / dn / 1e3) / 1e9 if ab else None
-    roof = {"kernel": dom, "bound": "hbm", "achieved": achieved, "peak": hbm,
-            "peak_source": "MEASURED_PEAKS.json hbm_gbs (measured)" if hbm else "fallback 6800",
-            "unit": "GB/s", "frac": (achieved / (hbm or 6800.0)) if achieved else None,
-            "traffic": traffic_from_profiles(dom, n), "algorithmic_bytes_per_launch": ab,
-            "avg_launch_us": dms / dn * 1e3}
+    roof = roofline(args.prec, dom, n, dms / dn)
     kernels = {k: {"ms_total": round(v[0], 4), "launches": v[1],
                    "share": round(v[0] / sum(x[0] for x in times.values()), 4)}
                for k, v in sorted(times.items(), key=lambda kv: -kv[1][0])}
@@ -227,9 +283,10 @@ def run_gb300(args):
         e2e = e2e_measure(fch, I, p, n, dev, min(K, 200))
         out = {"metric": METRIC, "value": value, "unit": "steps/s", "n_gpus": world, "steps": K,
                "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
-               "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64",
+               "scaling": "weak", "vs_baseline": None,
+               "dtype": {"fp32x2": "f32x2+f64", "fp64": "f64", "mixed": "f32+f64"}[args.prec],
                "data": "synthetic (seeded random bilayer network, no dataset)",
-               "config": dict(CONFIG, parallelism="replicas" if world > 1 else "single"),
+               "config": dict(config(args.prec), parallelism="replicas" if world > 1 else "single"),
                "ffts_per_s": world * nfft / (tot_ms / 1e3),
                "ffts_per_step": nfft / K,
                "accepted": st1["n_steps"] - st0["n_steps"], "rejected": st1["n_rejects"] - st0["n_rejects"],
@@ -238,12 +295,45 @@ def run_gb300(args):
                "kernels": kernels, "kernels_region": f"{K2} trials launched kernel by kernel "
                f"(per-launch events; {eager_ms_per_step:.4f} ms/step there vs {ms_per_step:.4f} "
                "with the CUDA graph)", "roofline": roof, "clocks": clk.summary(), "e2e": e2e}
+        if not args.no_t_final and world == 1:
+            out["time_to_t_final"] = time_to_t_final(fch, I, n)
         if not args.no_cpu_baseline and world == 1:
             out["cpu_baseline"] = cpu_baseline(args)
     ctx.close()
     if world > 1:
         torch.distributed.barrier()
         torch.distributed.destroy_process_group()
+    return out
+
+
+def time_to_t_final(fch, I, n, t_final=0.02):
+    """Wall time of fch_run_adaptive from the initial data to t_final at sigma_tol,
+    per precision, and the relative L2 error at t_final against a reference run
+    (double-float at sigma_tol/100; the global error scales like sigma^(2/3))."""
+    import numpy as np
+
+    u0 = I.random_network(n, d=0.75, seed=3)
+
+    def run(prec, sigma, budget=0):
+        p = fch.params_default(0.0, eta2=0.15, prec=prec, sync_every=64)
+        with fch.Context(n, p) as ctx:
+            ctx.set_state(u0)
+            t0 = time.perf_counter()
+            st = ctx.run_adaptive("imex", sigma, t_final, max_attempts=budget, raise_on_timeout=False)
+            wall = time.perf_counter() - t0
+            return st, wall, ctx.get_state()
+
+    ref_st, ref_wall, ref = run(fch.FCH_FP32X2, SIGMA / 100)
+    out = {"t_final": t_final, "sigma_tol": SIGMA,
+           "reference": {"precision": "fp32x2", "sigma_tol": SIGMA / 100, "trials": ref_st["n_attempts"],
+                         "wall_s": ref_wall}}
+    for name, prec, budget in (("fp32x2", fch.FCH_FP32X2, 0), ("fp64", fch.FCH_FP64, 0),
+                               ("mixed", fch.FCH_MIXED, 3000)):
+        st, wall, u = run(prec, SIGMA, budget)
+        reached = st["t"] >= t_final * (1 - 1e-12)
+        out[name] = {"wall_s": wall, "trials": st["n_attempts"], "rejected": st["n_rejects"],
+                     "t_reached": st["t"], "reached": bool(reached),
+                     "rel_l2_error": float(np.linalg.norm(u - ref) / np.linalg.norm(ref)) if reached else None}
     return out
 
 
@@ -301,19 +391,6 @@ def cpu_baseline(args):
                       f"was built), {dt:.1f} s"}
 
 
-def traffic_from_profiles(kernel: str, n: int):
-    """dram bytes per launch recorded by an ncu capture summarised in profiles/."""
-    path = os.path.join(ROOT, "profiles", "dram_traffic.txt")
-    try:
-        for line in open(path):
-            f = line.split("#")[0].split()
-            if len(f) >= 3 and f[0] == kernel and int(f[1]) == n:
-                return float(f[2])
-    except OSError:
-        pass
-    return None
-
-
 def run_reference(args):
     """The oracle as the reference arm: adaptive IMEX trials at 1024^2 on the host
     cores, each step one trial (bounded: at most ~150 s of timed work)."""
@@ -346,7 +423,7 @@ def run_reference(args):
             "steps": done, "warmup": args.warmup, "ms_per_step": 1e3 * dt / done,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic (seeded random bilayer network, no dataset)",
-            "config": dict(CONFIG, parallelism="single"),
+            "config": dict(config("fp64"), parallelism="single"),
             "cpu_baseline": {"value": v, "unit": "steps/s", "cores": 1, "kind": "oracle",
                              "sample": f"{done} adaptive IMEX trials at 1024^2 (of {K} asked; "
                                        "capped at 150 s)"},
@@ -360,9 +437,10 @@ def main():
     ap.add_argument("--warmup", type=int, default=20)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--prec", default="mixed", choices=["mixed", "fp64", "fp32x2"],
+    ap.add_argument("--prec", default="fp32x2", choices=["mixed", "fp64", "fp32x2"],
                     help="mixed (single-precision transforms), fp64, or fp32x2 (double-float)")
     ap.add_argument("--scheme", default="imex", choices=["imex", "sav", "etd"])
+    ap.add_argument("--no-t-final", action="store_true", help="skip the time-to-t_final runs")
     args = ap.parse_args()
     out = run_reference(args) if args.impl == "reference" else run_gb300(args)
     if out is not None:
