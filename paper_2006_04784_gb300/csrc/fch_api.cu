@@ -16,8 +16,11 @@ fch_geom fch_geometry(int N, int prec)
 {
     fch_geom g;
     const int csz = prec == 1 ? 8 : 16; // bytes per complex element (single: 8; double, double-float: 16)
+    // column pairs per block: enough that a block reads whole 32-byte sectors of
+    // each row (2 pairs of 8-byte or 1 pair of 16-byte elements) and has >= 256 threads
+    const int pmin = csz == 8 ? 2 : 1;
     int P = 1024 / N;
-    if (P < 2) P = 2;
+    if (P < pmin) P = pmin;
     if (P > N / 2) P = N / 2;
     g.P = P;
     g.col_threads = P * N / 4; // 2P sequences x N/8 threads

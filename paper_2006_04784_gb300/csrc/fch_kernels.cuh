@@ -96,9 +96,17 @@ template <int DIR, typename C> __device__ __forceinline__ void bfly8(C *v)
     bfly4<DIR>(v[0], v[2], v[4], v[6]);
     bfly4<DIR>(v[1], v[3], v[5], v[7]);
     const R s = (R)0.70710678118654752440;
-    C o1 = cmul(v[3], mk<C>(s, DIR * s));
+    // x W8 and x W8^3 with W8 = s (1 + DIR i): two adds and two scalings each
+    const C a = v[3], b = v[7];
+    C o1, o3;
+    if (DIR < 0) {
+        o1 = mk<C>((a.x + a.y) * s, (a.y - a.x) * s);
+        o3 = mk<C>((b.y - b.x) * s, -((b.x + b.y) * s));
+    } else {
+        o1 = mk<C>((a.x - a.y) * s, (a.x + a.y) * s);
+        o3 = mk<C>(-((b.x + b.y) * s), (b.x - b.y) * s);
+    }
     C o2 = rot<DIR>(v[5]);
-    C o3 = cmul(v[7], mk<C>(-s, DIR * s));
     C e0 = v[0], e1 = v[2], e2 = v[4], e3 = v[6], o0 = v[1];
     v[0] = cadd(e0, o0);
     v[4] = csub(e0, o0);
@@ -421,18 +429,22 @@ __device__ __forceinline__ void spec_elem(const fch_kparams &kp, const fch_const
     }
 }
 
-// LOGN > 0: the grid size is a compile-time constant (N = 2^LOGN >= 512, P = 2),
-// so the index arithmetic of the transforms folds into immediates; LOGN = 0 reads
-// N and P from the parameters.
+// column pairs per block at the compile-time sizes (N >= 512): 2 for 8-byte
+// elements, 1 for 16-byte ones (see fch_geometry)
+template <typename T> constexpr int spec_pairs() { return sizeof(T) == 4 ? 2 : 1; }
+
+// LOGN > 0: the grid size is a compile-time constant (N = 2^LOGN >= 512), so the
+// index arithmetic of the transforms folds into immediates; LOGN = 0 reads N and P
+// from the parameters.
 template <typename T, int MODE, int LOGN>
-__global__ void __launch_bounds__(LOGN ? ((2 << LOGN) >> 2) : 1024) col_pass(const fch_kparams kp)
+__global__ void __launch_bounds__(LOGN ? ((spec_pairs<T>() << LOGN) >> 2) : 1024) col_pass(const fch_kparams kp)
 {
     typedef typename CT<T>::t C;
     typedef ColTraits<MODE> TR;
     if (pass_skipped(kp)) return;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ double red_scratch[FCH_NRED * 32];
-    const int N = LOGN ? (1 << LOGN) : kp.N, P = LOGN ? 2 : kp.P, nc = 2 * P;
+    const int N = LOGN ? (1 << LOGN) : kp.N, P = LOGN ? spec_pairs<T>() : kp.P, nc = 2 * P;
     const int logN = LOGN ? LOGN : kp.logN;
     const int nthr = LOGN ? (P << LOGN) / 4 : (int)blockDim.x;
     C *tw = (C *)smem_raw;

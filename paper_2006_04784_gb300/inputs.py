@@ -17,6 +17,8 @@ seed * 2^32 + linear index, mapped to a 53-bit uniform in [-1, 1).
 """
 from __future__ import annotations
 
+import functools
+
 import numpy as np
 
 R_BILAYER = 0.14725
@@ -137,3 +139,100 @@ def smooth_random(N: int, seed: int, amp: float = 0.5, kmax: int = 4, offset: fl
     for (mx, my), a, t in zip(ms, r[: len(ms)], r[len(ms):]):
         f += amp / len(ms) ** 0.5 * a * np.cos(kf * (mx * X + my * Y) + np.pi * t)
     return np.ascontiguousarray(f)
+
+
+# --------------------------------------------------------------------------- the paper's initial data
+# Table t:Benchmark (Sec. 2.2-2.3): q, eta1/eps, eta2/eps, d, N for the five benchmarks
+BENCHMARKS = {
+    "subcritical": dict(q=0.0, eta1=1.45, eta2=3.0, d=0.2, N=256),
+    "critical": dict(q=0.0, eta1=1.45, eta2=1.5, d=0.75, N=256),
+    "supercritical": dict(q=0.0, eta1=1.45, eta2=3.0, d=0.5, N=256),
+    "foot1": dict(q=0.2, eta1=1.45, eta2=3.0, d=0.2, N=256),
+    "foot2": dict(q=0.5, eta1=1.45, eta2=3.0, d=0.2, N=512),
+}
+LAMBDA0 = 7.0269e-3
+
+
+def paper_curve(theta, eps=0.1, L=L_DEFAULT):
+    """Gamma of Sec. 2.3: radius rho(theta) = 3 - (eps/2) cos(6 (theta - pi/11))
+    - eps^2 cos(theta - 3 pi/11) about the centre of the square."""
+    return (3.0 - 0.5 * eps * np.cos(6.0 * (theta - np.pi / 11.0))
+            - eps * eps * np.cos(theta - 3.0 * np.pi / 11.0))
+
+
+def _curve_distance(px, py, eps=0.1, L=L_DEFAULT):
+    """distance from points (px, py), relative to the centre of the square, to
+    Gamma: minimised over curve points within +-0.15 rad of each point's polar
+    angle (R is far below Gamma's radius of curvature), refined twice."""
+    th0 = np.arctan2(py, px)
+    best = np.full(px.shape, np.inf)
+    bt = th0.copy()
+    for width, ns in ((0.15, 61), (0.006, 31), (0.0003, 31)):
+        centre = bt.copy()
+        for dt in np.linspace(-width, width, ns):
+            t = centre + dt
+            r = paper_curve(t, eps, L)
+            dist = np.hypot(px - r * np.cos(t), py - r * np.sin(t))
+            m = dist < best
+            best = np.where(m, dist, best)
+            bt = np.where(m, t, bt)
+    return best
+
+
+@functools.lru_cache(maxsize=4)
+def _paper_band_cached(No, eps, R, L, x0, sub):
+    return _paper_band(No, eps, R, L, x0, sub)
+
+
+def paper_band(No: int = 256, eps: float = 0.1, R: float = R_BILAYER, L: float = L_DEFAULT,
+               x0: float = X0_DEFAULT, sub: int = 16) -> np.ndarray:
+    """phi_Gamma (see _paper_band); cached, returns a copy."""
+    return _paper_band_cached(No, eps, R, L, x0, sub).copy()
+
+
+def _paper_band(No: int = 256, eps: float = 0.1, R: float = R_BILAYER, L: float = L_DEFAULT,
+                x0: float = X0_DEFAULT, sub: int = 16) -> np.ndarray:
+    """phi_Gamma on the No x No mesh: +1 inside the band Gamma_R (within normal
+    distance R of Gamma, between Gamma_+ and Gamma_-), -1 outside, taken as the cell
+    average of the indicator (the area fraction of each mesh cell inside the band,
+    by sub x sub sampling of the cells the band boundary crosses), so that its mean
+    is the band area 2 R |Gamma|."""
+    h = L / No
+    X, Y = grid(No, L, x0)
+    c = x0 + 0.5 * L
+    px, py = X.ravel() - c, Y.ravel() - c
+    dist = _curve_distance(px, py, eps, L)
+    frac = (dist <= R).astype(float)
+    edge = np.nonzero(np.abs(dist - R) < 0.75 * h)[0]
+    off = (np.arange(sub) + 0.5) / sub - 0.5
+    ox, oy = np.meshgrid(off * h, off * h, indexing="xy")
+    for chunk in np.array_split(edge, max(1, len(edge) // 512)):
+        qx = (px[chunk][:, None] + ox.ravel()[None, :]).ravel()
+        qy = (py[chunk][:, None] + oy.ravel()[None, :]).ravel()
+        dq = _curve_distance(qx, qy, eps, L).reshape(len(chunk), -1)
+        frac[chunk] = (dq <= R).mean(axis=1)
+    return (2.0 * frac - 1.0).reshape(No, No)
+
+
+def paper_initial_data(N: int, d: float, eps: float = 0.1, No: int = 256, lam0: float = LAMBDA0,
+                       filter_k: str = "physical", L: float = L_DEFAULT,
+                       x0: float = X0_DEFAULT) -> np.ndarray:
+    """u0 of eq. (dcoef): the band indicator on the No x No mesh, smoothed by the
+    Gaussian filter exp(-lam0 |k|^2), evaluated on the N x N grid by spectral
+    interpolation, plus the background eps d / alpha_m(0)^2, alpha_m(0) = 1.7.
+    filter_k = "physical": k = 2 pi m / L (the smoothed band keeps a bilayer-like
+    peak, ~0.57); "integer": k = m, the literal index of the printed sum (peak
+    ~-0.07). The mass does not depend on the choice (the k = 0 mode is kept)."""
+    phi = paper_band(No, eps, R_BILAYER, L, x0)
+    ph = np.fft.fft2(phi)
+    m_ = np.fft.fftfreq(No, 1.0 / No)
+    k = m_ if filter_k == "integer" else 2.0 * np.pi * m_ / L
+    ph = ph * np.exp(-lam0 * (k[None, :] ** 2 + k[:, None] ** 2))
+    m = min(N, No) // 2
+    out = np.zeros((N, N), dtype=complex)
+    out[:m, :m] = ph[:m, :m]
+    out[:m, -m:] = ph[:m, -m:]
+    out[-m:, :m] = ph[-m:, :m]
+    out[-m:, -m:] = ph[-m:, -m:]
+    phiN = np.real(np.fft.ifft2(out)) * (N * N) / (No * No)
+    return np.ascontiguousarray(phiN + eps * d / ALPHA_M0 ** 2)

@@ -504,3 +504,20 @@ def test_etd_stabiliser_splitting_is_consistent():
         errs.append(np.linalg.norm(s.state() - ref))
     assert errs[2] < 1e-3 * np.linalg.norm(ref)
     assert 1.7 < math.log2(errs[1] / errs[2]) < 2.4, errs
+
+
+def test_benchmark_initial_data_mass_matches_table():
+    # Table t:Benchmark prints the mass of each benchmark's initial data; it pins
+    # the mass functional (Sec. 2.3), the band width 2R, the curve Gamma and the
+    # background eps d / alpha_m(0)^2 of eq. (dcoef) together.
+    for case, d, n, mass in _golden("benchmark_mass.txt"):
+        u0 = I.paper_initial_data(int(n), float(d))
+        assert round(O.mass(u0, L), 2) == float(mass), case
+    # the band itself: area 2 R |Gamma|, |Gamma| from rho(theta) by quadrature
+    th = np.linspace(0, 2 * np.pi, 100001)[:-1]
+    rho = I.paper_curve(th)
+    drho = np.gradient(rho, th)
+    length = np.sum(np.hypot(rho, drho)) * (2 * np.pi / len(th))
+    band = I.paper_band()
+    area = np.sum((band + 1) / 2) * (L / 256) ** 2
+    assert abs(area - 2 * I.R_BILAYER * length) < 5e-4
