@@ -429,22 +429,25 @@ __device__ __forceinline__ void spec_elem(const fch_kparams &kp, const fch_const
     }
 }
 
-// column pairs per block at the compile-time sizes (N >= 512): 2 for 8-byte
-// elements, 1 for 16-byte ones (see fch_geometry)
-template <typename T> constexpr int spec_pairs() { return sizeof(T) == 4 ? 2 : 1; }
+// column pairs per block at a compile-time size, the same rule as fch_geometry:
+// max(pmin, 1024 / N), pmin = 2 for 8-byte elements and 1 for 16-byte ones
+template <typename T, int LOGN> constexpr int spec_pairs()
+{
+    return (1024 >> LOGN) > (sizeof(T) == 4 ? 2 : 1) ? (1024 >> LOGN) : (sizeof(T) == 4 ? 2 : 1);
+}
 
 // LOGN > 0: the grid size is a compile-time constant (N = 2^LOGN >= 512), so the
 // index arithmetic of the transforms folds into immediates; LOGN = 0 reads N and P
 // from the parameters.
 template <typename T, int MODE, int LOGN>
-__global__ void __launch_bounds__(LOGN ? ((spec_pairs<T>() << LOGN) >> 2) : 1024) col_pass(const fch_kparams kp)
+__global__ void __launch_bounds__(LOGN ? ((spec_pairs<T, LOGN>() << LOGN) >> 2) : 1024) col_pass(const fch_kparams kp)
 {
     typedef typename CT<T>::t C;
     typedef ColTraits<MODE> TR;
     if (pass_skipped(kp)) return;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ double red_scratch[FCH_NRED * 32];
-    const int N = LOGN ? (1 << LOGN) : kp.N, P = LOGN ? spec_pairs<T>() : kp.P, nc = 2 * P;
+    const int N = LOGN ? (1 << LOGN) : kp.N, P = LOGN ? spec_pairs<T, LOGN>() : kp.P, nc = 2 * P;
     const int logN = LOGN ? LOGN : kp.logN;
     const int nthr = LOGN ? (P << LOGN) / 4 : (int)blockDim.x;
     C *tw = (C *)smem_raw;

@@ -107,3 +107,11 @@ def test_create_rejects_bad_arguments_before_device_work():
     assert L.fch_create(C.byref(g), C.byref(bad), None, C.byref(h)) == 1
     assert L.fch_step(None, 0, 1e-3) == 1
     assert L.fch_fft_plan_create(100, 0, None, C.byref(h)) == 1
+
+
+def test_compile_time_pair_rule_matches_geometry():
+    # the specialised column kernels (N = 512, 1024, 2048) assume the pairs-per-block
+    # rule of fch_geometry: max(pmin, 1024 / N), pmin = 2 (8-byte) or 1 (16-byte)
+    for n in (512, 1024, 2048):
+        for prec, pmin in ((0, 1), (1, 2)):
+            assert fch.geometry(n, prec)["P"] == max(pmin, 1024 // n)
