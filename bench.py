@@ -193,9 +193,11 @@ def pass_bytes(name: str, n: int, csz: int) -> int:
     H = (n // 2 + 1) * n * csz
     Z = n * n * csz
     table = {
+        "row_nimex_direct": 2 * Z + Z,     # (u, Lap u) of u^n, u^{n-1} in; Z out
+        "row_sav_direct": 2 * Z + Z,
         "col_start": H * 2 + Z,            # u^n, u^{n-1} -> u*, packed Z
         "row_nimex": 2 * Z,                # Z in, Z out
-        "row_f": 2 * Z,
+        "row_f": 2 * Z + Z,                # Z in, Z out, (u, Lap u) of the trial kept
         "col_imex_solve": Z + 2 * H + H + Z,  # Z, u^n, u^{n-1} in; u^{n+1}, Z out
         "col_f_finish": Z + H + H + 3 * H,    # Z, u~ in; F~ out; u^n, F^n, F^{n-1} in (AM3)
     }
@@ -291,7 +293,7 @@ def run_gb300(args):
                "ffts_per_step": nfft / K,
                "accepted": st1["n_steps"] - st0["n_steps"], "rejected": st1["n_rejects"] - st0["n_rejects"],
                "t_reached": st1["t"],
-               "gpu_launches": 6 * K,  # per trial: 5 passes + 1 control kernel (one graph)
+               "gpu_launches": sum(v[1] for v in times.values()) // max(1, K2) * K,  # per trial, from the eager region
                "kernels": kernels, "kernels_region": f"{K2} trials launched kernel by kernel "
                f"(per-launch events; {eager_ms_per_step:.4f} ms/step there vs {ms_per_step:.4f} "
                "with the CUDA graph)", "roofline": roof, "clocks": clk.summary(), "e2e": e2e}
@@ -391,6 +393,53 @@ def cpu_baseline(args):
                       f"was built), {dt:.1f} s"}
 
 
+def paper_costs(args):
+    """The cost comparison of Sec. 5.2 on the super-critical benchmark (Table
+    t:Benchmark: q = 0, eta2 = 3 eps, d = 0.5, N = 256, the paper's initial data),
+    integrated to T = 250 by each scheme at the sigma_tol the paper quotes, with the
+    number of 2D real transforms and the global relative L2 error at T against a
+    reference run (IMEX at sigma_tol = 1e-9). FP32X2 throughout."""
+    import numpy as np
+
+    from paper_2006_04784_gb300 import build as B
+    B.build()
+    from paper_2006_04784_gb300 import fch
+    from paper_2006_04784_gb300 import inputs as I
+
+    b = I.BENCHMARKS["supercritical"]
+    n, T = b["N"], args.paper_T
+    u0 = I.paper_initial_data(n, b["d"])
+
+    def run(scheme, sigma):
+        p = fch.params_default(b["q"], eta1=b["eta1"] * 0.1, eta2=b["eta2"] * 0.1,
+                               prec=fch.FCH_FP32X2, sync_every=256)
+        with fch.Context(n, p) as ctx:
+            ctx.set_state(u0)
+            t0 = time.perf_counter()
+            st = ctx.run_adaptive(scheme, sigma, T)
+            wall = time.perf_counter() - t0
+            return st, wall, ctx.get_state(), ctx.mass(), ctx.energy()
+
+    ref_st, ref_wall, ref, m_ref, e_ref = run("imex", 1e-9)
+    out = {"benchmark": "supercritical", "N": n, "T": T, "precision": "fp32x2",
+           "fft_unit": "one 2D real transform of one field (R2C or C2R)",
+           "reference": {"scheme": "imex", "sigma_tol": 1e-9, "n_fft": ref_st["n_fft"],
+                         "steps": ref_st["n_steps"], "wall_s": ref_wall, "mass": m_ref, "energy": e_ref},
+           "runs": []}
+    for scheme, sigma, paper in (("imex", 3e-6, "1.5e5 FFT calls (Sec. 5.2)"),
+                                 ("sav", 3e-6, "2e5 FFT calls (Sec. 5.2; 2.1e5 in Sec. 1)"),
+                                 ("psd", 1e-3, "2e5 FFT calls (Sec. 5.2)"),
+                                 ("imex", 1e-5, None), ("imex", 1e-6, None),
+                                 ("etd", 1e-5, "2.5e6 FFT calls at error 2.5e-3 (Sec. 1)")):
+        st, wall, u, m, e = run(scheme, sigma)
+        out["runs"].append({"scheme": scheme, "sigma_tol": sigma, "n_fft": st["n_fft"],
+                            "steps": st["n_steps"], "rejects": st["n_rejects"],
+                            "psd_iter": st["n_psd_iter"], "wall_s": wall,
+                            "global_rel_l2": float(np.linalg.norm(u - ref) / np.linalg.norm(ref)),
+                            "mass": m, "energy": e, "paper": paper})
+    return out
+
+
 def run_reference(args):
     """The oracle as the reference arm: adaptive IMEX trials at 1024^2 on the host
     cores, each step one trial (bounded: at most ~150 s of timed work)."""
@@ -441,8 +490,14 @@ def main():
                     help="mixed (single-precision transforms), fp64, or fp32x2 (double-float)")
     ap.add_argument("--scheme", default="imex", choices=["imex", "sav", "etd"])
     ap.add_argument("--no-t-final", action="store_true", help="skip the time-to-t_final runs")
+    ap.add_argument("--paper-costs", action="store_true",
+                    help="run the Sec. 5.2 cost comparison (super-critical benchmark) instead")
+    ap.add_argument("--paper-T", type=float, default=250.0)
     args = ap.parse_args()
-    out = run_reference(args) if args.impl == "reference" else run_gb300(args)
+    if args.paper_costs:
+        out = paper_costs(args)
+    else:
+        out = run_reference(args) if args.impl == "reference" else run_gb300(args)
     if out is not None:
         print(json.dumps(out))
 

@@ -193,7 +193,7 @@ fch_status fch_adaptive_end(fch_ctx *ctx, fch_stats *stats);
  * counts per pass kind: index m < FCH_NCOL is the column pass in mode m, then
  * FCH_NROW row-pass modes, then the control kernel (n >= FCH_NPASS entries). */
 #define FCH_NCOL 10
-#define FCH_NROW 6
+#define FCH_NROW 8
 #define FCH_NPASS (FCH_NCOL + FCH_NROW + 1)
 fch_status fch_pass_timing(fch_ctx *ctx, int on);
 fch_status fch_pass_times(fch_ctx *ctx, double *ms, long long *launches, int n);

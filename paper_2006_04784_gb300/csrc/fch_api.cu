@@ -161,6 +161,8 @@ struct fch_ctx {
     fch_ctrl *dctrl;
     double *part;
     void *U[3], *F[3], *Pb, *Qb, *Vb, *Nb, *Z, *tw, *tw2;
+    void *Rs[3];         // real-space (u, Lap u) of the state slots, kept by adaptive trials
+    bool rvalid;         // Rs holds u^n (and u^{n-1} when k_n > 0)
     double *staging;     // N*N doubles for host io
     long long *nfft_dev;
     unsigned int *ticket;
@@ -427,9 +429,10 @@ static fch_status col(fch_ctx *ctx, int mode, int src = 0, int flags = 0, const 
 }
 
 static fch_status row(fch_ctx *ctx, int mode, int flags = 0, const void *in0 = nullptr,
-                      void *out0 = nullptr, int tail = -1, double tail_arg = 0.0)
+                      void *out0 = nullptr, int tail = -1, double tail_arg = 0.0, int src = 0)
 {
     fch_kparams kp = ctx->kp;
+    kp.src = src;
     kp.tail_op = tail;
     kp.tail_arg = tail_arg;
     kp.flags = flags;
@@ -509,6 +512,7 @@ extern "C" fch_status fch_create(const fch_grid *g, const fch_params *p, void *s
     for (void **b : bufs)
         if (e == cudaSuccess) e = cudaMalloc(b, hs);
     if (e == cudaSuccess) e = cudaMalloc(&ctx->Z, (size_t)N * N * csz);
+    for (int i = 0; i < 3 && e == cudaSuccess; i++) e = cudaMalloc(&ctx->Rs[i], (size_t)N * N * csz);
     if (e == cudaSuccess) e = cudaMalloc(&ctx->tw, (size_t)N * csz);
     if (e == cudaSuccess) e = cudaMalloc((void **)&ctx->part, sizeof(double) * FCH_NRED * FCH_MAXBLK);
     if (e == cudaSuccess) e = cudaMalloc((void **)&ctx->dctrl, sizeof(fch_ctrl));
@@ -533,6 +537,7 @@ extern "C" fch_status fch_create(const fch_grid *g, const fch_params *p, void *s
     ctx->kp.Vb = ctx->Vb;
     ctx->kp.Nb = ctx->Nb;
     ctx->kp.Z = ctx->Z;
+    for (int i = 0; i < 3; i++) ctx->kp.Rs[i] = ctx->Rs[i];
     ctx->kp.tw = ctx->tw;
     ctx->kp.part = ctx->part;
     ctx->kp.ctrl = ctx->dctrl;
@@ -564,7 +569,8 @@ extern "C" fch_status fch_destroy(fch_ctx *ctx)
     if (ctx->stream) cudaStreamSynchronize(ctx->stream);
     void *bufs[] = {ctx->U[0], ctx->U[1], ctx->U[2], ctx->F[0], ctx->F[1], ctx->F[2], ctx->Pb,
                     ctx->Qb, ctx->Vb, ctx->Nb, ctx->Z, ctx->tw, ctx->part, ctx->dctrl,
-                    ctx->staging, ctx->nfft_dev, ctx->ticket, ctx->tw2};
+                    ctx->staging, ctx->nfft_dev, ctx->ticket, ctx->tw2, ctx->Rs[0],
+                    ctx->Rs[1], ctx->Rs[2]};
     for (void *b : bufs)
         if (b) cudaFree(b);
     if (ctx->timing)
@@ -612,6 +618,7 @@ static fch_status set_state_common(fch_ctx *ctx, const void *u_dev, bool io64)
     ctx->have_state = true;
     ctx->failed = false;
     ctx->have_F = false;
+    ctx->rvalid = false;
     return FCH_OK;
 }
 
@@ -647,6 +654,7 @@ extern "C" fch_status fch_set_history(fch_ctx *ctx, const double *un, const doub
     ctx->have_state = true;
     ctx->failed = false;
     ctx->have_F = false;
+    ctx->rvalid = false;
     return fch_synchronize(ctx);
 }
 
@@ -679,21 +687,37 @@ extern "C" fch_status fch_get_state_device(fch_ctx *ctx, void *u_dev, int dtype)
 static fch_status enqueue_trial(fch_ctx *ctx, fch_scheme scheme, bool pack_f)
 {
     const int pf = pack_f ? FCH_FL_PACK_F : 0;
+    // with (u, Lap u) of u^n and u^{n-1} kept in real space (adaptive runs), the
+    // extrapolation u* and its Laplacian are formed pointwise by the first row pass
+    // instead of by an inverse column pass and inverse row transforms
+    const bool direct = ctx->rvalid;
     switch (scheme) {
     case FCH_IMEX:
-        TRY(col(ctx, CM_START, 4));
-        TRY(row(ctx, RM_NIMEX));
+        if (direct) {
+            TRY(row(ctx, RM_NIMEX_DIRECT));
+        } else {
+            TRY(col(ctx, CM_START, 4));
+            TRY(row(ctx, RM_NIMEX));
+        }
         TRY(col(ctx, CM_IMEX_SOLVE, 0, pf));
         return FCH_OK;
     case FCH_SAV:
-        TRY(col(ctx, CM_START, 4));
-        TRY(rowt(ctx, RM_SAV, 0, OP_SAV_E1, 0.0));
+        if (direct) {
+            TRY(rowt(ctx, RM_SAV_DIRECT, 0, OP_SAV_E1, 0.0));
+        } else {
+            TRY(col(ctx, CM_START, 4));
+            TRY(rowt(ctx, RM_SAV, 0, OP_SAV_E1, 0.0));
+        }
         TRY(colt(ctx, CM_SAV_PQ, 0, 0, OP_SAV_R));
         TRY(col(ctx, CM_SAV_COMBINE, 0, pf));
         return FCH_OK;
     case FCH_ETD:
-        TRY(col(ctx, CM_START, FCH_SRC_UN));
-        TRY(row(ctx, RM_NIMEX));
+        if (direct) {
+            TRY(row(ctx, RM_NIMEX_DIRECT, FCH_FL_GAMMA0));
+        } else {
+            TRY(col(ctx, CM_START, FCH_SRC_UN));
+            TRY(row(ctx, RM_NIMEX));
+        }
         TRY(col(ctx, CM_ETD_STAGE1));
         TRY(row(ctx, RM_NIMEX));
         TRY(col(ctx, CM_ETD_STAGE2, 0, pf));
@@ -723,6 +747,7 @@ extern "C" fch_status fch_step(fch_ctx *ctx, fch_scheme scheme, double dt)
 {
     if (!ctx || !(dt > 0) || scheme < FCH_IMEX || scheme > FCH_ETD) return FCH_EINVAL;
     if (!ctx->have_state || ctx->failed) return FCH_ESTATE;
+    ctx->rvalid = false; // fixed steps do not keep the real-space fields
     TRY(ctl(ctx, OP_INIT_TRIAL, 0, dt));
     fch_status s = enqueue_trial(ctx, scheme, false);
     if (s != FCH_OK) {
@@ -738,7 +763,7 @@ extern "C" fch_status fch_step(fch_ctx *ctx, fch_scheme scheme, double dt)
 static fch_status eval_F(fch_ctx *ctx, int src)
 {
     TRY(col(ctx, CM_START, src));
-    TRY(row(ctx, RM_F));
+    TRY(row(ctx, RM_F, FCH_FL_STORE_REAL, nullptr, nullptr, -1, 0.0, src));
     TRY(col(ctx, CM_F_FINISH, src));
     return FCH_OK;
 }
@@ -783,18 +808,20 @@ extern "C" fch_status fch_adaptive_begin(fch_ctx *ctx, fch_scheme scheme, double
     if (c.kn <= 0) {
         // first step k_1 = k_min by the backward-Euler start (Sec. 3.2)
         TRY(eval_F(ctx, FCH_SRC_UN));
+        ctx->rvalid = true; // u^n in real space (the start uses gam = 0: u^{n-1} not read)
         TRY(ctl(ctx, OP_INIT_TRIAL, 0, ctx->p.k_min));
         fch_status s = enqueue_trial(ctx, scheme, true);
         if (s != FCH_OK) {
             ctx->failed = true;
             return s;
         }
-        TRY(row(ctx, RM_F));
+        TRY(row(ctx, RM_F, FCH_FL_STORE_REAL, nullptr, nullptr, -1, 0.0, FCH_SRC_UNEW));
         TRY(col(ctx, CM_F_FINISH, FCH_SRC_UNEW));
         TRY(ctl(ctx, OP_ACCEPT, 0, 1.0));
     } else if (!ctx->have_F) {
         TRY(eval_F(ctx, FCH_SRC_UN));
         TRY(eval_F(ctx, 5));
+        ctx->rvalid = true;
     }
     ctx->have_F = true;
     TRY(ctl(ctx, OP_INIT_TRIAL, 0, -1.0)); // the first trial of this run
@@ -806,7 +833,7 @@ extern "C" fch_status fch_adaptive_begin(fch_ctx *ctx, fch_scheme scheme, double
 static fch_status enqueue_adaptive_trial(fch_ctx *ctx)
 {
     TRY(enqueue_trial(ctx, ctx->ad_scheme, true));
-    TRY(row(ctx, RM_F));
+    TRY(row(ctx, RM_F, FCH_FL_STORE_REAL, nullptr, nullptr, -1, 0.0, FCH_SRC_UNEW));
     TRY(col(ctx, CM_F_FINISH, FCH_SRC_UNEW, FCH_FL_AM3));
     TRY(ctl(ctx, OP_DECIDE_INIT, ctx->geom.col_blocks)); // decide, then set up the next trial
     return FCH_OK;

@@ -68,6 +68,7 @@ struct fch_kparams {
     double eps, eps2, q, gamma, bm, bp, eta1, eta2, am, beta1, beta2, zeta, D0, kappa0, kappa2;
     void *U[3], *F[3];              // state spectra and F spectra (rotated through fch_ctrl)
     void *Pb, *Qb, *Vb, *Nb;        // SAV p/q, PSD iterate, ETD N(u^n)
+    void *Rs[3];                    // real-space (u, Lap u) of the three state slots, N x N complex
     void *Z;                        // N x N complex pair-layout work array
     const void *tw;                 // per-stage Stockham twiddles (see fft_smem)
     const void *tw2;                // N = 1024 warp transform: [k2][n1] exp(-2 pi i n1 k2 / 1024), float
@@ -94,7 +95,9 @@ enum {
     FCH_FL_NOSKIP = 8,     // ignore ctrl->done (host-driven single evaluations)
     FCH_FL_COPYV = 16,     // F start from the PSD iterate: copy it into the trial slot
     FCH_FL_PSDSKIP = 32,   // pass belongs to a PSD iteration: return if converged
-    FCH_FL_F64IO = 64      // explicit real-space io in float64 (else the pass precision)
+    FCH_FL_F64IO = 64,     // explicit real-space io in float64 (else the pass precision)
+    FCH_FL_STORE_REAL = 256, // F row pass: also store (u, Lap u) into the real-space slot of src
+    FCH_FL_GAMMA0 = 512      // direct row passes: use u^n itself (gamma = 0, the ETD first stage)
 };
 
 // column-pass modes (the fused spectral stage between the column transforms)
@@ -120,6 +123,8 @@ enum {
     RM_F,              // (u, Lap u) -> pieces of mu(u) (+ energy density)
     RM_SAV,            // (u, Lap u) -> pieces of V[u] (+ G(u) density)
     RM_ENERGY,         // (u, Lap u) -> energy density only
+    RM_NIMEX_DIRECT,   // (u*, Lap u*) from the stored real-space slots -> pieces of N_IMEX(u*)
+    RM_SAV_DIRECT,     // same -> pieces of V[u*]
     RM_NMODES
 };
 

@@ -614,7 +614,23 @@ __global__ void __launch_bounds__(256) row_pass(const fch_kparams kp)
     const fch_consts<T> &K = consts<T>(kp);
 
     for (int i = threadIdx.x; i < N; i += nthr) tw[i] = ldg((const C *)kp.tw + i);
-    if (MODE == RM_R2C_LOAD) {
+    const bool direct = MODE == RM_NIMEX_DIRECT || MODE == RM_SAV_DIRECT;
+    if (direct) {
+        // (u*, Lap u*) = (u^n, Lap u^n) + gam [(u^n, Lap u^n) - (u^{n-1}, Lap u^{n-1})]
+        // pointwise from the stored real-space slots (eq. Richardson): no inverse transform
+        const fch_ctrl *cs = kp.ctrl;
+        const C *Rn = (const C *)kp.Rs[cs->iu_n];
+        const C *Rm = (const C *)kp.Rs[cs->iu_m];
+        const T g = load_coef<T>(cs).gam;
+        const bool plain = (kp.flags & FCH_FL_GAMMA0) || g == (T)0;
+        for (int i = threadIdx.x; i < rpb * N; i += nthr) {
+            const int r = i / N, x = i - r * N;
+            const long gi = (long)(y0 + r) * N + x;
+            const C zn = ldg(Rn + gi);
+            rows[r * SL + skew(x)] = plain ? zn : cadd(zn, cscale(csub(zn, ldg(Rm + gi)), g));
+        }
+        __syncthreads();
+    } else if (MODE == RM_R2C_LOAD) {
         for (int i = threadIdx.x; i < rpb * N; i += nthr) {
             const int r = i / N, x = i - r * N;
             const long g = (long)y0 * N + i;
@@ -652,9 +668,17 @@ __global__ void __launch_bounds__(256) row_pass(const fch_kparams kp)
     T red[FCH_NRED] = {0, 0, 0, 0};
     C *s = rows + rr * SL;
     const int y = y0 + rr;
+    // F row pass of an adaptive trial: keep (u, Lap u) of this state in real space
+    C *store = nullptr;
+    if (MODE == RM_F && (kp.flags & FCH_FL_STORE_REAL)) {
+        const fch_ctrl *cs = kp.ctrl;
+        const int slot = kp.src == FCH_SRC_UNEW ? cs->iu_new : (kp.src == 5 ? cs->iu_m : cs->iu_n);
+        store = (C *)kp.Rs[slot] + (long)y * N;
+    }
     if (MODE != RM_R2C_LOAD) {
         for (int x = t; x < N; x += tps) {
             const C z = s[skew(x)];
+            if (MODE == RM_F && store) store[x] = z;
             const T u = z.x, lu = z.y; // u and Lap u
             if (MODE == RM_C2R_STORE) {
                 const long g = (long)y * N + x;
@@ -670,7 +694,7 @@ __global__ void __launch_bounds__(256) row_pass(const fch_kparams kp)
             T W, W1, W2;
             well<T>(K, u, W, W1, W2);
             C o = mk<C>(0, 0);
-            if (MODE == RM_NIMEX) {
+            if (MODE == RM_NIMEX || MODE == RM_NIMEX_DIRECT) {
                 // N_IMEX = [eps^2 (am - W'' + eta1) Lap u + W''W' - am^2 u - eta2 W'] + eps^2 Lap (am u - W')
                 o.x = K.e2 * (K.am - W2 + K.eta1) * lu + W2 * W1 - K.am2 * u - K.eta2 * W1;
                 o.y = K.am * u - W1;
@@ -681,7 +705,7 @@ __global__ void __launch_bounds__(256) row_pass(const fch_kparams kp)
                 o.y = -W2 * w - K.eta2 * W1 + K.e2 * K.eta1 * lu;
                 if (MODE == RM_ENERGY || (kp.flags & FCH_FL_ENERGY))
                     red[0] += (T)0.5 * w * w - K.eta2 * W + (T)0.5 * K.e2 * K.eta1 * u * lu;
-            } else if (MODE == RM_SAV) {
+            } else if (MODE == RM_SAV || MODE == RM_SAV_DIRECT) {
                 // V = -eps^2 Lap (W' + zeta u) + [-eps^2 (W'' + zeta) Lap u + W' W'' - eta2 W']
                 o.x = W1 + K.zeta * u;
                 o.y = -K.e2 * (W2 + K.zeta) * lu + W1 * W2 - K.eta2 * W1;
@@ -690,7 +714,8 @@ __global__ void __launch_bounds__(256) row_pass(const fch_kparams kp)
             s[skew(x)] = o;
         }
     }
-    const bool has_red = MODE == RM_SAV || MODE == RM_ENERGY || (MODE == RM_F && (kp.flags & FCH_FL_ENERGY));
+    const bool has_red = MODE == RM_SAV || MODE == RM_SAV_DIRECT || MODE == RM_ENERGY ||
+                         (MODE == RM_F && (kp.flags & FCH_FL_ENERGY));
     if (has_red) {
         block_partials<1>(red, kp.part, red_scratch);
         if (kp.tail_op >= 0) pass_tail(kp);

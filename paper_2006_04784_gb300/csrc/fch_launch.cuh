@@ -124,6 +124,8 @@ cudaError_t FCH_CAT(fch_launch_row_, FCH_SUFFIX)(int mode, const fch_kparams &kp
     case RM_F: return launch_row<FCH_T, RM_F>(kp, s);
     case RM_SAV: return launch_row<FCH_T, RM_SAV>(kp, s);
     case RM_ENERGY: return launch_row<FCH_T, RM_ENERGY>(kp, s);
+    case RM_NIMEX_DIRECT: return launch_row<FCH_T, RM_NIMEX_DIRECT>(kp, s);
+    case RM_SAV_DIRECT: return launch_row<FCH_T, RM_SAV_DIRECT>(kp, s);
     }
     return cudaErrorInvalidValue;
 }

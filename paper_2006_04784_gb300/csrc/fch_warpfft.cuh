@@ -95,7 +95,7 @@ __device__ __forceinline__ float2 pointwise(const fch_kparams &kp, const fch_con
     float W, W1, W2;
     well<float>(K, u, W, W1, W2);
     float2 o = mk<float2>(0.f, 0.f);
-    if (MODE == RM_NIMEX) {
+    if (MODE == RM_NIMEX || MODE == RM_NIMEX_DIRECT) {
         o.x = K.e2 * (K.am - W2 + K.eta1) * lu + W2 * W1 - K.am2 * u - K.eta2 * W1;
         o.y = K.am * u - W1;
     } else if (MODE == RM_F || MODE == RM_ENERGY) {
@@ -104,7 +104,7 @@ __device__ __forceinline__ float2 pointwise(const fch_kparams &kp, const fch_con
         o.y = -W2 * w - K.eta2 * W1 + K.e2 * K.eta1 * lu;
         if (MODE == RM_ENERGY || (kp.flags & FCH_FL_ENERGY))
             red[0] += 0.5f * w * w - K.eta2 * W + 0.5f * K.e2 * K.eta1 * u * lu;
-    } else if (MODE == RM_SAV) {
+    } else if (MODE == RM_SAV || MODE == RM_SAV_DIRECT) {
         o.x = W1 + K.zeta * u;
         o.y = -K.e2 * (W2 + K.zeta) * lu + W1 * W2 - K.eta2 * W1;
         red[0] += -K.e2 * lu * (W1 + K.zeta * u) + 0.5f * W1 * W1 - K.eta2 * W;
@@ -128,7 +128,19 @@ __global__ void __launch_bounds__(32) row_pass_w(const fch_kparams kp)
     const bool f64io = kp.flags & FCH_FL_F64IO;
     C *row = (C *)kp.Z + (long)y * N;
     C v[32];
-    if (MODE == RM_R2C_LOAD) {
+    if (MODE == RM_NIMEX_DIRECT || MODE == RM_SAV_DIRECT) {
+        // (u*, Lap u*) pointwise from the stored real-space slots (eq. Richardson)
+        const fch_ctrl *cs = kp.ctrl;
+        const C *Rn = (const C *)kp.Rs[cs->iu_n] + (long)y * N;
+        const C *Rm = (const C *)kp.Rs[cs->iu_m] + (long)y * N;
+        const float g = cs->cof.gam;
+        const bool plain = (kp.flags & FCH_FL_GAMMA0) || g == 0.f;
+#pragma unroll
+        for (int n2 = 0; n2 < 32; n2++) {
+            const C zn = __ldg(Rn + lane + 32 * n2);
+            v[n2] = plain ? zn : cadd(zn, cscale(csub(zn, __ldg(Rm + lane + 32 * n2)), g));
+        }
+    } else if (MODE == RM_R2C_LOAD) {
 #pragma unroll
         for (int n2 = 0; n2 < 32; n2++) {
             const long g = (long)y * N + lane + 32 * n2;
@@ -158,11 +170,18 @@ __global__ void __launch_bounds__(32) row_pass_w(const fch_kparams kp)
     }
 
     float red[FCH_NRED] = {0.f, 0.f, 0.f, 0.f};
+    C *store = nullptr;
+    if (MODE == RM_F && (kp.flags & FCH_FL_STORE_REAL)) {
+        const fch_ctrl *cs = kp.ctrl;
+        const int slot = kp.src == FCH_SRC_UNEW ? cs->iu_new : (kp.src == 5 ? cs->iu_m : cs->iu_n);
+        store = (C *)kp.Rs[slot] + (long)y * N;
+    }
     if (MODE != RM_R2C_LOAD) {
         const fch_consts<float> &K = kp.cf;
 #pragma unroll
         for (int k1 = 0; k1 < 32; k1++) {
             const int x = lane + 32 * k1;
+            if (MODE == RM_F && store) store[x] = v[k1];
             const float u = v[k1].x, lu = v[k1].y;
             if (MODE == RM_C2R_STORE) {
                 const long g = (long)y * N + x;
@@ -178,7 +197,8 @@ __global__ void __launch_bounds__(32) row_pass_w(const fch_kparams kp)
             v[k1] = pointwise<MODE>(kp, K, u, lu, red);
         }
     }
-    const bool has_red = MODE == RM_SAV || MODE == RM_ENERGY || (MODE == RM_F && (kp.flags & FCH_FL_ENERGY));
+    const bool has_red = MODE == RM_SAV || MODE == RM_SAV_DIRECT || MODE == RM_ENERGY ||
+                         (MODE == RM_F && (kp.flags & FCH_FL_ENERGY));
     if (has_red) {
         block_partials<1>(red, kp.part, red_scratch);
         if (kp.tail_op >= 0) pass_tail(kp);

@@ -30,11 +30,12 @@ EXPORTS = ["fch_status_string", "fch_last_cuda_error", "fch_params_default", "fc
            "fch_fft_plan_create", "fch_fft_plan_destroy", "fch_fft_r2c", "fch_fft_c2r",
            "fch_adaptive_begin", "fch_adaptive_enqueue", "fch_adaptive_end", "fch_pass_timing",
            "fch_pass_times", "fch_fft_r2c_noalloc"]
-NCOL, NROW = 10, 6
+NCOL, NROW = 10, 8
 NPASS = NCOL + NROW + 1
 PASS_NAMES = (["col_fwd_store", "col_inv_load", "col_start", "col_imex_solve", "col_f_finish",
                "col_sav_pq", "col_sav_combine", "col_psd_iter", "col_etd_stage1", "col_etd_stage2"]
-              + ["row_r2c_load", "row_c2r_store", "row_nimex", "row_f", "row_sav", "row_energy"]
+              + ["row_r2c_load", "row_c2r_store", "row_nimex", "row_f", "row_sav", "row_energy",
+                 "row_nimex_direct", "row_sav_direct"]
               + ["ctrl"])
 
 

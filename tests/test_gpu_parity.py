@@ -371,3 +371,37 @@ def test_fp32x2_1024_one_step_vs_oracle():
         ctx.set_state(u0)
         ctx.step("imex", 1e-6)
         assert rel(ctx.get_state(), s.state()) < 1e-10
+
+
+@pytest.mark.parametrize("prec", [0, 2])
+def test_512_fixed_steps_vs_oracle(prec):
+    # the 512^2 grid of the all-schemes adaptive workload (multimode bilayer)
+    n = 512
+    p = lib_params(0.0, prec=prec)
+    u0 = I.multimode_bilayer(n)
+    s = O.Stepper(n, L, oparams(p))
+    s.set_state(u0)
+    with fch.Context(n, p) as ctx:
+        ctx.set_state(u0)
+        for dt in (1e-4, 1e-4, 2e-4):
+            s.step("imex", dt)
+            ctx.step("imex", dt)
+            assert rel(ctx.get_state(), s.state()) < 1e-10
+
+
+def test_paper_initial_data_adaptive_vs_oracle():
+    # the super-critical benchmark's own initial data (Sec. 2.3) at 64^2, adaptive IMEX
+    n = 64
+    p = lib_params(0.0, zero_stab_cap=1, prec=2)
+    u0 = I.paper_initial_data(n, 0.5)
+    s = O.Stepper(n, L, oparams(p))
+    s.set_state(u0)
+    assert s.run_adaptive("imex", 1e-5, 0.02) == 0
+    with fch.Context(n, p) as ctx:
+        ctx.set_state(u0)
+        st = ctx.run_adaptive("imex", 1e-5, 0.02)
+        assert st["n_steps"] == s.counts()["steps"]
+        assert rel(ctx.get_state(), s.state()) < 1e-9
+        # 95 steps; each rounds the mean mode a few dozen times at the double-float unit
+        # 2^-48 = 3.6e-15 (the FP64 oracle drifts 9.5e-14 over the same run, 2^-53 units)
+        assert ctx.mass() == pytest.approx(O.mass(u0, L), rel=1e-11)
