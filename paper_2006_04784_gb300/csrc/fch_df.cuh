@@ -72,6 +72,26 @@ __device__ __forceinline__ df operator+(df a, df b)
     return fast_two_sum(s.hi, s.lo);
 }
 
+// The sum above without its renormalisation (8 operations), for the butterflies of
+// a transform: |lo| may then exceed ulp(hi)/2 by a small factor. Products absorb
+// such operands (their low-order terms are summed into the error word) and
+// renorm() restores the invariant where a stage ends. A subtraction that cancels
+// the high parts leaves the result in lo, so no routine that reads only .hi
+// (division, comparisons) may take an unrenormalised value.
+__device__ __forceinline__ df add_lazy(df a, df b)
+{
+    df s = two_sum(a.hi, b.hi);
+    s.lo += a.lo + b.lo;
+    return s;
+}
+__device__ __forceinline__ df sub_lazy(df a, df b)
+{
+    df s = two_sum(a.hi, -b.hi);
+    s.lo += a.lo - b.lo;
+    return s;
+}
+__device__ __forceinline__ df renorm(df a) { return fast_two_sum(a.hi, a.lo); }
+
 __device__ __forceinline__ df operator-(df a) { return df(-a.hi, -a.lo); }
 __device__ __forceinline__ df operator-(df a, df b) { return a + (-b); }
 
@@ -97,6 +117,36 @@ __device__ __forceinline__ df operator/(df a, df b)
     const float q3 = r.hi * rb;
     df q = fast_two_sum(q1, q2);
     return q + df(q3, 0.f);
+}
+
+// Complex product a w for a twiddle factor w, each part a sum of two products
+// with one TwoSum: the high products are added exactly, their rounding errors
+// (from fused multiply-adds) and the four cross terms with the low words go into
+// one error word, left unrenormalised (16 operations a part instead of 25).
+__device__ __forceinline__ df2 cmul_lazy(df2 a, df2 w)
+{
+    df2 r;
+    {
+        const float p1 = a.x.hi * w.x.hi, p2 = a.y.hi * w.y.hi;
+        r.x = two_sum(p1, -p2);
+        float e = fmaf(a.x.hi, w.x.hi, -p1) - fmaf(a.y.hi, w.y.hi, -p2);
+        e = fmaf(a.x.hi, w.x.lo, e);
+        e = fmaf(a.x.lo, w.x.hi, e);
+        e = fmaf(-a.y.hi, w.y.lo, e);
+        e = fmaf(-a.y.lo, w.y.hi, e);
+        r.x.lo += e;
+    }
+    {
+        const float p1 = a.x.hi * w.y.hi, p2 = a.y.hi * w.x.hi;
+        r.y = two_sum(p1, p2);
+        float e = fmaf(a.x.hi, w.y.hi, -p1) + fmaf(a.y.hi, w.x.hi, -p2);
+        e = fmaf(a.x.hi, w.y.lo, e);
+        e = fmaf(a.x.lo, w.y.hi, e);
+        e = fmaf(a.y.hi, w.x.lo, e);
+        e = fmaf(a.y.lo, w.x.hi, e);
+        r.y.lo += e;
+    }
+    return r;
 }
 
 __device__ __forceinline__ df &operator+=(df &a, df b) { return a = a + b; }

@@ -67,6 +67,20 @@ template <typename C, typename S> __device__ __forceinline__ C cscale(C a, S s)
 {
     return mk<C>(a.x * s, a.y * s);
 }
+// Butterfly arithmetic: the plain complex operations for float and double; for
+// double-float the unrenormalised sums and twiddle product of fch_df.cuh, with
+// bnorm() renormalising where a transform stage stores its results.
+template <typename R> __device__ __forceinline__ R radd(R a, R b) { return a + b; }
+template <typename R> __device__ __forceinline__ R rsub(R a, R b) { return a - b; }
+template <> __device__ __forceinline__ df radd(df a, df b) { return add_lazy(a, b); }
+template <> __device__ __forceinline__ df rsub(df a, df b) { return sub_lazy(a, b); }
+template <typename C> __device__ __forceinline__ C badd(C a, C b) { return mk<C>(radd(a.x, b.x), radd(a.y, b.y)); }
+template <typename C> __device__ __forceinline__ C bsub(C a, C b) { return mk<C>(rsub(a.x, b.x), rsub(a.y, b.y)); }
+template <typename C> __device__ __forceinline__ C btw(C a, C w) { return cmul(a, w); }
+template <> __device__ __forceinline__ df2 btw(df2 a, df2 w) { return cmul_lazy(a, w); }
+template <typename C> __device__ __forceinline__ C bnorm(C a) { return a; }
+template <> __device__ __forceinline__ df2 bnorm(df2 a) { return mk<df2>(renorm(a.x), renorm(a.y)); }
+
 // a * (DIR i): DIR = -1 forward (-i), +1 inverse (+i)
 template <int DIR, typename C> __device__ __forceinline__ C rot(C a)
 {
@@ -76,17 +90,17 @@ template <int DIR, typename C> __device__ __forceinline__ C rot(C a)
 template <int DIR, typename C> __device__ __forceinline__ void bfly2(C &a, C &b)
 {
     C t = a;
-    a = cadd(t, b);
-    b = csub(t, b);
+    a = badd(t, b);
+    b = bsub(t, b);
 }
 
 template <int DIR, typename C> __device__ __forceinline__ void bfly4(C &x0, C &x1, C &x2, C &x3)
 {
-    C a = cadd(x0, x2), b = csub(x0, x2), c = cadd(x1, x3), d = rot<DIR>(csub(x1, x3));
-    x0 = cadd(a, c);
-    x1 = cadd(b, d);
-    x2 = csub(a, c);
-    x3 = csub(b, d);
+    C a = badd(x0, x2), b = bsub(x0, x2), c = badd(x1, x3), d = rot<DIR>(bsub(x1, x3));
+    x0 = badd(a, c);
+    x1 = badd(b, d);
+    x2 = bsub(a, c);
+    x3 = bsub(b, d);
 }
 
 template <int DIR, typename C> __device__ __forceinline__ void bfly8(C *v)
@@ -100,22 +114,22 @@ template <int DIR, typename C> __device__ __forceinline__ void bfly8(C *v)
     const C a = v[3], b = v[7];
     C o1, o3;
     if (DIR < 0) {
-        o1 = mk<C>((a.x + a.y) * s, (a.y - a.x) * s);
-        o3 = mk<C>((b.y - b.x) * s, -((b.x + b.y) * s));
+        o1 = mk<C>(radd(a.x, a.y) * s, rsub(a.y, a.x) * s);
+        o3 = mk<C>(rsub(b.y, b.x) * s, -(radd(b.x, b.y) * s));
     } else {
-        o1 = mk<C>((a.x - a.y) * s, (a.x + a.y) * s);
-        o3 = mk<C>(-((b.x + b.y) * s), (b.x - b.y) * s);
+        o1 = mk<C>(rsub(a.x, a.y) * s, radd(a.x, a.y) * s);
+        o3 = mk<C>(-(radd(b.x, b.y) * s), rsub(b.x, b.y) * s);
     }
     C o2 = rot<DIR>(v[5]);
     C e0 = v[0], e1 = v[2], e2 = v[4], e3 = v[6], o0 = v[1];
-    v[0] = cadd(e0, o0);
-    v[4] = csub(e0, o0);
-    v[1] = cadd(e1, o1);
-    v[5] = csub(e1, o1);
-    v[2] = cadd(e2, o2);
-    v[6] = csub(e2, o2);
-    v[3] = cadd(e3, o3);
-    v[7] = csub(e3, o3);
+    v[0] = badd(e0, o0);
+    v[4] = bsub(e0, o0);
+    v[1] = badd(e1, o1);
+    v[5] = bsub(e1, o1);
+    v[2] = badd(e2, o2);
+    v[6] = bsub(e2, o2);
+    v[3] = badd(e3, o3);
+    v[7] = bsub(e3, o3);
 }
 
 // Shared-memory skew: element n of a sequence is stored at n + n/8, which spreads
@@ -151,7 +165,7 @@ __device__ __forceinline__ void fft_stage(C *s, int N, int logN, int stride, int
             for (int r = 1; r < R; r++) {
                 C tv = tws[(r - 1) * Ns];
                 if (DIR > 0) tv = cconj(tv);
-                v[b * R + r] = cmul(v[b * R + r], tv);
+                v[b * R + r] = btw(v[b * R + r], tv);
             }
         }
         if (LR == 3)
@@ -167,7 +181,7 @@ __device__ __forceinline__ void fft_stage(C *s, int N, int logN, int stride, int
         const int j = t + b * tps;
         const int idxD = ((j >> lNs) << (lNs + LR)) + (j & (Ns - 1));
 #pragma unroll
-        for (int r = 0; r < R; r++) s[skew(idxD + r * Ns) * stride + off] = v[b * R + r];
+        for (int r = 0; r < R; r++) s[skew(idxD + r * Ns) * stride + off] = bnorm(v[b * R + r]);
     }
     __syncthreads();
 }
@@ -436,11 +450,22 @@ template <typename T, int LOGN> constexpr int spec_pairs()
     return (1024 >> LOGN) > (sizeof(T) == 4 ? 2 : 1) ? (1024 >> LOGN) : (sizeof(T) == 4 ? 2 : 1);
 }
 
+// Resident blocks per SM a compile-time pass is built for: four blocks of 256
+// threads (at most 64 registers a thread) at N <= 1024, so that the 512 blocks of a
+// 1024^2 pass run in one wave on the 152 SMs (with three per SM, 56 blocks would be
+// left for a second wave); other sizes keep the compiler's choice.
+template <int THREADS, int LOGN> constexpr int pass_min_blocks()
+{
+    return (LOGN > 0 && LOGN <= 10 && THREADS == 256) ? 4 : 1;
+}
+
 // LOGN > 0: the grid size is a compile-time constant (N = 2^LOGN >= 512), so the
 // index arithmetic of the transforms folds into immediates; LOGN = 0 reads N and P
 // from the parameters.
 template <typename T, int MODE, int LOGN>
-__global__ void __launch_bounds__(LOGN ? ((spec_pairs<T, LOGN>() << LOGN) >> 2) : 1024) col_pass(const fch_kparams kp)
+__global__ void __launch_bounds__(LOGN ? ((spec_pairs<T, LOGN>() << LOGN) >> 2) : 1024,
+                                  pass_min_blocks<LOGN ? ((spec_pairs<T, LOGN>() << LOGN) >> 2) : 1024, LOGN>())
+col_pass(const fch_kparams kp)
 {
     typedef typename CT<T>::t C;
     typedef ColTraits<MODE> TR;
@@ -508,7 +533,7 @@ __global__ void __launch_bounds__(LOGN ? ((spec_pairs<T, LOGN>() << LOGN) >> 2) 
     T red[FCH_NRED] = {0, 0, 0, 0};
     // spectral stage: work item (pair p, ky); pair 0 covers columns 0 and N/2
     // blockDim = P N / 4: exactly 4 work items per thread
-#pragma unroll
+#pragma unroll 1
     for (int it = 0; it < 4; it++) {
         const int i = threadIdx.x + it * nthr;
         const int pp = i / N, ky = i - pp * N;
@@ -593,7 +618,7 @@ __global__ void __launch_bounds__(LOGN ? ((spec_pairs<T, LOGN>() << LOGN) >> 2) 
 // ---------------------------------------------------------------------------
 // row pass: [inverse rows] -> pointwise stage -> [forward rows]
 template <typename T, int MODE, int LOGN>
-__global__ void __launch_bounds__(256) row_pass(const fch_kparams kp)
+__global__ void __launch_bounds__(256, pass_min_blocks<256, LOGN>()) row_pass(const fch_kparams kp)
 {
     typedef typename CT<T>::t C;
     if (pass_skipped(kp)) return;
@@ -676,6 +701,7 @@ __global__ void __launch_bounds__(256) row_pass(const fch_kparams kp)
         store = (C *)kp.Rs[slot] + (long)y * N;
     }
     if (MODE != RM_R2C_LOAD) {
+#pragma unroll 1
         for (int x = t; x < N; x += tps) {
             const C z = s[skew(x)];
             if (MODE == RM_F && store) store[x] = z;
