@@ -225,7 +225,8 @@ def run_gb300(args):
 
     n = N_GRID
     prec = {"mixed": fch.FCH_MIXED, "fp64": fch.FCH_FP64, "fp32x2": fch.FCH_FP32X2}[args.prec]
-    p = fch.params_default(0.0, eta2=1.5 * 0.1, prec=prec, sync_every=64)
+    p = fch.params_default(0.0, eta2=1.5 * 0.1, prec=prec, sync_every=64, autotune=int(args.autotune))
+    tiles = fch.autotune(n, prec) if args.autotune else None
     u0 = I.random_network(n, d=0.75, seed=3 + rank)
     stream = torch.cuda.Stream(device=dev)
     ctx = fch.Context(n, p, stream=stream)
@@ -294,9 +295,11 @@ def run_gb300(args):
                "accepted": st1["n_steps"] - st0["n_steps"], "rejected": st1["n_rejects"] - st0["n_rejects"],
                "t_reached": st1["t"],
                "gpu_launches": sum(v[1] for v in times.values()) // max(1, K2) * K,  # per trial, from the eager region
-               "kernels": kernels, "kernels_region": f"{K2} trials launched kernel by kernel "
+               "tiles": tiles, "kernels": kernels, "kernels_region": f"{K2} trials launched kernel by kernel "
                f"(per-launch events; {eager_ms_per_step:.4f} ms/step there vs {ms_per_step:.4f} "
                "with the CUDA graph)", "roofline": roof, "clocks": clk.summary(), "e2e": e2e}
+        if not args.no_fft:
+            out["fft"] = fft_throughput(fch, dev)
         if not args.no_t_final and world == 1:
             out["time_to_t_final"] = time_to_t_final(fch, I, n)
         if not args.no_cpu_baseline and world == 1:
@@ -336,6 +339,61 @@ def time_to_t_final(fch, I, n, t_final=0.02):
         out[name] = {"wall_s": wall, "trials": st["n_attempts"], "rejected": st["n_rejects"],
                      "t_reached": st["t"], "reached": bool(reached),
                      "rel_l2_error": float(np.linalg.norm(u - ref) / np.linalg.norm(ref)) if reached else None}
+    return out
+
+
+def fft_throughput(fch, dev, n=N_GRID, batch=32, iters=10, warmup=3):
+    """Standalone 2D real transforms at n^2 (fch_fft_r2c then fch_fft_c2r over a
+    batch of fields, inputs larger than L2) against cuFFT through torch.fft
+    (rfft2 / irfft2 of the same batch), FP64 and FP32. One transform = one field
+    one way. Roofline per transform: compulsory bytes (read the field or spectrum,
+    write the other) against HBM, and 2.5 n^2 log2(n^2) flops against the FP64
+    pipe for FP64."""
+    import torch
+
+    hbm = measured_peaks().get("hbm_gbs") or 6800.0
+    out = {"n": n, "batch": batch, "unit": "2D real transforms/s (one field, one way)"}
+    for name, prec, rdt in (("fp64", fch.FCH_FP64, torch.float64), ("fp32", fch.FCH_MIXED, torch.float32)):
+        stream = torch.cuda.Stream(device=dev)
+        x = torch.randn(batch, n, n, dtype=rdt, device=dev)
+        X = torch.empty(batch, n // 2 + 1, n, dtype=torch.complex128 if rdt == torch.float64 else torch.complex64,
+                        device=dev)
+        y = torch.empty_like(x)
+        plan = fch.FFTPlan(n, prec, stream=stream)
+
+        def ours():
+            plan.r2c(x, X)
+            plan.c2r(X, y)
+
+        def cufft():
+            torch.fft.irfft2(torch.fft.rfft2(x), s=(n, n))
+
+        res = {}
+        for label, fn in (("fch", ours), ("cufft", cufft)):
+            with torch.cuda.stream(stream):
+                for _ in range(warmup):
+                    fn()
+                a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                torch.cuda.synchronize()
+                a.record(stream)
+                for _ in range(iters):
+                    fn()
+                b.record(stream)
+            torch.cuda.synchronize()
+            res[label] = 2 * batch * iters / (a.elapsed_time(b) / 1e3)
+        err = float((y - x).abs().max() / x.abs().max())
+        plan.close()
+        rs = 8 if rdt == torch.float64 else 4
+        byt = n * n * rs + (n // 2 + 1) * n * 2 * rs
+        ent = {"fch": res["fch"], "cufft": res["cufft"], "fch_over_cufft": res["fch"] / res["cufft"],
+               "round_trip_max_rel_err": err, "bytes_per_transform": byt,
+               "hbm_frac": res["fch"] * byt / 1e9 / hbm, "hbm_peak_gbs": hbm}
+        if name == "fp64":
+            fl = 2.5 * n * n * math.log2(n * n)
+            ent["fp64_pipe_frac"] = res["fch"] * fl / 1.25e12
+            ent["fp64_pipe_peak"] = "1.25 TFLOP/s nominal FP64"
+        out[name] = ent
+        del x, X, y
     return out
 
 
@@ -440,6 +498,220 @@ def paper_costs(args):
     return out
 
 
+def _rel(a, b):
+    import numpy as np
+    return float(np.linalg.norm(a - b) / np.linalg.norm(b))
+
+
+def workloads(args):
+    """The other configurations of the hot path, measured end to end through the C ABI
+    (wall time of the calls, device work included):
+    (1) 128^2 circle bilayer, IMEX-BDF2, fixed dt = 1e-3, 400 steps (FP64 and FP32X2),
+        with the FP64 result against the oracle's;
+    (2) 512^2 multimode bilayer, adaptive IMEX / SAV / PSD / ETD, sigma_tol = 1e-5 to
+        t = 50, FP64 and FP32X2: steps, rejects, transforms, PSD iterations, wall time,
+        and the FP32X2 - FP64 difference at t = 50;
+    (3) 1024^2 and 2048^2 random bilayer network, critical parameters, adaptive IMEX at
+        sigma_tol = 1e-5 to t_final: FP32X2 and FP64 wall time and relative L2 error
+        against an FP32X2 run at sigma_tol / 100 (FP32 with a trial budget: its LTE
+        estimate is rounding-limited at these sizes)."""
+    import numpy as np
+
+    from paper_2006_04784_gb300 import build as B
+    B.build()
+    from paper_2006_04784_gb300 import fch
+    from paper_2006_04784_gb300 import inputs as I
+
+    def P(q=0.0, **kw):
+        p = fch.params_default(q, **kw)
+        return p
+
+    out = {}
+    # (1) fixed steps
+    n = 128
+    u0 = I.circle_bilayer(n)
+    cfg1 = {"n": n, "dt": 1e-3, "steps": 400}
+    for name, prec in (("fp64", fch.FCH_FP64), ("fp32x2", fch.FCH_FP32X2)):
+        with fch.Context(n, P(prec=prec)) as ctx:
+            ctx.set_state(u0)
+            ctx.synchronize()
+            t0 = time.perf_counter()
+            for _ in range(400):
+                ctx.step("imex", 1e-3)
+            ctx.synchronize()
+            wall = time.perf_counter() - t0
+            cfg1[name] = {"wall_s": wall, "steps_per_s": 400 / wall, "u": ctx.get_state()}
+    try:
+        from oracle import oracle as O
+        O.build()
+        p = P()
+        s = O.Stepper(n, 4 * math.pi, O.params(eps=p.eps, q=p.q, gamma=p.gamma, eta1=p.eta1, eta2=p.eta2,
+                                                zeta=p.zeta, D0=p.D0))
+        s.set_state(u0)
+        t0 = time.perf_counter()
+        for _ in range(400):
+            s.step("imex", 1e-3)
+        cfg1["oracle"] = {"wall_s": time.perf_counter() - t0, "cores": 1}
+        for name in ("fp64", "fp32x2"):
+            cfg1[name]["rel_l2_vs_oracle"] = _rel(cfg1[name]["u"], s.state())
+    except Exception as e:  # the oracle is a baseline only
+        cfg1["oracle"] = {"error": str(e)}
+    for name in ("fp64", "fp32x2"):
+        cfg1[name].pop("u")
+    out["cfg1_128_fixed_dt"] = cfg1
+
+    # (2) all schemes at 512^2
+    n, T = 512, args.workload_t2
+    u0 = I.multimode_bilayer(n)
+    cfg2 = {"n": n, "sigma_tol": SIGMA, "t_final": T, "runs": []}
+    for scheme in ("imex", "sav", "psd", "etd"):
+        res = {}
+        for name, prec in (("fp64", fch.FCH_FP64), ("fp32x2", fch.FCH_FP32X2)):
+            with fch.Context(n, P(prec=prec, sync_every=256)) as ctx:
+                ctx.set_state(u0)
+                t0 = time.perf_counter()
+                st = ctx.run_adaptive(scheme, SIGMA, T, max_attempts=args.workload_budget,
+                                      raise_on_timeout=False)
+                wall = time.perf_counter() - t0
+                res[name] = {"wall_s": wall, "t_reached": st["t"], "steps": st["n_steps"],
+                             "rejects": st["n_rejects"], "transforms": st["n_fft"],
+                             "psd_iter": st["n_psd_iter"], "mass": ctx.mass(), "energy": ctx.energy(),
+                             "u": ctx.get_state()}
+        d = _rel(res["fp32x2"]["u"], res["fp64"]["u"]) if res["fp32x2"]["t_reached"] == res["fp64"]["t_reached"] else None
+        for r in res.values():
+            r.pop("u")
+        cfg2["runs"].append({"scheme": scheme, **res, "fp32x2_vs_fp64_rel_l2": d})
+    out["cfg2_512_all_schemes"] = cfg2
+
+    # (3) large grids, adaptive IMEX to t_final
+    cfg3 = {"sigma_tol": SIGMA, "t_final": args.workload_t3, "runs": []}
+    for n in (1024, 2048):
+        u0 = I.random_network(n, d=0.75, seed=3)
+
+        def run(prec, sigma, budget):
+            with fch.Context(n, P(eta2=0.15, prec=prec, sync_every=256)) as ctx:
+                ctx.set_state(u0)
+                t0 = time.perf_counter()
+                st = ctx.run_adaptive("imex", sigma, args.workload_t3, max_attempts=budget, raise_on_timeout=False)
+                return st, time.perf_counter() - t0, ctx.get_state(), ctx.mass()
+
+        ref_st, ref_wall, ref, _ = run(fch.FCH_FP32X2, SIGMA / 100, 0)
+        row = {"n": n, "reference": {"precision": "fp32x2", "sigma_tol": SIGMA / 100,
+                                     "steps": ref_st["n_steps"], "wall_s": ref_wall}}
+        for name, prec, budget in (("fp32x2", fch.FCH_FP32X2, 0), ("fp64", fch.FCH_FP64, 0),
+                                   ("fp32", fch.FCH_MIXED, 2000)):
+            st, wall, u, m = run(prec, SIGMA, budget)
+            reached = st["t"] >= args.workload_t3 * (1 - 1e-12)
+            row[name] = {"wall_s": wall, "t_reached": st["t"], "steps": st["n_steps"], "rejects": st["n_rejects"],
+                         "transforms": st["n_fft"], "mass": m,
+                         "rel_l2_vs_reference": _rel(u, ref) if reached else None}
+        cfg3["runs"].append(row)
+    out["cfg3_large_adaptive"] = cfg3
+    return out
+
+
+def ensemble_bench(args):
+    """A batched ensemble: 64 instances on uneven grids (32 at 256^2, 24 at 512^2,
+    8 at 1024^2), eta1/eps swept linearly over [1, 3], seeds 100..163, multimode
+    bilayer initial data, adaptive IMEX-BDF2 at sigma_tol = 1e-5 to t_final, in
+    one CUDA graph per launch (fch_ensemble_run_adaptive), against the same 64
+    instances run one after another (fch_run_adaptive each). Pass tiles from the
+    autotuner for both."""
+    import numpy as np
+
+    from paper_2006_04784_gb300 import build as B
+    B.build()
+    from paper_2006_04784_gb300 import fch
+    from paper_2006_04784_gb300 import inputs as I
+
+    prec = {"mixed": fch.FCH_MIXED, "fp64": fch.FCH_FP64, "fp32x2": fch.FCH_FP32X2}[args.prec]
+    sizes = [256] * 32 + [512] * 24 + [1024] * 8
+    m = len(sizes)
+    eps = 0.1
+    params = [fch.params_default(0.0, eta1=eps * (1.0 + 2.0 * i / (m - 1)), prec=prec, autotune=1,
+                                 sync_every=64) for i in range(m)]
+    inits = [I.multimode_bilayer(n, seed=100 + i) for i, n in enumerate(sizes)]
+    tf = args.ensemble_t
+    out = {"members": m, "sizes": {"256": 32, "512": 24, "1024": 8}, "eta1_over_eps": [1.0, 3.0],
+           "seeds": [100, 100 + m - 1], "scheme": "imex", "sigma_tol": SIGMA, "t_final": tf,
+           "precision": args.prec, "rounds_per_launch": args.ensemble_rounds}
+    with fch.Ensemble(sizes, params) as ens:
+        for i in range(m):
+            ens[i].set_state(inits[i])
+        t0 = time.perf_counter()
+        st = ens.run_adaptive("imex", SIGMA, tf, rounds=args.ensemble_rounds)
+        wall = time.perf_counter() - t0
+        ens_states = [ens[i].get_state() for i in (0, 32, 56)]
+    trials = sum(s["n_attempts"] for s in st)
+    out["ensemble"] = {"wall_s": wall, "trials": trials, "trials_per_s": trials / wall,
+                       "steps": sum(s["n_steps"] for s in st), "rejects": sum(s["n_rejects"] for s in st),
+                       "all_reached": all(s["t"] >= tf * (1 - 1e-12) for s in st)}
+    wall_seq, trials_seq, same = 0.0, 0, True
+    for i in range(m):
+        with fch.Context(sizes[i], params[i]) as ctx:
+            ctx.set_state(inits[i])
+            t0 = time.perf_counter()
+            s = ctx.run_adaptive("imex", SIGMA, tf)
+            wall_seq += time.perf_counter() - t0
+            trials_seq += s["n_attempts"]
+            if i in (0, 32, 56):
+                same = same and bool(np.array_equal(ctx.get_state(), ens_states[(0, 32, 56).index(i)]))
+    out["sequential"] = {"wall_s": wall_seq, "trials": trials_seq, "trials_per_s": trials_seq / wall_seq}
+    out["speedup"] = wall_seq / wall
+    out["members_identical_to_solo_runs"] = same
+    return out
+
+
+def error_budget(args):
+    """Single precision against FP64 (and double-float against FP64) per field at
+    1024^2 and 2048^2 on the random bilayer network (critical parameters): F(u) of
+    the initial data, and after fixed IMEX steps u, F(u), mass and energy."""
+    import numpy as np
+    import torch
+
+    from paper_2006_04784_gb300 import build as B
+    B.build()
+    from paper_2006_04784_gb300 import fch
+    from paper_2006_04784_gb300 import inputs as I
+
+    dev = torch.device("cuda", 0)
+    out = {"steps": args.budget_steps, "dt": args.budget_dt, "runs": []}
+    for n in (1024, 2048):
+        u0 = I.random_network(n, d=0.75, seed=3)
+        res = {}
+        for name, prec in (("fp64", fch.FCH_FP64), ("fp32x2", fch.FCH_FP32X2), ("fp32", fch.FCH_MIXED)):
+            p = fch.params_default(0.0, eta2=0.15, prec=prec)
+            with fch.Context(n, p) as ctx:
+                ut = torch.tensor(u0, device=dev)
+                F0 = torch.empty_like(ut)
+                torch.cuda.synchronize()
+                ctx.rhs_device(ut, F0)
+                ctx.synchronize()
+                ctx.set_state(u0)
+                m0 = ctx.mass()
+                for _ in range(args.budget_steps):
+                    ctx.step("imex", args.budget_dt)
+                u = ctx.get_state()
+                F1 = torch.empty_like(ut)
+                ut1 = torch.tensor(u, device=dev)
+                torch.cuda.synchronize()
+                ctx.rhs_device(ut1, F1)
+                ctx.synchronize()
+                res[name] = {"F0": F0.cpu().numpy(), "u": u, "F1": F1.cpu().numpy(), "mass": ctx.mass(),
+                             "mass0": m0, "energy": ctx.energy()}
+        row = {"n": n}
+        for name in ("fp32x2", "fp32"):
+            a, b = res[name], res["fp64"]
+            row[name] = {"F_initial_rel_l2": _rel(a["F0"], b["F0"]), "u_rel_l2": _rel(a["u"], b["u"]),
+                         "F_final_rel_l2": _rel(a["F1"], b["F1"]),
+                         "mass_rel_drift": abs(a["mass"] - a["mass0"]) / abs(a["mass0"]),
+                         "mass_rel_vs_fp64": abs(a["mass"] - b["mass"]) / abs(b["mass"]),
+                         "energy_rel_vs_fp64": abs(a["energy"] - b["energy"]) / abs(b["energy"])}
+        row["fp64"] = {"mass_rel_drift": abs(res["fp64"]["mass"] - res["fp64"]["mass0"]) / abs(res["fp64"]["mass0"])}
+        out["runs"].append(row)
+    return out
+
+
 def run_reference(args):
     """The oracle as the reference arm: adaptive IMEX trials at 1024^2 on the host
     cores, each step one trial (bounded: at most ~150 s of timed work)."""
@@ -490,12 +762,33 @@ def main():
                     help="mixed (single-precision transforms), fp64, or fp32x2 (double-float)")
     ap.add_argument("--scheme", default="imex", choices=["imex", "sav", "etd"])
     ap.add_argument("--no-t-final", action="store_true", help="skip the time-to-t_final runs")
+    ap.add_argument("--no-fft", action="store_true", help="skip the standalone transform throughput")
+    ap.add_argument("--autotune", type=int, default=1, help="1: pass tiles from fch_autotune (default); 0: default tiles")
     ap.add_argument("--paper-costs", action="store_true",
                     help="run the Sec. 5.2 cost comparison (super-critical benchmark) instead")
     ap.add_argument("--paper-T", type=float, default=250.0)
+    ap.add_argument("--workloads", action="store_true",
+                    help="measure the 128^2 fixed-step, 512^2 all-scheme and 1024^2/2048^2 runs instead")
+    ap.add_argument("--workload-t2", type=float, default=50.0)
+    ap.add_argument("--workload-t3", type=float, default=10.0)
+    ap.add_argument("--workload-budget", type=int, default=400000)
+    ap.add_argument("--ensemble", action="store_true",
+                    help="the 64-instance uneven-grid ensemble against sequential runs instead")
+    ap.add_argument("--ensemble-t", type=float, default=0.02)
+    ap.add_argument("--ensemble-rounds", type=int, default=8)
+    ap.add_argument("--error-budget", action="store_true",
+                    help="per-field single/double-float vs FP64 errors at 1024^2 and 2048^2 instead")
+    ap.add_argument("--budget-steps", type=int, default=200)
+    ap.add_argument("--budget-dt", type=float, default=1e-6)
     args = ap.parse_args()
     if args.paper_costs:
         out = paper_costs(args)
+    elif args.workloads:
+        out = workloads(args)
+    elif args.error_budget:
+        out = error_budget(args)
+    elif args.ensemble:
+        out = ensemble_bench(args)
     else:
         out = run_reference(args) if args.impl == "reference" else run_gb300(args)
     if out is not None:

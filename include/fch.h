@@ -87,6 +87,15 @@ typedef struct {
     int sync_every;      /* adaptive runs: trial steps enqueued between host checks */
     int fft_path;        /* 0: automatic; 1: shared-memory Stockham passes for every N;
                           * 2: warp-transform passes where available (FCH_MIXED, N = 1024) */
+    int autotune;        /* 1: fch_create takes the tiles fch_autotune picks for (n, prec)
+                          * (timing them on first use in the process); 0: tile_row/tile_col */
+    int tile_row, tile_col; /* pass tiles: 0 default (warp-level passes where they exist,
+                          * else the kernel built for the grid size); -1 the shared-memory
+                          * kernels without the warp-level passes; r > 0 the generic row
+                          * kernel with r rows per block / the generic column kernel with
+                          * r column pairs per block (powers of two that fit the row
+                          * kernel's 256 threads or the column kernel's 1024 threads a
+                          * block and a block's shared memory; else FCH_EINVAL) */
 } fch_params;
 
 typedef struct {
@@ -198,15 +207,73 @@ fch_status fch_adaptive_end(fch_ctx *ctx, fch_stats *stats);
 fch_status fch_pass_timing(fch_ctx *ctx, int on);
 fch_status fch_pass_times(fch_ctx *ctx, double *ms, long long *launches, int n);
 
+/* ---- ensembles of independent instances ----
+ * The paper integrates one instance at a time; an ensemble advances m independent
+ * contexts (each its own grid size, parameters and initial data) together, for
+ * parameter sweeps and seeds. fch_ensemble_create makes m contexts as fch_create
+ * would (grids[i], params[i]), each on a stream of its own; the graphs of
+ * fch_ensemble_run_adaptive launch on `stream` (NULL: one the ensemble creates).
+ * The ensemble owns the members: use fch_ensemble_member to reach member i through
+ * the single-instance API (set_state, get_state, energy, mass, stats, ...), never
+ * fch_destroy it. Errors: FCH_EINVAL (m outside [1, FCH_ENSEMBLE_MAX], NULL
+ * arrays), a member's fch_create status (message in fch_last_cuda_error(NULL)).
+ *
+ * fch_ensemble_run_adaptive runs the adaptive algorithm of Sec. 3.2 on every
+ * member, from its current state, to t_final at the same sigma_tol: each member
+ * begins as fch_adaptive_begin and takes one trial on its own stream; then one CUDA
+ * graph, holding `rounds` trials of every member as one branch per member (the
+ * branches run concurrently), is launched until every member has reached t_final,
+ * or a member has failed, or max_launches launches (> 0) have run (FCH_ETIMEOUT).
+ * A member that has reached t_final skips its passes in later launches. stats
+ * (m entries, may be NULL) receive every member's fch_stats. Schemes: FCH_IMEX,
+ * FCH_SAV, FCH_ETD (PSD's convergence test runs on the host: FCH_EINVAL). Members
+ * with per-pass timing on: FCH_ESTATE. Returns after the members' streams are idle. */
+typedef struct fch_ensemble fch_ensemble;
+#define FCH_ENSEMBLE_MAX 4096
+fch_status fch_ensemble_create(int m, const fch_grid *grids, const fch_params *params, void *stream,
+                               fch_ensemble **out);
+fch_status fch_ensemble_destroy(fch_ensemble *e);
+fch_status fch_ensemble_member(fch_ensemble *e, int i, fch_ctx **ctx);
+fch_status fch_ensemble_run_adaptive(fch_ensemble *e, fch_scheme scheme, double sigma, double t_final, int rounds,
+                                     long long max_launches, fch_stats *stats);
+
+/* ---- pass tiles (the paper has no counterpart: a GPU launch choice) ----
+ * fch_autotune times the forward row pass (two real fields -> pair-layout work
+ * array) and the forward column pass (work array -> two half spectra) of one field
+ * pair at n x n in precision prec, for each candidate tile: the default, the
+ * shared-memory kernels where the default is the warp-level path (FCH_MIXED,
+ * n = 1024), and the generic kernels at 1, 2, 4, 8, 16 rows (column pairs) per
+ * block that fit. It allocates and frees its own scratch arrays on the given
+ * stream (NULL: the legacy default stream), synchronizes it, and keeps the fastest
+ * tiles per (n, prec) for the process: later calls return them without timing,
+ * contexts created with params.autotune = 1 and plans created afterwards use them.
+ * Tiles change launch shapes only; every tile computes the same transform (results
+ * may differ in rounding where the warp-level and shared-memory paths differ).
+ * Errors: FCH_EINVAL (n not a power of two in [16, 2048], prec not 0..2, out NULL),
+ * FCH_ECUDA (reason in fch_last_cuda_error(NULL)). fch_autotune_reset forgets the
+ * kept choices. */
+typedef struct {
+    int tile_row, tile_col;               /* chosen tiles (meaning as in fch_params) */
+    double row_us, col_us;                /* mean time of one launch with them */
+    double row_default_us, col_default_us; /* the same with the default tiles */
+    int candidates;                       /* tiles timed */
+} fch_tile;
+fch_status fch_autotune(int n, int prec, void *stream, fch_tile *out);
+fch_status fch_autotune_reset(void);
+
 /* ---- standalone 2D real transforms (the paper's cost unit, Sec. 1) ---- */
 
 /* Plan for N x N real transforms in precision prec on the given stream (NULL:
- * the legacy default stream). Allocates one N x N complex work array. */
+ * the legacy default stream). Allocates a work array of c N x N complex elements,
+ * c = min(64, max(1, 64 MiB / (N^2 x element size))): the field pairs one launch
+ * transforms. The plan must not be used from two streams at once. */
 fch_status fch_fft_plan_create(int n, int prec, void *stream, fch_fft_plan **out);
 fch_status fch_fft_plan_destroy(fch_fft_plan *plan);
 
 /* batch real fields x[b][N][N] -> half spectra X[b][N/2+1][N] (layout above);
- * elements are double (FCH_FP64) or float (FCH_MIXED). Enqueued, no wait. */
+ * elements are double (FCH_FP64) or float (FCH_MIXED). Fields 2j, 2j+1 share one
+ * complex transform; up to c such pairs go in one row and one column launch (the
+ * odd last field alone). Enqueued, no wait. */
 fch_status fch_fft_r2c(fch_fft_plan *plan, const void *x_dev, void *X_dev, int batch);
 
 /* inverse of fch_fft_r2c (divides by N^2); X is not modified. */

@@ -2,6 +2,7 @@
 // driver, the control kernel (FP64 reductions and the step-size controller) and
 // the standalone transforms. The C ABI is declared in include/fch.h.
 #include <math.h>
+#include <mutex>
 #include <stdio.h>
 #include <stdlib.h>
 #include <string.h>
@@ -36,6 +37,49 @@ fch_geom fch_geometry(int N, int prec)
     g.row_blocks = N / rpb;
     g.row_smem = (N + rpb * SL) * csz;
     return g;
+}
+
+fch_geom fch_geometry_tiled(int N, int prec, int tile_row, int tile_col)
+{
+    fch_geom g = fch_geometry(N, prec);
+    const int csz = prec == 1 ? 8 : 16, SL = N + N / 8;
+    if (tile_col > 0) {
+        g.P = tile_col;
+        g.col_threads = tile_col * N / 4;
+        g.col_blocks = N / (2 * tile_col);
+        g.col_smem = (N + 2 * tile_col * SL) * csz;
+    }
+    if (tile_row > 0) {
+        g.rpb = tile_row;
+        g.row_threads = tile_row * (N / 8);
+        g.row_blocks = N / tile_row;
+        g.row_smem = (N + tile_row * SL) * csz;
+    }
+    return g;
+}
+
+// generic-kernel tiles: powers of two, whole blocks, at most 256 threads for the row
+// kernel (its launch bound) and 1024 for the column kernel, and the opt-in shared
+// memory of a block (227 KiB, less the kernels' 1 KiB of static arrays)
+bool fch_tile_valid(int N, int prec, int tile_row, int tile_col)
+{
+    const int smem_max = 227 * 1024 - 1024;
+    const int pmin = prec == 1 ? 2 : 1;
+    if (tile_row > 0) {
+        if ((tile_row & (tile_row - 1)) || tile_row > N) return false;
+        const fch_geom g = fch_geometry_tiled(N, prec, tile_row, 0);
+        if (g.row_threads > 256 || g.row_smem > smem_max) return false;
+    } else if (tile_row < -1) {
+        return false;
+    }
+    if (tile_col > 0) {
+        if ((tile_col & (tile_col - 1)) || tile_col < pmin || tile_col > N / 2) return false;
+        const fch_geom g = fch_geometry_tiled(N, prec, 0, tile_col);
+        if (g.col_threads > 1024 || g.col_smem > smem_max) return false;
+    } else if (tile_col < -1) {
+        return false;
+    }
+    return true;
 }
 
 // ---------------------------------------------------------------------------
@@ -480,7 +524,8 @@ extern "C" fch_status fch_create(const fch_grid *g, const fch_params *p, void *s
     if (!g || !p || !out) return FCH_EINVAL;
     *out = nullptr;
     if (!pow2_in_range(g->n) || !(g->L > 0) || !(p->eps > 0) || p->prec < 0 || p->prec > 2 ||
-        p->fft_path < 0 || p->fft_path > 2 ||
+        p->fft_path < 0 || p->fft_path > 2 || p->autotune < 0 || p->autotune > 1 ||
+        !fch_tile_valid(g->n, p->prec == FCH_MIXED, p->tile_row, p->tile_col) ||
         !(p->k_min > 0) || !(p->rho_s > 0) || p->psd_max_iter < 1)
         return FCH_EINVAL;
     fch_ctx *ctx = (fch_ctx *)calloc(1, sizeof(fch_ctx));
@@ -496,7 +541,6 @@ extern "C" fch_status fch_create(const fch_grid *g, const fch_params *p, void *s
         if (ctx->p.zeta <= 0) ctx->p.zeta = z;
         if (ctx->p.D0 <= 0) ctx->p.D0 = d;
     }
-    ctx->geom = fch_geometry(ctx->N, ctx->prec == FCH_MIXED);
     const int N = ctx->N;
     const size_t csz = ctx->prec == FCH_MIXED ? 8 : 16;
     const size_t hs = (size_t)(N / 2 + 1) * N * csz;
@@ -507,6 +551,19 @@ extern "C" fch_status fch_create(const fch_grid *g, const fch_params *p, void *s
         e = cudaStreamCreateWithFlags(&ctx->stream, cudaStreamNonBlocking);
         ctx->own_stream = true;
     }
+    int trow = p->tile_row, tcol = p->tile_col;
+    if (e == cudaSuccess && p->autotune) {
+        fch_tile t;
+        const fch_status ts = fch_autotune(N, ctx->prec, ctx->stream, &t);
+        if (ts != FCH_OK) {
+            snprintf(ctx->errbuf, sizeof(ctx->errbuf), "fch_create: autotune: %.200s", g_plan_err);
+            fch_destroy(ctx);
+            return ts;
+        }
+        trow = t.tile_row;
+        tcol = t.tile_col;
+    }
+    ctx->geom = fch_geometry_tiled(N, ctx->prec == FCH_MIXED, trow, tcol);
     void **bufs[] = {&ctx->U[0], &ctx->U[1], &ctx->U[2], &ctx->F[0], &ctx->F[1], &ctx->F[2],
                      &ctx->Pb, &ctx->Qb, &ctx->Vb, &ctx->Nb};
     for (void **b : bufs)
@@ -528,6 +585,8 @@ extern "C" fch_status fch_create(const fch_grid *g, const fch_params *p, void *s
     }
     fill_kparams_model(ctx->kp, ctx->p, N, g->L);
     ctx->kp.P = ctx->geom.P;
+    ctx->kp.tile_row = trow;
+    ctx->kp.tile_col = tcol;
     for (int i = 0; i < 3; i++) {
         ctx->kp.U[i] = ctx->U[i];
         ctx->kp.F[i] = ctx->F[i];
@@ -940,6 +999,217 @@ extern "C" fch_status fch_run_adaptive(fch_ctx *ctx, fch_scheme scheme, double s
     return e != FCH_OK ? e : result;
 }
 
+// ---------------------------------------------------------------------------
+// ensembles: independent instances advanced together by one CUDA graph whose
+// branches (one per member, each on its own stream) hold `rounds` adaptive trials
+// of that member; branches of different members run concurrently, so small grids
+// fill the GPU together. Members are ordinary contexts: their control blocks keep
+// every per-trial value on the device, and a finished member's passes return at once.
+
+struct fch_ensemble {
+    int m;
+    cudaStream_t stream; // the stream graphs launch on
+    bool own_stream;
+    fch_ctx **ctx;
+    cudaStream_t *mstream; // member streams (owned)
+    cudaEvent_t fork, *join;
+    fch_ctrl **dctrls;     // the members' control blocks (device array)
+    int *dflags, *hflags;  // per member: done | status << 1 (device, pinned host)
+    cudaGraphExec_t graph;
+    int graph_scheme, graph_rounds;
+};
+
+__global__ void fch_ensemble_flags_kernel(fch_ctrl *const *c, int m, int *out)
+{
+    for (int i = threadIdx.x; i < m; i += blockDim.x) out[i] = c[i]->done | (c[i]->status << 1);
+}
+
+extern "C" fch_status fch_ensemble_destroy(fch_ensemble *e)
+{
+    if (!e) return FCH_OK;
+    if (e->stream) cudaStreamSynchronize(e->stream);
+    if (e->graph) cudaGraphExecDestroy(e->graph);
+    for (int i = 0; i < e->m; i++) {
+        if (e->ctx && e->ctx[i]) fch_destroy(e->ctx[i]);
+        if (e->mstream && e->mstream[i]) cudaStreamDestroy(e->mstream[i]);
+        if (e->join && e->join[i]) cudaEventDestroy(e->join[i]);
+    }
+    if (e->fork) cudaEventDestroy(e->fork);
+    if (e->dctrls) cudaFree(e->dctrls);
+    if (e->dflags) cudaFree(e->dflags);
+    if (e->hflags) cudaFreeHost(e->hflags);
+    if (e->own_stream && e->stream) cudaStreamDestroy(e->stream);
+    free(e->ctx);
+    free(e->mstream);
+    free(e->join);
+    free(e);
+    return FCH_OK;
+}
+
+extern "C" fch_status fch_ensemble_create(int m, const fch_grid *grids, const fch_params *params, void *stream,
+                                          fch_ensemble **out)
+{
+    if (!out || !grids || !params || m < 1 || m > FCH_ENSEMBLE_MAX) {
+        fch_set_thread_error("fch_ensemble_create: invalid argument");
+        return FCH_EINVAL;
+    }
+    *out = nullptr;
+    fch_ensemble *e = (fch_ensemble *)calloc(1, sizeof(fch_ensemble));
+    if (!e) return FCH_ENOMEM;
+    e->m = m;
+    e->graph_scheme = -1;
+    e->ctx = (fch_ctx **)calloc(m, sizeof(fch_ctx *));
+    e->mstream = (cudaStream_t *)calloc(m, sizeof(cudaStream_t));
+    e->join = (cudaEvent_t *)calloc(m, sizeof(cudaEvent_t));
+    if (!e->ctx || !e->mstream || !e->join) {
+        fch_ensemble_destroy(e);
+        return FCH_ENOMEM;
+    }
+    cudaError_t ce = cudaSuccess;
+    if (stream) {
+        e->stream = (cudaStream_t)stream;
+    } else {
+        ce = cudaStreamCreateWithFlags(&e->stream, cudaStreamNonBlocking);
+        e->own_stream = true;
+    }
+    if (ce == cudaSuccess) ce = cudaEventCreateWithFlags(&e->fork, cudaEventDisableTiming);
+    for (int i = 0; i < m && ce == cudaSuccess; i++) {
+        ce = cudaStreamCreateWithFlags(&e->mstream[i], cudaStreamNonBlocking);
+        if (ce == cudaSuccess) ce = cudaEventCreateWithFlags(&e->join[i], cudaEventDisableTiming);
+    }
+    if (ce == cudaSuccess) ce = cudaMalloc((void **)&e->dctrls, m * sizeof(fch_ctrl *));
+    if (ce == cudaSuccess) ce = cudaMalloc((void **)&e->dflags, m * sizeof(int));
+    if (ce == cudaSuccess) ce = cudaMallocHost((void **)&e->hflags, m * sizeof(int));
+    if (ce != cudaSuccess) {
+        snprintf(g_plan_err, sizeof(g_plan_err), "fch_ensemble_create: %s", cudaGetErrorString(ce));
+        fch_ensemble_destroy(e);
+        return ce == cudaErrorMemoryAllocation ? FCH_ENOMEM : FCH_ECUDA;
+    }
+    fch_ctrl **hc = (fch_ctrl **)malloc(m * sizeof(fch_ctrl *));
+    if (!hc) {
+        fch_ensemble_destroy(e);
+        return FCH_ENOMEM;
+    }
+    for (int i = 0; i < m; i++) {
+        const fch_status s = fch_create(&grids[i], &params[i], e->mstream[i], &e->ctx[i]);
+        if (s != FCH_OK) {
+            snprintf(g_plan_err, sizeof(g_plan_err), "fch_ensemble_create: member %d: %s", i,
+                     fch_status_string(s));
+            free(hc);
+            fch_ensemble_destroy(e);
+            return s;
+        }
+        hc[i] = e->ctx[i]->dctrl;
+    }
+    ce = cudaMemcpy(e->dctrls, hc, m * sizeof(fch_ctrl *), cudaMemcpyHostToDevice);
+    free(hc);
+    if (ce != cudaSuccess) {
+        fch_ensemble_destroy(e);
+        return FCH_ECUDA;
+    }
+    *out = e;
+    return FCH_OK;
+}
+
+extern "C" fch_status fch_ensemble_member(fch_ensemble *e, int i, fch_ctx **ctx)
+{
+    if (!e || !ctx || i < 0 || i >= e->m) return FCH_EINVAL;
+    *ctx = e->ctx[i];
+    return FCH_OK;
+}
+
+// capture the ensemble graph: fork from e->stream to every member stream, `rounds`
+// trials per member, join back, then gather the members' flags to pinned memory
+static fch_status ensemble_capture(fch_ensemble *e, int scheme, int rounds)
+{
+    if (e->graph && e->graph_scheme == scheme && e->graph_rounds == rounds) return FCH_OK;
+    if (e->graph) {
+        cudaGraphExecDestroy(e->graph);
+        e->graph = nullptr;
+    }
+    cudaError_t ce = cudaStreamBeginCapture(e->stream, cudaStreamCaptureModeRelaxed);
+    if (ce != cudaSuccess) return FCH_ECUDA;
+    fch_status s = FCH_OK;
+    if (cudaEventRecord(e->fork, e->stream) != cudaSuccess) s = FCH_ECUDA;
+    for (int i = 0; i < e->m && s == FCH_OK; i++) {
+        fch_ctx *c = e->ctx[i];
+        if (cudaStreamWaitEvent(c->stream, e->fork, 0) != cudaSuccess) s = FCH_ECUDA;
+        for (int r = 0; r < rounds && s == FCH_OK; r++) s = enqueue_adaptive_trial(c);
+        if (s == FCH_OK && cudaEventRecord(e->join[i], c->stream) != cudaSuccess) s = FCH_ECUDA;
+        if (s == FCH_OK && cudaStreamWaitEvent(e->stream, e->join[i], 0) != cudaSuccess) s = FCH_ECUDA;
+    }
+    if (s == FCH_OK) {
+        fch_ensemble_flags_kernel<<<1, 256, 0, e->stream>>>(e->dctrls, e->m, e->dflags);
+        if (cudaGetLastError() != cudaSuccess ||
+            cudaMemcpyAsync(e->hflags, e->dflags, e->m * sizeof(int), cudaMemcpyDeviceToHost, e->stream) !=
+                cudaSuccess)
+            s = FCH_ECUDA;
+    }
+    cudaGraph_t g = nullptr;
+    ce = cudaStreamEndCapture(e->stream, &g);
+    if (s == FCH_OK && (ce != cudaSuccess || !g)) s = FCH_ECUDA;
+    if (s == FCH_OK && cudaGraphInstantiate(&e->graph, g, 0) != cudaSuccess) {
+        e->graph = nullptr;
+        s = FCH_ECUDA;
+    }
+    if (g) cudaGraphDestroy(g);
+    if (s != FCH_OK) {
+        cudaGetLastError();
+        return s;
+    }
+    e->graph_scheme = scheme;
+    e->graph_rounds = rounds;
+    return FCH_OK;
+}
+
+extern "C" fch_status fch_ensemble_run_adaptive(fch_ensemble *e, fch_scheme scheme, double sigma, double t_final,
+                                                int rounds, long long max_launches, fch_stats *stats)
+{
+    if (!e || !(sigma > 0) || rounds < 1 || rounds > 1024 || max_launches < 0 ||
+        (scheme != FCH_IMEX && scheme != FCH_SAV && scheme != FCH_ETD))
+        return FCH_EINVAL;
+    for (int i = 0; i < e->m; i++)
+        if (e->ctx[i]->timing) return FCH_ESTATE;
+    // every member begins (host checks, backward-Euler start) and runs one trial
+    // on its own stream; the first trial also sets the kernels' attributes
+    for (int i = 0; i < e->m; i++) {
+        TRY(fch_adaptive_begin(e->ctx[i], scheme, sigma, t_final));
+        TRY(fch_adaptive_enqueue(e->ctx[i], 1));
+        if (cudaEventRecord(e->join[i], e->ctx[i]->stream) != cudaSuccess ||
+            cudaStreamWaitEvent(e->stream, e->join[i], 0) != cudaSuccess)
+            return FCH_ECUDA;
+    }
+    fch_status result = ensemble_capture(e, scheme, rounds);
+    if (result != FCH_OK) {
+        for (int i = 0; i < e->m; i++) fch_adaptive_end(e->ctx[i], nullptr);
+        return result;
+    }
+    for (long long l = 0;; l++) {
+        if (max_launches > 0 && l >= max_launches) {
+            result = FCH_ETIMEOUT;
+            break;
+        }
+        if (cudaGraphLaunch(e->graph, e->stream) != cudaSuccess || cudaStreamSynchronize(e->stream) != cudaSuccess) {
+            result = FCH_ECUDA;
+            break;
+        }
+        bool all_done = true;
+        for (int i = 0; i < e->m; i++) {
+            all_done = all_done && (e->hflags[i] & 1);
+            if ((e->hflags[i] >> 1) && result == FCH_OK) result = (fch_status)(e->hflags[i] >> 1);
+        }
+        if (all_done || result != FCH_OK) break;
+    }
+    // the members' own streams follow the graph's work before their next calls
+    if (cudaEventRecord(e->fork, e->stream) != cudaSuccess) return FCH_ECUDA;
+    for (int i = 0; i < e->m; i++) {
+        if (cudaStreamWaitEvent(e->ctx[i]->stream, e->fork, 0) != cudaSuccess) return FCH_ECUDA;
+        const fch_status s = fch_adaptive_end(e->ctx[i], stats ? &stats[i] : nullptr);
+        if (s != FCH_OK && result == FCH_OK) result = s;
+    }
+    return result;
+}
+
 extern "C" fch_status fch_pass_timing(fch_ctx *ctx, int on)
 {
     if (!ctx) return FCH_EINVAL;
@@ -1041,13 +1311,171 @@ extern "C" fch_status fch_get_sav_r(fch_ctx *ctx, double *r_n, double *r_nm1)
 
 // ---------------------------------------------------------------------------
 // standalone transforms
+// ---------------------------------------------------------------------------
+// autotuner of the pass tiles
+
+static std::mutex g_tune_mutex;
+static fch_tile g_tune[3][12];
+static bool g_tune_ok[3][12];
+
+// the tiles fch_autotune chose for (n, prec) in this process, if it ran
+static bool tuned_tiles(int n, int prec, int *row, int *col)
+{
+    std::lock_guard<std::mutex> lock(g_tune_mutex);
+    const int l = ilog2(n);
+    if (prec < 0 || prec > 2 || l < 0 || l >= 12 || !g_tune_ok[prec][l]) return false;
+    *row = g_tune[prec][l].tile_row;
+    *col = g_tune[prec][l].tile_col;
+    return true;
+}
+
+// Mean time (us) of `reps` launches of one pass after two untimed ones.
+template <typename F> static cudaError_t time_pass(F launch, cudaStream_t s, int reps, double *us)
+{
+    cudaEvent_t a = nullptr, b = nullptr;
+    cudaError_t e = cudaEventCreate(&a);
+    if (e == cudaSuccess) e = cudaEventCreate(&b);
+    for (int i = 0; i < 2 && e == cudaSuccess; i++) e = launch();
+    if (e == cudaSuccess) e = cudaEventRecord(a, s);
+    for (int i = 0; i < reps && e == cudaSuccess; i++) e = launch();
+    if (e == cudaSuccess) e = cudaEventRecord(b, s);
+    if (e == cudaSuccess) e = cudaEventSynchronize(b);
+    float ms = 0.f;
+    if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, a, b);
+    if (a) cudaEventDestroy(a);
+    if (b) cudaEventDestroy(b);
+    *us = 1e3 * ms / reps;
+    return e;
+}
+
+extern "C" fch_status fch_autotune(int n, int prec, void *stream, fch_tile *out)
+{
+    if (!out || !pow2_in_range(n) || prec < 0 || prec > 2) {
+        fch_set_thread_error("fch_autotune: invalid argument");
+        return FCH_EINVAL;
+    }
+    {
+        std::lock_guard<std::mutex> lock(g_tune_mutex);
+        if (g_tune_ok[prec][ilog2(n)]) {
+            *out = g_tune[prec][ilog2(n)];
+            return FCH_OK;
+        }
+    }
+    cudaStream_t s = (cudaStream_t)stream;
+    const bool single = prec == FCH_MIXED;
+    const size_t csz = single ? 8 : 16, rsz = single ? 4 : 8;
+    void *x = nullptr, *Z = nullptr, *X = nullptr, *tw = nullptr, *tw2 = nullptr;
+    cudaError_t e = cudaMalloc(&x, 2 * (size_t)n * n * rsz);
+    if (e == cudaSuccess) e = cudaMalloc(&Z, (size_t)n * n * csz);
+    if (e == cudaSuccess) e = cudaMalloc(&X, 2 * (size_t)(n / 2 + 1) * n * csz);
+    if (e == cudaSuccess) e = cudaMalloc(&tw, (size_t)n * csz);
+    if (e == cudaSuccess) e = cudaMemsetAsync(x, 0, 2 * (size_t)n * n * rsz, s);
+    fch_ctx dummy;
+    if (e == cudaSuccess && upload_twiddles(&dummy, n, prec, tw, s) != FCH_OK) e = cudaErrorUnknown;
+    if (e == cudaSuccess && single && n == 1024) e = upload_tw2(&tw2, s);
+    fch_kparams kp;
+    memset(&kp, 0, sizeof(kp));
+    kp.N = n;
+    kp.logN = ilog2(n);
+    kp.inv_n2 = 1.0 / ((double)n * n);
+    kp.Z = Z;
+    kp.tw = tw;
+    kp.tw2 = tw2;
+    kp.tail_op = -1;
+    kp.flags = FCH_FL_NOSKIP | (single ? 0 : FCH_FL_F64IO);
+    kp.in0 = x;
+    kp.in1 = (const char *)x + (size_t)n * n * rsz;
+    kp.out0 = X;
+    kp.out1 = (char *)X + (size_t)(n / 2 + 1) * n * csz;
+    auto launch = [&](bool is_col, const fch_kparams &k) {
+        if (is_col)
+            return prec == FCH_MIXED    ? fch_launch_col_f32(CM_FWD_STORE, k, s)
+                   : prec == FCH_FP32X2 ? fch_launch_col_dfl(CM_FWD_STORE, k, s)
+                                        : fch_launch_col_f64(CM_FWD_STORE, k, s);
+        return prec == FCH_MIXED    ? fch_launch_row_f32(RM_R2C_LOAD, k, s)
+               : prec == FCH_FP32X2 ? fch_launch_row_dfl(RM_R2C_LOAD, k, s)
+                                    : fch_launch_row_f64(RM_R2C_LOAD, k, s);
+    };
+    // candidates: the default tiles (timed first), the shared-memory kernels where the
+    // default is the warp-level path, and the generic kernel at 1..16 rows (column
+    // pairs) a block; another tile replaces the default only if 3 % faster
+    fch_tile best;
+    memset(&best, 0, sizeof(best));
+    const int reps = n >= 1024 ? 10 : 20;
+    for (int is_col = 0; is_col < 2 && e == cudaSuccess; is_col++) {
+        double best_us = 1e30, def_us = 0;
+        int best_t = 0;
+        const int cands[] = {0, -1, 1, 2, 4, 8, 16};
+        for (int c : cands) {
+            if (c == -1 && !(single && n == 1024)) continue;
+            if (!fch_tile_valid(n, single, is_col ? 0 : c, is_col ? c : 0)) continue;
+            fch_kparams k = kp;
+            k.tile_row = is_col ? 0 : c;
+            k.tile_col = is_col ? c : 0;
+            k.P = fch_geometry_tiled(n, single, 0, k.tile_col).P;
+            double us = 0;
+            e = time_pass([&] { return launch(is_col != 0, k); }, s, reps, &us);
+            if (e != cudaSuccess) break;
+            best.candidates++;
+            if (c == 0) {
+                def_us = us;
+                best_us = us;
+            } else if (us < best_us && us < 0.97 * def_us) { // the default unless 3 % faster
+                best_us = us;
+                best_t = c;
+            }
+        }
+        if (is_col) {
+            best.tile_col = best_t;
+            best.col_us = best_us;
+            best.col_default_us = def_us;
+        } else {
+            best.tile_row = best_t;
+            best.row_us = best_us;
+            best.row_default_us = def_us;
+        }
+    }
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    for (void *b : {x, Z, X, tw, tw2})
+        if (b) cudaFree(b);
+    if (e != cudaSuccess) {
+        snprintf(g_plan_err, sizeof(g_plan_err), "fch_autotune: %s", cudaGetErrorString(e));
+        return FCH_ECUDA;
+    }
+    std::lock_guard<std::mutex> lock(g_tune_mutex);
+    g_tune[prec][ilog2(n)] = best;
+    g_tune_ok[prec][ilog2(n)] = true;
+    *out = best;
+    return FCH_OK;
+}
+
+extern "C" fch_status fch_autotune_reset(void)
+{
+    std::lock_guard<std::mutex> lock(g_tune_mutex);
+    memset(g_tune_ok, 0, sizeof(g_tune_ok));
+    return FCH_OK;
+}
+
 struct fch_fft_plan {
     int N, prec;
+    int chunk; // field pairs transformed by one launch (the work array holds that many)
     cudaStream_t stream;
     fch_geom geom;
     fch_kparams kp;
     void *Z, *tw, *tw2;
 };
+
+// Field pairs per launch of a standalone transform: as many as a 64 MiB work array
+// holds (at most 64), so a batch runs as a few launches of many blocks rather than
+// one launch pair per two fields, and the work array stays in L2 between the passes.
+static int plan_chunk(int n, int prec)
+{
+    const size_t per = (size_t)n * n * (prec ? 8 : 16);
+    size_t c = ((size_t)64 << 20) / per;
+    if (c < 1) c = 1;
+    if (c > 64) c = 64;
+    return (int)c;
+}
 
 extern "C" fch_status fch_fft_plan_create(int n, int prec, void *stream, fch_fft_plan **out)
 {
@@ -1057,9 +1485,12 @@ extern "C" fch_status fch_fft_plan_create(int n, int prec, void *stream, fch_fft
     pl->N = n;
     pl->prec = prec;
     pl->stream = (cudaStream_t)stream;
-    pl->geom = fch_geometry(n, prec);
+    int trow = 0, tcol = 0;
+    tuned_tiles(n, prec, &trow, &tcol);
+    pl->geom = fch_geometry_tiled(n, prec, trow, tcol);
+    pl->chunk = plan_chunk(n, prec);
     const size_t csz = prec ? 8 : 16;
-    cudaError_t e = cudaMalloc(&pl->Z, (size_t)n * n * csz);
+    cudaError_t e = cudaMalloc(&pl->Z, (size_t)pl->chunk * n * n * csz);
     if (e == cudaSuccess) e = cudaMalloc(&pl->tw, (size_t)n * csz);
     if (e != cudaSuccess) {
         fch_fft_plan_destroy(pl);
@@ -1074,6 +1505,8 @@ extern "C" fch_status fch_fft_plan_create(int n, int prec, void *stream, fch_fft
     pl->kp.N = n;
     pl->kp.logN = ilog2(n);
     pl->kp.P = pl->geom.P;
+    pl->kp.tile_row = trow;
+    pl->kp.tile_col = tcol;
     pl->kp.inv_n2 = 1.0 / ((double)n * n);
     pl->kp.tail_op = -1;
     pl->kp.cf.inv_n2 = (float)pl->kp.inv_n2;
@@ -1102,7 +1535,7 @@ extern "C" fch_status fch_fft_plan_destroy(fch_fft_plan *pl)
 }
 
 static cudaError_t plan_pass(fch_fft_plan *pl, bool is_col, int mode, const void *in0, const void *in1,
-                             void *out0, void *out1)
+                             void *out0, void *out1, int npairs, long long pstride_in, long long pstride_out)
 {
     fch_kparams kp = pl->kp;
     kp.flags = FCH_FL_NOSKIP | (pl->prec ? 0 : FCH_FL_F64IO);
@@ -1110,6 +1543,9 @@ static cudaError_t plan_pass(fch_fft_plan *pl, bool is_col, int mode, const void
     kp.in1 = in1;
     kp.out0 = out0;
     kp.out1 = out1;
+    kp.npairs = npairs;
+    kp.pstride_in = pstride_in;
+    kp.pstride_out = pstride_out;
     cudaError_t e;
     if (is_col)
         e = pl->prec ? fch_launch_col_f32(mode, kp, pl->stream) : fch_launch_col_f64(mode, kp, pl->stream);
@@ -1121,17 +1557,30 @@ static cudaError_t plan_pass(fch_fft_plan *pl, bool is_col, int mode, const void
     return e;
 }
 
+// Fields 2j and 2j+1 form pair j (one complex transform); pairs go chunk at a time,
+// each chunk as one row and one column launch with a grid row per pair; an odd last
+// field is a pair of its own with no second field.
 extern "C" fch_status fch_fft_r2c(fch_fft_plan *pl, const void *x, void *X, int batch)
 {
     if (!pl || !x || !X || batch < 0) return FCH_EINVAL;
-    const size_t N = pl->N, rb = N * N * (pl->prec ? 4 : 8), cb = (N / 2 + 1) * N * (pl->prec ? 8 : 16);
-    for (int b = 0; b < batch; b += 2) {
-        const char *x0 = (const char *)x + b * rb;
-        const char *x1 = b + 1 < batch ? x0 + rb : nullptr;
-        char *X0 = (char *)X + b * cb;
-        char *X1 = b + 1 < batch ? X0 + cb : nullptr;
-        if (plan_pass(pl, false, RM_R2C_LOAD, x0, x1, nullptr, nullptr) != cudaSuccess) return FCH_ECUDA;
-        if (plan_pass(pl, true, CM_FWD_STORE, nullptr, nullptr, X0, X1) != cudaSuccess) return FCH_ECUDA;
+    const long long N = pl->N, rb = N * N * (pl->prec ? 4 : 8), cb = (N / 2 + 1) * N * (pl->prec ? 8 : 16);
+    const int full = batch / 2;
+    for (int j = 0; j < full; j += pl->chunk) {
+        const int np = full - j < pl->chunk ? full - j : pl->chunk;
+        const char *x0 = (const char *)x + 2 * j * rb;
+        char *X0 = (char *)X + 2 * j * cb;
+        if (plan_pass(pl, false, RM_R2C_LOAD, x0, x0 + rb, nullptr, nullptr, np, 2 * rb, 0) != cudaSuccess)
+            return FCH_ECUDA;
+        if (plan_pass(pl, true, CM_FWD_STORE, nullptr, nullptr, X0, X0 + cb, np, 0, 2 * cb) != cudaSuccess)
+            return FCH_ECUDA;
+    }
+    if (batch & 1) {
+        const char *x0 = (const char *)x + (batch - 1) * rb;
+        char *X0 = (char *)X + (batch - 1) * cb;
+        if (plan_pass(pl, false, RM_R2C_LOAD, x0, nullptr, nullptr, nullptr, 1, 0, 0) != cudaSuccess)
+            return FCH_ECUDA;
+        if (plan_pass(pl, true, CM_FWD_STORE, nullptr, nullptr, X0, nullptr, 1, 0, 0) != cudaSuccess)
+            return FCH_ECUDA;
     }
     return FCH_OK;
 }
@@ -1139,16 +1588,43 @@ extern "C" fch_status fch_fft_r2c(fch_fft_plan *pl, const void *x, void *X, int 
 extern "C" fch_status fch_fft_c2r(fch_fft_plan *pl, const void *X, void *x, int batch)
 {
     if (!pl || !x || !X || batch < 0) return FCH_EINVAL;
-    const size_t N = pl->N, rb = N * N * (pl->prec ? 4 : 8), cb = (N / 2 + 1) * N * (pl->prec ? 8 : 16);
-    for (int b = 0; b < batch; b += 2) {
-        const char *X0 = (const char *)X + b * cb;
-        const char *X1 = b + 1 < batch ? X0 + cb : nullptr;
-        char *x0 = (char *)x + b * rb;
-        char *x1 = b + 1 < batch ? x0 + rb : nullptr;
-        if (plan_pass(pl, true, CM_INV_LOAD, X0, X1, nullptr, nullptr) != cudaSuccess) return FCH_ECUDA;
-        if (plan_pass(pl, false, RM_C2R_STORE, nullptr, nullptr, x0, x1) != cudaSuccess) return FCH_ECUDA;
+    const long long N = pl->N, rb = N * N * (pl->prec ? 4 : 8), cb = (N / 2 + 1) * N * (pl->prec ? 8 : 16);
+    const int full = batch / 2;
+    for (int j = 0; j < full; j += pl->chunk) {
+        const int np = full - j < pl->chunk ? full - j : pl->chunk;
+        const char *X0 = (const char *)X + 2 * j * cb;
+        char *x0 = (char *)x + 2 * j * rb;
+        if (plan_pass(pl, true, CM_INV_LOAD, X0, X0 + cb, nullptr, nullptr, np, 2 * cb, 0) != cudaSuccess)
+            return FCH_ECUDA;
+        if (plan_pass(pl, false, RM_C2R_STORE, nullptr, nullptr, x0, x0 + rb, np, 0, 2 * rb) != cudaSuccess)
+            return FCH_ECUDA;
+    }
+    if (batch & 1) {
+        const char *X0 = (const char *)X + (batch - 1) * cb;
+        char *x0 = (char *)x + (batch - 1) * rb;
+        if (plan_pass(pl, true, CM_INV_LOAD, X0, nullptr, nullptr, nullptr, 1, 0, 0) != cudaSuccess)
+            return FCH_ECUDA;
+        if (plan_pass(pl, false, RM_C2R_STORE, nullptr, nullptr, x0, nullptr, 1, 0, 0) != cudaSuccess)
+            return FCH_ECUDA;
     }
     return FCH_OK;
+}
+
+// host-side geometry of tiles row / col and whether they launch (CPU tests);
+// returns 1 valid, 0 invalid, -1 bad arguments
+extern "C" int fch_debug_tile(int n, int prec, int row, int col, int *out)
+{
+    if (!pow2_in_range(n) || !out || prec < 0 || prec > 2) return -1;
+    const fch_geom g = fch_geometry_tiled(n, prec, row, col);
+    out[0] = g.col_blocks;
+    out[1] = g.col_threads;
+    out[2] = g.col_smem;
+    out[3] = g.row_blocks;
+    out[4] = g.row_threads;
+    out[5] = g.row_smem;
+    out[6] = g.rpb;
+    out[7] = g.P;
+    return fch_tile_valid(n, prec, row, col) ? 1 : 0;
 }
 
 // host-side geometry query (used by the CPU tests of the launch configuration)

@@ -5,6 +5,7 @@
 // the partial sums.
 #pragma once
 #include <math.h>
+#include <stddef.h>
 #include "fch_internal.h"
 #include "../../include/fch.h"
 
@@ -198,42 +199,23 @@ __device__ inline bool ctrl_op(fch_ctrl *c, const fch_kparams &kp, int op, doubl
     return !c->done;
 }
 
-// float and double mirrors of the per-trial coefficients read by the passes
-__device__ inline void sync_coef(fch_ctrl *c)
+// Float, double and double-float mirrors of the per-trial coefficients read by
+// the passes, lane i of the calling warp converting coefficient i: conversions run
+// on the double pipe, where one warp instruction costs the same for eleven lanes as
+// for one, so the eleven conversions cost one instruction sequence instead of eleven.
+static_assert(offsetof(fch_ctrl, lam) == offsetof(fch_ctrl, a) + 7 * sizeof(double),
+              "a, b, c, gam, w1, w2, w3, lam are consecutive doubles");
+static_assert(sizeof(fch_coef<float>) == 11 * sizeof(float) && sizeof(fch_coef<double>) == 11 * sizeof(double) &&
+                  sizeof(fch_coef<fch::df>) == 11 * sizeof(fch::df),
+              "fch_coef is eleven coefficients in declaration order");
+__device__ inline void sync_coef_lanes(fch_ctrl *c, int lane)
 {
-    c->cod.a = c->a;
-    c->cod.b = c->b;
-    c->cod.c = c->c;
-    c->cod.gam = c->gam;
-    c->cod.w1 = c->w1;
-    c->cod.w2 = c->w2;
-    c->cod.w3 = c->w3;
-    c->cod.lam = c->lam;
-    c->cod.k1 = c->k1;
-    c->cod.r_new = c->r_new;
-    c->cod.isq = c->inv_sqrt_e1;
-    c->cof.a = (float)c->a;
-    c->cof.b = (float)c->b;
-    c->cof.c = (float)c->c;
-    c->cof.gam = (float)c->gam;
-    c->cof.w1 = (float)c->w1;
-    c->cof.w2 = (float)c->w2;
-    c->cof.w3 = (float)c->w3;
-    c->cof.lam = (float)c->lam;
-    c->cof.k1 = (float)c->k1;
-    c->cof.r_new = (float)c->r_new;
-    c->cof.isq = (float)c->inv_sqrt_e1;
-    c->codf.a = fch::df(c->a);
-    c->codf.b = fch::df(c->b);
-    c->codf.c = fch::df(c->c);
-    c->codf.gam = fch::df(c->gam);
-    c->codf.w1 = fch::df(c->w1);
-    c->codf.w2 = fch::df(c->w2);
-    c->codf.w3 = fch::df(c->w3);
-    c->codf.lam = fch::df(c->lam);
-    c->codf.k1 = fch::df(c->k1);
-    c->codf.r_new = fch::df(c->r_new);
-    c->codf.isq = fch::df(c->inv_sqrt_e1);
+    if (lane < 11) {
+        const double v = lane < 8 ? (&c->a)[lane] : lane == 8 ? c->k1 : lane == 9 ? c->r_new : c->inv_sqrt_e1;
+        ((float *)&c->cof)[lane] = (float)v;
+        ((double *)&c->cod)[lane] = v;
+        ((fch::df *)&c->codf)[lane] = fch::df(v);
+    }
 }
 
 
@@ -284,7 +266,10 @@ __device__ inline void ctrl_block(const fch_kparams &kp, int op, int na, double 
             op = OP_INIT_TRIAL;
             arg0 = -1.0;
         }
-        sync_coef(&cs);
+    }
+    if (threadIdx.x < 32) {
+        __syncwarp();
+        sync_coef_lanes(&cs, threadIdx.x);
     }
     __syncthreads();
     for (int i = threadIdx.x; i < nw; i += nthr) ((long long *)kp.ctrl)[i] = ((const long long *)&cs)[i];

@@ -77,6 +77,11 @@ struct fch_kparams {
     unsigned long long *nfft;       // 2D real-transform counter (may be null)
     const void *in0, *in1;          // explicit inputs (standalone transforms, device fields)
     void *out0, *out1;              // explicit outputs
+    int tile_row, tile_col;         // pass tiles: 0 default; -1 shared-memory kernel without the
+                                    // warp-level path; > 0 generic kernel with that many rows
+                                    // (column pairs) per block
+    int npairs;                     // standalone transforms: field pairs of one launch (grid y; 0 = 1)
+    long long pstride_in, pstride_out; // bytes from one pair's in0/in1 (out0/out1) to the next's
     int src;                        // spectrum a start pass reads (FCH_SRC_*)
     int flags;                      // FCH_FL_*
     int tail_op;                    // < 0: none; else the control op the pass's last block runs
@@ -147,6 +152,10 @@ struct fch_geom {
     int P;
 };
 fch_geom fch_geometry(int N, int prec);
+// the geometry of tiles tile_row / tile_col (as in fch_kparams) at grid size N
+fch_geom fch_geometry_tiled(int N, int prec, int tile_row, int tile_col);
+// whether tiles tile_row / tile_col launch at grid size N (threads, shared memory)
+bool fch_tile_valid(int N, int prec, int tile_row, int tile_col);
 
 cudaError_t fch_launch_col_f64(int mode, const fch_kparams &kp, cudaStream_t s);
 cudaError_t fch_launch_row_f64(int mode, const fch_kparams &kp, cudaStream_t s);

@@ -262,6 +262,32 @@ __device__ void block_partials(const T *red, double *part, double *scratch)
     }
 }
 
+// Double-float partials: the warp and block sums in double-float arithmetic on the
+// FP32 pipe (the double pipe runs a warp instruction in many cycles, and a block
+// sum in double would cost dozens of them per block), one conversion per slot.
+template <int NR>
+__device__ void block_partials(const df *red, double *part, double *scratch)
+{
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
+    float2 *sc = (float2 *)scratch;
+#pragma unroll
+    for (int r = 0; r < NR; r++) {
+        df v = red[r];
+        for (int o = 16; o > 0; o >>= 1)
+            v = v + df(__shfl_down_sync(0xffffffffu, v.hi, o), __shfl_down_sync(0xffffffffu, v.lo, o));
+        if (lane == 0) sc[r * 32 + wid] = make_float2(v.hi, v.lo);
+    }
+    __syncthreads();
+    if (threadIdx.x < NR) {
+        df s(0.f, 0.f);
+        for (int w = 0; w < nw; w++) {
+            const float2 e = sc[threadIdx.x * 32 + w];
+            s = s + df(e.x, e.y);
+        }
+        part[threadIdx.x * FCH_MAXBLK + blockIdx.x] = (double)s;
+    }
+}
+
 __device__ __forceinline__ bool pass_skipped(const fch_kparams &kp)
 {
     if (kp.flags & FCH_FL_NOSKIP) return false;
@@ -315,7 +341,26 @@ template <int MODE> struct ColTraits {
 template <typename C> struct ColBufs {
     const C *Un, *Um, *src, *Fn, *Fm;
     C *Unew, *dst;
+    const C *i0, *i1; // standalone transforms: this pair's half spectra in / out
+    C *o0, *o1;
 };
+
+// Standalone transforms of several field pairs in one launch: pair blockIdx.y
+// reads and writes its own fields (pstride_in / pstride_out bytes after the
+// previous pair's) and its own N x N slice of the work array. Other launches have
+// one pair (blockIdx.y = 0).
+__device__ __forceinline__ const void *pair_in(const void *p, const fch_kparams &kp)
+{
+    return p ? (const void *)((const char *)p + blockIdx.y * kp.pstride_in) : nullptr;
+}
+__device__ __forceinline__ void *pair_out(void *p, const fch_kparams &kp)
+{
+    return p ? (void *)((char *)p + blockIdx.y * kp.pstride_out) : nullptr;
+}
+template <typename C> __device__ __forceinline__ C *pair_Z(const fch_kparams &kp, int N)
+{
+    return (C *)kp.Z + (size_t)blockIdx.y * N * N;
+}
 
 template <typename T, int MODE>
 __device__ __forceinline__ void spec_elem(const fch_kparams &kp, const fch_consts<T> &K,
@@ -335,13 +380,13 @@ __device__ __forceinline__ void spec_elem(const fch_kparams &kp, const fch_const
     bool pack = false;
 
     if (MODE == CM_FWD_STORE) {
-        ((C *)kp.out0)[idx] = A;
-        if (kp.out1) ((C *)kp.out1)[idx] = B;
+        bf.o0[idx] = A;
+        if (bf.o1) bf.o1[idx] = B;
         return;
     }
     if (MODE == CM_INV_LOAD) {
-        Co = cscale(((const C *)kp.in0)[idx], K.inv_n2);
-        Do = kp.in1 ? cscale(((const C *)kp.in1)[idx], K.inv_n2) : mk<C>(0, 0);
+        Co = cscale(bf.i0[idx], K.inv_n2);
+        Do = bf.i1 ? cscale(bf.i1[idx], K.inv_n2) : mk<C>(0, 0);
         return;
     }
     if (MODE == CM_START) {
@@ -483,11 +528,15 @@ col_pass(const fch_kparams kp)
     const bool inv = TR::INV_ALWAYS || (TR::INV_OPT && (kp.flags & FCH_FL_PACK_F));
     const bool has_red = MODE == CM_SAV_PQ || MODE == CM_PSD_ITER ||
                          (MODE == CM_F_FINISH && (kp.flags & FCH_FL_AM3));
-    C *Z = (C *)kp.Z;
+    C *Z = pair_Z<C>(kp, N);
 
     // per-block constants from the control block
     fch_coef<T> co;
     ColBufs<C> bf;
+    bf.i0 = (const C *)pair_in(kp.in0, kp);
+    bf.i1 = (const C *)pair_in(kp.in1, kp);
+    bf.o0 = (C *)pair_out(kp.out0, kp);
+    bf.o1 = (C *)pair_out(kp.out1, kp);
     if (kp.ctrl) {
         const fch_ctrl *cs = kp.ctrl;
         co = load_coef<T>(cs);
@@ -634,7 +683,7 @@ __global__ void __launch_bounds__(256, pass_min_blocks<256, LOGN>()) row_pass(co
     const int rpb = nthr / tps;
     const int rr = threadIdx.x / tps, t = threadIdx.x - rr * tps;
     const int y0 = blockIdx.x * rpb;
-    C *Z = (C *)kp.Z;
+    C *Z = pair_Z<C>(kp, N);
     const bool f64io = kp.flags & FCH_FL_F64IO;
     const fch_consts<T> &K = consts<T>(kp);
 
@@ -656,16 +705,17 @@ __global__ void __launch_bounds__(256, pass_min_blocks<256, LOGN>()) row_pass(co
         }
         __syncthreads();
     } else if (MODE == RM_R2C_LOAD) {
+        const void *in0 = pair_in(kp.in0, kp), *in1 = pair_in(kp.in1, kp);
         for (int i = threadIdx.x; i < rpb * N; i += nthr) {
             const int r = i / N, x = i - r * N;
             const long g = (long)y0 * N + i;
             T a, b = 0;
             if (f64io) {
-                a = (T)((const double *)kp.in0)[g];
-                if (kp.in1) b = (T)((const double *)kp.in1)[g];
+                a = (T)((const double *)in0)[g];
+                if (in1) b = (T)((const double *)in1)[g];
             } else {
-                a = (T)((const float *)kp.in0)[g];
-                if (kp.in1) b = (T)((const float *)kp.in1)[g];
+                a = (T)((const float *)in0)[g];
+                if (in1) b = (T)((const float *)in1)[g];
             }
             rows[r * SL + skew(x)] = mk<C>(a, b);
         }
@@ -708,12 +758,13 @@ __global__ void __launch_bounds__(256, pass_min_blocks<256, LOGN>()) row_pass(co
             const T u = z.x, lu = z.y; // u and Lap u
             if (MODE == RM_C2R_STORE) {
                 const long g = (long)y * N + x;
+                void *out0 = pair_out(kp.out0, kp), *out1 = pair_out(kp.out1, kp);
                 if (f64io) {
-                    if (kp.out0) ((double *)kp.out0)[g] = (double)u;
-                    if (kp.out1) ((double *)kp.out1)[g] = (double)lu;
+                    if (out0) ((double *)out0)[g] = (double)u;
+                    if (out1) ((double *)out1)[g] = (double)lu;
                 } else {
-                    if (kp.out0) ((float *)kp.out0)[g] = (float)u;
-                    if (kp.out1) ((float *)kp.out1)[g] = (float)lu;
+                    if (out0) ((float *)out0)[g] = (float)u;
+                    if (out1) ((float *)out1)[g] = (float)lu;
                 }
                 continue;
             }

@@ -7,13 +7,19 @@ namespace {
 
 typedef void (*pass_fn)(const fch_kparams);
 
-// Raise the kernel's dynamic shared-memory limit once, to what the largest grid
-// (FCH_MAX_N) needs, so every smaller launch fits under it.
-template <typename T, int M> cudaError_t set_smem(pass_fn f, int bytes, bool &done)
+// grid y: the field pairs of a batched standalone transform (one otherwise)
+inline unsigned pair_grid(const fch_kparams &kp) { return kp.npairs > 1 ? (unsigned)kp.npairs : 1u; }
+
+// Raise the kernel's dynamic shared-memory limit, at its first launch to what the
+// default tiles of the largest grid (FCH_MAX_N) need, later only for larger tuned
+// tiles (those launch first while a context or the tuner is set up, before any
+// stream capture).
+inline cudaError_t set_smem(pass_fn f, int bytes, int floor_bytes, int &cur)
 {
-    if (done) return cudaSuccess;
-    cudaError_t e = cudaFuncSetAttribute((const void *)f, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
-    if (e == cudaSuccess) done = true;
+    const int want = bytes > floor_bytes ? bytes : floor_bytes;
+    if (want <= cur) return cudaSuccess;
+    cudaError_t e = cudaFuncSetAttribute((const void *)f, cudaFuncAttributeMaxDynamicSharedMemorySize, want);
+    if (e == cudaSuccess) cur = want;
     return e;
 }
 
@@ -48,44 +54,49 @@ template <typename T> constexpr bool warp_path() { return sizeof(T) == 4; }
 
 template <int M> cudaError_t launch_col_w(const fch_kparams &kp, cudaStream_t s)
 {
-    static bool attr = false;
+    static int attr = 0;
     const int smem = (1024 * 5 + 4 * 33 * 32) * 8;
     pass_fn f = fch::col_pass_w<M>;
-    cudaError_t e = set_smem<float, M>(f, smem, attr);
+    cudaError_t e = set_smem(f, smem, 0, attr);
     if (e != cudaSuccess) return e;
-    f<<<256, 128, smem, s>>>(kp);
+    f<<<dim3(256, pair_grid(kp)), 128, smem, s>>>(kp);
     return cudaGetLastError();
 }
 
 template <int M> cudaError_t launch_row_w(const fch_kparams &kp, cudaStream_t s)
 {
-    fch::row_pass_w<M><<<1024, 32, 0, s>>>(kp);
+    fch::row_pass_w<M><<<dim3(1024, pair_grid(kp)), 32, 0, s>>>(kp);
     return cudaGetLastError();
 }
 
+// Tiles (fch_kparams::tile_col, tile_row): 0 takes the warp-level passes where they
+// exist (single precision, N = 1024), else the compile-time kernel of the grid size
+// where one is built, else the generic kernel; -1 the same without the warp-level
+// passes; > 0 the generic kernel with that many column pairs (rows) per block. The
+// generic column kernel reads P from kp.P, which the caller sets to the tile's.
 template <typename T, int M> cudaError_t launch_col(const fch_kparams &kp, cudaStream_t s)
 {
-    if (warp_path<T>() && kp.N == 1024 && kp.tw2) return launch_col_w<M>(kp, s);
-    static bool attr[12] = {};
-    const fch_geom g = fch_geometry(kp.N, sizeof(T) == 4);
-    const int li = (kp.logN >= 9 && kp.logN <= 11) ? kp.logN : 0;
+    if (warp_path<T>() && kp.N == 1024 && kp.tw2 && kp.tile_col == 0) return launch_col_w<M>(kp, s);
+    static int attr[12] = {};
+    const fch_geom g = fch_geometry_tiled(kp.N, sizeof(T) == 4, 0, kp.tile_col);
+    const int li = (kp.tile_col <= 0 && kp.logN >= 9 && kp.logN <= 11) ? kp.logN : 0;
     pass_fn f = col_fn<T, M>(li);
-    cudaError_t e = set_smem<T, M>(f, fch_geometry(FCH_MAX_N, sizeof(T) == 4).col_smem, attr[li]);
+    cudaError_t e = set_smem(f, g.col_smem, fch_geometry(FCH_MAX_N, sizeof(T) == 4).col_smem, attr[li]);
     if (e != cudaSuccess) return e;
-    f<<<g.col_blocks, g.col_threads, g.col_smem, s>>>(kp);
+    f<<<dim3(g.col_blocks, pair_grid(kp)), g.col_threads, g.col_smem, s>>>(kp);
     return cudaGetLastError();
 }
 
 template <typename T, int M> cudaError_t launch_row(const fch_kparams &kp, cudaStream_t s)
 {
-    if (warp_path<T>() && kp.N == 1024 && kp.tw2) return launch_row_w<M>(kp, s);
-    static bool attr[12] = {};
-    const fch_geom g = fch_geometry(kp.N, sizeof(T) == 4);
-    const int li = (kp.logN >= 9 && kp.logN <= 11) ? kp.logN : 0;
+    if (warp_path<T>() && kp.N == 1024 && kp.tw2 && kp.tile_row == 0) return launch_row_w<M>(kp, s);
+    static int attr[12] = {};
+    const fch_geom g = fch_geometry_tiled(kp.N, sizeof(T) == 4, kp.tile_row, 0);
+    const int li = (kp.tile_row <= 0 && kp.logN >= 9 && kp.logN <= 11) ? kp.logN : 0;
     pass_fn f = row_fn<T, M>(li);
-    cudaError_t e = set_smem<T, M>(f, fch_geometry(FCH_MAX_N, sizeof(T) == 4).row_smem, attr[li]);
+    cudaError_t e = set_smem(f, g.row_smem, fch_geometry(FCH_MAX_N, sizeof(T) == 4).row_smem, attr[li]);
     if (e != cudaSuccess) return e;
-    f<<<g.row_blocks, g.row_threads, g.row_smem, s>>>(kp);
+    f<<<dim3(g.row_blocks, pair_grid(kp)), g.row_threads, g.row_smem, s>>>(kp);
     return cudaGetLastError();
 }
 

@@ -126,7 +126,7 @@ __global__ void __launch_bounds__(32) row_pass_w(const fch_kparams kp)
         atomicAdd(kp.nfft, (MODE == RM_R2C_LOAD || MODE == RM_C2R_STORE || MODE == RM_ENERGY) ? 2ull : 4ull);
     const C *tw2 = (const C *)kp.tw2;
     const bool f64io = kp.flags & FCH_FL_F64IO;
-    C *row = (C *)kp.Z + (long)y * N;
+    C *row = pair_Z<C>(kp, N) + (long)y * N;
     C v[32];
     if (MODE == RM_NIMEX_DIRECT || MODE == RM_SAV_DIRECT) {
         // (u*, Lap u*) pointwise from the stored real-space slots (eq. Richardson)
@@ -141,16 +141,17 @@ __global__ void __launch_bounds__(32) row_pass_w(const fch_kparams kp)
             v[n2] = plain ? zn : cadd(zn, cscale(csub(zn, __ldg(Rm + lane + 32 * n2)), g));
         }
     } else if (MODE == RM_R2C_LOAD) {
+        const void *in0 = pair_in(kp.in0, kp), *in1 = pair_in(kp.in1, kp);
 #pragma unroll
         for (int n2 = 0; n2 < 32; n2++) {
             const long g = (long)y * N + lane + 32 * n2;
             float a, b = 0.f;
             if (f64io) {
-                a = (float)((const double *)kp.in0)[g];
-                if (kp.in1) b = (float)((const double *)kp.in1)[g];
+                a = (float)((const double *)in0)[g];
+                if (in1) b = (float)((const double *)in1)[g];
             } else {
-                a = ((const float *)kp.in0)[g];
-                if (kp.in1) b = ((const float *)kp.in1)[g];
+                a = ((const float *)in0)[g];
+                if (in1) b = ((const float *)in1)[g];
             }
             v[n2] = mk<C>(a, b);
         }
@@ -185,12 +186,13 @@ __global__ void __launch_bounds__(32) row_pass_w(const fch_kparams kp)
             const float u = v[k1].x, lu = v[k1].y;
             if (MODE == RM_C2R_STORE) {
                 const long g = (long)y * N + x;
+                void *out0 = pair_out(kp.out0, kp), *out1 = pair_out(kp.out1, kp);
                 if (f64io) {
-                    if (kp.out0) ((double *)kp.out0)[g] = (double)u;
-                    if (kp.out1) ((double *)kp.out1)[g] = (double)lu;
+                    if (out0) ((double *)out0)[g] = (double)u;
+                    if (out1) ((double *)out1)[g] = (double)lu;
                 } else {
-                    if (kp.out0) ((float *)kp.out0)[g] = u;
-                    if (kp.out1) ((float *)kp.out1)[g] = lu;
+                    if (out0) ((float *)out0)[g] = u;
+                    if (out1) ((float *)out1)[g] = lu;
                 }
                 continue;
             }
@@ -240,11 +242,15 @@ __global__ void __launch_bounds__(128) col_pass_w(const fch_kparams kp)
     const bool inv = TR::INV_ALWAYS || (TR::INV_OPT && (kp.flags & FCH_FL_PACK_F));
     const bool has_red = MODE == CM_SAV_PQ || MODE == CM_PSD_ITER ||
                          (MODE == CM_F_FINISH && (kp.flags & FCH_FL_AM3));
-    C *Z = (C *)kp.Z;
+    C *Z = pair_Z<C>(kp, N);
 
-    fch_coef<float> co;
-    ColBufs<C> bf;
-    {
+    fch_coef<float> co = fch_coef<float>();
+    ColBufs<C> bf = ColBufs<C>();
+    bf.i0 = (const C *)pair_in(kp.in0, kp);
+    bf.i1 = (const C *)pair_in(kp.in1, kp);
+    bf.o0 = (C *)pair_out(kp.out0, kp);
+    bf.o1 = (C *)pair_out(kp.out1, kp);
+    if (kp.ctrl) {
         const fch_ctrl *cs = kp.ctrl;
         co = load_coef<float>(cs);
         bf.Un = (const C *)kp.U[cs->iu_n];

@@ -29,7 +29,9 @@ EXPORTS = ["fch_status_string", "fch_last_cuda_error", "fch_params_default", "fc
            "fch_mass", "fch_rhs_device", "fch_get_sav_r", "fch_run_adaptive", "fch_get_stats",
            "fch_fft_plan_create", "fch_fft_plan_destroy", "fch_fft_r2c", "fch_fft_c2r",
            "fch_adaptive_begin", "fch_adaptive_enqueue", "fch_adaptive_end", "fch_pass_timing",
-           "fch_pass_times", "fch_fft_r2c_noalloc"]
+           "fch_pass_times", "fch_fft_r2c_noalloc", "fch_autotune", "fch_autotune_reset",
+           "fch_ensemble_create", "fch_ensemble_destroy", "fch_ensemble_member",
+           "fch_ensemble_run_adaptive"]
 NCOL, NROW = 10, 8
 NPASS = NCOL + NROW + 1
 PASS_NAMES = (["col_fwd_store", "col_inv_load", "col_start", "col_imex_solve", "col_f_finish",
@@ -60,8 +62,17 @@ class Params(C.Structure):
         ("psd_nu", C.c_double), ("psd_itol", C.c_double), ("psd_lambda", C.c_double),
         ("psd_k_max", C.c_double),
         ("psd_max_iter", C.c_int), ("prec", C.c_int), ("sync_every", C.c_int),
-        ("fft_path", C.c_int),
+        ("fft_path", C.c_int), ("autotune", C.c_int), ("tile_row", C.c_int), ("tile_col", C.c_int),
     ]
+
+    def as_dict(self):
+        return {f: getattr(self, f) for f, _ in self._fields_}
+
+
+class Tile(C.Structure):
+    _fields_ = [("tile_row", C.c_int), ("tile_col", C.c_int), ("row_us", C.c_double),
+                ("col_us", C.c_double), ("row_default_us", C.c_double), ("col_default_us", C.c_double),
+                ("candidates", C.c_int)]
 
     def as_dict(self):
         return {f: getattr(self, f) for f, _ in self._fields_}
@@ -111,6 +122,13 @@ def lib():
                                        C.POINTER(Stats)]
         L.fch_get_stats.argtypes = [vp, C.POINTER(Stats)]
         L.fch_fft_plan_create.argtypes = [C.c_int, C.c_int, vp, C.POINTER(vp)]
+        L.fch_autotune.argtypes = [C.c_int, C.c_int, vp, C.POINTER(Tile)]
+        L.fch_ensemble_create.argtypes = [C.c_int, C.POINTER(Grid), C.POINTER(Params), vp, C.POINTER(vp)]
+        L.fch_ensemble_destroy.argtypes = [vp]
+        L.fch_ensemble_member.argtypes = [vp, C.c_int, C.POINTER(vp)]
+        L.fch_ensemble_run_adaptive.argtypes = [vp, C.c_int, C.c_double, C.c_double, C.c_int, C.c_longlong,
+                                                C.POINTER(Stats)]
+        L.fch_autotune_reset.argtypes = []
         L.fch_fft_plan_destroy.argtypes = [vp]
         L.fch_fft_r2c.argtypes = [vp, vp, vp, C.c_int]
         L.fch_fft_c2r.argtypes = [vp, vp, vp, C.c_int]
@@ -139,6 +157,17 @@ def _dp(a):
     return a.ctypes.data_as(C.POINTER(C.c_double))
 
 
+def autotune(n: int, prec: int, stream=None) -> dict:
+    """fch_autotune: the pass tiles kept for (n, prec), timed on first use."""
+    t = Tile()
+    _check(lib().fch_autotune(n, prec, _stream_ptr(stream), C.byref(t)), "fch_autotune")
+    return t.as_dict()
+
+
+def autotune_reset():
+    _check(lib().fch_autotune_reset(), "fch_autotune_reset")
+
+
 def params_default(q: float = 0.0, **kw) -> Params:
     p = Params()
     _check(lib().fch_params_default(C.byref(p), float(q)), "fch_params_default")
@@ -156,6 +185,16 @@ def geometry(n: int, prec: int = 0):
     keys = ["col_blocks", "col_threads", "col_smem", "row_blocks", "row_threads", "row_smem",
             "rpb", "P", "ctrl_bytes"]
     return dict(zip(keys, list(out)))
+
+
+def tile_geometry(n: int, prec: int, tile_row: int, tile_col: int):
+    """(valid, geometry) of the pass tiles (host-side query; no device work)"""
+    out = (C.c_int * 8)()
+    r = lib().fch_debug_tile(n, prec, tile_row, tile_col, out)
+    if r < 0:
+        raise ValueError(n)
+    keys = ["col_blocks", "col_threads", "col_smem", "row_blocks", "row_threads", "row_smem", "rpb", "P"]
+    return bool(r), dict(zip(keys, list(out)))
 
 
 def _stream_ptr(stream):
@@ -324,3 +363,70 @@ class FFTPlan:
     def c2r(self, X, x):
         b = x.shape[0] if x.dim() == 3 else 1
         _check(lib().fch_fft_c2r(self._h, _tensor_ptr(X), _tensor_ptr(x), b), "fch_fft_c2r")
+
+
+class _Member(Context):
+    """A context owned by an Ensemble (the single-instance API; not destroyed here)."""
+
+    def __init__(self, h, n, L, params):
+        self._h, self.n, self.L, self.params = h, n, L, params
+
+    def close(self):
+        self._h = None
+
+    __del__ = close
+
+
+class Ensemble:
+    """m independent contexts advanced together by one CUDA graph per launch
+    (fch_ensemble_*); members are reached with member(i) or indexing."""
+
+    def __init__(self, sizes, params, L: float = 4 * math.pi, x0: float = -2 * math.pi, stream=None):
+        m = len(sizes)
+        assert len(params) == m
+        self.sizes, self.L = list(sizes), L
+        self.params = list(params)
+        grids = (Grid * m)(*[Grid(n, L, x0) for n in sizes])
+        pars = (Params * m)(*self.params)
+        h = C.c_void_p()
+        _check(lib().fch_ensemble_create(m, grids, pars, _stream_ptr(stream), C.byref(h)),
+               "fch_ensemble_create")
+        self._h = h
+        self._members = []
+        for i in range(m):
+            c = C.c_void_p()
+            _check(lib().fch_ensemble_member(h, i, C.byref(c)), "fch_ensemble_member")
+            self._members.append(_Member(c, self.sizes[i], L, self.params[i]))
+
+    def __len__(self):
+        return len(self._members)
+
+    def member(self, i: int) -> Context:
+        return self._members[i]
+
+    __getitem__ = member
+
+    def close(self):
+        if getattr(self, "_h", None):
+            for mb in self._members:
+                mb.close()
+            lib().fch_ensemble_destroy(self._h)
+            self._h = None
+
+    __del__ = close
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def run_adaptive(self, scheme, sigma: float, t_final: float, rounds: int = 8, max_launches: int = 0,
+                     raise_on_timeout: bool = True):
+        s = SCHEMES[scheme] if isinstance(scheme, str) else int(scheme)
+        st = (Stats * len(self))()
+        rc = lib().fch_ensemble_run_adaptive(self._h, s, float(sigma), float(t_final), int(rounds),
+                                             int(max_launches), st)
+        if not (rc == 6 and not raise_on_timeout):
+            _check(rc, "fch_ensemble_run_adaptive")
+        return [x.as_dict() for x in st]

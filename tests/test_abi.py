@@ -60,6 +60,34 @@ def test_geometry_covers_grid(n, prec):
     assert max(g["row_blocks"], g["col_blocks"]) <= 4096
 
 
+@pytest.mark.parametrize("n", [16, 64, 256, 512, 1024, 2048])
+@pytest.mark.parametrize("prec", [0, 1, 2])
+def test_tiles_cover_grid(n, prec):
+    # every tile the autotuner may pick launches whole blocks over the grid within a
+    # block's thread and shared-memory limits; invalid ones are refused
+    csz = 8 if prec == 1 else 16
+    sl = n + n // 8
+    nvalid = 0
+    for t in (1, 2, 4, 8, 16, 32):
+        ok_r, g = fch.tile_geometry(n, prec, t, 0)
+        fits_r = t <= n and t * (n // 8) <= 256 and (n + t * sl) * csz <= 226 * 1024
+        assert ok_r == fits_r, (t, g)
+        if ok_r:
+            nvalid += 1
+            assert g["rpb"] == t and g["row_blocks"] * t == n
+            assert g["row_threads"] == t * (n // 8) and g["row_smem"] == (n + t * sl) * csz
+        ok_c, g = fch.tile_geometry(n, prec, 0, t)
+        fits_c = (t >= (2 if prec == 1 else 1) and t <= n // 2 and t * n // 4 <= 1024
+                  and (n + 2 * t * sl) * csz <= 226 * 1024)
+        assert ok_c == fits_c, (t, g)
+        if ok_c:
+            assert g["P"] == t and g["col_blocks"] * t == n // 2
+            assert g["col_threads"] == 2 * t * (n // 8) and g["col_smem"] == (n + 2 * t * sl) * csz
+    assert nvalid >= 1
+    assert fch.tile_geometry(n, prec, 0, 0)[0] and fch.tile_geometry(n, prec, -1, -1)[0]
+    assert not fch.tile_geometry(n, prec, 3, 0)[0] and not fch.tile_geometry(n, prec, -2, 0)[0]
+
+
 def test_stockham_index_map_is_a_permutation():
     # the store index of every Stockham stage (fft_smem) is a bijection on [0, N)
     for logn in range(4, 12):

@@ -76,6 +76,40 @@ def test_fft_r2c_c2r_vs_oracle(n, prec):
     assert np.abs(back.cpu().numpy() - x).max() <= tol * 10 * np.abs(x).max()
 
 
+@pytest.mark.parametrize("n,prec,batch", [(64, 1, 259), (128, 0, 131), (1024, 1, 19), (1024, 0, 11)])
+def test_fft_batched_launches_match_single_fields(n, prec, batch):
+    # a batch runs as launches of many field pairs (up to a 64 MiB work array each)
+    # plus an odd last field: every pair must come out exactly as when transformed
+    # alone (fields 2j, 2j+1 share one complex transform, so the pair is the unit),
+    # and match the oracle
+    rng = np.random.default_rng(n + batch)
+    x = rng.standard_normal((batch, n, n))
+    dt = torch.float64 if prec == 0 else torch.float32
+    cdt = torch.complex128 if prec == 0 else torch.complex64
+    xt = torch.tensor(x, dtype=dt, device=DEV)
+    X = torch.empty((batch, n // 2 + 1, n), dtype=cdt, device=DEV)
+    plan = fch.FFTPlan(n, prec)
+    plan.r2c(xt, X)
+    back = torch.empty_like(xt)
+    plan.c2r(X, back)
+    for b in sorted({0, 2 * (batch // 4), batch - 3, batch - 1}):
+        m = 1 if b == batch - 1 else 2
+        X1 = torch.empty((m, n // 2 + 1, n), dtype=cdt, device=DEV)
+        b1 = torch.empty((m, n, n), dtype=dt, device=DEV)
+        plan.r2c(xt[b:b + m], X1)
+        plan.c2r(X[b:b + m], b1)
+        torch.cuda.synchronize()
+        assert torch.equal(X1, X[b:b + m]), b
+        assert torch.equal(b1, back[b:b + m]), b
+        if n <= 128:
+            for f in range(b, b + m):
+                ref = O.fft2(x[f], -1)[:, : n // 2 + 1].T
+                tol = 1e-13 if prec == 0 else 2e-6
+                assert np.abs(X[f].cpu().numpy() - ref).max() <= tol * np.abs(ref).max() * math.log2(n)
+    tol = 1e-12 if prec == 0 else 3e-5
+    assert (back - xt).abs().max().item() <= tol * xt.abs().max().item()
+
+
 @pytest.mark.parametrize("n,prec", [(1024, 0), (2048, 0), (1024, 1), (2048, 1)])
 def test_fft_full_size_sampled_outputs(n, prec):
     rng = np.random.default_rng(7)
