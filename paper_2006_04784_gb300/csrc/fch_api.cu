@@ -28,14 +28,16 @@ fch_geom fch_geometry(int N, int prec)
     g.col_blocks = N / (2 * P);
     const int SL = N + N / 8; // skewed sequence length in shared memory
     g.col_smem = (N + 2 * P * SL) * csz;
+    // rows per block: one at N = 1024 (the compile-time kernel's 128 threads), else
+    // 256 threads' worth; the row pass keeps its twiddles in global memory
     const int tps = N / 8;
-    int rpb = 256 / tps;
+    int rpb = N == 1024 ? 1 : 256 / tps;
     if (rpb < 1) rpb = 1;
     if (rpb > N) rpb = N;
     g.rpb = rpb;
     g.row_threads = rpb * tps;
     g.row_blocks = N / rpb;
-    g.row_smem = (N + rpb * SL) * csz;
+    g.row_smem = rpb * SL * csz;
     return g;
 }
 
@@ -53,7 +55,7 @@ fch_geom fch_geometry_tiled(int N, int prec, int tile_row, int tile_col)
         g.rpb = tile_row;
         g.row_threads = tile_row * (N / 8);
         g.row_blocks = N / tile_row;
-        g.row_smem = (N + tile_row * SL) * csz;
+        g.row_smem = tile_row * SL * csz;
     }
     return g;
 }

@@ -139,7 +139,7 @@ __host__ __device__ inline int skewed_len(int n) { return n + (n >> 3); }
 
 // One Stockham stage of radix R = 2^LR on a length-N sequence at
 // s[skew(n)*stride + off]; thread t of tps = N/8 owns 8/R butterflies.
-template <int DIR, int LR, typename C>
+template <int DIR, int LR, bool TWG, typename C>
 __device__ __forceinline__ void fft_stage(C *s, int N, int logN, int stride, int off, const C *tw,
                                           int t, int Ns, int lNs)
 {
@@ -163,7 +163,7 @@ __device__ __forceinline__ void fft_stage(C *s, int N, int logN, int stride, int
             const C *tws = tw + (Ns - 8) + (j & (Ns - 1));
 #pragma unroll
             for (int r = 1; r < R; r++) {
-                C tv = tws[(r - 1) * Ns];
+                C tv = TWG ? ldg(tws + (r - 1) * Ns) : tws[(r - 1) * Ns];
                 if (DIR > 0) tv = cconj(tv);
                 v[b * R + r] = btw(v[b * R + r], tv);
             }
@@ -189,22 +189,23 @@ __device__ __forceinline__ void fft_stage(C *s, int N, int logN, int stride, int
 // In-place transform of one sequence (all sequences of a block in lockstep);
 // starts and ends with a barrier of the whole block. tw holds the forward
 // twiddles of every stage with Ns > 1 (stage with Ns: entries Ns - 8 + (r-1) Ns + j,
-// value exp(-2 pi i r j / (Ns R)), r = 1..R-1, j < Ns).
-template <int DIR, typename C>
+// value exp(-2 pi i r j / (Ns R)), r = 1..R-1, j < Ns), in shared memory, or in
+// global memory read through the read-only cache when TWG.
+template <int DIR, bool TWG = false, typename C>
 __device__ void fft_smem(C *s, int N, int logN, int stride, int off, const C *tw, int t)
 {
     int Ns = 1, lNs = 0, rem = logN;
     __syncthreads();
     while (rem >= 3) {
-        fft_stage<DIR, 3>(s, N, logN, stride, off, tw, t, Ns, lNs);
+        fft_stage<DIR, 3, TWG>(s, N, logN, stride, off, tw, t, Ns, lNs);
         Ns <<= 3;
         lNs += 3;
         rem -= 3;
     }
     if (rem == 2)
-        fft_stage<DIR, 2>(s, N, logN, stride, off, tw, t, Ns, lNs);
+        fft_stage<DIR, 2, TWG>(s, N, logN, stride, off, tw, t, Ns, lNs);
     else if (rem == 1)
-        fft_stage<DIR, 1>(s, N, logN, stride, off, tw, t, Ns, lNs);
+        fft_stage<DIR, 1, TWG>(s, N, logN, stride, off, tw, t, Ns, lNs);
 }
 
 // natural kx of slot q of a pair-layout row
@@ -666,8 +667,21 @@ col_pass(const fch_kparams kp)
 
 // ---------------------------------------------------------------------------
 // row pass: [inverse rows] -> pointwise stage -> [forward rows]
+// Threads a compile-time row pass is built for: one row of 128 threads at N = 1024
+// (seven blocks an SM with at most 73 registers a thread: the 1024 rows run in one
+// wave on the 152 SMs, six or seven to an SM), N/8 at N = 2048, else 256.
+template <int LOGN> constexpr int row_threads()
+{
+    return LOGN == 10 ? 128 : (LOGN >= 11 ? (1 << LOGN) / 8 : 256);
+}
+template <int LOGN> constexpr int row_min_blocks()
+{
+    return LOGN == 10 ? 7 : pass_min_blocks<256, LOGN>();
+}
+
 template <typename T, int MODE, int LOGN>
-__global__ void __launch_bounds__(256, pass_min_blocks<256, LOGN>()) row_pass(const fch_kparams kp)
+__global__ void __launch_bounds__(LOGN ? row_threads<LOGN>() : 256, LOGN ? row_min_blocks<LOGN>() : 1)
+row_pass(const fch_kparams kp)
 {
     typedef typename CT<T>::t C;
     if (pass_skipped(kp)) return;
@@ -675,11 +689,13 @@ __global__ void __launch_bounds__(256, pass_min_blocks<256, LOGN>()) row_pass(co
     __shared__ double red_scratch[FCH_NRED * 32];
     const int N = LOGN ? (1 << LOGN) : kp.N, tps = N >> 3, SL = skewed_len(N);
     const int logN = LOGN ? LOGN : kp.logN;
-    const int nthr = LOGN ? (N >= 2048 ? tps : 256) : (int)blockDim.x;
+    const int nthr = LOGN ? row_threads<LOGN>() : (int)blockDim.x;
     if (kp.nfft && blockIdx.x == 0 && threadIdx.x == 0)
         atomicAdd(kp.nfft, (MODE == RM_R2C_LOAD || MODE == RM_C2R_STORE || MODE == RM_ENERGY) ? 2ull : 4ull);
-    C *tw = (C *)smem_raw;
-    C *rows = tw + N;
+    // twiddles stay in global memory (read-only cache): the shared memory holds
+    // only the rows, so more blocks fit an SM
+    const C *tw = (const C *)kp.tw;
+    C *rows = (C *)smem_raw;
     const int rpb = nthr / tps;
     const int rr = threadIdx.x / tps, t = threadIdx.x - rr * tps;
     const int y0 = blockIdx.x * rpb;
@@ -687,7 +703,6 @@ __global__ void __launch_bounds__(256, pass_min_blocks<256, LOGN>()) row_pass(co
     const bool f64io = kp.flags & FCH_FL_F64IO;
     const fch_consts<T> &K = consts<T>(kp);
 
-    for (int i = threadIdx.x; i < N; i += nthr) tw[i] = ldg((const C *)kp.tw + i);
     const bool direct = MODE == RM_NIMEX_DIRECT || MODE == RM_SAV_DIRECT;
     if (direct) {
         // (u*, Lap u*) = (u^n, Lap u^n) + gam [(u^n, Lap u^n) - (u^{n-1}, Lap u^{n-1})]
@@ -737,7 +752,7 @@ __global__ void __launch_bounds__(256, pass_min_blocks<256, LOGN>()) row_pass(co
             rows[r * SL + skew(pp)] = ld[2 * k];
             rows[r * SL + skew(pp ? N - pp : (N >> 1))] = ld[2 * k + 1];
         }
-        fft_smem<+1>(rows + rr * SL, N, logN, 1, 0, tw, t);
+        fft_smem<+1, true>(rows + rr * SL, N, logN, 1, 0, tw, t);
     }
 
     T red[FCH_NRED] = {0, 0, 0, 0};
@@ -799,7 +814,7 @@ __global__ void __launch_bounds__(256, pass_min_blocks<256, LOGN>()) row_pass(co
     }
     if (MODE == RM_C2R_STORE || MODE == RM_ENERGY) return;
 
-    fft_smem<-1>(rows + rr * SL, N, logN, 1, 0, tw, t);
+    fft_smem<-1, true>(rows + rr * SL, N, logN, 1, 0, tw, t);
 #pragma unroll
     for (int k = 0; k < 4; k++) {
         const int i = threadIdx.x + k * nthr;

@@ -55,7 +55,7 @@ def test_geometry_covers_grid(n, prec):
     assert g["row_blocks"] * g["rpb"] == n
     assert g["row_threads"] == g["rpb"] * (n // 8) and g["row_threads"] <= 256
     assert g["row_threads"] % 32 == 0
-    assert g["row_smem"] == (n + g["rpb"] * sl) * csz and g["row_smem"] <= 227 * 1024
+    assert g["row_smem"] == g["rpb"] * sl * csz and g["row_smem"] <= 227 * 1024  # twiddles in global
     # per-block partial sums fit their slots (FCH_MAXBLK = 4096)
     assert max(g["row_blocks"], g["col_blocks"]) <= 4096
 
@@ -70,12 +70,12 @@ def test_tiles_cover_grid(n, prec):
     nvalid = 0
     for t in (1, 2, 4, 8, 16, 32):
         ok_r, g = fch.tile_geometry(n, prec, t, 0)
-        fits_r = t <= n and t * (n // 8) <= 256 and (n + t * sl) * csz <= 226 * 1024
+        fits_r = t <= n and t * (n // 8) <= 256 and t * sl * csz <= 226 * 1024
         assert ok_r == fits_r, (t, g)
         if ok_r:
             nvalid += 1
             assert g["rpb"] == t and g["row_blocks"] * t == n
-            assert g["row_threads"] == t * (n // 8) and g["row_smem"] == (n + t * sl) * csz
+            assert g["row_threads"] == t * (n // 8) and g["row_smem"] == t * sl * csz
         ok_c, g = fch.tile_geometry(n, prec, 0, t)
         fits_c = (t >= (2 if prec == 1 else 1) and t <= n // 2 and t * n // 4 <= 1024
                   and (n + 2 * t * sl) * csz <= 226 * 1024)
