@@ -11,8 +11,8 @@
 // Addition sums the high parts with TwoSum and the low parts with one rounding
 // (error bounded relative to the operands); multiplication adds the cross terms to
 // the exact product of the high parts; division refines a float quotient with two
-// correction terms. Transcendental functions (used only by the
-// q > 0 well and the ETD phi functions) go through double.
+// correction terms, the reciprocal takes one Newton step. Transcendental functions
+// (used only by the q > 0 well and the ETD phi functions) go through double.
 // Compile without fast-math: the transformations rely on IEEE rounding of each step.
 #pragma once
 #include <math.h>
@@ -59,25 +59,18 @@ __device__ __forceinline__ df fast_two_sum(float a, float b)
     return df(s, b - (s - a));
 }
 
-// Sum with an error of a few u^2 (|a| + |b|), u = 2^-24: the high parts are added
-// exactly (TwoSum), the low parts with one rounding, then renormalised. The bound
-// is relative to the operands, not to a cancelled result; that is the norm-wise
-// accuracy a transform's error analysis needs (its output error is bounded by
-// eps log N times the input norm), at 11 operations instead of the 20 of the
-// sum that is accurate relative to the result.
-__device__ __forceinline__ df operator+(df a, df b)
-{
-    df s = two_sum(a.hi, b.hi);
-    s.lo += a.lo + b.lo;
-    return fast_two_sum(s.hi, s.lo);
-}
-
-// The sum above without its renormalisation (8 operations), for the butterflies of
-// a transform: |lo| may then exceed ulp(hi)/2 by a small factor. Products absorb
-// such operands (their low-order terms are summed into the error word) and
-// renorm() restores the invariant where a stage ends. A subtraction that cancels
-// the high parts leaves the result in lo, so no routine that reads only .hi
-// (division, comparisons) may take an unrenormalised value.
+// Sums. The high parts are added exactly (TwoSum), the low parts with one rounding:
+// an error of a few u^2 (|a| + |b|), u = 2^-24, relative to the operands rather
+// than to a cancelled result. That is the norm-wise accuracy a transform's error
+// analysis needs (its output error is bounded by eps log N times the input norm).
+//
+// The operators renormalise the sum (add_norm, 11 operations). add_lazy / sub_lazy
+// leave it unrenormalised (8 operations): |lo| may exceed ulp(hi)/2, and after a
+// cancellation of the high parts it may exceed |hi|; the transform butterflies use
+// them and renormalise once where a stage stores (renorm restores |lo| <= ulp(hi)/2
+// where |hi| >= |lo|, renorm_exact in every case). Whatever reads only the high
+// word -- division, reciprocal, comparisons, signs -- renormalises its operands
+// first with renorm_exact.
 __device__ __forceinline__ df add_lazy(df a, df b)
 {
     df s = two_sum(a.hi, b.hi);
@@ -91,9 +84,16 @@ __device__ __forceinline__ df sub_lazy(df a, df b)
     return s;
 }
 __device__ __forceinline__ df renorm(df a) { return fast_two_sum(a.hi, a.lo); }
+__device__ __forceinline__ df renorm_exact(df a) { return two_sum(a.hi, a.lo); }
+__device__ __forceinline__ df add_norm(df a, df b)
+{
+    const df s = add_lazy(a, b);
+    return fast_two_sum(s.hi, s.lo);
+}
 
+__device__ __forceinline__ df operator+(df a, df b) { return add_norm(a, b); }
 __device__ __forceinline__ df operator-(df a) { return df(-a.hi, -a.lo); }
-__device__ __forceinline__ df operator-(df a, df b) { return a + (-b); }
+__device__ __forceinline__ df operator-(df a, df b) { return add_norm(a, -b); }
 
 __device__ __forceinline__ df operator*(df a, df b)
 {
@@ -107,17 +107,42 @@ __device__ __forceinline__ df operator*(df a, df b)
 // by +-1 (the DIR factors of the butterflies)
 __device__ __forceinline__ df operator*(int s, df a) { return s < 0 ? -a : a; }
 
+// Quotient by long division: three float quotient digits, each remainder
+// renormalised before its leading word is read.
 __device__ __forceinline__ df operator/(df a, df b)
 {
+    a = renorm_exact(a);
+    b = renorm_exact(b);
     const float rb = 1.0f / b.hi;
     const float q1 = a.hi * rb;
-    df r = a - b * df(q1, 0.f);
+    df r = renorm_exact(sub_lazy(a, b * df(q1, 0.f)));
     const float q2 = r.hi * rb;
-    r = r - b * df(q2, 0.f);
+    r = renorm_exact(sub_lazy(r, b * df(q2, 0.f)));
     const float q3 = r.hi * rb;
-    df q = fast_two_sum(q1, q2);
-    return q + df(q3, 0.f);
+    const df q = fast_two_sum(q1, q2);
+    return add_norm(q, df(q3, 0.f));
 }
+
+// Reciprocal by one Newton step from the float reciprocal r0 of the leading word:
+// 1/d = r0 (1 + e) + O(e^2) with e = 1 - d r0 = O(2^-24), e formed to about 2^-48
+// absolute (d.hi r0 split exactly by a fused multiply-add; 1 - p exact since p is
+// within 2^-23 of 1), so the result carries a few u^2 relative error.
+__device__ __forceinline__ df recip(df d)
+{
+    d = renorm_exact(d);
+    const float r0 = 1.0f / d.hi;
+    const float p = d.hi * r0;
+    const float pe = fmaf(d.hi, r0, -p);
+    const float e = ((1.0f - p) - pe) - d.lo * r0;
+    return fast_two_sum(r0, r0 * e);
+}
+__device__ __forceinline__ float recip(float d) { return 1.0f / d; }
+__device__ __forceinline__ double recip(double d) { return 1.0 / d; }
+
+// a s for an exact power of two s (both words scale exactly; s.lo is 0)
+__device__ __forceinline__ df mul_p2(df a, df s) { return df(a.hi * s.hi, a.lo * s.hi); }
+__device__ __forceinline__ float mul_p2(float a, float s) { return a * s; }
+__device__ __forceinline__ double mul_p2(double a, double s) { return a * s; }
 
 // Complex product a w for a twiddle factor w, each part a sum of two products
 // with one TwoSum: the high products are added exactly, their rounding errors
@@ -154,9 +179,20 @@ __device__ __forceinline__ df &operator-=(df &a, df b) { return a = a - b; }
 __device__ __forceinline__ df &operator*=(df &a, df b) { return a = a * b; }
 __device__ __forceinline__ df &operator/=(df &a, df b) { return a = a / b; }
 
-__device__ __forceinline__ bool operator<(df a, df b) { return a.hi < b.hi || (a.hi == b.hi && a.lo < b.lo); }
+// comparisons (on renormalised operands)
+__device__ __forceinline__ bool operator<(df a, df b)
+{
+    a = renorm_exact(a);
+    b = renorm_exact(b);
+    return a.hi < b.hi || (a.hi == b.hi && a.lo < b.lo);
+}
 __device__ __forceinline__ bool operator>(df a, df b) { return b < a; }
-__device__ __forceinline__ bool operator==(df a, df b) { return a.hi == b.hi && a.lo == b.lo; }
+__device__ __forceinline__ bool operator==(df a, df b)
+{
+    a = renorm_exact(a);
+    b = renorm_exact(b);
+    return a.hi == b.hi && a.lo == b.lo;
+}
 __device__ __forceinline__ bool operator!=(df a, df b) { return !(a == b); }
 
 // float and double forms next to the double-float ones, so unqualified calls in
@@ -170,8 +206,17 @@ __device__ __forceinline__ double expm1(double a) { return ::expm1(a); }
 __device__ __forceinline__ float copysign(float a, float b) { return ::copysignf(a, b); }
 __device__ __forceinline__ double copysign(double a, double b) { return ::copysign(a, b); }
 
-__device__ __forceinline__ df fabs(df a) { return a.hi < 0.f ? -a : a; }
-__device__ __forceinline__ df copysign(df a, df s) { return (a.hi < 0.f) != (s.hi < 0.f) ? -a : a; }
+__device__ __forceinline__ df fabs(df a)
+{
+    a = renorm_exact(a);
+    return a.hi < 0.f ? -a : a;
+}
+__device__ __forceinline__ df copysign(df a, df s)
+{
+    a = renorm_exact(a);
+    s = renorm_exact(s);
+    return (a.hi < 0.f) != (s.hi < 0.f) ? -a : a;
+}
 __device__ __forceinline__ df exp(df a) { return df(::exp((double)a)); }
 __device__ __forceinline__ df expm1(df a) { return df(::expm1((double)a)); }
 

@@ -67,6 +67,11 @@ template <typename C, typename S> __device__ __forceinline__ C cscale(C a, S s)
 {
     return mk<C>(a.x * s, a.y * s);
 }
+// a s for an exact power of two s
+template <typename C, typename S> __device__ __forceinline__ C cscale_p2(C a, S s)
+{
+    return mk<C>(mul_p2(a.x, s), mul_p2(a.y, s));
+}
 // Butterfly arithmetic: the plain complex operations for float and double; for
 // double-float the unrenormalised sums and twiddle product of fch_df.cuh, with
 // bnorm() renormalising where a transform stage stores its results.
@@ -74,6 +79,7 @@ template <typename R> __device__ __forceinline__ R radd(R a, R b) { return a + b
 template <typename R> __device__ __forceinline__ R rsub(R a, R b) { return a - b; }
 template <> __device__ __forceinline__ df radd(df a, df b) { return add_lazy(a, b); }
 template <> __device__ __forceinline__ df rsub(df a, df b) { return sub_lazy(a, b); }
+
 template <typename C> __device__ __forceinline__ C badd(C a, C b) { return mk<C>(radd(a.x, b.x), radd(a.y, b.y)); }
 template <typename C> __device__ __forceinline__ C bsub(C a, C b) { return mk<C>(rsub(a.x, b.x), rsub(a.y, b.y)); }
 template <typename C> __device__ __forceinline__ C btw(C a, C w) { return cmul(a, w); }
@@ -222,23 +228,23 @@ template <typename T>
 __device__ __forceinline__ void well(const fch_consts<T> &k, T u, T &W, T &W1, T &W2)
 {
     const T v = u - k.bm;
-    T A = (T)0.5 * v * v, A1 = v, A2 = (T)1;
+    T A = mul_p2(v * v, (T)0.5), A1 = v, A2 = (T)1;
     if (k.q != (T)0) {
         const T x = v / k.eps;
         const T e = exp(-fabs(x)); // e^{-|x|} in (0, 1]
-        const T id = (T)1 / ((T)1 + e * e);
-        const T sech = (T)2 * e * id;
+        const T id = recip((T)1 + e * e);
+        const T sech = mul_p2(e * id, (T)2);
         const T th = copysign(((T)1 - e * e) * id, x);
         A += k.qeps * ((T)1 - sech);
         A1 += k.q * sech * th;
-        A2 += k.qoe * sech * ((T)2 * sech * sech - (T)1);
+        A2 += k.qoe * sech * (mul_p2(sech * sech, (T)2) - (T)1);
     }
     const T w = u - k.bp;
-    const T B = (T)0.5 * w * w + k.g3 * (u - k.c3);
+    const T B = mul_p2(w * w, (T)0.5) + k.g3 * (u - k.c3);
     const T B1 = w + k.g3;
     W = A * B;
     W1 = A1 * B + A * B1;
-    W2 = A2 * B + (T)2 * A1 * B1 + A;
+    W2 = (k.q != (T)0 ? A2 * B : B) + mul_p2(A1 * B1, (T)2) + A;
 }
 
 // ---------------------------------------------------------------------------
@@ -386,8 +392,8 @@ __device__ __forceinline__ void spec_elem(const fch_kparams &kp, const fch_const
         return;
     }
     if (MODE == CM_INV_LOAD) {
-        Co = cscale(bf.i0[idx], K.inv_n2);
-        Do = bf.i1 ? cscale(bf.i1[idx], K.inv_n2) : mk<C>(0, 0);
+        Co = cscale_p2(bf.i0[idx], K.inv_n2);
+        Do = bf.i1 ? cscale_p2(bf.i1[idx], K.inv_n2) : mk<C>(0, 0);
         return;
     }
     if (MODE == CM_START) {
@@ -404,7 +410,7 @@ __device__ __forceinline__ void spec_elem(const fch_kparams &kp, const fch_const
         // eq. (IMEX-eq): (a + |k|^2 s) u^{n+1} = -b u^n - c u^{n-1} - |k|^2 N_IMEX(u*)^
         const C Nh = csub(A, cscale(B, K.e2 * k2));
         const C rhs = csub(cscale(ldg(bf.Un + idx), -co.b), cadd(cscale(ldg(bf.Um + idx), co.c), cscale(Nh, k2)));
-        v = cscale(rhs, (T)1 / (co.a + k2 * sk));
+        v = cscale(rhs, recip(co.a + k2 * sk));
         bf.Unew[idx] = v;
         pack = kp.flags & FCH_FL_PACK_F;
     } else if (MODE == CM_F_FINISH) {
@@ -430,7 +436,7 @@ __device__ __forceinline__ void spec_elem(const fch_kparams &kp, const fch_const
         const C us = co.gam != (T)0 ? cadd(un, cscale(csub(un, um), co.gam)) : un;
         const T l0 = K.e4 * k2 * k2 + K.b1am_e2 * k2 + K.b2am2;
         const T l1 = -K.l1c * k2 - K.b1am_e2 * k2 - K.b2am2;
-        const T iden = (T)1 / (co.a + k2 * l0);
+        const T iden = recip(co.a + k2 * l0);
         const C p = cscale(csub(cscale(un, -co.b), cadd(cscale(um, co.c), cscale(us, k2 * l1))), iden);
         const C q = cscale(X, -k2 * iden);
         ((C *)kp.Pb)[idx] = p;
@@ -451,10 +457,10 @@ __device__ __forceinline__ void spec_elem(const fch_kparams &kp, const fch_const
         C d = mk<C>(0, 0);
         if (k2 > (T)0) {
             const C mu = cadd(cadd(cscale(vv, K.e4 * k2 * k2), cscale(A, K.e2 * k2)), B);
-            const T ik2 = (T)1 / k2;
+            const T ik2 = recip(k2);
             const C R = cadd(mu, cscale(cadd(cscale(vv, co.a), cadd(cscale(bf.Un[idx], co.b),
                                                                     cscale(bf.Um[idx], co.c))), ik2));
-            d = cscale(R, (T)-1 / (sk + co.a * ik2));
+            d = cscale(R, -recip(sk + co.a * ik2));
         }
         v = cadd(vv, cscale(d, co.lam));
         Vb[idx] = v;
@@ -484,8 +490,8 @@ __device__ __forceinline__ void spec_elem(const fch_kparams &kp, const fch_const
         }
     }
     if (pack) {
-        Co = cscale(v, K.inv_n2);
-        Do = cscale(v, -k2 * K.inv_n2);
+        Co = cscale_p2(v, K.inv_n2);
+        Do = cscale(v, -mul_p2(k2, K.inv_n2));
     }
 }
 
@@ -595,9 +601,9 @@ col_pass(const fch_kparams kp)
             C A = mk<C>(0, 0), B = mk<C>(0, 0);
             if (TR::FWD) {
                 const C z0 = tile[rk + s0], z1 = cconj(tile[rm + s1]);
-                A = cscale(cadd(z0, z1), (T)0.5);
+                A = cscale_p2(cadd(z0, z1), (T)0.5);
                 const C dm = csub(z0, z1);
-                B = mk<C>((T)0.5 * dm.y, (T)-0.5 * dm.x);
+                B = mk<C>(mul_p2(dm.y, (T)0.5), mul_p2(dm.x, (T)-0.5));
             }
             C Co = mk<C>(0, 0), Do = mk<C>(0, 0);
             spec_elem<T, MODE>(kp, K, co, bf, p, ky, A, B, Co, Do, red);
@@ -627,9 +633,9 @@ col_pass(const fch_kparams kp)
                     C A = mk<C>(0, 0), B = mk<C>(0, 0);
                     if (TR::FWD) {
                         const C z1 = cconj(zo);
-                        A = cscale(cadd(zr, z1), (T)0.5);
+                        A = cscale_p2(cadd(zr, z1), (T)0.5);
                         const C dm = csub(zr, z1);
-                        B = mk<C>((T)0.5 * dm.y, (T)-0.5 * dm.x);
+                        B = mk<C>(mul_p2(dm.y, (T)0.5), mul_p2(dm.x, (T)-0.5));
                     }
                     C Co = mk<C>(0, 0), Do = mk<C>(0, 0);
                     spec_elem<T, MODE>(kp, K, co, bf, kx, kyy, A, B, Co, Do, red);
