@@ -237,6 +237,44 @@ fch_status fch_ensemble_member(fch_ensemble *e, int i, fch_ctx **ctx);
 fch_status fch_ensemble_run_adaptive(fch_ensemble *e, fch_scheme scheme, double sigma, double t_final, int rounds,
                                      long long max_launches, fch_stats *stats);
 
+/* ---- learned initial iterate for the PSD iteration (a Fourier neural operator) ----
+ * Sec. 3.3 starts the PSD iteration, eqs. (residual), (recurrence), from any v_0
+ * (the scheme uses u*); the network predicts a better one. Inputs per sample: two
+ * channels a = (u^n, (u* - u^n)/s), u* the extrapolation of eq. (Richardson), s the
+ * RMS of u* - u^n; output y, the predicted (u^{n+1} - u*)/s, so v_0 = u* + s y.
+ * Network: lifting to `width` channels (8, 16 or 32), `layers` Fourier layers
+ * (GELU after all but the last) keeping `modes` x (2 modes - 1) Fourier modes,
+ * projection through `proj` hidden channels (<= 128, proj x width <= 2048); FP32
+ * throughout, on this library's kernels and real transforms. Parameters are one
+ * flat float vector (order P, bP, {W_l, b_l, R_l}, Q1, bQ1, Q2, bQ2; R_l as
+ * [modes (2 modes - 1)][width][width] complex, re/im interleaved); they start at 0.
+ * fch_fno_forward(batch B, grid n, a [B][2][n][n], y [B][n][n], device float) keeps
+ * what the backward pass needs; fch_fno_backward(target [B][n][n]) then writes the
+ * gradient of mean((y - target)^2) over all B n^2 points (read with
+ * fch_fno_get_grads) and that mean in *loss (may be NULL); fch_fno_adam takes one
+ * Adam step with that gradient. n: power of two in [16, 2048], n >= 2 modes.
+ * Errors: FCH_EINVAL (arguments), FCH_ESTATE (backward without a forward pass),
+ * FCH_ENOMEM / FCH_ECUDA (reason in fch_last_cuda_error(NULL)). Work runs on
+ * `stream`; the get/set calls synchronize it. */
+typedef struct fch_fno fch_fno;
+fch_status fch_fno_create(int width, int layers, int modes, int proj, void *stream, fch_fno **out);
+fch_status fch_fno_destroy(fch_fno *f);
+fch_status fch_fno_num_params(const fch_fno *f, size_t *count);
+fch_status fch_fno_set_params(fch_fno *f, const float *host, size_t count);
+fch_status fch_fno_get_params(fch_fno *f, float *host, size_t count);
+fch_status fch_fno_get_grads(fch_fno *f, float *host, size_t count);
+fch_status fch_fno_forward(fch_fno *f, int batch, int n, const float *a_dev, float *y_dev);
+fch_status fch_fno_backward(fch_fno *f, const float *target_dev, double *loss);
+fch_status fch_fno_adam(fch_fno *f, float lr, float beta1, float beta2, float eps);
+
+/* One PSD-BDF2 step of size dt (as fch_step with FCH_PSD) whose iteration starts
+ * from the real field v0 (device, n x n, dtype 0 double / 1 float) instead of u*.
+ * v0 must carry the mass of u*: the residual acts on the k != 0 modes only, so the
+ * iteration keeps the k = 0 mode of its start; pass u* plus a correction of zero
+ * mean. The converged iterate agrees with the plain step's to within the PSD
+ * tolerance. */
+fch_status fch_step_psd_from(fch_ctx *ctx, double dt, const void *v0_dev, int dtype);
+
 /* ---- pass tiles (the paper has no counterpart: a GPU launch choice) ----
  * fch_autotune times the forward row pass (two real fields -> pair-layout work
  * array) and the forward column pass (work array -> two half spectra) of one field

@@ -745,6 +745,26 @@ extern "C" fch_status fch_get_state_device(fch_ctx *ctx, void *u_dev, int dtype)
 
 // one trial step from the current history into the trial slot (parameters already
 // in the control block). pack_f: leave (u_new, Lap u_new) packed for F(u_new).
+// PSD iterations, eqs. (residual), (recurrence), from the iterate in Vb (packed in Z
+// by the pass before) until the stopping test holds; the trial slot then receives
+// the converged iterate
+static fch_status psd_iterate(fch_ctx *ctx)
+{
+    const int chunk = 4;
+    for (int guard = 0;; guard++) {
+        if (guard * chunk > ctx->p.psd_max_iter + 2 * chunk) return FCH_ENOCONV;
+        for (int i = 0; i < chunk; i++) {
+            TRY(row(ctx, RM_F, FCH_FL_PSDSKIP));
+            TRY(colt(ctx, CM_PSD_ITER, 0, FCH_FL_PSDSKIP, OP_PSD_CHECK));
+        }
+        TRY(pull_ctrl(ctx));
+        if (ctx->hc.status || ctx->hc.done || ctx->hc.psd_conv) break;
+    }
+    if (ctx->hc.status) return (fch_status)ctx->hc.status;
+    TRY(col(ctx, CM_START, FCH_SRC_V, FCH_FL_COPYV));
+    return FCH_OK;
+}
+
 static fch_status enqueue_trial(fch_ctx *ctx, fch_scheme scheme, bool pack_f)
 {
     const int pf = pack_f ? FCH_FL_PACK_F : 0;
@@ -783,23 +803,9 @@ static fch_status enqueue_trial(fch_ctx *ctx, fch_scheme scheme, bool pack_f)
         TRY(row(ctx, RM_NIMEX));
         TRY(col(ctx, CM_ETD_STAGE2, 0, pf));
         return FCH_OK;
-    case FCH_PSD: {
+    case FCH_PSD:
         TRY(col(ctx, CM_START, 4, 128));
-        const int chunk = 4;
-        for (int guard = 0;; guard++) {
-            if (guard * chunk > ctx->p.psd_max_iter + 2 * chunk) return FCH_ENOCONV;
-            for (int i = 0; i < chunk; i++) {
-                TRY(row(ctx, RM_F, FCH_FL_PSDSKIP));
-                TRY(colt(ctx, CM_PSD_ITER, 0, FCH_FL_PSDSKIP, OP_PSD_CHECK));
-            }
-            TRY(pull_ctrl(ctx));
-            if (ctx->hc.status || ctx->hc.done || ctx->hc.psd_conv) break;
-        }
-        if (ctx->hc.status) return (fch_status)ctx->hc.status;
-        // trial = converged iterate
-        TRY(col(ctx, CM_START, FCH_SRC_V, FCH_FL_COPYV));
-        return FCH_OK;
-    }
+        return psd_iterate(ctx);
     }
     return FCH_EINVAL;
 }
@@ -821,6 +827,26 @@ extern "C" fch_status fch_step(fch_ctx *ctx, fch_scheme scheme, double dt)
 }
 
 // F of the state in slot src into its F slot (src: FCH_SRC_UN -> F(u^n), 5 -> F(u^{n-1}))
+extern "C" fch_status fch_step_psd_from(fch_ctx *ctx, double dt, const void *v0, int dtype)
+{
+    if (!ctx || !(dt > 0) || !v0 || (dtype != 0 && dtype != 1)) return FCH_EINVAL;
+    if (!ctx->have_state || ctx->failed) return FCH_ESTATE;
+    ctx->rvalid = false;
+    TRY(ctl(ctx, OP_INIT_TRIAL, 0, dt));
+    // v_0: the given field's spectrum is the first iterate; packed into Z for the
+    // first F pass of the iteration
+    TRY(load_field(ctx, v0, dtype == 0, ctx->Vb));
+    TRY(col(ctx, CM_START, FCH_SRC_V));
+    fch_status s = psd_iterate(ctx);
+    if (s != FCH_OK) {
+        ctx->failed = true;
+        return s;
+    }
+    TRY(ctl(ctx, OP_ACCEPT, 0, 0.0));
+    ctx->have_F = false;
+    return FCH_OK;
+}
+
 static fch_status eval_F(fch_ctx *ctx, int src)
 {
     TRY(col(ctx, CM_START, src));

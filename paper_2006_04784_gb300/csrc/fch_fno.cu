@@ -1,0 +1,712 @@
+// fch_fno.cu -- a Fourier neural operator (FNO) that predicts the initial iterate
+// of the PSD iteration (Sec. 3.3 leaves v_0 free): forward pass, backward pass,
+// mean-square loss and Adam, all in FP32 on this library's own kernels and its
+// own batched real 2D transforms (no cuFFT, no cuBLAS).
+//
+// Network (restating Li et al.'s Fourier neural operator): two input channels per
+// point, a = (u^n, (u* - u^n)/s), u* the extrapolation of eq. (Richardson), s the
+// RMS of u* - u^n; output y = predicted (u^{n+1} - u*)/s.
+//   h_0 = P a + bP;  h_{l+1} = act_l(W_l h_l + b_l + S_l(h_l));  y = Q2 GELU(Q1 h_L + bQ1) + bQ2
+//   S(h)[o] = C2R(H(sum_i R[m][o][i] R2C(h[i])(m)))  over the retained modes m,
+// act = GELU (x Phi(x), with erf) except after the last layer (identity). Retained
+// modes: kx in [0, M), ky in {0..M-1} and {N-M+1..N-1}, weight index
+// kx (2M-1) + kyi with ky = kyi (kyi < M) or -(kyi - M + 1). H replaces the kx = 0
+// column of the retained modes by its Hermitian part (Y(ky) + conj Y(-ky))/2, the
+// part a real inverse transform reads. The backward pass uses the adjoints: of C2R
+// on retained modes w(kx)/N^2 R2C (w = 1 at kx = 0, else 2), of R2C
+// N^2 C2R(v(kx) .), v = 1 at kx = 0, else 1/2, both through H at kx = 0.
+//
+// Layouts: fields [b][c][y][x] (channel fields contiguous, n x n each); spectra as
+// the library's transforms write them, kx-major [field][kx][ky]; parameters one
+// flat float vector in the order P, bP, {W_l, b_l, R_l} for each layer, Q1, bQ1,
+// Q2, bQ2, with R_l as [K][W_out][W_in] complex (re, im interleaved).
+// Weight gradients are summed over points in a fixed order (per-block partials,
+// then one pass over the blocks), so a backward pass is deterministic.
+#include <math.h>
+#include <stdio.h>
+#include <stdlib.h>
+#include <string.h>
+
+#include "../../include/fch.h"
+#include "fch_internal.h"
+
+namespace {
+
+constexpr int kMaxW2 = 128;  // hidden channels of the projection
+
+__device__ __forceinline__ float gelu(float x) { return 0.5f * x * (1.0f + erff(x * 0.70710678118654752f)); }
+__device__ __forceinline__ float gelu_grad(float x)
+{
+    return 0.5f * (1.0f + erff(x * 0.70710678118654752f)) + x * 0.39894228040143268f * expf(-0.5f * x * x);
+}
+
+// ky of retained-mode row kyi
+__device__ __forceinline__ int mode_ky(int kyi, int M, int n) { return kyi < M ? kyi : n - (kyi - M + 1); }
+
+// h0[b][c][p] = sum_i P[c][i] a[b][i][p] + bP[c]
+__global__ void fno_lift(const float *__restrict__ a, const float *__restrict__ P, const float *__restrict__ bP,
+                         float *__restrict__ h, int B, int n2, int W, int cin)
+{
+    const long t = (long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= (long)B * n2) return;
+    const int b = (int)(t / n2), p = (int)(t - (long)b * n2);
+    float in[4];
+    for (int i = 0; i < cin; i++) in[i] = a[((long)b * cin + i) * n2 + p];
+    for (int c = 0; c < W; c++) {
+        float acc = bP[c];
+        for (int i = 0; i < cin; i++) acc += P[c * cin + i] * in[i];
+        h[((long)b * W + c) * n2 + p] = acc;
+    }
+}
+
+// z[b][c][p] = sum_j Wl[c][j] h[b][j][p] + bl[c] + s[b][c][p];  out = act(z)
+// (W, the channel count, is a compile-time constant so the per-point channel
+// vectors stay in registers)
+template <int W>
+__global__ void fno_pointwise(const float *__restrict__ h, const float *__restrict__ s,
+                              const float *__restrict__ Wl, const float *__restrict__ bl, float *__restrict__ z,
+                              float *__restrict__ out, int B, int n2, int act)
+{
+    __shared__ float ws[W * W];
+    __shared__ float bs[W];
+    for (int i = threadIdx.x; i < W * W; i += blockDim.x) ws[i] = Wl[i];
+    for (int i = threadIdx.x; i < W; i += blockDim.x) bs[i] = bl[i];
+    __syncthreads();
+    const long t = (long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= (long)B * n2) return;
+    const int b = (int)(t / n2), p = (int)(t - (long)b * n2);
+    float in[W];
+#pragma unroll
+    for (int j = 0; j < W; j++) in[j] = h[((long)b * W + j) * n2 + p];
+    for (int c = 0; c < W; c++) {
+        const long o = ((long)b * W + c) * n2 + p;
+        float acc = bs[c] + s[o];
+#pragma unroll
+        for (int j = 0; j < W; j++) acc += ws[c * W + j] * in[j];
+        z[o] = acc;
+        out[o] = act ? gelu(acc) : acc;
+    }
+}
+
+// y[b][p] = bQ2 + sum_d Q2[d] GELU(bQ1[d] + sum_c Q1[d][c] h[b][c][p])
+template <int W>
+__global__ void fno_project(const float *__restrict__ h, const float *__restrict__ Q1, const float *__restrict__ bQ1,
+                            const float *__restrict__ Q2, const float *__restrict__ bQ2, float *__restrict__ y,
+                            int B, int n2, int W2)
+{
+    const long t = (long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= (long)B * n2) return;
+    const int b = (int)(t / n2), p = (int)(t - (long)b * n2);
+    float in[W];
+#pragma unroll
+    for (int c = 0; c < W; c++) in[c] = h[((long)b * W + c) * n2 + p];
+    float acc = bQ2[0];
+    for (int d = 0; d < W2; d++) {
+        float zq = bQ1[d];
+#pragma unroll
+        for (int c = 0; c < W; c++) zq += Q1[d * W + c] * in[c];
+        acc += Q2[d] * gelu(zq);
+    }
+    y[(long)b * n2 + p] = acc;
+}
+
+// Backward of the projection and the loss mean((y - target)^2): per point dy, the
+// hidden activations q, their gradients dzq and dh = Q1^T dzq; also (y - target)^2
+// per point for the loss.
+template <int W>
+__global__ void fno_project_bwd(const float *__restrict__ h, const float *__restrict__ Q1,
+                                const float *__restrict__ bQ1, const float *__restrict__ Q2,
+                                const float *__restrict__ y, const float *__restrict__ target, float *__restrict__ dy,
+                                float *__restrict__ q, float *__restrict__ dzq, float *__restrict__ dh,
+                                float *__restrict__ sq, int B, int n2, int W2, float scale)
+{
+    const long t = (long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= (long)B * n2) return;
+    const int b = (int)(t / n2), p = (int)(t - (long)b * n2);
+    float in[W], g[W];
+#pragma unroll
+    for (int c = 0; c < W; c++) {
+        in[c] = h[((long)b * W + c) * n2 + p];
+        g[c] = 0.f;
+    }
+    const float r = y[t] - target[t];
+    const float d = scale * r;
+    dy[t] = d;
+    sq[t] = r * r;
+    for (int k = 0; k < W2; k++) {
+        float zq = bQ1[k];
+#pragma unroll
+        for (int c = 0; c < W; c++) zq += Q1[k * W + c] * in[c];
+        const long o = ((long)b * W2 + k) * n2 + p;
+        q[o] = gelu(zq);
+        const float dz = d * Q2[k] * gelu_grad(zq);
+        dzq[o] = dz;
+#pragma unroll
+        for (int c = 0; c < W; c++) g[c] += Q1[k * W + c] * dz;
+    }
+#pragma unroll
+    for (int c = 0; c < W; c++) dh[((long)b * W + c) * n2 + p] = g[c];
+}
+
+// Backward of a Fourier layer's pointwise part: dz = dout act'(z); dh = Wl^T dz.
+template <int W>
+__global__ void fno_pointwise_bwd(const float *__restrict__ dout, const float *__restrict__ z,
+                                  const float *__restrict__ Wl, float *__restrict__ dz, float *__restrict__ dh,
+                                  int B, int n2, int act)
+{
+    __shared__ float ws[W * W];
+    for (int i = threadIdx.x; i < W * W; i += blockDim.x) ws[i] = Wl[i];
+    __syncthreads();
+    const long t = (long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= (long)B * n2) return;
+    const int b = (int)(t / n2), p = (int)(t - (long)b * n2);
+    float g[W], acc[W];
+#pragma unroll
+    for (int c = 0; c < W; c++) {
+        const long o = ((long)b * W + c) * n2 + p;
+        g[c] = act ? dout[o] * gelu_grad(z[o]) : dout[o];
+        dz[o] = g[c];
+        acc[c] = 0.f;
+    }
+#pragma unroll
+    for (int c = 0; c < W; c++)
+#pragma unroll
+        for (int j = 0; j < W; j++) acc[j] += ws[c * W + j] * g[c];
+#pragma unroll
+    for (int j = 0; j < W; j++) dh[((long)b * W + j) * n2 + p] = acc[j];
+}
+
+// Y[b W + o](m) = sum_i R[m][o][i] X[b W + i](m) on the retained modes, written
+// through H at kx = 0 (work item: one mode, or at kx = 0 the pair ky, -ky).
+// X and Y are spectra [field][kx][ky]; S = (n/2 + 1) n complex per field.
+__global__ void fno_mix(const float2 *__restrict__ X, const float2 *__restrict__ R, float2 *__restrict__ Y,
+                        int B, int W, int M, int n)
+{
+    const int items = M + (M - 1) * (2 * M - 1);
+    const long t = (long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= (long)B * W * items) return;
+    const int it = (int)(t % items), o = (int)((t / items) % W), b = (int)(t / ((long)items * W));
+    const long S = (long)(n / 2 + 1) * n;
+    const int K2 = 2 * M - 1;
+    auto mixed = [&](int kx, int kyi) {
+        const int ky = mode_ky(kyi, M, n);
+        const float2 *r = R + ((long)(kx * K2 + kyi) * W + o) * W;
+        float re = 0.f, im = 0.f;
+        for (int i = 0; i < W; i++) {
+            const float2 x = X[((long)b * W + i) * S + (long)kx * n + ky];
+            const float2 w = r[i];
+            re += w.x * x.x - w.y * x.y;
+            im += w.x * x.y + w.y * x.x;
+        }
+        return make_float2(re, im);
+    };
+    float2 *Yf = Y + ((long)b * W + o) * S;
+    if (it < M) { // kx = 0: ky = it and -it
+        const int ky = it;
+        const float2 yp = mixed(0, ky);
+        if (ky == 0) {
+            Yf[0] = make_float2(yp.x, 0.f);
+        } else {
+            const float2 ym = mixed(0, ky + M - 1);
+            const float2 hh = make_float2(0.5f * (yp.x + ym.x), 0.5f * (yp.y - ym.y));
+            Yf[ky] = hh;
+            Yf[n - ky] = make_float2(hh.x, -hh.y);
+        }
+    } else {
+        const int j = it - M, kx = 1 + j / K2, kyi = j % K2;
+        Yf[(long)kx * n + mode_ky(kyi, M, n)] = mixed(kx, kyi);
+    }
+}
+
+// dY[b][o][m] (compact, K modes a field) = H(w(kx)/n^2 Fd(m)), Fd = R2C of the
+// spectral branch's output gradient
+__global__ void fno_dY(const float2 *__restrict__ Fd, float2 *__restrict__ dY, int B, int W, int M, int n)
+{
+    const int K2 = 2 * M - 1, K = M * K2;
+    const long t = (long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= (long)B * W * K) return;
+    const int m = (int)(t % K);
+    const long f = t / K;
+    const long S = (long)(n / 2 + 1) * n;
+    const int kx = m / K2, kyi = m % K2, ky = mode_ky(kyi, M, n);
+    const float inv = 1.0f / ((float)n * (float)n);
+    const float2 *F = Fd + f * S;
+    float2 v;
+    if (kx == 0) {
+        const float2 a = F[ky], c = F[(n - ky) % n]; // w = 1 at kx = 0
+        v = make_float2(0.5f * (a.x + c.x) * inv, 0.5f * (a.y - c.y) * inv);
+    } else {
+        const float2 a = F[(long)kx * n + ky];
+        v = make_float2(2.f * a.x * inv, 2.f * a.y * inv);
+    }
+    dY[t] = v;
+}
+
+// dR[m][o][i] = sum_b dY[b][o][m] conj(X[b][i](m))
+__global__ void fno_dR(const float2 *__restrict__ dY, const float2 *__restrict__ X, float2 *__restrict__ dR,
+                       int B, int W, int M, int n)
+{
+    const int K2 = 2 * M - 1, K = M * K2;
+    const long t = (long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= (long)K * W * W) return;
+    const int i = (int)(t % W), o = (int)((t / W) % W), m = (int)(t / ((long)W * W));
+    const long S = (long)(n / 2 + 1) * n;
+    const int kx = m / K2, ky = mode_ky(m % K2, M, n);
+    float re = 0.f, im = 0.f;
+    for (int b = 0; b < B; b++) {
+        const float2 d = dY[((long)b * W + o) * K + m];
+        const float2 x = X[((long)b * W + i) * S + (long)kx * n + ky];
+        re += d.x * x.x + d.y * x.y;
+        im += d.y * x.x - d.x * x.y;
+    }
+    dR[t] = make_float2(re, im);
+}
+
+// Z[b W + i](m) = n^2 v(kx) sum_o conj(R[m][o][i]) dY[b][o][m], through H at kx = 0,
+// so that C2R(Z) is the gradient of the layer input through the spectral branch
+__global__ void fno_dX(const float2 *__restrict__ dY, const float2 *__restrict__ R, float2 *__restrict__ Z,
+                       int B, int W, int M, int n)
+{
+    const int K2 = 2 * M - 1, K = M * K2;
+    const int items = M + (M - 1) * K2;
+    const long t = (long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= (long)B * W * items) return;
+    const int it = (int)(t % items), i = (int)((t / items) % W), b = (int)(t / ((long)items * W));
+    const long S = (long)(n / 2 + 1) * n;
+    const float n2 = (float)n * (float)n;
+    auto back = [&](int m) {
+        float re = 0.f, im = 0.f;
+        for (int o = 0; o < W; o++) {
+            const float2 d = dY[((long)b * W + o) * K + m];
+            const float2 w = R[((long)m * W + o) * W + i];
+            re += w.x * d.x + w.y * d.y;
+            im += w.x * d.y - w.y * d.x;
+        }
+        return make_float2(re, im);
+    };
+    float2 *Zf = Z + ((long)b * W + i) * S;
+    if (it < M) { // kx = 0, v = 1
+        const int ky = it;
+        const float2 dp = back(ky);
+        if (ky == 0) {
+            Zf[0] = make_float2(n2 * dp.x, 0.f);
+        } else {
+            const float2 dm = back(ky + M - 1);
+            const float2 hh = make_float2(0.5f * n2 * (dp.x + dm.x), 0.5f * n2 * (dp.y - dm.y));
+            Zf[ky] = hh;
+            Zf[n - ky] = make_float2(hh.x, -hh.y);
+        }
+    } else { // v = 1/2
+        const int j = it - M, kx = 1 + j / K2, kyi = j % K2;
+        const float2 d = back(kx * K2 + kyi);
+        Zf[(long)kx * n + mode_ky(kyi, M, n)] = make_float2(0.5f * n2 * d.x, 0.5f * n2 * d.y);
+    }
+}
+
+__global__ void fno_add(float *__restrict__ a, const float *__restrict__ b, long cnt)
+{
+    const long t = (long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t < cnt) a[t] += b[t];
+}
+
+// Weight-gradient partials: G[a][c] = sum over points of A(a, pt) Bm(c, pt), with
+// A(a, (b, p)) = A[(b CA + a) n2 + p] (Bm alike; Bm null: 1). Block k sums points
+// [k chunk, (k+1) chunk) in order into part[k][a nb + c].
+__global__ void fno_wgrad_part(const float *__restrict__ A, int CA, int na, const float *__restrict__ Bm, int CB,
+                               int nb, int n2, long npts, int chunk, float *__restrict__ part)
+{
+    extern __shared__ float sm[];
+    float *sa = sm, *sb = sm + (long)na * 32;
+    const int nout = na * nb;
+    const long p0 = (long)blockIdx.x * chunk;
+    float acc[8];
+    for (int k = 0; k < 8; k++) acc[k] = 0.f;
+    for (long q0 = p0; q0 < p0 + chunk && q0 < npts; q0 += 32) {
+        const int cnt = (int)min((long)32, min(p0 + chunk, npts) - q0);
+        __syncthreads();
+        for (int e = threadIdx.x; e < na * 32; e += blockDim.x) {
+            const int a = e / 32, k = e % 32;
+            float v = 0.f;
+            if (k < cnt) {
+                const long pt = q0 + k, b = pt / n2, p = pt - b * n2;
+                v = A[(b * CA + a) * n2 + p];
+            }
+            sa[e] = v;
+        }
+        for (int e = threadIdx.x; e < nb * 32; e += blockDim.x) {
+            const int c = e / 32, k = e % 32;
+            float v = 0.f;
+            if (k < cnt) {
+                const long pt = q0 + k, b = pt / n2, p = pt - b * n2;
+                v = Bm ? Bm[(b * CB + c) * n2 + p] : 1.f;
+            }
+            sb[e] = v;
+        }
+        __syncthreads();
+        for (int k = 0; k < 8; k++) {
+            const int o = threadIdx.x + k * blockDim.x;
+            if (o >= nout) break;
+            const int a = o / nb, c = o % nb;
+            float s = 0.f;
+            for (int j = 0; j < cnt; j++) s += sa[a * 32 + j] * sb[c * 32 + j];
+            acc[k] += s;
+        }
+    }
+    for (int k = 0; k < 8; k++) {
+        const int o = threadIdx.x + k * blockDim.x;
+        if (o < nout) part[(long)blockIdx.x * nout + o] = acc[k];
+    }
+}
+
+__global__ void fno_wgrad_sum(const float *__restrict__ part, int nblk, int nout, float *__restrict__ out)
+{
+    const int o = blockIdx.x * blockDim.x + threadIdx.x;
+    if (o >= nout) return;
+    float s = 0.f;
+    for (int k = 0; k < nblk; k++) s += part[(long)k * nout + o];
+    out[o] = s;
+}
+
+// Adam (Kingma & Ba), bias-corrected, on the flat parameter vector
+__global__ void fno_adam(float *__restrict__ w, const float *__restrict__ g, float *__restrict__ m,
+                         float *__restrict__ v, long cnt, float lr, float b1, float b2, float eps, float c1, float c2)
+{
+    const long t = (long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= cnt) return;
+    const float gg = g[t];
+    const float mm = b1 * m[t] + (1.f - b1) * gg;
+    const float vv = b2 * v[t] + (1.f - b2) * gg * gg;
+    m[t] = mm;
+    v[t] = vv;
+    w[t] -= lr * (mm / c1) / (sqrtf(vv / c2) + eps);
+}
+
+} // namespace
+
+struct fch_fno {
+    int W, L, M, W2, cin, K;
+    cudaStream_t stream;
+    size_t np;
+    float *params, *grads, *am, *av;
+    long long adam_t;
+    // per (B, n) buffers
+    int B, n;
+    fch_fft_plan *plan;
+    float *h;     // (L + 1) x [B][W][n^2]
+    float *z;     // L x [B][W][n^2]
+    float2 *X;    // L x [B W][(n/2+1) n]
+    float2 *Ysp;  // [B W][(n/2+1) n], zero outside the retained modes
+    float2 *Fd;   // [B W][(n/2+1) n]
+    float2 *dY;   // [B][W][K]
+    float *s;     // [B][W][n^2]
+    float *dh, *dz, *tmp; // [B][W][n^2]
+    float *q, *dzq;       // [B][W2][n^2]
+    float *y, *dy, *sq;   // [B][n^2]
+    float *part;          // weight-gradient partials
+    const float *a;       // the last forward pass's input
+    bool have_fwd;
+    double *hsum;
+    char err[256];
+};
+
+namespace {
+
+size_t offset_of(const fch_fno *f, int what, int l)
+{
+    // what: 0 P, 1 bP, 2 W_l, 3 b_l, 4 R_l, 5 Q1, 6 bQ1, 7 Q2, 8 bQ2
+    const size_t W = f->W, lay = W * W + W + (size_t)f->K * W * W * 2;
+    const size_t base = W * f->cin + W;
+    switch (what) {
+    case 0: return 0;
+    case 1: return W * f->cin;
+    case 2: return base + l * lay;
+    case 3: return base + l * lay + W * W;
+    case 4: return base + l * lay + W * W + W;
+    case 5: return base + f->L * lay;
+    case 6: return base + f->L * lay + (size_t)f->W2 * W;
+    case 7: return base + f->L * lay + (size_t)f->W2 * W + f->W2;
+    default: return base + f->L * lay + (size_t)f->W2 * W + 2 * f->W2;
+    }
+}
+
+void free_buffers(fch_fno *f)
+{
+    void *bufs[] = {f->h, f->z, f->X, f->Ysp, f->Fd, f->dY, f->s, f->dh, f->dz, f->tmp,
+                    f->q, f->dzq, f->y, f->dy, f->sq, f->part};
+    for (void *b : bufs)
+        if (b) cudaFree(b);
+    f->h = f->z = f->s = f->dh = f->dz = f->tmp = f->q = f->dzq = f->y = f->dy = f->sq = f->part = nullptr;
+    f->X = f->Ysp = f->Fd = f->dY = nullptr;
+    if (f->plan) fch_fft_plan_destroy(f->plan);
+    f->plan = nullptr;
+    f->B = f->n = 0;
+}
+
+fch_status ensure_buffers(fch_fno *f, int B, int n)
+{
+    if (f->B == B && f->n == n) return FCH_OK;
+    free_buffers(f);
+    const size_t n2 = (size_t)n * n, fld = (size_t)B * f->W * n2, S = (size_t)(n / 2 + 1) * n;
+    cudaError_t e = cudaSuccess;
+    auto al = [&](void **p, size_t bytes) {
+        if (e == cudaSuccess) e = cudaMalloc(p, bytes);
+    };
+    al((void **)&f->h, (f->L + 1) * fld * 4);
+    al((void **)&f->z, f->L * fld * 4);
+    al((void **)&f->X, (size_t)f->L * B * f->W * S * 8);
+    al((void **)&f->Ysp, (size_t)B * f->W * S * 8);
+    al((void **)&f->Fd, (size_t)B * f->W * S * 8);
+    al((void **)&f->dY, (size_t)B * f->W * f->K * 8);
+    al((void **)&f->s, fld * 4);
+    al((void **)&f->dh, fld * 4);
+    al((void **)&f->dz, fld * 4);
+    al((void **)&f->tmp, fld * 4);
+    al((void **)&f->q, (size_t)B * f->W2 * n2 * 4);
+    al((void **)&f->dzq, (size_t)B * f->W2 * n2 * 4);
+    al((void **)&f->y, (size_t)B * n2 * 4);
+    al((void **)&f->dy, (size_t)B * n2 * 4);
+    al((void **)&f->sq, (size_t)B * n2 * 4);
+    al((void **)&f->part, (size_t)1024 * 2048 * 4);
+    if (e == cudaSuccess) e = cudaMemsetAsync(f->Ysp, 0, (size_t)B * f->W * S * 8, f->stream);
+    if (e != cudaSuccess) {
+        snprintf(f->err, sizeof(f->err), "fch_fno: %s", cudaGetErrorString(e));
+        free_buffers(f);
+        return e == cudaErrorMemoryAllocation ? FCH_ENOMEM : FCH_ECUDA;
+    }
+    fch_status s = fch_fft_plan_create(n, 1, f->stream, &f->plan);
+    if (s != FCH_OK) {
+        free_buffers(f);
+        return s;
+    }
+    f->B = B;
+    f->n = n;
+    return FCH_OK;
+}
+
+inline unsigned grid(long cnt, int bs) { return (unsigned)((cnt + bs - 1) / bs); }
+
+// launch kernel<W> for the channel count W (8, 16 or 32)
+#define WDISPATCH(Wv, kern, g, b, st, ...)                                                          \
+    do {                                                                                           \
+        if ((Wv) == 8)                                                                             \
+            kern<8><<<(g), (b), 0, (st)>>>(__VA_ARGS__);                                           \
+        else if ((Wv) == 16)                                                                       \
+            kern<16><<<(g), (b), 0, (st)>>>(__VA_ARGS__);                                          \
+        else                                                                                       \
+            kern<32><<<(g), (b), 0, (st)>>>(__VA_ARGS__);                                          \
+    } while (0)
+
+// weight gradient G[na][nb] = sum_points A Bm^T into out (device)
+cudaError_t wgrad(fch_fno *f, const float *A, int CA, int na, const float *Bm, int CB, int nb, float *out)
+{
+    const long npts = (long)f->B * f->n * f->n;
+    int nblk = 1024;
+    const int chunk = (int)((npts + nblk - 1) / nblk);
+    nblk = (int)((npts + chunk - 1) / chunk);
+    const int nthr = 256;
+    const size_t smem = (size_t)(na + nb) * 32 * 4;
+    fno_wgrad_part<<<nblk, nthr, smem, f->stream>>>(A, CA, na, Bm, CB, nb, f->n * f->n, npts, chunk, f->part);
+    fno_wgrad_sum<<<grid(na * nb, 256), 256, 0, f->stream>>>(f->part, nblk, na * nb, out);
+    return cudaGetLastError();
+}
+
+} // namespace
+
+extern "C" fch_status fch_fno_create(int width, int layers, int modes, int proj, void *stream, fch_fno **out)
+{
+    if (!out || (width != 8 && width != 16 && width != 32) || layers < 1 || layers > 16 || modes < 1 ||
+        proj < 1 || proj > kMaxW2 || proj * width > 8 * 256) {
+        fch_set_thread_error("fch_fno_create: invalid argument");
+        return FCH_EINVAL;
+    }
+    fch_fno *f = (fch_fno *)calloc(1, sizeof(fch_fno));
+    if (!f) return FCH_ENOMEM;
+    f->W = width;
+    f->L = layers;
+    f->M = modes;
+    f->W2 = proj;
+    f->cin = 2;
+    f->K = modes * (2 * modes - 1);
+    f->stream = (cudaStream_t)stream;
+    f->np = offset_of(f, 8, 0) + 1;
+    cudaError_t e = cudaMalloc((void **)&f->params, f->np * 4);
+    if (e == cudaSuccess) e = cudaMalloc((void **)&f->grads, f->np * 4);
+    if (e == cudaSuccess) e = cudaMalloc((void **)&f->am, f->np * 4);
+    if (e == cudaSuccess) e = cudaMalloc((void **)&f->av, f->np * 4);
+    if (e == cudaSuccess) e = cudaMallocHost((void **)&f->hsum, sizeof(double));
+    if (e == cudaSuccess) e = cudaMemsetAsync(f->params, 0, f->np * 4, f->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(f->grads, 0, f->np * 4, f->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(f->am, 0, f->np * 4, f->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(f->av, 0, f->np * 4, f->stream);
+    if (e != cudaSuccess) {
+        fch_set_thread_error(cudaGetErrorString(e));
+        fch_fno_destroy(f);
+        return FCH_ECUDA;
+    }
+    *out = f;
+    return FCH_OK;
+}
+
+extern "C" fch_status fch_fno_destroy(fch_fno *f)
+{
+    if (!f) return FCH_OK;
+    if (f->stream) cudaStreamSynchronize(f->stream);
+    free_buffers(f);
+    for (void *b : {(void *)f->params, (void *)f->grads, (void *)f->am, (void *)f->av})
+        if (b) cudaFree(b);
+    if (f->hsum) cudaFreeHost(f->hsum);
+    free(f);
+    return FCH_OK;
+}
+
+extern "C" fch_status fch_fno_num_params(const fch_fno *f, size_t *count)
+{
+    if (!f || !count) return FCH_EINVAL;
+    *count = f->np;
+    return FCH_OK;
+}
+
+static fch_status copy_vec(fch_fno *f, float *dev, const float *src_host, float *dst_host, size_t cnt)
+{
+    if (!f || cnt != f->np) return FCH_EINVAL;
+    cudaError_t e = src_host ? cudaMemcpyAsync(dev, src_host, cnt * 4, cudaMemcpyHostToDevice, f->stream)
+                             : cudaMemcpyAsync(dst_host, dev, cnt * 4, cudaMemcpyDeviceToHost, f->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(f->stream);
+    return e == cudaSuccess ? FCH_OK : FCH_ECUDA;
+}
+
+extern "C" fch_status fch_fno_set_params(fch_fno *f, const float *host, size_t cnt)
+{
+    if (!host) return FCH_EINVAL;
+    fch_status s = copy_vec(f, f ? f->params : nullptr, host, nullptr, cnt);
+    if (s == FCH_OK) {
+        cudaMemsetAsync(f->am, 0, f->np * 4, f->stream);
+        cudaMemsetAsync(f->av, 0, f->np * 4, f->stream);
+        f->adam_t = 0;
+    }
+    return s;
+}
+
+extern "C" fch_status fch_fno_get_params(fch_fno *f, float *host, size_t cnt)
+{
+    if (!host) return FCH_EINVAL;
+    return copy_vec(f, f ? f->params : nullptr, nullptr, host, cnt);
+}
+
+extern "C" fch_status fch_fno_get_grads(fch_fno *f, float *host, size_t cnt)
+{
+    if (!host) return FCH_EINVAL;
+    return copy_vec(f, f ? f->grads : nullptr, nullptr, host, cnt);
+}
+
+extern "C" fch_status fch_fno_forward(fch_fno *f, int batch, int n, const float *a, float *y)
+{
+    if (!f || !a || !y || batch < 1 || n < 2 * f->M || n < 16 || n > 2048 || (n & (n - 1))) {
+        fch_set_thread_error("fch_fno_forward: invalid argument");
+        return FCH_EINVAL;
+    }
+    fch_status st = ensure_buffers(f, batch, n);
+    if (st != FCH_OK) return st;
+    const int W = f->W, n2 = n * n;
+    const long pts = (long)batch * n2;
+    const size_t fld = (size_t)batch * W * n2, S = (size_t)(n / 2 + 1) * n;
+    cudaStream_t s = f->stream;
+    const float *P = f->params;
+    fno_lift<<<grid(pts, 256), 256, 0, s>>>(a, P + offset_of(f, 0, 0), P + offset_of(f, 1, 0), f->h, batch, n2, W,
+                                            f->cin);
+    for (int l = 0; l < f->L; l++) {
+        float *hin = f->h + l * fld, *hout = f->h + (l + 1) * fld;
+        float2 *X = f->X + (size_t)l * batch * W * S;
+        if ((st = fch_fft_r2c(f->plan, hin, X, batch * W)) != FCH_OK) return st;
+        const int items = f->M + (f->M - 1) * (2 * f->M - 1);
+        fno_mix<<<grid((long)batch * W * items, 256), 256, 0, s>>>(
+            X, (const float2 *)(P + offset_of(f, 4, l)), f->Ysp, batch, W, f->M, n);
+        if ((st = fch_fft_c2r(f->plan, f->Ysp, f->s, batch * W)) != FCH_OK) return st;
+        WDISPATCH(W, fno_pointwise, grid(pts, 128), 128, s, hin, f->s, P + offset_of(f, 2, l),
+                  P + offset_of(f, 3, l), f->z + l * fld, hout, batch, n2, l < f->L - 1);
+    }
+    WDISPATCH(W, fno_project, grid(pts, 128), 128, s, f->h + f->L * fld, P + offset_of(f, 5, 0),
+              P + offset_of(f, 6, 0), P + offset_of(f, 7, 0), P + offset_of(f, 8, 0), y, batch, n2, f->W2);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) {
+        snprintf(f->err, sizeof(f->err), "fch_fno_forward: %s", cudaGetErrorString(e));
+        fch_set_thread_error(f->err);
+        return FCH_ECUDA;
+    }
+    f->a = a;
+    f->have_fwd = true;
+    // keep y for the backward pass (the caller owns its array)
+    e = cudaMemcpyAsync(f->y, y, (size_t)pts * 4, cudaMemcpyDeviceToDevice, s);
+    return e == cudaSuccess ? FCH_OK : FCH_ECUDA;
+}
+
+extern "C" fch_status fch_fno_backward(fch_fno *f, const float *target, double *loss)
+{
+    if (!f || !target) return FCH_EINVAL;
+    if (!f->have_fwd) return FCH_ESTATE;
+    const int B = f->B, n = f->n, W = f->W, W2 = f->W2, n2 = n * n;
+    const long pts = (long)B * n2;
+    const size_t fld = (size_t)B * W * n2, S = (size_t)(n / 2 + 1) * n;
+    cudaStream_t s = f->stream;
+    const float *P = f->params;
+    float *G = f->grads;
+    cudaError_t e = cudaSuccess;
+    // projection and the loss (y kept by the forward pass)
+    WDISPATCH(W, fno_project_bwd, grid(pts, 128), 128, s, f->h + f->L * fld, P + offset_of(f, 5, 0),
+              P + offset_of(f, 6, 0), P + offset_of(f, 7, 0), f->y, target, f->dy, f->q, f->dzq, f->dh, f->sq, B,
+              n2, W2, 2.0f / (float)pts);
+    if (e == cudaSuccess) e = wgrad(f, f->dy, 1, 1, nullptr, 1, 1, G + offset_of(f, 8, 0));         // bQ2
+    if (e == cudaSuccess) e = wgrad(f, f->q, W2, W2, f->dy, 1, 1, G + offset_of(f, 7, 0));          // Q2
+    if (e == cudaSuccess) e = wgrad(f, f->dzq, W2, W2, nullptr, 1, 1, G + offset_of(f, 6, 0));      // bQ1
+    if (e == cudaSuccess) e = wgrad(f, f->dzq, W2, W2, f->h + f->L * fld, W, W, G + offset_of(f, 5, 0)); // Q1
+    for (int l = f->L - 1; l >= 0 && e == cudaSuccess; l--) {
+        float *hin = f->h + l * fld;
+        const float2 *R = (const float2 *)(P + offset_of(f, 4, l));
+        // dz = dh act'(z); dh_l = W^T dz (into tmp)
+        WDISPATCH(W, fno_pointwise_bwd, grid(pts, 128), 128, s, f->dh, f->z + l * fld, P + offset_of(f, 2, l),
+                  f->dz, f->tmp, B, n2, l < f->L - 1);
+        e = wgrad(f, f->dz, W, W, nullptr, 1, 1, G + offset_of(f, 3, l)); // b_l
+        if (e == cudaSuccess) e = wgrad(f, f->dz, W, W, hin, W, W, G + offset_of(f, 2, l)); // W_l
+        if (e != cudaSuccess) break;
+        // spectral branch
+        if (fch_fft_r2c(f->plan, f->dz, f->Fd, B * W) != FCH_OK) return FCH_ECUDA;
+        const int K = f->K;
+        fno_dY<<<grid((long)B * W * K, 256), 256, 0, s>>>(f->Fd, f->dY, B, W, f->M, n);
+        fno_dR<<<grid((long)K * W * W, 256), 256, 0, s>>>(f->dY, f->X + (size_t)l * B * W * S,
+                                                          (float2 *)(G + offset_of(f, 4, l)), B, W, f->M, n);
+        const int items = f->M + (f->M - 1) * (2 * f->M - 1);
+        fno_dX<<<grid((long)B * W * items, 256), 256, 0, s>>>(f->dY, R, f->Ysp, B, W, f->M, n);
+        if (fch_fft_c2r(f->plan, f->Ysp, f->dh, B * W) != FCH_OK) return FCH_ECUDA;
+        fno_add<<<grid((long)fld, 256), 256, 0, s>>>(f->dh, f->tmp, (long)fld);
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = wgrad(f, f->dh, W, W, nullptr, 1, 1, G + offset_of(f, 1, 0));     // bP
+    if (e == cudaSuccess) e = wgrad(f, f->dh, W, W, f->a, f->cin, f->cin, G + offset_of(f, 0, 0)); // P
+    // loss = mean of the squared residuals (host sum of a device copy, in double)
+    if (e == cudaSuccess && loss) {
+        float *hb = (float *)malloc((size_t)pts * 4);
+        if (!hb) return FCH_ENOMEM;
+        e = cudaMemcpyAsync(hb, f->sq, (size_t)pts * 4, cudaMemcpyDeviceToHost, s);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+        double acc = 0;
+        for (long i = 0; i < pts; i++) acc += hb[i];
+        free(hb);
+        *loss = acc / (double)pts;
+    }
+    if (e != cudaSuccess) {
+        snprintf(f->err, sizeof(f->err), "fch_fno_backward: %s", cudaGetErrorString(e));
+        fch_set_thread_error(f->err);
+        return FCH_ECUDA;
+    }
+    return FCH_OK;
+}
+
+extern "C" fch_status fch_fno_adam(fch_fno *f, float lr, float beta1, float beta2, float eps)
+{
+    if (!f || !(lr > 0) || !(beta1 >= 0 && beta1 < 1) || !(beta2 >= 0 && beta2 < 1) || !(eps > 0)) return FCH_EINVAL;
+    f->adam_t++;
+    const float c1 = 1.f - powf(beta1, (float)f->adam_t), c2 = 1.f - powf(beta2, (float)f->adam_t);
+    fno_adam<<<grid((long)f->np, 256), 256, 0, f->stream>>>(f->params, f->grads, f->am, f->av, (long)f->np, lr, beta1,
+                                                            beta2, eps, c1, c2);
+    return cudaGetLastError() == cudaSuccess ? FCH_OK : FCH_ECUDA;
+}

@@ -31,7 +31,9 @@ EXPORTS = ["fch_status_string", "fch_last_cuda_error", "fch_params_default", "fc
            "fch_adaptive_begin", "fch_adaptive_enqueue", "fch_adaptive_end", "fch_pass_timing",
            "fch_pass_times", "fch_fft_r2c_noalloc", "fch_autotune", "fch_autotune_reset",
            "fch_ensemble_create", "fch_ensemble_destroy", "fch_ensemble_member",
-           "fch_ensemble_run_adaptive"]
+           "fch_ensemble_run_adaptive", "fch_fno_create", "fch_fno_destroy", "fch_fno_num_params",
+           "fch_fno_set_params", "fch_fno_get_params", "fch_fno_get_grads", "fch_fno_forward",
+           "fch_fno_backward", "fch_fno_adam", "fch_step_psd_from"]
 NCOL, NROW = 10, 8
 NPASS = NCOL + NROW + 1
 PASS_NAMES = (["col_fwd_store", "col_inv_load", "col_start", "col_imex_solve", "col_f_finish",
@@ -125,6 +127,17 @@ def lib():
         L.fch_autotune.argtypes = [C.c_int, C.c_int, vp, C.POINTER(Tile)]
         L.fch_ensemble_create.argtypes = [C.c_int, C.POINTER(Grid), C.POINTER(Params), vp, C.POINTER(vp)]
         L.fch_ensemble_destroy.argtypes = [vp]
+        fp = C.POINTER(C.c_float)
+        L.fch_fno_create.argtypes = [C.c_int, C.c_int, C.c_int, C.c_int, vp, C.POINTER(vp)]
+        L.fch_fno_destroy.argtypes = [vp]
+        L.fch_fno_num_params.argtypes = [vp, C.POINTER(C.c_size_t)]
+        L.fch_fno_set_params.argtypes = [vp, fp, C.c_size_t]
+        L.fch_fno_get_params.argtypes = [vp, fp, C.c_size_t]
+        L.fch_fno_get_grads.argtypes = [vp, fp, C.c_size_t]
+        L.fch_fno_forward.argtypes = [vp, C.c_int, C.c_int, vp, vp]
+        L.fch_fno_backward.argtypes = [vp, vp, C.POINTER(C.c_double)]
+        L.fch_fno_adam.argtypes = [vp, C.c_float, C.c_float, C.c_float, C.c_float]
+        L.fch_step_psd_from.argtypes = [vp, C.c_double, vp, C.c_int]
         L.fch_ensemble_member.argtypes = [vp, C.c_int, C.POINTER(vp)]
         L.fch_ensemble_run_adaptive.argtypes = [vp, C.c_int, C.c_double, C.c_double, C.c_int, C.c_longlong,
                                                 C.POINTER(Stats)]
@@ -279,6 +292,12 @@ class Context:
         s = SCHEMES[scheme] if isinstance(scheme, str) else int(scheme)
         self._ck(lib().fch_step(self._h, s, float(dt)), "fch_step")
 
+    def step_psd_from(self, dt: float, v0):
+        """one PSD-BDF2 step whose iteration starts from the device field v0"""
+        assert v0.is_cuda and v0.is_contiguous() and tuple(v0.shape) == (self.n, self.n)
+        self._ck(lib().fch_step_psd_from(self._h, float(dt), _tensor_ptr(v0), _dtype_code(v0)),
+                 "fch_step_psd_from")
+
     def energy(self) -> float:
         e = C.c_double()
         self._ck(lib().fch_energy(self._h, C.byref(e)), "fch_energy")
@@ -430,3 +449,57 @@ class Ensemble:
         if not (rc == 6 and not raise_on_timeout):
             _check(rc, "fch_ensemble_run_adaptive")
         return [x.as_dict() for x in st]
+
+
+class FNO:
+    """Fourier neural operator for the PSD initial iterate (fch_fno_*); tensors on
+    the device, float32."""
+
+    def __init__(self, width=32, layers=4, modes=16, proj=64, stream=None):
+        self.width, self.layers, self.modes, self.proj = width, layers, modes, proj
+        h = C.c_void_p()
+        _check(lib().fch_fno_create(width, layers, modes, proj, _stream_ptr(stream), C.byref(h)),
+               "fch_fno_create")
+        self._h = h
+        n = C.c_size_t()
+        _check(lib().fch_fno_num_params(h, C.byref(n)), "fch_fno_num_params")
+        self.num_params = n.value
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().fch_fno_destroy(self._h)
+            self._h = None
+
+    __del__ = close
+
+    def set_params(self, p: np.ndarray):
+        p = np.ascontiguousarray(p, dtype=np.float32)
+        assert p.size == self.num_params
+        _check(lib().fch_fno_set_params(self._h, p.ctypes.data_as(C.POINTER(C.c_float)), p.size),
+               "fch_fno_set_params")
+
+    def params(self) -> np.ndarray:
+        p = np.empty(self.num_params, dtype=np.float32)
+        _check(lib().fch_fno_get_params(self._h, p.ctypes.data_as(C.POINTER(C.c_float)), p.size),
+               "fch_fno_get_params")
+        return p
+
+    def grads(self) -> np.ndarray:
+        g = np.empty(self.num_params, dtype=np.float32)
+        _check(lib().fch_fno_get_grads(self._h, g.ctypes.data_as(C.POINTER(C.c_float)), g.size),
+               "fch_fno_get_grads")
+        return g
+
+    def forward(self, a, y):
+        """a: (B, 2, n, n) float32 device tensor; y: (B, n, n) output"""
+        assert a.dtype == y.dtype and a.is_contiguous() and y.is_contiguous()
+        B, _, n, _ = a.shape
+        _check(lib().fch_fno_forward(self._h, B, n, _tensor_ptr(a), _tensor_ptr(y)), "fch_fno_forward")
+
+    def backward(self, target) -> float:
+        loss = C.c_double()
+        _check(lib().fch_fno_backward(self._h, _tensor_ptr(target), C.byref(loss)), "fch_fno_backward")
+        return loss.value
+
+    def adam(self, lr=1e-3, beta1=0.9, beta2=0.999, eps=1e-8):
+        _check(lib().fch_fno_adam(self._h, lr, beta1, beta2, eps), "fch_fno_adam")

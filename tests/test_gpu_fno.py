@@ -1,0 +1,110 @@
+"""GPU: the Fourier neural operator (forward, backward, Adam) against its FP64 CPU
+oracle, and the PSD step started from a given iterate."""
+import math
+
+import numpy as np
+import pytest
+
+from oracle import fno_oracle as F
+from paper_2006_04784_gb300 import inputs as I
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():  # pragma: no cover
+    pytest.skip("needs a CUDA device", allow_module_level=True)
+
+from paper_2006_04784_gb300 import build as B  # noqa: E402
+
+B.build()
+from paper_2006_04784_gb300 import fch  # noqa: E402
+
+DEV = torch.device("cuda:0")
+
+
+def rel(a, b):
+    return float(np.linalg.norm(np.asarray(a, dtype=np.float64) - b) / np.linalg.norm(b))
+
+
+@pytest.mark.parametrize("width,layers,modes,proj,n,batch", [(8, 2, 4, 16, 32, 2), (32, 4, 16, 64, 64, 2)])
+def test_fno_forward_backward_vs_oracle(width, layers, modes, proj, n, batch):
+    cfg = F.Config(width=width, layers=layers, modes=modes, proj=proj)
+    rng = np.random.default_rng(width + n)
+    params = (F.init_params(cfg, 0) + 0.05 * rng.standard_normal(cfg.size())).astype(np.float32)
+    a = rng.standard_normal((batch, 2, n, n)).astype(np.float32)
+    target = rng.standard_normal((batch, n, n)).astype(np.float32)
+    net = fch.FNO(width, layers, modes, proj)
+    assert net.num_params == cfg.size()
+    net.set_params(params)
+    at = torch.tensor(a, device=DEV)
+    y = torch.empty((batch, n, n), device=DEV)
+    net.forward(at, y)
+    loss = net.backward(torch.tensor(target, device=DEV))
+    p64, a64, t64 = params.astype(np.float64), a.astype(np.float64), target.astype(np.float64)
+    y_ref = F.forward(p64, a64, cfg)
+    assert rel(y.cpu().numpy(), y_ref) < 2e-5
+    assert loss == pytest.approx(F.loss(p64, a64, t64, cfg), rel=1e-4)
+    g, g_ref = net.grads(), F.backward(p64, a64, t64, cfg)
+    o = 0
+    for name, sh in cfg.shapes():
+        k = int(np.prod(sh))
+        assert rel(g[o:o + k], g_ref[o:o + k]) < 2e-4, name
+        o += k
+
+
+def test_fno_training_reduces_the_loss():
+    # fit a fixed smooth map (a band-limited filter of the first channel plus a
+    # quadratic term) on a fixed batch: Adam on the library's gradients
+    n, batch = 32, 4
+    rng = np.random.default_rng(3)
+    x = np.arange(n) * 2 * np.pi / n
+    X, Y = np.meshgrid(x, x, indexing="xy")
+    a = np.zeros((batch, 2, n, n), dtype=np.float32)
+    for b in range(batch):
+        for c in range(2):
+            for k in range(1, 4):
+                a[b, c] += rng.standard_normal() * np.cos(k * X + rng.uniform(0, 6)) + \
+                    rng.standard_normal() * np.sin(k * Y + rng.uniform(0, 6))
+    target = (0.5 * np.roll(a[:, 0], 1, axis=-1) + 0.2 * a[:, 1] ** 2).astype(np.float32)
+    cfg = F.Config(width=16, layers=2, modes=6, proj=32)
+    net = fch.FNO(16, 2, 6, 32)
+    net.set_params(F.init_params(cfg, 1).astype(np.float32))
+    at, tt = torch.tensor(a, device=DEV), torch.tensor(target, device=DEV)
+    y = torch.empty((batch, n, n), device=DEV)
+    losses = []
+    for it in range(300):
+        net.forward(at, y)
+        losses.append(net.backward(tt))
+        net.adam(3e-3)
+    assert losses[-1] < 0.1 * losses[0]
+
+
+def test_psd_step_from_a_given_iterate():
+    n, L = 64, 4 * math.pi
+    p = fch.params_default(0.0, psd_itol=1e-12)
+    p.zeta, p.D0 = 1.1, 170.0
+    u0 = I.circle_bilayer(n, noise=1e-3)
+    dt = 2e-4
+    with fch.Context(n, p) as a, fch.Context(n, p) as b:
+        for c in (a, b):
+            c.set_state(u0)
+            c.step("psd", dt)
+        u1 = a.get_state()
+        a.step("psd", dt)
+        plain = a.get_state()
+        it_plain = a.stats()["last_psd_iter"]
+        ustar = 2 * u1 - u0  # eq. (Richardson) with equal steps
+        noise = 1e-3 * np.random.default_rng(0).standard_normal((n, n))
+        noise -= noise.mean()
+        snap = b.get_state()
+        # from u* plus a zero-mean perturbation: the same fixed point, the same mass
+        b.step_psd_from(dt, torch.tensor(ustar + noise, device=DEV))
+        assert rel(b.get_state(), plain) < 1e-9
+        assert b.mass() == pytest.approx(a.mass(), rel=1e-12)
+        # from the converged answer itself: at most two iterations
+        b.set_state(u0)
+        b.step("psd", dt)
+        assert np.array_equal(b.get_state(), snap)
+        b.step_psd_from(dt, torch.tensor(plain, device=DEV))
+        assert b.stats()["last_psd_iter"] <= 2 < it_plain
+        assert rel(b.get_state(), plain) < 1e-10
