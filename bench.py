@@ -662,6 +662,94 @@ def ensemble_bench(args):
     return out
 
 
+def fno_bench(args):
+    """The learned PSD initial iterate: a 4-layer FNO (32 channels, 16 modes) trained
+    on PSD-BDF2 trajectories the library computes at 128^2 (the 128^2 circle-bilayer
+    physics, step sizes 1e-3 x 2^U(-1,1)), then PSD steps started from u* (the plain
+    method) and from the FNO's v_0 on held-out trajectories at 128^2 and at 1024^2:
+    PSD iterations, initial-iterate error, and the network's inference time."""
+    import numpy as np
+    import torch
+
+    from paper_2006_04784_gb300 import build as B
+    B.build()
+    from paper_2006_04784_gb300 import fch
+    from paper_2006_04784_gb300 import fno_train as T
+    from paper_2006_04784_gb300 import inputs as I
+
+    dev = torch.device("cuda", 0)
+    rng = np.random.default_rng(11)
+    p = fch.params_default(0.0, psd_itol=1e-10)
+    n = 128
+    data, t0 = [], time.perf_counter()
+    inits = [I.circle_bilayer(n, radius=r, noise=1e-3, seed=s) for r, s in ((1.6, 1), (2.0, 2), (2.4, 3), (1.8, 4))]
+    inits += [I.multimode_bilayer(n, r0=r, seed=s) for r, s in ((2.2, 5), (2.8, 6), (3.2, 7), (2.5, 8))]
+    for u0 in inits:
+        dts = T.random_steps(rng, args.fno_steps, 1e-3)
+        data += T.samples_from(T.psd_trajectory(n, u0, dts, p), dts)
+    t_data = time.perf_counter() - t0
+    net = fch.FNO(32, 4, 16, 64)
+    net.set_params(T.init_params(net, seed=0))
+    t0 = time.perf_counter()
+    hist = T.train(net, data, args.fno_iters, 8, args.fno_lr, dev)
+    torch.cuda.synchronize()
+    t_train = time.perf_counter() - t0
+    out = {"network": {"width": 32, "layers": 4, "modes": 16, "proj": 64, "params": net.num_params,
+                       "precision": "fp32"},
+           "training": {"grid": n, "samples": len(data), "data_s": t_data, "iterations": args.fno_iters,
+                        "batch": 8, "lr": args.fno_lr, "train_s": t_train, "loss_first": hist[0],
+                        "loss_last10": float(np.mean(hist[-10:]))}}
+
+    def evaluate(m, u0, steps):
+        dts = T.random_steps(np.random.default_rng(99), steps, 1e-3)
+        it_plain, it_fno, e_plain, e_fno = [], [], [], []
+        diffs = []
+        with fch.Context(m, p) as a, fch.Context(m, p) as b:
+            a.set_state(u0)
+            hist_u = [np.array(u0)]
+            for i, dt in enumerate(dts):
+                if i < 2:
+                    a.step("psd", dt)
+                    hist_u.append(a.get_state())
+                    continue
+                g = dt / dts[i - 1]
+                un, um = hist_u[-1], hist_u[-2]
+                ustar = un + g * (un - um)
+                v0, _ = T.learned_start(net, un, ustar, dev)
+                torch.cuda.synchronize()
+                a.step("psd", dt)
+                it_plain.append(a.stats()["last_psd_iter"])
+                # the same BDF2 step (same history) from the learned start
+                b.set_history(un, um, dts[i - 1])
+                b.step_psd_from(dt, v0)
+                it_fno.append(b.stats()["last_psd_iter"])
+                u1 = a.get_state()
+                diffs.append(float(np.linalg.norm(b.get_state() - u1) / np.linalg.norm(u1)))
+                e_plain.append(float(np.linalg.norm(ustar - u1)))
+                e_fno.append(float(np.linalg.norm(v0.cpu().numpy() - u1)))
+                hist_u.append(u1)
+            diff = max(diffs)
+        return {"grid": m, "steps": len(it_plain), "psd_iter_plain": float(np.mean(it_plain)),
+                "psd_iter_fno": float(np.mean(it_fno)),
+                "start_error_ratio": float(np.mean(np.array(e_fno) / np.array(e_plain))),
+                "max_rel_diff_learned_vs_plain": diff}
+
+    out["eval_128"] = evaluate(128, I.circle_bilayer(128, radius=2.1, noise=1e-3, seed=21), 30)
+    out["eval_1024"] = evaluate(1024, I.circle_bilayer(1024, radius=2.1, noise=1e-3, seed=21), 8)
+    # inference time at 1024^2 and the PSD iteration it is traded against
+    a = torch.zeros((1, 2, 1024, 1024), device=dev)
+    y = torch.empty((1, 1024, 1024), device=dev)
+    for _ in range(3):
+        net.forward(a, y)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(10):
+        net.forward(a, y)
+    torch.cuda.synchronize()
+    out["fno_forward_ms_1024"] = (time.perf_counter() - t0) / 10 * 1e3
+    return out
+
+
 def error_budget(args):
     """Single precision against FP64 (and double-float against FP64) per field at
     1024^2 and 2048^2 on the random bilayer network (critical parameters): F(u) of
@@ -776,6 +864,11 @@ def main():
                     help="the 64-instance uneven-grid ensemble against sequential runs instead")
     ap.add_argument("--ensemble-t", type=float, default=0.02)
     ap.add_argument("--ensemble-rounds", type=int, default=8)
+    ap.add_argument("--fno", action="store_true",
+                    help="train the FNO initial iterate and compare PSD started from it instead")
+    ap.add_argument("--fno-steps", type=int, default=60)
+    ap.add_argument("--fno-iters", type=int, default=1500)
+    ap.add_argument("--fno-lr", type=float, default=1e-3)
     ap.add_argument("--error-budget", action="store_true",
                     help="per-field single/double-float vs FP64 errors at 1024^2 and 2048^2 instead")
     ap.add_argument("--budget-steps", type=int, default=200)
@@ -789,6 +882,8 @@ def main():
         out = error_budget(args)
     elif args.ensemble:
         out = ensemble_bench(args)
+    elif args.fno:
+        out = fno_bench(args)
     else:
         out = run_reference(args) if args.impl == "reference" else run_gb300(args)
     if out is not None:

@@ -28,6 +28,12 @@ fch_geom fch_geometry(int N, int prec)
     g.col_blocks = N / (2 * P);
     const int SL = N + N / 8; // skewed sequence length in shared memory
     g.col_smem = (N + 2 * P * SL) * csz;
+    if (N == 1024 && csz == 16) {
+        // two-block clusters, one column of a pair per block, twiddles in global memory
+        g.col_threads = N / 8;
+        g.col_blocks = N;
+        g.col_smem = SL * csz;
+    }
     // rows per block: one at N = 1024 (the compile-time kernel's 128 threads), else
     // 256 threads' worth; the row pass keeps its twiddles in global memory
     const int tps = N / 8;
@@ -45,6 +51,12 @@ fch_geom fch_geometry_tiled(int N, int prec, int tile_row, int tile_col)
 {
     fch_geom g = fch_geometry(N, prec);
     const int csz = prec == 1 ? 8 : 16, SL = N + N / 8;
+    if (tile_col == -1 && N == 1024 && csz == 16) {
+        // the compile-time kernel without clusters: one pair of columns per block
+        g.col_threads = N / 4;
+        g.col_blocks = N / 2;
+        g.col_smem = (N + 2 * SL) * csz;
+    }
     if (tile_col > 0) {
         g.P = tile_col;
         g.col_threads = tile_col * N / 4;
@@ -1435,7 +1447,7 @@ extern "C" fch_status fch_autotune(int n, int prec, void *stream, fch_tile *out)
         int best_t = 0;
         const int cands[] = {0, -1, 1, 2, 4, 8, 16};
         for (int c : cands) {
-            if (c == -1 && !(single && n == 1024)) continue;
+            if (c == -1 && n != 1024) continue;
             if (!fch_tile_valid(n, single, is_col ? 0 : c, is_col ? c : 0)) continue;
             fch_kparams k = kp;
             k.tile_row = is_col ? 0 : c;

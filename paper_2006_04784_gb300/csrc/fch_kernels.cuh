@@ -21,6 +21,7 @@
 // double pipe of this GPU runs at a small fraction of the float rate, so every
 // constant arrives precomputed in the pass precision (fch_consts, fch_coef).
 #pragma once
+#include <cooperative_groups.h>
 #include <math.h>
 #include "fch_ctrl.cuh"
 #include "fch_df.cuh"
@@ -668,6 +669,160 @@ col_pass(const fch_kparams kp)
             const int n = i / nc, cc = i - n * nc;
             Z[(long)n * N + 2 * p0 + cc] = tile[skew(n) * nc + cc];
         }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Column pass for 16-byte elements at N = 1024 as clusters of two blocks: block
+// rank r of cluster p owns column slot r of pair p (r = 0: kx, r = 1: N - kx; pair
+// 0: kx = 0 and N/2), 128 threads, one column in shared memory, twiddles read from
+// global memory. The spectral stage couples the pair's columns (the Hermitian split
+// reads Z(kx, ky) and Z(N - kx, -ky)); each block takes half of the pair's work
+// items and reaches the partner's column through distributed shared memory, with a
+// cluster barrier before (forward transforms done) and after (before the inverse
+// transforms, and before any block may exit while its partner still reads it).
+// 1024 blocks of 128 threads fit seven to an SM: one wave over the 152 SMs at six or
+// seven blocks each, where 512 blocks of a pair each leave a fifth of the SM time idle.
+template <typename T, int MODE>
+__global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(128, 7) col_pass_cl(const fch_kparams kp)
+{
+    typedef typename CT<T>::t C;
+    typedef ColTraits<MODE> TR;
+    namespace cg = cooperative_groups;
+    if (pass_skipped(kp)) return;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    __shared__ double red_scratch[FCH_NRED * 32];
+    constexpr int N = 1024, LOGN = 10, NT = 128;
+    cg::cluster_group cluster = cg::this_cluster();
+    const int rank = (int)cluster.block_rank(), p = blockIdx.x >> 1;
+    C *tile = (C *)smem_raw;                      // own column, skewed
+    C *peer = cluster.map_shared_rank(tile, rank ^ 1); // the partner's column
+    const C *tw = (const C *)kp.tw;
+    const fch_consts<T> &K = consts<T>(kp);
+    const bool inv = TR::INV_ALWAYS || (TR::INV_OPT && (kp.flags & FCH_FL_PACK_F));
+    const bool has_red = MODE == CM_SAV_PQ || MODE == CM_PSD_ITER ||
+                         (MODE == CM_F_FINISH && (kp.flags & FCH_FL_AM3));
+    C *Z = pair_Z<C>(kp, N);
+    const int col = 2 * p + rank; // pair-layout slot of this block's column
+
+    fch_coef<T> co;
+    ColBufs<C> bf;
+    bf.i0 = (const C *)pair_in(kp.in0, kp);
+    bf.i1 = (const C *)pair_in(kp.in1, kp);
+    bf.o0 = (C *)pair_out(kp.out0, kp);
+    bf.o1 = (C *)pair_out(kp.out1, kp);
+    if (kp.ctrl) {
+        const fch_ctrl *cs = kp.ctrl;
+        co = load_coef<T>(cs);
+        bf.Un = (const C *)kp.U[cs->iu_n];
+        bf.Um = (const C *)kp.U[cs->iu_m];
+        bf.Unew = (C *)kp.U[cs->iu_new];
+        bf.Fn = (const C *)kp.F[cs->if_n];
+        bf.Fm = (const C *)kp.F[cs->if_m];
+        switch (kp.src) {
+        case FCH_SRC_UN: bf.src = bf.Un; bf.dst = (C *)kp.F[cs->if_n]; break;
+        case 5: bf.src = bf.Um; bf.dst = (C *)kp.F[cs->if_m]; break;
+        case FCH_SRC_UNEW: bf.src = bf.Unew; bf.dst = (C *)kp.F[cs->if_new]; break;
+        case FCH_SRC_V: bf.src = (const C *)kp.Vb; bf.dst = nullptr; break;
+        default: bf.src = (const C *)kp.in0; bf.dst = (C *)kp.out0; break;
+        }
+    } else {
+        bf.Un = bf.Um = bf.src = bf.Fn = bf.Fm = nullptr;
+        bf.Unew = bf.dst = nullptr;
+        co = fch_coef<T>();
+    }
+
+    if (TR::FWD) {
+        C ld[8];
+#pragma unroll
+        for (int k = 0; k < 8; k++) ld[k] = Z[(long)(threadIdx.x + k * NT) * N + col];
+#pragma unroll
+        for (int k = 0; k < 8; k++) tile[skew(threadIdx.x + k * NT)] = ld[k];
+        fft_smem<-1, true>(tile, N, LOGN, 1, 0, tw, (int)threadIdx.x);
+    }
+    cluster.sync(); // both columns transformed (or, without a forward part, nothing read yet)
+
+    // slot 0 / slot 1 of the pair at skewed row r: own tile or the partner's
+    auto s0 = [&](int r) -> C & { return rank == 0 ? tile[skew(r)] : peer[skew(r)]; };
+    auto s1 = [&](int r) -> C & { return rank == 1 ? tile[skew(r)] : peer[skew(r)]; };
+    T red[FCH_NRED] = {0, 0, 0, 0};
+    if (p > 0) {
+        // items ky in [rank N/2, (rank + 1) N/2): rows ky of slot 0 and -ky of slot 1
+#pragma unroll 1
+        for (int it = 0; it < 4; it++) {
+            const int ky = rank * (N / 2) + threadIdx.x + it * NT;
+            const int mky = (N - ky) & (N - 1);
+            C A = mk<C>(0, 0), B = mk<C>(0, 0);
+            if (TR::FWD) {
+                const C z0 = s0(ky), z1 = cconj(s1(mky));
+                A = cscale_p2(cadd(z0, z1), (T)0.5);
+                const C dm = csub(z0, z1);
+                B = mk<C>(mul_p2(dm.y, (T)0.5), mul_p2(dm.x, (T)-0.5));
+            }
+            C Co = mk<C>(0, 0), Do = mk<C>(0, 0);
+            spec_elem<T, MODE>(kp, K, co, bf, p, ky, A, B, Co, Do, red);
+            if (inv) {
+                s0(ky) = mk<C>(Co.x - Do.y, Co.y + Do.x);
+                s1(mky) = mk<C>(Co.x + Do.y, Do.x - Co.y);
+            }
+        }
+    } else {
+        // pair 0: columns kx = 0 (slot 0) and kx = N/2 (slot 1), items ky in [0, N/2]
+        // (rows ky and -ky of both), even ky to rank 0 and odd ky to rank 1
+#pragma unroll 1
+        for (int ky = rank + 2 * (int)threadIdx.x; ky <= (N >> 1); ky += 2 * NT) {
+            const int mky = (N - ky) & (N - 1);
+            const int nrow = (ky == 0 || ky == (N >> 1)) ? 1 : 2;
+            C za[2], zb[2];
+            za[0] = s0(ky);
+            za[1] = s0(mky);
+            zb[0] = s1(ky);
+            zb[1] = s1(mky);
+            C outa[2], outb[2];
+#pragma unroll
+            for (int side = 0; side < 2; side++) {
+                const int kx = side ? (N >> 1) : 0;
+#pragma unroll
+                for (int rr = 0; rr < 2; rr++) {
+                    if (rr >= nrow) break;
+                    const int kyy = rr ? mky : ky;
+                    const C zr = side ? zb[rr] : za[rr];
+                    const C zo = side ? zb[rr ^ 1] : za[rr ^ 1];
+                    C A = mk<C>(0, 0), B = mk<C>(0, 0);
+                    if (TR::FWD) {
+                        const C z1 = cconj(zo);
+                        A = cscale_p2(cadd(zr, z1), (T)0.5);
+                        const C dm = csub(zr, z1);
+                        B = mk<C>(mul_p2(dm.y, (T)0.5), mul_p2(dm.x, (T)-0.5));
+                    }
+                    C Co = mk<C>(0, 0), Do = mk<C>(0, 0);
+                    spec_elem<T, MODE>(kp, K, co, bf, kx, kyy, A, B, Co, Do, red);
+                    const C o = mk<C>(Co.x - Do.y, Co.y + Do.x);
+                    if (side)
+                        outb[rr] = o;
+                    else
+                        outa[rr] = o;
+                }
+            }
+            if (inv) {
+                s0(ky) = outa[0];
+                s1(ky) = outb[0];
+                if (nrow == 2) {
+                    s0(mky) = outa[1];
+                    s1(mky) = outb[1];
+                }
+            }
+        }
+    }
+    if (has_red) {
+        block_partials<2>(red, kp.part, red_scratch);
+        if (kp.tail_op >= 0) pass_tail(kp);
+    }
+    cluster.sync(); // every write into the partner's column is done and visible
+    if (inv) {
+        fft_smem<+1, true>(tile, N, LOGN, 1, 0, tw, (int)threadIdx.x);
+#pragma unroll
+        for (int k = 0; k < 8; k++) Z[(long)(threadIdx.x + k * NT) * N + col] = tile[skew(threadIdx.x + k * NT)];
     }
 }
 

@@ -70,13 +70,29 @@ template <int M> cudaError_t launch_row_w(const fch_kparams &kp, cudaStream_t s)
 }
 
 // Tiles (fch_kparams::tile_col, tile_row): 0 takes the warp-level passes where they
-// exist (single precision, N = 1024), else the compile-time kernel of the grid size
-// where one is built, else the generic kernel; -1 the same without the warp-level
-// passes; > 0 the generic kernel with that many column pairs (rows) per block. The
-// generic column kernel reads P from kp.P, which the caller sets to the tile's.
+// exist (single precision, N = 1024), the two-block-cluster column pass for double
+// and double-float at N = 1024, else the compile-time kernel of the grid size where
+// one is built, else the generic kernel; -1 the same without the warp-level passes
+// and the clusters; > 0 the generic kernel with that many column pairs (rows) per
+// block. The generic column kernel reads P from kp.P, which the caller sets.
+// double and double-float at N = 1024: the column pass as clusters of two blocks
+template <typename T, int M> cudaError_t launch_col_cl(const fch_kparams &kp, cudaStream_t s)
+{
+    static int attr = 0;
+    const int smem = fch::skewed_len(1024) * 16;
+    pass_fn f = fch::col_pass_cl<T, M>;
+    cudaError_t e = set_smem(f, smem, 0, attr);
+    if (e != cudaSuccess) return e;
+    f<<<dim3(1024, pair_grid(kp)), 128, smem, s>>>(kp);
+    return cudaGetLastError();
+}
+
 template <typename T, int M> cudaError_t launch_col(const fch_kparams &kp, cudaStream_t s)
 {
     if (warp_path<T>() && kp.N == 1024 && kp.tw2 && kp.tile_col == 0) return launch_col_w<M>(kp, s);
+    if constexpr (sizeof(T) == 8) {
+        if (kp.N == 1024 && kp.tile_col == 0) return launch_col_cl<T, M>(kp, s);
+    }
     static int attr[12] = {};
     const fch_geom g = fch_geometry_tiled(kp.N, sizeof(T) == 4, 0, kp.tile_col);
     const int li = (kp.tile_col <= 0 && kp.logN >= 9 && kp.logN <= 11) ? kp.logN : 0;

@@ -45,12 +45,16 @@ def test_status_strings():
 def test_geometry_covers_grid(n, prec):
     g = fch.geometry(n, prec)
     csz = 8 if prec else 16
-    # column pass: P pairs per block, 2P sequences of N/8 threads, all N/2 pairs covered
-    assert g["col_blocks"] * g["P"] == n // 2
-    assert g["col_threads"] == 2 * g["P"] * (n // 8) and g["col_threads"] <= 1024
-    assert g["col_threads"] % 32 == 0
     sl = n + n // 8  # skewed sequence length
-    assert g["col_smem"] == (n + 2 * g["P"] * sl) * csz and g["col_smem"] <= 227 * 1024
+    if n == 1024 and csz == 16:
+        # two-block clusters: one column of each pair per block of N/8 threads
+        assert g["col_blocks"] == n and g["col_threads"] == n // 8 and g["col_smem"] == sl * csz
+    else:
+        # column pass: P pairs per block, 2P sequences of N/8 threads, all N/2 pairs covered
+        assert g["col_blocks"] * g["P"] == n // 2
+        assert g["col_threads"] == 2 * g["P"] * (n // 8) and g["col_threads"] <= 1024
+        assert g["col_smem"] == (n + 2 * g["P"] * sl) * csz and g["col_smem"] <= 227 * 1024
+    assert g["col_threads"] % 32 == 0
     # row pass: rpb rows of N/8 threads, all N rows covered
     assert g["row_blocks"] * g["rpb"] == n
     assert g["row_threads"] == g["rpb"] * (n // 8) and g["row_threads"] <= 256

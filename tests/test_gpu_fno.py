@@ -108,3 +108,43 @@ def test_psd_step_from_a_given_iterate():
         b.step_psd_from(dt, torch.tensor(plain, device=DEV))
         assert b.stats()["last_psd_iter"] <= 2 < it_plain
         assert rel(b.get_state(), plain) < 1e-10
+
+
+def test_trained_fno_start_beats_the_extrapolation():
+    # train a small FNO on PSD trajectories at 64^2 (the library's own steps), then on
+    # a held-out trajectory the learned start must be closer to the PSD fixed point
+    # than u*, reach the same fixed point, and need no more iterations on average
+    from paper_2006_04784_gb300 import fno_train as T
+
+    n = 64
+    p = fch.params_default(0.0, psd_itol=1e-10)
+    rng = np.random.default_rng(5)
+    data = []
+    for r, s in ((1.6, 1), (2.0, 2), (2.4, 3), (2.8, 4)):
+        dts = T.random_steps(rng, 50, 1e-3)
+        data += T.samples_from(T.psd_trajectory(n, I.circle_bilayer(n, radius=r, noise=1e-3, seed=s), dts, p), dts)
+    net = fch.FNO(16, 2, 8, 32)
+    net.set_params(T.init_params(net, seed=0))
+    hist = T.train(net, data, 800, 8, 2e-3, DEV)
+    assert np.mean(hist[-20:]) < 0.2 * np.mean(hist[:20])
+    dts = T.random_steps(np.random.default_rng(9), 20, 1e-3)
+    u = [I.circle_bilayer(n, radius=2.2, noise=1e-3, seed=7)]
+    ratios, it_p, it_f = [], [], []
+    with fch.Context(n, p) as a, fch.Context(n, p) as b:
+        a.set_state(u[0])
+        for i, dt in enumerate(dts):
+            if i >= 2:
+                ustar = u[-1] + dt / dts[i - 1] * (u[-1] - u[-2])
+                v0, _ = T.learned_start(net, u[-1], ustar, DEV)
+            a.step("psd", dt)
+            u.append(a.get_state())
+            if i >= 2:
+                it_p.append(a.stats()["last_psd_iter"])
+                b.set_history(u[-2], u[-3], dts[i - 1])
+                b.step_psd_from(dt, v0)
+                it_f.append(b.stats()["last_psd_iter"])
+                assert rel(b.get_state(), u[-1]) < 1e-8
+                assert b.mass() == pytest.approx(a.mass(), rel=1e-12)
+                ratios.append(np.linalg.norm(v0.cpu().numpy() - u[-1]) / np.linalg.norm(ustar - u[-1]))
+    assert np.mean(ratios) < 0.8
+    assert np.mean(it_f) <= np.mean(it_p)
