@@ -162,6 +162,14 @@ fch_status fch_get_state_device(fch_ctx *ctx, void *u_dev, int dtype);
  * PSD waits after every few iterations to test convergence. */
 fch_status fch_step(fch_ctx *ctx, fch_scheme scheme, double dt);
 
+/* nsteps fixed steps of size dt, as nsteps fch_step calls, without host work
+ * between them: after the first step, one step captured as a CUDA graph is replayed
+ * (IMEX, SAV, ETD; PSD, whose stopping test runs on the host, and contexts with
+ * per-pass timing on take fch_step calls). Enqueued; a failure inside the steps
+ * (non-finite values) shows at the next call that reads the control block
+ * (fch_synchronize, fch_get_stats, fch_get_state). */
+fch_status fch_run_fixed(fch_ctx *ctx, fch_scheme scheme, double dt, long long nsteps);
+
 /* E(u^n) of eq. (Functional), FP64 accumulation (waits for the stream). */
 fch_status fch_energy(fch_ctx *ctx, double *E);
 

@@ -233,6 +233,9 @@ struct fch_ctx {
     // graph replays any trial; PSD (host convergence test) is not captured
     cudaGraphExec_t trial_graph[4];
     bool trial_warm[4], trial_nograph[4];
+    // one fixed step (step size fixed_dt[s]) of IMEX, SAV, ETD captured as a CUDA graph
+    cudaGraphExec_t fixed_graph[4];
+    double fixed_dt[4];
     // per-pass event timing
     bool timing;
     int nev;
@@ -648,8 +651,10 @@ extern "C" fch_status fch_destroy(fch_ctx *ctx)
         if (b) cudaFree(b);
     if (ctx->timing)
         for (int i = 0; i < 2 * 2048; i++) cudaEventDestroy(ctx->ev[i]);
-    for (int i = 0; i < 4; i++)
+    for (int i = 0; i < 4; i++) {
         if (ctx->trial_graph[i]) cudaGraphExecDestroy(ctx->trial_graph[i]);
+        if (ctx->fixed_graph[i]) cudaGraphExecDestroy(ctx->fixed_graph[i]);
+    }
     if (ctx->own_stream && ctx->stream) cudaStreamDestroy(ctx->stream);
     free(ctx);
     return FCH_OK;
@@ -839,6 +844,60 @@ extern "C" fch_status fch_step(fch_ctx *ctx, fch_scheme scheme, double dt)
 }
 
 // F of the state in slot src into its F slot (src: FCH_SRC_UN -> F(u^n), 5 -> F(u^{n-1}))
+// one fixed step without host checks: control set-up, the scheme's step, acceptance
+static fch_status enqueue_fixed_step(fch_ctx *ctx, fch_scheme scheme, double dt)
+{
+    TRY(ctl(ctx, OP_INIT_TRIAL, 0, dt));
+    TRY(enqueue_trial(ctx, scheme, false));
+    TRY(ctl(ctx, OP_ACCEPT, 0, 0.0));
+    return FCH_OK;
+}
+
+extern "C" fch_status fch_run_fixed(fch_ctx *ctx, fch_scheme scheme, double dt, long long nsteps)
+{
+    if (!ctx || !(dt > 0) || nsteps < 0 || scheme < FCH_IMEX || scheme > FCH_ETD) return FCH_EINVAL;
+    if (!ctx->have_state || ctx->failed) return FCH_ESTATE;
+    if (nsteps == 0) return FCH_OK;
+    // PSD tests convergence on the host; with per-pass timing every launch is timed
+    if (scheme == FCH_PSD || ctx->timing) {
+        for (long long i = 0; i < nsteps; i++) TRY(fch_step(ctx, scheme, dt));
+        return FCH_OK;
+    }
+    ctx->rvalid = false;
+    ctx->have_F = false;
+    // the first step runs eagerly (it also sets the kernels' attributes)
+    fch_status s = enqueue_fixed_step(ctx, scheme, dt);
+    if (s != FCH_OK) {
+        ctx->failed = true;
+        return s;
+    }
+    if (nsteps == 1) return FCH_OK;
+    if (ctx->fixed_graph[scheme] && ctx->fixed_dt[scheme] != dt) {
+        cudaGraphExecDestroy(ctx->fixed_graph[scheme]);
+        ctx->fixed_graph[scheme] = nullptr;
+    }
+    if (!ctx->fixed_graph[scheme]) {
+        cudaGraph_t g = nullptr;
+        bool ok = cudaStreamBeginCapture(ctx->stream, cudaStreamCaptureModeRelaxed) == cudaSuccess;
+        if (ok) {
+            s = enqueue_fixed_step(ctx, scheme, dt);
+            ok = cudaStreamEndCapture(ctx->stream, &g) == cudaSuccess && g && s == FCH_OK;
+        }
+        if (ok) ok = cudaGraphInstantiate(&ctx->fixed_graph[scheme], g, 0) == cudaSuccess;
+        if (g) cudaGraphDestroy(g);
+        if (!ok) {
+            // no graph: the remaining steps launch one kernel at a time
+            cudaGetLastError();
+            ctx->fixed_graph[scheme] = nullptr;
+            for (long long i = 1; i < nsteps; i++) TRY(enqueue_fixed_step(ctx, scheme, dt));
+            return FCH_OK;
+        }
+        ctx->fixed_dt[scheme] = dt;
+    }
+    for (long long i = 1; i < nsteps; i++) CKC(ctx, cudaGraphLaunch(ctx->fixed_graph[scheme], ctx->stream));
+    return FCH_OK;
+}
+
 extern "C" fch_status fch_step_psd_from(fch_ctx *ctx, double dt, const void *v0, int dtype)
 {
     if (!ctx || !(dt > 0) || !v0 || (dtype != 0 && dtype != 1)) return FCH_EINVAL;

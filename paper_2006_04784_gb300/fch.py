@@ -33,7 +33,7 @@ EXPORTS = ["fch_status_string", "fch_last_cuda_error", "fch_params_default", "fc
            "fch_ensemble_create", "fch_ensemble_destroy", "fch_ensemble_member",
            "fch_ensemble_run_adaptive", "fch_fno_create", "fch_fno_destroy", "fch_fno_num_params",
            "fch_fno_set_params", "fch_fno_get_params", "fch_fno_get_grads", "fch_fno_forward",
-           "fch_fno_backward", "fch_fno_adam", "fch_step_psd_from"]
+           "fch_fno_backward", "fch_fno_adam", "fch_step_psd_from", "fch_run_fixed"]
 NCOL, NROW = 10, 8
 NPASS = NCOL + NROW + 1
 PASS_NAMES = (["col_fwd_store", "col_inv_load", "col_start", "col_imex_solve", "col_f_finish",
@@ -138,6 +138,7 @@ def lib():
         L.fch_fno_backward.argtypes = [vp, vp, C.POINTER(C.c_double)]
         L.fch_fno_adam.argtypes = [vp, C.c_float, C.c_float, C.c_float, C.c_float]
         L.fch_step_psd_from.argtypes = [vp, C.c_double, vp, C.c_int]
+        L.fch_run_fixed.argtypes = [vp, C.c_int, C.c_double, C.c_longlong]
         L.fch_ensemble_member.argtypes = [vp, C.c_int, C.POINTER(vp)]
         L.fch_ensemble_run_adaptive.argtypes = [vp, C.c_int, C.c_double, C.c_double, C.c_int, C.c_longlong,
                                                 C.POINTER(Stats)]
@@ -291,6 +292,11 @@ class Context:
     def step(self, scheme, dt: float):
         s = SCHEMES[scheme] if isinstance(scheme, str) else int(scheme)
         self._ck(lib().fch_step(self._h, s, float(dt)), "fch_step")
+
+    def run_fixed(self, scheme, dt: float, nsteps: int):
+        """nsteps fixed steps (a captured step replayed after the first)"""
+        s = SCHEMES[scheme] if isinstance(scheme, str) else int(scheme)
+        self._ck(lib().fch_run_fixed(self._h, s, float(dt), int(nsteps)), "fch_run_fixed")
 
     def step_psd_from(self, dt: float, v0):
         """one PSD-BDF2 step whose iteration starts from the device field v0"""

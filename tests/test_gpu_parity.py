@@ -215,6 +215,27 @@ def test_one_step_from_identical_history(scheme, prec):
         assert rel(ctx.get_state(), s.state()) < 1e-12
 
 
+@pytest.mark.parametrize("prec", [0, 2])
+@pytest.mark.parametrize("scheme", ["imex", "sav", "etd", "psd"])
+def test_run_fixed_equals_single_steps(scheme, prec):
+    # graph-replayed fixed steps launch the same kernels as fch_step calls
+    n = 64
+    p = lib_params(0.0, prec=prec)
+    u0 = I.circle_bilayer(n, noise=1e-3)
+    with fch.Context(n, p) as a, fch.Context(n, p) as b:
+        a.set_state(u0)
+        b.set_state(u0)
+        for _ in range(12):
+            a.step(scheme, 2e-4)
+        b.run_fixed(scheme, 2e-4, 12)
+        assert np.array_equal(a.get_state(), b.get_state())
+        assert a.stats()["n_steps"] == b.stats()["n_steps"] == 12
+        b.run_fixed(scheme, 1e-4, 3)  # another step size: a new graph
+        for _ in range(3):
+            a.step(scheme, 1e-4)
+        assert np.array_equal(a.get_state(), b.get_state())
+
+
 def test_imex_128_fixed_dt_400_steps():
     # the 128^2 fixed-step workload: circle of radius 2, d = 0.2, noise 1e-3 (seed 1)
     n = 128
