@@ -100,13 +100,37 @@ bool fch_tile_valid(int N, int prec, int tile_row, int tile_col)
 // control kernel: one block of 256 threads running ctrl_block
 __global__ void __launch_bounds__(256) fch_ctrl_kernel(const fch_kparams kp, int op, int na, double arg0)
 {
+    pdl_begin();
     ctrl_block(kp, op, na, arg0);
 }
 
 cudaError_t fch_launch_ctrl(int op, const fch_kparams &kp, int na, int, double arg0, cudaStream_t s)
 {
-    fch_ctrl_kernel<<<1, 256, 0, s>>>(kp, op, na, arg0);
-    return cudaGetLastError();
+    cudaLaunchConfig_t cfg = {};
+    cudaLaunchAttribute at[1];
+    fch_pdl_config(cfg, at, dim3(1), dim3(256), 0, s);
+    return cudaLaunchKernelEx(&cfg, fch_ctrl_kernel, kp, op, na, arg0);
+}
+
+// launch configuration of a pass or control kernel: programmatic stream
+// serialization (see pdl_begin), unless FCH_NO_PDL is set in the environment
+bool fch_pdl_enabled()
+{
+    static const bool on = getenv("FCH_NO_PDL") == nullptr;
+    return on;
+}
+
+void fch_pdl_config(cudaLaunchConfig_t &cfg, cudaLaunchAttribute *at, dim3 grid, dim3 block, size_t smem,
+                    cudaStream_t s)
+{
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = fch_pdl_enabled() ? 1 : 0;
 }
 
 // ---------------------------------------------------------------------------

@@ -9,6 +9,18 @@
 #include "fch_internal.h"
 #include "../../include/fch.h"
 
+// Programmatic dependent launch: the passes and the control kernel are launched
+// with programmatic stream serialization, so a launch may begin while its
+// predecessor in the stream drains. Every kernel first waits for the predecessor to
+// complete (its writes visible), before it reads anything, then allows its own
+// successor to begin launching; the successor's blocks wait in turn. Launched
+// without the attribute, both instructions return at once.
+__device__ __forceinline__ void pdl_begin()
+{
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+
 // Double-precision reciprocal and sixth root from single-precision seeds and
 // Newton steps (two steps take a 1e-7 seed to full double precision). This
 // GPU's double pipe is slow and the controller runs on one thread, so the

@@ -163,6 +163,10 @@ cudaError_t fch_launch_col_f32(int mode, const fch_kparams &kp, cudaStream_t s);
 cudaError_t fch_launch_row_f32(int mode, const fch_kparams &kp, cudaStream_t s);
 cudaError_t fch_launch_col_dfl(int mode, const fch_kparams &kp, cudaStream_t s);
 cudaError_t fch_launch_row_dfl(int mode, const fch_kparams &kp, cudaStream_t s);
+// launch configuration with programmatic stream serialization (when enabled)
+bool fch_pdl_enabled();
+void fch_pdl_config(cudaLaunchConfig_t &cfg, cudaLaunchAttribute *at, dim3 grid, dim3 block, size_t smem,
+                    cudaStream_t s);
 cudaError_t fch_launch_ctrl(int op, const fch_kparams &kp, int nblk_a, int nblk_b, double arg0,
                             cudaStream_t s);
 

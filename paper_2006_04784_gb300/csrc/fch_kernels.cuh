@@ -522,6 +522,7 @@ col_pass(const fch_kparams kp)
 {
     typedef typename CT<T>::t C;
     typedef ColTraits<MODE> TR;
+    pdl_begin();
     if (pass_skipped(kp)) return;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ double red_scratch[FCH_NRED * 32];
@@ -689,6 +690,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(128, 7) col_pass_cl(
     typedef typename CT<T>::t C;
     typedef ColTraits<MODE> TR;
     namespace cg = cooperative_groups;
+    pdl_begin();
     if (pass_skipped(kp)) return;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ double red_scratch[FCH_NRED * 32];
@@ -845,6 +847,7 @@ __global__ void __launch_bounds__(LOGN ? row_threads<LOGN>() : 256, LOGN ? row_m
 row_pass(const fch_kparams kp)
 {
     typedef typename CT<T>::t C;
+    pdl_begin();
     if (pass_skipped(kp)) return;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ double red_scratch[FCH_NRED * 32];

@@ -7,6 +7,15 @@ namespace {
 
 typedef void (*pass_fn)(const fch_kparams);
 
+// launch a pass with programmatic stream serialization (fch_pdl_config)
+inline cudaError_t launch_pass(pass_fn f, dim3 grid, dim3 block, size_t smem, cudaStream_t s, const fch_kparams &kp)
+{
+    cudaLaunchConfig_t cfg = {};
+    cudaLaunchAttribute at[1];
+    fch_pdl_config(cfg, at, grid, block, smem, s);
+    return cudaLaunchKernelEx(&cfg, f, kp);
+}
+
 // grid y: the field pairs of a batched standalone transform (one otherwise)
 inline unsigned pair_grid(const fch_kparams &kp) { return kp.npairs > 1 ? (unsigned)kp.npairs : 1u; }
 
@@ -59,14 +68,12 @@ template <int M> cudaError_t launch_col_w(const fch_kparams &kp, cudaStream_t s)
     pass_fn f = fch::col_pass_w<M>;
     cudaError_t e = set_smem(f, smem, 0, attr);
     if (e != cudaSuccess) return e;
-    f<<<dim3(256, pair_grid(kp)), 128, smem, s>>>(kp);
-    return cudaGetLastError();
+    return launch_pass(f, dim3(256, pair_grid(kp)), dim3(128), smem, s, kp);
 }
 
 template <int M> cudaError_t launch_row_w(const fch_kparams &kp, cudaStream_t s)
 {
-    fch::row_pass_w<M><<<dim3(1024, pair_grid(kp)), 32, 0, s>>>(kp);
-    return cudaGetLastError();
+    return launch_pass(fch::row_pass_w<M>, dim3(1024, pair_grid(kp)), dim3(32), 0, s, kp);
 }
 
 // Tiles (fch_kparams::tile_col, tile_row): 0 takes the warp-level passes where they
@@ -83,8 +90,7 @@ template <typename T, int M> cudaError_t launch_col_cl(const fch_kparams &kp, cu
     pass_fn f = fch::col_pass_cl<T, M>;
     cudaError_t e = set_smem(f, smem, 0, attr);
     if (e != cudaSuccess) return e;
-    f<<<dim3(1024, pair_grid(kp)), 128, smem, s>>>(kp);
-    return cudaGetLastError();
+    return launch_pass(f, dim3(1024, pair_grid(kp)), dim3(128), smem, s, kp);
 }
 
 template <typename T, int M> cudaError_t launch_col(const fch_kparams &kp, cudaStream_t s)
@@ -99,8 +105,7 @@ template <typename T, int M> cudaError_t launch_col(const fch_kparams &kp, cudaS
     pass_fn f = col_fn<T, M>(li);
     cudaError_t e = set_smem(f, g.col_smem, fch_geometry(FCH_MAX_N, sizeof(T) == 4).col_smem, attr[li]);
     if (e != cudaSuccess) return e;
-    f<<<dim3(g.col_blocks, pair_grid(kp)), g.col_threads, g.col_smem, s>>>(kp);
-    return cudaGetLastError();
+    return launch_pass(f, dim3(g.col_blocks, pair_grid(kp)), dim3(g.col_threads), g.col_smem, s, kp);
 }
 
 template <typename T, int M> cudaError_t launch_row(const fch_kparams &kp, cudaStream_t s)
@@ -112,8 +117,7 @@ template <typename T, int M> cudaError_t launch_row(const fch_kparams &kp, cudaS
     pass_fn f = row_fn<T, M>(li);
     cudaError_t e = set_smem(f, g.row_smem, fch_geometry(FCH_MAX_N, sizeof(T) == 4).row_smem, attr[li]);
     if (e != cudaSuccess) return e;
-    f<<<dim3(g.row_blocks, pair_grid(kp)), g.row_threads, g.row_smem, s>>>(kp);
-    return cudaGetLastError();
+    return launch_pass(f, dim3(g.row_blocks, pair_grid(kp)), dim3(g.row_threads), g.row_smem, s, kp);
 }
 
 } // namespace

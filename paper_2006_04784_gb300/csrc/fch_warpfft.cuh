@@ -117,6 +117,7 @@ template <int MODE>
 __global__ void __launch_bounds__(32) row_pass_w(const fch_kparams kp)
 {
     typedef float2 C;
+    pdl_begin();
     if (pass_skipped(kp)) return;
     constexpr int N = 1024;
     __shared__ __align__(16) C buf[33 * 32];
@@ -228,6 +229,7 @@ __global__ void __launch_bounds__(128) col_pass_w(const fch_kparams kp)
 {
     typedef float2 C;
     typedef ColTraits<MODE> TR;
+    pdl_begin();
     if (pass_skipped(kp)) return;
     constexpr int N = 1024, P = 2, RS = 5, NT = 128; // 2P = 4 columns, rows padded to 5
     extern __shared__ __align__(16) unsigned char smem_raw[];
