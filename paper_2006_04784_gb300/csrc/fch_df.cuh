@@ -67,7 +67,7 @@ __device__ __forceinline__ df fast_two_sum(float a, float b)
 // The operators renormalise the sum (add_norm, 11 operations). add_lazy / sub_lazy
 // leave it unrenormalised (8 operations): |lo| may exceed ulp(hi)/2, and after a
 // cancellation of the high parts it may exceed |hi|; the transform butterflies use
-// them and renormalise once where a stage stores (renorm restores |lo| <= ulp(hi)/2
+// them and renormalise once where a transform ends (renorm restores |lo| <= ulp(hi)/2
 // where |hi| >= |lo|, renorm_exact in every case). Whatever reads only the high
 // word -- division, reciprocal, comparisons, signs -- renormalises its operands
 // first with renorm_exact.

@@ -75,7 +75,7 @@ template <typename C, typename S> __device__ __forceinline__ C cscale_p2(C a, S 
 }
 // Butterfly arithmetic: the plain complex operations for float and double; for
 // double-float the unrenormalised sums and twiddle product of fch_df.cuh, with
-// bnorm() renormalising where a transform stage stores its results.
+// bnorm() renormalising where the last transform stage stores its results.
 template <typename R> __device__ __forceinline__ R radd(R a, R b) { return a + b; }
 template <typename R> __device__ __forceinline__ R rsub(R a, R b) { return a - b; }
 template <> __device__ __forceinline__ df radd(df a, df b) { return add_lazy(a, b); }
@@ -153,6 +153,9 @@ __device__ __forceinline__ void fft_stage(C *s, int N, int logN, int stride, int
     constexpr int R = 1 << LR;
     constexpr int NB = 8 / R;
     const int tps = N >> 3, nb = N >> LR;
+    // double-float values stay unrenormalised between stages (the sums and twiddle
+    // products take such operands); the last stage renormalises what it stores
+    const bool last = (Ns << LR) == N;
     C v[8];
 #pragma unroll
     for (int b = 0; b < NB; b++) {
@@ -188,7 +191,8 @@ __device__ __forceinline__ void fft_stage(C *s, int N, int logN, int stride, int
         const int j = t + b * tps;
         const int idxD = ((j >> lNs) << (lNs + LR)) + (j & (Ns - 1));
 #pragma unroll
-        for (int r = 0; r < R; r++) s[skew(idxD + r * Ns) * stride + off] = bnorm(v[b * R + r]);
+        for (int r = 0; r < R; r++)
+            s[skew(idxD + r * Ns) * stride + off] = last ? bnorm(v[b * R + r]) : v[b * R + r];
     }
     __syncthreads();
 }
