@@ -243,14 +243,15 @@ __device__ inline void ctrl_block(const fch_kparams &kp, int op, int na, double 
     const int nw = (int)(sizeof(fch_ctrl) / 8);
     const int nthr = blockDim.x;
     for (int i = threadIdx.x; i < nw; i += nthr) ((long long *)&cs)[i] = ((const long long *)kp.ctrl)[i];
-    __syncthreads();
-    if (cs.done && !(kp.flags & FCH_FL_NOSKIP)) return;
-    if (op == OP_PSD_CHECK && cs.psd_conv) return;
+    // the partial sums load while the control block arrives (discarded if it says done)
     double s0 = 0, s1 = 0;
     for (int i = threadIdx.x; i < na; i += nthr) {
         s0 += kp.part[i];
         s1 += kp.part[FCH_MAXBLK + i];
     }
+    __syncthreads();
+    if (cs.done && !(kp.flags & FCH_FL_NOSKIP)) return;
+    if (op == OP_PSD_CHECK && cs.psd_conv) return;
     for (int o = 16; o > 0; o >>= 1) {
         s0 += __shfl_down_sync(0xffffffffu, s0, o);
         s1 += __shfl_down_sync(0xffffffffu, s1, o);
