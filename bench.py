@@ -346,8 +346,8 @@ def time_to_t_final(fch, I, n, t_final=0.02):
 def fft_throughput(fch, dev, n=N_GRID, batch=32, iters=10, warmup=3):
     """Standalone 2D real transforms at n^2 (fch_fft_r2c then fch_fft_c2r over a
     batch of fields, inputs larger than L2) against cuFFT through torch.fft
-    (rfft2 / irfft2 of the same batch), FP64 and FP32. One transform = one field
-    one way. Roofline per transform: compulsory bytes (read the field or spectrum,
+    (rfft2 / irfft2 of the same batch), FP64 and FP32, with the tiles fch_autotune
+    picks for (n, precision). One transform = one field one way. Roofline per transform: compulsory bytes (read the field or spectrum,
     write the other) against HBM, and 2.5 n^2 log2(n^2) flops against the FP64
     pipe for FP64."""
     import torch
@@ -360,6 +360,7 @@ def fft_throughput(fch, dev, n=N_GRID, batch=32, iters=10, warmup=3):
         X = torch.empty(batch, n // 2 + 1, n, dtype=torch.complex128 if rdt == torch.float64 else torch.complex64,
                         device=dev)
         y = torch.empty_like(x)
+        fch.autotune(n, prec)  # plans take the tuned tiles of (n, precision)
         plan = fch.FFTPlan(n, prec, stream=stream)
 
         def ours():
@@ -527,6 +528,23 @@ def _rel(a, b):
     return float(np.linalg.norm(a - b) / np.linalg.norm(b))
 
 
+def cfg1_cpu_baseline(n, u0, p):
+    """CPU baseline of the 128^2 fixed-step run: the oracle (single-threaded FP64 C)
+    takes the same 400 IMEX steps; returns its timing and final state."""
+    from oracle import oracle as O
+
+    O.build()
+    s = O.Stepper(n, 4 * math.pi, O.params(eps=p.eps, q=p.q, gamma=p.gamma, eta1=p.eta1, eta2=p.eta2,
+                                            zeta=p.zeta, D0=p.D0))
+    s.set_state(u0)
+    t0 = time.perf_counter()
+    for _ in range(400):
+        s.step("imex", 1e-3)
+    wall = time.perf_counter() - t0
+    return {"kind": "oracle", "wall_s": wall, "steps_per_s": 400 / wall, "cores": 1,
+            "sample": "the full 400 steps"}, s.state()
+
+
 def workloads(args):
     """The other configurations of the hot path, measured end to end through the C ABI
     (wall time of the calls, device work included):
@@ -575,20 +593,11 @@ def workloads(args):
                           "steps_per_s_one_call_per_step": 400 / wall, "u": ctx.get_state(),
                           "graph_equals_calls": bool(np.array_equal(ctx.get_state(), u_calls))}
     try:
-        from oracle import oracle as O
-        O.build()
-        p = P()
-        s = O.Stepper(n, 4 * math.pi, O.params(eps=p.eps, q=p.q, gamma=p.gamma, eta1=p.eta1, eta2=p.eta2,
-                                                zeta=p.zeta, D0=p.D0))
-        s.set_state(u0)
-        t0 = time.perf_counter()
-        for _ in range(400):
-            s.step("imex", 1e-3)
-        cfg1["oracle"] = {"wall_s": time.perf_counter() - t0, "cores": 1}
+        cfg1["cpu_baseline"], u_ref = cfg1_cpu_baseline(n, u0, P())
         for name in ("fp64", "fp32x2"):
-            cfg1[name]["rel_l2_vs_oracle"] = _rel(cfg1[name]["u"], s.state())
-    except Exception as e:  # the oracle is a baseline only
-        cfg1["oracle"] = {"error": str(e)}
+            cfg1[name]["rel_l2_vs_cpu_baseline"] = _rel(cfg1[name]["u"], u_ref)
+    except Exception as e:  # a baseline only
+        cfg1["cpu_baseline"] = {"error": str(e)}
     for name in ("fp64", "fp32x2"):
         cfg1[name].pop("u")
     out["cfg1_128_fixed_dt"] = cfg1

@@ -415,7 +415,10 @@ __device__ __forceinline__ void spec_elem(const fch_kparams &kp, const fch_const
         // eq. (IMEX-eq): (a + |k|^2 s) u^{n+1} = -b u^n - c u^{n-1} - |k|^2 N_IMEX(u*)^
         const C Nh = csub(A, cscale(B, K.e2 * k2));
         const C rhs = csub(cscale(ldg(bf.Un + idx), -co.b), cadd(cscale(ldg(bf.Um + idx), co.c), cscale(Nh, k2)));
-        v = cscale(rhs, recip(co.a + k2 * sk));
+        // the mean mode (k = 0) carries the mass: divide there, where a bias of the
+        // one-Newton-step reciprocal would repeat every step and accumulate
+        const T den = co.a + k2 * sk;
+        v = k2 == (T)0 ? mk<C>(rhs.x / den, rhs.y / den) : cscale(rhs, recip(den));
         bf.Unew[idx] = v;
         pack = kp.flags & FCH_FL_PACK_F;
     } else if (MODE == CM_F_FINISH) {
@@ -441,8 +444,10 @@ __device__ __forceinline__ void spec_elem(const fch_kparams &kp, const fch_const
         const C us = co.gam != (T)0 ? cadd(un, cscale(csub(un, um), co.gam)) : un;
         const T l0 = K.e4 * k2 * k2 + K.b1am_e2 * k2 + K.b2am2;
         const T l1 = -K.l1c * k2 - K.b1am_e2 * k2 - K.b2am2;
-        const T iden = recip(co.a + k2 * l0);
-        const C p = cscale(csub(cscale(un, -co.b), cadd(cscale(um, co.c), cscale(us, k2 * l1))), iden);
+        const T den = co.a + k2 * l0;
+        const T iden = recip(den);
+        const C pr = csub(cscale(un, -co.b), cadd(cscale(um, co.c), cscale(us, k2 * l1)));
+        const C p = k2 == (T)0 ? mk<C>(pr.x / den, pr.y / den) : cscale(pr, iden); // mean mode: as above
         const C q = cscale(X, -k2 * iden);
         ((C *)kp.Pb)[idx] = p;
         ((C *)kp.Qb)[idx] = q;

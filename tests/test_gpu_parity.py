@@ -290,6 +290,22 @@ def test_adaptive_vs_oracle(scheme, prec):
         assert rel(ctx.get_state(), s.state()) < 1e-9
 
 
+@pytest.mark.parametrize("prec", [0, 2])
+@pytest.mark.parametrize("scheme", ["imex", "sav"])
+def test_long_adaptive_run_conserves_mass(scheme, prec):
+    # thousands of adaptive steps: the mean mode (the mass) may only carry rounding
+    # of no systematic sign; a per-step bias of 2^-48 would add up to ~1e-11
+    n = 64
+    p = lib_params(0.0, zero_stab_cap=1, prec=prec)
+    u0 = I.paper_initial_data(n, 0.5)
+    with fch.Context(n, p) as ctx:
+        ctx.set_state(u0)
+        m0 = ctx.mass()
+        st = ctx.run_adaptive(scheme, 1e-6, 2.0)
+        assert st["n_steps"] > 1000
+        assert abs(ctx.mass() - m0) / m0 < (1e-12 if prec == 0 else 3e-12)
+
+
 def test_adaptive_attempt_budget_and_resume():
     n = 32
     p = lib_params(0.0)
