@@ -89,10 +89,11 @@ typedef struct {
                           * 2: warp-transform passes where available (FCH_MIXED, N = 1024) */
     int autotune;        /* 1: fch_create takes the tiles fch_autotune picks for (n, prec)
                           * (timing them on first use in the process); 0: tile_row/tile_col */
-    int tile_row, tile_col; /* pass tiles: 0 default (warp-level passes for FCH_MIXED and
-                          * two-block-cluster column passes for FCH_FP64 / FCH_FP32X2 at
-                          * n = 1024, else the kernel built for the grid size); -1 the
-                          * shared-memory kernels without those; r > 0 the generic row
+    int tile_row, tile_col; /* pass tiles: 0 default (at n = 1024 two-block-cluster
+                          * column passes for FCH_FP64 / FCH_FP32X2, warp-level row passes
+                          * for FCH_MIXED; else the kernel built for the grid size); -1 the shared-memory
+                          * kernels without those; -2 (tile_col, FCH_MIXED at n = 1024) the
+                          * warp-level column passes; r > 0 the generic row
                           * kernel with r rows per block / the generic column kernel with
                           * r column pairs per block (powers of two that fit the row
                           * kernel's 256 threads or the column kernel's 1024 threads a
@@ -289,7 +290,8 @@ fch_status fch_step_psd_from(fch_ctx *ctx, double dt, const void *v0_dev, int dt
  * array) and the forward column pass (work array -> two half spectra) of one field
  * pair at n x n in precision prec, for each candidate tile: the default, the
  * plain shared-memory kernels at n = 1024 (where the default is the warp-level path
- * or the two-block clusters), and the generic kernels at 1, 2, 4, 8, 16 rows (column pairs) per
+ * or the two-block clusters), the warp-level column passes (FCH_MIXED, n = 1024), and
+ * the generic kernels at 1, 2, 4, 8, 16 rows (column pairs) per
  * block that fit. It allocates and frees its own scratch arrays on the given
  * stream (NULL: the legacy default stream), synchronizes it, and keeps the fastest
  * tiles per (n, prec) for the process: later calls return them without timing,

@@ -51,11 +51,15 @@ fch_geom fch_geometry_tiled(int N, int prec, int tile_row, int tile_col)
 {
     fch_geom g = fch_geometry(N, prec);
     const int csz = prec == 1 ? 8 : 16, SL = N + N / 8;
-    if (tile_col == -1 && N == 1024 && csz == 16) {
-        // the compile-time kernel without clusters: one pair of columns per block
-        g.col_threads = N / 4;
-        g.col_blocks = N / 2;
-        g.col_smem = (N + 2 * SL) * csz;
+    if ((tile_col == -1 || tile_col == -2) && N == 1024) {
+        // without clusters: the compile-time kernel (-1) with 1 (16-byte) or 2 (8-byte)
+        // column pairs per block, or the warp-level kernel (-2, single precision) with
+        // two pairs per block
+        const int P = csz == 16 ? 1 : 2;
+        g.P = P;
+        g.col_threads = tile_col == -2 ? 128 : P * N / 4;
+        g.col_blocks = N / (2 * P);
+        g.col_smem = tile_col == -2 ? (N * 5 + 4 * 33 * 32) * csz : (N + 2 * P * SL) * csz;
     }
     if (tile_col > 0) {
         g.P = tile_col;
@@ -90,7 +94,7 @@ bool fch_tile_valid(int N, int prec, int tile_row, int tile_col)
         if ((tile_col & (tile_col - 1)) || tile_col < pmin || tile_col > N / 2) return false;
         const fch_geom g = fch_geometry_tiled(N, prec, 0, tile_col);
         if (g.col_threads > 1024 || g.col_smem > smem_max) return false;
-    } else if (tile_col < -1) {
+    } else if (tile_col < -2 || (tile_col == -2 && !(prec == 1 && N == 1024))) {
         return false;
     }
     return true;
@@ -593,6 +597,8 @@ extern "C" fch_status fch_create(const fch_grid *g, const fch_params *p, void *s
         ctx->own_stream = true;
     }
     int trow = p->tile_row, tcol = p->tile_col;
+    // fft_path 2 asks for the warp-level passes where they exist (single precision, 1024^2)
+    if (p->fft_path == 2 && p->prec == FCH_MIXED && g->n == 1024 && tcol == 0) tcol = -2;
     if (e == cudaSuccess && p->autotune) {
         fch_tile t;
         const fch_status ts = fch_autotune(N, ctx->prec, ctx->stream, &t);
@@ -1528,9 +1534,9 @@ extern "C" fch_status fch_autotune(int n, int prec, void *stream, fch_tile *out)
     for (int is_col = 0; is_col < 2 && e == cudaSuccess; is_col++) {
         double best_us = 1e30, def_us = 0;
         int best_t = 0;
-        const int cands[] = {0, -1, 1, 2, 4, 8, 16};
+        const int cands[] = {0, -1, -2, 1, 2, 4, 8, 16};
         for (int c : cands) {
-            if (c == -1 && n != 1024) continue;
+            if (c < 0 && n != 1024) continue;
             if (!fch_tile_valid(n, single, is_col ? 0 : c, is_col ? c : 0)) continue;
             fch_kparams k = kp;
             k.tile_row = is_col ? 0 : c;

@@ -418,7 +418,7 @@ __device__ __forceinline__ void spec_elem(const fch_kparams &kp, const fch_const
         // the mean mode (k = 0) carries the mass: divide there, where a bias of the
         // one-Newton-step reciprocal would repeat every step and accumulate
         const T den = co.a + k2 * sk;
-        v = k2 == (T)0 ? mk<C>(rhs.x / den, rhs.y / den) : cscale(rhs, recip(den));
+        v = (kx | ky) == 0 ? mk<C>(rhs.x / den, rhs.y / den) : cscale(rhs, recip(den));
         bf.Unew[idx] = v;
         pack = kp.flags & FCH_FL_PACK_F;
     } else if (MODE == CM_F_FINISH) {
@@ -447,7 +447,7 @@ __device__ __forceinline__ void spec_elem(const fch_kparams &kp, const fch_const
         const T den = co.a + k2 * l0;
         const T iden = recip(den);
         const C pr = csub(cscale(un, -co.b), cadd(cscale(um, co.c), cscale(us, k2 * l1)));
-        const C p = k2 == (T)0 ? mk<C>(pr.x / den, pr.y / den) : cscale(pr, iden); // mean mode: as above
+        const C p = (kx | ky) == 0 ? mk<C>(pr.x / den, pr.y / den) : cscale(pr, iden); // mean mode: as above
         const C q = cscale(X, -k2 * iden);
         ((C *)kp.Pb)[idx] = p;
         ((C *)kp.Qb)[idx] = q;

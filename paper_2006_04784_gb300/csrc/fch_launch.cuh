@@ -76,17 +76,18 @@ template <int M> cudaError_t launch_row_w(const fch_kparams &kp, cudaStream_t s)
     return launch_pass(fch::row_pass_w<M>, dim3(1024, pair_grid(kp)), dim3(32), 0, s, kp);
 }
 
-// Tiles (fch_kparams::tile_col, tile_row): 0 takes the warp-level passes where they
-// exist (single precision, N = 1024), the two-block-cluster column pass for double
-// and double-float at N = 1024, else the compile-time kernel of the grid size where
-// one is built, else the generic kernel; -1 the same without the warp-level passes
-// and the clusters; > 0 the generic kernel with that many column pairs (rows) per
-// block. The generic column kernel reads P from kp.P, which the caller sets.
-// double and double-float at N = 1024: the column pass as clusters of two blocks
+// Tiles (fch_kparams::tile_col, tile_row): 0 takes the two-block-cluster column pass
+// for double and double-float at N = 1024, the warp-level row pass for single
+// precision at N = 1024, else the compile-time kernel of the grid size where one is
+// built, else the generic kernel; -1 the same without the clusters and the warp-level
+// rows; -2 (columns, single precision at N = 1024) the warp-level column pass; > 0 the
+// generic kernel with that many column pairs (rows) per block. The generic column
+// kernel reads P from kp.P, which the caller sets.
+// N = 1024, double and double-float: the column pass as clusters of two blocks
 template <typename T, int M> cudaError_t launch_col_cl(const fch_kparams &kp, cudaStream_t s)
 {
     static int attr = 0;
-    const int smem = fch::skewed_len(1024) * 16;
+    const int smem = fch::skewed_len(1024) * (int)sizeof(typename fch::CT<T>::t);
     pass_fn f = fch::col_pass_cl<T, M>;
     cudaError_t e = set_smem(f, smem, 0, attr);
     if (e != cudaSuccess) return e;
@@ -95,13 +96,15 @@ template <typename T, int M> cudaError_t launch_col_cl(const fch_kparams &kp, cu
 
 template <typename T, int M> cudaError_t launch_col(const fch_kparams &kp, cudaStream_t s)
 {
-    if (warp_path<T>() && kp.N == 1024 && kp.tw2 && kp.tile_col == 0) return launch_col_w<M>(kp, s);
+    if (warp_path<T>() && kp.N == 1024 && kp.tw2 && kp.tile_col == -2) return launch_col_w<M>(kp, s);
     if constexpr (sizeof(T) == 8) {
         if (kp.N == 1024 && kp.tile_col == 0) return launch_col_cl<T, M>(kp, s);
     }
     static int attr[12] = {};
-    const fch_geom g = fch_geometry_tiled(kp.N, sizeof(T) == 4, 0, kp.tile_col);
-    const int li = (kp.tile_col <= 0 && kp.logN >= 9 && kp.logN <= 11) ? kp.logN : 0;
+    // the warp-level tile without its table (a context made with fft_path = 1) is -1
+    const int tc = kp.tile_col == -2 ? -1 : kp.tile_col;
+    const fch_geom g = fch_geometry_tiled(kp.N, sizeof(T) == 4, 0, tc);
+    const int li = (tc <= 0 && kp.logN >= 9 && kp.logN <= 11) ? kp.logN : 0;
     pass_fn f = col_fn<T, M>(li);
     cudaError_t e = set_smem(f, g.col_smem, fch_geometry(FCH_MAX_N, sizeof(T) == 4).col_smem, attr[li]);
     if (e != cudaSuccess) return e;

@@ -90,6 +90,11 @@ def test_tiles_cover_grid(n, prec):
     assert nvalid >= 1
     assert fch.tile_geometry(n, prec, 0, 0)[0] and fch.tile_geometry(n, prec, -1, -1)[0]
     assert not fch.tile_geometry(n, prec, 3, 0)[0] and not fch.tile_geometry(n, prec, -2, 0)[0]
+    # the warp-level column passes exist for single precision at 1024^2 only
+    ok, g = fch.tile_geometry(n, prec, 0, -2)
+    assert ok == (prec == 1 and n == 1024)
+    if ok:
+        assert g["col_blocks"] == n // 4 and g["col_threads"] == 128
 
 
 def test_stockham_index_map_is_a_permutation():

@@ -68,12 +68,13 @@ def test_forced_tiles_match_oracle(n, prec, tiles):
 
 
 def test_forced_tiles_mixed_1024_warp_and_shared_memory():
-    # single precision at 1024^2: warp-level passes (default), shared-memory kernels
-    # (-1) and a generic tile agree with each other to single-precision rounding
+    # single precision at 1024^2: the default (warp-level rows), the shared-memory
+    # kernels (-1), a generic tile and the warp-level columns (-2) agree with each
+    # other to single-precision rounding
     n = 1024
     u0 = I.random_network(n, d=0.75, seed=3)
     out = {}
-    for tiles in ((0, 0), (-1, -1), (2, 4)):
+    for tiles in ((0, 0), (-1, -1), (2, 4), (0, -2)):
         with fch.Context(n, lib_params(eta2=0.15, prec=1, tile_row=tiles[0], tile_col=tiles[1])) as ctx:
             ctx.set_state(u0)
             for _ in range(3):
@@ -81,6 +82,7 @@ def test_forced_tiles_mixed_1024_warp_and_shared_memory():
             out[tiles] = ctx.get_state()
     assert rel(out[(-1, -1)], out[(0, 0)]) < 3e-5
     assert rel(out[(2, 4)], out[(-1, -1)]) < 3e-5
+    assert rel(out[(0, -2)], out[(0, 0)]) < 3e-5
 
 
 @pytest.mark.parametrize("n,prec", [(256, 0), (1024, 1), (1024, 2)])
