@@ -285,6 +285,20 @@ fch_status fch_fno_adam(fch_fno *f, float lr, float beta1, float beta2, float ep
  * tolerance. */
 fch_status fch_step_psd_from(fch_ctx *ctx, double dt, const void *v0_dev, int dtype);
 
+/* Adaptive PSD runs with a caller-given first iterate per trial (the same trial as
+ * fch_adaptive_enqueue: PSD iteration, F of the trial, AM3 estimate, decision):
+ *  - fch_adaptive_trial_info: after fch_adaptive_begin or a trial, the next trial's
+ *    step size k and gamma = k/k_n (0 for a backward-Euler start), and whether the run
+ *    is done (t_final reached or a failure); synchronizes the context's stream;
+ *  - fch_get_history_device: u^n and u^{n-1} as real n x n fields (dtype as
+ *    fch_get_state_device), from which the caller forms u* = u^n + gamma (u^n - u^{n-1});
+ *  - fch_adaptive_enqueue_psd_from: one trial whose PSD iteration starts from v0 (a
+ *    real field with the mass of u*, as fch_step_psd_from). FCH_ESTATE unless an
+ *    adaptive PSD run is open. */
+fch_status fch_adaptive_trial_info(fch_ctx *ctx, double *k_trial, double *gamma, int *done);
+fch_status fch_get_history_device(fch_ctx *ctx, void *un_dev, void *unm1_dev, int dtype);
+fch_status fch_adaptive_enqueue_psd_from(fch_ctx *ctx, const void *v0_dev, int dtype);
+
 /* ---- pass tiles (the paper has no counterpart: a GPU launch choice) ----
  * fch_autotune times the forward row pass (two real fields -> pair-layout work
  * array) and the forward column pass (work array -> two half spectra) of one field

@@ -928,6 +928,42 @@ extern "C" fch_status fch_run_fixed(fch_ctx *ctx, fch_scheme scheme, double dt, 
     return FCH_OK;
 }
 
+extern "C" fch_status fch_get_history_device(fch_ctx *ctx, void *un_dev, void *unm1_dev, int dtype)
+{
+    if (!ctx || !un_dev || !unm1_dev || (dtype != 0 && dtype != 1)) return FCH_EINVAL;
+    if (!ctx->have_state) return FCH_ESTATE;
+    TRY(col(ctx, CM_START, FCH_SRC_UN, FCH_FL_NOSKIP));
+    TRY(row(ctx, RM_C2R_STORE, FCH_FL_NOSKIP | (dtype == 0 ? FCH_FL_F64IO : 0), nullptr, un_dev));
+    TRY(col(ctx, CM_START, 5, FCH_FL_NOSKIP)); // u^{n-1}
+    TRY(row(ctx, RM_C2R_STORE, FCH_FL_NOSKIP | (dtype == 0 ? FCH_FL_F64IO : 0), nullptr, unm1_dev));
+    return FCH_OK;
+}
+
+extern "C" fch_status fch_adaptive_trial_info(fch_ctx *ctx, double *k_trial, double *gamma, int *done)
+{
+    if (!ctx || !k_trial || !gamma || !done) return FCH_EINVAL;
+    if (!ctx->ad_open) return FCH_ESTATE;
+    TRY(pull_ctrl(ctx));
+    *done = ctx->hc.done || ctx->hc.status;
+    *k_trial = ctx->hc.k1;
+    *gamma = ctx->hc.kn > 0 ? ctx->hc.gam : 0.0;
+    return ctx->hc.status ? (fch_status)ctx->hc.status : FCH_OK;
+}
+
+extern "C" fch_status fch_adaptive_enqueue_psd_from(fch_ctx *ctx, const void *v0, int dtype)
+{
+    if (!ctx || !v0 || (dtype != 0 && dtype != 1)) return FCH_EINVAL;
+    if (!ctx->ad_open || ctx->failed || ctx->ad_scheme != FCH_PSD) return FCH_ESTATE;
+    TRY(load_field(ctx, v0, dtype == 0, ctx->Vb));
+    TRY(col(ctx, CM_START, FCH_SRC_V));
+    fch_status s = psd_iterate(ctx);
+    if (s == FCH_OK) s = row(ctx, RM_F, FCH_FL_STORE_REAL, nullptr, nullptr, -1, 0.0, FCH_SRC_UNEW);
+    if (s == FCH_OK) s = col(ctx, CM_F_FINISH, FCH_SRC_UNEW, FCH_FL_AM3);
+    if (s == FCH_OK) s = ctl(ctx, OP_DECIDE_INIT, ctx->geom.col_blocks);
+    if (s != FCH_OK) ctx->failed = true;
+    return s;
+}
+
 extern "C" fch_status fch_step_psd_from(fch_ctx *ctx, double dt, const void *v0, int dtype)
 {
     if (!ctx || !(dt > 0) || !v0 || (dtype != 0 && dtype != 1)) return FCH_EINVAL;

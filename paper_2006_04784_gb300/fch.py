@@ -33,7 +33,8 @@ EXPORTS = ["fch_status_string", "fch_last_cuda_error", "fch_params_default", "fc
            "fch_ensemble_create", "fch_ensemble_destroy", "fch_ensemble_member",
            "fch_ensemble_run_adaptive", "fch_fno_create", "fch_fno_destroy", "fch_fno_num_params",
            "fch_fno_set_params", "fch_fno_get_params", "fch_fno_get_grads", "fch_fno_forward",
-           "fch_fno_backward", "fch_fno_adam", "fch_step_psd_from", "fch_run_fixed"]
+           "fch_fno_backward", "fch_fno_adam", "fch_step_psd_from", "fch_run_fixed",
+           "fch_adaptive_trial_info", "fch_get_history_device", "fch_adaptive_enqueue_psd_from"]
 NCOL, NROW = 10, 8
 NPASS = NCOL + NROW + 1
 PASS_NAMES = (["col_fwd_store", "col_inv_load", "col_start", "col_imex_solve", "col_f_finish",
@@ -139,6 +140,10 @@ def lib():
         L.fch_fno_adam.argtypes = [vp, C.c_float, C.c_float, C.c_float, C.c_float]
         L.fch_step_psd_from.argtypes = [vp, C.c_double, vp, C.c_int]
         L.fch_run_fixed.argtypes = [vp, C.c_int, C.c_double, C.c_longlong]
+        L.fch_adaptive_trial_info.argtypes = [vp, C.POINTER(C.c_double), C.POINTER(C.c_double),
+                                              C.POINTER(C.c_int)]
+        L.fch_get_history_device.argtypes = [vp, vp, vp, C.c_int]
+        L.fch_adaptive_enqueue_psd_from.argtypes = [vp, vp, C.c_int]
         L.fch_ensemble_member.argtypes = [vp, C.c_int, C.POINTER(vp)]
         L.fch_ensemble_run_adaptive.argtypes = [vp, C.c_int, C.c_double, C.c_double, C.c_int, C.c_longlong,
                                                 C.POINTER(Stats)]
@@ -297,6 +302,21 @@ class Context:
         """nsteps fixed steps (a captured step replayed after the first)"""
         s = SCHEMES[scheme] if isinstance(scheme, str) else int(scheme)
         self._ck(lib().fch_run_fixed(self._h, s, float(dt), int(nsteps)), "fch_run_fixed")
+
+    def adaptive_trial_info(self):
+        """(k, gamma, done) of the next trial of the open adaptive run"""
+        k, g, d = C.c_double(), C.c_double(), C.c_int()
+        self._ck(lib().fch_adaptive_trial_info(self._h, C.byref(k), C.byref(g), C.byref(d)),
+                 "fch_adaptive_trial_info")
+        return k.value, g.value, bool(d.value)
+
+    def get_history_device(self, un, unm1):
+        self._ck(lib().fch_get_history_device(self._h, _tensor_ptr(un), _tensor_ptr(unm1), _dtype_code(un)),
+                 "fch_get_history_device")
+
+    def adaptive_enqueue_psd_from(self, v0):
+        self._ck(lib().fch_adaptive_enqueue_psd_from(self._h, _tensor_ptr(v0), _dtype_code(v0)),
+                 "fch_adaptive_enqueue_psd_from")
 
     def step_psd_from(self, dt: float, v0):
         """one PSD-BDF2 step whose iteration starts from the device field v0"""

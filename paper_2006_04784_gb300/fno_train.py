@@ -109,3 +109,31 @@ def learned_start(net, un, ustar, device):
     yc = y[0].double()
     v0 = torch.tensor(ustar, device=device) + s * (yc - yc.mean())
     return v0.contiguous(), y[0].cpu().numpy()
+
+
+def run_adaptive_psd(ctx, sigma, t_final, device, net=None, max_trials=100000):
+    """The adaptive PSD-BDF2 run of Sec. 3.2 trial by trial, each PSD iteration started
+    from u* (net None) or from the network's v_0; returns (stats, trials)."""
+    import torch
+
+    n = ctx.n
+    ctx.adaptive_begin("psd", sigma, t_final)
+    un = torch.empty((n, n), dtype=torch.float64, device=device)
+    um = torch.empty_like(un)
+    trials = 0
+    while trials < max_trials:
+        k, g, done = ctx.adaptive_trial_info()
+        if done:
+            break
+        if net is None or g == 0.0:
+            ctx.adaptive_enqueue(1)
+        else:
+            ctx.get_history_device(un, um)
+            ctx.synchronize()
+            a = un.cpu().numpy()
+            ustar = a + g * (a - um.cpu().numpy())
+            v0, _ = learned_start(net, a, ustar, device)
+            torch.cuda.synchronize()
+            ctx.adaptive_enqueue_psd_from(v0)
+        trials += 1
+    return ctx.adaptive_end(), trials

@@ -110,10 +110,9 @@ def test_psd_step_from_a_given_iterate():
         assert rel(b.get_state(), plain) < 1e-10
 
 
-def test_trained_fno_start_beats_the_extrapolation():
-    # train a small FNO on PSD trajectories at 64^2 (the library's own steps), then on
-    # a held-out trajectory the learned start must be closer to the PSD fixed point
-    # than u*, reach the same fixed point, and need no more iterations on average
+@pytest.fixture(scope="module")
+def small_trained_net():
+    # a small FNO trained on PSD trajectories at 64^2 (the library's own steps)
     from paper_2006_04784_gb300 import fno_train as T
 
     n = 64
@@ -126,7 +125,18 @@ def test_trained_fno_start_beats_the_extrapolation():
     net = fch.FNO(16, 2, 8, 32)
     net.set_params(T.init_params(net, seed=0))
     hist = T.train(net, data, 800, 8, 2e-3, DEV)
+    return net, hist
+
+
+def test_trained_fno_start_beats_the_extrapolation(small_trained_net):
+    # on a held-out trajectory the learned start must be closer to the PSD fixed point
+    # than u*, reach the same fixed point, and need no more iterations on average
+    from paper_2006_04784_gb300 import fno_train as T
+
+    net, hist = small_trained_net
     assert np.mean(hist[-20:]) < 0.2 * np.mean(hist[:20])
+    n = 64
+    p = fch.params_default(0.0, psd_itol=1e-10)
     dts = T.random_steps(np.random.default_rng(9), 20, 1e-3)
     u = [I.circle_bilayer(n, radius=2.2, noise=1e-3, seed=7)]
     ratios, it_p, it_f = [], [], []
@@ -148,3 +158,25 @@ def test_trained_fno_start_beats_the_extrapolation():
                 ratios.append(np.linalg.norm(v0.cpu().numpy() - u[-1]) / np.linalg.norm(ustar - u[-1]))
     assert np.mean(ratios) < 0.8
     assert np.mean(it_f) <= np.mean(it_p)
+
+
+def test_adaptive_psd_with_learned_start(small_trained_net):
+    # the adaptive PSD run of Sec. 3.2 trial by trial: started from u* and from the
+    # network's v_0, both reach t_final, agree to the PSD tolerance and conserve mass
+    from paper_2006_04784_gb300 import fno_train as T
+
+    net, _ = small_trained_net
+    n = 64
+    p = fch.params_default(0.0, zero_stab_cap=1)
+    u0 = I.circle_bilayer(n, radius=2.2, noise=1e-3, seed=7)
+    out = {}
+    for name, use in (("plain", None), ("learned", net)):
+        with fch.Context(n, p) as ctx:
+            ctx.set_state(u0)
+            m0 = ctx.mass()
+            st, trials = T.run_adaptive_psd(ctx, 1e-5, 5e-3, DEV, net=use)
+            assert st["t"] == pytest.approx(5e-3, rel=1e-12) and trials > 5
+            assert abs(ctx.mass() - m0) < 1e-12 * abs(m0)
+            out[name] = (st, ctx.get_state())
+    assert rel(out["learned"][1], out["plain"][1]) < 1e-6
+    assert out["learned"][0]["n_psd_iter"] <= 1.05 * out["plain"][0]["n_psd_iter"]
