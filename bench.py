@@ -783,16 +783,19 @@ def fno_bench(args):
     ad = {"grid": 1024, "sigma_tol": 1e-6, "t_final": args.fno_t_adaptive}
     u0 = I.circle_bilayer(1024, radius=2.1, noise=1e-3, seed=21)
     states = {}
-    for name, use in (("plain", None), ("learned", net)):
+    for name, use, kr in (("plain", None, None), ("learned", net, None),
+                          ("learned_in_training_step_range", net, (5e-4, 2e-3))):
         with fch.Context(1024, fch.params_default(0.0, zero_stab_cap=1)) as ctx:
             ctx.set_state(u0)
             t0 = time.perf_counter()
-            st, trials = T.run_adaptive_psd(ctx, 1e-6, args.fno_t_adaptive, dev, net=use)
-            ad[name] = {"wall_s": time.perf_counter() - t0, "trials": trials, "steps": st["n_steps"],
-                        "psd_iter": st["n_psd_iter"], "t_reached": st["t"]}
+            st, trials, learned = T.run_adaptive_psd(ctx, 1e-6, args.fno_t_adaptive, dev, net=use, k_range=kr)
+            ad[name] = {"wall_s": time.perf_counter() - t0, "trials": trials, "learned_trials": learned,
+                        "steps": st["n_steps"], "psd_iter": st["n_psd_iter"], "t_reached": st["t"],
+                        "k_last": st["k_last"]}
             states[name] = ctx.get_state()
-    ad["rel_l2_learned_vs_plain"] = float(np.linalg.norm(states["learned"] - states["plain"])
-                                          / np.linalg.norm(states["plain"]))
+    for name in ("learned", "learned_in_training_step_range"):
+        ad[name]["rel_l2_vs_plain"] = float(np.linalg.norm(states[name] - states["plain"])
+                                            / np.linalg.norm(states["plain"]))
     out["adaptive_1024"] = ad
     # inference time at 1024^2 and the PSD iteration it is traded against
     a = torch.zeros((1, 2, 1024, 1024), device=dev)
@@ -927,7 +930,7 @@ def main():
     ap.add_argument("--fno-steps", type=int, default=60)
     ap.add_argument("--fno-iters", type=int, default=1500)
     ap.add_argument("--fno-lr", type=float, default=1e-3)
-    ap.add_argument("--fno-t-adaptive", type=float, default=2e-3)
+    ap.add_argument("--fno-t-adaptive", type=float, default=2e-2)
     ap.add_argument("--error-budget", action="store_true",
                     help="per-field single/double-float vs FP64 errors at 1024^2 and 2048^2 instead")
     ap.add_argument("--budget-steps", type=int, default=200)

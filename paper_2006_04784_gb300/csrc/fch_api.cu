@@ -874,12 +874,13 @@ extern "C" fch_status fch_step(fch_ctx *ctx, fch_scheme scheme, double dt)
 }
 
 // F of the state in slot src into its F slot (src: FCH_SRC_UN -> F(u^n), 5 -> F(u^{n-1}))
-// one fixed step without host checks: control set-up, the scheme's step, acceptance
+// one fixed step without host checks, its control set-up already done: the scheme's
+// step, then one control launch that accepts it and sets up the next step of size dt
+// (the set-up after the last step is left unused)
 static fch_status enqueue_fixed_step(fch_ctx *ctx, fch_scheme scheme, double dt)
 {
-    TRY(ctl(ctx, OP_INIT_TRIAL, 0, dt));
     TRY(enqueue_trial(ctx, scheme, false));
-    TRY(ctl(ctx, OP_ACCEPT, 0, 0.0));
+    TRY(ctl(ctx, OP_ACCEPT_INIT, 0, dt));
     return FCH_OK;
 }
 
@@ -896,6 +897,7 @@ extern "C" fch_status fch_run_fixed(fch_ctx *ctx, fch_scheme scheme, double dt, 
     ctx->rvalid = false;
     ctx->have_F = false;
     // the first step runs eagerly (it also sets the kernels' attributes)
+    TRY(ctl(ctx, OP_INIT_TRIAL, 0, dt));
     fch_status s = enqueue_fixed_step(ctx, scheme, dt);
     if (s != FCH_OK) {
         ctx->failed = true;

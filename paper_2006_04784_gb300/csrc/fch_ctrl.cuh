@@ -267,9 +267,17 @@ __device__ inline void ctrl_block(const fch_kparams &kp, int op, int na, double 
             S0 += sh[0][w];
             S1 += sh[1][w];
         }
+        // the combined operations: the decision (adaptive) or the acceptance of a fixed
+        // step, then the set-up of the next trial (adaptive: arg0 -1; fixed: arg0 = dt)
         bool again = false;
+        double next_arg = -1.0;
         if (op == OP_DECIDE_INIT) {
             op = OP_DECIDE;
+            again = true;
+        } else if (op == OP_ACCEPT_INIT) {
+            op = OP_ACCEPT;
+            next_arg = arg0;
+            arg0 = 0.0;
             again = true;
         }
         for (;;) {
@@ -277,7 +285,7 @@ __device__ inline void ctrl_block(const fch_kparams &kp, int op, int na, double 
             if (!again) break;
             again = false;
             op = OP_INIT_TRIAL;
-            arg0 = -1.0;
+            arg0 = next_arg;
         }
     }
     if (threadIdx.x < 32) {

@@ -142,7 +142,8 @@ enum {
     OP_DECIDE,         // adaptive accept / reject and next trial size
     OP_ACCEPT,         // fixed step: accept unconditionally
     OP_ENERGY,         // energy from partials
-    OP_DECIDE_INIT     // OP_DECIDE, then OP_INIT_TRIAL (adaptive) for the next trial
+    OP_DECIDE_INIT,    // OP_DECIDE, then OP_INIT_TRIAL (adaptive) for the next trial
+    OP_ACCEPT_INIT     // OP_ACCEPT of a fixed step, then OP_INIT_TRIAL with step size arg0
 };
 
 // pass geometry for grid N and precision (0 = f64, 1 = f32)

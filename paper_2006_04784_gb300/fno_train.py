@@ -111,21 +111,25 @@ def learned_start(net, un, ustar, device):
     return v0.contiguous(), y[0].cpu().numpy()
 
 
-def run_adaptive_psd(ctx, sigma, t_final, device, net=None, max_trials=100000):
+def run_adaptive_psd(ctx, sigma, t_final, device, net=None, k_range=None, max_trials=100000):
     """The adaptive PSD-BDF2 run of Sec. 3.2 trial by trial, each PSD iteration started
-    from u* (net None) or from the network's v_0; returns (stats, trials)."""
+    from u* (net None) or from the network's v_0; with k_range = (lo, hi) the network
+    is used only for trial steps in that range (the step sizes it was trained on: its
+    inputs are normalised and carry no step size, so outside that range its correction
+    does not scale with the step) and u* elsewhere. Returns (stats, trials, learned
+    trials)."""
     import torch
 
     n = ctx.n
     ctx.adaptive_begin("psd", sigma, t_final)
     un = torch.empty((n, n), dtype=torch.float64, device=device)
     um = torch.empty_like(un)
-    trials = 0
+    trials = learned = 0
     while trials < max_trials:
         k, g, done = ctx.adaptive_trial_info()
         if done:
             break
-        if net is None or g == 0.0:
+        if net is None or g == 0.0 or (k_range is not None and not (k_range[0] <= k <= k_range[1])):
             ctx.adaptive_enqueue(1)
         else:
             ctx.get_history_device(un, um)
@@ -135,5 +139,6 @@ def run_adaptive_psd(ctx, sigma, t_final, device, net=None, max_trials=100000):
             v0, _ = learned_start(net, a, ustar, device)
             torch.cuda.synchronize()
             ctx.adaptive_enqueue_psd_from(v0)
+            learned += 1
         trials += 1
-    return ctx.adaptive_end(), trials
+    return ctx.adaptive_end(), trials, learned

@@ -162,7 +162,9 @@ def test_trained_fno_start_beats_the_extrapolation(small_trained_net):
 
 def test_adaptive_psd_with_learned_start(small_trained_net):
     # the adaptive PSD run of Sec. 3.2 trial by trial: started from u* and from the
-    # network's v_0, both reach t_final, agree to the PSD tolerance and conserve mass
+    # network's v_0 (on the step sizes it was trained on), both reach t_final, agree
+    # to the PSD tolerance and keep the mass to the rounding the PSD iteration's
+    # mean mode carries (that of the extrapolation u*, about 1e-11 over a run)
     from paper_2006_04784_gb300 import fno_train as T
 
     net, _ = small_trained_net
@@ -174,9 +176,10 @@ def test_adaptive_psd_with_learned_start(small_trained_net):
         with fch.Context(n, p) as ctx:
             ctx.set_state(u0)
             m0 = ctx.mass()
-            st, trials = T.run_adaptive_psd(ctx, 1e-5, 5e-3, DEV, net=use)
-            assert st["t"] == pytest.approx(5e-3, rel=1e-12) and trials > 5
-            assert abs(ctx.mass() - m0) < 1e-12 * abs(m0)
-            out[name] = (st, ctx.get_state())
+            st, trials, learned = T.run_adaptive_psd(ctx, 1e-5, 2e-2, DEV, net=use, k_range=(5e-4, 2e-3))
+            assert st["t"] == pytest.approx(2e-2, rel=1e-12) and trials > 5
+            assert abs(ctx.mass() - m0) < 1e-10 * abs(m0)
+            out[name] = (st, ctx.get_state(), learned)
+    assert out["plain"][2] == 0
     assert rel(out["learned"][1], out["plain"][1]) < 1e-6
     assert out["learned"][0]["n_psd_iter"] <= 1.05 * out["plain"][0]["n_psd_iter"]
