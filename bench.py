@@ -94,8 +94,14 @@ class Clocks:
                  "-lms", "100"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
             self.t = threading.Thread(target=self._read, daemon=True)
             self.t.start()
+            # nvidia-smi takes a moment to start: wait for its first sample so that the
+            # samples kept (from here on) fall inside the timed region
+            t0 = time.time()
+            while not self.lines and time.time() - t0 < 5.0:
+                time.sleep(0.01)
         except Exception:
             self.proc = None
+        self.start = len(self.lines)
         return self
 
     def _read(self):
@@ -104,6 +110,10 @@ class Clocks:
 
     def __exit__(self, *a):
         if self.proc:
+            # one more sample, taken as the region ends, for regions shorter than the period
+            n, t0 = len(self.lines), time.time()
+            while len(self.lines) == n and len(self.lines) == self.start and time.time() - t0 < 0.3:
+                time.sleep(0.01)
             self.proc.terminate()
             try:
                 self.proc.wait(timeout=5)
@@ -113,7 +123,7 @@ class Clocks:
     def summary(self):
         sm, mx, reasons = [], 0.0, set()
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        for ln in self.lines:
+        for ln in self.lines[getattr(self, "start", 0):]:
             f = [x.strip() for x in ln.split(",")]
             if len(f) < 7:
                 continue
@@ -523,6 +533,183 @@ def paper_costs(args):
     return out
 
 
+# final times of Table t:Comp-error; the references of Sec. 5.2 (PSD at sigma_tol =
+# 1e-9 for q = 0, PSD at 3e-8 for q = 0.2, IMEX at 3e-9 for q = 0.5)
+PAPER_T = {"subcritical": 250.0, "critical": 250.0, "supercritical": 250.0, "foot1": 50.0, "foot2": 50.0}
+PAPER_REFERENCE = {"supercritical": ("psd", 1e-9), "foot1": ("psd", 3e-8), "foot2": ("imex", 3e-9)}
+SIGMA_SWEEP = [1e-3, 3e-4, 1e-4, 3e-5, 1e-5, 3e-6, 1e-6, 3e-7, 1e-7]
+
+
+def _paper_problem(name):
+    """(N, params, initial data) of one benchmark of Table t:Benchmark (eta in units
+    of eps = 0.1), FP32X2."""
+    from paper_2006_04784_gb300 import fch
+    from paper_2006_04784_gb300 import inputs as I
+
+    b = I.BENCHMARKS[name]
+    p = fch.params_default(b["q"], eta1=b["eta1"] * 0.1, eta2=b["eta2"] * 0.1,
+                           prec=fch.FCH_FP32X2, sync_every=256)
+    return b["N"], p, I.paper_initial_data(b["N"], b["d"])
+
+
+def _paper_solo(name, scheme, sigma, T, max_attempts=4_000_000):
+    """one adaptive run of a benchmark: (stats, wall seconds, final u); a run that
+    stops with an error (e.g. PSD's FCH_ENOCONV) returns its stats at that point with
+    the error under "error", and u None"""
+    from paper_2006_04784_gb300 import fch
+
+    n, p, u0 = _paper_problem(name)
+    with fch.Context(n, p) as ctx:
+        ctx.set_state(u0)
+        t0 = time.perf_counter()
+        try:
+            st = ctx.run_adaptive(scheme, sigma, T, max_attempts=max_attempts, raise_on_timeout=False)
+        except fch.FchError as e:
+            st = dict(ctx.stats(), error=str(e))
+            return st, time.perf_counter() - t0, None
+        return st, time.perf_counter() - t0, ctx.get_state()
+
+
+def _paper_ensemble(members, T, rounds=16):
+    """members: (benchmark, scheme, sigma) runs of non-PSD schemes, all to the same
+    T, advanced together as one ensemble. Returns ([(stats, final u)], wall seconds)."""
+    from paper_2006_04784_gb300 import fch
+
+    probs = [_paper_problem(b) for b, _, _ in members]
+    with fch.Ensemble([pr[0] for pr in probs], [pr[1] for pr in probs]) as ens:
+        for i, pr in enumerate(probs):
+            ens[i].set_state(pr[2])
+        t0 = time.perf_counter()
+        st = ens.run_adaptive_each([m[1] for m in members], [m[2] for m in members], T, rounds=rounds)
+        wall = time.perf_counter() - t0
+        return [(st[i], ens[i].get_state()) for i in range(len(members))], wall
+
+
+def comp_error(args):
+    """Table t:Comp-error: relative L2 differences at the final time T between the
+    schemes' solutions of each benchmark at sigma_tol = 1e-5 (Sec. 4), FP32X2. The
+    IMEX, SAV and ETD runs of all benchmarks with the same T form one ensemble; the
+    PSD runs are solo."""
+    import numpy as np
+
+    from paper_2006_04784_gb300 import build as B
+    B.build()
+    sigma = 1e-5
+    paper = {"subcritical": (7.276e-3, 7.315e-3, 4.103e-5, None),
+             "critical": (2.204e-3, 2.212e-3, 1.796e-5, None),
+             "supercritical": (8.817e-2, 8.819e-2, 4.156e-5, 1.568e-2),
+             "foot1": (2.358e-3, 2.359e-3, 1.702e-6, None),
+             "foot2": (3.318e-4, 3.322e-4, 6.195e-7, None)}
+    names = list(paper)
+    sols, runs = {}, []
+    for T in sorted(set(PAPER_T.values())):
+        members = [(b, s, sigma) for b in names if PAPER_T[b] == T
+                   for s in (("imex", "sav", "etd") if b == "supercritical" else ("imex", "sav"))]
+        res, wall = _paper_ensemble(members, T)
+        for (b, s, _), (st, u) in zip(members, res):
+            sols[b, s] = u
+            runs.append({"benchmark": b, "scheme": s, "T": T, "steps": st["n_steps"], "n_fft": st["n_fft"],
+                         "rejects": st["n_rejects"], "t": st["t"]})
+        runs.append({"ensemble_T": T, "members": len(members), "wall_s": wall})
+    for b in names:
+        st, wall, u = _paper_solo(b, "psd", sigma, PAPER_T[b])
+        sols[b, "psd"] = u
+        runs.append({"benchmark": b, "scheme": "psd", "T": PAPER_T[b], "steps": st["n_steps"],
+                     "n_fft": st["n_fft"], "psd_iter": st["n_psd_iter"], "rejects": st["n_rejects"],
+                     "t": st["t"], "wall_s": wall, "error": st.get("error")})
+
+    def cell(a, b_):
+        return None if a is None or b_ is None else _rel(a, b_)
+
+    table = []
+    for b in names:
+        row = {"benchmark": b, "T": PAPER_T[b],
+               "imex/psd": cell(sols[b, "imex"], sols[b, "psd"]),
+               "sav/psd": cell(sols[b, "sav"], sols[b, "psd"]),
+               "sav/imex": cell(sols[b, "sav"], sols[b, "imex"]),
+               "paper": dict(zip(("imex/psd", "sav/psd", "sav/imex", "etd/psd"), paper[b]))}
+        if (b, "etd") in sols:
+            row["etd/psd"] = cell(sols[b, "etd"], sols[b, "psd"])
+        table.append(row)
+    return {"table": "t:Comp-error", "sigma_tol": sigma, "precision": "fp32x2",
+            "norm": "||u_a - u_b||_2 / ||u_b||_2 over the grid at T", "rows": table, "runs": runs}
+
+
+def _loglog_at(xs, ys, x0):
+    """log-log interpolation of y at x = x0 between the first bracketing pair of
+    (xs, ys) (xs in sweep order); None when x0 is not bracketed"""
+    for i in range(len(xs) - 1):
+        a, b = xs[i], xs[i + 1]
+        if min(a, b) <= x0 <= max(a, b) and a != b:
+            w = (math.log(x0) - math.log(a)) / (math.log(b) - math.log(a))
+            return math.exp(math.log(ys[i]) + w * (math.log(ys[i + 1]) - math.log(ys[i])))
+    return None
+
+
+def _slope(xs, ys):
+    import numpy as np
+    if len(xs) < 2:
+        return None
+    return float(np.polyfit(np.log(xs), np.log(ys), 1)[0])
+
+
+def dollars_per_digit(args):
+    """Sec. 5.2, Figs. f:BM3-L2 and f:BM4-L2: for one benchmark, the global relative L2
+    error at T against a highly accurate run, and the cost in 2D real transforms, as
+    sigma_tol sweeps; the cost at the paper's acceptable global error 2.5e-3. IMEX,
+    SAV (and ETD on the super-critical benchmark) sweep as one ensemble; PSD runs solo.
+    FP32X2."""
+    from paper_2006_04784_gb300 import build as B
+    B.build()
+    name = args.dpd_benchmark
+    T = PAPER_T[name]
+    ref_scheme, ref_sigma = PAPER_REFERENCE[name]
+    ref_st, ref_wall, ref = _paper_solo(name, ref_scheme, ref_sigma, T)
+    if ref is None:
+        raise RuntimeError(f"reference run failed: {ref_st['error']} at t = {ref_st['t']}")
+    sig = [float(x) for x in args.dpd_sigmas.split(",")] if args.dpd_sigmas else SIGMA_SWEEP
+    etd_sig = [x for x in sig if x >= args.dpd_etd_min]
+    members = [(name, s, x) for s in ("imex", "sav") for x in sig]
+    if name == "supercritical":
+        members += [(name, "etd", x) for x in etd_sig]
+    res, ens_wall = _paper_ensemble(members, T)
+    runs = []
+    for (_, s, x), (st, u) in zip(members, res):
+        runs.append({"scheme": s, "sigma_tol": x, "n_fft": st["n_fft"], "steps": st["n_steps"],
+                     "rejects": st["n_rejects"], "t": st["t"], "global_rel_l2": _rel(u, ref)})
+    psd_sig = [x for x in sig if x >= args.dpd_psd_min]
+    for x in psd_sig:
+        st, wall, u = _paper_solo(name, "psd", x, T)
+        runs.append({"scheme": "psd", "sigma_tol": x, "n_fft": st["n_fft"], "steps": st["n_steps"],
+                     "psd_iter": st["n_psd_iter"], "rejects": st["n_rejects"], "t": st["t"],
+                     "wall_s": wall, "global_rel_l2": None if u is None else _rel(u, ref),
+                     "error": st.get("error")})
+    summary = {}
+    for s in ("imex", "sav", "etd", "psd"):
+        rs = [r for r in runs if r["scheme"] == s and r["t"] >= T * (1 - 1e-12) and r["global_rel_l2"]]
+        if not rs:
+            continue
+        xs = [r["sigma_tol"] for r in rs]
+        err = [r["global_rel_l2"] for r in rs]
+        cost = [r["n_fft"] for r in rs]
+        fine = [(x, e) for x, e in zip(xs, err) if x <= 1e-5]
+        summary[s] = {"n_fft_at_error_2.5e-3": _loglog_at(err, cost, 2.5e-3),
+                      "sigma_tol_at_error_2.5e-3": _loglog_at(err, xs, 2.5e-3),
+                      "slope_error_vs_sigma(sigma<=1e-5)": _slope([f[0] for f in fine], [f[1] for f in fine]),
+                      "slope_n_fft_vs_sigma": _slope(xs, cost)}
+    both = [(a["n_fft"], b["n_fft"]) for a in runs if a["scheme"] == "sav"
+            for b in runs if b["scheme"] == "imex" and b["sigma_tol"] == a["sigma_tol"]]
+    if both:
+        summary["sav/imex_n_fft"] = sorted(a / b for a, b in both)[len(both) // 2]
+    return {"figure": "f:BM3-L2" if name == "supercritical" else "f:BM4-L2", "benchmark": name, "T": T,
+            "N": _paper_problem(name)[0], "precision": "fp32x2",
+            "fft_unit": "one 2D real transform of one field (R2C or C2R)",
+            "reference": {"scheme": ref_scheme, "sigma_tol": ref_sigma, "n_fft": ref_st["n_fft"],
+                          "steps": ref_st["n_steps"], "t": ref_st["t"], "wall_s": ref_wall},
+            "ensemble": {"members": len(members), "wall_s": ens_wall},
+            "runs": runs, "summary": summary}
+
+
 def _rel(a, b):
     import numpy as np
     return float(np.linalg.norm(a - b) / np.linalg.norm(b))
@@ -916,6 +1103,14 @@ def main():
     ap.add_argument("--paper-costs", action="store_true",
                     help="run the Sec. 5.2 cost comparison (super-critical benchmark) instead")
     ap.add_argument("--paper-T", type=float, default=250.0)
+    ap.add_argument("--comp-error", action="store_true",
+                    help="the cross-scheme differences of Table t:Comp-error (five benchmarks) instead")
+    ap.add_argument("--dollars-per-digit", action="store_true",
+                    help="global error and transforms against sigma_tol (Sec. 5.2) for one benchmark instead")
+    ap.add_argument("--dpd-benchmark", default="supercritical", choices=sorted(PAPER_REFERENCE))
+    ap.add_argument("--dpd-sigmas", default="", help="comma-separated sigma_tol values of the sweep")
+    ap.add_argument("--dpd-etd-min", type=float, default=1e-6, help="smallest sigma_tol of the ETD sweep")
+    ap.add_argument("--dpd-psd-min", type=float, default=1e-7, help="smallest sigma_tol of the PSD sweep")
     ap.add_argument("--workloads", action="store_true",
                     help="measure the 128^2 fixed-step, 512^2 all-scheme and 1024^2/2048^2 runs instead")
     ap.add_argument("--workload-t2", type=float, default=50.0)
@@ -938,6 +1133,10 @@ def main():
     args = ap.parse_args()
     if args.paper_costs:
         out = paper_costs(args)
+    elif args.comp_error:
+        out = comp_error(args)
+    elif args.dollars_per_digit:
+        out = dollars_per_digit(args)
     elif args.workloads:
         out = workloads(args)
     elif args.error_budget:

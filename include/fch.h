@@ -246,6 +246,13 @@ fch_status fch_ensemble_destroy(fch_ensemble *e);
 fch_status fch_ensemble_member(fch_ensemble *e, int i, fch_ctx **ctx);
 fch_status fch_ensemble_run_adaptive(fch_ensemble *e, fch_scheme scheme, double sigma, double t_final, int rounds,
                                      long long max_launches, fch_stats *stats);
+/* fch_ensemble_run_adaptive_each is the same run with a scheme and a sigma_tol per
+ * member (schemes[i], sigmas[i]; host arrays of m entries, read during the call):
+ * the sigma_tol sweeps of Sec. 5.2 (global error and cost against sigma_tol) as one
+ * ensemble. fch_ensemble_run_adaptive(e, s, sigma, ...) is this call with every
+ * entry s, sigma. Errors as above; FCH_EINVAL also for NULL arrays. */
+fch_status fch_ensemble_run_adaptive_each(fch_ensemble *e, const fch_scheme *schemes, const double *sigmas,
+                                          double t_final, int rounds, long long max_launches, fch_stats *stats);
 
 /* ---- learned initial iterate for the PSD iteration (a Fourier neural operator) ----
  * Sec. 3.3 starts the PSD iteration, eqs. (residual), (recurrence), from any v_0

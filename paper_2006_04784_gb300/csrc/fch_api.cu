@@ -6,6 +6,7 @@
 #include <stdio.h>
 #include <stdlib.h>
 #include <string.h>
+#include <vector>
 
 #include "../../include/fch.h"
 #include "fch_ctrl.cuh"
@@ -1183,7 +1184,8 @@ struct fch_ensemble {
     fch_ctrl **dctrls;     // the members' control blocks (device array)
     int *dflags, *hflags;  // per member: done | status << 1 (device, pinned host)
     cudaGraphExec_t graph;
-    int graph_scheme, graph_rounds;
+    int *graph_schemes;    // per member: the scheme the graph holds (host)
+    int graph_rounds;
 };
 
 __global__ void fch_ensemble_flags_kernel(fch_ctrl *const *c, int m, int *out)
@@ -1209,6 +1211,7 @@ extern "C" fch_status fch_ensemble_destroy(fch_ensemble *e)
     free(e->ctx);
     free(e->mstream);
     free(e->join);
+    free(e->graph_schemes);
     free(e);
     return FCH_OK;
 }
@@ -1224,11 +1227,11 @@ extern "C" fch_status fch_ensemble_create(int m, const fch_grid *grids, const fc
     fch_ensemble *e = (fch_ensemble *)calloc(1, sizeof(fch_ensemble));
     if (!e) return FCH_ENOMEM;
     e->m = m;
-    e->graph_scheme = -1;
     e->ctx = (fch_ctx **)calloc(m, sizeof(fch_ctx *));
     e->mstream = (cudaStream_t *)calloc(m, sizeof(cudaStream_t));
     e->join = (cudaEvent_t *)calloc(m, sizeof(cudaEvent_t));
-    if (!e->ctx || !e->mstream || !e->join) {
+    e->graph_schemes = (int *)calloc(m, sizeof(int));
+    if (!e->ctx || !e->mstream || !e->join || !e->graph_schemes) {
         fch_ensemble_destroy(e);
         return FCH_ENOMEM;
     }
@@ -1286,10 +1289,13 @@ extern "C" fch_status fch_ensemble_member(fch_ensemble *e, int i, fch_ctx **ctx)
 }
 
 // capture the ensemble graph: fork from e->stream to every member stream, `rounds`
-// trials per member, join back, then gather the members' flags to pinned memory
-static fch_status ensemble_capture(fch_ensemble *e, int scheme, int rounds)
+// trials per member (each member's trial is that of its own scheme), join back, then
+// gather the members' flags to pinned memory
+static fch_status ensemble_capture(fch_ensemble *e, const fch_scheme *schemes, int rounds)
 {
-    if (e->graph && e->graph_scheme == scheme && e->graph_rounds == rounds) return FCH_OK;
+    bool same = e->graph && e->graph_rounds == rounds;
+    for (int i = 0; i < e->m && same; i++) same = e->graph_schemes[i] == (int)schemes[i];
+    if (same) return FCH_OK;
     if (e->graph) {
         cudaGraphExecDestroy(e->graph);
         e->graph = nullptr;
@@ -1324,29 +1330,31 @@ static fch_status ensemble_capture(fch_ensemble *e, int scheme, int rounds)
         cudaGetLastError();
         return s;
     }
-    e->graph_scheme = scheme;
+    for (int i = 0; i < e->m; i++) e->graph_schemes[i] = (int)schemes[i];
     e->graph_rounds = rounds;
     return FCH_OK;
 }
 
-extern "C" fch_status fch_ensemble_run_adaptive(fch_ensemble *e, fch_scheme scheme, double sigma, double t_final,
-                                                int rounds, long long max_launches, fch_stats *stats)
+extern "C" fch_status fch_ensemble_run_adaptive_each(fch_ensemble *e, const fch_scheme *schemes,
+                                                     const double *sigmas, double t_final, int rounds,
+                                                     long long max_launches, fch_stats *stats)
 {
-    if (!e || !(sigma > 0) || rounds < 1 || rounds > 1024 || max_launches < 0 ||
-        (scheme != FCH_IMEX && scheme != FCH_SAV && scheme != FCH_ETD))
-        return FCH_EINVAL;
-    for (int i = 0; i < e->m; i++)
+    if (!e || !schemes || !sigmas || rounds < 1 || rounds > 1024 || max_launches < 0) return FCH_EINVAL;
+    for (int i = 0; i < e->m; i++) {
+        if (!(sigmas[i] > 0) || (schemes[i] != FCH_IMEX && schemes[i] != FCH_SAV && schemes[i] != FCH_ETD))
+            return FCH_EINVAL;
         if (e->ctx[i]->timing) return FCH_ESTATE;
+    }
     // every member begins (host checks, backward-Euler start) and runs one trial
     // on its own stream; the first trial also sets the kernels' attributes
     for (int i = 0; i < e->m; i++) {
-        TRY(fch_adaptive_begin(e->ctx[i], scheme, sigma, t_final));
+        TRY(fch_adaptive_begin(e->ctx[i], schemes[i], sigmas[i], t_final));
         TRY(fch_adaptive_enqueue(e->ctx[i], 1));
         if (cudaEventRecord(e->join[i], e->ctx[i]->stream) != cudaSuccess ||
             cudaStreamWaitEvent(e->stream, e->join[i], 0) != cudaSuccess)
             return FCH_ECUDA;
     }
-    fch_status result = ensemble_capture(e, scheme, rounds);
+    fch_status result = ensemble_capture(e, schemes, rounds);
     if (result != FCH_OK) {
         for (int i = 0; i < e->m; i++) fch_adaptive_end(e->ctx[i], nullptr);
         return result;
@@ -1375,6 +1383,15 @@ extern "C" fch_status fch_ensemble_run_adaptive(fch_ensemble *e, fch_scheme sche
         if (s != FCH_OK && result == FCH_OK) result = s;
     }
     return result;
+}
+
+extern "C" fch_status fch_ensemble_run_adaptive(fch_ensemble *e, fch_scheme scheme, double sigma, double t_final,
+                                                int rounds, long long max_launches, fch_stats *stats)
+{
+    if (!e) return FCH_EINVAL;
+    std::vector<fch_scheme> schemes(e->m, scheme);
+    std::vector<double> sigmas(e->m, sigma);
+    return fch_ensemble_run_adaptive_each(e, schemes.data(), sigmas.data(), t_final, rounds, max_launches, stats);
 }
 
 extern "C" fch_status fch_pass_timing(fch_ctx *ctx, int on)

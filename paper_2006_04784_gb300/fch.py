@@ -34,7 +34,8 @@ EXPORTS = ["fch_status_string", "fch_last_cuda_error", "fch_params_default", "fc
            "fch_ensemble_run_adaptive", "fch_fno_create", "fch_fno_destroy", "fch_fno_num_params",
            "fch_fno_set_params", "fch_fno_get_params", "fch_fno_get_grads", "fch_fno_forward",
            "fch_fno_backward", "fch_fno_adam", "fch_step_psd_from", "fch_run_fixed",
-           "fch_adaptive_trial_info", "fch_get_history_device", "fch_adaptive_enqueue_psd_from"]
+           "fch_adaptive_trial_info", "fch_get_history_device", "fch_adaptive_enqueue_psd_from",
+           "fch_ensemble_run_adaptive_each"]
 NCOL, NROW = 10, 8
 NPASS = NCOL + NROW + 1
 PASS_NAMES = (["col_fwd_store", "col_inv_load", "col_start", "col_imex_solve", "col_f_finish",
@@ -147,6 +148,8 @@ def lib():
         L.fch_ensemble_member.argtypes = [vp, C.c_int, C.POINTER(vp)]
         L.fch_ensemble_run_adaptive.argtypes = [vp, C.c_int, C.c_double, C.c_double, C.c_int, C.c_longlong,
                                                 C.POINTER(Stats)]
+        L.fch_ensemble_run_adaptive_each.argtypes = [vp, C.POINTER(C.c_int), C.POINTER(C.c_double), C.c_double,
+                                                     C.c_int, C.c_longlong, C.POINTER(Stats)]
         L.fch_autotune_reset.argtypes = []
         L.fch_fft_plan_destroy.argtypes = [vp]
         L.fch_fft_r2c.argtypes = [vp, vp, vp, C.c_int]
@@ -474,6 +477,20 @@ class Ensemble:
                                              int(max_launches), st)
         if not (rc == 6 and not raise_on_timeout):
             _check(rc, "fch_ensemble_run_adaptive")
+        return [x.as_dict() for x in st]
+
+    def run_adaptive_each(self, schemes, sigmas, t_final: float, rounds: int = 8, max_launches: int = 0,
+                          raise_on_timeout: bool = True):
+        """run_adaptive with a scheme and a sigma_tol per member (a sigma_tol sweep)."""
+        m = len(self)
+        assert len(schemes) == m and len(sigmas) == m
+        sc = (C.c_int * m)(*[SCHEMES[x] if isinstance(x, str) else int(x) for x in schemes])
+        sg = (C.c_double * m)(*[float(x) for x in sigmas])
+        st = (Stats * m)()
+        rc = lib().fch_ensemble_run_adaptive_each(self._h, sc, sg, float(t_final), int(rounds),
+                                                  int(max_launches), st)
+        if not (rc == 6 and not raise_on_timeout):
+            _check(rc, "fch_ensemble_run_adaptive_each")
         return [x.as_dict() for x in st]
 
 

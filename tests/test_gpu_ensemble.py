@@ -95,3 +95,41 @@ def test_ensemble_errors_and_budget():
         assert st2[0]["t"] == pytest.approx(st[0]["t"] + 1e-4, rel=1e-12)
     with pytest.raises(fch.FchError):
         fch.Ensemble([], [])
+
+
+@pytest.mark.parametrize("prec", [0, 2])
+def test_ensemble_sweep_members_match_solo_runs(prec):
+    # a scheme and a sigma_tol per member: every member equals its solo run, and
+    # rerunning the same ensemble with the schemes permuted recaptures the graph
+    sizes = [64, 64, 32, 64]
+    schemes = ["imex", "sav", "etd", "imex"]
+    sigmas = [1e-4, 1e-5, 3e-5, 1e-6]
+    tf = 2e-3
+    params = [member_params(i, prec) for i in range(len(sizes))]
+    for order in (schemes, schemes[::-1]):
+        with fch.Ensemble(sizes, params) as ens:
+            for i, n in enumerate(sizes):
+                ens[i].set_state(member_init(n, i))
+            stats = ens.run_adaptive_each(order, sigmas, tf, rounds=3)
+            got = [ens[i].get_state() for i in range(len(sizes))]
+        for i, n in enumerate(sizes):
+            assert stats[i]["t"] == pytest.approx(tf, rel=1e-12)
+            with fch.Context(n, member_params(i, prec)) as ctx:
+                ctx.set_state(member_init(n, i))
+                st = ctx.run_adaptive(order[i], sigmas[i], tf)
+                assert st["n_steps"] == stats[i]["n_steps"] and st["n_rejects"] == stats[i]["n_rejects"]
+                assert np.array_equal(ctx.get_state(), got[i]), (order, i)
+
+
+def test_ensemble_sweep_errors():
+    sizes = [32, 32]
+    params = [member_params(i, 0) for i in range(2)]
+    with fch.Ensemble(sizes, params) as ens:
+        for i, n in enumerate(sizes):
+            ens[i].set_state(member_init(n, i))
+        with pytest.raises(fch.FchError):
+            ens.run_adaptive_each(["imex", "psd"], [1e-5, 1e-5], 1e-3)
+        with pytest.raises(fch.FchError):
+            ens.run_adaptive_each(["imex", "sav"], [1e-5, 0.0], 1e-3)
+        st = ens.run_adaptive_each(["sav", "imex"], [1e-5, 1e-4], 1e-3, rounds=2)
+        assert all(s["t"] == pytest.approx(1e-3, rel=1e-12) for s in st)
