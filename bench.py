@@ -457,7 +457,7 @@ def e2e_measure(fch, I, p, n, dev, K):
     ctrl_bytes = fch.geometry(n)["ctrl_bytes"]
     return {"value": K / (t1 - t0), "unit": "steps/s",
             "h2d_bytes_per_step": (8 * n * n) / K + 2 * ctrl_bytes,
-            "d2h_bytes_per_step": (8 * n * n) / K + 3 * ctrl_bytes,
+            "d2h_bytes_per_step": (8 * n * n) / K + 2 * ctrl_bytes,
             "note": "public API with host arrays: fch_set_state (host u0), one fch_run_adaptive "
                     "call per step (control block in and out), fch_get_state (host) at the end; "
                     "includes the backward-Euler restart of set_state"}
@@ -540,6 +540,13 @@ PAPER_REFERENCE = {"supercritical": ("psd", 1e-9), "foot1": ("psd", 3e-8), "foot
 SIGMA_SWEEP = [1e-3, 3e-4, 1e-4, 3e-5, 1e-5, 3e-6, 1e-6, 3e-7, 1e-7]
 
 
+PSD_MAX_ITER = [1000]  # PSD iterations per step before FCH_ENOCONV (--psd-max-iter)
+
+
+def _progress(*a):
+    print(*a, file=sys.stderr, flush=True)
+
+
 def _paper_problem(name):
     """(N, params, initial data) of one benchmark of Table t:Benchmark (eta in units
     of eps = 0.1), FP32X2."""
@@ -548,11 +555,11 @@ def _paper_problem(name):
 
     b = I.BENCHMARKS[name]
     p = fch.params_default(b["q"], eta1=b["eta1"] * 0.1, eta2=b["eta2"] * 0.1,
-                           prec=fch.FCH_FP32X2, sync_every=256)
+                           prec=fch.FCH_FP32X2, sync_every=256, psd_max_iter=PSD_MAX_ITER[0])
     return b["N"], p, I.paper_initial_data(b["N"], b["d"])
 
 
-def _paper_solo(name, scheme, sigma, T, max_attempts=4_000_000):
+def _paper_solo(name, scheme, sigma, T, max_attempts=2_000_000):
     """one adaptive run of a benchmark: (stats, wall seconds, final u); a run that
     stops with an error (e.g. PSD's FCH_ENOCONV) returns its stats at that point with
     the error under "error", and u None"""
@@ -566,8 +573,11 @@ def _paper_solo(name, scheme, sigma, T, max_attempts=4_000_000):
             st = ctx.run_adaptive(scheme, sigma, T, max_attempts=max_attempts, raise_on_timeout=False)
         except fch.FchError as e:
             st = dict(ctx.stats(), error=str(e))
+            _progress(name, scheme, sigma, "stopped:", st)
             return st, time.perf_counter() - t0, None
-        return st, time.perf_counter() - t0, ctx.get_state()
+        wall = time.perf_counter() - t0
+        _progress(name, scheme, sigma, f"{wall:.1f} s", st)
+        return st, wall, (ctx.get_state() if st["t"] >= T * (1 - 1e-12) else None)
 
 
 def _paper_ensemble(members, T, rounds=16):
@@ -582,6 +592,7 @@ def _paper_ensemble(members, T, rounds=16):
         t0 = time.perf_counter()
         st = ens.run_adaptive_each([m[1] for m in members], [m[2] for m in members], T, rounds=rounds)
         wall = time.perf_counter() - t0
+        _progress(f"ensemble of {len(members)} to T = {T}: {wall:.1f} s")
         return [(st[i], ens[i].get_state()) for i in range(len(members))], wall
 
 
@@ -695,6 +706,7 @@ def dollars_per_digit(args):
         fine = [(x, e) for x, e in zip(xs, err) if x <= 1e-5]
         summary[s] = {"n_fft_at_error_2.5e-3": _loglog_at(err, cost, 2.5e-3),
                       "sigma_tol_at_error_2.5e-3": _loglog_at(err, xs, 2.5e-3),
+                      "n_fft_at_error_7e-4": _loglog_at(err, cost, 7e-4),
                       "slope_error_vs_sigma(sigma<=1e-5)": _slope([f[0] for f in fine], [f[1] for f in fine]),
                       "slope_n_fft_vs_sigma": _slope(xs, cost)}
     both = [(a["n_fft"], b["n_fft"]) for a in runs if a["scheme"] == "sav"
@@ -1111,6 +1123,8 @@ def main():
     ap.add_argument("--dpd-sigmas", default="", help="comma-separated sigma_tol values of the sweep")
     ap.add_argument("--dpd-etd-min", type=float, default=1e-6, help="smallest sigma_tol of the ETD sweep")
     ap.add_argument("--dpd-psd-min", type=float, default=1e-7, help="smallest sigma_tol of the PSD sweep")
+    ap.add_argument("--psd-max-iter", type=int, default=1000,
+                    help="PSD iterations per step before FCH_ENOCONV in the paper-benchmark modes")
     ap.add_argument("--workloads", action="store_true",
                     help="measure the 128^2 fixed-step, 512^2 all-scheme and 1024^2/2048^2 runs instead")
     ap.add_argument("--workload-t2", type=float, default=50.0)
@@ -1131,6 +1145,7 @@ def main():
     ap.add_argument("--budget-steps", type=int, default=200)
     ap.add_argument("--budget-dt", type=float, default=1e-6)
     args = ap.parse_args()
+    PSD_MAX_ITER[0] = args.psd_max_iter
     if args.paper_costs:
         out = paper_costs(args)
     elif args.comp_error:

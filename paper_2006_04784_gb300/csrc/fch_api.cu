@@ -1010,8 +1010,10 @@ static void fill_stats(fch_ctx *ctx, fch_stats *st)
     st->last_psd_iter = ctx->hc.last_psd_iter;
 }
 
-extern "C" fch_status fch_adaptive_begin(fch_ctx *ctx, fch_scheme scheme, double sigma,
-                                         double t_final)
+// att0 (may be NULL): the attempts counted before this run; started (may be NULL):
+// whether the run began with the backward-Euler start (one attempt)
+static fch_status adaptive_begin(fch_ctx *ctx, fch_scheme scheme, double sigma, double t_final,
+                                 long long *att0, bool *started)
 {
     if (!ctx || !(sigma > 0) || scheme < FCH_IMEX || scheme > FCH_ETD) return FCH_EINVAL;
     if (!ctx->have_state || ctx->failed) return FCH_ESTATE;
@@ -1022,6 +1024,8 @@ extern "C" fch_status fch_adaptive_begin(fch_ctx *ctx, fch_scheme scheme, double
     }
     if (!(t_final >= ctx->hc.t)) return FCH_EINVAL;
     fch_ctrl &c = ctx->hc;
+    if (att0) *att0 = c.n_attempts;
+    if (started) *started = c.kn <= 0;
     c.sigma = sigma;
     c.sigma2 = sigma * sigma;
     c.t_final = t_final;
@@ -1053,6 +1057,11 @@ extern "C" fch_status fch_adaptive_begin(fch_ctx *ctx, fch_scheme scheme, double
     ctx->have_F = true;
     TRY(ctl(ctx, OP_INIT_TRIAL, 0, -1.0)); // the first trial of this run
     return FCH_OK;
+}
+
+extern "C" fch_status fch_adaptive_begin(fch_ctx *ctx, fch_scheme scheme, double sigma, double t_final)
+{
+    return adaptive_begin(ctx, scheme, sigma, t_final, nullptr, nullptr);
 }
 
 // one adaptive trial: the scheme's trial step, F of the trial with the AM3
@@ -1117,10 +1126,13 @@ extern "C" fch_status fch_adaptive_enqueue(fch_ctx *ctx, int n)
     return FCH_OK;
 }
 
-extern "C" fch_status fch_adaptive_end(fch_ctx *ctx, fch_stats *stats)
+// pulled: the host mirror already holds the device's control block (no launch since);
+// done (may be NULL) receives whether the run had reached t_final
+static fch_status adaptive_end(fch_ctx *ctx, fch_stats *stats, bool pulled, bool *done = nullptr)
 {
     if (!ctx) return FCH_EINVAL;
-    TRY(pull_ctrl(ctx));
+    if (!pulled) TRY(pull_ctrl(ctx));
+    if (done) *done = ctx->hc.done != 0;
     fch_status result = FCH_OK;
     if (ctx->hc.status) {
         ctx->failed = true;
@@ -1132,39 +1144,57 @@ extern "C" fch_status fch_adaptive_end(fch_ctx *ctx, fch_stats *stats)
     c.adaptive = 0;
     c.itol = ctx->p.psd_itol;
     c.kmax = ctx->p.k_max;
+    // a copy from pageable host memory has staged hc when it returns: hc stays the
+    // device's block without reading it back
     TRY(push_ctrl(ctx));
-    TRY(pull_ctrl(ctx));
     ctx->ad_open = false;
     if (stats) fill_stats(ctx, stats);
     return result;
 }
 
+extern "C" fch_status fch_adaptive_end(fch_ctx *ctx, fch_stats *stats)
+{
+    return adaptive_end(ctx, stats, false);
+}
+
+// The host reads the control block once per batch of trials: the first batch is
+// enqueued right after the run's set-up (trials enqueued after the run has ended,
+// or failed, return at once on the device), and the last read serves the end.
 extern "C" fch_status fch_run_adaptive(fch_ctx *ctx, fch_scheme scheme, double sigma, double t_final,
                                        long long max_attempts, fch_stats *stats)
 {
-    const long long att0 = ctx && ctx->have_state ? (pull_ctrl(ctx), ctx->hc.n_attempts) : 0;
-    TRY(fch_adaptive_begin(ctx, scheme, sigma, t_final));
-    fch_status result = FCH_OK;
+    long long att0 = 0;
+    bool started = false;
+    TRY(adaptive_begin(ctx, scheme, sigma, t_final, &att0, &started));
+    long long used = started ? 1 : 0; // the backward-Euler start is an attempt
+    bool out_of_attempts = false, pulled = false;
     for (;;) {
-        fch_status s = pull_ctrl(ctx);
-        if (s != FCH_OK) return s;
-        const fch_ctrl &c = ctx->hc;
-        if (c.status || c.done) break;
-        const long long used = c.n_attempts - att0;
+        if (pulled) {
+            const fch_status s = pull_ctrl(ctx);
+            if (s != FCH_OK) return s;
+            const fch_ctrl &c = ctx->hc;
+            if (c.status || c.done) break;
+            used = c.n_attempts - att0;
+        }
         if (max_attempts > 0 && used >= max_attempts) {
-            result = FCH_ETIMEOUT;
+            out_of_attempts = true;
             break;
         }
         long long nb = scheme == FCH_PSD ? 1 : ctx->p.sync_every;
         if (max_attempts > 0 && nb > max_attempts - used) nb = max_attempts - used;
-        s = fch_adaptive_enqueue(ctx, (int)nb);
+        const fch_status s = fch_adaptive_enqueue(ctx, (int)nb);
         if (s != FCH_OK) {
             ctx->ad_open = false;
             return s;
         }
+        pulled = true; // from here on every pass of the loop begins with a read
     }
-    fch_status e = fch_adaptive_end(ctx, stats);
-    return e != FCH_OK ? e : result;
+    // the loop ends right after a read of the block unless the start alone used up
+    // the attempts (then the start was enqueued after adaptive_begin's read)
+    bool done = false;
+    const fch_status e = adaptive_end(ctx, stats, pulled, &done);
+    if (e != FCH_OK) return e;
+    return out_of_attempts && !done ? FCH_ETIMEOUT : FCH_OK;
 }
 
 // ---------------------------------------------------------------------------
