@@ -236,7 +236,8 @@ def run_gb300(args):
     n = N_GRID
     prec = {"mixed": fch.FCH_MIXED, "fp64": fch.FCH_FP64, "fp32x2": fch.FCH_FP32X2}[args.prec]
     p = fch.params_default(0.0, eta2=1.5 * 0.1, prec=prec, sync_every=64, autotune=int(args.autotune))
-    tiles = fch.autotune(n, prec) if args.autotune else None
+    tiles = ((fch.autotune_step if args.autotune == 2 else fch.autotune)(n, prec)
+             if args.autotune else None)
     u0 = I.random_network(n, d=0.75, seed=3 + rank)
     stream = torch.cuda.Stream(device=dev)
     ctx = fch.Context(n, p, stream=stream)
@@ -555,7 +556,7 @@ def _paper_problem(name):
 
     b = I.BENCHMARKS[name]
     p = fch.params_default(b["q"], eta1=b["eta1"] * 0.1, eta2=b["eta2"] * 0.1,
-                           prec=fch.FCH_FP32X2, sync_every=256, psd_max_iter=PSD_MAX_ITER[0])
+                           prec=fch.FCH_FP32X2, sync_every=256, psd_max_iter=PSD_MAX_ITER[0], autotune=2)
     return b["N"], p, I.paper_initial_data(b["N"], b["d"])
 
 
@@ -764,8 +765,8 @@ def workloads(args):
     from paper_2006_04784_gb300 import inputs as I
 
     def P(q=0.0, **kw):
-        p = fch.params_default(q, **kw)
-        return p
+        # pass tiles timed on adaptive trials of each grid size and precision
+        return fch.params_default(q, **dict({"autotune": 2}, **kw))
 
     out = {}
     # (1) fixed steps
@@ -1111,7 +1112,9 @@ def main():
     ap.add_argument("--scheme", default="imex", choices=["imex", "sav", "etd"])
     ap.add_argument("--no-t-final", action="store_true", help="skip the time-to-t_final runs")
     ap.add_argument("--no-fft", action="store_true", help="skip the standalone transform throughput")
-    ap.add_argument("--autotune", type=int, default=1, help="1: pass tiles from fch_autotune (default); 0: default tiles")
+    ap.add_argument("--autotune", type=int, default=2,
+                    help="2: pass tiles from fch_autotune_step (timed on adaptive trials; default); "
+                         "1: from fch_autotune (timed on transforms); 0: default tiles")
     ap.add_argument("--paper-costs", action="store_true",
                     help="run the Sec. 5.2 cost comparison (super-critical benchmark) instead")
     ap.add_argument("--paper-T", type=float, default=250.0)

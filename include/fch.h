@@ -88,7 +88,8 @@ typedef struct {
     int fft_path;        /* 0: automatic; 1: shared-memory Stockham passes for every N;
                           * 2: warp-transform passes where available (FCH_MIXED, N = 1024) */
     int autotune;        /* 1: fch_create takes the tiles fch_autotune picks for (n, prec)
-                          * (timing them on first use in the process); 0: tile_row/tile_col */
+                          * (timing them on first use in the process); 2: the tiles
+                          * fch_autotune_step picks; 0: tile_row/tile_col */
     int tile_row, tile_col; /* pass tiles: 0 default (at n = 1024 two-block-cluster
                           * column passes for FCH_FP64 / FCH_FP32X2, warp-level row passes
                           * for FCH_MIXED; else the kernel built for the grid size); -1 the shared-memory
@@ -330,6 +331,18 @@ typedef struct {
 } fch_tile;
 fch_status fch_autotune(int n, int prec, void *stream, fch_tile *out);
 fch_status fch_autotune_reset(void);
+/* fch_autotune_step picks the tiles by timing what a context runs: adaptive IMEX
+ * trials (sigma_tol 1e-5, default parameters at q = 0, a circular bilayer) of a
+ * scratch context per candidate, the row tiles first (default columns), then the
+ * column tiles with the chosen rows; a tile replaces the default only if 3 % faster.
+ * At small n the transform-only timing of fch_autotune can mislead: fewer rows a
+ * block speed up the bare transform but slow the fused passes. out: the chosen tiles;
+ * row_us / col_us the mean trial time after each search, *_default_us the same with
+ * the default tiles of that search, candidates the contexts timed. Kept per
+ * (n, prec) for the process (reset by fch_autotune_reset); contexts created with
+ * params.autotune = 2 use them. Errors as fch_autotune, and any status of fch_create
+ * for the scratch contexts (FCH_ENOMEM). */
+fch_status fch_autotune_step(int n, int prec, void *stream, fch_tile *out);
 
 /* ---- standalone 2D real transforms (the paper's cost unit, Sec. 1) ---- */
 

@@ -570,7 +570,7 @@ extern "C" fch_status fch_create(const fch_grid *g, const fch_params *p, void *s
     if (!g || !p || !out) return FCH_EINVAL;
     *out = nullptr;
     if (!pow2_in_range(g->n) || !(g->L > 0) || !(p->eps > 0) || p->prec < 0 || p->prec > 2 ||
-        p->fft_path < 0 || p->fft_path > 2 || p->autotune < 0 || p->autotune > 1 ||
+        p->fft_path < 0 || p->fft_path > 2 || p->autotune < 0 || p->autotune > 2 ||
         !fch_tile_valid(g->n, p->prec == FCH_MIXED, p->tile_row, p->tile_col) ||
         !(p->k_min > 0) || !(p->rho_s > 0) || p->psd_max_iter < 1)
         return FCH_EINVAL;
@@ -602,7 +602,8 @@ extern "C" fch_status fch_create(const fch_grid *g, const fch_params *p, void *s
     if (p->fft_path == 2 && p->prec == FCH_MIXED && g->n == 1024 && tcol == 0) tcol = -2;
     if (e == cudaSuccess && p->autotune) {
         fch_tile t;
-        const fch_status ts = fch_autotune(N, ctx->prec, ctx->stream, &t);
+        const fch_status ts = p->autotune == 2 ? fch_autotune_step(N, ctx->prec, ctx->stream, &t)
+                                               : fch_autotune(N, ctx->prec, ctx->stream, &t);
         if (ts != FCH_OK) {
             snprintf(ctx->errbuf, sizeof(ctx->errbuf), "fch_create: autotune: %.200s", g_plan_err);
             fch_destroy(ctx);
@@ -1663,10 +1664,118 @@ extern "C" fch_status fch_autotune(int n, int prec, void *stream, fch_tile *out)
     return FCH_OK;
 }
 
+static fch_tile g_tune_step[3][12];
+static bool g_tune_step_ok[3][12];
+
+// Mean time (us) of one adaptive IMEX trial (sigma_tol 1e-5, the library's default
+// parameters at q = 0) of an n x n context with the given tiles, on stream s: the
+// start and four trials untimed (the second one captures the trial graph), then
+// `reps` trials between two events. The state is a circular bilayer of radius 2.
+static fch_status time_trials(int n, int prec, int tr, int tc, cudaStream_t s, int reps, double *us)
+{
+    fch_params p;
+    fch_params_default(&p, 0.0);
+    p.prec = prec;
+    p.tile_row = tr;
+    p.tile_col = tc;
+    const double L = 4.0 * M_PI, h = L / n;
+    const fch_grid g = {n, L, -0.5 * L};
+    fch_ctx *c = nullptr;
+    TRY(fch_create(&g, &p, s, &c));
+    std::vector<double> u0((size_t)n * n);
+    for (int j = 0; j < n; j++)
+        for (int i = 0; i < n; i++) {
+            const double x = g.x0 + i * h, y = g.x0 + j * h, r = sqrt(x * x + y * y) - 2.0;
+            u0[(size_t)j * n + i] = -1.0 + 1.5 * exp(-r * r / (2.0 * p.eps * p.eps));
+        }
+    cudaEvent_t a = nullptr, b = nullptr;
+    fch_status st = fch_set_state(c, u0.data(), u0.size());
+    if (st == FCH_OK) st = fch_adaptive_begin(c, FCH_IMEX, 1e-5, 1e30);
+    if (st == FCH_OK) st = fch_adaptive_enqueue(c, 4);
+    // the context's stream (its own one when s is NULL)
+    if (st == FCH_OK && (cudaEventCreate(&a) != cudaSuccess || cudaEventCreate(&b) != cudaSuccess ||
+                         cudaEventRecord(a, c->stream) != cudaSuccess))
+        st = FCH_ECUDA;
+    if (st == FCH_OK) st = fch_adaptive_enqueue(c, reps);
+    float ms = 0.f;
+    if (st == FCH_OK && (cudaEventRecord(b, c->stream) != cudaSuccess || cudaEventSynchronize(b) != cudaSuccess ||
+                         cudaEventElapsedTime(&ms, a, b) != cudaSuccess))
+        st = FCH_ECUDA;
+    if (st == FCH_OK) st = fch_adaptive_end(c, nullptr);
+    if (a) cudaEventDestroy(a);
+    if (b) cudaEventDestroy(b);
+    if (st != FCH_OK) snprintf(g_plan_err, sizeof(g_plan_err), "fch_autotune_step: %s", fch_last_cuda_error(c));
+    fch_destroy(c);
+    *us = 1e3 * ms / reps;
+    return st;
+}
+
+extern "C" fch_status fch_autotune_step(int n, int prec, void *stream, fch_tile *out)
+{
+    if (!out || !pow2_in_range(n) || prec < 0 || prec > 2) {
+        fch_set_thread_error("fch_autotune_step: invalid argument");
+        return FCH_EINVAL;
+    }
+    {
+        std::lock_guard<std::mutex> lock(g_tune_mutex);
+        if (g_tune_step_ok[prec][ilog2(n)]) {
+            *out = g_tune_step[prec][ilog2(n)];
+            return FCH_OK;
+        }
+    }
+    cudaStream_t s = (cudaStream_t)stream;
+    const bool single = prec == FCH_MIXED;
+    const int reps = n >= 2048 ? 8 : n >= 1024 ? 16 : 32;
+    // the row tiles with the default columns, then the column tiles with the chosen
+    // rows; another tile replaces the default only if 3 % faster
+    fch_tile best;
+    memset(&best, 0, sizeof(best));
+    const int cands[] = {0, -1, -2, 1, 2, 4, 8, 16};
+    for (int is_col = 0; is_col < 2; is_col++) {
+        double best_us = 1e30, def_us = 0;
+        int best_t = 0;
+        for (int c : cands) {
+            if (c < 0 && n != 1024) continue;
+            const int tr = is_col ? best.tile_row : c, tc = is_col ? c : 0;
+            if (!fch_tile_valid(n, single, tr, tc)) continue;
+            double us = 0;
+            if (is_col && c == 0) {
+                us = best.row_us; // the rows' winner with the default columns
+            } else {
+                const fch_status st = time_trials(n, prec, tr, tc, s, reps, &us);
+                if (st != FCH_OK) return st;
+                best.candidates++;
+            }
+            if (c == 0) {
+                def_us = us;
+                best_us = us;
+            } else if (us < best_us && us < 0.97 * def_us) {
+                best_us = us;
+                best_t = c;
+            }
+        }
+        if (is_col) {
+            best.tile_col = best_t;
+            best.col_us = best_us;
+            best.col_default_us = def_us;
+        } else {
+            best.tile_row = best_t;
+            best.row_us = best_us;
+            best.row_default_us = def_us;
+        }
+    }
+    std::lock_guard<std::mutex> lock(g_tune_mutex);
+    g_tune_step[prec][ilog2(n)] = best;
+    g_tune_step_ok[prec][ilog2(n)] = true;
+    *out = best;
+    return FCH_OK;
+}
+
 extern "C" fch_status fch_autotune_reset(void)
 {
     std::lock_guard<std::mutex> lock(g_tune_mutex);
     memset(g_tune_ok, 0, sizeof(g_tune_ok));
+    memset(g_tune_step_ok, 0, sizeof(g_tune_step_ok));
     return FCH_OK;
 }
 

@@ -46,6 +46,17 @@ template <typename T, int M> pass_fn col_fn(int logN)
     return fch::col_pass<T, M, 0>;
 }
 
+// the slot of the kernel launched for a grid of 2^logN at the default tiles: logN
+// where a compile-time kernel is built in this translation unit, else 0 (the
+// generic kernel), so that one kernel has one shared-memory limit record
+inline int kernel_slot(int logN)
+{
+#ifndef FCH_ONLY_1024
+    if (logN == 9 || logN == 11) return logN;
+#endif
+    return logN == 10 ? 10 : 0;
+}
+
 template <typename T, int M> pass_fn row_fn(int logN)
 {
     switch (logN) {
@@ -104,7 +115,7 @@ template <typename T, int M> cudaError_t launch_col(const fch_kparams &kp, cudaS
     // the warp-level tile without its table (a context made with fft_path = 1) is -1
     const int tc = kp.tile_col == -2 ? -1 : kp.tile_col;
     const fch_geom g = fch_geometry_tiled(kp.N, sizeof(T) == 4, 0, tc);
-    const int li = (tc <= 0 && kp.logN >= 9 && kp.logN <= 11) ? kp.logN : 0;
+    const int li = tc <= 0 ? kernel_slot(kp.logN) : 0;
     pass_fn f = col_fn<T, M>(li);
     cudaError_t e = set_smem(f, g.col_smem, fch_geometry(FCH_MAX_N, sizeof(T) == 4).col_smem, attr[li]);
     if (e != cudaSuccess) return e;
@@ -116,7 +127,7 @@ template <typename T, int M> cudaError_t launch_row(const fch_kparams &kp, cudaS
     if (warp_path<T>() && kp.N == 1024 && kp.tw2 && kp.tile_row == 0) return launch_row_w<M>(kp, s);
     static int attr[12] = {};
     const fch_geom g = fch_geometry_tiled(kp.N, sizeof(T) == 4, kp.tile_row, 0);
-    const int li = (kp.tile_row <= 0 && kp.logN >= 9 && kp.logN <= 11) ? kp.logN : 0;
+    const int li = kp.tile_row <= 0 ? kernel_slot(kp.logN) : 0;
     pass_fn f = row_fn<T, M>(li);
     cudaError_t e = set_smem(f, g.row_smem, fch_geometry(FCH_MAX_N, sizeof(T) == 4).row_smem, attr[li]);
     if (e != cudaSuccess) return e;

@@ -35,7 +35,7 @@ EXPORTS = ["fch_status_string", "fch_last_cuda_error", "fch_params_default", "fc
            "fch_fno_set_params", "fch_fno_get_params", "fch_fno_get_grads", "fch_fno_forward",
            "fch_fno_backward", "fch_fno_adam", "fch_step_psd_from", "fch_run_fixed",
            "fch_adaptive_trial_info", "fch_get_history_device", "fch_adaptive_enqueue_psd_from",
-           "fch_ensemble_run_adaptive_each"]
+           "fch_ensemble_run_adaptive_each", "fch_autotune_step"]
 NCOL, NROW = 10, 8
 NPASS = NCOL + NROW + 1
 PASS_NAMES = (["col_fwd_store", "col_inv_load", "col_start", "col_imex_solve", "col_f_finish",
@@ -127,6 +127,7 @@ def lib():
         L.fch_get_stats.argtypes = [vp, C.POINTER(Stats)]
         L.fch_fft_plan_create.argtypes = [C.c_int, C.c_int, vp, C.POINTER(vp)]
         L.fch_autotune.argtypes = [C.c_int, C.c_int, vp, C.POINTER(Tile)]
+        L.fch_autotune_step.argtypes = [C.c_int, C.c_int, vp, C.POINTER(Tile)]
         L.fch_ensemble_create.argtypes = [C.c_int, C.POINTER(Grid), C.POINTER(Params), vp, C.POINTER(vp)]
         L.fch_ensemble_destroy.argtypes = [vp]
         fp = C.POINTER(C.c_float)
@@ -183,6 +184,13 @@ def autotune(n: int, prec: int, stream=None) -> dict:
     """fch_autotune: the pass tiles kept for (n, prec), timed on first use."""
     t = Tile()
     _check(lib().fch_autotune(n, prec, _stream_ptr(stream), C.byref(t)), "fch_autotune")
+    return t.as_dict()
+
+
+def autotune_step(n: int, prec: int, stream=None) -> dict:
+    """fch_autotune_step: the pass tiles timed on adaptive IMEX trials, kept for (n, prec)."""
+    t = Tile()
+    _check(lib().fch_autotune_step(n, prec, _stream_ptr(stream), C.byref(t)), "fch_autotune_step")
     return t.as_dict()
 
 

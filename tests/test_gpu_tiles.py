@@ -126,3 +126,44 @@ def test_plan_created_after_autotune_uses_tuned_tiles():
         ref = O.fft2(x[b], -1)[:, : n // 2 + 1].T
         assert np.abs(X[b].cpu().numpy() - ref).max() <= 1e-13 * np.abs(ref).max() * math.log2(n)
     fch.autotune_reset()
+
+
+def test_tile_shared_memory_limits_survive_other_grids():
+    # double-float at 512^2 runs the generic kernels at the default tiles too: a large
+    # generic tile at 1024^2, then the default tiles at 512^2, then a large tile at
+    # 512^2 must all launch (one shared-memory limit per kernel)
+    u = {n: I.circle_bilayer(n, noise=1e-3) for n in (512, 1024)}
+    out = []
+    for n, tc in ((1024, 4), (512, 0), (512, 8), (1024, 4)):
+        with fch.Context(n, lib_params(prec=2, tile_col=tc)) as ctx:
+            ctx.set_state(u[n])
+            ctx.step("imex", 1e-4)
+            out.append(ctx.get_state())
+    assert rel(out[2], out[1]) < 1e-12 and np.array_equal(out[3], out[0])
+
+
+@pytest.mark.parametrize("n,prec", [(256, 0), (512, 2)])
+def test_autotune_step_picks_valid_tiles_and_adaptive_run_matches(n, prec):
+    # the tuner that times adaptive trials: valid, kept, never slower than the default
+    # it measured, and a context that takes its tiles runs the method like the oracle
+    fch.autotune_reset()
+    t = fch.autotune_step(n, prec)
+    assert t["candidates"] >= 3
+    assert 0 < t["row_us"] <= t["row_default_us"] * (1 + 1e-9)
+    assert 0 < t["col_us"] <= t["col_default_us"] * (1 + 1e-9)
+    assert t["col_default_us"] == t["row_us"]  # the column search starts from the rows' winner
+    assert fch.tile_geometry(n, prec, t["tile_row"], t["tile_col"])[0]
+    assert fch.autotune_step(n, prec) == t
+    m = 128
+    fch.autotune_step(m, prec)
+    p = lib_params(prec=prec, zero_stab_cap=1, autotune=2)
+    u0 = I.circle_bilayer(m, noise=1e-3)
+    s = O.Stepper(m, L, oparams(p))
+    s.set_state(u0)
+    assert s.run_adaptive("imex", 1e-5, 2e-3) == 0
+    with fch.Context(m, p) as ctx:
+        ctx.set_state(u0)
+        st = ctx.run_adaptive("imex", 1e-5, 2e-3)
+        assert st["n_steps"] == s.counts()["steps"]
+        assert rel(ctx.get_state(), s.state()) < 1e-9
+    fch.autotune_reset()
