@@ -113,12 +113,13 @@ cudaError_t fch_launch_ctrl(int op, const fch_kparams &kp, int na, int, double a
 {
     cudaLaunchConfig_t cfg = {};
     cudaLaunchAttribute at[1];
-    fch_pdl_config(cfg, at, dim3(1), dim3(256), 0, s);
+    fch_pdl_config(cfg, at, dim3(1), dim3(256), 0, s, kp.pdl != 0);
     return cudaLaunchKernelEx(&cfg, fch_ctrl_kernel, kp, op, na, arg0);
 }
 
 // launch configuration of a pass or control kernel: programmatic stream
-// serialization (see pdl_begin), unless FCH_NO_PDL is set in the environment
+// serialization (see pdl_begin) where the launch asks for it (fch_kparams::pdl),
+// unless FCH_NO_PDL is set in the environment
 bool fch_pdl_enabled()
 {
     static const bool on = getenv("FCH_NO_PDL") == nullptr;
@@ -126,7 +127,7 @@ bool fch_pdl_enabled()
 }
 
 void fch_pdl_config(cudaLaunchConfig_t &cfg, cudaLaunchAttribute *at, dim3 grid, dim3 block, size_t smem,
-                    cudaStream_t s)
+                    cudaStream_t s, bool pdl)
 {
     cfg.gridDim = grid;
     cfg.blockDim = block;
@@ -135,7 +136,7 @@ void fch_pdl_config(cudaLaunchConfig_t &cfg, cudaLaunchAttribute *at, dim3 grid,
     at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
     at[0].val.programmaticStreamSerializationAllowed = 1;
     cfg.attrs = at;
-    cfg.numAttrs = fch_pdl_enabled() ? 1 : 0;
+    cfg.numAttrs = pdl && fch_pdl_enabled() ? 1 : 0;
 }
 
 // ---------------------------------------------------------------------------
@@ -636,6 +637,14 @@ extern "C" fch_status fch_create(const fch_grid *g, const fch_params *p, void *s
     ctx->kp.P = ctx->geom.P;
     ctx->kp.tile_row = trow;
     ctx->kp.tile_col = tcol;
+    // Programmatic dependent launch pays where every pass is one full wave: the default
+    // tiles at 1024^2 in double and double-float (1024 blocks of 128 threads, seven a
+    // SM), where a successor's blocks can only take the slots the tail frees. Where a
+    // pass leaves SMs free (smaller grids) the successor's waiting blocks take them
+    // early and the running pass ends up packed onto fewer SMs (512^2: 2.3x slower
+    // trials in double); where it has several waves (2048^2) they take later waves'
+    // slots.
+    ctx->kp.pdl = N == 1024 && ctx->prec != FCH_MIXED && trow == 0 && tcol == 0;
     for (int i = 0; i < 3; i++) {
         ctx->kp.U[i] = ctx->U[i];
         ctx->kp.F[i] = ctx->F[i];
@@ -1830,6 +1839,7 @@ extern "C" fch_status fch_fft_plan_create(int n, int prec, void *stream, fch_fft
     pl->kp.P = pl->geom.P;
     pl->kp.tile_row = trow;
     pl->kp.tile_col = tcol;
+    pl->kp.pdl = 1;
     pl->kp.inv_n2 = 1.0 / ((double)n * n);
     pl->kp.tail_op = -1;
     pl->kp.cf.inv_n2 = (float)pl->kp.inv_n2;

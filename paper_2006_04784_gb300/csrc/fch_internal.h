@@ -64,6 +64,7 @@ static_assert(sizeof(fch_ctrl) % 8 == 0, "the control kernel copies fch_ctrl as 
 // Everything a pass needs, passed by value.
 struct fch_kparams {
     int N, logN, P;                 // grid size, log2 N, column pairs per block
+    int pdl;                        // launch with programmatic stream serialization
     double L, kf, inv_n2, h2;       // period, 2 pi / L, 1/N^2, (L/N)^2
     double eps, eps2, q, gamma, bm, bp, eta1, eta2, am, beta1, beta2, zeta, D0, kappa0, kappa2;
     void *U[3], *F[3];              // state spectra and F spectra (rotated through fch_ctrl)
@@ -167,7 +168,7 @@ cudaError_t fch_launch_row_dfl(int mode, const fch_kparams &kp, cudaStream_t s);
 // launch configuration with programmatic stream serialization (when enabled)
 bool fch_pdl_enabled();
 void fch_pdl_config(cudaLaunchConfig_t &cfg, cudaLaunchAttribute *at, dim3 grid, dim3 block, size_t smem,
-                    cudaStream_t s);
+                    cudaStream_t s, bool pdl);
 cudaError_t fch_launch_ctrl(int op, const fch_kparams &kp, int nblk_a, int nblk_b, double arg0,
                             cudaStream_t s);
 

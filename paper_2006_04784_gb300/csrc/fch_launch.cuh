@@ -12,7 +12,7 @@ inline cudaError_t launch_pass(pass_fn f, dim3 grid, dim3 block, size_t smem, cu
 {
     cudaLaunchConfig_t cfg = {};
     cudaLaunchAttribute at[1];
-    fch_pdl_config(cfg, at, grid, block, smem, s);
+    fch_pdl_config(cfg, at, grid, block, smem, s, kp.pdl != 0);
     return cudaLaunchKernelEx(&cfg, f, kp);
 }
 

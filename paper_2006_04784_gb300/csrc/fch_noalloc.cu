@@ -116,6 +116,7 @@ extern "C" fch_status fch_fft_r2c_noalloc(int n, int prec, const void *x, void *
     kp.N = n;
     kp.logN = logN;
     kp.P = fch_geometry(n, prec).P;
+    kp.pdl = 1;
     kp.inv_n2 = 1.0 / ((double)n * n);
     kp.cf.inv_n2 = (float)kp.inv_n2;
     kp.cd.inv_n2 = kp.inv_n2;
