@@ -51,3 +51,17 @@ def test_gpu_arm_line():
     assert e["value"] > 0 and e["h2d_bytes_per_step"] > 0 and e["d2h_bytes_per_step"] > 0
     assert d["gpu_launches"] >= 5 * d["steps"]
     assert {"sm_mhz", "sm_max_mhz", "reasons"} <= set(d["clocks"])
+
+
+def test_sweep_interpolation_helpers():
+    # the error-against-cost summary interpolates a power law exactly in log-log
+    sys.path.insert(0, ROOT)
+    import bench
+
+    xs = [1e-1, 1e-2, 1e-3]
+    ys = [x ** -0.5 for x in xs]
+    assert abs(bench._loglog_at(xs, ys, 3e-2) - 3e-2 ** -0.5) < 1e-12
+    assert abs(bench._loglog_at(xs[::-1], ys[::-1], 5e-3) - 5e-3 ** -0.5) < 1e-12
+    assert bench._loglog_at(xs, ys, 1.0) is None
+    assert abs(bench._slope(xs, ys) + 0.5) < 1e-12
+    assert bench._slope([1.0], [2.0]) is None
