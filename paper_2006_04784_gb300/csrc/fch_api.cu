@@ -263,6 +263,9 @@ struct fch_ctx {
     // graph replays any trial; PSD (host convergence test) is not captured
     cudaGraphExec_t trial_graph[4];
     bool trial_warm[4], trial_nograph[4];
+    cudaGraphExec_t psd_graph; // one chunk of PSD iterations
+    bool psd_warm, psd_nograph;
+    int psd_hint;              // iterations the last PSD solve took
     // one fixed step (step size fixed_dt[s]) of IMEX, SAV, ETD captured as a CUDA graph
     cudaGraphExec_t fixed_graph[4];
     double fixed_dt[4];
@@ -696,6 +699,7 @@ extern "C" fch_status fch_destroy(fch_ctx *ctx)
         if (ctx->trial_graph[i]) cudaGraphExecDestroy(ctx->trial_graph[i]);
         if (ctx->fixed_graph[i]) cudaGraphExecDestroy(ctx->fixed_graph[i]);
     }
+    if (ctx->psd_graph) cudaGraphExecDestroy(ctx->psd_graph);
     if (ctx->own_stream && ctx->stream) cudaStreamDestroy(ctx->stream);
     free(ctx);
     return FCH_OK;
@@ -806,19 +810,62 @@ extern "C" fch_status fch_get_state_device(fch_ctx *ctx, void *u_dev, int dtype)
 // PSD iterations, eqs. (residual), (recurrence), from the iterate in Vb (packed in Z
 // by the pass before) until the stopping test holds; the trial slot then receives
 // the converged iterate
+static const int kPsdChunk = 4;
+
+static fch_status psd_chunk_eager(fch_ctx *ctx)
+{
+    for (int i = 0; i < kPsdChunk; i++) {
+        TRY(row(ctx, RM_F, FCH_FL_PSDSKIP));
+        TRY(colt(ctx, CM_PSD_ITER, 0, FCH_FL_PSDSKIP, OP_PSD_CHECK));
+    }
+    return FCH_OK;
+}
+
+// kPsdChunk iterations: the first chunk of a context runs eagerly (it also sets the
+// kernels' attributes), later ones replay a captured graph unless per-pass timing is
+// on. Once the stopping test holds, the remaining passes of a chunk return at once.
+static fch_status psd_chunk(fch_ctx *ctx)
+{
+    const bool graph_ok = !ctx->timing && ctx->psd_warm && !ctx->psd_nograph;
+    if (graph_ok && !ctx->psd_graph) {
+        bool ok = cudaStreamBeginCapture(ctx->stream, cudaStreamCaptureModeRelaxed) == cudaSuccess;
+        if (ok) {
+            const fch_status st = psd_chunk_eager(ctx);
+            cudaGraph_t g = nullptr;
+            ok = cudaStreamEndCapture(ctx->stream, &g) == cudaSuccess && g && st == FCH_OK;
+            if (ok) ok = cudaGraphInstantiate(&ctx->psd_graph, g, 0) == cudaSuccess;
+            if (g) cudaGraphDestroy(g);
+        }
+        if (!ok) {
+            ctx->psd_graph = nullptr;
+            ctx->psd_nograph = true;
+            cudaGetLastError();
+        }
+    }
+    if (graph_ok && ctx->psd_graph) {
+        CKC(ctx, cudaGraphLaunch(ctx->psd_graph, ctx->stream));
+        return FCH_OK;
+    }
+    TRY(psd_chunk_eager(ctx));
+    ctx->psd_warm = true;
+    return FCH_OK;
+}
+
+// The host reads the control block after each batch of chunks; the first batch
+// covers as many iterations as the previous solve took (rounded down to chunks),
+// later ones one chunk each.
 static fch_status psd_iterate(fch_ctx *ctx)
 {
-    const int chunk = 4;
-    for (int guard = 0;; guard++) {
-        if (guard * chunk > ctx->p.psd_max_iter + 2 * chunk) return FCH_ENOCONV;
-        for (int i = 0; i < chunk; i++) {
-            TRY(row(ctx, RM_F, FCH_FL_PSDSKIP));
-            TRY(colt(ctx, CM_PSD_ITER, 0, FCH_FL_PSDSKIP, OP_PSD_CHECK));
-        }
+    int chunks = ctx->psd_hint >= kPsdChunk ? ctx->psd_hint / kPsdChunk : 1;
+    for (long long launched = 0;; chunks = 1) {
+        if (launched > ctx->p.psd_max_iter + 2 * kPsdChunk) return FCH_ENOCONV;
+        for (int c = 0; c < chunks; c++) TRY(psd_chunk(ctx));
+        launched += (long long)chunks * kPsdChunk;
         TRY(pull_ctrl(ctx));
         if (ctx->hc.status || ctx->hc.done || ctx->hc.psd_conv) break;
     }
     if (ctx->hc.status) return (fch_status)ctx->hc.status;
+    ctx->psd_hint = ctx->hc.last_psd_iter;
     TRY(col(ctx, CM_START, FCH_SRC_V, FCH_FL_COPYV));
     return FCH_OK;
 }

@@ -476,3 +476,23 @@ def test_paper_initial_data_adaptive_vs_oracle():
         # 95 steps; each rounds the mean mode a few dozen times at the double-float unit
         # 2^-48 = 3.6e-15 (the FP64 oracle drifts 9.5e-14 over the same run, 2^-53 units)
         assert ctx.mass() == pytest.approx(O.mass(u0, L), rel=1e-11)
+
+
+def test_psd_iteration_graph_equals_eager_launches():
+    # the PSD iterations replay a captured chunk after the first solve; with per-pass
+    # timing on every pass launches eagerly: same iterations, same result
+    n = 64
+    u0 = I.circle_bilayer(n, noise=1e-3)
+    out = []
+    for timing in (False, True):
+        with fch.Context(n, lib_params(0.0)) as ctx:
+            ctx.set_state(u0)
+            ctx.pass_timing(timing)
+            st = ctx.run_adaptive("psd", 1e-5, 5e-3)
+            for _ in range(3):
+                ctx.step("psd", 1e-4)
+            out.append((st, ctx.stats(), ctx.get_state()))
+    (a, a2, ua), (b, b2, ub) = out
+    assert a["n_psd_iter"] == b["n_psd_iter"] and a["n_steps"] == b["n_steps"] and a["n_fft"] == b["n_fft"]
+    assert a2["n_psd_iter"] == b2["n_psd_iter"]
+    assert np.array_equal(ua, ub)
