@@ -947,6 +947,9 @@ def fno_bench(args):
         dts = T.random_steps(np.random.default_rng(99), steps, 1e-3)
         it_plain, it_fno, e_plain, e_fno = [], [], [], []
         diffs = []
+        # IMEX / SAV with the learned extrapolation: distance of the step to the
+        # fully implicit BDF2 step (the PSD fixed point) from u* and from v_0
+        gap = {(sc, w): [] for sc in ("imex", "sav") for w in ("plain", "learned")}
         with fch.Context(m, p) as a, fch.Context(m, p) as b:
             a.set_state(u0)
             hist_u = [np.array(u0)]
@@ -970,12 +973,23 @@ def fno_bench(args):
                 diffs.append(float(np.linalg.norm(b.get_state() - u1) / np.linalg.norm(u1)))
                 e_plain.append(float(np.linalg.norm(ustar - u1)))
                 e_fno.append(float(np.linalg.norm(v0.cpu().numpy() - u1)))
+                for sc in ("imex", "sav"):
+                    for w in ("plain", "learned"):
+                        b.set_history(un, um, dts[i - 1])
+                        if w == "plain":
+                            b.step(sc, dt)
+                        else:
+                            b.step_from(sc, dt, v0)
+                        gap[sc, w].append(_rel(b.get_state(), u1))
                 hist_u.append(u1)
             diff = max(diffs)
         return {"grid": m, "steps": len(it_plain), "psd_iter_plain": float(np.mean(it_plain)),
                 "psd_iter_fno": float(np.mean(it_fno)),
                 "start_error_ratio": float(np.mean(np.array(e_fno) / np.array(e_plain))),
-                "max_rel_diff_learned_vs_plain": diff}
+                "max_rel_diff_learned_vs_plain": diff,
+                "learned_extrapolation": {
+                    f"{sc}_gap_to_implicit_{w}": float(np.mean(gap[sc, w]))
+                    for sc in ("imex", "sav") for w in ("plain", "learned")}}
 
     out["eval_128"] = evaluate(128, I.circle_bilayer(128, radius=2.1, noise=1e-3, seed=21), 30)
     out["eval_1024"] = evaluate(1024, I.circle_bilayer(1024, radius=2.1, noise=1e-3, seed=21), 8)

@@ -293,6 +293,15 @@ fch_status fch_fno_adam(fch_fno *f, float lr, float beta1, float beta2, float ep
  * tolerance. */
 fch_status fch_step_psd_from(fch_ctx *ctx, double dt, const void *v0_dev, int dtype);
 
+/* One fixed IMEX-BDF2 (eq. IMEX-eq) or SAV-BDF2 (eqs. 4.7-4.8) step of size dt whose
+ * extrapolation u* is the real field ustar (device, n x n, dtype 0 double / 1 float)
+ * instead of eq. (Richardson): the explicit part is evaluated at the caller's
+ * prediction of u^{n+1}, e.g. a learned one. Given the fully implicit BDF2 solution,
+ * the IMEX step returns it. Mass does not depend on ustar (the k = 0 mode of either
+ * solve involves u^n and u^{n-1} only). Otherwise as fch_step: FCH_EINVAL for another
+ * scheme, dt <= 0, a NULL field or another dtype; FCH_ESTATE without a state. */
+fch_status fch_step_from(fch_ctx *ctx, fch_scheme scheme, double dt, const void *ustar_dev, int dtype);
+
 /* Adaptive PSD runs with a caller-given first iterate per trial (the same trial as
  * fch_adaptive_enqueue: PSD iteration, F of the trial, AM3 estimate, decision):
  *  - fch_adaptive_trial_info: after fch_adaptive_begin or a trial, the next trial's

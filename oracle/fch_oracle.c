@@ -416,6 +416,7 @@ typedef struct {
     long n_steps, n_rejects, n_psd_iter, n_attempts;
     int last_psd_iter;
     double last_e;
+    const double *ustar_given; /* a caller's u* for the next step (orc_step_from), else NULL */
     /* work */
     double *w[10];
     cplx *c1, *c2, *c3, *c4;
@@ -497,10 +498,16 @@ void orc_get_counts(const orc_ctx *s, long *out)
 }
 double orc_get_last_e(const orc_ctx *s) { return s->last_e; }
 
-/* u* = u^n + (k_{n+1}/k_n)(u^n - u^{n-1}), eq. (Richardson); u* = u^n at the start */
+/* u* = u^n + (k_{n+1}/k_n)(u^n - u^{n-1}), eq. (Richardson); u* = u^n at the start.
+ * A u* given by orc_step_from replaces the extrapolation: eqs. (IMEX-eq) and
+ * (4.7)-(4.8) take u* as an input like u^n and u^{n-1}. */
 static void extrapolate(const orc_ctx *s, double k1, double *ustar)
 {
     long n = npts(&s->g);
+    if (s->ustar_given) {
+        memcpy(ustar, s->ustar_given, sizeof(double) * n);
+        return;
+    }
     if (s->kn <= 0) {
         memcpy(ustar, s->u, sizeof(double) * n);
         return;
@@ -752,6 +759,19 @@ static void accept(orc_ctx *s, const double *unew, double rnew, double k1)
     s->kn = k1;
     s->t += k1;
     s->n_steps++;
+}
+
+int orc_step(orc_ctx *s, int scheme, double dt);
+
+/* one fixed IMEX or SAV step whose extrapolation u* is the given field (real
+ * space, N x N) instead of eq. (Richardson); otherwise as orc_step */
+int orc_step_from(orc_ctx *s, int scheme, double dt, const double *ustar)
+{
+    if (scheme != ORC_IMEX && scheme != ORC_SAV) return -2;
+    s->ustar_given = ustar;
+    int rc = orc_step(s, scheme, dt);
+    s->ustar_given = NULL;
+    return rc;
 }
 
 /* fixed step of size dt (first step after orc_set_state is backward Euler) */

@@ -94,6 +94,8 @@ def lib():
             L.orc_get_last_e.restype = C.c_double
             L.orc_step.argtypes = [C.c_void_p, C.c_int, C.c_double]
             L.orc_step.restype = C.c_int
+            L.orc_step_from.argtypes = [C.c_void_p, C.c_int, C.c_double, C.POINTER(C.c_double)]
+            L.orc_step_from.restype = C.c_int
             L.orc_run_adaptive.argtypes = [C.c_void_p, C.c_int, C.c_double, C.c_double, C.c_long]
             L.orc_run_adaptive.restype = C.c_int
             _lib = L
@@ -251,6 +253,15 @@ class Stepper:
     def step(self, scheme, dt):
         s = SCHEMES[scheme] if isinstance(scheme, str) else scheme
         rc = lib().orc_step(self._h, s, float(dt))
+        if rc:
+            raise RuntimeError(f"oracle step failed ({rc})")
+
+    def step_from(self, scheme, dt, ustar):
+        """one IMEX or SAV step whose extrapolation u* is the given N x N field"""
+        s = SCHEMES[scheme] if isinstance(scheme, str) else scheme
+        a = np.ascontiguousarray(ustar, dtype=np.float64)
+        assert a.shape == (self.N, self.N)
+        rc = lib().orc_step_from(self._h, s, float(dt), _dp(a))
         if rc:
             raise RuntimeError(f"oracle step failed ({rc})")
 

@@ -1024,6 +1024,34 @@ extern "C" fch_status fch_adaptive_enqueue_psd_from(fch_ctx *ctx, const void *v0
     return s;
 }
 
+extern "C" fch_status fch_step_from(fch_ctx *ctx, fch_scheme scheme, double dt, const void *ustar, int dtype)
+{
+    if (!ctx || !(dt > 0) || !ustar || (dtype != 0 && dtype != 1) || (scheme != FCH_IMEX && scheme != FCH_SAV))
+        return FCH_EINVAL;
+    if (!ctx->have_state || ctx->failed) return FCH_ESTATE;
+    ctx->rvalid = false;
+    TRY(ctl(ctx, OP_INIT_TRIAL, 0, dt));
+    // the given u*: its spectrum in Vb, (u*, Lap u*) packed for the row pass
+    TRY(load_field(ctx, ustar, dtype == 0, ctx->Vb));
+    TRY(col(ctx, CM_START, FCH_SRC_V));
+    fch_status s;
+    if (scheme == FCH_IMEX) {
+        s = row(ctx, RM_NIMEX);
+        if (s == FCH_OK) s = col(ctx, CM_IMEX_SOLVE, 0, 0);
+    } else {
+        s = rowt(ctx, RM_SAV, 0, OP_SAV_E1, 0.0);
+        if (s == FCH_OK) s = colt(ctx, CM_SAV_PQ, 0, FCH_FL_USTAR_V, OP_SAV_R);
+        if (s == FCH_OK) s = col(ctx, CM_SAV_COMBINE, 0, 0);
+    }
+    if (s != FCH_OK) {
+        ctx->failed = true;
+        return s;
+    }
+    TRY(ctl(ctx, OP_ACCEPT, 0, 0.0));
+    ctx->have_F = false;
+    return FCH_OK;
+}
+
 extern "C" fch_status fch_step_psd_from(fch_ctx *ctx, double dt, const void *v0, int dtype)
 {
     if (!ctx || !(dt > 0) || !v0 || (dtype != 0 && dtype != 1)) return FCH_EINVAL;

@@ -103,7 +103,8 @@ enum {
     FCH_FL_PSDSKIP = 32,   // pass belongs to a PSD iteration: return if converged
     FCH_FL_F64IO = 64,     // explicit real-space io in float64 (else the pass precision)
     FCH_FL_STORE_REAL = 256, // F row pass: also store (u, Lap u) into the real-space slot of src
-    FCH_FL_GAMMA0 = 512      // direct row passes: use u^n itself (gamma = 0, the ETD first stage)
+    FCH_FL_GAMMA0 = 512,     // direct row passes: use u^n itself (gamma = 0, the ETD first stage)
+    FCH_FL_USTAR_V = 1024    // SAV p/q pass: u* is the caller's field in Vb, not eq. (Richardson)
 };
 
 // column-pass modes (the fused spectral stage between the column transforms)

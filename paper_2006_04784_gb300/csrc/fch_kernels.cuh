@@ -441,7 +441,9 @@ __device__ __forceinline__ void spec_elem(const fch_kparams &kp, const fch_const
         //                   (a + |k|^2 l0) q = -|k|^2 X,  X = V[u*]/sqrt(E1(u*) + D0)
         const C X = cscale(cadd(cscale(A, K.e2 * k2), B), co.isq);
         const C un = ldg(bf.Un + idx), um = ldg(bf.Um + idx);
-        const C us = co.gam != (T)0 ? cadd(un, cscale(csub(un, um), co.gam)) : un;
+        const C us = (kp.flags & FCH_FL_USTAR_V) ? ((const C *)kp.Vb)[idx]
+                     : co.gam != (T)0           ? cadd(un, cscale(csub(un, um), co.gam))
+                                                : un;
         const T l0 = K.e4 * k2 * k2 + K.b1am_e2 * k2 + K.b2am2;
         const T l1 = -K.l1c * k2 - K.b1am_e2 * k2 - K.b2am2;
         const T den = co.a + k2 * l0;

@@ -35,7 +35,7 @@ EXPORTS = ["fch_status_string", "fch_last_cuda_error", "fch_params_default", "fc
            "fch_fno_set_params", "fch_fno_get_params", "fch_fno_get_grads", "fch_fno_forward",
            "fch_fno_backward", "fch_fno_adam", "fch_step_psd_from", "fch_run_fixed",
            "fch_adaptive_trial_info", "fch_get_history_device", "fch_adaptive_enqueue_psd_from",
-           "fch_ensemble_run_adaptive_each", "fch_autotune_step"]
+           "fch_ensemble_run_adaptive_each", "fch_autotune_step", "fch_step_from"]
 NCOL, NROW = 10, 8
 NPASS = NCOL + NROW + 1
 PASS_NAMES = (["col_fwd_store", "col_inv_load", "col_start", "col_imex_solve", "col_f_finish",
@@ -141,6 +141,7 @@ def lib():
         L.fch_fno_backward.argtypes = [vp, vp, C.POINTER(C.c_double)]
         L.fch_fno_adam.argtypes = [vp, C.c_float, C.c_float, C.c_float, C.c_float]
         L.fch_step_psd_from.argtypes = [vp, C.c_double, vp, C.c_int]
+        L.fch_step_from.argtypes = [vp, C.c_int, C.c_double, vp, C.c_int]
         L.fch_run_fixed.argtypes = [vp, C.c_int, C.c_double, C.c_longlong]
         L.fch_adaptive_trial_info.argtypes = [vp, C.POINTER(C.c_double), C.POINTER(C.c_double),
                                               C.POINTER(C.c_int)]
@@ -328,6 +329,13 @@ class Context:
     def adaptive_enqueue_psd_from(self, v0):
         self._ck(lib().fch_adaptive_enqueue_psd_from(self._h, _tensor_ptr(v0), _dtype_code(v0)),
                  "fch_adaptive_enqueue_psd_from")
+
+    def step_from(self, scheme, dt: float, ustar):
+        """one IMEX or SAV step whose extrapolation u* is the device field ustar"""
+        assert ustar.is_cuda and ustar.is_contiguous() and tuple(ustar.shape) == (self.n, self.n)
+        s = SCHEMES[scheme] if isinstance(scheme, str) else int(scheme)
+        self._ck(lib().fch_step_from(self._h, s, float(dt), _tensor_ptr(ustar), _dtype_code(ustar)),
+                 "fch_step_from")
 
     def step_psd_from(self, dt: float, v0):
         """one PSD-BDF2 step whose iteration starts from the device field v0"""

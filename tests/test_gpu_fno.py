@@ -183,3 +183,34 @@ def test_adaptive_psd_with_learned_start(small_trained_net):
     assert out["plain"][2] == 0
     assert rel(out["learned"][1], out["plain"][1]) < 1e-6
     assert out["learned"][0]["n_psd_iter"] <= 1.05 * out["plain"][0]["n_psd_iter"]
+
+
+def test_learned_extrapolation_brings_imex_to_the_implicit_step(small_trained_net):
+    # the IMEX step's explicit part at the network's prediction of u^{n+1} instead of
+    # eq. (Richardson): on a held-out trajectory the step lands closer to the fully
+    # implicit BDF2 step (the PSD fixed point); the plain method stays the reference
+    from paper_2006_04784_gb300 import fno_train as T
+
+    net, _ = small_trained_net
+    n = 64
+    p = fch.params_default(0.0, psd_itol=1e-12)
+    dts = T.random_steps(np.random.default_rng(11), 16, 1e-3)
+    u = [I.circle_bilayer(n, radius=2.2, noise=1e-3, seed=7)]
+    plain, learned = [], []
+    with fch.Context(n, p) as a, fch.Context(n, p) as b:
+        a.set_state(u[0])
+        for i, dt in enumerate(dts):
+            if i >= 2:
+                ustar = u[-1] + dt / dts[i - 1] * (u[-1] - u[-2])
+                v0, _ = T.learned_start(net, u[-1], ustar, DEV)
+            a.step("psd", dt)
+            u.append(a.get_state())
+            if i >= 2:
+                b.set_history(u[-2], u[-3], dts[i - 1])
+                b.step("imex", dt)
+                plain.append(rel(b.get_state(), u[-1]))
+                b.set_history(u[-2], u[-3], dts[i - 1])
+                b.step_from("imex", dt, v0)
+                learned.append(rel(b.get_state(), u[-1]))
+                assert b.mass() == pytest.approx(a.mass(), rel=1e-12)
+    assert np.mean(learned) < 0.9 * np.mean(plain)

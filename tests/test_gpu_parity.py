@@ -496,3 +496,34 @@ def test_psd_iteration_graph_equals_eager_launches():
     assert a["n_psd_iter"] == b["n_psd_iter"] and a["n_steps"] == b["n_steps"] and a["n_fft"] == b["n_fft"]
     assert a2["n_psd_iter"] == b2["n_psd_iter"]
     assert np.array_equal(ua, ub)
+
+
+@pytest.mark.parametrize("prec", [0, 2])
+@pytest.mark.parametrize("scheme", ["imex", "sav"])
+def test_step_from_a_given_extrapolation_matches_oracle(scheme, prec):
+    # fch_step_from: the IMEX / SAV step with the caller's u*, against the oracle's
+    # step with the same u*; with u* = eq. (Richardson) it is the plain step
+    n = 64
+    p = lib_params(0.2, prec=prec)
+    un = I.smooth_random(n, seed=3)
+    um = I.smooth_random(n, seed=4, amp=0.49)
+    kn, dt = 1e-3, 1.5e-3
+    extrap = un + (dt / kn) * (un - um)
+    given = extrap + 0.05 * I.smooth_random(n, seed=9)
+    for ustar in (extrap, given):
+        s = O.Stepper(n, L, oparams(p))
+        s.set_history(un, um, kn)
+        s.step_from(scheme, dt, ustar)
+        with fch.Context(n, p) as ctx:
+            ctx.set_history(un, um, kn)
+            ctx.step_from(scheme, dt, torch.tensor(ustar, device=DEV))
+            assert rel(ctx.get_state(), s.state()) < 1e-12
+    with fch.Context(n, p) as ctx:
+        ctx.set_history(un, um, kn)
+        ctx.step_from(scheme, dt, torch.tensor(extrap, device=DEV, dtype=torch.float32))
+        s = O.Stepper(n, L, oparams(p))
+        s.set_history(un, um, kn)
+        s.step(scheme, dt)
+        assert rel(ctx.get_state(), s.state()) < 1e-6  # u* rounded to float
+        with pytest.raises(fch.FchError):
+            ctx.step_from("psd", dt, torch.tensor(extrap, device=DEV))

@@ -521,3 +521,52 @@ def test_benchmark_initial_data_mass_matches_table():
     band = I.paper_band()
     area = np.sum((band + 1) / 2) * (L / 256) ** 2
     assert abs(area - 2 * I.R_BILAYER * length) < 5e-4
+
+
+# ----------------------------------------------------------------------------- given extrapolation
+def _two_level_state(N, q=0.0):
+    u1 = I.circle_bilayer(N, noise=1e-3)
+    s = O.Stepper(N, L, O.params(q=q))
+    s.set_state(u1)
+    s.step("imex", 1e-4)
+    return u1, s.state()
+
+
+@pytest.mark.parametrize("scheme", ["imex", "sav"])
+def test_step_from_with_the_extrapolation_is_the_plain_step(scheme):
+    # eq. (Richardson) fed in from outside gives the plain step, bit for bit
+    N, kn, dt = 32, 1e-4, 1.5e-4
+    um, un = _two_level_state(N)
+    ustar = un + (dt / kn) * (un - um)
+    out = []
+    for given in (False, True):
+        s = O.Stepper(N, L, O.params())
+        s.set_history(un, um, kn)
+        if given:
+            s.step_from(scheme, dt, ustar)
+        else:
+            s.step(scheme, dt)
+        out.append(s.state())
+    assert np.array_equal(out[0], out[1])
+
+
+@pytest.mark.parametrize("q", [0.0, 0.2])
+def test_imex_step_from_the_implicit_solution_returns_it(q):
+    # a fixed point of the fully implicit BDF2, eq. (BDF2), is a fixed point of the
+    # IMEX step, eq. (IMEX-eq), whose extrapolation is that fixed point: the IMEX
+    # splitting only moves the nonlinear part to u*
+    N, kn, dt = 32, 1e-4, 2e-4
+    um, un = _two_level_state(N, q)
+    s = O.Stepper(N, L, O.params(q=q, psd_itol=1e-14, psd_max_iter=5000))
+    s.set_history(un, um, kn)
+    s.step("psd", dt)
+    u_bdf2 = s.state()
+    t = O.Stepper(N, L, O.params(q=q))
+    t.set_history(un, um, kn)
+    t.step_from("imex", dt, u_bdf2)
+    assert np.linalg.norm(t.state() - u_bdf2) / np.linalg.norm(u_bdf2) < 1e-11
+    # while the plain extrapolation leaves the IMEX splitting error
+    t2 = O.Stepper(N, L, O.params(q=q))
+    t2.set_history(un, um, kn)
+    t2.step("imex", dt)
+    assert np.linalg.norm(t2.state() - u_bdf2) / np.linalg.norm(u_bdf2) > 1e-9
