@@ -724,6 +724,80 @@ def dollars_per_digit(args):
             "runs": runs, "summary": summary}
 
 
+TRACE_TIMES = [1, 2, 5, 10, 20, 30, 50, 75, 100, 125, 150, 175, 185, 200, 210, 225, 250]
+
+
+def traces(args):
+    """Time traces on one benchmark (Secs. 4-5): the global relative L2 error against
+    the highly accurate run (Fig. f:L2temp_error), the adaptive step size (Fig.
+    f:Stepsize) and u - b_- at the domain centre and corner (Fig. f:corner-1), at
+    output times up to T, for IMEX, SAV and PSD at sigma_tol = 1e-5, 1e-6, 1e-7 (and
+    ETD at 1e-5). Every run advances from output time to output time (the adaptive
+    step is clipped at each, reading R4); IMEX, SAV and ETD as one ensemble. FP32X2."""
+    from paper_2006_04784_gb300 import build as B
+    B.build()
+    from paper_2006_04784_gb300 import fch
+
+    name = args.trace_benchmark
+    T = PAPER_T[name]
+    times = [t for t in TRACE_TIMES if t < T] + [T]
+    n, p, u0 = _paper_problem(name)
+    ref_scheme, ref_sigma = PAPER_REFERENCE.get(name, ("psd", 1e-9))
+
+    def probe(u):
+        c = n // 2  # x = 0 on the grid x0 + i L / n, x0 = -L / 2; the corner is i = 0
+        return float(u[c, c] - p.b_minus), float(u[0, 0] - p.b_minus)
+
+    def solo(scheme, sigma):
+        rows, states = [], []
+        with fch.Context(n, p) as ctx:
+            ctx.set_state(u0)
+            t0 = time.perf_counter()
+            for t in times:
+                st = ctx.run_adaptive(scheme, sigma, t, max_attempts=4_000_000, raise_on_timeout=False)
+                u = ctx.get_state()
+                states.append(u)
+                rows.append({"t": st["t"], "k": st["k_last"], "steps": st["n_steps"], "n_fft": st["n_fft"],
+                             "centre_corner": probe(u)})
+            _progress(name, scheme, sigma, f"{time.perf_counter() - t0:.1f} s")
+        return rows, states
+
+    ref_rows, ref_states = solo(ref_scheme, ref_sigma)
+    runs = {f"{ref_scheme}_{ref_sigma:g}_reference": ref_rows}
+    members = [(s, x) for s in ("imex", "sav") for x in (1e-5, 1e-6, 1e-7)] + [("etd", 1e-5)]
+    with fch.Ensemble([n] * len(members), [p] * len(members)) as ens:
+        for i in range(len(members)):
+            ens[i].set_state(u0)
+        rows = [[] for _ in members]
+        t0 = time.perf_counter()
+        for j, t in enumerate(times):
+            st = ens.run_adaptive_each([m[0] for m in members], [m[1] for m in members], t, rounds=16)
+            for i in range(len(members)):
+                u = ens[i].get_state()
+                rows[i].append({"t": st[i]["t"], "k": st[i]["k_last"], "steps": st[i]["n_steps"],
+                                "n_fft": st[i]["n_fft"], "centre_corner": probe(u),
+                                "global_rel_l2": _rel(u, ref_states[j])})
+        _progress(f"ensemble of {len(members)}: {time.perf_counter() - t0:.1f} s")
+    for (s, x), r in zip(members, rows):
+        runs[f"{s}_{x:g}"] = r
+    for x in (1e-5, 1e-6, 1e-7):
+        r, states = solo("psd", x)
+        for row, u, ur in zip(r, states, ref_states):
+            row["global_rel_l2"] = _rel(u, ur)
+        runs[f"psd_{x:g}"] = r
+    # the mean accepted step over each output interval (the last step before an output
+    # time is clipped to it, so k_last there understates the controller's step)
+    for r in runs.values():
+        for j, row in enumerate(r):
+            t_prev, s_prev = (0.0, 0) if j == 0 else (r[j - 1]["t"], r[j - 1]["steps"])
+            row["mean_k"] = (row["t"] - t_prev) / max(1, row["steps"] - s_prev)
+    return {"figures": ["f:L2temp_error", "f:Stepsize", "f:corner-1"], "benchmark": name, "N": n, "T": T,
+            "precision": "fp32x2", "times": times,
+            "reference": {"scheme": ref_scheme, "sigma_tol": ref_sigma},
+            "probes": "u - b_- at the centre (x = y = 0) and the corner (x = y = -L/2) of the domain",
+            "runs": runs}
+
+
 def _rel(a, b):
     import numpy as np
     return float(np.linalg.norm(a - b) / np.linalg.norm(b))
@@ -1138,6 +1212,9 @@ def main():
     ap.add_argument("--dollars-per-digit", action="store_true",
                     help="global error and transforms against sigma_tol (Sec. 5.2) for one benchmark instead")
     ap.add_argument("--dpd-benchmark", default="supercritical", choices=sorted(PAPER_REFERENCE))
+    ap.add_argument("--traces", action="store_true",
+                    help="global error, step size and far-field traces over time on one benchmark instead")
+    ap.add_argument("--trace-benchmark", default="supercritical", choices=sorted(PAPER_T))
     ap.add_argument("--dpd-sigmas", default="", help="comma-separated sigma_tol values of the sweep")
     ap.add_argument("--dpd-etd-min", type=float, default=1e-6, help="smallest sigma_tol of the ETD sweep")
     ap.add_argument("--dpd-psd-min", type=float, default=1e-7, help="smallest sigma_tol of the PSD sweep")
@@ -1170,6 +1247,8 @@ def main():
         out = comp_error(args)
     elif args.dollars_per_digit:
         out = dollars_per_digit(args)
+    elif args.traces:
+        out = traces(args)
     elif args.workloads:
         out = workloads(args)
     elif args.error_budget:
