@@ -598,6 +598,37 @@ def _paper_ensemble(members, T, rounds=16):
         return [(st[i], ens[i].get_state()) for i in range(len(members))], wall
 
 
+def _periodic_labels(mask):
+    """connected components (4-neighbour) of a boolean field on the periodic grid"""
+    import numpy as np
+    from scipy import ndimage
+
+    lab, m = ndimage.label(mask)
+    parent = list(range(m + 1))
+
+    def find(a):
+        while parent[a] != a:
+            parent[a] = parent[parent[a]]
+            a = parent[a]
+        return a
+
+    for a, b in ((lab[:, 0], lab[:, -1]), (lab[0, :], lab[-1, :])):
+        for x, y in zip(a, b):
+            if x and y:
+                rx, ry = find(int(x)), find(int(y))
+                if rx != ry:
+                    parent[rx] = ry
+    return len({find(i) for i in range(1, m + 1)})
+
+
+def _topology(u, level=-0.12):
+    """(components, holes) of the bilayer region {u > level} (the contour level of
+    Fig. f:contour): a closed bilayer loop is one component with one hole, an open
+    (end-capped) curve or a pearl one without; holes = components of the rest - 1"""
+    above = u > level
+    return _periodic_labels(above), max(0, _periodic_labels(~above) - 1)
+
+
 def comp_error(args):
     """Table t:Comp-error: relative L2 differences at the final time T between the
     schemes' solutions of each benchmark at sigma_tol = 1e-5 (Sec. 4), FP32X2. The
@@ -634,6 +665,13 @@ def comp_error(args):
     def cell(a, b_):
         return None if a is None or b_ is None else _rel(a, b_)
 
+    # E1: the morphology at T of every run (the paper's descriptions: sub-critical and
+    # critical a single closed curve; Foot 1 six closed loops; Foot 2 four loops and
+    # two double loops)
+    topo = {f"{b}/{sc}": (None if u is None else
+                          dict(zip(("components", "holes"), _topology(u))) | {"max_u": float(u.max())})
+            for (b, sc), u in sols.items()}
+
     table = []
     for b in names:
         row = {"benchmark": b, "T": PAPER_T[b],
@@ -645,7 +683,8 @@ def comp_error(args):
             row["etd/psd"] = cell(sols[b, "etd"], sols[b, "psd"])
         table.append(row)
     return {"table": "t:Comp-error", "sigma_tol": sigma, "precision": "fp32x2",
-            "norm": "||u_a - u_b||_2 / ||u_b||_2 over the grid at T", "rows": table, "runs": runs}
+            "norm": "||u_a - u_b||_2 / ||u_b||_2 over the grid at T", "rows": table, "runs": runs,
+            "morphology_at_T": topo}
 
 
 def _loglog_at(xs, ys, x0):

@@ -65,3 +65,31 @@ def test_sweep_interpolation_helpers():
     assert bench._loglog_at(xs, ys, 1.0) is None
     assert abs(bench._slope(xs, ys) + 0.5) < 1e-12
     assert bench._slope([1.0], [2.0]) is None
+
+
+def test_morphology_counts_on_the_periodic_grid():
+    # loops (one hole each), a disc, and a loop that wraps around the corner
+    sys.path.insert(0, ROOT)
+    import numpy as np
+
+    import bench
+
+    n = 128
+    y, x = np.mgrid[0:n, 0:n]
+
+    def ring(cx, cy, r0, r1):
+        dx = np.minimum(abs(x - cx), n - abs(x - cx))
+        dy = np.minimum(abs(y - cy), n - abs(y - cy))
+        r = np.hypot(dx, dy)
+        return (r > r0) & (r < r1)
+
+    u = -np.ones((n, n))
+    u[ring(64, 64, 20, 26)] = 0.5
+    assert bench._topology(u) == (1, 1)
+    u[ring(2, 2, 8, 12)] = 0.5
+    assert bench._topology(u) == (2, 2)
+    u[ring(100, 30, -1, 4)] = 0.5
+    assert bench._topology(u) == (3, 2)
+    band = -np.ones((n, n))
+    band[:, 60:64] = 0.5
+    assert bench._topology(band) == (1, 0)
