@@ -1136,6 +1136,17 @@ def fno_bench(args):
         net.forward(a, y)
     torch.cuda.synchronize()
     out["fno_forward_ms_1024"] = (time.perf_counter() - t0) / 10 * 1e3
+    # BF16 weights with FP32 sums (inference): the same timing and the learned start
+    # on the held-out trajectories
+    net.set_bf16(True)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(10):
+        net.forward(a, y)
+    torch.cuda.synchronize()
+    out["fno_forward_ms_1024_bf16_weights"] = (time.perf_counter() - t0) / 10 * 1e3
+    out["eval_128_bf16_weights"] = evaluate(128, I.circle_bilayer(128, radius=2.1, noise=1e-3, seed=21), 30)
+    net.set_bf16(False)
     return out
 
 

@@ -284,6 +284,12 @@ fch_status fch_fno_get_grads(fch_fno *f, float *host, size_t count);
 fch_status fch_fno_forward(fch_fno *f, int batch, int n, const float *a_dev, float *y_dev);
 fch_status fch_fno_backward(fch_fno *f, const float *target_dev, double *loss);
 fch_status fch_fno_adam(fch_fno *f, float lr, float beta1, float beta2, float eps);
+/* fch_fno_set_bf16(f, 1): later forward passes read a bfloat16 copy of the
+ * parameters (rounded to nearest even; refreshed by set_params and every Adam step),
+ * products and sums staying in FP32: BF16 weights with FP32 accumulation for
+ * inference. Training keeps the FP32 weights: fch_fno_backward after a forward pass
+ * on the bfloat16 copy returns FCH_ESTATE. fch_fno_set_bf16(f, 0) frees the copy. */
+fch_status fch_fno_set_bf16(fch_fno *f, int on);
 
 /* One PSD-BDF2 step of size dt (as fch_step with FCH_PSD) whose iteration starts
  * from the real field v0 (device, n x n, dtype 0 double / 1 float) instead of u*.

@@ -37,6 +37,16 @@ def gelu(x):
     return 0.5 * x * (1.0 + erf(x * SQRT1_2))
 
 
+def bf16_round(x):
+    """float32 values rounded to bfloat16 (1 sign, 8 exponent, 7 stored mantissa
+    bits: the top half of the float32 pattern), to nearest with ties to even; finite
+    inputs. Returned as float32."""
+    b = np.ascontiguousarray(x, dtype=np.float32).view(np.uint32).astype(np.uint64)
+    lsb = (b >> 16) & 1
+    b = ((b + 0x7FFF + lsb) >> 16) << 16
+    return b.astype(np.uint32).view(np.float32)
+
+
 def gelu_grad(x):
     return 0.5 * (1.0 + erf(x * SQRT1_2)) + x * INV_SQRT_2PI * np.exp(-0.5 * x * x)
 

@@ -22,6 +22,7 @@
 // Q2, bQ2, with R_l as [K][W_out][W_in] complex (re, im interleaved).
 // Weight gradients are summed over points in a fixed order (per-block partials,
 // then one pass over the blocks), so a backward pass is deterministic.
+#include <cuda_bf16.h>
 #include <math.h>
 #include <stdio.h>
 #include <stdlib.h>
@@ -43,8 +44,25 @@ __device__ __forceinline__ float gelu_grad(float x)
 // ky of retained-mode row kyi
 __device__ __forceinline__ int mode_ky(int kyi, int M, int n) { return kyi < M ? kyi : n - (kyi - M + 1); }
 
+// a weight as float: the forward pass reads FP32 weights, or (inference with
+// fch_fno_set_bf16) their bfloat16 copy; sums stay in FP32 either way
+__device__ __forceinline__ float wld(const float *p, long i) { return p[i]; }
+__device__ __forceinline__ float wld(const __nv_bfloat16 *p, long i) { return __bfloat162float(p[i]); }
+__device__ __forceinline__ float2 wld2(const float *p, long i) { return make_float2(p[2 * i], p[2 * i + 1]); }
+__device__ __forceinline__ float2 wld2(const __nv_bfloat16 *p, long i)
+{
+    return __bfloat1622float2(reinterpret_cast<const __nv_bfloat162 *>(p)[i]);
+}
+
+__global__ void fno_to_bf16(const float *__restrict__ w, __nv_bfloat16 *__restrict__ out, long cnt)
+{
+    const long t = (long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t < cnt) out[t] = __float2bfloat16_rn(w[t]);
+}
+
 // h0[b][c][p] = sum_i P[c][i] a[b][i][p] + bP[c]
-__global__ void fno_lift(const float *__restrict__ a, const float *__restrict__ P, const float *__restrict__ bP,
+template <typename WT>
+__global__ void fno_lift(const float *__restrict__ a, const WT *__restrict__ P, const WT *__restrict__ bP,
                          float *__restrict__ h, int B, int n2, int W, int cin)
 {
     const long t = (long)blockIdx.x * blockDim.x + threadIdx.x;
@@ -53,8 +71,8 @@ __global__ void fno_lift(const float *__restrict__ a, const float *__restrict__ 
     float in[4];
     for (int i = 0; i < cin; i++) in[i] = a[((long)b * cin + i) * n2 + p];
     for (int c = 0; c < W; c++) {
-        float acc = bP[c];
-        for (int i = 0; i < cin; i++) acc += P[c * cin + i] * in[i];
+        float acc = wld(bP, c);
+        for (int i = 0; i < cin; i++) acc += wld(P, c * cin + i) * in[i];
         h[((long)b * W + c) * n2 + p] = acc;
     }
 }
@@ -62,15 +80,15 @@ __global__ void fno_lift(const float *__restrict__ a, const float *__restrict__ 
 // z[b][c][p] = sum_j Wl[c][j] h[b][j][p] + bl[c] + s[b][c][p];  out = act(z)
 // (W, the channel count, is a compile-time constant so the per-point channel
 // vectors stay in registers)
-template <int W>
+template <int W, typename WT = float>
 __global__ void fno_pointwise(const float *__restrict__ h, const float *__restrict__ s,
-                              const float *__restrict__ Wl, const float *__restrict__ bl, float *__restrict__ z,
+                              const WT *__restrict__ Wl, const WT *__restrict__ bl, float *__restrict__ z,
                               float *__restrict__ out, int B, int n2, int act)
 {
     __shared__ float ws[W * W];
     __shared__ float bs[W];
-    for (int i = threadIdx.x; i < W * W; i += blockDim.x) ws[i] = Wl[i];
-    for (int i = threadIdx.x; i < W; i += blockDim.x) bs[i] = bl[i];
+    for (int i = threadIdx.x; i < W * W; i += blockDim.x) ws[i] = wld(Wl, i);
+    for (int i = threadIdx.x; i < W; i += blockDim.x) bs[i] = wld(bl, i);
     __syncthreads();
     const long t = (long)blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= (long)B * n2) return;
@@ -89,9 +107,9 @@ __global__ void fno_pointwise(const float *__restrict__ h, const float *__restri
 }
 
 // y[b][p] = bQ2 + sum_d Q2[d] GELU(bQ1[d] + sum_c Q1[d][c] h[b][c][p])
-template <int W>
-__global__ void fno_project(const float *__restrict__ h, const float *__restrict__ Q1, const float *__restrict__ bQ1,
-                            const float *__restrict__ Q2, const float *__restrict__ bQ2, float *__restrict__ y,
+template <int W, typename WT = float>
+__global__ void fno_project(const float *__restrict__ h, const WT *__restrict__ Q1, const WT *__restrict__ bQ1,
+                            const WT *__restrict__ Q2, const WT *__restrict__ bQ2, float *__restrict__ y,
                             int B, int n2, int W2)
 {
     const long t = (long)blockIdx.x * blockDim.x + threadIdx.x;
@@ -100,12 +118,12 @@ __global__ void fno_project(const float *__restrict__ h, const float *__restrict
     float in[W];
 #pragma unroll
     for (int c = 0; c < W; c++) in[c] = h[((long)b * W + c) * n2 + p];
-    float acc = bQ2[0];
+    float acc = wld(bQ2, 0);
     for (int d = 0; d < W2; d++) {
-        float zq = bQ1[d];
+        float zq = wld(bQ1, d);
 #pragma unroll
-        for (int c = 0; c < W; c++) zq += Q1[d * W + c] * in[c];
-        acc += Q2[d] * gelu(zq);
+        for (int c = 0; c < W; c++) zq += wld(Q1, d * W + c) * in[c];
+        acc += wld(Q2, d) * gelu(zq);
     }
     y[(long)b * n2 + p] = acc;
 }
@@ -179,7 +197,8 @@ __global__ void fno_pointwise_bwd(const float *__restrict__ dout, const float *_
 // Y[b W + o](m) = sum_i R[m][o][i] X[b W + i](m) on the retained modes, written
 // through H at kx = 0 (work item: one mode, or at kx = 0 the pair ky, -ky).
 // X and Y are spectra [field][kx][ky]; S = (n/2 + 1) n complex per field.
-__global__ void fno_mix(const float2 *__restrict__ X, const float2 *__restrict__ R, float2 *__restrict__ Y,
+template <typename WT>
+__global__ void fno_mix(const float2 *__restrict__ X, const WT *__restrict__ R, float2 *__restrict__ Y,
                         int B, int W, int M, int n)
 {
     const int items = M + (M - 1) * (2 * M - 1);
@@ -190,11 +209,11 @@ __global__ void fno_mix(const float2 *__restrict__ X, const float2 *__restrict__
     const int K2 = 2 * M - 1;
     auto mixed = [&](int kx, int kyi) {
         const int ky = mode_ky(kyi, M, n);
-        const float2 *r = R + ((long)(kx * K2 + kyi) * W + o) * W;
+        const long r = ((long)(kx * K2 + kyi) * W + o) * W; // complex index of R[m][o][0]
         float re = 0.f, im = 0.f;
         for (int i = 0; i < W; i++) {
             const float2 x = X[((long)b * W + i) * S + (long)kx * n + ky];
-            const float2 w = r[i];
+            const float2 w = wld2(R, r + i);
             re += w.x * x.x - w.y * x.y;
             im += w.x * x.y + w.y * x.x;
         }
@@ -405,6 +424,8 @@ struct fch_fno {
     float *part;          // weight-gradient partials
     const float *a;       // the last forward pass's input
     bool have_fwd;
+    __nv_bfloat16 *pbf;   // bfloat16 copy of params (fch_fno_set_bf16), else null
+    bool fwd_bf16;        // the last forward pass read the bfloat16 copy
     double *hsum;
     char err[256];
 };
@@ -496,6 +517,17 @@ inline unsigned grid(long cnt, int bs) { return (unsigned)((cnt + bs - 1) / bs);
             kern<32><<<(g), (b), 0, (st)>>>(__VA_ARGS__);                                          \
     } while (0)
 
+// the same for a kernel templated on the channel count and the weight type
+#define WDISPATCH_T(Wv, kern, WT, g, b, st, ...)                                                   \
+    do {                                                                                           \
+        if ((Wv) == 8)                                                                             \
+            kern<8, WT><<<(g), (b), 0, (st)>>>(__VA_ARGS__);                                       \
+        else if ((Wv) == 16)                                                                       \
+            kern<16, WT><<<(g), (b), 0, (st)>>>(__VA_ARGS__);                                      \
+        else                                                                                       \
+            kern<32, WT><<<(g), (b), 0, (st)>>>(__VA_ARGS__);                                      \
+    } while (0)
+
 // weight gradient G[na][nb] = sum_points A Bm^T into out (device)
 cudaError_t wgrad(fch_fno *f, const float *A, int CA, int na, const float *Bm, int CB, int nb, float *out)
 {
@@ -552,7 +584,7 @@ extern "C" fch_status fch_fno_destroy(fch_fno *f)
     if (!f) return FCH_OK;
     if (f->stream) cudaStreamSynchronize(f->stream);
     free_buffers(f);
-    for (void *b : {(void *)f->params, (void *)f->grads, (void *)f->am, (void *)f->av})
+    for (void *b : {(void *)f->params, (void *)f->grads, (void *)f->am, (void *)f->av, (void *)f->pbf})
         if (b) cudaFree(b);
     if (f->hsum) cudaFreeHost(f->hsum);
     free(f);
@@ -565,6 +597,8 @@ extern "C" fch_status fch_fno_num_params(const fch_fno *f, size_t *count)
     *count = f->np;
     return FCH_OK;
 }
+
+static fch_status refresh_bf16(fch_fno *f);
 
 static fch_status copy_vec(fch_fno *f, float *dev, const float *src_host, float *dst_host, size_t cnt)
 {
@@ -583,6 +617,7 @@ extern "C" fch_status fch_fno_set_params(fch_fno *f, const float *host, size_t c
         cudaMemsetAsync(f->am, 0, f->np * 4, f->stream);
         cudaMemsetAsync(f->av, 0, f->np * 4, f->stream);
         f->adam_t = 0;
+        s = refresh_bf16(f);
     }
     return s;
 }
@@ -599,34 +634,31 @@ extern "C" fch_status fch_fno_get_grads(fch_fno *f, float *host, size_t cnt)
     return copy_vec(f, f ? f->grads : nullptr, nullptr, host, cnt);
 }
 
-extern "C" fch_status fch_fno_forward(fch_fno *f, int batch, int n, const float *a, float *y)
+// the forward pass with weights P of type WT (FP32 parameters or their bfloat16 copy)
+template <typename WT>
+static fch_status forward_impl(fch_fno *f, int batch, int n, const float *a, float *y, const WT *P)
 {
-    if (!f || !a || !y || batch < 1 || n < 2 * f->M || n < 16 || n > 2048 || (n & (n - 1))) {
-        fch_set_thread_error("fch_fno_forward: invalid argument");
-        return FCH_EINVAL;
-    }
     fch_status st = ensure_buffers(f, batch, n);
     if (st != FCH_OK) return st;
     const int W = f->W, n2 = n * n;
     const long pts = (long)batch * n2;
     const size_t fld = (size_t)batch * W * n2, S = (size_t)(n / 2 + 1) * n;
     cudaStream_t s = f->stream;
-    const float *P = f->params;
-    fno_lift<<<grid(pts, 256), 256, 0, s>>>(a, P + offset_of(f, 0, 0), P + offset_of(f, 1, 0), f->h, batch, n2, W,
-                                            f->cin);
+    fno_lift<WT><<<grid(pts, 256), 256, 0, s>>>(a, P + offset_of(f, 0, 0), P + offset_of(f, 1, 0), f->h, batch, n2,
+                                                W, f->cin);
     for (int l = 0; l < f->L; l++) {
         float *hin = f->h + l * fld, *hout = f->h + (l + 1) * fld;
         float2 *X = f->X + (size_t)l * batch * W * S;
         if ((st = fch_fft_r2c(f->plan, hin, X, batch * W)) != FCH_OK) return st;
         const int items = f->M + (f->M - 1) * (2 * f->M - 1);
-        fno_mix<<<grid((long)batch * W * items, 256), 256, 0, s>>>(
-            X, (const float2 *)(P + offset_of(f, 4, l)), f->Ysp, batch, W, f->M, n);
+        fno_mix<WT><<<grid((long)batch * W * items, 256), 256, 0, s>>>(X, P + offset_of(f, 4, l), f->Ysp, batch, W,
+                                                                      f->M, n);
         if ((st = fch_fft_c2r(f->plan, f->Ysp, f->s, batch * W)) != FCH_OK) return st;
-        WDISPATCH(W, fno_pointwise, grid(pts, 128), 128, s, hin, f->s, P + offset_of(f, 2, l),
-                  P + offset_of(f, 3, l), f->z + l * fld, hout, batch, n2, l < f->L - 1);
+        WDISPATCH_T(W, fno_pointwise, WT, grid(pts, 128), 128, s, hin, f->s, P + offset_of(f, 2, l),
+                    P + offset_of(f, 3, l), f->z + l * fld, hout, batch, n2, l < f->L - 1);
     }
-    WDISPATCH(W, fno_project, grid(pts, 128), 128, s, f->h + f->L * fld, P + offset_of(f, 5, 0),
-              P + offset_of(f, 6, 0), P + offset_of(f, 7, 0), P + offset_of(f, 8, 0), y, batch, n2, f->W2);
+    WDISPATCH_T(W, fno_project, WT, grid(pts, 128), 128, s, f->h + f->L * fld, P + offset_of(f, 5, 0),
+                P + offset_of(f, 6, 0), P + offset_of(f, 7, 0), P + offset_of(f, 8, 0), y, batch, n2, f->W2);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) {
         snprintf(f->err, sizeof(f->err), "fch_fno_forward: %s", cudaGetErrorString(e));
@@ -640,10 +672,47 @@ extern "C" fch_status fch_fno_forward(fch_fno *f, int batch, int n, const float 
     return e == cudaSuccess ? FCH_OK : FCH_ECUDA;
 }
 
+// refresh the bfloat16 copy of the parameters (round to nearest even)
+static fch_status refresh_bf16(fch_fno *f)
+{
+    if (!f->pbf) return FCH_OK;
+    fno_to_bf16<<<grid((long)f->np, 256), 256, 0, f->stream>>>(f->params, f->pbf, (long)f->np);
+    return cudaGetLastError() == cudaSuccess ? FCH_OK : FCH_ECUDA;
+}
+
+extern "C" fch_status fch_fno_set_bf16(fch_fno *f, int on)
+{
+    if (!f) return FCH_EINVAL;
+    if (on && !f->pbf) {
+        if (cudaMalloc((void **)&f->pbf, f->np * sizeof(__nv_bfloat16)) != cudaSuccess) {
+            f->pbf = nullptr;
+            return FCH_ENOMEM;
+        }
+        return refresh_bf16(f);
+    }
+    if (!on && f->pbf) {
+        cudaStreamSynchronize(f->stream);
+        cudaFree(f->pbf);
+        f->pbf = nullptr;
+    }
+    return FCH_OK;
+}
+
+extern "C" fch_status fch_fno_forward(fch_fno *f, int batch, int n, const float *a, float *y)
+{
+    if (!f || !a || !y || batch < 1 || n < 2 * f->M || n < 16 || n > 2048 || (n & (n - 1))) {
+        fch_set_thread_error("fch_fno_forward: invalid argument");
+        return FCH_EINVAL;
+    }
+    f->fwd_bf16 = f->pbf != nullptr;
+    return f->pbf ? forward_impl(f, batch, n, a, y, (const __nv_bfloat16 *)f->pbf)
+                  : forward_impl(f, batch, n, a, y, (const float *)f->params);
+}
+
 extern "C" fch_status fch_fno_backward(fch_fno *f, const float *target, double *loss)
 {
     if (!f || !target) return FCH_EINVAL;
-    if (!f->have_fwd) return FCH_ESTATE;
+    if (!f->have_fwd || f->fwd_bf16) return FCH_ESTATE; // training runs on the FP32 weights
     const int B = f->B, n = f->n, W = f->W, W2 = f->W2, n2 = n * n;
     const long pts = (long)B * n2;
     const size_t fld = (size_t)B * W * n2, S = (size_t)(n / 2 + 1) * n;
@@ -708,5 +777,6 @@ extern "C" fch_status fch_fno_adam(fch_fno *f, float lr, float beta1, float beta
     const float c1 = 1.f - powf(beta1, (float)f->adam_t), c2 = 1.f - powf(beta2, (float)f->adam_t);
     fno_adam<<<grid((long)f->np, 256), 256, 0, f->stream>>>(f->params, f->grads, f->am, f->av, (long)f->np, lr, beta1,
                                                             beta2, eps, c1, c2);
-    return cudaGetLastError() == cudaSuccess ? FCH_OK : FCH_ECUDA;
+    if (cudaGetLastError() != cudaSuccess) return FCH_ECUDA;
+    return refresh_bf16(f);
 }

@@ -35,7 +35,7 @@ EXPORTS = ["fch_status_string", "fch_last_cuda_error", "fch_params_default", "fc
            "fch_fno_set_params", "fch_fno_get_params", "fch_fno_get_grads", "fch_fno_forward",
            "fch_fno_backward", "fch_fno_adam", "fch_step_psd_from", "fch_run_fixed",
            "fch_adaptive_trial_info", "fch_get_history_device", "fch_adaptive_enqueue_psd_from",
-           "fch_ensemble_run_adaptive_each", "fch_autotune_step", "fch_step_from"]
+           "fch_ensemble_run_adaptive_each", "fch_autotune_step", "fch_step_from", "fch_fno_set_bf16"]
 NCOL, NROW = 10, 8
 NPASS = NCOL + NROW + 1
 PASS_NAMES = (["col_fwd_store", "col_inv_load", "col_start", "col_imex_solve", "col_f_finish",
@@ -140,6 +140,7 @@ def lib():
         L.fch_fno_forward.argtypes = [vp, C.c_int, C.c_int, vp, vp]
         L.fch_fno_backward.argtypes = [vp, vp, C.POINTER(C.c_double)]
         L.fch_fno_adam.argtypes = [vp, C.c_float, C.c_float, C.c_float, C.c_float]
+        L.fch_fno_set_bf16.argtypes = [vp, C.c_int]
         L.fch_step_psd_from.argtypes = [vp, C.c_double, vp, C.c_int]
         L.fch_step_from.argtypes = [vp, C.c_int, C.c_double, vp, C.c_int]
         L.fch_run_fixed.argtypes = [vp, C.c_int, C.c_double, C.c_longlong]
@@ -562,3 +563,7 @@ class FNO:
 
     def adam(self, lr=1e-3, beta1=0.9, beta2=0.999, eps=1e-8):
         _check(lib().fch_fno_adam(self._h, lr, beta1, beta2, eps), "fch_fno_adam")
+
+    def set_bf16(self, on: bool):
+        """forward passes on a bfloat16 copy of the weights (FP32 sums), or back to FP32"""
+        _check(lib().fch_fno_set_bf16(self._h, int(bool(on))), "fch_fno_set_bf16")

@@ -77,3 +77,16 @@ def test_gradient_matches_finite_differences(seed):
             e[i] = eps
             fd = (F.loss(params + e, a, target, cfg) - F.loss(params - e, a, target, cfg)) / (2 * eps)
             assert abs(fd - g[i]) <= 1e-6 * max(1e-3, abs(fd)) + 1e-9, (name, i, fd, g[i])
+
+
+def test_bf16_round_ties_to_even_and_matches_torch():
+    # the bfloat16 grid near 1 has spacing 2^-7: ties go to the even pattern
+    x = np.array([1.0, 1 + 2.0 ** -8, 1 + 3 * 2.0 ** -8, 1 + 2.0 ** -8 + 2.0 ** -20, -2.5, 3e-30, 65504.0],
+                 dtype=np.float32)
+    got = F.bf16_round(x)
+    assert list(got[:4]) == [1.0, 1.0, 1 + 2.0 ** -6, 1 + 2.0 ** -7]
+    torch = pytest.importorskip("torch")
+    r = np.random.default_rng(4).standard_normal(10000).astype(np.float32) * 10.0 ** np.random.default_rng(5).uniform(-6, 6, 10000).astype(np.float32)
+    for v in (x, r):
+        ref = torch.tensor(v).to(torch.bfloat16).float().numpy()
+        assert np.array_equal(F.bf16_round(v), ref)

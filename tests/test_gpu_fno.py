@@ -52,6 +52,33 @@ def test_fno_forward_backward_vs_oracle(width, layers, modes, proj, n, batch):
         o += k
 
 
+def test_fno_bf16_weights_forward_vs_oracle():
+    # BF16 weights, FP32 sums: the forward pass equals the oracle's on the weights
+    # rounded to bfloat16; training refuses the bfloat16 forward pass
+    cfg = F.Config(width=32, layers=4, modes=16, proj=64)
+    n, batch = 64, 2
+    rng = np.random.default_rng(12)
+    params = (F.init_params(cfg, 0) + 0.05 * rng.standard_normal(cfg.size())).astype(np.float32)
+    a = rng.standard_normal((batch, 2, n, n)).astype(np.float32)
+    net = fch.FNO(32, 4, 16, 64)
+    net.set_params(params)
+    net.set_bf16(True)
+    at = torch.tensor(a, device=DEV)
+    y = torch.empty((batch, n, n), device=DEV)
+    net.forward(at, y)
+    a64 = a.astype(np.float64)
+    y_bf = F.forward(F.bf16_round(params).astype(np.float64), a64, cfg)
+    y_32 = F.forward(params.astype(np.float64), a64, cfg)
+    assert rel(y.cpu().numpy(), y_bf) < 2e-5
+    assert rel(y_bf, y_32) > 1e-4  # the rounding is visible, so the copy was read
+    with pytest.raises(fch.FchError):
+        net.backward(torch.zeros((batch, n, n), device=DEV))
+    net.set_bf16(False)
+    net.forward(at, y)
+    assert rel(y.cpu().numpy(), y_32) < 2e-5
+    net.backward(torch.zeros((batch, n, n), device=DEV))
+
+
 def test_fno_training_reduces_the_loss():
     # fit a fixed smooth map (a band-limited filter of the first channel plus a
     # quadratic term) on a fixed batch: Adam on the library's gradients
