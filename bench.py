@@ -972,7 +972,7 @@ def ensemble_bench(args):
     bilayer initial data, adaptive IMEX-BDF2 at sigma_tol = 1e-5 to t_final, in
     one CUDA graph per launch (fch_ensemble_run_adaptive), against the same 64
     instances run one after another (fch_run_adaptive each). Pass tiles from the
-    autotuner for both."""
+    step tuner (fch_autotune_step) for both unless --ensemble-autotune says otherwise."""
     import numpy as np
 
     from paper_2006_04784_gb300 import build as B
@@ -984,7 +984,7 @@ def ensemble_bench(args):
     sizes = [256] * 32 + [512] * 24 + [1024] * 8
     m = len(sizes)
     eps = 0.1
-    params = [fch.params_default(0.0, eta1=eps * (1.0 + 2.0 * i / (m - 1)), prec=prec, autotune=1,
+    params = [fch.params_default(0.0, eta1=eps * (1.0 + 2.0 * i / (m - 1)), prec=prec, autotune=args.ensemble_autotune,
                                  sync_every=64) for i in range(m)]
     inits = [I.multimode_bilayer(n, seed=100 + i) for i, n in enumerate(sizes)]
     tf = args.ensemble_t
@@ -1279,6 +1279,8 @@ def main():
                     help="the 64-instance uneven-grid ensemble against sequential runs instead")
     ap.add_argument("--ensemble-t", type=float, default=0.02)
     ap.add_argument("--ensemble-rounds", type=int, default=8)
+    ap.add_argument("--ensemble-autotune", type=int, default=2, choices=[0, 1, 2],
+                    help="pass tiles of the ensemble's members (as fch_params.autotune)")
     ap.add_argument("--fno", action="store_true",
                     help="train the FNO initial iterate and compare PSD started from it instead")
     ap.add_argument("--fno-steps", type=int, default=60)
