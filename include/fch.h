@@ -161,7 +161,9 @@ fch_status fch_get_state_device(fch_ctx *ctx, void *u_dev, int dtype);
 /* One step of size dt with the given scheme (Secs. 3.3-3.6):
  * IMEX eq. (IMEX-eq); SAV eqs. (4.7)-(4.8); PSD eqs. (residual), (recurrence)
  * with i_tol = psd_itol; ETDRK2 eqs. (ETDRK2), (ETD-L). Enqueued without waiting;
- * PSD waits after every few iterations to test convergence. */
+ * PSD enqueues its iterations in chunks of four (as many chunks as the previous
+ * solve took, then one at a time) and waits after each batch to read the stopping
+ * test; chunks after convergence return at once on the device. */
 fch_status fch_step(fch_ctx *ctx, fch_scheme scheme, double dt);
 
 /* nsteps fixed steps of size dt, as nsteps fch_step calls, without host work
