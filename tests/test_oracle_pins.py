@@ -550,6 +550,15 @@ def test_step_from_with_the_extrapolation_is_the_plain_step(scheme):
     assert np.array_equal(out[0], out[1])
 
 
+def test_step_from_takes_imex_and_sav_only():
+    N = 16
+    s = O.Stepper(N, L, O.params())
+    s.set_state(I.circle_bilayer(N))
+    for scheme in ("psd", "etd"):
+        with pytest.raises(RuntimeError):
+            s.step_from(scheme, 1e-4, s.state())
+
+
 @pytest.mark.parametrize("q", [0.0, 0.2])
 def test_imex_step_from_the_implicit_solution_returns_it(q):
     # a fixed point of the fully implicit BDF2, eq. (BDF2), is a fixed point of the
