@@ -416,6 +416,12 @@ typedef struct {
     long n_steps, n_rejects, n_psd_iter, n_attempts;
     int last_psd_iter;
     double last_e;
+    /* adaptive runs, Sec. 3.2: the next trial size (Step 0 / Step 4), the size and
+     * the decision of the last trial, and the open run's scheme, sigma_tol, t_final */
+    double ktrial, last_k;
+    int last_accepted;
+    int ad_scheme;
+    double ad_sigma, ad_tfinal;
     const double *ustar_given; /* a caller's u* for the next step (orc_step_from), else NULL */
     /* work */
     double *w[10];
@@ -463,6 +469,7 @@ void orc_set_state(orc_ctx *s, const double *u0)
     memcpy(s->u, u0, sizeof(double) * n);
     memset(s->um, 0, sizeof(double) * n);
     s->kn = 0;
+    s->ktrial = 0;
     s->t = 0;
     s->have_F = 0;
     s->r = sav_r_of(s, s->u);
@@ -478,6 +485,7 @@ void orc_set_history(orc_ctx *s, const double *un, const double *unm1, double kn
     memcpy(s->u, un, sizeof(double) * n);
     memcpy(s->um, unm1, sizeof(double) * n);
     s->kn = kn;
+    s->ktrial = kn; /* Step 0: the first trial repeats k_n */
     s->have_F = 0;
     s->r = sav_r_of(s, s->u);
     s->rm = sav_r_of(s, s->um);
@@ -497,6 +505,10 @@ void orc_get_counts(const orc_ctx *s, long *out)
     out[4] = s->last_psd_iter;
 }
 double orc_get_last_e(const orc_ctx *s) { return s->last_e; }
+/* size of the last trial step, its decision (1 accepted), and the next trial size */
+double orc_get_last_k(const orc_ctx *s) { return s->last_k; }
+int orc_get_last_accepted(const orc_ctx *s) { return s->last_accepted; }
+double orc_get_next_k(const orc_ctx *s) { return s->ktrial; }
 
 /* u* = u^n + (k_{n+1}/k_n)(u^n - u^{n-1}), eq. (Richardson); u* = u^n at the start.
  * A u* given by orc_step_from replaces the extrapolation: eqs. (IMEX-eq) and
@@ -757,6 +769,7 @@ static void accept(orc_ctx *s, const double *unew, double rnew, double k1)
     s->rm = s->r;
     s->r = rnew;
     s->kn = k1;
+    s->ktrial = k1; /* Step 0: the next step's first trial repeats k_n */
     s->t += k1;
     s->n_steps++;
 }
@@ -803,17 +816,21 @@ static double clampk(const orc_params *p, double k)
     return kk > p->k_min ? kk : p->k_min;
 }
 
-/* The adaptive algorithm of Sec. 3.2, Steps 0-4, with the AM3 predictor of eq. (Predictor)
- * and e = ||ut - u_p|| / ||u_p||. Runs until t_final or max_attempts trial steps.
- * Returns 0, -1 (PSD did not converge), or 1 (attempt budget used up). */
-int orc_run_adaptive(orc_ctx *s, int scheme, double sigma, double t_final, long max_attempts)
+/* Set-up of an adaptive run, Sec. 3.2: the first step k_1 = k_min by the
+ * backward-Euler start when there is no history (reading R1), and the F history
+ * F(u^n), F(u^{n-1}) the predictor needs. The run continues from the current trial
+ * size (Step 0 after a fixed step or a new history; the last proposal of Step 4
+ * when a run is resumed). Returns 0, or -1 when the PSD iteration failed. */
+int orc_adaptive_begin(orc_ctx *s, int scheme, double sigma, double t_final)
 {
     long n = npts(&s->g);
     double itol = s->p.psd_nu * sigma;
-    double *ut = s->w[9], *up = s->w[8], *Ft = s->w[7];
+    double *ut = s->w[9];
     double rnew;
+    s->ad_scheme = scheme;
+    s->ad_sigma = sigma;
+    s->ad_tfinal = t_final;
     if (s->kn <= 0) {
-        /* first step: k_1 = k_min by the backward-Euler start (reading R1) */
         double k1 = s->p.k_min;
         orc_rhs(&s->p, s->g.N, s->g.L, s->u, s->Fn);
         int rc = trial(s, scheme, k1, itol, ut, &rnew);
@@ -828,39 +845,70 @@ int orc_run_adaptive(orc_ctx *s, int scheme, double sigma, double t_final, long 
         orc_rhs(&s->p, s->g.N, s->g.L, s->um, s->Fm);
         s->have_F = 1;
     }
-    double ktrial = s->kn; /* Step 0 */
-    long attempts = 0;
-    while (t_final - s->t > 1e-12 * (t_final > 1 ? t_final : 1)) {
-        if (attempts >= max_attempts) return 1;
-        double k1 = ktrial;
-        if (k1 > t_final - s->t) k1 = t_final - s->t; /* reading R4 */
-        int rc = trial(s, scheme, k1, itol, ut, &rnew); /* Step 1 */
-        attempts++;
-        s->n_attempts++;
-        if (rc) return rc;
-        /* Step 2: AM3 predictor */
-        orc_rhs(&s->p, s->g.N, s->g.L, ut, Ft);
-        double w1, w2, w3;
-        orc_am3_coef(k1, s->kn, &w1, &w2, &w3);
-        for (long i = 0; i < n; i++) up[i] = s->u[i] + w1 * Ft[i] + w2 * s->Fn[i] + w3 * s->Fm[i];
-        /* Step 3: relative error (reading R6) */
-        double num = 0, den = 0;
-        for (long i = 0; i < n; i++) {
-            num += (ut[i] - up[i]) * (ut[i] - up[i]);
-            den += up[i] * up[i];
-        }
-        double e = sqrt(num) / sqrt(den);
-        s->last_e = e;
-        double knew = clampk(&s->p, a_dp(&s->p, sigma, e, k1));
-        /* Step 4 */
-        if (e <= sigma || k1 <= s->p.k_min) {
-            accept(s, ut, rnew, k1);
-            memcpy(s->Fm, s->Fn, sizeof(double) * n);
-            memcpy(s->Fn, Ft, sizeof(double) * n);
-        } else {
-            s->n_rejects++;
-        }
-        ktrial = knew;
-    }
     return 0;
+}
+
+/* One pass through Steps 1-4 of the adaptive algorithm of Sec. 3.2 for the run
+ * opened by orc_adaptive_begin: the trial of size k~ (clipped to t_final, reading
+ * R4), the AM3 predictor of eq. (Predictor), e = ||ut - u_p|| / ||u_p|| (reading R6),
+ * and the decision: accept when e <= sigma_tol or k~ <= k_min (reading R5); either
+ * way the next trial size is max(k_min, min(A_dp(e, k~), k_max)) (reading R2).
+ * Returns 0 after a trial, 2 when t_final is reached (no trial), -1 when the PSD
+ * iteration did not converge. */
+int orc_adaptive_trial(orc_ctx *s)
+{
+    long n = npts(&s->g);
+    const double sigma = s->ad_sigma, t_final = s->ad_tfinal;
+    double itol = s->p.psd_nu * sigma;
+    double *ut = s->w[9], *up = s->w[8], *Ft = s->w[7];
+    double rnew;
+    if (!(t_final - s->t > 1e-12 * (t_final > 1 ? t_final : 1))) return 2;
+    double k1 = s->ktrial;
+    if (k1 > t_final - s->t) k1 = t_final - s->t; /* reading R4 */
+    s->last_k = k1;
+    int rc = trial(s, s->ad_scheme, k1, itol, ut, &rnew); /* Step 1 */
+    s->n_attempts++;
+    if (rc) return rc;
+    /* Step 2: AM3 predictor */
+    orc_rhs(&s->p, s->g.N, s->g.L, ut, Ft);
+    double w1, w2, w3;
+    orc_am3_coef(k1, s->kn, &w1, &w2, &w3);
+    for (long i = 0; i < n; i++) up[i] = s->u[i] + w1 * Ft[i] + w2 * s->Fn[i] + w3 * s->Fm[i];
+    /* Step 3: relative error (reading R6) */
+    double num = 0, den = 0;
+    for (long i = 0; i < n; i++) {
+        num += (ut[i] - up[i]) * (ut[i] - up[i]);
+        den += up[i] * up[i];
+    }
+    double e = sqrt(num) / sqrt(den);
+    s->last_e = e;
+    double knew = clampk(&s->p, a_dp(&s->p, sigma, e, k1));
+    /* Step 4 */
+    if (e <= sigma || k1 <= s->p.k_min) {
+        accept(s, ut, rnew, k1);
+        memcpy(s->Fm, s->Fn, sizeof(double) * n);
+        memcpy(s->Fn, Ft, sizeof(double) * n);
+        s->last_accepted = 1;
+    } else {
+        s->n_rejects++;
+        s->last_accepted = 0;
+    }
+    s->ktrial = knew;
+    return 0;
+}
+
+/* The adaptive algorithm of Sec. 3.2, Steps 0-4 (orc_adaptive_begin, then
+ * orc_adaptive_trial until t_final or max_attempts trial steps).
+ * Returns 0, -1 (PSD did not converge), or 1 (attempt budget used up). */
+int orc_run_adaptive(orc_ctx *s, int scheme, double sigma, double t_final, long max_attempts)
+{
+    int rc = orc_adaptive_begin(s, scheme, sigma, t_final);
+    if (rc) return rc;
+    for (long attempts = 0;; attempts++) {
+        if (!(t_final - s->t > 1e-12 * (t_final > 1 ? t_final : 1))) return 0;
+        if (attempts >= max_attempts) return 1;
+        rc = orc_adaptive_trial(s);
+        if (rc == 2) return 0;
+        if (rc) return rc;
+    }
 }

@@ -98,6 +98,16 @@ def lib():
             L.orc_step_from.restype = C.c_int
             L.orc_run_adaptive.argtypes = [C.c_void_p, C.c_int, C.c_double, C.c_double, C.c_long]
             L.orc_run_adaptive.restype = C.c_int
+            L.orc_adaptive_begin.argtypes = [C.c_void_p, C.c_int, C.c_double, C.c_double]
+            L.orc_adaptive_begin.restype = C.c_int
+            L.orc_adaptive_trial.argtypes = [C.c_void_p]
+            L.orc_adaptive_trial.restype = C.c_int
+            L.orc_get_last_k.argtypes = [C.c_void_p]
+            L.orc_get_last_k.restype = C.c_double
+            L.orc_get_next_k.argtypes = [C.c_void_p]
+            L.orc_get_next_k.restype = C.c_double
+            L.orc_get_last_accepted.argtypes = [C.c_void_p]
+            L.orc_get_last_accepted.restype = C.c_int
             _lib = L
     return _lib
 
@@ -268,3 +278,26 @@ class Stepper:
     def run_adaptive(self, scheme, sigma, t_final, max_attempts=10**9):
         s = SCHEMES[scheme] if isinstance(scheme, str) else scheme
         return lib().orc_run_adaptive(self._h, s, float(sigma), float(t_final), int(max_attempts))
+
+    def adaptive_begin(self, scheme, sigma, t_final):
+        """open an adaptive run (start step and F history); 0 or -1 (PSD failure)"""
+        s = SCHEMES[scheme] if isinstance(scheme, str) else scheme
+        return lib().orc_adaptive_begin(self._h, s, float(sigma), float(t_final))
+
+    def adaptive_trial(self):
+        """one trial of the open run: 0 after a trial, 2 at t_final, -1 PSD failure"""
+        return lib().orc_adaptive_trial(self._h)
+
+    @property
+    def last_k(self):
+        """size of the last trial step"""
+        return lib().orc_get_last_k(self._h)
+
+    @property
+    def next_k(self):
+        """size of the next trial step"""
+        return lib().orc_get_next_k(self._h)
+
+    @property
+    def last_accepted(self):
+        return bool(lib().orc_get_last_accepted(self._h))

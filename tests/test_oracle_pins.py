@@ -579,3 +579,176 @@ def test_imex_step_from_the_implicit_solution_returns_it(q):
     t2.set_history(un, um, kn)
     t2.step("imex", dt)
     assert np.linalg.norm(t2.state() - u_bdf2) / np.linalg.norm(u_bdf2) > 1e-9
+
+
+# ----------------------------------------------------------------------------- step-size controller
+# Sec. 3.2, Steps 0-4 and A_dp, pinned on the linear problem (quadratic well,
+# eta = 0), where a trial and its error estimate have closed forms per Fourier
+# mode: the BDF2 trial (a + s(k)) U~ = -b U^n - c U^{n-1} of eq. (BDF2Coef), the
+# right-hand side F(U) = -s(k) U, the AM3 predictor of eq. (Predictor) and
+# e = ||U~ - U_p|| / ||U_p|| (Parseval: the ratio of the real-space norms). The
+# decisions are then checked against the algorithm as printed, with the paper's
+# safety factor rho_s = 0.9 and exponent 1/3.
+RHO_S = 0.9  # Sec. 3.2
+
+
+def _bdf2_abc(k1, kn):
+    # eq. (BDF2Coef)
+    return 1 / k1 + 1 / (k1 + kn), -1 / k1 - 1 / kn, 1 / kn - 1 / (k1 + kn)
+
+
+def _am3_w(k1, kn):
+    # eq. (Predictor) with gamma = k1 / kn
+    g = k1 / kn
+    return k1 / 6 * (3 + 2 * g) / (1 + g), k1 / 6 * (3 + g), -k1 / 6 * g * g / (1 + g)
+
+
+class _Linear:
+    """the linear problem on 16^2 started from its exact solution at t0 - kn, t0"""
+
+    N, t0, kn = 16, 0.02, 2e-3
+
+    def __init__(self):
+        self.p0 = O.params(well=1, eta1=0.0, eta2=0.0)
+        am = float(_golden("alpha_m.txt")[0][1])  # alpha_m(0) = 1.7, Table t:Benchmark
+        k2 = ksq(self.N)
+        self.sym = k2 * (self.p0.eps ** 2 * k2 + am) ** 2
+        u0 = I.smooth_random(self.N, seed=12, amp=0.4, offset=-0.6, kmax=3)
+        self.U0 = np.fft.fft2(u0)
+        self.Un = np.exp(-self.sym * self.t0) * self.U0
+        self.Um = np.exp(-self.sym * (self.t0 - self.kn)) * self.U0
+        self.un = np.real(np.fft.ifft2(self.Un))
+        self.um = np.real(np.fft.ifft2(self.Um))
+
+    def trial(self, k1):
+        """closed-form trial of size k1 from (U^n, U^{n-1}, k_n): (U~, e)"""
+        a, b, c = _bdf2_abc(k1, self.kn)
+        Ut = (-b * self.Un - c * self.Um) / (a + self.sym)
+        w1, w2, w3 = _am3_w(k1, self.kn)
+        F = lambda U: -self.sym * U
+        Up = self.Un + w1 * F(Ut) + w2 * F(self.Un) + w3 * F(self.Um)
+        e = np.linalg.norm(Ut - Up) / np.linalg.norm(Up)
+        return np.real(np.fft.ifft2(Ut)), float(e)
+
+    def stepper(self, **kw):
+        s = O.Stepper(self.N, L, O.params(well=1, eta1=0.0, eta2=0.0, **kw))
+        s.set_history(self.un, self.um, self.kn)
+        return s
+
+
+def _proposal(sigma, e, k, k_min=1e-9, k_max=np.inf, cap=False):
+    kk = RHO_S * (sigma / e) ** (1.0 / 3.0) * k  # A_dp
+    if cap:
+        kk = min(kk, (1 + math.sqrt(2)) * k)
+    return max(k_min, min(kk, k_max))
+
+
+def test_controller_accepts_below_sigma_and_proposes_a_dp():
+    lp = _Linear()
+    ut, e = lp.trial(lp.kn)  # Step 0: the first trial repeats k_n
+    assert 1e-9 < e < 1e-3
+    sigma = 10 * e
+    s = lp.stepper()
+    t0 = s.t
+    assert s.adaptive_begin("imex", sigma, 1.0) == 0
+    assert s.adaptive_trial() == 0
+    assert s.last_k == lp.kn
+    assert s.last_e == pytest.approx(e, rel=1e-8)
+    assert s.last_accepted and s.counts()["steps"] == 1 and s.counts()["rejects"] == 0
+    assert s.t == t0 + lp.kn and s.kn == lp.kn
+    assert np.abs(s.state() - ut).max() < 1e-12 * np.abs(ut).max()
+    assert np.array_equal(s.prev(), lp.un)
+    assert s.next_k == pytest.approx(_proposal(sigma, s.last_e, lp.kn), rel=1e-14)
+    # 10^(1/3) * 0.9 * k: neither exponent 1/2 nor rho_s = 1 gives this
+    assert s.next_k == pytest.approx(0.9 * 10 ** (1 / 3) * lp.kn, rel=1e-8)
+
+
+def test_controller_rejects_above_sigma_and_retries_at_the_proposal():
+    lp = _Linear()
+    _, e = lp.trial(lp.kn)
+    sigma = e / 10
+    s = lp.stepper()
+    assert s.adaptive_begin("imex", sigma, 1.0) == 0
+    assert s.adaptive_trial() == 0
+    assert not s.last_accepted and s.counts()["rejects"] == 1 and s.counts()["steps"] == 0
+    assert s.t == 0.0 and s.kn == lp.kn  # time and history unchanged
+    assert np.array_equal(s.state(), lp.un) and np.array_equal(s.prev(), lp.um)
+    k2 = _proposal(sigma, s.last_e, lp.kn)
+    assert k2 == pytest.approx(0.9 * 0.1 ** (1 / 3) * lp.kn, rel=1e-8)
+    assert s.next_k == pytest.approx(k2, rel=1e-14)
+    # Step 4 "Goto Step 1": the retry uses the proposal from the same history
+    assert s.adaptive_trial() == 0
+    assert s.last_k == pytest.approx(k2, rel=1e-14)
+    ut2, e2 = lp.trial(s.last_k)
+    assert s.last_e == pytest.approx(e2, rel=1e-8)
+    assert s.last_accepted == (e2 <= sigma)
+    if s.last_accepted:
+        assert np.abs(s.state() - ut2).max() < 1e-12 * np.abs(ut2).max()
+        assert s.t == s.last_k
+
+
+def test_controller_accepts_any_error_at_k_min():
+    lp = _Linear()
+    _, e = lp.trial(lp.kn)
+    s = lp.stepper(k_min=lp.kn)  # the trial size is k_min
+    assert s.adaptive_begin("imex", e / 100, 1.0) == 0
+    assert s.adaptive_trial() == 0
+    assert s.last_accepted and s.counts()["rejects"] == 0
+    assert s.t == lp.kn
+    # the proposal 0.9 (1/100)^(1/3) k is below k_min: clamped
+    assert s.next_k == lp.kn
+
+
+def test_controller_clips_the_last_trial_to_t_final():
+    lp = _Linear()
+    tf = 0.4 * lp.kn
+    ut, e = lp.trial(tf)
+    s = lp.stepper()
+    assert s.adaptive_begin("imex", 1e3 * e, tf) == 0
+    assert s.adaptive_trial() == 0
+    assert s.last_k == pytest.approx(tf, rel=1e-15) and s.last_accepted
+    assert s.t == pytest.approx(tf, rel=1e-15)
+    assert s.last_e == pytest.approx(e, rel=1e-8)
+    assert np.abs(s.state() - ut).max() < 1e-12 * np.abs(ut).max()
+    assert s.adaptive_trial() == 2  # t_final reached: no further trial
+
+
+@pytest.mark.parametrize("cap", [0, 1])
+def test_controller_zero_stability_cap_and_k_max(cap):
+    lp = _Linear()
+    _, e = lp.trial(lp.kn)
+    sigma = 1e3 * e  # A_dp = 9 k without the cap
+    s = lp.stepper(zero_stab_cap=cap)
+    assert s.adaptive_begin("imex", sigma, 1.0) == 0
+    assert s.adaptive_trial() == 0 and s.last_accepted
+    want = (1 + math.sqrt(2)) * lp.kn if cap else 9.0 * lp.kn
+    assert s.next_k == pytest.approx(want, rel=1e-8)
+    assert s.next_k == pytest.approx(_proposal(sigma, s.last_e, lp.kn, cap=bool(cap)), rel=1e-14)
+    s2 = lp.stepper(zero_stab_cap=cap, k_max=1.5 * lp.kn)
+    assert s2.adaptive_begin("imex", sigma, 1.0) == 0
+    assert s2.adaptive_trial() == 0
+    assert s2.next_k == 1.5 * lp.kn
+
+
+def test_controller_run_is_a_sequence_of_trials():
+    # orc_run_adaptive is orc_adaptive_begin plus orc_adaptive_trial until t_final
+    # (bit for bit), and a resumed run's first trial is the last proposal of the run
+    # before it (reading: the run of Sec. 3.2 split over calls continues at Step 1)
+    lp = _Linear()
+    _, e = lp.trial(lp.kn)
+    sigma, tf = 3 * e, 0.05
+    a = lp.stepper()
+    assert a.run_adaptive("imex", sigma, tf) == 0
+    c = lp.stepper()
+    assert c.adaptive_begin("imex", sigma, tf) == 0
+    n = 0
+    while n < 100000 and c.adaptive_trial() == 0:
+        n += 1
+    assert n == a.counts()["attempts"] and a.counts()["steps"] > 5
+    assert np.array_equal(c.state(), a.state()) and c.t == a.t
+    assert c.counts()["steps"] == a.counts()["steps"]
+    b = lp.stepper()
+    assert b.run_adaptive("imex", sigma, 0.01) == 0
+    nk = b.next_k
+    assert b.adaptive_begin("imex", sigma, tf) == 0 and b.adaptive_trial() == 0
+    assert b.last_k == nk
