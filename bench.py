@@ -140,12 +140,6 @@ class Clocks:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
-# FP32 peak from unit counts: 152 SMs x 128 FP32 lanes x 2 flops (FMA) x 2.07 GHz
-FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
-# FP64 peak of this GPU: the nominal 1.25 TFLOP/s figure
-FP64_PEAK_TFLOPS = 1.25
-
-
 def profile_table(name: str):
     """rows of a whitespace table in profiles/<name> (ncu-derived figures)"""
     rows = []
@@ -159,59 +153,86 @@ def profile_table(name: str):
     return rows
 
 
-def roofline(prec: str, kernel: str, n: int, launch_s_ms: float):
-    """Roofline of the dominant pass. fp32x2 and fp64 passes are bound by the FP32 /
-    FP64 pipes: achieved = floating-point operations per launch (counted by ncu for
-    this kernel and size, profiles/flops_per_launch.txt) / the live mean launch time.
-    mixed passes stream memory: achieved = algorithmic bytes per launch / time. The
-    HBM view of the same launch is reported beside the ALU one."""
+def _profile_value(name: str, prec: str, kernel: str, n: int):
+    for r in profile_table(name):
+        if len(r) >= 4 and r[0] == prec and r[1] == kernel and int(r[2]) == n:
+            return float(r[3])
+    return None
+
+
+def compulsory_bytes(name: str, n: int, csz: int):
+    """Compulsory HBM bytes of one launch of a pass (SURVEY 8(d) accounting): the
+    arrays of the step's own inputs and outputs it must read or write, once. The
+    trial reads u^n, u^{n-1}, F(u^n), F(u^{n-1}) and writes u~, F(u~) (6H in all);
+    the work array between the passes and the real-space fields a trial keeps for the
+    next one are intermediates (L2-resident) and do not count. H = one half spectrum
+    (n/2+1) n complex elements of csz bytes."""
+    H = (n // 2 + 1) * n * csz
+    table = {
+        "row_nimex_direct": 2 * H,     # u^n, u^{n-1} (read in their kept real-space form)
+        "row_sav_direct": 2 * H,
+        "col_imex_solve": 3 * H,       # u^n, u^{n-1} in; u~ out (eq. IMEX-eq)
+        "col_f_finish": 5 * H,         # u~, u^n, F(u^n), F(u^{n-1}) in; F(u~) out (eq. Predictor)
+        "row_f": None,                 # intermediates only
+    }
+    return table.get(name)
+
+
+def method_flops(name: str, n: int):
+    """Floating-point operations the method itself needs in one launch of a pass
+    (SURVEY 8(d)): 2.5 n^2 log2(n^2) per 2D real transform, a row or column pass
+    doing one half of each transform it touches, plus the pointwise flops of the
+    pass per grid point (the IMEX step's ~60 a point split over its passes)."""
+    T = 2.5 * n * n * math.log2(n * n)
+    table = {
+        "row_nimex_direct": T + 40 * n * n,    # W', W'' and N_IMEX pieces; forward rows of 2 fields
+        "col_imex_solve": 2 * T + 10 * n * n,  # forward columns of 2, solve, inverse columns of 2
+        "row_f": 2 * T + 50 * n * n,           # inverse rows of 2, mu pieces, forward rows of 2
+        "col_f_finish": T + 15 * n * n,        # forward columns of 2, F, AM3, two norms
+    }
+    return table.get(name)
+
+
+def roofline(prec: str, kernel: str, n: int, launch_ms: float, alu: dict, ms_per_step: float):
+    """Roofline of the dominant pass against the measured HBM copy bandwidth:
+    achieved = compulsory bytes of one launch (compulsory_bytes) over the live mean
+    launch time. Beside it: the same launch's method flops (method_flops) against the
+    measured FMA-pipe peak of its precision (the FP32 pipe for double-float and single
+    precision, the FP64 pipe for double), the pipe use of the floating-point
+    instructions the kernel executes (ncu SASS counts, profiles/flops_per_launch.txt),
+    and the whole trial's compulsory bytes (6H) over the time per step."""
     peaks = measured_peaks()
     hbm = peaks.get("hbm_gbs") or 6800.0
-    t = launch_s_ms / 1e3
+    t = launch_ms / 1e3
     csz = 8 if prec == "mixed" else 16
-    ab = pass_bytes(kernel, n, csz)
-    hbm_view = {"achieved_gbs": ab / t / 1e9 if ab else None, "peak_gbs": hbm,
-                "frac": (ab / t / 1e9) / hbm if ab else None, "algorithmic_bytes_per_launch": ab}
-    traffic = None
-    for r in profile_table("dram_traffic.txt"):
-        if len(r) >= 4 and r[0] == prec and r[1] == kernel and int(r[2]) == n:
-            traffic = float(r[3])
-    if prec == "mixed":
-        return {"kernel": kernel, "bound": "hbm", "achieved": hbm_view["achieved_gbs"], "peak": hbm,
-                "unit": "GB/s", "frac": hbm_view["frac"], "traffic": traffic,
-                "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)" if peaks.get("hbm_gbs")
-                else "fallback 6800 GB/s", "algorithmic_bytes_per_launch": ab,
-                "avg_launch_us": launch_s_ms * 1e3}
-    flops = None
-    for r in profile_table("flops_per_launch.txt"):
-        if len(r) >= 4 and r[0] == prec and r[1] == kernel and int(r[2]) == n:
-            flops = float(r[3])
-    peak = FP32_PEAK_TFLOPS if prec == "fp32x2" else FP64_PEAK_TFLOPS
-    ach = flops / t / 1e12 if flops else None
-    return {"kernel": kernel, "bound": "alu", "achieved": ach, "peak": peak, "unit": "TFLOP/s",
-            "frac": ach / peak if ach else None, "traffic": traffic,
-            "peak_source": ("FP32 pipe from unit counts: 152 SM x 128 lanes x 2 x 2.07 GHz"
-                            if prec == "fp32x2" else "FP64 nominal 1.25 TFLOP/s"),
-            "flops_per_launch": flops, "flops_source": "ncu sass op counts (profiles/flops_per_launch.txt)",
-            "avg_launch_us": launch_s_ms * 1e3, "hbm_view": hbm_view}
-
-
-def pass_bytes(name: str, n: int, csz: int) -> int:
-    """Algorithmic bytes of one launch of a pass: each array it must read or
-    write, once. H = one half spectrum (n/2+1)*n complex; Z = the n*n complex
-    work array between the column and row passes."""
+    cb = compulsory_bytes(kernel, n, csz)
+    ach = cb / t / 1e9 if cb else None
+    pipe = "fp64" if prec == "fp64" else "fp32"
+    peak_flops = alu.get(pipe)
+    mf = method_flops(kernel, n)
+    sass = _profile_value("flops_per_launch.txt", prec, kernel, n)
     H = (n // 2 + 1) * n * csz
-    Z = n * n * csz
-    table = {
-        "row_nimex_direct": 2 * Z + Z,     # (u, Lap u) of u^n, u^{n-1} in; Z out
-        "row_sav_direct": 2 * Z + Z,
-        "col_start": H * 2 + Z,            # u^n, u^{n-1} -> u*, packed Z
-        "row_nimex": 2 * Z,                # Z in, Z out
-        "row_f": 2 * Z + Z,                # Z in, Z out, (u, Lap u) of the trial kept
-        "col_imex_solve": Z + 2 * H + H + Z,  # Z, u^n, u^{n-1} in; u^{n+1}, Z out
-        "col_f_finish": Z + H + H + 3 * H,    # Z, u~ in; F~ out; u^n, F^n, F^{n-1} in (AM3)
+    return {
+        "kernel": kernel, "bound": "hbm", "achieved": ach, "peak": hbm, "unit": "GB/s",
+        "frac": ach / hbm if ach else None,
+        "traffic": _profile_value("dram_traffic.txt", prec, kernel, n),
+        "compulsory_bytes_per_launch": cb, "avg_launch_us": launch_ms * 1e3,
+        "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)" if peaks.get("hbm_gbs")
+        else "fallback 6800 GB/s (of fallback)",
+        "method_flops_view": {
+            "flops_per_launch": mf, "achieved_tflops": mf / t / 1e12 if mf else None,
+            "peak_tflops": peak_flops / 1e12 if peak_flops else None,
+            "frac": mf / t / peak_flops if mf and peak_flops else None,
+            "peak_source": f"measured {pipe.upper()} FMA pipe (fch_alu_peak, {alu.get('sms')} SMs)"},
+        "pipe_use": {
+            "sass_flops_per_launch": sass, "achieved_tflops": sass / t / 1e12 if sass else None,
+            "frac": sass / t / peak_flops if sass and peak_flops else None,
+            "source": "ncu SASS op counts (fadd + fmul + 2 ffma, or the d- forms), "
+                      "profiles/flops_per_launch.txt, over the measured pipe peak"},
+        "step_view": {"compulsory_bytes_per_step": 6 * H,
+                      "achieved_gbs": 6 * H / (ms_per_step / 1e3) / 1e9,
+                      "frac": 6 * H / (ms_per_step / 1e3) / 1e9 / hbm},
     }
-    return table.get(name, 0)
 
 
 def run_gb300(args):
@@ -240,6 +261,10 @@ def run_gb300(args):
              if args.autotune else None)
     u0 = I.random_network(n, d=0.75, seed=3 + rank)
     stream = torch.cuda.Stream(device=dev)
+    # the arithmetic peaks of this GPU (denominators of the passes' ALU views)
+    f32, sms = fch.alu_peak(fch.FCH_MIXED, stream)
+    f64, _ = fch.alu_peak(fch.FCH_FP64, stream)
+    alu = {"fp32": f32, "fp64": f64, "sms": sms}
     ctx = fch.Context(n, p, stream=stream)
     ctx.set_state(u0)
     ctx.adaptive_begin(args.scheme, SIGMA, T_FINAL)
@@ -287,7 +312,7 @@ def run_gb300(args):
     # dominant kernel and its roofline
     dom = max((k for k in times if k != "ctrl"), key=lambda k: times[k][0])
     dms, dn = times[dom]
-    roof = roofline(args.prec, dom, n, dms / dn)
+    roof = roofline(args.prec, dom, n, dms / dn, alu, ms_per_step)
     kernels = {k: {"ms_total": round(v[0], 4), "launches": v[1],
                    "share": round(v[0] / sum(x[0] for x in times.values()), 4)}
                for k, v in sorted(times.items(), key=lambda kv: -kv[1][0])}
@@ -308,9 +333,11 @@ def run_gb300(args):
                "gpu_launches": sum(v[1] for v in times.values()) // max(1, K2) * K,  # per trial, from the eager region
                "tiles": tiles, "kernels": kernels, "kernels_region": f"{K2} trials launched kernel by kernel "
                f"(per-launch events; {eager_ms_per_step:.4f} ms/step there vs {ms_per_step:.4f} "
-               "with the CUDA graph)", "roofline": roof, "clocks": clk.summary(), "e2e": e2e}
+               "with the CUDA graph)", "roofline": roof, "clocks": clk.summary(), "e2e": e2e,
+               "alu_peaks": {"fp32_tflops": f32 / 1e12, "fp64_tflops": f64 / 1e12, "sms": sms,
+                             "source": "fch_alu_peak: independent FMA chains, best of 5 launches"}}
         if not args.no_fft:
-            out["fft"] = fft_throughput(fch, dev)
+            out["fft"] = fft_throughput(fch, dev, alu)
             out["fixed_step"] = fixed_step_throughput(fch, I, dev)
         if not args.no_t_final and world == 1:
             out["time_to_t_final"] = time_to_t_final(fch, I, n)
@@ -354,13 +381,13 @@ def time_to_t_final(fch, I, n, t_final=0.02):
     return out
 
 
-def fft_throughput(fch, dev, n=N_GRID, batch=32, iters=10, warmup=3):
+def fft_throughput(fch, dev, alu, n=N_GRID, batch=32, iters=10, warmup=3):
     """Standalone 2D real transforms at n^2 (fch_fft_r2c then fch_fft_c2r over a
     batch of fields, inputs larger than L2) against cuFFT through torch.fft
     (rfft2 / irfft2 of the same batch), FP64 and FP32, with the tiles fch_autotune
     picks for (n, precision). One transform = one field one way. Roofline per transform: compulsory bytes (read the field or spectrum,
-    write the other) against HBM, and 2.5 n^2 log2(n^2) flops against the FP64
-    pipe for FP64."""
+    write the other) against HBM, and 2.5 n^2 log2(n^2) flops against the measured
+    FMA-pipe peak of the precision (alu: fch_alu_peak figures)."""
     import torch
 
     hbm = measured_peaks().get("hbm_gbs") or 6800.0
@@ -401,10 +428,11 @@ def fft_throughput(fch, dev, n=N_GRID, batch=32, iters=10, warmup=3):
         ent = {"fch": res["fch"], "cufft": res["cufft"], "fch_over_cufft": res["fch"] / res["cufft"],
                "round_trip_max_rel_err": err, "bytes_per_transform": byt,
                "hbm_frac": res["fch"] * byt / 1e9 / hbm, "hbm_peak_gbs": hbm}
-        if name == "fp64":
-            fl = 2.5 * n * n * math.log2(n * n)
-            ent["fp64_pipe_frac"] = res["fch"] * fl / 1.25e12
-            ent["fp64_pipe_peak"] = "1.25 TFLOP/s nominal FP64"
+        fl = 2.5 * n * n * math.log2(n * n)
+        pk = alu["fp64" if name == "fp64" else "fp32"]
+        ent["pipe_frac"] = res["fch"] * fl / pk
+        ent["pipe_peak_tflops"] = pk / 1e12
+        ent["pipe_peak_source"] = f"measured {name[:4].upper()} FMA pipe (fch_alu_peak)"
         out[name] = ent
         del x, X, y
     return out
@@ -464,27 +492,59 @@ def e2e_measure(fch, I, p, n, dev, K):
                     "includes the backward-Euler restart of set_state"}
 
 
-def cpu_baseline(args):
-    """The oracle as it stands (single-threaded FP64 C) on a bounded sample of
-    the workload: two adaptive IMEX trials at 1024^2."""
-    import numpy as np
-
+def _oracle_sample(n: int, trials: int, barrier=None, out=None):
+    """A bounded sample of the workload on the oracle: the F history of the
+    network initial data, then `trials` adaptive IMEX trials, timed. With a barrier
+    (all-cores runs) the timed regions of the workers start together."""
     from oracle import oracle as O
     from paper_2006_04784_gb300 import inputs as I
 
-    n = N_GRID
     u0 = I.random_network(n, d=0.75, seed=3)
-    L = 4 * math.pi
-    p = O.params(eta2=0.15, zeta=1.1, D0=170.0)
-    s = O.Stepper(n, L, p)
+    s = O.Stepper(n, 4 * math.pi, O.params(eta2=0.15))
     s.set_history(u0, u0, 1e-6)
-    s.run_adaptive("imex", SIGMA, T_FINAL, max_attempts=1)  # F history + one trial
+    s.adaptive_begin("imex", SIGMA, T_FINAL)
+    if barrier is not None:
+        barrier.wait()
     t0 = time.perf_counter()
-    s.run_adaptive("imex", SIGMA, T_FINAL, max_attempts=2)
+    for _ in range(trials):
+        s.adaptive_trial()
     dt = time.perf_counter() - t0
-    return {"value": 2 / dt, "unit": "steps/s", "cores": 1, "kind": "oracle",
-            "sample": "2 adaptive IMEX-BDF2 trials at 1024^2 (FP64 oracle, after its F history "
-                      f"was built), {dt:.1f} s"}
+    if out is not None:
+        out.put(dt)
+    return dt
+
+
+def cpu_baseline(args, trials: int = 2):
+    """The oracle as it stands (FP64 C, one thread per process) on a bounded sample
+    of the workload: two adaptive IMEX trials at 1024^2, single-threaded, and the
+    same sample on every host core at once (one spawned process per core, timed
+    regions started together; value = all trials / the slowest worker's time)."""
+    import multiprocessing as mp
+
+    from oracle import oracle as O
+
+    O.build()
+    n = N_GRID
+    dt1 = _oracle_sample(n, trials)
+    one = {"value": trials / dt1, "unit": "steps/s", "cores": 1, "kind": "oracle",
+           "sample": f"{trials} adaptive IMEX-BDF2 trials at 1024^2 (FP64 oracle, after its F "
+                     f"history was built), {dt1:.1f} s, one thread"}
+    cores = os.cpu_count() or 1
+    try:
+        ctx = mp.get_context("spawn")
+        bar, q = ctx.Barrier(cores), ctx.Queue()
+        ps = [ctx.Process(target=_oracle_sample, args=(n, trials, bar, q)) for _ in range(cores)]
+        for p in ps:
+            p.start()
+        dts = [q.get(timeout=600) for _ in ps]
+        for p in ps:
+            p.join()
+        allc = {"value": cores * trials / max(dts), "unit": "steps/s", "cores": cores, "kind": "oracle",
+                "sample": f"{trials} trials per process on {cores} processes (one per host core), "
+                          f"slowest {max(dts):.1f} s"}
+    except Exception as ex:  # the single-thread figure stands alone
+        allc = {"unavailable": f"{type(ex).__name__}: {ex}"}
+    return dict(one, all_cores=allc)
 
 
 def paper_costs(args):

@@ -361,6 +361,19 @@ fch_status fch_autotune_reset(void);
  * for the scratch contexts (FCH_ENOMEM). */
 fch_status fch_autotune_step(int n, int prec, void *stream, fch_tile *out);
 
+/* ---- measured arithmetic peaks (the paper has no counterpart) ----
+ * fch_alu_peak times a kernel of independent fused multiply-add chains (eight per
+ * thread, 256 threads a block, eight blocks per SM, no memory traffic) on the
+ * current device and returns the best of five timed launches (after one warm-up)
+ * as floating-point operations per second (an FMA counts as two): the peak of the
+ * FP32 pipe for prec = FCH_MIXED, of the FP64 pipe for prec = FCH_FP64. These are
+ * the denominators of the passes' arithmetic roofline (double-float passes run on
+ * the FP32 pipe). sm_count (may be NULL) receives the device's SM count. Allocates
+ * and frees an 8-byte device word; runs on `stream` (NULL: the legacy default
+ * stream) and synchronizes it. Errors: FCH_EINVAL (another prec, flops_per_s NULL),
+ * FCH_ENOMEM, FCH_ECUDA (reason in fch_last_cuda_error(NULL)). */
+fch_status fch_alu_peak(int prec, void *stream, double *flops_per_s, int *sm_count);
+
 /* ---- standalone 2D real transforms (the paper's cost unit, Sec. 1) ---- */
 
 /* Plan for N x N real transforms in precision prec on the given stream (NULL:
@@ -393,6 +406,8 @@ fch_status fch_fft_c2r(fch_fft_plan *plan, const void *X_dev, void *x_dev, int b
  *    pointers: FCH_EINVAL, with the reason in fch_last_cuda_error(NULL).
  *  - The first call on a device looks up that array's device address with the
  *    device current and caches it; make that first call before any stream capture.
+ *    The cached address belongs to the device's context of that moment: after
+ *    cudaDeviceReset, do not call this entry point again in the process.
  *  - All calls share the array and it keeps the last call's contents; nothing in it
  *    needs clearing (each call rewrites the twiddles and writes each work element
  *    before reading it). Calls whose GPU work overlaps (different streams or host

@@ -12,7 +12,9 @@
 // library holds it (FCH_NOALLOC_BYTES) until the process exits. In host code its
 // name is only a host-side stand-in, never a device address: the device address
 // is looked up once per device with cudaGetSymbolAddress (with that device
-// current) and cached. All calls share the array and it keeps the last call's
+// current) and cached. The cached address belongs to the device's context of that
+// moment; after cudaDeviceReset the entry point must not be called again in the
+// process. All calls share the array and it keeps the last call's
 // contents; nothing in it needs clearing, because every call rewrites the twiddle
 // table and writes each work element before reading it. Calls whose GPU work
 // overlaps (other streams, other host threads) race on the array.
@@ -105,18 +107,24 @@ extern "C" fch_status fch_fft_r2c_noalloc(int n, int prec, const void *x, void *
     while ((1 << logN) < n) logN++;
     void *Z = scratch;
     void *tw = (unsigned char *)scratch + (size_t)n * n * csz;
+    // launched through cudaLaunchKernelEx so that the status is this launch's own,
+    // not an error left pending by earlier, unrelated work on this thread
+    cudaLaunchConfig_t cfg;
+    memset(&cfg, 0, sizeof(cfg));
+    cfg.gridDim = dim3((n + 127) / 128);
+    cfg.blockDim = dim3(128);
+    cfg.stream = s;
     if (prec)
-        noalloc_twiddles<float><<<(n + 127) / 128, 128, 0, s>>>((float *)tw, n, logN);
+        e = cudaLaunchKernelEx(&cfg, noalloc_twiddles<float>, (float *)tw, n, logN);
     else
-        noalloc_twiddles<double><<<(n + 127) / 128, 128, 0, s>>>((double *)tw, n, logN);
-    e = cudaGetLastError();
+        e = cudaLaunchKernelEx(&cfg, noalloc_twiddles<double>, (double *)tw, n, logN);
 
     fch_kparams kp;
     memset(&kp, 0, sizeof(kp));
     kp.N = n;
     kp.logN = logN;
     kp.P = fch_geometry(n, prec).P;
-    kp.pdl = 1;
+    kp.pdl = 0; // n <= 512: passes of several waves, where programmatic launch measured slower
     kp.inv_n2 = 1.0 / ((double)n * n);
     kp.cf.inv_n2 = (float)kp.inv_n2;
     kp.cd.inv_n2 = kp.inv_n2;

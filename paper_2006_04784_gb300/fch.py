@@ -35,7 +35,8 @@ EXPORTS = ["fch_status_string", "fch_last_cuda_error", "fch_params_default", "fc
            "fch_fno_set_params", "fch_fno_get_params", "fch_fno_get_grads", "fch_fno_forward",
            "fch_fno_backward", "fch_fno_adam", "fch_step_psd_from", "fch_run_fixed",
            "fch_adaptive_trial_info", "fch_get_history_device", "fch_adaptive_enqueue_psd_from",
-           "fch_ensemble_run_adaptive_each", "fch_autotune_step", "fch_step_from", "fch_fno_set_bf16"]
+           "fch_ensemble_run_adaptive_each", "fch_autotune_step", "fch_step_from", "fch_fno_set_bf16",
+           "fch_alu_peak"]
 NCOL, NROW = 10, 8
 NPASS = NCOL + NROW + 1
 PASS_NAMES = (["col_fwd_store", "col_inv_load", "col_start", "col_imex_solve", "col_f_finish",
@@ -154,6 +155,7 @@ def lib():
         L.fch_ensemble_run_adaptive_each.argtypes = [vp, C.POINTER(C.c_int), C.POINTER(C.c_double), C.c_double,
                                                      C.c_int, C.c_longlong, C.POINTER(Stats)]
         L.fch_autotune_reset.argtypes = []
+        L.fch_alu_peak.argtypes = [C.c_int, vp, C.POINTER(C.c_double), C.POINTER(C.c_int)]
         L.fch_fft_plan_destroy.argtypes = [vp]
         L.fch_fft_r2c.argtypes = [vp, vp, vp, C.c_int]
         L.fch_fft_c2r.argtypes = [vp, vp, vp, C.c_int]
@@ -198,6 +200,14 @@ def autotune_step(n: int, prec: int, stream=None) -> dict:
 
 def autotune_reset():
     _check(lib().fch_autotune_reset(), "fch_autotune_reset")
+
+
+def alu_peak(prec: int, stream=None) -> tuple:
+    """(measured FMA-pipe peak in flop/s, SM count) of the current device: FP32 pipe
+    for FCH_MIXED, FP64 pipe for FCH_FP64 (fch_alu_peak)"""
+    r, sms = C.c_double(), C.c_int()
+    _check(lib().fch_alu_peak(int(prec), _stream_ptr(stream), C.byref(r), C.byref(sms)), "fch_alu_peak")
+    return r.value, sms.value
 
 
 def params_default(q: float = 0.0, **kw) -> Params:
