@@ -1123,6 +1123,7 @@ def fno_bench(args):
         # IMEX / SAV with the learned extrapolation: distance of the step to the
         # fully implicit BDF2 step (the PSD fixed point) from u* and from v_0
         gap = {(sc, w): [] for sc in ("imex", "sav") for w in ("plain", "learned")}
+        v0 = torch.empty((m, m), dtype=torch.float64, device=dev)
         with fch.Context(m, p) as a, fch.Context(m, p) as b:
             a.set_state(u0)
             hist_u = [np.array(u0)]
@@ -1133,9 +1134,10 @@ def fno_bench(args):
                     continue
                 g = dt / dts[i - 1]
                 un, um = hist_u[-1], hist_u[-2]
-                ustar = un + g * (un - um)
-                v0, _ = T.learned_start(net, un, ustar, dev)
-                torch.cuda.synchronize()
+                ustar = un + g * (un - um)  # for the error figures only
+                b.set_history(un, um, dts[i - 1])
+                T.learned_start(b, net, v0, dt)  # v_0 on the device from b's history
+                b.synchronize()
                 a.step("psd", dt)
                 it_plain.append(a.stats()["last_psd_iter"])
                 # the same BDF2 step (same history) from the learned start

@@ -324,6 +324,23 @@ fch_status fch_adaptive_trial_info(fch_ctx *ctx, double *k_trial, double *gamma,
 fch_status fch_get_history_device(fch_ctx *ctx, void *un_dev, void *unm1_dev, int dtype);
 fch_status fch_adaptive_enqueue_psd_from(fch_ctx *ctx, const void *v0_dev, int dtype);
 
+/* The learned first iterate itself, on the device (Sec. 3.3: the PSD iteration of
+ * eqs. (residual), (recurrence) may start from any v_0; eq. (Richardson) gives u*):
+ * from the context's history u^n, u^{n-1} and the step ratio gam of the next step
+ * (dt = 0: the next trial of the open adaptive run, gam from the control block;
+ * dt > 0: a fixed step of size dt, gam = dt / k_n), it forms
+ *   u* = u^n + gam (u^n - u^{n-1}),  s = RMS(u* - u^n),  a = (u^n, (u* - u^n)/s),
+ *   y = net(a) (fch_fno_forward, batch 1),  v_0 = u* + s (y - mean y)
+ * and writes v_0 (n x n doubles, device, caller-owned) for fch_step_psd_from or
+ * fch_adaptive_enqueue_psd_from, or as the u* of fch_step_from. Sums are FP64 in a
+ * fixed order; with no history (gam = 0) or u^n = u^{n-1}, s = 0 and v_0 = u*. The
+ * network's forward pass runs on its own stream, ordered after the input kernels
+ * and before the output kernel by events; nothing is read back to the host. The
+ * first call allocates the network's input and output arrays for the grid (kept by
+ * the context). Errors: FCH_EINVAL (NULL arguments, dt < 0), FCH_ESTATE (no state, a
+ * failed context, or dt = 0 without an open adaptive run), the network's status. */
+fch_status fch_fno_learned_start(fch_ctx *ctx, fch_fno *net, double dt, void *v0_dev);
+
 /* ---- pass tiles (the paper has no counterpart: a GPU launch choice) ----
  * fch_autotune times the forward row pass (two real fields -> pair-layout work
  * array) and the forward column pass (work array -> two half spectra) of one field

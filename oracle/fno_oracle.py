@@ -141,6 +141,23 @@ def forward(params, a, cfg: Config, keep=False):
     return y
 
 
+def learned_start(params, un, um, gam, cfg: Config):
+    """The learned first iterate of the PSD iteration (Sec. 3.3 leaves v_0 free; u* is
+    eq. (Richardson)), for one state: u* = u^n + gam (u^n - u^{n-1}), s = RMS(u* - u^n),
+    a = (u^n, (u* - u^n)/s), y = forward(a), v_0 = u* + s (y - mean y). With s = 0
+    (gam = 0 or u^n = u^{n-1}) v_0 = u*. Returns (v_0, y, s)."""
+    un = np.asarray(un, dtype=np.float64)
+    um = np.asarray(um, dtype=np.float64)
+    ustar = un + gam * (un - um)
+    d = ustar - un
+    s = float(np.sqrt(np.mean(d * d)))
+    if not s > 0:
+        return ustar, None, 0.0
+    a = np.stack([un, d / s])[None]
+    y = forward(params, a, cfg)[0]
+    return ustar + s * (y - y.mean()), y, s
+
+
 def loss(params, a, target, cfg: Config):
     """mean over samples and points of (y - target)^2"""
     y = forward(params, a, cfg)

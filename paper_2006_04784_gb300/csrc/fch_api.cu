@@ -252,6 +252,11 @@ struct fch_ctx {
     void *Rs[3];         // real-space (u, Lap u) of the state slots, kept by adaptive trials
     bool rvalid;         // Rs holds u^n (and u^{n-1} when k_n > 0)
     double *staging;     // N*N doubles for host io
+    // learned first iterate (fch_fno_learned_start): network input [2][N][N] and
+    // output [N][N] floats, per-block partial sums, two events; made on first use
+    float *ls_a, *ls_y;
+    double *ls_part;
+    cudaEvent_t ls_ev[2];
     long long *nfft_dev;
     unsigned int *ticket;
     long long nfft_base;
@@ -690,9 +695,11 @@ extern "C" fch_status fch_destroy(fch_ctx *ctx)
     void *bufs[] = {ctx->U[0], ctx->U[1], ctx->U[2], ctx->F[0], ctx->F[1], ctx->F[2], ctx->Pb,
                     ctx->Qb, ctx->Vb, ctx->Nb, ctx->Z, ctx->tw, ctx->part, ctx->dctrl,
                     ctx->staging, ctx->nfft_dev, ctx->ticket, ctx->tw2, ctx->Rs[0],
-                    ctx->Rs[1], ctx->Rs[2]};
+                    ctx->Rs[1], ctx->Rs[2], ctx->ls_a, ctx->ls_y, ctx->ls_part};
     for (void *b : bufs)
         if (b) cudaFree(b);
+    for (int i = 0; i < 2; i++)
+        if (ctx->ls_ev[i]) cudaEventDestroy(ctx->ls_ev[i]);
     if (ctx->timing)
         for (int i = 0; i < 2 * 2048; i++) cudaEventDestroy(ctx->ev[i]);
     for (int i = 0; i < 4; i++) {
@@ -1069,6 +1076,150 @@ extern "C" fch_status fch_step_psd_from(fch_ctx *ctx, double dt, const void *v0,
     }
     TRY(ctl(ctx, OP_ACCEPT, 0, 0.0));
     ctx->have_F = false;
+    return FCH_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Learned first iterate of the PSD iteration (Sec. 3.3: eqs. (residual),
+// (recurrence) start from any v_0). From the context's history u^n, u^{n-1} and the
+// step ratio gam of the next step (the open adaptive run's next trial from the
+// control block, or dt / k_n for a fixed step of size dt):
+//   u* = u^n + gam (u^n - u^{n-1})                   (eq. Richardson)
+//   s  = RMS(u* - u^n) = gam RMS(u^n - u^{n-1})
+//   a  = (u^n, (u* - u^n) / s)                        (network input, float)
+//   y  = network(a)                                   (predicts (u^{n+1} - u*) / s)
+//   v_0 = u* + s (y - mean y)                         (mass of u*)
+// All of it on the device: FP64 sums over per-block partials in a fixed order
+// (every block re-adds the partials itself, so no single-block pass is needed), the
+// network's forward pass ordered between the kernels by events. With gam = 0 (no
+// history) or u^n = u^{n-1}, s = 0 and v_0 = u*.
+static const int kLsBlocks = 256, kLsThreads = 256;
+
+__device__ inline double ls_block_sum(double v)
+{
+    __shared__ double sh[kLsThreads / 32];
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = v;
+    __syncthreads();
+    double t = 0.0;
+    if (threadIdx.x == 0)
+        for (int w = 0; w < kLsThreads / 32; w++) t += sh[w];
+    __syncthreads();
+    return t; // valid in thread 0
+}
+
+// the total of the nb partials, in index order, by one warp (valid in every lane)
+__device__ inline double ls_total(const double *part, int nb)
+{
+    const int lane = threadIdx.x & 31;
+    double v = 0.0;
+    for (int i = lane; i < nb; i += 32) v += part[i];
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+__device__ inline double ls_gam(const fch_ctrl *c, double dt)
+{
+    if (dt > 0) return c->kn > 0 ? dt / c->kn : 0.0;
+    return c->kn > 0 ? c->gam : 0.0;
+}
+
+// part[b] = sum over the block's points of (u^n - u^{n-1})^2
+__global__ void __launch_bounds__(kLsThreads) ls_diff_sums(const double *__restrict__ un,
+                                                           const double *__restrict__ um, long cnt,
+                                                           double *__restrict__ part)
+{
+    double v = 0.0;
+    for (long i = blockIdx.x * (long)kLsThreads + threadIdx.x; i < cnt; i += (long)gridDim.x * kLsThreads) {
+        const double d = un[i] - um[i];
+        v += d * d;
+    }
+    const double t = ls_block_sum(v);
+    if (threadIdx.x == 0) part[blockIdx.x] = t;
+}
+
+// a[0] = u^n, a[1] = (u* - u^n) / s as floats
+__global__ void __launch_bounds__(kLsThreads) ls_inputs(const double *__restrict__ un, const double *__restrict__ um,
+                                                        long cnt, const fch_ctrl *__restrict__ c, double dt,
+                                                        const double *__restrict__ part, int nb,
+                                                        float *__restrict__ a)
+{
+    const double g = ls_gam(c, dt);
+    const double r = sqrt(ls_total(part, nb) / (double)cnt); // RMS(u^n - u^{n-1})
+    const double s = g * r;
+    const double inv = s > 0 ? 1.0 / s : 0.0;
+    for (long i = blockIdx.x * (long)kLsThreads + threadIdx.x; i < cnt; i += (long)gridDim.x * kLsThreads) {
+        const double d = g * (un[i] - um[i]);
+        a[i] = (float)un[i];
+        a[cnt + i] = (float)(d * inv);
+    }
+}
+
+// part[b] = sum over the block's points of y
+__global__ void __launch_bounds__(kLsThreads) ls_y_sums(const float *__restrict__ y, long cnt,
+                                                        double *__restrict__ part)
+{
+    double v = 0.0;
+    for (long i = blockIdx.x * (long)kLsThreads + threadIdx.x; i < cnt; i += (long)gridDim.x * kLsThreads)
+        v += (double)y[i];
+    const double t = ls_block_sum(v);
+    if (threadIdx.x == 0) part[blockIdx.x] = t;
+}
+
+// v_0 = u* + s (y - mean y)
+__global__ void __launch_bounds__(kLsThreads) ls_v0(const double *__restrict__ un, const double *__restrict__ um,
+                                                    const float *__restrict__ y, long cnt,
+                                                    const fch_ctrl *__restrict__ c, double dt,
+                                                    const double *__restrict__ part_d,
+                                                    const double *__restrict__ part_y, int nb,
+                                                    double *__restrict__ v0)
+{
+    const double g = ls_gam(c, dt);
+    const double s = g * sqrt(ls_total(part_d, nb) / (double)cnt);
+    const double ym = ls_total(part_y, nb) / (double)cnt;
+    for (long i = blockIdx.x * (long)kLsThreads + threadIdx.x; i < cnt; i += (long)gridDim.x * kLsThreads) {
+        const double ustar = un[i] + g * (un[i] - um[i]);
+        v0[i] = s > 0 ? ustar + s * ((double)y[i] - ym) : ustar;
+    }
+}
+
+extern "C" fch_status fch_fno_learned_start(fch_ctx *ctx, fch_fno *net, double dt, void *v0_dev)
+{
+    if (!ctx || !net || !v0_dev || !(dt >= 0)) return FCH_EINVAL;
+    if (!ctx->have_state || ctx->failed) return FCH_ESTATE;
+    if (dt == 0 && !ctx->ad_open) return FCH_ESTATE;
+    const long cnt = (long)ctx->N * ctx->N;
+    if (!ctx->ls_a) {
+        CKC(ctx, cudaMalloc((void **)&ctx->ls_a, sizeof(float) * 2 * cnt));
+        CKC(ctx, cudaMalloc((void **)&ctx->ls_y, sizeof(float) * cnt));
+        CKC(ctx, cudaMalloc((void **)&ctx->ls_part, sizeof(double) * 2 * kLsBlocks));
+        for (int i = 0; i < 2; i++) CKC(ctx, cudaEventCreateWithFlags(&ctx->ls_ev[i], cudaEventDisableTiming));
+    }
+    // u^n, u^{n-1} as real fields in the staging buffer (2 N^2 doubles)
+    double *un = ctx->staging, *um = ctx->staging + cnt;
+    TRY(col(ctx, CM_START, FCH_SRC_UN, FCH_FL_NOSKIP));
+    TRY(row(ctx, RM_C2R_STORE, FCH_FL_NOSKIP | FCH_FL_F64IO, nullptr, un));
+    TRY(col(ctx, CM_START, 5, FCH_FL_NOSKIP));
+    TRY(row(ctx, RM_C2R_STORE, FCH_FL_NOSKIP | FCH_FL_F64IO, nullptr, um));
+    cudaStream_t s = ctx->stream, fs = fch_fno_stream_of(net);
+    double *pd = ctx->ls_part, *py = ctx->ls_part + kLsBlocks;
+    ls_diff_sums<<<kLsBlocks, kLsThreads, 0, s>>>(un, um, cnt, pd);
+    ls_inputs<<<kLsBlocks, kLsThreads, 0, s>>>(un, um, cnt, ctx->dctrl, dt, pd, kLsBlocks, ctx->ls_a);
+    CKC(ctx, cudaGetLastError());
+    // the network's forward pass on its own stream, between the kernels above and below
+    CKC(ctx, cudaEventRecord(ctx->ls_ev[0], s));
+    CKC(ctx, cudaStreamWaitEvent(fs, ctx->ls_ev[0], 0));
+    const fch_status fst = fch_fno_forward(net, 1, ctx->N, ctx->ls_a, ctx->ls_y);
+    if (fst != FCH_OK) {
+        snprintf(ctx->errbuf, sizeof(ctx->errbuf), "fch_fno_learned_start: %s", fch_last_cuda_error(nullptr));
+        return fst;
+    }
+    CKC(ctx, cudaEventRecord(ctx->ls_ev[1], fs));
+    CKC(ctx, cudaStreamWaitEvent(s, ctx->ls_ev[1], 0));
+    ls_y_sums<<<kLsBlocks, kLsThreads, 0, s>>>(ctx->ls_y, cnt, py);
+    ls_v0<<<kLsBlocks, kLsThreads, 0, s>>>(un, um, ctx->ls_y, cnt, ctx->dctrl, dt, pd, py, kLsBlocks,
+                                           (double *)v0_dev);
+    CKC(ctx, cudaGetLastError());
     return FCH_OK;
 }
 

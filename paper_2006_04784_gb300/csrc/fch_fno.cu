@@ -544,6 +544,8 @@ cudaError_t wgrad(fch_fno *f, const float *A, int CA, int na, const float *Bm, i
 
 } // namespace
 
+cudaStream_t fch_fno_stream_of(const fch_fno *f) { return f->stream; }
+
 extern "C" fch_status fch_fno_create(int width, int layers, int modes, int proj, void *stream, fch_fno **out)
 {
     if (!out || (width != 8 && width != 16 && width != 32) || layers < 1 || layers > 16 || modes < 1 ||

@@ -175,3 +175,7 @@ cudaError_t fch_launch_ctrl(int op, const fch_kparams &kp, int nblk_a, int nblk_
 
 // sets the per-thread message returned by fch_last_cuda_error(NULL)
 void fch_set_thread_error(const char *msg);
+
+// the stream a network's work runs on (fch_fno.cu)
+struct fch_fno;
+cudaStream_t fch_fno_stream_of(const fch_fno *f);

@@ -36,7 +36,7 @@ EXPORTS = ["fch_status_string", "fch_last_cuda_error", "fch_params_default", "fc
            "fch_fno_backward", "fch_fno_adam", "fch_step_psd_from", "fch_run_fixed",
            "fch_adaptive_trial_info", "fch_get_history_device", "fch_adaptive_enqueue_psd_from",
            "fch_ensemble_run_adaptive_each", "fch_autotune_step", "fch_step_from", "fch_fno_set_bf16",
-           "fch_alu_peak"]
+           "fch_alu_peak", "fch_fno_learned_start"]
 NCOL, NROW = 10, 8
 NPASS = NCOL + NROW + 1
 PASS_NAMES = (["col_fwd_store", "col_inv_load", "col_start", "col_imex_solve", "col_f_finish",
@@ -156,6 +156,7 @@ def lib():
                                                      C.c_int, C.c_longlong, C.POINTER(Stats)]
         L.fch_autotune_reset.argtypes = []
         L.fch_alu_peak.argtypes = [C.c_int, vp, C.POINTER(C.c_double), C.POINTER(C.c_int)]
+        L.fch_fno_learned_start.argtypes = [vp, vp, C.c_double, vp]
         L.fch_fft_plan_destroy.argtypes = [vp]
         L.fch_fft_r2c.argtypes = [vp, vp, vp, C.c_int]
         L.fch_fft_c2r.argtypes = [vp, vp, vp, C.c_int]
@@ -347,6 +348,14 @@ class Context:
         s = SCHEMES[scheme] if isinstance(scheme, str) else int(scheme)
         self._ck(lib().fch_step_from(self._h, s, float(dt), _tensor_ptr(ustar), _dtype_code(ustar)),
                  "fch_step_from")
+
+    def fno_learned_start(self, net, v0, dt: float = 0.0):
+        """v_0 = u* + s (y - mean y) from the history and the network (fch_fno_learned_start):
+        dt = 0 for the open adaptive run's next trial, dt > 0 for a fixed step"""
+        assert v0.is_cuda and v0.is_contiguous() and v0.dtype.is_floating_point and v0.element_size() == 8
+        assert tuple(v0.shape) == (self.n, self.n)
+        self._ck(lib().fch_fno_learned_start(self._h, net._h, float(dt), _tensor_ptr(v0)),
+                 "fch_fno_learned_start")
 
     def step_psd_from(self, dt: float, v0):
         """one PSD-BDF2 step whose iteration starts from the device field v0"""

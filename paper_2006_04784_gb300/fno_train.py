@@ -6,7 +6,13 @@ inputs a = (u^n, (u* - u^n)/s), target (u^{n+1} - u*)/s, s = RMS(u* - u^n). Samp
 come from PSD-BDF2 trajectories the library itself computes (Sec. 3.3) with
 randomly varied step sizes; the learned start is v_0 = u* + s (y - mean y), which
 keeps the mass of u* (the PSD iteration keeps the k = 0 mode of its start).
-Every step runs in the library's kernels; this module only moves tensors.
+
+The learned start of a step (u*, s, the network's input, its forward pass and v_0)
+runs in the library's kernels (fch_fno_learned_start), and the trials in its
+steppers; this module calls them and moves tensors. The training samples are
+assembled on the host from the states of trajectories the library computed
+(samples_from: the input pairs and targets of the regression), once, before
+training.
 """
 from __future__ import annotations
 
@@ -95,20 +101,12 @@ def train(net, data, iters, batch, lr, device, seed=0, log_every=0):
     return hist
 
 
-def learned_start(net, un, ustar, device):
-    """v_0 = u* + s (y - mean y) for the state u^n and the extrapolation u* (host
-    arrays); returns (v0 as a device float64 tensor, the prediction y)"""
-    import torch
-
-    d = ustar - un
-    s = float(np.sqrt(np.mean(d * d)))
-    n = un.shape[-1]
-    a = torch.tensor(np.stack([un, d / s])[None].astype(np.float32), device=device)
-    y = torch.empty((1, n, n), device=device)
-    net.forward(a, y)
-    yc = y[0].double()
-    v0 = torch.tensor(ustar, device=device) + s * (yc - yc.mean())
-    return v0.contiguous(), y[0].cpu().numpy()
+def learned_start(ctx, net, v0, dt: float = 0.0):
+    """v_0 for the next step of ctx from its history and the network, written into the
+    device float64 tensor v0 (fch_fno_learned_start: dt = 0 for the open adaptive
+    run's next trial, dt > 0 for a fixed step of size dt)"""
+    ctx.fno_learned_start(net, v0, dt)
+    return v0
 
 
 def run_adaptive_psd(ctx, sigma, t_final, device, net=None, k_range=None, max_trials=100000):
@@ -116,14 +114,14 @@ def run_adaptive_psd(ctx, sigma, t_final, device, net=None, k_range=None, max_tr
     from u* (net None) or from the network's v_0; with k_range = (lo, hi) the network
     is used only for trial steps in that range (the step sizes it was trained on: its
     inputs are normalised and carry no step size, so outside that range its correction
-    does not scale with the step) and u* elsewhere. Returns (stats, trials, learned
-    trials)."""
+    does not scale with the step) and u* elsewhere. The host reads each trial's size
+    (fch_adaptive_trial_info) to choose; v_0 is formed on the device. Returns (stats,
+    trials, learned trials)."""
     import torch
 
     n = ctx.n
     ctx.adaptive_begin("psd", sigma, t_final)
-    un = torch.empty((n, n), dtype=torch.float64, device=device)
-    um = torch.empty_like(un)
+    v0 = torch.empty((n, n), dtype=torch.float64, device=device)
     trials = learned = 0
     while trials < max_trials:
         k, g, done = ctx.adaptive_trial_info()
@@ -132,12 +130,7 @@ def run_adaptive_psd(ctx, sigma, t_final, device, net=None, k_range=None, max_tr
         if net is None or g == 0.0 or (k_range is not None and not (k_range[0] <= k <= k_range[1])):
             ctx.adaptive_enqueue(1)
         else:
-            ctx.get_history_device(un, um)
-            ctx.synchronize()
-            a = un.cpu().numpy()
-            ustar = a + g * (a - um.cpu().numpy())
-            v0, _ = learned_start(net, a, ustar, device)
-            torch.cuda.synchronize()
+            ctx.fno_learned_start(net, v0)
             ctx.adaptive_enqueue_psd_from(v0)
             learned += 1
         trials += 1

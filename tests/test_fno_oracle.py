@@ -90,3 +90,29 @@ def test_bf16_round_ties_to_even_and_matches_torch():
     for v in (x, r):
         ref = torch.tensor(v).to(torch.bfloat16).float().numpy()
         assert np.array_equal(F.bf16_round(v), ref)
+
+
+def test_learned_start_keeps_the_mass_and_reduces_to_the_extrapolation():
+    # v_0 = u* + s (y - mean y): the k = 0 mode (mass) of u* is kept for any network;
+    # a network whose output is constant (Q2 = 0) gives v_0 = u*, and so does s = 0
+    cfg = F.Config(width=8, layers=2, modes=4, proj=16)
+    n = 16
+    rng = np.random.default_rng(3)
+    params = F.init_params(cfg, 1) + 0.05 * rng.standard_normal(cfg.size())
+    un = rng.standard_normal((n, n))
+    um = un + 0.01 * rng.standard_normal((n, n))
+    gam = 1.7
+    ustar = un + gam * (un - um)
+    v0, y, s = F.learned_start(params, un, um, gam, cfg)
+    assert s == pytest.approx(gam * np.sqrt(np.mean((un - um) ** 2)), rel=1e-14)
+    assert np.mean(v0) == pytest.approx(np.mean(ustar), abs=1e-15)
+    assert np.linalg.norm(v0 - ustar) > 1e-3 * s  # the network moved it
+    # the prediction is the network's forward pass on (u^n, (u* - u^n)/s)
+    a = np.stack([un, (ustar - un) / s])[None]
+    assert np.array_equal(y, F.forward(params, a, cfg)[0])
+    d = cfg.unpack(params)
+    d["Q2"][:] = 0.0
+    v0c, _, _ = F.learned_start(cfg.pack(d), un, um, gam, cfg)
+    assert np.abs(v0c - ustar).max() < 1e-14
+    v00, _, s0 = F.learned_start(params, un, um, 0.0, cfg)
+    assert s0 == 0.0 and np.array_equal(v00, un)

@@ -167,17 +167,18 @@ def test_trained_fno_start_beats_the_extrapolation(small_trained_net):
     dts = T.random_steps(np.random.default_rng(9), 20, 1e-3)
     u = [I.circle_bilayer(n, radius=2.2, noise=1e-3, seed=7)]
     ratios, it_p, it_f = [], [], []
+    v0 = torch.empty((n, n), dtype=torch.float64, device=DEV)
     with fch.Context(n, p) as a, fch.Context(n, p) as b:
         a.set_state(u[0])
         for i, dt in enumerate(dts):
             if i >= 2:
                 ustar = u[-1] + dt / dts[i - 1] * (u[-1] - u[-2])
-                v0, _ = T.learned_start(net, u[-1], ustar, DEV)
+                b.set_history(u[-1], u[-2], dts[i - 1])
+                T.learned_start(b, net, v0, dt)  # on the device, from b's history
             a.step("psd", dt)
             u.append(a.get_state())
             if i >= 2:
                 it_p.append(a.stats()["last_psd_iter"])
-                b.set_history(u[-2], u[-3], dts[i - 1])
                 b.step_psd_from(dt, v0)
                 it_f.append(b.stats()["last_psd_iter"])
                 assert rel(b.get_state(), u[-1]) < 1e-8
@@ -224,12 +225,13 @@ def test_learned_extrapolation_brings_imex_to_the_implicit_step(small_trained_ne
     dts = T.random_steps(np.random.default_rng(11), 16, 1e-3)
     u = [I.circle_bilayer(n, radius=2.2, noise=1e-3, seed=7)]
     plain, learned = [], []
+    v0 = torch.empty((n, n), dtype=torch.float64, device=DEV)
     with fch.Context(n, p) as a, fch.Context(n, p) as b:
         a.set_state(u[0])
         for i, dt in enumerate(dts):
             if i >= 2:
-                ustar = u[-1] + dt / dts[i - 1] * (u[-1] - u[-2])
-                v0, _ = T.learned_start(net, u[-1], ustar, DEV)
+                b.set_history(u[-1], u[-2], dts[i - 1])
+                T.learned_start(b, net, v0, dt)
             a.step("psd", dt)
             u.append(a.get_state())
             if i >= 2:
@@ -241,3 +243,42 @@ def test_learned_extrapolation_brings_imex_to_the_implicit_step(small_trained_ne
                 learned.append(rel(b.get_state(), u[-1]))
                 assert b.mass() == pytest.approx(a.mass(), rel=1e-12)
     assert np.mean(learned) < 0.9 * np.mean(plain)
+
+
+@pytest.mark.parametrize("mode", ["fixed", "adaptive"])
+def test_learned_start_on_the_device_vs_oracle(small_trained_net, mode):
+    # fch_fno_learned_start forms u*, s, the network input, y and v_0 on the device
+    # from the context's history; against the FNO oracle's construction
+    # (oracle/fno_oracle.py learned_start, FP64) on the same history and gam: v_0
+    # differs by s times the forward pass's float rounding (2e-5 of y), and keeps the
+    # mass of u* to rounding
+    net, _ = small_trained_net
+    cfg = F.Config(width=16, layers=2, modes=8, proj=32)
+    params = net.params().astype(np.float64)
+    n, kn = 64, 1e-3
+    un = I.circle_bilayer(n, radius=2.2, noise=1e-3, seed=7)
+    um = un - 3e-3 * I.smooth_random(n, seed=4, amp=0.5, kmax=3, offset=0.0)
+    v0 = torch.empty((n, n), dtype=torch.float64, device=DEV)
+    with fch.Context(n, fch.params_default(0.0)) as ctx:
+        ctx.set_history(un, um, kn)
+        if mode == "fixed":
+            dt = 1.4e-3
+            gam = dt / kn
+            ctx.fno_learned_start(net, v0, dt)
+        else:
+            ctx.adaptive_begin("psd", 1e-5, 1.0)
+            k, gam, done = ctx.adaptive_trial_info()
+            assert not done and k == pytest.approx(kn) and gam == pytest.approx(1.0)
+            ctx.fno_learned_start(net, v0)
+        ctx.synchronize()
+        got = v0.cpu().numpy()
+        if mode == "adaptive":
+            ctx.adaptive_enqueue_psd_from(v0)  # the trial runs from it
+            st = ctx.adaptive_end()
+            assert st["n_attempts"] >= 1
+    ref, y, s = F.learned_start(params, un, um, gam, cfg)
+    ustar = un + gam * (un - um)
+    assert s > 0
+    assert np.linalg.norm(got - ref) <= 4e-5 * s * np.linalg.norm(y)
+    assert np.linalg.norm(ref - ustar) > 1e-2 * s * np.linalg.norm(y)  # not just u*
+    assert abs(np.mean(got) - np.mean(ustar)) < 1e-15
