@@ -1213,51 +1213,103 @@ def fno_bench(args):
 
 
 def error_budget(args):
-    """Single precision against FP64 (and double-float against FP64) per field at
-    1024^2 and 2048^2 on the random bilayer network (critical parameters): F(u) of
-    the initial data, and after fixed IMEX steps u, F(u), mass and energy."""
+    """Per-field error of each precision against the FP64 oracle (the benchmark spec's mixed-
+    precision budget) on the random bilayer network (critical parameters) at 1024^2
+    and 2048^2: F(u) of the initial data; u, F(u), mass and energy after one and after
+    budget_steps fixed IMEX steps of budget_dt (one step at 2048^2); SAV's u and r after
+    one step; the LTE estimate e and the state after the backward-Euler start and one
+    adaptive IMEX trial (Sec. 3.2). Each cell is the relative error against the oracle;
+    the GPU's own FP64 mode is a second column."""
     import numpy as np
     import torch
 
+    from oracle import oracle as O
     from paper_2006_04784_gb300 import build as B
     B.build()
+    O.build()
     from paper_2006_04784_gb300 import fch
     from paper_2006_04784_gb300 import inputs as I
 
     dev = torch.device("cuda", 0)
-    out = {"steps": args.budget_steps, "dt": args.budget_dt, "runs": []}
-    for n in (1024, 2048):
+    L = 4 * math.pi
+    out = {"dt": args.budget_dt, "runs": []}
+    for n, nsteps in ((1024, args.budget_steps), (2048, 1)):
         u0 = I.random_network(n, d=0.75, seed=3)
+        p0 = fch.params_default(0.0, eta2=0.15)
+        p0.zeta, p0.D0 = 1.1, 170.0  # explicit SAV constants, the same on both sides
+        op = O.params(eps=p0.eps, q=p0.q, gamma=p0.gamma, eta1=p0.eta1, eta2=p0.eta2, zeta=p0.zeta,
+                      D0=p0.D0, beta1=p0.beta1, beta2=p0.beta2, kappa0=p0.kappa0, kappa2=p0.kappa2)
+        t0 = time.perf_counter()
+        ref = {"F0": O.rhs(op, u0, L)}
+        s = O.Stepper(n, L, op)
+        s.set_state(u0)
+        for k in range(nsteps):
+            s.step("imex", args.budget_dt)
+            if k == 0:
+                ref["u1"] = s.state()
+        ref["uN"] = s.state()
+        ref["FN"] = O.rhs(op, ref["uN"], L)
+        ref["mass"], ref["energy"] = O.mass(ref["uN"], L), O.energy(op, ref["uN"], L)
+        s = O.Stepper(n, L, op)
+        s.set_state(u0)
+        s.step("sav", args.budget_dt)
+        ref["sav_u"], ref["sav_r"] = s.state(), s.r(0)
+        s = O.Stepper(n, L, op)
+        s.set_state(u0)
+        s.adaptive_begin("imex", SIGMA, T_FINAL)
+        s.adaptive_trial()
+        ref["lte_e"], ref["ad_u"] = s.last_e, s.state()
+        oracle_s = time.perf_counter() - t0
         res = {}
         for name, prec in (("fp64", fch.FCH_FP64), ("fp32x2", fch.FCH_FP32X2), ("fp32", fch.FCH_MIXED)):
             p = fch.params_default(0.0, eta2=0.15, prec=prec)
+            p.zeta, p.D0 = p0.zeta, p0.D0
+            r = {}
             with fch.Context(n, p) as ctx:
-                ut = torch.tensor(u0, device=dev)
-                F0 = torch.empty_like(ut)
-                torch.cuda.synchronize()
-                ctx.rhs_device(ut, F0)
-                ctx.synchronize()
+                def rhs(u):
+                    ut = torch.tensor(u, device=dev)
+                    F = torch.empty_like(ut)
+                    torch.cuda.synchronize()
+                    ctx.rhs_device(ut, F)
+                    ctx.synchronize()
+                    return F.cpu().numpy()
+                r["F0"] = rhs(u0)
                 ctx.set_state(u0)
-                m0 = ctx.mass()
-                for _ in range(args.budget_steps):
+                for k in range(nsteps):
                     ctx.step("imex", args.budget_dt)
-                u = ctx.get_state()
-                F1 = torch.empty_like(ut)
-                ut1 = torch.tensor(u, device=dev)
-                torch.cuda.synchronize()
-                ctx.rhs_device(ut1, F1)
-                ctx.synchronize()
-                res[name] = {"F0": F0.cpu().numpy(), "u": u, "F1": F1.cpu().numpy(), "mass": ctx.mass(),
-                             "mass0": m0, "energy": ctx.energy()}
-        row = {"n": n}
-        for name in ("fp32x2", "fp32"):
-            a, b = res[name], res["fp64"]
-            row[name] = {"F_initial_rel_l2": _rel(a["F0"], b["F0"]), "u_rel_l2": _rel(a["u"], b["u"]),
-                         "F_final_rel_l2": _rel(a["F1"], b["F1"]),
-                         "mass_rel_drift": abs(a["mass"] - a["mass0"]) / abs(a["mass0"]),
-                         "mass_rel_vs_fp64": abs(a["mass"] - b["mass"]) / abs(b["mass"]),
-                         "energy_rel_vs_fp64": abs(a["energy"] - b["energy"]) / abs(b["energy"])}
-        row["fp64"] = {"mass_rel_drift": abs(res["fp64"]["mass"] - res["fp64"]["mass0"]) / abs(res["fp64"]["mass0"])}
+                    if k == 0:
+                        r["u1"] = ctx.get_state()
+                r["uN"] = ctx.get_state()
+                r["FN"] = rhs(r["uN"])
+                r["mass"], r["energy"] = ctx.mass(), ctx.energy()
+                ctx.set_state(u0)
+                ctx.step("sav", args.budget_dt)
+                r["sav_u"], r["sav_r"] = ctx.get_state(), ctx.sav_r()[0]
+                ctx.set_state(u0)
+                ctx.adaptive_begin("imex", SIGMA, T_FINAL)
+                ctx.adaptive_enqueue(1)
+                st = ctx.adaptive_end()
+                r["lte_e"], r["ad_u"] = st["e_last"], ctx.get_state()
+            res[name] = r
+
+        def errs(a, b):
+            e = {}
+            for f in ("F0", "u1", "uN", "FN", "sav_u", "ad_u"):
+                e[f] = _rel(a[f], b[f])
+            for f in ("mass", "energy", "sav_r", "lte_e"):
+                e[f] = abs(a[f] - b[f]) / abs(b[f])
+            return e
+
+        row = {"n": n, "steps": nsteps, "oracle_s": oracle_s,
+               "fields": {"F0": "F(u0)", "u1": "u after 1 IMEX step", "uN": f"u after {nsteps} IMEX steps",
+                          "FN": f"F(u) after {nsteps} steps", "mass": f"mass after {nsteps} steps",
+                          "energy": f"energy after {nsteps} steps", "sav_u": "u after 1 SAV step",
+                          "sav_r": "SAV r after 1 step", "lte_e": "LTE estimate e of the first trial",
+                          "ad_u": "u after the start and one adaptive trial"}}
+        for name in ("fp64", "fp32x2", "fp32"):
+            row[name] = {"vs_oracle": errs(res[name], ref)}
+            if name != "fp64":
+                row[name]["vs_gpu_fp64"] = errs(res[name], res["fp64"])
         out["runs"].append(row)
     return out
 
@@ -1351,7 +1403,7 @@ def main():
     ap.add_argument("--fno-t-adaptive", type=float, default=2e-2)
     ap.add_argument("--error-budget", action="store_true",
                     help="per-field single/double-float vs FP64 errors at 1024^2 and 2048^2 instead")
-    ap.add_argument("--budget-steps", type=int, default=200)
+    ap.add_argument("--budget-steps", type=int, default=5)
     ap.add_argument("--budget-dt", type=float, default=1e-6)
     args = ap.parse_args()
     PSD_MAX_ITER[0] = args.psd_max_iter

@@ -324,6 +324,14 @@ fch_status fch_adaptive_trial_info(fch_ctx *ctx, double *k_trial, double *gamma,
 fch_status fch_get_history_device(fch_ctx *ctx, void *un_dev, void *unm1_dev, int dtype);
 fch_status fch_adaptive_enqueue_psd_from(fch_ctx *ctx, const void *v0_dev, int dtype);
 
+/* One trial of the open adaptive IMEX or SAV run (as fch_adaptive_enqueue: trial, F of
+ * the trial, AM3 estimate, decision on the device) whose explicit part is evaluated at
+ * the caller's u* (device, n x n, dtype 0 double / 1 float) instead of eq.
+ * (Richardson), as fch_step_from does for a fixed step: the learned extrapolation
+ * inside adaptive runs. FCH_EINVAL for NULL or another dtype; FCH_ESTATE unless an
+ * adaptive IMEX or SAV run is open. */
+fch_status fch_adaptive_enqueue_from(fch_ctx *ctx, const void *ustar_dev, int dtype);
+
 /* The learned first iterate itself, on the device (Sec. 3.3: the PSD iteration of
  * eqs. (residual), (recurrence) may start from any v_0; eq. (Richardson) gives u*):
  * from the context's history u^n, u^{n-1} and the step ratio gam of the next step

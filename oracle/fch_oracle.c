@@ -897,6 +897,19 @@ int orc_adaptive_trial(orc_ctx *s)
     return 0;
 }
 
+/* One trial of the open adaptive run (as orc_adaptive_trial) whose extrapolation is
+ * the given field (real space, N x N) instead of eq. (Richardson): the explicit part
+ * of IMEX and SAV (eqs. (IMEX-eq), (4.7)-(4.8)), or the first PSD iterate v_0
+ * (Sec. 3.3). Returns as orc_adaptive_trial, or -2 for ETD. */
+int orc_adaptive_trial_from(orc_ctx *s, const double *ustar)
+{
+    if (s->ad_scheme == ORC_ETD) return -2;
+    s->ustar_given = ustar;
+    int rc = orc_adaptive_trial(s);
+    s->ustar_given = NULL;
+    return rc;
+}
+
 /* The adaptive algorithm of Sec. 3.2, Steps 0-4 (orc_adaptive_begin, then
  * orc_adaptive_trial until t_final or max_attempts trial steps).
  * Returns 0, -1 (PSD did not converge), or 1 (attempt budget used up). */

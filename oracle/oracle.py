@@ -102,6 +102,8 @@ def lib():
             L.orc_adaptive_begin.restype = C.c_int
             L.orc_adaptive_trial.argtypes = [C.c_void_p]
             L.orc_adaptive_trial.restype = C.c_int
+            L.orc_adaptive_trial_from.argtypes = [C.c_void_p, C.POINTER(C.c_double)]
+            L.orc_adaptive_trial_from.restype = C.c_int
             L.orc_get_last_k.argtypes = [C.c_void_p]
             L.orc_get_last_k.restype = C.c_double
             L.orc_get_next_k.argtypes = [C.c_void_p]
@@ -287,6 +289,12 @@ class Stepper:
     def adaptive_trial(self):
         """one trial of the open run: 0 after a trial, 2 at t_final, -1 PSD failure"""
         return lib().orc_adaptive_trial(self._h)
+
+    def adaptive_trial_from(self, ustar):
+        """one trial of the open run whose u* (IMEX, SAV) or v_0 (PSD) is the given field"""
+        a = np.ascontiguousarray(ustar, dtype=np.float64)
+        assert a.shape == (self.N, self.N)
+        return lib().orc_adaptive_trial_from(self._h, _dp(a))
 
     @property
     def last_k(self):

@@ -246,6 +246,7 @@ struct fch_ctx {
     fch_geom geom;
     fch_kparams kp;      // base parameters; passes copy and adjust
     fch_ctrl hc;         // host mirror of the control block
+    bool hc_fresh;       // hc equals the device's block: no launch since the last copy
     fch_ctrl *dctrl;
     double *part;
     void *U[3], *F[3], *Pb, *Qb, *Vb, *Nb, *Z, *tw, *tw2;
@@ -494,6 +495,7 @@ static void reset_ctrl(fch_ctx *ctx)
 static fch_status push_ctrl(fch_ctx *ctx)
 {
     CKC(ctx, cudaMemcpyAsync(ctx->dctrl, &ctx->hc, sizeof(fch_ctrl), cudaMemcpyHostToDevice, ctx->stream));
+    ctx->hc_fresh = true;
     return FCH_OK;
 }
 
@@ -501,6 +503,7 @@ static fch_status pull_ctrl(fch_ctx *ctx)
 {
     CKC(ctx, cudaMemcpyAsync(&ctx->hc, ctx->dctrl, sizeof(fch_ctrl), cudaMemcpyDeviceToHost, ctx->stream));
     CKC(ctx, cudaStreamSynchronize(ctx->stream));
+    ctx->hc_fresh = true;
     return FCH_OK;
 }
 
@@ -518,6 +521,7 @@ static fch_status col(fch_ctx *ctx, int mode, int src = 0, int flags = 0, const 
     kp.in1 = in1;
     kp.out0 = out0;
     kp.out1 = out1;
+    ctx->hc_fresh = false;
     timing_begin(ctx);
     cudaError_t e = ctx->prec == FCH_MIXED    ? fch_launch_col_f32(mode, kp, ctx->stream)
                     : ctx->prec == FCH_FP32X2 ? fch_launch_col_dfl(mode, kp, ctx->stream)
@@ -537,6 +541,7 @@ static fch_status row(fch_ctx *ctx, int mode, int flags = 0, const void *in0 = n
     kp.flags = flags;
     kp.in0 = in0;
     kp.out0 = out0;
+    ctx->hc_fresh = false;
     timing_begin(ctx);
     cudaError_t e = ctx->prec == FCH_MIXED    ? fch_launch_row_f32(mode, kp, ctx->stream)
                     : ctx->prec == FCH_FP32X2 ? fch_launch_row_dfl(mode, kp, ctx->stream)
@@ -550,6 +555,7 @@ static fch_status ctl(fch_ctx *ctx, int op, int na, double arg0 = 0.0, int flags
 {
     fch_kparams kp = ctx->kp;
     kp.flags = flags;
+    ctx->hc_fresh = false;
     timing_begin(ctx);
     cudaError_t e = fch_launch_ctrl(op, kp, na, 0, arg0, ctx->stream);
     timing_end(ctx, FCH_NCOL + FCH_NROW);
@@ -850,6 +856,7 @@ static fch_status psd_chunk(fch_ctx *ctx)
         }
     }
     if (graph_ok && ctx->psd_graph) {
+        ctx->hc_fresh = false;
         CKC(ctx, cudaGraphLaunch(ctx->psd_graph, ctx->stream));
         return FCH_OK;
     }
@@ -991,6 +998,7 @@ extern "C" fch_status fch_run_fixed(fch_ctx *ctx, fch_scheme scheme, double dt, 
         }
         ctx->fixed_dt[scheme] = dt;
     }
+    if (nsteps > 1) ctx->hc_fresh = false;
     for (long long i = 1; i < nsteps; i++) CKC(ctx, cudaGraphLaunch(ctx->fixed_graph[scheme], ctx->stream));
     return FCH_OK;
 }
@@ -1024,6 +1032,32 @@ extern "C" fch_status fch_adaptive_enqueue_psd_from(fch_ctx *ctx, const void *v0
     TRY(load_field(ctx, v0, dtype == 0, ctx->Vb));
     TRY(col(ctx, CM_START, FCH_SRC_V));
     fch_status s = psd_iterate(ctx);
+    if (s == FCH_OK) s = row(ctx, RM_F, FCH_FL_STORE_REAL, nullptr, nullptr, -1, 0.0, FCH_SRC_UNEW);
+    if (s == FCH_OK) s = col(ctx, CM_F_FINISH, FCH_SRC_UNEW, FCH_FL_AM3);
+    if (s == FCH_OK) s = ctl(ctx, OP_DECIDE_INIT, ctx->geom.col_blocks);
+    if (s != FCH_OK) ctx->failed = true;
+    return s;
+}
+
+// one adaptive IMEX or SAV trial (as fch_adaptive_enqueue) whose explicit part is
+// evaluated at the caller's u* instead of eq. (Richardson)
+extern "C" fch_status fch_adaptive_enqueue_from(fch_ctx *ctx, const void *ustar, int dtype)
+{
+    if (!ctx || !ustar || (dtype != 0 && dtype != 1)) return FCH_EINVAL;
+    if (!ctx->ad_open || ctx->failed || (ctx->ad_scheme != FCH_IMEX && ctx->ad_scheme != FCH_SAV))
+        return FCH_ESTATE;
+    // the given u*: its spectrum in Vb, (u*, Lap u*) packed for the row pass
+    TRY(load_field(ctx, ustar, dtype == 0, ctx->Vb));
+    TRY(col(ctx, CM_START, FCH_SRC_V));
+    fch_status s;
+    if (ctx->ad_scheme == FCH_IMEX) {
+        s = row(ctx, RM_NIMEX);
+        if (s == FCH_OK) s = col(ctx, CM_IMEX_SOLVE, 0, FCH_FL_PACK_F);
+    } else {
+        s = rowt(ctx, RM_SAV, 0, OP_SAV_E1, 0.0);
+        if (s == FCH_OK) s = colt(ctx, CM_SAV_PQ, 0, FCH_FL_USTAR_V, OP_SAV_R);
+        if (s == FCH_OK) s = col(ctx, CM_SAV_COMBINE, 0, FCH_FL_PACK_F);
+    }
     if (s == FCH_OK) s = row(ctx, RM_F, FCH_FL_STORE_REAL, nullptr, nullptr, -1, 0.0, FCH_SRC_UNEW);
     if (s == FCH_OK) s = col(ctx, CM_F_FINISH, FCH_SRC_UNEW, FCH_FL_AM3);
     if (s == FCH_OK) s = ctl(ctx, OP_DECIDE_INIT, ctx->geom.col_blocks);
@@ -1253,7 +1287,9 @@ static fch_status adaptive_begin(fch_ctx *ctx, fch_scheme scheme, double sigma, 
 {
     if (!ctx || !(sigma > 0) || scheme < FCH_IMEX || scheme > FCH_ETD) return FCH_EINVAL;
     if (!ctx->have_state || ctx->failed) return FCH_ESTATE;
-    TRY(pull_ctrl(ctx));
+    // the host mirror is read back only if something ran since it was last copied
+    // (a run resumed right after the end of the last one needs no device read)
+    if (!ctx->hc_fresh) TRY(pull_ctrl(ctx));
     if (ctx->hc.status) {
         ctx->failed = true;
         return (fch_status)ctx->hc.status;
@@ -1349,6 +1385,7 @@ extern "C" fch_status fch_adaptive_enqueue(fch_ctx *ctx, int n)
         const bool graph_ok = sc != FCH_PSD && !ctx->timing && ctx->trial_warm[sc] && !ctx->trial_nograph[sc];
         if (graph_ok && !ctx->trial_graph[sc] && !capture_trial(ctx)) ctx->trial_nograph[sc] = true;
         if (graph_ok && ctx->trial_graph[sc]) {
+            ctx->hc_fresh = false;
             CKC(ctx, cudaGraphLaunch(ctx->trial_graph[sc], ctx->stream));
             continue;
         }
@@ -1625,6 +1662,7 @@ extern "C" fch_status fch_ensemble_run_adaptive_each(fch_ensemble *e, const fch_
         for (int i = 0; i < e->m; i++) fch_adaptive_end(e->ctx[i], nullptr);
         return result;
     }
+    for (int i = 0; i < e->m; i++) e->ctx[i]->hc_fresh = false; // the graph writes their blocks
     for (long long l = 0;; l++) {
         if (max_launches > 0 && l >= max_launches) {
             result = FCH_ETIMEOUT;

@@ -36,7 +36,7 @@ EXPORTS = ["fch_status_string", "fch_last_cuda_error", "fch_params_default", "fc
            "fch_fno_backward", "fch_fno_adam", "fch_step_psd_from", "fch_run_fixed",
            "fch_adaptive_trial_info", "fch_get_history_device", "fch_adaptive_enqueue_psd_from",
            "fch_ensemble_run_adaptive_each", "fch_autotune_step", "fch_step_from", "fch_fno_set_bf16",
-           "fch_alu_peak", "fch_fno_learned_start"]
+           "fch_alu_peak", "fch_fno_learned_start", "fch_adaptive_enqueue_from"]
 NCOL, NROW = 10, 8
 NPASS = NCOL + NROW + 1
 PASS_NAMES = (["col_fwd_store", "col_inv_load", "col_start", "col_imex_solve", "col_f_finish",
@@ -157,6 +157,7 @@ def lib():
         L.fch_autotune_reset.argtypes = []
         L.fch_alu_peak.argtypes = [C.c_int, vp, C.POINTER(C.c_double), C.POINTER(C.c_int)]
         L.fch_fno_learned_start.argtypes = [vp, vp, C.c_double, vp]
+        L.fch_adaptive_enqueue_from.argtypes = [vp, vp, C.c_int]
         L.fch_fft_plan_destroy.argtypes = [vp]
         L.fch_fft_r2c.argtypes = [vp, vp, vp, C.c_int]
         L.fch_fft_c2r.argtypes = [vp, vp, vp, C.c_int]
@@ -341,6 +342,12 @@ class Context:
     def adaptive_enqueue_psd_from(self, v0):
         self._ck(lib().fch_adaptive_enqueue_psd_from(self._h, _tensor_ptr(v0), _dtype_code(v0)),
                  "fch_adaptive_enqueue_psd_from")
+
+    def adaptive_enqueue_from(self, ustar):
+        """one IMEX or SAV trial of the open adaptive run whose u* is the device field ustar"""
+        assert ustar.is_cuda and ustar.is_contiguous() and tuple(ustar.shape) == (self.n, self.n)
+        self._ck(lib().fch_adaptive_enqueue_from(self._h, _tensor_ptr(ustar), _dtype_code(ustar)),
+                 "fch_adaptive_enqueue_from")
 
     def step_from(self, scheme, dt: float, ustar):
         """one IMEX or SAV step whose extrapolation u* is the device field ustar"""

@@ -109,18 +109,19 @@ def learned_start(ctx, net, v0, dt: float = 0.0):
     return v0
 
 
-def run_adaptive_psd(ctx, sigma, t_final, device, net=None, k_range=None, max_trials=100000):
-    """The adaptive PSD-BDF2 run of Sec. 3.2 trial by trial, each PSD iteration started
-    from u* (net None) or from the network's v_0; with k_range = (lo, hi) the network
-    is used only for trial steps in that range (the step sizes it was trained on: its
-    inputs are normalised and carry no step size, so outside that range its correction
-    does not scale with the step) and u* elsewhere. The host reads each trial's size
-    (fch_adaptive_trial_info) to choose; v_0 is formed on the device. Returns (stats,
-    trials, learned trials)."""
+def run_adaptive_learned(ctx, scheme, sigma, t_final, device, net=None, k_range=None, max_trials=100000):
+    """The adaptive run of Sec. 3.2 trial by trial, each trial from the network's v_0
+    (net given, trial size in k_range when given) or the plain trial: for PSD v_0 is the
+    first iterate of the iteration (fch_adaptive_enqueue_psd_from), for IMEX and SAV the
+    extrapolation u* of the trial (fch_adaptive_enqueue_from). The network's inputs are
+    normalised and carry no step size, so outside the step sizes it was trained on its
+    correction does not scale with the step: k_range limits it to those. The host reads
+    each trial's size (fch_adaptive_trial_info) to choose; v_0 is formed on the device.
+    Returns (stats, trials, learned trials)."""
     import torch
 
     n = ctx.n
-    ctx.adaptive_begin("psd", sigma, t_final)
+    ctx.adaptive_begin(scheme, sigma, t_final)
     v0 = torch.empty((n, n), dtype=torch.float64, device=device)
     trials = learned = 0
     while trials < max_trials:
@@ -131,7 +132,15 @@ def run_adaptive_psd(ctx, sigma, t_final, device, net=None, k_range=None, max_tr
             ctx.adaptive_enqueue(1)
         else:
             ctx.fno_learned_start(net, v0)
-            ctx.adaptive_enqueue_psd_from(v0)
+            if scheme == "psd":
+                ctx.adaptive_enqueue_psd_from(v0)
+            else:
+                ctx.adaptive_enqueue_from(v0)
             learned += 1
         trials += 1
     return ctx.adaptive_end(), trials, learned
+
+
+def run_adaptive_psd(ctx, sigma, t_final, device, net=None, k_range=None, max_trials=100000):
+    """run_adaptive_learned for PSD-BDF2 (the learned first iterate of Sec. 3.3)"""
+    return run_adaptive_learned(ctx, "psd", sigma, t_final, device, net, k_range, max_trials)

@@ -52,6 +52,15 @@ def oparams(fp, **kw):
     return O.params(**d)
 
 
+def lib_params(q=0.0, **kw):
+    """the library's parameters with explicit SAV constants zeta and D0 (the library
+    computes them at fch_create when 0; the oracle gets the same explicit values)"""
+    p = fch.params_default(q, **kw)
+    p.zeta = 1.1 if q < 0.35 else 1.8
+    p.D0 = 170.0
+    return p
+
+
 _CACHE = {}
 
 
@@ -102,8 +111,9 @@ def compare_trials(ctx, recs, scheme, sigma, t_final, state_tol=1e-10):
         assert st["t"] == pytest.approx(r["t"], rel=1e-9, abs=1e-15), i
         err = rel(ctx.get_state(), r["state"])
         assert err < state_tol, (i, err)
-        k_next, _, _ = ctx.adaptive_trial_info()
-        assert k_next == pytest.approx(r["next_k"], rel=E_TOL / (3 * e_orc) + 1e-12), i
+        k_next, _, done = ctx.adaptive_trial_info()
+        if not done:  # at t_final the run ends: no next trial
+            assert k_next == pytest.approx(r["next_k"], rel=E_TOL / (3 * e_orc) + 1e-12), i
     ctx.adaptive_end()
     return seen
 
@@ -120,7 +130,7 @@ def test_benchmark_chain_1024_trial_by_trial(prec, sigma):
     # seed 3; default tiles) from its backward-Euler start: the first trials, each
     # accepted, growing the step from k_min
     n = 1024
-    p = fch.params_default(0.0, eta2=0.15, prec=prec)
+    p = lib_params(0.0, eta2=0.15, prec=prec)
     u0 = network(n)
 
     def run():
@@ -142,7 +152,7 @@ def test_1024_trials_from_a_history(prec):
     # start's transient makes the first trials fail (e ~ 1e-3 > sigma_tol) and the
     # controller retry at the A_dp proposals
     n, kn = 1024, 1e-6
-    p = fch.params_default(0.0, eta2=0.15, prec=prec)
+    p = lib_params(0.0, eta2=0.15, prec=prec)
     um = network(n)
 
     def run():
@@ -167,7 +177,7 @@ def test_1024_trials_from_a_history(prec):
 def test_adaptive_64_every_trial(scheme, prec):
     # the whole adaptive run of test_adaptive_vs_oracle, compared after every trial
     n = 64
-    p = fch.params_default(0.0, zero_stab_cap=1, prec=prec)
+    p = lib_params(0.0, zero_stab_cap=1, prec=prec)
     if scheme == "psd":
         p.k_max = 0.05
     u0 = I.circle_bilayer(n, noise=1e-3)
@@ -211,7 +221,7 @@ def test_fixed_step_default_kernels_vs_oracle(n, scheme, prec):
     # one variable-step BDF2 (or ETDRK2) step of every scheme on the compile-time
     # kernels of the grid with the default tiles, from identical history: 1e-12
     kn, dt = 1e-5, 1.5e-5
-    p = fch.params_default(0.0, eta2=0.15, prec=prec, psd_itol=1e-12)
+    p = lib_params(0.0, eta2=0.15, prec=prec, psd_itol=1e-12)
     ref, iters, r = _oracle_step(n, scheme, p, kn, dt)
     un, um = _history(n)
     with fch.Context(n, p) as ctx:
@@ -228,7 +238,7 @@ def test_fixed_step_default_kernels_vs_oracle(n, scheme, prec):
 def test_imex_2048_step_vs_oracle(prec):
     # the largest grid: the backward-Euler start and one BDF2 step of IMEX
     n = 2048
-    p = fch.params_default(0.0, eta2=0.15, prec=prec)
+    p = lib_params(0.0, eta2=0.15, prec=prec)
     u0 = network(n)
 
     def make():
@@ -246,3 +256,44 @@ def test_imex_2048_step_vs_oracle(prec):
         assert rel(ctx.get_state(), u1) < 1e-10
         ctx.step("imex", 1.5e-6)
         assert rel(ctx.get_state(), u2) < 1e-10
+
+
+# --------------------------------------------------------------------------- given extrapolation, adaptive
+@pytest.mark.parametrize("prec", [0, 2])
+@pytest.mark.parametrize("scheme", ["imex", "sav"])
+def test_adaptive_trials_from_a_given_extrapolation(scheme, prec):
+    # fch_adaptive_enqueue_from: adaptive trials whose u* is the caller's field (the
+    # learned extrapolation's entry point) against the oracle's trials with the same u*
+    n, kn, sigma = 64, 1e-3, 1e-4
+    p = lib_params(0.2, prec=prec)
+    un = I.smooth_random(n, seed=3)
+    um = I.smooth_random(n, seed=4, amp=0.49)
+    pert = 0.05 * I.smooth_random(n, seed=9, offset=0.0)
+
+    def run():
+        s = O.Stepper(n, L, oparams(p))
+        s.set_history(un, um, kn)
+        assert s.adaptive_begin(scheme, sigma, 1.0) == 0
+        recs = []
+        for _ in range(4):
+            ustar = s.state() + pert
+            assert s.adaptive_trial_from(ustar) == 0
+            recs.append(dict(ustar=ustar, k=s.last_k, e=s.last_e, accepted=s.last_accepted,
+                             t=s.t, state=s.state(), next_k=s.next_k))
+        return recs
+
+    recs = cached(("from", scheme), run)
+    with fch.Context(n, p) as ctx:
+        ctx.set_history(un, um, kn)
+        ctx.adaptive_begin(scheme, sigma, 1.0)
+        for i, r in enumerate(recs):
+            k_gpu, _, done = ctx.adaptive_trial_info()
+            assert not done and k_gpu == pytest.approx(r["k"], rel=1e-9)
+            before = ctx.stats()
+            ctx.adaptive_enqueue_from(torch.tensor(r["ustar"], device=torch.device("cuda:0")))
+            st = ctx.stats()
+            assert abs(st["e_last"] - r["e"]) <= E_TOL, (i, st["e_last"], r["e"])
+            assert (st["n_steps"] == before["n_steps"] + 1) == r["accepted"]
+            assert rel(ctx.get_state(), r["state"]) < 1e-10, i
+        ctx.adaptive_end()
+    assert any(r["accepted"] for r in recs)

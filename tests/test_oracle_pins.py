@@ -752,3 +752,28 @@ def test_controller_run_is_a_sequence_of_trials():
     nk = b.next_k
     assert b.adaptive_begin("imex", sigma, tf) == 0 and b.adaptive_trial() == 0
     assert b.last_k == nk
+
+
+@pytest.mark.parametrize("scheme", ["imex", "sav", "psd"])
+def test_adaptive_trial_from_the_extrapolation_is_the_plain_trial(scheme):
+    # a trial of an adaptive run given eq. (Richardson) from outside is the plain trial,
+    # bit for bit (state, error estimate, decision, next size); ETD takes no u*
+    N, kn = 32, 1e-4
+    um, un = _two_level_state(N)
+    out = []
+    for given in (False, True):
+        s = O.Stepper(N, L, O.params(k_max=0.05 if scheme == "psd" else np.inf))
+        s.set_history(un, um, kn)
+        assert s.adaptive_begin(scheme, 1e-5, 1.0) == 0
+        for _ in range(3):
+            k = s.next_k
+            ustar = s.state() + (k / s.kn) * (s.state() - s.prev())
+            rc = s.adaptive_trial_from(ustar) if given else s.adaptive_trial()
+            assert rc == 0
+        out.append((s.state(), s.last_e, s.next_k, s.counts()))
+    assert np.array_equal(out[0][0], out[1][0])
+    assert out[0][1:] == out[1][1:]
+    s = O.Stepper(N, L, O.params())
+    s.set_history(un, um, kn)
+    s.adaptive_begin("etd", 1e-5, 1.0)
+    assert s.adaptive_trial_from(un) == -2
