@@ -287,7 +287,7 @@ def test_learned_start_on_the_device_vs_oracle(small_trained_net, mode):
 @pytest.mark.parametrize("scheme", ["imex", "sav"])
 def test_adaptive_imex_sav_with_learned_extrapolation(small_trained_net, scheme):
     # the adaptive IMEX / SAV run of Sec. 3.2 with the network's v_0 as every trial's
-    # u* on the trained step sizes (fch_fno_learned_start + fch_adaptive_enqueue_from):
+    # u* after the start (fch_fno_learned_start + fch_adaptive_enqueue_from):
     # it reaches t_final, keeps the mass (u* does not enter the k = 0 mode of either
     # solve) and stays within the local-error tolerance's reach of the plain run
     from paper_2006_04784_gb300 import fno_train as T
@@ -301,8 +301,7 @@ def test_adaptive_imex_sav_with_learned_extrapolation(small_trained_net, scheme)
         with fch.Context(n, p) as ctx:
             ctx.set_state(u0)
             m0 = ctx.mass()
-            st, trials, learned = T.run_adaptive_learned(ctx, scheme, 1e-5, 2e-2, DEV, net=use,
-                                                         k_range=(5e-4, 2e-3))
+            st, trials, learned = T.run_adaptive_learned(ctx, scheme, 1e-5, 2e-2, DEV, net=use)
             assert st["t"] == pytest.approx(2e-2, rel=1e-12) and trials > 5
             assert abs(ctx.mass() - m0) < 1e-12 * abs(m0)
             out[name] = (st, ctx.get_state(), learned)
