@@ -350,9 +350,10 @@ fch_status fch_adaptive_enqueue_from(fch_ctx *ctx, const void *ustar_dev, int dt
 fch_status fch_fno_learned_start(fch_ctx *ctx, fch_fno *net, double dt, void *v0_dev);
 
 /* ---- pass tiles (the paper has no counterpart: a GPU launch choice) ----
- * fch_autotune times the forward row pass (two real fields -> pair-layout work
- * array) and the forward column pass (work array -> two half spectra) of one field
- * pair at n x n in precision prec, for each candidate tile: the default, the
+ * fch_autotune times the forward row pass (real fields -> pair-layout work array)
+ * and the forward column pass (work array -> half spectra) at n x n in precision
+ * prec as a standalone transform plan launches them (as many field pairs per launch
+ * as a plan's work array holds; one pair for FCH_FP32X2), for each candidate tile: the default, the
  * plain shared-memory kernels at n = 1024 (where the default is the warp-level path
  * or the two-block clusters), the warp-level column passes (FCH_MIXED, n = 1024), and
  * the generic kernels at 1, 2, 4, 8, 16 rows (column pairs) per

@@ -1818,6 +1818,8 @@ static bool tuned_tiles(int n, int prec, int *row, int *col)
 }
 
 // Mean time (us) of `reps` launches of one pass after two untimed ones.
+static int plan_chunk(int n, int prec);
+
 template <typename F> static cudaError_t time_pass(F launch, cudaStream_t s, int reps, double *us)
 {
     cudaEvent_t a = nullptr, b = nullptr;
@@ -1852,12 +1854,17 @@ extern "C" fch_status fch_autotune(int n, int prec, void *stream, fch_tile *out)
     cudaStream_t s = (cudaStream_t)stream;
     const bool single = prec == FCH_MIXED;
     const size_t csz = single ? 8 : 16, rsz = single ? 4 : 8;
+    // the passes are timed as a standalone transform plan launches them: as many
+    // field pairs per launch as a plan's work array holds (FCH_FP32X2, which has no
+    // plans, one pair)
+    const int np = prec == FCH_FP32X2 ? 1 : plan_chunk(n, prec);
+    const size_t rb = (size_t)n * n * rsz, cb = (size_t)(n / 2 + 1) * n * csz;
     void *x = nullptr, *Z = nullptr, *X = nullptr, *tw = nullptr, *tw2 = nullptr;
-    cudaError_t e = cudaMalloc(&x, 2 * (size_t)n * n * rsz);
-    if (e == cudaSuccess) e = cudaMalloc(&Z, (size_t)n * n * csz);
-    if (e == cudaSuccess) e = cudaMalloc(&X, 2 * (size_t)(n / 2 + 1) * n * csz);
+    cudaError_t e = cudaMalloc(&x, 2 * np * rb);
+    if (e == cudaSuccess) e = cudaMalloc(&Z, (size_t)np * n * n * csz);
+    if (e == cudaSuccess) e = cudaMalloc(&X, 2 * np * cb);
     if (e == cudaSuccess) e = cudaMalloc(&tw, (size_t)n * csz);
-    if (e == cudaSuccess) e = cudaMemsetAsync(x, 0, 2 * (size_t)n * n * rsz, s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(x, 0, 2 * np * rb, s);
     fch_ctx dummy;
     if (e == cudaSuccess && upload_twiddles(&dummy, n, prec, tw, s) != FCH_OK) e = cudaErrorUnknown;
     if (e == cudaSuccess && single && n == 1024) e = upload_tw2(&tw2, s);
@@ -1872,10 +1879,15 @@ extern "C" fch_status fch_autotune(int n, int prec, void *stream, fch_tile *out)
     kp.tail_op = -1;
     kp.flags = FCH_FL_NOSKIP | (single ? 0 : FCH_FL_F64IO);
     kp.in0 = x;
-    kp.in1 = (const char *)x + (size_t)n * n * rsz;
+    kp.in1 = (const char *)x + rb;
     kp.out0 = X;
-    kp.out1 = (char *)X + (size_t)(n / 2 + 1) * n * csz;
-    auto launch = [&](bool is_col, const fch_kparams &k) {
+    kp.out1 = (char *)X + cb;
+    kp.npairs = np;
+    kp.pdl = prec == FCH_FP32X2 ? 0 : 1; // as plans launch
+    auto launch = [&](bool is_col, const fch_kparams &kk) {
+        fch_kparams k = kk; // pair j reads fields 2j, 2j+1 and writes their spectra
+        k.pstride_in = is_col ? 0 : 2 * (long long)rb;
+        k.pstride_out = is_col ? 2 * (long long)cb : 0;
         if (is_col)
             return prec == FCH_MIXED    ? fch_launch_col_f32(CM_FWD_STORE, k, s)
                    : prec == FCH_FP32X2 ? fch_launch_col_dfl(CM_FWD_STORE, k, s)

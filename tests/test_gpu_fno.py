@@ -306,4 +306,7 @@ def test_adaptive_imex_sav_with_learned_extrapolation(small_trained_net, scheme)
             assert abs(ctx.mass() - m0) < 1e-12 * abs(m0)
             out[name] = (st, ctx.get_state(), learned)
     assert out["plain"][2] == 0 and out["learned"][2] > 0
-    assert rel(out["learned"][1], out["plain"][1]) < 1e-4
+    # two runs at sigma_tol = 1e-5 through different trials: apart by the global error
+    # that tolerance allows (~sigma_tol^(2/3), Sec. 5.2)
+    assert rel(out["learned"][1], out["plain"][1]) < 1e-3
+    assert out["learned"][0]["n_steps"] <= 1.5 * out["plain"][0]["n_steps"]
