@@ -398,7 +398,7 @@ def fft_throughput(fch, dev, alu, n=N_GRID, batch=32, iters=10, warmup=3):
         X = torch.empty(batch, n // 2 + 1, n, dtype=torch.complex128 if rdt == torch.float64 else torch.complex64,
                         device=dev)
         y = torch.empty_like(x)
-        fch.autotune(n, prec)  # plans take the tuned tiles of (n, precision)
+        tiles = fch.autotune(n, prec)  # plans take the tuned tiles of (n, precision)
         plan = fch.FFTPlan(n, prec, stream=stream)
 
         def ours():
@@ -426,6 +426,7 @@ def fft_throughput(fch, dev, alu, n=N_GRID, batch=32, iters=10, warmup=3):
         rs = 8 if rdt == torch.float64 else 4
         byt = n * n * rs + (n // 2 + 1) * n * 2 * rs
         ent = {"fch": res["fch"], "cufft": res["cufft"], "fch_over_cufft": res["fch"] / res["cufft"],
+               "tiles": tiles,
                "round_trip_max_rel_err": err, "bytes_per_transform": byt,
                "hbm_frac": res["fch"] * byt / 1e9 / hbm, "hbm_peak_gbs": hbm}
         fl = 2.5 * n * n * math.log2(n * n)
@@ -436,6 +437,22 @@ def fft_throughput(fch, dev, alu, n=N_GRID, batch=32, iters=10, warmup=3):
         out[name] = ent
         del x, X, y
     return out
+
+
+def fft_only(args):
+    """the `fft` entry of the benchmark line alone (--fft-only): standalone transforms at
+    1024^2 with the tiles fch_autotune picks, against cuFFT"""
+    import torch
+
+    from paper_2006_04784_gb300 import build as B
+    B.build()
+    from paper_2006_04784_gb300 import fch
+
+    dev = torch.device("cuda", 0)
+    f32, sms = fch.alu_peak(fch.FCH_MIXED)
+    f64, _ = fch.alu_peak(fch.FCH_FP64)
+    return fft_throughput(fch, dev, {"fp32": f32, "fp64": f64, "sms": sms}, batch=args.fft_batch,
+                          iters=args.fft_iters)
 
 
 def fixed_step_throughput(fch, I, dev, n=N_GRID, steps=200, dt=1e-6):
@@ -1401,6 +1418,10 @@ def main():
     ap.add_argument("--fno-iters", type=int, default=1500)
     ap.add_argument("--fno-lr", type=float, default=1e-3)
     ap.add_argument("--fno-t-adaptive", type=float, default=2e-2)
+    ap.add_argument("--fft-only", action="store_true",
+                    help="only the standalone transform throughput (fch_fft_r2c / c2r against cuFFT)")
+    ap.add_argument("--fft-batch", type=int, default=32)
+    ap.add_argument("--fft-iters", type=int, default=10)
     ap.add_argument("--error-budget", action="store_true",
                     help="per-field single/double-float vs FP64 errors at 1024^2 and 2048^2 instead")
     ap.add_argument("--budget-steps", type=int, default=5)
@@ -1419,6 +1440,8 @@ def main():
         out = workloads(args)
     elif args.error_budget:
         out = error_budget(args)
+    elif args.fft_only:
+        out = fft_only(args)
     elif args.ensemble:
         out = ensemble_bench(args)
     elif args.fno:

@@ -642,6 +642,12 @@ extern "C" fch_status fch_create(const fch_grid *g, const fch_params *p, void *s
     if (e == cudaSuccess) e = cudaMemsetAsync(ctx->nfft_dev, 0, sizeof(long long), ctx->stream);
     if (e == cudaSuccess) e = cudaMalloc((void **)&ctx->ticket, sizeof(unsigned int));
     if (e == cudaSuccess) e = cudaMemsetAsync(ctx->ticket, 0, sizeof(unsigned int), ctx->stream);
+    // every state array starts at zero: a backward-Euler start multiplies u^{n-1} by
+    // c = 0, which must not meet whatever the memory held before (0 x NaN = NaN)
+    for (void **b : bufs)
+        if (e == cudaSuccess) e = cudaMemsetAsync(*b, 0, hs, ctx->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(ctx->Z, 0, (size_t)N * N * csz, ctx->stream);
+    for (int i = 0; i < 3 && e == cudaSuccess; i++) e = cudaMemsetAsync(ctx->Rs[i], 0, (size_t)N * N * csz, ctx->stream);
     if (e != cudaSuccess) {
         snprintf(ctx->errbuf, sizeof(ctx->errbuf), "fch_create: %s", cudaGetErrorString(e));
         fch_destroy(ctx);
@@ -749,6 +755,9 @@ static fch_status set_state_common(fch_ctx *ctx, const void *u_dev, bool io64)
 {
     reset_ctrl(ctx);
     TRY(push_ctrl(ctx));
+    // u^{n-1} (slot 1) enters the start step with the coefficient c = 0: keep it finite
+    CKC(ctx, cudaMemsetAsync(ctx->U[1], 0, (size_t)(ctx->N / 2 + 1) * ctx->N * (ctx->prec == FCH_MIXED ? 8 : 16),
+                             ctx->stream));
     TRY(load_field(ctx, u_dev, io64, ctx->U[0]));
     TRY(sav_r_init(ctx, FCH_SRC_UN, 1.0));
     ctx->have_state = true;

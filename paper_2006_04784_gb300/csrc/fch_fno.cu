@@ -30,6 +30,7 @@
 
 #include "../../include/fch.h"
 #include "fch_internal.h"
+#include "fch_tc.cuh"
 
 namespace {
 
@@ -237,6 +238,268 @@ __global__ void fno_mix(const float2 *__restrict__ X, const WT *__restrict__ R, 
     }
 }
 
+// ---------------------------------------------------------------------------
+// Inference with the spectral convolutions as truncated DFTs over the retained
+// modes (fch_fno_set_bf16(f, 2)): for a layer input h[b][i][y][x],
+//   X[b][i][y][kx] = sum_x h (cos - i sin)(2 pi kx x / n),  kx < M     (rows)
+//   Y[b][i][kyi][kx] = sum_y X e^{-2 pi i ky y / n}                     (columns)
+//   Z[b][o][kyi][kx] = sum_i R[m][o][i] Y[b][i][kyi][kx], m = kx (2M-1) + kyi
+//   V[b][o][y][kx] = sum_kyi Z e^{+2 pi i ky y / n}
+//   S[b][o][y][x] = (1/n^2) sum_kx w(kx) Re(V e^{+2 pi i kx x / n}),  w(0) = 1, else 2
+// which is the C2R of the retained spectrum through H (the real part of the kx = 0
+// sum is what H keeps), without the full 2D transforms of every channel. The row
+// DFT, a GEMM with K = n, runs on the tensor cores (tcgen05, BF16 operands, FP32
+// sums); the other stages are small and run as plain kernels in FP32.
+
+constexpr int kTcRows = 128, kTcKc = 64, kTcLBO = 144, kTcSBO = 8 * kTcLBO, kTcNB = 32;
+constexpr int kTcBound = 1 << 22; // polls of an mbarrier before a kernel gives up
+
+// Bt[j][x] (bf16): cos(2 pi j x / n) for j < 16, -sin(2 pi (j - 16) x / n) for j >= 16;
+// tw[kx][x] (float2): (cos, sin)(2 pi kx x / n), kx < 16
+__global__ void fno_dft_tables(__nv_bfloat16 *__restrict__ Bt, float2 *__restrict__ tw, int n)
+{
+    const long t = (long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= 16L * n) return;
+    const int kx = (int)(t / n), x = (int)(t - (long)kx * n);
+    double sn, cs;
+    sincospi(2.0 * (double)((kx * (long)x) % n) / (double)n, &sn, &cs);
+    Bt[(long)kx * n + x] = __double2bfloat16(cs);
+    Bt[(long)(16 + kx) * n + x] = __double2bfloat16(-sn);
+    tw[(long)kx * n + x] = make_float2((float)cs, (float)sn);
+}
+
+// X[r][kx] = (D[r][kx], D[r][16 + kx]) with D = bf16(h) Bt^T over K = n: one CTA of 128
+// threads per 128 rows, K in chunks of 64 staged in two shared-memory buffers
+// (core-matrix layout, see fch_tc.cuh); thread 0 issues four K = 16 MMAs per chunk
+// into a 128 x 32 FP32 accumulator in tensor memory and commits them to the buffer's
+// mbarrier, which the threads wait on before they refill that buffer. A wait that
+// runs out of polls sets *err and the CTA stops issuing, waits (bounded) for what it
+// issued, frees its tensor memory and returns.
+__global__ void __launch_bounds__(128) fno_rowdft_tc(const float *__restrict__ h, const __nv_bfloat16 *__restrict__ Bt,
+                                                     float2 *__restrict__ X, int R, int n, int *err)
+{
+    constexpr int A_BYTES = (kTcRows / 8) * kTcSBO, B_BYTES = (kTcNB / 8) * kTcSBO;
+    __shared__ __align__(128) unsigned char sA[2][A_BYTES];
+    __shared__ __align__(128) unsigned char sB[2][B_BYTES];
+    __shared__ __align__(8) uint64_t bar[2];
+    __shared__ uint32_t tslot;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const long row0 = (long)blockIdx.x * kTcRows;
+    if (warp == 0) {
+        fch::tc::tmem_alloc(&tslot, 32);
+        fch::tc::tmem_relinquish();
+    }
+    if (tid == 0) {
+        fch::tc::mbar_init(&bar[0], 1);
+        fch::tc::mbar_init(&bar[1], 1);
+        fch::tc::mbar_init_fence();
+    }
+    fch::tc::fence_before_sync();
+    __syncthreads();
+    fch::tc::fence_after_sync();
+    const uint32_t tmem = tslot;
+    constexpr uint32_t idesc = fch::tc::idesc_bf16_f32(kTcRows, kTcNB);
+    const int nch = n / kTcKc;
+    bool ok = true;
+    int issued = 0; // chunks whose MMAs thread 0 committed
+    for (int c = 0; c < nch; c++) {
+        const int b = c & 1;
+        if (c >= 2) ok = fch::tc::mbar_wait(&bar[b], (uint32_t)(((c >> 1) - 1) & 1), kTcBound);
+        if (!__syncthreads_and(ok)) break;
+        // A: 128 rows x 8 K-cores of 16 bytes (8 bf16); thread -> (row, core) with a
+        // warp covering 4 rows x 8 cores, so each row's 64 floats are read contiguously
+        unsigned char *a = sA[b];
+#pragma unroll
+        for (int i = 0; i < 8; i++) {
+            const int j = tid + 128 * i, r = j >> 3, kc = j & 7;
+            const long gr = row0 + r;
+            uint4 v = make_uint4(0, 0, 0, 0);
+            if (gr < R) {
+                const float4 *src = reinterpret_cast<const float4 *>(h + gr * n + (long)c * kTcKc + kc * 8);
+                const float4 p = __ldg(src), q = __ldg(src + 1);
+                __nv_bfloat162 b0 = __floats2bfloat162_rn(p.x, p.y), b1 = __floats2bfloat162_rn(p.z, p.w);
+                __nv_bfloat162 b2 = __floats2bfloat162_rn(q.x, q.y), b3 = __floats2bfloat162_rn(q.z, q.w);
+                v = make_uint4(*reinterpret_cast<uint32_t *>(&b0), *reinterpret_cast<uint32_t *>(&b1),
+                               *reinterpret_cast<uint32_t *>(&b2), *reinterpret_cast<uint32_t *>(&b3));
+            }
+            *reinterpret_cast<uint4 *>(a + (r >> 3) * kTcSBO + kc * kTcLBO + (r & 7) * 16) = v;
+        }
+        // B: the 32 table rows x 8 K-cores
+        unsigned char *bb = sB[b];
+#pragma unroll
+        for (int i = 0; i < 2; i++) {
+            const int j = tid + 128 * i, r = j >> 3, kc = j & 7;
+            const uint4 v = __ldg(reinterpret_cast<const uint4 *>(Bt + (long)r * n + (long)c * kTcKc + kc * 8));
+            *reinterpret_cast<uint4 *>(bb + (r >> 3) * kTcSBO + kc * kTcLBO + (r & 7) * 16) = v;
+        }
+        fch::tc::fence_async_smem();
+        __syncthreads();
+        if (tid == 0) {
+            fch::tc::fence_after_sync();
+            const uint32_t sa = fch::tc::smem_u32(a), sb = fch::tc::smem_u32(bb);
+#pragma unroll
+            for (int k = 0; k < kTcKc / 16; k++)
+                fch::tc::mma_bf16(tmem, fch::tc::smem_desc(sa + 2 * k * kTcLBO, kTcLBO, kTcSBO),
+                                  fch::tc::smem_desc(sb + 2 * k * kTcLBO, kTcLBO, kTcSBO), idesc,
+                                  (c | k) != 0);
+            fch::tc::mma_commit(&bar[b]);
+        }
+        issued = c + 1;
+    }
+    // the last commit covers every MMA issued
+    bool done = issued == 0;
+    if (issued > 0) done = fch::tc::mbar_wait(&bar[(issued - 1) & 1], (uint32_t)(((issued - 1) >> 1) & 1), kTcBound);
+    ok = __syncthreads_and(ok && done && issued == nch);
+    fch::tc::fence_after_sync();
+    if (ok) {
+        float v[32];
+        fch::tc::tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16), v);
+        const long r = row0 + warp * 32 + lane;
+        if (r < R) {
+            float4 *dst = reinterpret_cast<float4 *>(X + r * 16);
+#pragma unroll
+            for (int k = 0; k < 8; k++)
+                dst[k] = make_float4(v[2 * k], v[16 + 2 * k], v[2 * k + 1], v[16 + 2 * k + 1]);
+        }
+    } else if (tid == 0) {
+        atomicExch(err, 1);
+    }
+    fch::tc::fence_before_sync();
+    __syncthreads();
+    if (warp == 0) fch::tc::tmem_dealloc(tmem, 32);
+}
+
+// Y[f][kyi][kx] = sum_y X[f][y][kx] e^{-2 pi i ky y / n}: one block per (field f, kx),
+// threads over y, the 2M-1 sums reduced in a fixed order (warp shuffles, then warps)
+template <int MM>
+__global__ void __launch_bounds__(256) fno_coldft(const float2 *__restrict__ X, const float2 *__restrict__ tw1,
+                                                  float2 *__restrict__ Y, int n)
+{
+    constexpr int K2 = 2 * MM - 1;
+    __shared__ float2 part[8][K2];
+    const int f = blockIdx.x, kx = blockIdx.y, tid = threadIdx.x;
+    float2 acc[K2];
+#pragma unroll
+    for (int k = 0; k < K2; k++) acc[k] = make_float2(0.f, 0.f);
+    for (int y = tid; y < n; y += 256) {
+        const float2 v = X[((long)f * n + y) * 16 + kx];
+#pragma unroll
+        for (int k = 0; k < K2; k++) {
+            const int ky = k < MM ? k : n - (k - MM + 1);
+            const float2 w = tw1[(int)(((long)ky * y) & (n - 1))]; // (cos, sin)(2 pi ky y / n)
+            acc[k].x += v.x * w.x + v.y * w.y;
+            acc[k].y += v.y * w.x - v.x * w.y;
+        }
+    }
+#pragma unroll
+    for (int k = 0; k < K2; k++)
+        for (int o = 16; o > 0; o >>= 1) {
+            acc[k].x += __shfl_down_sync(0xffffffffu, acc[k].x, o);
+            acc[k].y += __shfl_down_sync(0xffffffffu, acc[k].y, o);
+        }
+    if ((tid & 31) == 0)
+#pragma unroll
+        for (int k = 0; k < K2; k++) part[tid >> 5][k] = acc[k];
+    __syncthreads();
+    if (tid < K2) {
+        float2 sum = make_float2(0.f, 0.f);
+        for (int w = 0; w < 8; w++) {
+            sum.x += part[w][tid].x;
+            sum.y += part[w][tid].y;
+        }
+        Y[((long)f * K2 + tid) * MM + kx] = sum;
+    }
+}
+
+// Z[b][o][kyi][kx] = sum_i R[m][o][i] Y[b][i][kyi][kx], m = kx (2M-1) + kyi
+template <typename WT>
+__global__ void fno_mix_modes(const float2 *__restrict__ Y, const WT *__restrict__ R, float2 *__restrict__ Z,
+                              int B, int W, int M)
+{
+    const int K2 = 2 * M - 1, K = M * K2;
+    const long t = (long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= (long)B * W * K) return;
+    const int q = (int)(t % K), o = (int)((t / K) % W), b = (int)(t / ((long)K * W));
+    const int kyi = q / M, kx = q - kyi * M, m = kx * K2 + kyi;
+    float re = 0.f, im = 0.f;
+    for (int i = 0; i < W; i++) {
+        const float2 x = Y[(((long)b * W + i) * K2 + kyi) * M + kx];
+        const float2 w = wld2(R, ((long)m * W + o) * W + i);
+        re += w.x * x.x - w.y * x.y;
+        im += w.x * x.y + w.y * x.x;
+    }
+    Z[(((long)b * W + o) * K2 + kyi) * M + kx] = make_float2(re, im);
+}
+
+// V[f][y][kx] = sum_kyi Z[f][kyi][kx] e^{+2 pi i ky y / n}
+template <int MM>
+__global__ void fno_icoldft(const float2 *__restrict__ Z, const float2 *__restrict__ tw1, float2 *__restrict__ V,
+                            long nf, int n)
+{
+    constexpr int K2 = 2 * MM - 1;
+    const long t = (long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= nf * n * MM) return;
+    const int kx = (int)(t % MM);
+    const long fy = t / MM;
+    const int y = (int)(fy % n);
+    const long f = fy / n;
+    float re = 0.f, im = 0.f;
+#pragma unroll
+    for (int k = 0; k < K2; k++) {
+        const int ky = k < MM ? k : n - (k - MM + 1);
+        const float2 z = Z[(f * K2 + k) * MM + kx];
+        const float2 w = tw1[(int)(((long)ky * y) & (n - 1))];
+        re += z.x * w.x - z.y * w.y;
+        im += z.x * w.y + z.y * w.x;
+    }
+    V[fy * 16 + kx] = make_float2(re, im);
+}
+
+// out[b][c][p] = act(sum_j Wl[c][j] h[b][j][p] + bl[c] + S[b][c][p]) with S from V by
+// the inverse row DFT (one block per row y of one sample, threads over x)
+template <int W, int MM, typename WT>
+__global__ void __launch_bounds__(256) fno_pointwise_idft(const float *__restrict__ h, const float2 *__restrict__ V,
+                                                          const float2 *__restrict__ tw, const WT *__restrict__ Wl,
+                                                          const WT *__restrict__ bl, float *__restrict__ out, int n,
+                                                          int act)
+{
+    __shared__ float ws[W * W];
+    __shared__ float bs[W];
+    __shared__ float2 vs[W * MM];
+    const int b = blockIdx.y, y = blockIdx.x;
+    const long n2 = (long)n * n;
+    for (int i = threadIdx.x; i < W * W; i += blockDim.x) ws[i] = wld(Wl, i);
+    for (int i = threadIdx.x; i < W; i += blockDim.x) bs[i] = wld(bl, i);
+    const float sc = 1.0f / ((float)n * (float)n);
+    for (int i = threadIdx.x; i < W * MM; i += blockDim.x) {
+        const int o = i / MM, kx = i - o * MM;
+        const float2 v = V[(((long)b * W + o) * n + y) * 16 + kx];
+        const float wk = (kx == 0 ? 1.f : 2.f) * sc;
+        vs[i] = make_float2(wk * v.x, wk * v.y);
+    }
+    __syncthreads();
+    for (int x = threadIdx.x; x < n; x += blockDim.x) {
+        const long p = (long)y * n + x;
+        float in[W];
+#pragma unroll
+        for (int j = 0; j < W; j++) in[j] = h[((long)b * W + j) * n2 + p];
+        float2 e[MM];
+#pragma unroll
+        for (int kx = 0; kx < MM; kx++) e[kx] = tw[(long)kx * n + x];
+        for (int c = 0; c < W; c++) {
+            float acc = bs[c];
+#pragma unroll
+            for (int j = 0; j < W; j++) acc += ws[c * W + j] * in[j];
+#pragma unroll
+            for (int kx = 0; kx < MM; kx++) {
+                const float2 v = vs[c * MM + kx];
+                acc += v.x * e[kx].x - v.y * e[kx].y;
+            }
+            out[((long)b * W + c) * n2 + p] = act ? gelu(acc) : acc;
+        }
+    }
+}
+
 // dY[b][o][m] (compact, K modes a field) = H(w(kx)/n^2 Fd(m)), Fd = R2C of the
 // spectral branch's output gradient
 __global__ void fno_dY(const float2 *__restrict__ Fd, float2 *__restrict__ dY, int B, int W, int M, int n)
@@ -426,6 +689,15 @@ struct fch_fno {
     bool have_fwd;
     __nv_bfloat16 *pbf;   // bfloat16 copy of params (fch_fno_set_bf16), else null
     bool fwd_bf16;        // the last forward pass read the bfloat16 copy
+    // truncated-DFT spectral convolutions (fch_fno_set_bf16(f, 2)): tables for tc_n,
+    // work arrays for (tc_B, tc_n), the device error flag of the tensor-core kernel
+    bool tc;
+    int tc_B, tc_n;
+    __nv_bfloat16 *tc_Bt; // [32][n]
+    float2 *tc_tw;        // [16][n]
+    float2 *tc_X, *tc_V;  // [B W n][16]
+    float2 *tc_Y, *tc_Z;  // [B W][2M-1][M]
+    int *tc_err;
     double *hsum;
     char err[256];
 };
@@ -586,7 +858,9 @@ extern "C" fch_status fch_fno_destroy(fch_fno *f)
     if (!f) return FCH_OK;
     if (f->stream) cudaStreamSynchronize(f->stream);
     free_buffers(f);
-    for (void *b : {(void *)f->params, (void *)f->grads, (void *)f->am, (void *)f->av, (void *)f->pbf})
+    for (void *b : {(void *)f->params, (void *)f->grads, (void *)f->am, (void *)f->av, (void *)f->pbf,
+                    (void *)f->tc_Bt, (void *)f->tc_tw, (void *)f->tc_X, (void *)f->tc_V, (void *)f->tc_Y,
+                    (void *)f->tc_Z, (void *)f->tc_err})
         if (b) cudaFree(b);
     if (f->hsum) cudaFreeHost(f->hsum);
     free(f);
@@ -674,6 +948,93 @@ static fch_status forward_impl(fch_fno *f, int batch, int n, const float *a, flo
     return e == cudaSuccess ? FCH_OK : FCH_ECUDA;
 }
 
+// tables and work arrays of the truncated-DFT forward pass for (B, n)
+static fch_status ensure_tc(fch_fno *f, int B, int n)
+{
+    if (f->tc_B == B && f->tc_n == n) return FCH_OK;
+    for (void *b : {(void *)f->tc_Bt, (void *)f->tc_tw, (void *)f->tc_X, (void *)f->tc_V, (void *)f->tc_Y,
+                    (void *)f->tc_Z})
+        if (b) cudaFree(b);
+    f->tc_Bt = nullptr;
+    f->tc_tw = f->tc_X = f->tc_V = f->tc_Y = f->tc_Z = nullptr;
+    f->tc_B = f->tc_n = 0;
+    const size_t rows = (size_t)B * f->W * n, modes = (size_t)B * f->W * f->K;
+    cudaError_t e = cudaMalloc((void **)&f->tc_Bt, (size_t)32 * n * sizeof(__nv_bfloat16));
+    if (e == cudaSuccess) e = cudaMalloc((void **)&f->tc_tw, (size_t)16 * n * sizeof(float2));
+    if (e == cudaSuccess) e = cudaMalloc((void **)&f->tc_X, rows * 16 * sizeof(float2));
+    if (e == cudaSuccess) e = cudaMalloc((void **)&f->tc_V, rows * 16 * sizeof(float2));
+    if (e == cudaSuccess) e = cudaMalloc((void **)&f->tc_Y, modes * sizeof(float2));
+    if (e == cudaSuccess) e = cudaMalloc((void **)&f->tc_Z, modes * sizeof(float2));
+    if (e == cudaSuccess && !f->tc_err) e = cudaMalloc((void **)&f->tc_err, sizeof(int));
+    if (e == cudaSuccess) e = cudaMemsetAsync(f->tc_err, 0, sizeof(int), f->stream);
+    if (e == cudaSuccess) {
+        fno_dft_tables<<<grid(16L * n, 256), 256, 0, f->stream>>>(f->tc_Bt, f->tc_tw, n);
+        e = cudaGetLastError();
+    }
+    if (e != cudaSuccess) {
+        snprintf(f->err, sizeof(f->err), "fch_fno (truncated DFT): %s", cudaGetErrorString(e));
+        fch_set_thread_error(f->err);
+        return e == cudaErrorMemoryAllocation ? FCH_ENOMEM : FCH_ECUDA;
+    }
+    f->tc_B = B;
+    f->tc_n = n;
+    return FCH_OK;
+}
+
+// the forward pass with the spectral convolutions as truncated DFTs, the row DFT on
+// the tensor cores (BF16 operands, FP32 sums); BF16 weights elsewhere, FP32 sums
+static fch_status forward_tc(fch_fno *f, int batch, int n, const float *a, float *y)
+{
+    typedef __nv_bfloat16 WT;
+    const WT *P = f->pbf;
+    fch_status st = ensure_buffers(f, batch, n);
+    if (st == FCH_OK) st = ensure_tc(f, batch, n);
+    if (st != FCH_OK) return st;
+    const int W = f->W, M = f->M, n2 = n * n;
+    const long pts = (long)batch * n2, R = (long)batch * W * n;
+    const size_t fld = (size_t)batch * W * n2;
+    cudaStream_t s = f->stream;
+    fno_lift<WT><<<grid(pts, 256), 256, 0, s>>>(a, P + offset_of(f, 0, 0), P + offset_of(f, 1, 0), f->h, batch, n2,
+                                                W, f->cin);
+    for (int l = 0; l < f->L; l++) {
+        float *hin = f->h + l * fld, *hout = f->h + (l + 1) * fld;
+        fno_rowdft_tc<<<(unsigned)((R + kTcRows - 1) / kTcRows), 128, 0, s>>>(hin, f->tc_Bt, f->tc_X, (int)R, n,
+                                                                              f->tc_err);
+        fno_coldft<16><<<dim3(batch * W, M), 256, 0, s>>>(f->tc_X, f->tc_tw + n, f->tc_Y, n);
+        fno_mix_modes<WT><<<grid((long)batch * W * f->K, 256), 256, 0, s>>>(f->tc_Y, P + offset_of(f, 4, l),
+                                                                           f->tc_Z, batch, W, M);
+        fno_icoldft<16><<<grid((long)batch * W * n * M, 256), 256, 0, s>>>(f->tc_Z, f->tc_tw + n, f->tc_V,
+                                                                          (long)batch * W, n);
+        const dim3 g((unsigned)n, (unsigned)batch);
+        const int act = l < f->L - 1;
+        if (W == 8)
+            fno_pointwise_idft<8, 16, WT><<<g, 256, 0, s>>>(hin, f->tc_V, f->tc_tw, P + offset_of(f, 2, l),
+                                                            P + offset_of(f, 3, l), hout, n, act);
+        else if (W == 16)
+            fno_pointwise_idft<16, 16, WT><<<g, 256, 0, s>>>(hin, f->tc_V, f->tc_tw, P + offset_of(f, 2, l),
+                                                             P + offset_of(f, 3, l), hout, n, act);
+        else
+            fno_pointwise_idft<32, 16, WT><<<g, 256, 0, s>>>(hin, f->tc_V, f->tc_tw, P + offset_of(f, 2, l),
+                                                             P + offset_of(f, 3, l), hout, n, act);
+    }
+    WDISPATCH_T(W, fno_project, WT, grid(pts, 128), 128, s, f->h + f->L * fld, P + offset_of(f, 5, 0),
+                P + offset_of(f, 6, 0), P + offset_of(f, 7, 0), P + offset_of(f, 8, 0), y, batch, n2, f->W2);
+    cudaError_t e = cudaGetLastError();
+    int herr = 0;
+    // the tensor-core kernel's bounded waits report through a device flag
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&herr, f->tc_err, sizeof(int), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess || herr) {
+        snprintf(f->err, sizeof(f->err), "fch_fno_forward (tensor cores): %s",
+                 e != cudaSuccess ? cudaGetErrorString(e) : "an mbarrier wait ran out");
+        fch_set_thread_error(f->err);
+        return FCH_ECUDA;
+    }
+    f->a = a;
+    f->have_fwd = true;
+    return FCH_OK;
+}
+
 // refresh the bfloat16 copy of the parameters (round to nearest even)
 static fch_status refresh_bf16(fch_fno *f)
 {
@@ -684,14 +1045,16 @@ static fch_status refresh_bf16(fch_fno *f)
 
 extern "C" fch_status fch_fno_set_bf16(fch_fno *f, int on)
 {
-    if (!f) return FCH_EINVAL;
+    if (!f || on < 0 || on > 2) return FCH_EINVAL;
     if (on && !f->pbf) {
         if (cudaMalloc((void **)&f->pbf, f->np * sizeof(__nv_bfloat16)) != cudaSuccess) {
             f->pbf = nullptr;
             return FCH_ENOMEM;
         }
+        f->tc = on == 2;
         return refresh_bf16(f);
     }
+    f->tc = on == 2;
     if (!on && f->pbf) {
         cudaStreamSynchronize(f->stream);
         cudaFree(f->pbf);
@@ -707,6 +1070,13 @@ extern "C" fch_status fch_fno_forward(fch_fno *f, int batch, int n, const float 
         return FCH_EINVAL;
     }
     f->fwd_bf16 = f->pbf != nullptr;
+    if (f->tc && f->pbf) {
+        if (f->M != 16 || n % 64 != 0) {
+            fch_set_thread_error("fch_fno_forward: the truncated-DFT pass needs modes = 16 and n a multiple of 64");
+            return FCH_EINVAL;
+        }
+        return forward_tc(f, batch, n, a, y);
+    }
     return f->pbf ? forward_impl(f, batch, n, a, y, (const __nv_bfloat16 *)f->pbf)
                   : forward_impl(f, batch, n, a, y, (const float *)f->params);
 }
@@ -781,4 +1151,33 @@ extern "C" fch_status fch_fno_adam(fch_fno *f, float lr, float beta1, float beta
                                                             beta2, eps, c1, c2);
     if (cudaGetLastError() != cudaSuccess) return FCH_ECUDA;
     return refresh_bf16(f);
+}
+
+// test hook (not part of the C ABI of fch.h): the tensor-core row DFT alone,
+// X[r][kx] for kx < 16 of R rows of n floats (device arrays); returns 0 or a status
+extern "C" int fch_debug_rowdft_tc(const float *h, float *X, int R, int n, void *stream)
+{
+    if (!h || !X || R < 1 || n < 64 || n % 64 != 0 || n > 2048) return FCH_EINVAL;
+    cudaStream_t s = (cudaStream_t)stream;
+    __nv_bfloat16 *Bt = nullptr;
+    float2 *tw = nullptr;
+    int *err = nullptr, herr = 0;
+    cudaError_t e = cudaMalloc((void **)&Bt, (size_t)32 * n * sizeof(__nv_bfloat16));
+    if (e == cudaSuccess) e = cudaMalloc((void **)&tw, (size_t)16 * n * sizeof(float2));
+    if (e == cudaSuccess) e = cudaMalloc((void **)&err, sizeof(int));
+    if (e == cudaSuccess) e = cudaMemsetAsync(err, 0, sizeof(int), s);
+    if (e == cudaSuccess) {
+        fno_dft_tables<<<grid(16L * n, 256), 256, 0, s>>>(Bt, tw, n);
+        fno_rowdft_tc<<<(unsigned)((R + kTcRows - 1) / kTcRows), 128, 0, s>>>(h, Bt, (float2 *)X, R, n, err);
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&herr, err, sizeof(int), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    for (void *b : {(void *)Bt, (void *)tw, (void *)err})
+        if (b) cudaFree(b);
+    if (e != cudaSuccess) {
+        fch_set_thread_error(cudaGetErrorString(e));
+        return FCH_ECUDA;
+    }
+    return herr ? FCH_ECUDA : FCH_OK;
 }

@@ -590,6 +590,9 @@ class FNO:
     def adam(self, lr=1e-3, beta1=0.9, beta2=0.999, eps=1e-8):
         _check(lib().fch_fno_adam(self._h, lr, beta1, beta2, eps), "fch_fno_adam")
 
-    def set_bf16(self, on: bool):
-        """forward passes on a bfloat16 copy of the weights (FP32 sums), or back to FP32"""
-        _check(lib().fch_fno_set_bf16(self._h, int(bool(on))), "fch_fno_set_bf16")
+    def set_bf16(self, on):
+        """forward passes on a bfloat16 copy of the weights (FP32 sums), or back to FP32;
+        on = 2: also the spectral convolutions as truncated DFTs, the one along x on the
+        tensor cores with bfloat16 operands (fch_fno_set_bf16)"""
+        mode = 2 if on == 2 else int(bool(on))
+        _check(lib().fch_fno_set_bf16(self._h, mode), "fch_fno_set_bf16")

