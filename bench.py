@@ -1225,6 +1225,18 @@ def fno_bench(args):
     torch.cuda.synchronize()
     out["fno_forward_ms_1024_bf16_weights"] = (time.perf_counter() - t0) / 10 * 1e3
     out["eval_128_bf16_weights"] = evaluate(128, I.circle_bilayer(128, radius=2.1, noise=1e-3, seed=21), 30)
+    # the spectral convolutions as truncated DFTs, the x DFT on the tensor cores
+    net.set_bf16(2)
+    for _ in range(3):
+        net.forward(a, y)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(10):
+        net.forward(a, y)
+    torch.cuda.synchronize()
+    out["fno_forward_ms_1024_truncated_dft_tensor_cores"] = (time.perf_counter() - t0) / 10 * 1e3
+    out["eval_128_truncated_dft"] = evaluate(128, I.circle_bilayer(128, radius=2.1, noise=1e-3, seed=21), 30)
+    out["eval_1024_truncated_dft"] = evaluate(1024, I.circle_bilayer(1024, radius=2.1, noise=1e-3, seed=21), 8)
     net.set_bf16(False)
     return out
 

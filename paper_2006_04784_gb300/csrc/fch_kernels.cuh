@@ -522,13 +522,23 @@ template <int THREADS, int LOGN> constexpr int pass_min_blocks()
 {
     return (LOGN > 0 && LOGN <= 10 && THREADS == 256) ? 4 : 1;
 }
+// The standalone transforms' column passes of 512 threads (single precision, N = 1024,
+// two column pairs a block) are built for three resident blocks an SM (at most 42
+// registers a thread): their launches carry many field pairs, so occupancy, not the
+// wave count, is what they need.
+template <int THREADS, int LOGN, int MODE> constexpr int col_min_blocks()
+{
+    return (THREADS == 512 && LOGN == 10 && (MODE == CM_FWD_STORE || MODE == CM_INV_LOAD))
+               ? 3
+               : pass_min_blocks<THREADS, LOGN>();
+}
 
 // LOGN > 0: the grid size is a compile-time constant (N = 2^LOGN >= 512), so the
 // index arithmetic of the transforms folds into immediates; LOGN = 0 reads N and P
 // from the parameters.
 template <typename T, int MODE, int LOGN>
 __global__ void __launch_bounds__(LOGN ? ((spec_pairs<T, LOGN>() << LOGN) >> 2) : 1024,
-                                  pass_min_blocks<LOGN ? ((spec_pairs<T, LOGN>() << LOGN) >> 2) : 1024, LOGN>())
+                                  col_min_blocks<LOGN ? ((spec_pairs<T, LOGN>() << LOGN) >> 2) : 1024, LOGN, MODE>())
 col_pass(const fch_kparams kp)
 {
     typedef typename CT<T>::t C;

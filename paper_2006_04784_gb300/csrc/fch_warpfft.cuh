@@ -114,7 +114,10 @@ __device__ __forceinline__ float2 pointwise(const fch_kparams &kp, const fch_con
 
 // row pass, N = 1024, single precision: one warp (= one block) per row
 template <int MODE>
-__global__ void __launch_bounds__(32) row_pass_w(const fch_kparams kp)
+// (the standalone transforms' row passes, launched over many field pairs, are built
+// for sixteen resident warps an SM: at most 128 registers a thread)
+__global__ void __launch_bounds__(32, (MODE == RM_R2C_LOAD || MODE == RM_C2R_STORE) ? 16 : 1)
+row_pass_w(const fch_kparams kp)
 {
     typedef float2 C;
     pdl_begin();
