@@ -455,6 +455,45 @@ def fft_only(args):
                           iters=args.fft_iters)
 
 
+def fno_forward_times(args, sizes=(128, 256, 512, 1024), reps=10):
+    """the forward pass of the configured network (32 channels, 4 layers, 16 modes, 64
+    projection channels; seeded weights) per grid size, batch 1, in each mode: FP32
+    weights and full transforms (0), bfloat16 weights (1), bfloat16 weights and
+    truncated-DFT spectral convolutions with the x DFT on the tensor cores (2); times
+    from CUDA events around `reps` passes after three untimed ones"""
+    import torch
+
+    from paper_2006_04784_gb300 import build as B
+    B.build()
+    from paper_2006_04784_gb300 import fch
+    from paper_2006_04784_gb300 import fno_train as T
+
+    dev = torch.device("cuda", 0)
+    net = fch.FNO(32, 4, 16, 64)
+    net.set_params(T.init_params(net, seed=0))
+    out = {"network": "32 channels, 4 layers, 16 modes, 64 projection channels", "unit": "ms per forward pass",
+           "modes": {"0": "fp32", "1": "bf16 weights", "2": "bf16 weights, truncated DFTs, tensor cores"}}
+    for n in sizes:
+        a = torch.randn((1, 2, n, n), device=dev, generator=torch.Generator(device=dev).manual_seed(n))
+        y = torch.empty((1, n, n), device=dev)
+        row = {}
+        for mode in (0, 1, 2):
+            net.set_bf16(mode)
+            for _ in range(3):
+                net.forward(a, y)
+            ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+            torch.cuda.synchronize()
+            ev[0].record()
+            for _ in range(reps):
+                net.forward(a, y)
+            ev[1].record()
+            torch.cuda.synchronize()
+            row[str(mode)] = ev[0].elapsed_time(ev[1]) / reps
+        out[str(n)] = row
+    net.set_bf16(0)
+    return out
+
+
 def fixed_step_throughput(fch, I, dev, n=N_GRID, steps=200, dt=1e-6):
     """Fixed-dt IMEX-BDF2 steps at n^2 (fch_run_fixed: a captured step replayed),
     per precision, timed with CUDA events on the context's stream (the step's
@@ -1430,6 +1469,8 @@ def main():
     ap.add_argument("--fno-iters", type=int, default=1500)
     ap.add_argument("--fno-lr", type=float, default=1e-3)
     ap.add_argument("--fno-t-adaptive", type=float, default=2e-2)
+    ap.add_argument("--fno-forward", action="store_true",
+                    help="only the FNO forward pass time per grid and mode (FP32, BF16 weights, truncated DFTs)")
     ap.add_argument("--fft-only", action="store_true",
                     help="only the standalone transform throughput (fch_fft_r2c / c2r against cuFFT)")
     ap.add_argument("--fft-batch", type=int, default=32)
@@ -1454,6 +1495,8 @@ def main():
         out = error_budget(args)
     elif args.fft_only:
         out = fft_only(args)
+    elif args.fno_forward:
+        out = fno_forward_times(args)
     elif args.ensemble:
         out = ensemble_bench(args)
     elif args.fno:
