@@ -121,52 +121,55 @@ def spectral_conv(h, Rc, cfg: Config):
 
 def spectral_conv_dft(h, Rc, cfg: Config, bf16_operands=False):
     """S(h) of spectral_conv written as truncated DFTs over the retained modes, in the
-    order the truncated-DFT forward pass takes them: along x for kx < M, along y for
-    the 2M - 1 retained ky, the mode mixing, back along y, and back along x as the real
+    order the tensor-core forward pass takes them: along x for kx < M, along y for the
+    2M - 1 retained ky, the mode mixing, back along y, and back along x as the real
     part of the sum over kx < M with weight 1 at kx = 0 and 2 elsewhere, over n^2 (the
-    C2R of the retained half spectrum through H). With bf16_operands the input h and
-    the cos / -sin table of the x transform are rounded to bfloat16 first (the tensor-
-    core GEMM's operands); every sum is exact here."""
+    C2R of the retained half spectrum through H). With bf16_operands the operands of
+    the two x DFTs are rounded to bfloat16 first, as the tensor cores take them: the
+    input h and the cos / -sin table forward; the cos / sin table and w(kx)/n^2 V
+    (real part, and minus the imaginary part) back. Every sum is exact here."""
     B, W, n, _ = h.shape
     M, K2 = cfg.M, 2 * cfg.M - 1
+    rnd = bf16_round if bf16_operands else (lambda v: v)
     xs = np.arange(n)
     kxs = np.arange(M)
     ang = 2.0 * np.pi * ((kxs[:, None] * xs[None, :]) % n) / n
-    cx, sx = np.cos(ang), -np.sin(ang)
-    hh = h
-    if bf16_operands:
-        hh, cx, sx = bf16_round(h), bf16_round(cx), bf16_round(sx)
-    X = np.einsum("bwyt,kt->bwyk", hh, cx) + 1j * np.einsum("bwyt,kt->bwyk", hh, sx)
+    cx, sx = np.cos(ang), np.sin(ang)
+    hh = rnd(h)
+    X = np.einsum("bwyt,kt->bwyk", hh, rnd(cx)) + 1j * np.einsum("bwyt,kt->bwyk", hh, rnd(-sx))
     kys = np.array([q if q < M else n - (q - M + 1) for q in range(K2)])
     ey = np.exp(-2j * np.pi * np.outer(kys, xs) / n)          # [K2, n(y)]
     Y = np.einsum("bwyk,qy->bwqk", X, ey)                     # [B, W, kyi, kx]
     R4 = Rc.reshape(M, K2, W, W)                              # m = kx (2M - 1) + kyi
     Z = np.einsum("kqoi,biqk->boqk", R4, Y)
     V = np.einsum("boqk,qy->boyk", Z, np.conj(ey))            # [B, W, y, kx]
-    w = np.where(kxs == 0, 1.0, 2.0)
-    ex = np.exp(2j * np.pi * np.outer(kxs, xs) / n)           # [M, n(x)]
-    return np.real(np.einsum("boyk,kt->boyt", V * w, ex)) / (n * n)
+    w = np.where(kxs == 0, 1.0, 2.0) / (n * n)
+    return (np.einsum("boyk,kt->boyt", rnd(w * V.real), rnd(cx))
+            + np.einsum("boyk,kt->boyt", rnd(-w * V.imag), rnd(sx)))
 
 
-def forward(params, a, cfg: Config, keep=False, dft_bf16=False):
+def forward(params, a, cfg: Config, keep=False, tc=False):
     """y [B, n, n] for inputs a [B, cin, n, n]; with keep, also the activations the
-    backward pass needs. dft_bf16: the spectral convolutions by spectral_conv_dft with
-    bfloat16 operands of the x transform (the library's tensor-core forward pass)."""
+    backward pass needs. tc: the library's tensor-core forward pass, whose contractions
+    take bfloat16 operands (the weights are rounded by the caller): the spectral
+    convolutions by spectral_conv_dft with bf16_operands, and the layer input rounded to
+    bfloat16 where the channel mixing W h and the projection Q1 h read it."""
     p = cfg.unpack(params)
+    rnd = bf16_round if tc else (lambda v: v)
     h = np.einsum("ci,bixy->bcxy", p["P"], a) + p["bP"][None, :, None, None]
     hs, zs, Xs = [h], [], []
     for l in range(cfg.L):
         Rc = p[f"R{l}"][..., 0] + 1j * p[f"R{l}"][..., 1]
-        if dft_bf16:
+        if tc:
             s, X = spectral_conv_dft(h, Rc, cfg, bf16_operands=True), None
         else:
             s, X = spectral_conv(h, Rc, cfg)
-        z = np.einsum("cj,bjxy->bcxy", p[f"W{l}"], h) + p[f"b{l}"][None, :, None, None] + s
+        z = np.einsum("cj,bjxy->bcxy", p[f"W{l}"], rnd(h)) + p[f"b{l}"][None, :, None, None] + s
         h = gelu(z) if l < cfg.L - 1 else z
         hs.append(h)
         zs.append(z)
         Xs.append(X)
-    zq = np.einsum("dc,bcxy->bdxy", p["Q1"], h) + p["bQ1"][None, :, None, None]
+    zq = np.einsum("dc,bcxy->bdxy", p["Q1"], rnd(h)) + p["bQ1"][None, :, None, None]
     q = gelu(zq)
     y = np.einsum("d,bdxy->bxy", p["Q2"], q) + p["bQ2"][0]
     if keep:

@@ -500,6 +500,206 @@ __global__ void __launch_bounds__(256) fno_pointwise_idft(const float *__restric
     }
 }
 
+// 8 floats rounded to bfloat16 (nearest even), packed as one 16-byte core row
+__device__ __forceinline__ uint4 pack8_bf16(const float *f)
+{
+    uint32_t w[4];
+#pragma unroll
+    for (int i = 0; i < 4; i++) {
+        __nv_bfloat162 b = __floats2bfloat162_rn(f[2 * i], f[2 * i + 1]);
+        w[i] = *reinterpret_cast<uint32_t *>(&b);
+    }
+    return make_uint4(w[0], w[1], w[2], w[3]);
+}
+// row r, K-core kc of a core-layout tile (see fch_tc.cuh)
+__device__ __forceinline__ void core_store(unsigned char *tile, int r, int kc, uint4 v)
+{
+    *reinterpret_cast<uint4 *>(tile + (r >> 3) * kTcSBO + kc * kTcLBO + (r & 7) * 16) = v;
+}
+
+// set up (tensor memory, mbarrier) and tear down of the one-tile tensor-core kernels
+struct TcTile {
+    uint32_t tmem;
+};
+
+// The pointwise layer on the tensor cores: for the 128 points x of one row segment
+// (thread t, TMEM lane t), z[o] = sum_j W[o][j] h[j] + b[o] + S[o] with S the inverse
+// x DFT of V, as one MMA chain with K = W + 32:
+//   A[t][:] = (bf16 h[b][j][y][x], j < W | bf16 cos(2 pi kx x/n), kx < 16 | bf16 sin(...))
+//   B[o][:] = (W[o][j] | bf16(w(kx)/n^2 Re V[o][y][kx]) | bf16(-w(kx)/n^2 Im V[o][y][kx]))
+// D = A B^T (128 x W, FP32 in tensor memory); out = act(D + b).
+template <int W>
+__global__ void __launch_bounds__(128) fno_pw_tc(const float *__restrict__ h, const float2 *__restrict__ V,
+                                                 const float2 *__restrict__ tw, const __nv_bfloat16 *__restrict__ Wl,
+                                                 const __nv_bfloat16 *__restrict__ bl, float *__restrict__ out,
+                                                 int n, int act, int *err)
+{
+    constexpr int K = W + 32, NKC = K / 8;
+    __shared__ __align__(128) unsigned char sA[16 * kTcSBO];
+    __shared__ __align__(128) unsigned char sB[(W / 8) * kTcSBO];
+    __shared__ float bs[W];
+    __shared__ __align__(8) uint64_t bar;
+    __shared__ uint32_t tslot;
+    const int tid = threadIdx.x, warp = tid >> 5;
+    const int segs = n >> 7, seg = blockIdx.x % segs, y = blockIdx.x / segs, b = blockIdx.y;
+    const int x = seg * 128 + tid;
+    const long n2 = (long)n * n, p = (long)y * n + x;
+    if (warp == 0) {
+        fch::tc::tmem_alloc(&tslot, 32);
+        fch::tc::tmem_relinquish();
+    }
+    if (tid == 0) {
+        fch::tc::mbar_init(&bar, 1);
+        fch::tc::mbar_init_fence();
+    }
+    float f[8];
+#pragma unroll
+    for (int kc = 0; kc < W / 8; kc++) {
+#pragma unroll
+        for (int e = 0; e < 8; e++) f[e] = h[((long)b * W + kc * 8 + e) * n2 + p];
+        core_store(sA, tid, kc, pack8_bf16(f));
+    }
+#pragma unroll
+    for (int part = 0; part < 2; part++)
+#pragma unroll
+        for (int kc = 0; kc < 2; kc++) {
+#pragma unroll
+            for (int e = 0; e < 8; e++) {
+                const float2 t = tw[(long)(kc * 8 + e) * n + x];
+                f[e] = part ? t.y : t.x;
+            }
+            core_store(sA, tid, W / 8 + 2 * part + kc, pack8_bf16(f));
+        }
+    const float sc = 1.0f / ((float)n * (float)n);
+    for (int i = tid; i < W * NKC; i += 128) {
+        const int o = i / NKC, kc = i - o * NKC;
+        uint4 v;
+        if (kc < W / 8) {
+            v = *reinterpret_cast<const uint4 *>(Wl + o * W + kc * 8); // already bf16
+        } else {
+            const int part = (kc - W / 8) >> 1, k0 = ((kc - W / 8) & 1) * 8;
+            const float2 *Vr = V + (((long)b * W + o) * n + y) * 16;
+#pragma unroll
+            for (int e = 0; e < 8; e++) {
+                const int k = k0 + e;
+                const float wk = (k == 0 ? 1.f : 2.f) * sc;
+                const float2 vv = Vr[k];
+                f[e] = part ? -wk * vv.y : wk * vv.x;
+            }
+            v = pack8_bf16(f);
+        }
+        core_store(sB, o, kc, v);
+    }
+    for (int i = tid; i < W; i += 128) bs[i] = __bfloat162float(bl[i]);
+    fch::tc::fence_async_smem();
+    fch::tc::fence_before_sync();
+    __syncthreads();
+    fch::tc::fence_after_sync();
+    const uint32_t tmem = tslot;
+    if (tid == 0) {
+        constexpr uint32_t idesc = fch::tc::idesc_bf16_f32(128, W);
+        const uint32_t sa = fch::tc::smem_u32(sA), sb = fch::tc::smem_u32(sB);
+#pragma unroll
+        for (int k = 0; k < K / 16; k++)
+            fch::tc::mma_bf16(tmem, fch::tc::smem_desc(sa + 2 * k * kTcLBO, kTcLBO, kTcSBO),
+                              fch::tc::smem_desc(sb + 2 * k * kTcLBO, kTcLBO, kTcSBO), idesc, k != 0);
+        fch::tc::mma_commit(&bar);
+    }
+    const bool ok = __syncthreads_and(fch::tc::mbar_wait(&bar, 0, kTcBound));
+    fch::tc::fence_after_sync();
+    if (ok) {
+        float v[32];
+        fch::tc::tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16), v);
+#pragma unroll
+        for (int o = 0; o < W; o++) {
+            const float z = v[o] + bs[o];
+            out[((long)b * W + o) * n2 + p] = act ? gelu(z) : z;
+        }
+    } else if (tid == 0) {
+        atomicExch(err, 1);
+    }
+    fch::tc::fence_before_sync();
+    __syncthreads();
+    if (warp == 0) fch::tc::tmem_dealloc(tmem, 32);
+}
+
+// The projection on the tensor cores: for 128 points (thread t, TMEM lane t),
+// zq = Q1 bf16(h) + bQ1 as D = A B^T with A[t][:] = bf16 h[b][c][p] (K = W) and
+// B = Q1 (W2 x W), then y = bQ2 + sum_d Q2[d] GELU(zq[d]) in the epilogue.
+template <int W>
+__global__ void __launch_bounds__(128) fno_proj_tc(const float *__restrict__ h, const __nv_bfloat16 *__restrict__ Q1,
+                                                   const __nv_bfloat16 *__restrict__ bQ1,
+                                                   const __nv_bfloat16 *__restrict__ Q2,
+                                                   const __nv_bfloat16 *__restrict__ bQ2, float *__restrict__ y,
+                                                   long pts, int n2, int W2, int *err)
+{
+    __shared__ __align__(128) unsigned char sA[16 * kTcSBO];
+    __shared__ __align__(128) unsigned char sB[(kMaxW2 / 8) * kTcSBO];
+    __shared__ float bq[kMaxW2], q2[kMaxW2];
+    __shared__ __align__(8) uint64_t bar;
+    __shared__ uint32_t tslot;
+    const int tid = threadIdx.x, warp = tid >> 5;
+    const long g = (long)blockIdx.x * 128 + tid;
+    const bool live = g < pts;
+    const long b = live ? g / n2 : 0, p = live ? g - b * n2 : 0;
+    const uint32_t ncols = W2 <= 32 ? 32 : (W2 <= 64 ? 64 : 128);
+    if (warp == 0) {
+        fch::tc::tmem_alloc(&tslot, ncols);
+        fch::tc::tmem_relinquish();
+    }
+    if (tid == 0) {
+        fch::tc::mbar_init(&bar, 1);
+        fch::tc::mbar_init_fence();
+    }
+    float f[8];
+#pragma unroll
+    for (int kc = 0; kc < W / 8; kc++) {
+#pragma unroll
+        for (int e = 0; e < 8; e++) f[e] = live ? h[(b * W + kc * 8 + e) * n2 + p] : 0.f;
+        core_store(sA, tid, kc, pack8_bf16(f));
+    }
+    for (int i = tid; i < W2 * (W / 8); i += 128) {
+        const int d = i / (W / 8), kc = i - d * (W / 8);
+        core_store(sB, d, kc, *reinterpret_cast<const uint4 *>(Q1 + d * W + kc * 8));
+    }
+    for (int i = tid; i < W2; i += 128) {
+        bq[i] = __bfloat162float(bQ1[i]);
+        q2[i] = __bfloat162float(Q2[i]);
+    }
+    fch::tc::fence_async_smem();
+    fch::tc::fence_before_sync();
+    __syncthreads();
+    fch::tc::fence_after_sync();
+    const uint32_t tmem = tslot;
+    if (tid == 0) {
+        const uint32_t idesc = fch::tc::idesc_bf16_f32(128, W2);
+        const uint32_t sa = fch::tc::smem_u32(sA), sb = fch::tc::smem_u32(sB);
+#pragma unroll
+        for (int k = 0; k < W / 16; k++)
+            fch::tc::mma_bf16(tmem, fch::tc::smem_desc(sa + 2 * k * kTcLBO, kTcLBO, kTcSBO),
+                              fch::tc::smem_desc(sb + 2 * k * kTcLBO, kTcLBO, kTcSBO), idesc, k != 0);
+        fch::tc::mma_commit(&bar);
+    }
+    const bool ok = __syncthreads_and(fch::tc::mbar_wait(&bar, 0, kTcBound));
+    fch::tc::fence_after_sync();
+    if (ok) {
+        float acc = __bfloat162float(bQ2[0]);
+        for (int c0 = 0; c0 < W2; c0 += 32) {
+            float v[32];
+            fch::tc::tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0, v);
+#pragma unroll
+            for (int d = 0; d < 32; d++)
+                if (c0 + d < W2) acc += q2[c0 + d] * gelu(v[d] + bq[c0 + d]);
+        }
+        if (live) y[g] = acc;
+    } else if (tid == 0) {
+        atomicExch(err, 1);
+    }
+    fch::tc::fence_before_sync();
+    __syncthreads();
+    if (warp == 0) fch::tc::tmem_dealloc(tmem, ncols);
+}
+
 // dY[b][o][m] (compact, K modes a field) = H(w(kx)/n^2 Fd(m)), Fd = R2C of the
 // spectral branch's output gradient
 __global__ void fno_dY(const float2 *__restrict__ Fd, float2 *__restrict__ dY, int B, int W, int M, int n)
@@ -1005,20 +1205,25 @@ static fch_status forward_tc(fch_fno *f, int batch, int n, const float *a, float
                                                                            f->tc_Z, batch, W, M);
         fno_icoldft<16><<<grid((long)batch * W * n * M, 256), 256, 0, s>>>(f->tc_Z, f->tc_tw + n, f->tc_V,
                                                                           (long)batch * W, n);
-        const dim3 g((unsigned)n, (unsigned)batch);
+        // the channel mixing and the inverse x DFT: one MMA chain per 128 points
+        const dim3 g((unsigned)(n / 128 * n), (unsigned)batch);
         const int act = l < f->L - 1;
-        if (W == 8)
-            fno_pointwise_idft<8, 16, WT><<<g, 256, 0, s>>>(hin, f->tc_V, f->tc_tw, P + offset_of(f, 2, l),
-                                                            P + offset_of(f, 3, l), hout, n, act);
-        else if (W == 16)
-            fno_pointwise_idft<16, 16, WT><<<g, 256, 0, s>>>(hin, f->tc_V, f->tc_tw, P + offset_of(f, 2, l),
-                                                             P + offset_of(f, 3, l), hout, n, act);
+        if (W == 16)
+            fno_pw_tc<16><<<g, 128, 0, s>>>(hin, f->tc_V, f->tc_tw, P + offset_of(f, 2, l), P + offset_of(f, 3, l),
+                                           hout, n, act, f->tc_err);
         else
-            fno_pointwise_idft<32, 16, WT><<<g, 256, 0, s>>>(hin, f->tc_V, f->tc_tw, P + offset_of(f, 2, l),
-                                                             P + offset_of(f, 3, l), hout, n, act);
+            fno_pw_tc<32><<<g, 128, 0, s>>>(hin, f->tc_V, f->tc_tw, P + offset_of(f, 2, l), P + offset_of(f, 3, l),
+                                           hout, n, act, f->tc_err);
     }
-    WDISPATCH_T(W, fno_project, WT, grid(pts, 128), 128, s, f->h + f->L * fld, P + offset_of(f, 5, 0),
-                P + offset_of(f, 6, 0), P + offset_of(f, 7, 0), P + offset_of(f, 8, 0), y, batch, n2, f->W2);
+    const unsigned gp = (unsigned)((pts + 127) / 128);
+    if (W == 16)
+        fno_proj_tc<16><<<gp, 128, 0, s>>>(f->h + f->L * fld, P + offset_of(f, 5, 0), P + offset_of(f, 6, 0),
+                                           P + offset_of(f, 7, 0), P + offset_of(f, 8, 0), y, pts, n2, f->W2,
+                                           f->tc_err);
+    else
+        fno_proj_tc<32><<<gp, 128, 0, s>>>(f->h + f->L * fld, P + offset_of(f, 5, 0), P + offset_of(f, 6, 0),
+                                           P + offset_of(f, 7, 0), P + offset_of(f, 8, 0), y, pts, n2, f->W2,
+                                           f->tc_err);
     cudaError_t e = cudaGetLastError();
     int herr = 0;
     // the tensor-core kernel's bounded waits report through a device flag
@@ -1071,8 +1276,9 @@ extern "C" fch_status fch_fno_forward(fch_fno *f, int batch, int n, const float 
     }
     f->fwd_bf16 = f->pbf != nullptr;
     if (f->tc && f->pbf) {
-        if (f->M != 16 || n % 64 != 0) {
-            fch_set_thread_error("fch_fno_forward: the truncated-DFT pass needs modes = 16 and n a multiple of 64");
+        if (f->M != 16 || n % 128 != 0 || (f->W != 16 && f->W != 32) || f->W2 % 16 != 0) {
+            fch_set_thread_error("fch_fno_forward: the tensor-core pass needs modes = 16, width 16 or 32, "
+                                 "proj a multiple of 16 and n a multiple of 128");
             return FCH_EINVAL;
         }
         return forward_tc(f, batch, n, a, y);
