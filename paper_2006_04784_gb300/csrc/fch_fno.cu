@@ -269,71 +269,94 @@ __global__ void fno_dft_tables(__nv_bfloat16 *__restrict__ Bt, float2 *__restric
 }
 
 // X[r][kx] = (D[r][kx], D[r][16 + kx]) with D = bf16(h) Bt^T over K = n: one CTA of 128
-// threads per 128 rows, K in chunks of 64 staged in two shared-memory buffers
-// (core-matrix layout, see fch_tc.cuh); thread 0 issues four K = 16 MMAs per chunk
-// into a 128 x 32 FP32 accumulator in tensor memory and commits them to the buffer's
-// mbarrier, which the threads wait on before they refill that buffer. A wait that
-// runs out of polls sets *err and the CTA stops issuing, waits (bounded) for what it
+// threads per 128 rows, K in chunks of 64. The FP32 rows of a chunk arrive by bulk copies
+// (the TMA engine, 256 bytes a row, two chunks ahead, completion counted in bytes on the
+// stage's `full` mbarrier); the threads round them to bfloat16 into the core-matrix
+// layout of the stage's A tile (see fch_tc.cuh) and copy the table's chunk; thread 0
+// issues four K = 16 MMAs into a 128 x 32 FP32 accumulator in tensor memory and commits
+// them to the stage's `mma` mbarrier, which guards the stage's tiles. A wait that runs
+// out of polls sets *err; the CTA then stops, waits (bounded) for the copies and MMAs it
 // issued, frees its tensor memory and returns.
+constexpr int kRawBytes = kTcRows * kTcKc * 4;                       // one chunk of FP32 rows
+constexpr int kAtBytes = (kTcRows / 8) * kTcSBO, kBtBytes = (kTcNB / 8) * kTcSBO;
+constexpr int kRowdftSmem = 2 * kRawBytes + 2 * kAtBytes + 2 * kBtBytes;  // 111,616 bytes
+
 __global__ void __launch_bounds__(128) fno_rowdft_tc(const float *__restrict__ h, const __nv_bfloat16 *__restrict__ Bt,
                                                      float2 *__restrict__ X, int R, int n, int *err)
 {
-    constexpr int A_BYTES = (kTcRows / 8) * kTcSBO, B_BYTES = (kTcNB / 8) * kTcSBO;
-    __shared__ __align__(128) unsigned char sA[2][A_BYTES];
-    __shared__ __align__(128) unsigned char sB[2][B_BYTES];
-    __shared__ __align__(8) uint64_t bar[2];
+    extern __shared__ __align__(128) unsigned char dsm[];
+    unsigned char *raw = dsm, *sA = dsm + 2 * kRawBytes, *sB = sA + 2 * kAtBytes;
+    __shared__ __align__(8) uint64_t full[2], mmab[2];
     __shared__ uint32_t tslot;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const long row0 = (long)blockIdx.x * kTcRows;
+    const int rows = (int)(R - row0 < kTcRows ? R - row0 : kTcRows);
+    const int nch = n / kTcKc;
     if (warp == 0) {
         fch::tc::tmem_alloc(&tslot, 32);
         fch::tc::tmem_relinquish();
     }
     if (tid == 0) {
-        fch::tc::mbar_init(&bar[0], 1);
-        fch::tc::mbar_init(&bar[1], 1);
+        for (int i = 0; i < 2; i++) {
+            fch::tc::mbar_init(&full[i], 1);
+            fch::tc::mbar_init(&mmab[i], 1);
+        }
         fch::tc::mbar_init_fence();
     }
     fch::tc::fence_before_sync();
     __syncthreads();
     fch::tc::fence_after_sync();
     const uint32_t tmem = tslot;
+    // warp 0 fetches chunk c into stage c & 1: lane 0 announces the bytes, then the 32
+    // lanes issue the rows' copies
+    auto fetch = [&](int c) {
+        uint64_t *bar = &full[c & 1];
+        unsigned char *dst = raw + (c & 1) * kRawBytes;
+        if (lane == 0) fch::tc::mbar_expect_tx(bar, (uint32_t)rows * (kTcKc * 4));
+        __syncwarp();
+        for (int r = lane; r < rows; r += 32)
+            fch::tc::bulk_g2s(dst + r * (kTcKc * 4), h + (row0 + r) * n + (long)c * kTcKc, kTcKc * 4, bar);
+    };
+    if (warp == 0)
+        for (int c = 0; c < 2 && c < nch; c++) fetch(c);
+    // rows beyond R are zero in every stage's A tile (their raw rows are never written)
     constexpr uint32_t idesc = fch::tc::idesc_bf16_f32(kTcRows, kTcNB);
-    const int nch = n / kTcKc;
     bool ok = true;
-    int issued = 0; // chunks whose MMAs thread 0 committed
+    int fetched = nch < 2 ? nch : 2, issued = 0;
     for (int c = 0; c < nch; c++) {
-        const int b = c & 1;
-        if (c >= 2) ok = fch::tc::mbar_wait(&bar[b], (uint32_t)(((c >> 1) - 1) & 1), kTcBound);
+        const int st = c & 1;
+        ok = fch::tc::mbar_wait(&full[st], (uint32_t)((c >> 1) & 1), kTcBound);
+        if (ok && c >= 2) ok = fch::tc::mbar_wait(&mmab[st], (uint32_t)(((c >> 1) - 1) & 1), kTcBound);
         if (!__syncthreads_and(ok)) break;
-        // A: 128 rows x 8 K-cores of 16 bytes (8 bf16); thread -> (row, core) with a
-        // warp covering 4 rows x 8 cores, so each row's 64 floats are read contiguously
-        unsigned char *a = sA[b];
-#pragma unroll
-        for (int i = 0; i < 8; i++) {
-            const int j = tid + 128 * i, r = j >> 3, kc = j & 7;
-            const long gr = row0 + r;
-            uint4 v = make_uint4(0, 0, 0, 0);
-            if (gr < R) {
-                const float4 *src = reinterpret_cast<const float4 *>(h + gr * n + (long)c * kTcKc + kc * 8);
-                const float4 p = __ldg(src), q = __ldg(src + 1);
-                __nv_bfloat162 b0 = __floats2bfloat162_rn(p.x, p.y), b1 = __floats2bfloat162_rn(p.z, p.w);
-                __nv_bfloat162 b2 = __floats2bfloat162_rn(q.x, q.y), b3 = __floats2bfloat162_rn(q.z, q.w);
-                v = make_uint4(*reinterpret_cast<uint32_t *>(&b0), *reinterpret_cast<uint32_t *>(&b1),
-                               *reinterpret_cast<uint32_t *>(&b2), *reinterpret_cast<uint32_t *>(&b3));
+        // raw -> A: 16 bytes (4 floats) a thread and step, a warp reading two whole rows
+        const unsigned char *rs = raw + st * kRawBytes;
+        unsigned char *a = sA + st * kAtBytes;
+#pragma unroll 4
+        for (int i = 0; i < 16; i++) {
+            const int idx = tid + 128 * i, r = idx >> 4, q = idx & 15, kc = q >> 1, half = q & 1;
+            uint2 v = make_uint2(0, 0);
+            if (r < rows) {
+                const float4 f4 = *reinterpret_cast<const float4 *>(rs + r * (kTcKc * 4) + q * 16);
+                __nv_bfloat162 b0 = __floats2bfloat162_rn(f4.x, f4.y), b1 = __floats2bfloat162_rn(f4.z, f4.w);
+                v = make_uint2(*reinterpret_cast<uint32_t *>(&b0), *reinterpret_cast<uint32_t *>(&b1));
             }
-            *reinterpret_cast<uint4 *>(a + (r >> 3) * kTcSBO + kc * kTcLBO + (r & 7) * 16) = v;
+            *reinterpret_cast<uint2 *>(a + (r >> 3) * kTcSBO + kc * kTcLBO + (r & 7) * 16 + half * 8) = v;
         }
-        // B: the 32 table rows x 8 K-cores
-        unsigned char *bb = sB[b];
+        unsigned char *bb = sB + st * kBtBytes;
 #pragma unroll
         for (int i = 0; i < 2; i++) {
             const int j = tid + 128 * i, r = j >> 3, kc = j & 7;
             const uint4 v = __ldg(reinterpret_cast<const uint4 *>(Bt + (long)r * n + (long)c * kTcKc + kc * 8));
             *reinterpret_cast<uint4 *>(bb + (r >> 3) * kTcSBO + kc * kTcLBO + (r & 7) * 16) = v;
         }
+        // the tiles go to the tensor core and the raw stage back to the copy engine
         fch::tc::fence_async_smem();
+        fch::tc::fence_before_sync();
         __syncthreads();
+        if (warp == 0 && c + 2 < nch) {
+            fetch(c + 2);
+            fetched = c + 3;
+        }
         if (tid == 0) {
             fch::tc::fence_after_sync();
             const uint32_t sa = fch::tc::smem_u32(a), sb = fch::tc::smem_u32(bb);
@@ -342,13 +365,17 @@ __global__ void __launch_bounds__(128) fno_rowdft_tc(const float *__restrict__ h
                 fch::tc::mma_bf16(tmem, fch::tc::smem_desc(sa + 2 * k * kTcLBO, kTcLBO, kTcSBO),
                                   fch::tc::smem_desc(sb + 2 * k * kTcLBO, kTcLBO, kTcSBO), idesc,
                                   (c | k) != 0);
-            fch::tc::mma_commit(&bar[b]);
+            fch::tc::mma_commit(&mmab[st]);
         }
         issued = c + 1;
     }
-    // the last commit covers every MMA issued
-    bool done = issued == 0;
-    if (issued > 0) done = fch::tc::mbar_wait(&bar[(issued - 1) & 1], (uint32_t)(((issued - 1) >> 1) & 1), kTcBound);
+    // the last commit covers every MMA issued; copies fetched beyond what was consumed
+    // (an early stop) are waited for too before the CTA's shared memory goes away
+    bool done = true;
+    if (issued > 0)
+        done = fch::tc::mbar_wait(&mmab[(issued - 1) & 1], (uint32_t)(((issued - 1) >> 1) & 1), kTcBound);
+    for (int c = issued; c < fetched; c++)
+        fch::tc::mbar_wait(&full[c & 1], (uint32_t)((c >> 1) & 1), kTcBound);
     ok = __syncthreads_and(ok && done && issued == nch);
     fch::tc::fence_after_sync();
     if (ok) {
@@ -367,6 +394,21 @@ __global__ void __launch_bounds__(128) fno_rowdft_tc(const float *__restrict__ h
     fch::tc::fence_before_sync();
     __syncthreads();
     if (warp == 0) fch::tc::tmem_dealloc(tmem, 32);
+}
+
+// launch of fno_rowdft_tc with its dynamic shared memory (the limit raised once)
+cudaError_t launch_rowdft_tc(const float *h, const __nv_bfloat16 *Bt, float2 *X, long R, int n, int *err,
+                             cudaStream_t s)
+{
+    static bool attr = false;
+    if (!attr) {
+        const cudaError_t e =
+            cudaFuncSetAttribute(fno_rowdft_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, kRowdftSmem);
+        if (e != cudaSuccess) return e;
+        attr = true;
+    }
+    fno_rowdft_tc<<<(unsigned)((R + kTcRows - 1) / kTcRows), 128, kRowdftSmem, s>>>(h, Bt, X, (int)R, n, err);
+    return cudaGetLastError();
 }
 
 // Y[f][kyi][kx] = sum_y X[f][y][kx] e^{-2 pi i ky y / n}: one block per (field f, kx),
@@ -1198,8 +1240,7 @@ static fch_status forward_tc(fch_fno *f, int batch, int n, const float *a, float
                                                 W, f->cin);
     for (int l = 0; l < f->L; l++) {
         float *hin = f->h + l * fld, *hout = f->h + (l + 1) * fld;
-        fno_rowdft_tc<<<(unsigned)((R + kTcRows - 1) / kTcRows), 128, 0, s>>>(hin, f->tc_Bt, f->tc_X, (int)R, n,
-                                                                              f->tc_err);
+        launch_rowdft_tc(hin, f->tc_Bt, f->tc_X, R, n, f->tc_err, s);
         fno_coldft<16><<<dim3(batch * W, M), 256, 0, s>>>(f->tc_X, f->tc_tw + n, f->tc_Y, n);
         fno_mix_modes<WT><<<grid((long)batch * W * f->K, 256), 256, 0, s>>>(f->tc_Y, P + offset_of(f, 4, l),
                                                                            f->tc_Z, batch, W, M);
@@ -1374,8 +1415,8 @@ extern "C" int fch_debug_rowdft_tc(const float *h, float *X, int R, int n, void 
     if (e == cudaSuccess) e = cudaMemsetAsync(err, 0, sizeof(int), s);
     if (e == cudaSuccess) {
         fno_dft_tables<<<grid(16L * n, 256), 256, 0, s>>>(Bt, tw, n);
-        fno_rowdft_tc<<<(unsigned)((R + kTcRows - 1) / kTcRows), 128, 0, s>>>(h, Bt, (float2 *)X, R, n, err);
         e = cudaGetLastError();
+        if (e == cudaSuccess) e = launch_rowdft_tc(h, Bt, (float2 *)X, R, n, err, s);
     }
     if (e == cudaSuccess) e = cudaMemcpyAsync(&herr, err, sizeof(int), cudaMemcpyDeviceToHost, s);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);

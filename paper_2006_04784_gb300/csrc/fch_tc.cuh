@@ -42,6 +42,25 @@ __device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t par, int bound
     return false;
 }
 
+// one thread announces `bytes` of asynchronous copies that the barrier's current
+// phase waits for (and arrives once)
+__device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, uint32_t bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+                 : "memory");
+}
+
+// ---- bulk copies (the TMA engine, no tensor map) ----
+// `bytes` (a multiple of 16; both addresses 16-byte aligned) from global to shared
+// memory; completion is counted in bytes on the mbarrier
+__device__ __forceinline__ void bulk_g2s(void *dst_smem, const void *src, uint32_t bytes, uint64_t *bar)
+{
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                     smem_u32(dst_smem)),
+                 "l"(src), "r"(bytes), "r"(smem_u32(bar))
+                 : "memory");
+}
+
 // ---- tensor memory ----
 // one warp allocates ncols (a power of two >= 32) columns of all 128 lanes; the
 // address lands in shared memory
