@@ -277,9 +277,11 @@ __global__ void fno_dft_tables(__nv_bfloat16 *__restrict__ Bt, float2 *__restric
 // them to the stage's `mma` mbarrier, which guards the stage's tiles. A wait that runs
 // out of polls sets *err; the CTA then stops, waits (bounded) for the copies and MMAs it
 // issued, frees its tensor memory and returns.
-constexpr int kRawBytes = kTcRows * kTcKc * 4;                       // one chunk of FP32 rows
-constexpr int kAtBytes = (kTcRows / 8) * kTcSBO, kBtBytes = (kTcNB / 8) * kTcSBO;
-constexpr int kRowdftSmem = 2 * kRawBytes + 2 * kAtBytes + 2 * kBtBytes;  // 111,616 bytes
+constexpr int kDftKc = 32;                                  // K of a chunk (two K = 16 MMAs)
+constexpr int kDftSBO = (kDftKc / 8) * kTcLBO;              // 8-row groups of four K cores
+constexpr int kRawBytes = kTcRows * kDftKc * 4;             // one chunk of FP32 rows
+constexpr int kAtBytes = (kTcRows / 8) * kDftSBO, kBtBytes = (kTcNB / 8) * kDftSBO;
+constexpr int kRowdftSmem = 2 * kRawBytes + 2 * kAtBytes + 2 * kBtBytes;  // 55,808 bytes: four CTAs an SM
 
 __global__ void __launch_bounds__(128) fno_rowdft_tc(const float *__restrict__ h, const __nv_bfloat16 *__restrict__ Bt,
                                                      float2 *__restrict__ X, int R, int n, int *err)
@@ -291,7 +293,7 @@ __global__ void __launch_bounds__(128) fno_rowdft_tc(const float *__restrict__ h
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const long row0 = (long)blockIdx.x * kTcRows;
     const int rows = (int)(R - row0 < kTcRows ? R - row0 : kTcRows);
-    const int nch = n / kTcKc;
+    const int nch = n / kDftKc;
     if (warp == 0) {
         fch::tc::tmem_alloc(&tslot, 32);
         fch::tc::tmem_relinquish();
@@ -312,10 +314,10 @@ __global__ void __launch_bounds__(128) fno_rowdft_tc(const float *__restrict__ h
     auto fetch = [&](int c) {
         uint64_t *bar = &full[c & 1];
         unsigned char *dst = raw + (c & 1) * kRawBytes;
-        if (lane == 0) fch::tc::mbar_expect_tx(bar, (uint32_t)rows * (kTcKc * 4));
+        if (lane == 0) fch::tc::mbar_expect_tx(bar, (uint32_t)rows * (kDftKc * 4));
         __syncwarp();
         for (int r = lane; r < rows; r += 32)
-            fch::tc::bulk_g2s(dst + r * (kTcKc * 4), h + (row0 + r) * n + (long)c * kTcKc, kTcKc * 4, bar);
+            fch::tc::bulk_g2s(dst + r * (kDftKc * 4), h + (row0 + r) * n + (long)c * kDftKc, kDftKc * 4, bar);
     };
     if (warp == 0)
         for (int c = 0; c < 2 && c < nch; c++) fetch(c);
@@ -328,26 +330,25 @@ __global__ void __launch_bounds__(128) fno_rowdft_tc(const float *__restrict__ h
         ok = fch::tc::mbar_wait(&full[st], (uint32_t)((c >> 1) & 1), kTcBound);
         if (ok && c >= 2) ok = fch::tc::mbar_wait(&mmab[st], (uint32_t)(((c >> 1) - 1) & 1), kTcBound);
         if (!__syncthreads_and(ok)) break;
-        // raw -> A: 16 bytes (4 floats) a thread and step, a warp reading two whole rows
+        // raw -> A: 16 bytes (4 floats) a thread and step, a warp reading four whole rows
         const unsigned char *rs = raw + st * kRawBytes;
         unsigned char *a = sA + st * kAtBytes;
-#pragma unroll 4
-        for (int i = 0; i < 16; i++) {
-            const int idx = tid + 128 * i, r = idx >> 4, q = idx & 15, kc = q >> 1, half = q & 1;
+#pragma unroll
+        for (int i = 0; i < 8; i++) {
+            const int idx = tid + 128 * i, r = idx >> 3, q = idx & 7, kc = q >> 1, half = q & 1;
             uint2 v = make_uint2(0, 0);
             if (r < rows) {
-                const float4 f4 = *reinterpret_cast<const float4 *>(rs + r * (kTcKc * 4) + q * 16);
+                const float4 f4 = *reinterpret_cast<const float4 *>(rs + r * (kDftKc * 4) + q * 16);
                 __nv_bfloat162 b0 = __floats2bfloat162_rn(f4.x, f4.y), b1 = __floats2bfloat162_rn(f4.z, f4.w);
                 v = make_uint2(*reinterpret_cast<uint32_t *>(&b0), *reinterpret_cast<uint32_t *>(&b1));
             }
-            *reinterpret_cast<uint2 *>(a + (r >> 3) * kTcSBO + kc * kTcLBO + (r & 7) * 16 + half * 8) = v;
+            *reinterpret_cast<uint2 *>(a + (r >> 3) * kDftSBO + kc * kTcLBO + (r & 7) * 16 + half * 8) = v;
         }
         unsigned char *bb = sB + st * kBtBytes;
-#pragma unroll
-        for (int i = 0; i < 2; i++) {
-            const int j = tid + 128 * i, r = j >> 3, kc = j & 7;
-            const uint4 v = __ldg(reinterpret_cast<const uint4 *>(Bt + (long)r * n + (long)c * kTcKc + kc * 8));
-            *reinterpret_cast<uint4 *>(bb + (r >> 3) * kTcSBO + kc * kTcLBO + (r & 7) * 16) = v;
+        {
+            const int r = tid >> 2, kc = tid & 3; // 32 table rows x 4 K cores
+            const uint4 v = __ldg(reinterpret_cast<const uint4 *>(Bt + (long)r * n + (long)c * kDftKc + kc * 8));
+            *reinterpret_cast<uint4 *>(bb + (r >> 3) * kDftSBO + kc * kTcLBO + (r & 7) * 16) = v;
         }
         // the tiles go to the tensor core and the raw stage back to the copy engine
         fch::tc::fence_async_smem();
@@ -361,9 +362,9 @@ __global__ void __launch_bounds__(128) fno_rowdft_tc(const float *__restrict__ h
             fch::tc::fence_after_sync();
             const uint32_t sa = fch::tc::smem_u32(a), sb = fch::tc::smem_u32(bb);
 #pragma unroll
-            for (int k = 0; k < kTcKc / 16; k++)
-                fch::tc::mma_bf16(tmem, fch::tc::smem_desc(sa + 2 * k * kTcLBO, kTcLBO, kTcSBO),
-                                  fch::tc::smem_desc(sb + 2 * k * kTcLBO, kTcLBO, kTcSBO), idesc,
+            for (int k = 0; k < kDftKc / 16; k++)
+                fch::tc::mma_bf16(tmem, fch::tc::smem_desc(sa + 2 * k * kTcLBO, kTcLBO, kDftSBO),
+                                  fch::tc::smem_desc(sb + 2 * k * kTcLBO, kTcLBO, kDftSBO), idesc,
                                   (c | k) != 0);
             fch::tc::mma_commit(&mmab[st]);
         }
