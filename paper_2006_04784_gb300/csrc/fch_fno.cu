@@ -22,6 +22,7 @@
 // Q2, bQ2, with R_l as [K][W_out][W_in] complex (re, im interleaved).
 // Weight gradients are summed over points in a fixed order (per-block partials,
 // then one pass over the blocks), so a backward pass is deterministic.
+#include <cuda.h> // CUtensorMap and its enums (the encoder is fetched at run time)
 #include <cuda_bf16.h>
 #include <math.h>
 #include <stdio.h>
@@ -251,7 +252,7 @@ __global__ void fno_mix(const float2 *__restrict__ X, const WT *__restrict__ R, 
 // DFT, a GEMM with K = n, runs on the tensor cores (tcgen05, BF16 operands, FP32
 // sums); the other stages are small and run as plain kernels in FP32.
 
-constexpr int kTcRows = 128, kTcKc = 64, kTcLBO = 144, kTcSBO = 8 * kTcLBO, kTcNB = 32;
+constexpr int kTcRows = 128, kTcLBO = 144, kTcSBO = 8 * kTcLBO, kTcNB = 32;
 constexpr int kTcBound = 1 << 22; // polls of an mbarrier before a kernel gives up
 
 // Bt[j][x] (bf16): cos(2 pi j x / n) for j < 16, -sin(2 pi (j - 16) x / n) for j >= 16;
@@ -269,33 +270,38 @@ __global__ void fno_dft_tables(__nv_bfloat16 *__restrict__ Bt, float2 *__restric
 }
 
 // X[r][kx] = (D[r][kx], D[r][16 + kx]) with D = bf16(h) Bt^T over K = n: one CTA of 128
-// threads per 128 rows, K in chunks of 64. The FP32 rows of a chunk arrive by bulk copies
-// (the TMA engine, 256 bytes a row, two chunks ahead, completion counted in bytes on the
-// stage's `full` mbarrier); the threads round them to bfloat16 into the core-matrix
-// layout of the stage's A tile (see fch_tc.cuh) and copy the table's chunk; thread 0
-// issues four K = 16 MMAs into a 128 x 32 FP32 accumulator in tensor memory and commits
-// them to the stage's `mma` mbarrier, which guards the stage's tiles. A wait that runs
-// out of polls sets *err; the CTA then stops, waits (bounded) for the copies and MMAs it
-// issued, frees its tensor memory and returns.
+// threads per 128 rows, K in chunks of 32. A chunk of the FP32 rows arrives as one 2D
+// tile of a tensor map over h (the TMA engine: 128 rows x 32 floats, two chunks ahead,
+// completion counted in bytes on the stage's `full` mbarrier; rows beyond R read as
+// zero); the threads round it to bfloat16 into the core-matrix layout of the stage's A
+// tile (see fch_tc.cuh) and copy the table's chunk; thread 0 issues two K = 16 MMAs
+// into a 128 x 32 FP32 accumulator in tensor memory and commits them to the stage's
+// `mma` mbarrier, which guards the stage's tiles. A wait that runs out of polls sets
+// *err; the CTA then stops, waits (bounded) for the loads and MMAs it issued, frees its
+// tensor memory and returns.
 constexpr int kDftKc = 32;                                  // K of a chunk (two K = 16 MMAs)
 constexpr int kDftSBO = (kDftKc / 8) * kTcLBO;              // 8-row groups of four K cores
-constexpr int kRawBytes = kTcRows * kDftKc * 4;             // one chunk of FP32 rows
+constexpr int kRawBytes = kTcRows * kDftKc * 4;             // one tile of FP32 rows (16 KB)
 constexpr int kAtBytes = (kTcRows / 8) * kDftSBO, kBtBytes = (kTcNB / 8) * kDftSBO;
-constexpr int kRowdftSmem = 2 * kRawBytes + 2 * kAtBytes + 2 * kBtBytes;  // 55,808 bytes: four CTAs an SM
+// the stages, then the mbarriers and the tensor-memory address, and 1 KB of slack to
+// align the tiles to 1024 bytes
+constexpr int kRowdftSmem = 2 * kRawBytes + 2 * kAtBytes + 2 * kBtBytes + 64 + 1024;
 
-__global__ void __launch_bounds__(128) fno_rowdft_tc(const float *__restrict__ h, const __nv_bfloat16 *__restrict__ Bt,
-                                                     float2 *__restrict__ X, int R, int n, int *err)
+__global__ void __launch_bounds__(128) fno_rowdft_tc(const __grid_constant__ CUtensorMap tmap,
+                                                     const __nv_bfloat16 *__restrict__ Bt, float2 *__restrict__ X,
+                                                     int R, int n, int *err)
 {
-    extern __shared__ __align__(128) unsigned char dsm[];
+    extern __shared__ unsigned char dsm_raw[];
+    // the TMA destination wants an aligned tile: the window's start rounded up to 1024 B
+    unsigned char *dsm = dsm_raw + ((1024u - (fch::tc::smem_u32(dsm_raw) & 1023u)) & 1023u);
     unsigned char *raw = dsm, *sA = dsm + 2 * kRawBytes, *sB = sA + 2 * kAtBytes;
-    __shared__ __align__(8) uint64_t full[2], mmab[2];
-    __shared__ uint32_t tslot;
+    uint64_t *full = reinterpret_cast<uint64_t *>(sB + 2 * kBtBytes), *mmab = full + 2;
+    uint32_t *tslot = reinterpret_cast<uint32_t *>(mmab + 2);
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const long row0 = (long)blockIdx.x * kTcRows;
-    const int rows = (int)(R - row0 < kTcRows ? R - row0 : kTcRows);
     const int nch = n / kDftKc;
     if (warp == 0) {
-        fch::tc::tmem_alloc(&tslot, 32);
+        fch::tc::tmem_alloc(tslot, 32);
         fch::tc::tmem_relinquish();
     }
     if (tid == 0) {
@@ -308,20 +314,13 @@ __global__ void __launch_bounds__(128) fno_rowdft_tc(const float *__restrict__ h
     fch::tc::fence_before_sync();
     __syncthreads();
     fch::tc::fence_after_sync();
-    const uint32_t tmem = tslot;
-    // warp 0 fetches chunk c into stage c & 1: lane 0 announces the bytes, then the 32
-    // lanes issue the rows' copies
-    auto fetch = [&](int c) {
-        uint64_t *bar = &full[c & 1];
-        unsigned char *dst = raw + (c & 1) * kRawBytes;
-        if (lane == 0) fch::tc::mbar_expect_tx(bar, (uint32_t)rows * (kDftKc * 4));
-        __syncwarp();
-        for (int r = lane; r < rows; r += 32)
-            fch::tc::bulk_g2s(dst + r * (kDftKc * 4), h + (row0 + r) * n + (long)c * kDftKc, kDftKc * 4, bar);
+    const uint32_t tmem = *tslot;
+    auto fetch = [&](int c) { // thread 0
+        fch::tc::mbar_expect_tx(&full[c & 1], kRawBytes);
+        fch::tc::tma_load_2d(raw + (c & 1) * kRawBytes, &tmap, c * kDftKc, (int)row0, &full[c & 1]);
     };
-    if (warp == 0)
+    if (tid == 0)
         for (int c = 0; c < 2 && c < nch; c++) fetch(c);
-    // rows beyond R are zero in every stage's A tile (their raw rows are never written)
     constexpr uint32_t idesc = fch::tc::idesc_bf16_f32(kTcRows, kTcNB);
     bool ok = true;
     int fetched = nch < 2 ? nch : 2, issued = 0;
@@ -336,12 +335,9 @@ __global__ void __launch_bounds__(128) fno_rowdft_tc(const float *__restrict__ h
 #pragma unroll
         for (int i = 0; i < 8; i++) {
             const int idx = tid + 128 * i, r = idx >> 3, q = idx & 7, kc = q >> 1, half = q & 1;
-            uint2 v = make_uint2(0, 0);
-            if (r < rows) {
-                const float4 f4 = *reinterpret_cast<const float4 *>(rs + r * (kDftKc * 4) + q * 16);
-                __nv_bfloat162 b0 = __floats2bfloat162_rn(f4.x, f4.y), b1 = __floats2bfloat162_rn(f4.z, f4.w);
-                v = make_uint2(*reinterpret_cast<uint32_t *>(&b0), *reinterpret_cast<uint32_t *>(&b1));
-            }
+            const float4 f4 = *reinterpret_cast<const float4 *>(rs + r * (kDftKc * 4) + q * 16);
+            __nv_bfloat162 b0 = __floats2bfloat162_rn(f4.x, f4.y), b1 = __floats2bfloat162_rn(f4.z, f4.w);
+            const uint2 v = make_uint2(*reinterpret_cast<uint32_t *>(&b0), *reinterpret_cast<uint32_t *>(&b1));
             *reinterpret_cast<uint2 *>(a + (r >> 3) * kDftSBO + kc * kTcLBO + (r & 7) * 16 + half * 8) = v;
         }
         unsigned char *bb = sB + st * kBtBytes;
@@ -354,11 +350,11 @@ __global__ void __launch_bounds__(128) fno_rowdft_tc(const float *__restrict__ h
         fch::tc::fence_async_smem();
         fch::tc::fence_before_sync();
         __syncthreads();
-        if (warp == 0 && c + 2 < nch) {
-            fetch(c + 2);
-            fetched = c + 3;
-        }
         if (tid == 0) {
+            if (c + 2 < nch) {
+                fetch(c + 2);
+                fetched = c + 3;
+            }
             fch::tc::fence_after_sync();
             const uint32_t sa = fch::tc::smem_u32(a), sb = fch::tc::smem_u32(bb);
 #pragma unroll
@@ -370,13 +366,14 @@ __global__ void __launch_bounds__(128) fno_rowdft_tc(const float *__restrict__ h
         }
         issued = c + 1;
     }
-    // the last commit covers every MMA issued; copies fetched beyond what was consumed
-    // (an early stop) are waited for too before the CTA's shared memory goes away
+    // the last commit covers every MMA issued; tiles fetched beyond what was consumed (an
+    // early stop) are waited for before the CTA's shared memory goes away
     bool done = true;
     if (issued > 0)
         done = fch::tc::mbar_wait(&mmab[(issued - 1) & 1], (uint32_t)(((issued - 1) >> 1) & 1), kTcBound);
-    for (int c = issued; c < fetched; c++)
-        fch::tc::mbar_wait(&full[c & 1], (uint32_t)((c >> 1) & 1), kTcBound);
+    if (tid == 0)
+        for (int c = issued; c < fetched; c++)
+            fch::tc::mbar_wait(&full[c & 1], (uint32_t)((c >> 1) & 1), kTcBound);
     ok = __syncthreads_and(ok && done && issued == nch);
     fch::tc::fence_after_sync();
     if (ok) {
@@ -397,7 +394,36 @@ __global__ void __launch_bounds__(128) fno_rowdft_tc(const float *__restrict__ h
     if (warp == 0) fch::tc::tmem_dealloc(tmem, 32);
 }
 
-// launch of fno_rowdft_tc with its dynamic shared memory (the limit raised once)
+// the tensor map of R rows of n floats (row-major, 16-byte aligned rows), tiles of 128
+// rows x 32 floats, zero outside; the encoder comes from the driver through the runtime
+typedef CUresult (*EncodeTiledFn)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
+                                  const cuuint64_t *, const cuuint32_t *, const cuuint32_t *, CUtensorMapInterleave,
+                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+cudaError_t rows_tensor_map(CUtensorMap *m, const float *h, long R, int n)
+{
+    static EncodeTiledFn enc = nullptr;
+    if (!enc) {
+        void *p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        const cudaError_t e =
+            cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q);
+        if (e != cudaSuccess) return e;
+        if (q != cudaDriverEntryPointSuccess || !p) return cudaErrorNotSupported;
+        enc = (EncodeTiledFn)p;
+    }
+    const cuuint64_t dims[2] = {(cuuint64_t)n, (cuuint64_t)R};
+    const cuuint64_t strides[1] = {(cuuint64_t)n * sizeof(float)};
+    const cuuint32_t box[2] = {(cuuint32_t)kDftKc, (cuuint32_t)kTcRows};
+    const cuuint32_t estr[2] = {1, 1};
+    const CUresult r = enc(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, (void *)h, dims, strides, box, estr,
+                           CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                           CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
+}
+
+// launch of fno_rowdft_tc over R rows of n floats at h (n a multiple of 32), with its
+// tensor map and dynamic shared memory (the limit raised once)
 cudaError_t launch_rowdft_tc(const float *h, const __nv_bfloat16 *Bt, float2 *X, long R, int n, int *err,
                              cudaStream_t s)
 {
@@ -408,7 +434,10 @@ cudaError_t launch_rowdft_tc(const float *h, const __nv_bfloat16 *Bt, float2 *X,
         if (e != cudaSuccess) return e;
         attr = true;
     }
-    fno_rowdft_tc<<<(unsigned)((R + kTcRows - 1) / kTcRows), 128, kRowdftSmem, s>>>(h, Bt, X, (int)R, n, err);
+    CUtensorMap m;
+    const cudaError_t e = rows_tensor_map(&m, h, R, n);
+    if (e != cudaSuccess) return e;
+    fno_rowdft_tc<<<(unsigned)((R + kTcRows - 1) / kTcRows), 128, kRowdftSmem, s>>>(m, Bt, X, (int)R, n, err);
     return cudaGetLastError();
 }
 

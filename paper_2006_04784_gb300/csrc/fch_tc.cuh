@@ -61,6 +61,18 @@ __device__ __forceinline__ void bulk_g2s(void *dst_smem, const void *src, uint32
                  : "memory");
 }
 
+// a 2D tile of a tensor map (the TMA engine with a tensor map) into shared memory:
+// box at coordinates (x, y) of the map, x innermost; completion counted in bytes on
+// the mbarrier; out-of-range elements of the box read as the map's fill value
+__device__ __forceinline__ void tma_load_2d(void *dst_smem, const void *tmap, int x, int y, uint64_t *bar)
+{
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::"r"(
+            smem_u32(dst_smem)),
+        "l"(tmap), "r"(x), "r"(y), "r"(smem_u32(bar))
+        : "memory");
+}
+
 // ---- tensor memory ----
 // one warp allocates ncols (a power of two >= 32) columns of all 128 lanes; the
 // address lands in shared memory
