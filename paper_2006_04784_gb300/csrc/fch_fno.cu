@@ -62,19 +62,23 @@ __global__ void fno_to_bf16(const float *__restrict__ w, __nv_bfloat16 *__restri
     if (t < cnt) out[t] = __float2bfloat16_rn(w[t]);
 }
 
-// h0[b][c][p] = sum_i P[c][i] a[b][i][p] + bP[c]
+// h0[b][c][p] = sum_i P[c][i] a[b][i][p] + bP[c] (the weights staged in shared memory)
 template <typename WT>
 __global__ void fno_lift(const float *__restrict__ a, const WT *__restrict__ P, const WT *__restrict__ bP,
                          float *__restrict__ h, int B, int n2, int W, int cin)
 {
+    __shared__ float ps[32 * 4], bs[32];
+    for (int i = threadIdx.x; i < W * cin; i += blockDim.x) ps[i] = wld(P, i);
+    for (int i = threadIdx.x; i < W; i += blockDim.x) bs[i] = wld(bP, i);
+    __syncthreads();
     const long t = (long)blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= (long)B * n2) return;
     const int b = (int)(t / n2), p = (int)(t - (long)b * n2);
     float in[4];
     for (int i = 0; i < cin; i++) in[i] = a[((long)b * cin + i) * n2 + p];
     for (int c = 0; c < W; c++) {
-        float acc = wld(bP, c);
-        for (int i = 0; i < cin; i++) acc += wld(P, c * cin + i) * in[i];
+        float acc = bs[c];
+        for (int i = 0; i < cin; i++) acc += ps[c * cin + i] * in[i];
         h[((long)b * W + c) * n2 + p] = acc;
     }
 }
