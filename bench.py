@@ -341,6 +341,9 @@ def run_gb300(args):
             out["fixed_step"] = fixed_step_throughput(fch, I, dev)
         if not args.no_t_final and world == 1:
             out["time_to_t_final"] = time_to_t_final(fch, I, n)
+        if not args.no_ensemble and world == 1:
+            # the batched ensemble (64 instances on 256^2 to 1024^2 grids, one graph a launch)
+            out["ensemble"] = ensemble_bench(args)
         if not args.no_cpu_baseline and world == 1:
             out["cpu_baseline"] = cpu_baseline(args)
     ctx.close()
@@ -1433,6 +1436,7 @@ def main():
     ap.add_argument("--scheme", default="imex", choices=["imex", "sav", "etd"])
     ap.add_argument("--no-t-final", action="store_true", help="skip the time-to-t_final runs")
     ap.add_argument("--no-fft", action="store_true", help="skip the standalone transform throughput")
+    ap.add_argument("--no-ensemble", action="store_true", help="skip the batched-ensemble entry")
     ap.add_argument("--autotune", type=int, default=2,
                     help="2: pass tiles from fch_autotune_step (timed on adaptive trials; default); "
                          "1: from fch_autotune (timed on transforms); 0: default tiles")

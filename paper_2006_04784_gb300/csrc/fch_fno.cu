@@ -284,7 +284,10 @@ __global__ void fno_dft_tables(__nv_bfloat16 *__restrict__ Bt, float2 *__restric
 // *err; the CTA then stops, waits (bounded) for the loads and MMAs it issued, frees its
 // tensor memory and returns.
 constexpr int kDftKc = 32;                                  // K of a chunk (two K = 16 MMAs)
-constexpr int kDftSBO = (kDftKc / 8) * kTcLBO;              // 8-row groups of four K cores
+// 192 bytes between K cores: the 8-byte stores of a warp (four rows x four cores x two
+// halves) then fall on 16 distinct bank pairs, two lanes each (the minimum for 256 bytes)
+constexpr int kDftLBO = 192;
+constexpr int kDftSBO = (kDftKc / 8) * kDftLBO;             // 8-row groups of four K cores
 constexpr int kRawBytes = kTcRows * kDftKc * 4;             // one tile of FP32 rows (16 KB)
 constexpr int kAtBytes = (kTcRows / 8) * kDftSBO, kBtBytes = (kTcNB / 8) * kDftSBO;
 // the stages, then the mbarriers and the tensor-memory address, and 1 KB of slack to
@@ -342,13 +345,13 @@ __global__ void __launch_bounds__(128) fno_rowdft_tc(const __grid_constant__ CUt
             const float4 f4 = *reinterpret_cast<const float4 *>(rs + r * (kDftKc * 4) + q * 16);
             __nv_bfloat162 b0 = __floats2bfloat162_rn(f4.x, f4.y), b1 = __floats2bfloat162_rn(f4.z, f4.w);
             const uint2 v = make_uint2(*reinterpret_cast<uint32_t *>(&b0), *reinterpret_cast<uint32_t *>(&b1));
-            *reinterpret_cast<uint2 *>(a + (r >> 3) * kDftSBO + kc * kTcLBO + (r & 7) * 16 + half * 8) = v;
+            *reinterpret_cast<uint2 *>(a + (r >> 3) * kDftSBO + kc * kDftLBO + (r & 7) * 16 + half * 8) = v;
         }
         unsigned char *bb = sB + st * kBtBytes;
         {
             const int r = tid >> 2, kc = tid & 3; // 32 table rows x 4 K cores
             const uint4 v = __ldg(reinterpret_cast<const uint4 *>(Bt + (long)r * n + (long)c * kDftKc + kc * 8));
-            *reinterpret_cast<uint4 *>(bb + (r >> 3) * kDftSBO + kc * kTcLBO + (r & 7) * 16) = v;
+            *reinterpret_cast<uint4 *>(bb + (r >> 3) * kDftSBO + kc * kDftLBO + (r & 7) * 16) = v;
         }
         // the tiles go to the tensor core and the raw stage back to the copy engine
         fch::tc::fence_async_smem();
@@ -363,8 +366,8 @@ __global__ void __launch_bounds__(128) fno_rowdft_tc(const __grid_constant__ CUt
             const uint32_t sa = fch::tc::smem_u32(a), sb = fch::tc::smem_u32(bb);
 #pragma unroll
             for (int k = 0; k < kDftKc / 16; k++)
-                fch::tc::mma_bf16(tmem, fch::tc::smem_desc(sa + 2 * k * kTcLBO, kTcLBO, kDftSBO),
-                                  fch::tc::smem_desc(sb + 2 * k * kTcLBO, kTcLBO, kDftSBO), idesc,
+                fch::tc::mma_bf16(tmem, fch::tc::smem_desc(sa + 2 * k * kDftLBO, kDftLBO, kDftSBO),
+                                  fch::tc::smem_desc(sb + 2 * k * kDftLBO, kDftLBO, kDftSBO), idesc,
                                   (c | k) != 0);
             fch::tc::mma_commit(&mmab[st]);
         }
