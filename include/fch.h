@@ -291,14 +291,16 @@ fch_status fch_fno_adam(fch_fno *f, float lr, float beta1, float beta2, float ep
  * products and sums staying in FP32: BF16 weights with FP32 accumulation for
  * inference. Training keeps the FP32 weights: fch_fno_backward after a forward pass
  * on the bfloat16 copy returns FCH_ESTATE. fch_fno_set_bf16(f, 0) frees the copy.
- * fch_fno_set_bf16(f, 2): as 1, and each spectral convolution runs as truncated DFTs
- * over the retained modes instead of full transforms of every channel: the DFT along
- * x (a GEMM with K = n) on the tensor cores (tcgen05, bfloat16 operands: the layer
- * input and the cos / sin table rounded to nearest even; FP32 sums), the DFTs along y,
- * the mode mixing and the inverse DFTs in FP32 kernels, the inverse along x fused
- * into the pointwise layer. Needs modes = 16 and n a multiple of 64 at forward time
- * (else FCH_EINVAL); the forward pass then synchronizes its stream once to read the
- * tensor-core kernel's status (FCH_ECUDA if one of its bounded waits ran out). */
+ * fch_fno_set_bf16(f, 2): as 1, and the forward pass runs its dense contractions on
+ * the tensor cores (tcgen05 GEMMs, bfloat16 operands rounded to nearest even, FP32
+ * sums): each spectral convolution as truncated DFTs over the retained modes instead
+ * of full transforms of every channel (the DFT along x, a GEMM with K = n whose input
+ * tiles arrive by TMA; the DFTs along y, the mode mixing and the inverse DFT along y
+ * in FP32 kernels), the channel mixing W h fused with the inverse DFT along x, and
+ * the projection Q1 h. Needs modes = 16, width 16 or 32, proj a multiple of 16 and n a
+ * multiple of 128 at forward time (else FCH_EINVAL); the forward pass then
+ * synchronizes its stream once to read the tensor-core kernels' status (FCH_ECUDA if
+ * one of their bounded waits ran out). */
 fch_status fch_fno_set_bf16(fch_fno *f, int on);
 
 /* One PSD-BDF2 step of size dt (as fch_step with FCH_PSD) whose iteration starts

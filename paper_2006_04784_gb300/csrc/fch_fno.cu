@@ -284,9 +284,10 @@ __global__ void fno_dft_tables(__nv_bfloat16 *__restrict__ Bt, float2 *__restric
 // *err; the CTA then stops, waits (bounded) for the loads and MMAs it issued, frees its
 // tensor memory and returns.
 constexpr int kDftKc = 32;                                  // K of a chunk (two K = 16 MMAs)
-// 192 bytes between K cores: the 8-byte stores of a warp (four rows x four cores x two
-// halves) then fall on 16 distinct bank pairs, two lanes each (the minimum for 256 bytes)
-constexpr int kDftLBO = 192;
+// 160 bytes between K cores: a half warp's 8-byte stores (two rows x four cores x two
+// halves, one 128-byte wavefront) then fall on 16 distinct bank pairs, and a quarter
+// warp's 16-byte stores of the table (two rows x four cores) on 8 distinct bank quads
+constexpr int kDftLBO = 160;
 constexpr int kDftSBO = (kDftKc / 8) * kDftLBO;             // 8-row groups of four K cores
 constexpr int kRawBytes = kTcRows * kDftKc * 4;             // one tile of FP32 rows (16 KB)
 constexpr int kAtBytes = (kTcRows / 8) * kDftSBO, kBtBytes = (kTcNB / 8) * kDftSBO;
