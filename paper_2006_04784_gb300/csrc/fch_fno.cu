@@ -257,7 +257,7 @@ __global__ void fno_mix(const float2 *__restrict__ X, const WT *__restrict__ R, 
 // sums); the other stages are small and run as plain kernels in FP32.
 
 constexpr int kTcRows = 128, kTcLBO = 144, kTcSBO = 8 * kTcLBO, kTcNB = 32;
-constexpr int kTcBound = 1 << 22; // polls of an mbarrier before a kernel gives up
+constexpr uint64_t kTcBound = 1000000000ull; // ns an mbarrier wait lasts before a kernel gives up
 
 // Bt[j][x] (bf16): cos(2 pi j x / n) for j < 16, -sin(2 pi (j - 16) x / n) for j >= 16;
 // tw[kx][x] (float2): (cos, sin)(2 pi kx x / n), kx < 16
@@ -280,7 +280,7 @@ __global__ void fno_dft_tables(__nv_bfloat16 *__restrict__ Bt, float2 *__restric
 // zero); the threads round it to bfloat16 into the core-matrix layout of the stage's A
 // tile (see fch_tc.cuh) and copy the table's chunk; thread 0 issues two K = 16 MMAs
 // into a 128 x 32 FP32 accumulator in tensor memory and commits them to the stage's
-// `mma` mbarrier, which guards the stage's tiles. A wait that runs out of polls sets
+// `mma` mbarrier, which guards the stage's tiles. A wait that runs out of time (1 s) sets
 // *err; the CTA then stops, waits (bounded) for the loads and MMAs it issued, frees its
 // tensor memory and returns.
 constexpr int kDftKc = 32;                                  // K of a chunk (two K = 16 MMAs)

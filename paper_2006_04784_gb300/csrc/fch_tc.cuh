@@ -24,11 +24,22 @@ __device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count)
 }
 __device__ __forceinline__ void mbar_init_fence() { asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory"); }
 
-// wait for the completion of phase parity `par`, at most `bound` polls; false on timeout
-__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t par, int bound)
+// nanoseconds of the GPU's global timer
+__device__ __forceinline__ uint64_t globaltimer_ns()
+{
+    uint64_t t;
+    asm volatile("mov.u64 %0, %globaltimer;" : "=l"(t));
+    return t;
+}
+
+// wait for the completion of phase parity `par` for at most `limit_ns` nanoseconds
+// of the global timer (polls of try_wait, each of which may suspend the thread for
+// a short while); false on timeout
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t par, uint64_t limit_ns)
 {
     const uint32_t a = smem_u32(bar);
-    for (int i = 0; i < bound; i++) {
+    uint64_t t0 = 0;
+    for (int i = 0;; i++) {
         uint32_t done;
         asm volatile(
             "{\n\t.reg .pred p;\n\t"
@@ -38,8 +49,12 @@ __device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t par, int bound
             : "r"(a), "r"(par)
             : "memory");
         if (done) return true;
+        if (i == 0) {
+            t0 = globaltimer_ns();
+        } else if (globaltimer_ns() - t0 > limit_ns) {
+            return false;
+        }
     }
-    return false;
 }
 
 // one thread announces `bytes` of asynchronous copies that the barrier's current
