@@ -428,6 +428,15 @@ fch_status fch_fft_r2c(fch_fft_plan *plan, const void *x_dev, void *X_dev, int b
 /* inverse of fch_fft_r2c (divides by N^2); X is not modified. */
 fch_status fch_fft_c2r(fch_fft_plan *plan, const void *X_dev, void *x_dev, int batch);
 
+/* Synchronizes the plan's stream and reports whether the plan's transforms since its
+ * creation (or the previous call) ran into a device-side timeout: the single-precision
+ * column passes at N = 1024 fetch their input by bulk copies (the TMA engine) and wait
+ * for each at most 1 s; a wait that runs out (not expected) leaves the rest of that
+ * pass's work unwritten and sets the plan's error word. FCH_OK, or FCH_ECUDA (the word
+ * was set, and is cleared; or the stream reports an error) with the reason in
+ * fch_last_cuda_error(NULL); FCH_EINVAL for a NULL plan. */
+fch_status fch_fft_plan_status(fch_fft_plan *plan);
+
 /* ---- standalone R2C transform without device allocation ----
  * The paper has no counterpart to this entry point; it serves callers that must
  * not allocate device memory once running (another component owns the device's

@@ -2080,6 +2080,7 @@ struct fch_fft_plan {
     fch_geom geom;
     fch_kparams kp;
     void *Z, *tw, *tw2;
+    int *err; // device word: set by a pass whose bounded wait on a bulk copy ran out
 };
 
 // Field pairs per launch of a standalone transform: as many as a 64 MiB work array
@@ -2109,6 +2110,8 @@ extern "C" fch_status fch_fft_plan_create(int n, int prec, void *stream, fch_fft
     const size_t csz = prec ? 8 : 16;
     cudaError_t e = cudaMalloc(&pl->Z, (size_t)pl->chunk * n * n * csz);
     if (e == cudaSuccess) e = cudaMalloc(&pl->tw, (size_t)n * csz);
+    if (e == cudaSuccess) e = cudaMalloc(&pl->err, sizeof(int));
+    if (e == cudaSuccess) e = cudaMemsetAsync(pl->err, 0, sizeof(int), pl->stream);
     if (e != cudaSuccess) {
         fch_fft_plan_destroy(pl);
         return e == cudaErrorMemoryAllocation ? FCH_ENOMEM : FCH_ECUDA;
@@ -2131,6 +2134,7 @@ extern "C" fch_status fch_fft_plan_create(int n, int prec, void *stream, fch_fft
     pl->kp.cd.inv_n2 = pl->kp.inv_n2;
     pl->kp.Z = pl->Z;
     pl->kp.tw = pl->tw;
+    pl->kp.err = pl->err;
     if (prec && n == 1024) {
         if (upload_tw2(&pl->tw2, pl->stream) != cudaSuccess) {
             fch_fft_plan_destroy(pl);
@@ -2148,7 +2152,27 @@ extern "C" fch_status fch_fft_plan_destroy(fch_fft_plan *pl)
     if (pl->Z) cudaFree(pl->Z);
     if (pl->tw) cudaFree(pl->tw);
     if (pl->tw2) cudaFree(pl->tw2);
+    if (pl->err) cudaFree(pl->err);
     free(pl);
+    return FCH_OK;
+}
+
+extern "C" fch_status fch_fft_plan_status(fch_fft_plan *pl)
+{
+    if (!pl) return FCH_EINVAL;
+    int h = 0;
+    cudaError_t e = cudaMemcpyAsync(&h, pl->err, sizeof(int), cudaMemcpyDeviceToHost, pl->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(pl->stream);
+    if (e != cudaSuccess) {
+        snprintf(g_plan_err, sizeof(g_plan_err), "plan status: %s", cudaGetErrorString(e));
+        return FCH_ECUDA;
+    }
+    if (h) {
+        snprintf(g_plan_err, sizeof(g_plan_err), "a column pass's wait on a bulk copy ran out of time");
+        if (cudaMemsetAsync(pl->err, 0, sizeof(int), pl->stream) == cudaSuccess)
+            cudaStreamSynchronize(pl->stream);
+        return FCH_ECUDA;
+    }
     return FCH_OK;
 }
 

@@ -32,6 +32,7 @@
 #include "../../include/fch.h"
 #include "fch_internal.h"
 #include "fch_tc.cuh"
+#include "fch_tmap.h"
 
 namespace {
 
@@ -402,34 +403,6 @@ __global__ void __launch_bounds__(128) fno_rowdft_tc(const __grid_constant__ CUt
     if (warp == 0) fch::tc::tmem_dealloc(tmem, 32);
 }
 
-// the tensor map of R rows of n floats (row-major, 16-byte aligned rows), tiles of 128
-// rows x 32 floats, zero outside; the encoder comes from the driver through the runtime
-typedef CUresult (*EncodeTiledFn)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
-                                  const cuuint64_t *, const cuuint32_t *, const cuuint32_t *, CUtensorMapInterleave,
-                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
-
-cudaError_t rows_tensor_map(CUtensorMap *m, const float *h, long R, int n)
-{
-    static EncodeTiledFn enc = nullptr;
-    if (!enc) {
-        void *p = nullptr;
-        cudaDriverEntryPointQueryResult q;
-        const cudaError_t e =
-            cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q);
-        if (e != cudaSuccess) return e;
-        if (q != cudaDriverEntryPointSuccess || !p) return cudaErrorNotSupported;
-        enc = (EncodeTiledFn)p;
-    }
-    const cuuint64_t dims[2] = {(cuuint64_t)n, (cuuint64_t)R};
-    const cuuint64_t strides[1] = {(cuuint64_t)n * sizeof(float)};
-    const cuuint32_t box[2] = {(cuuint32_t)kDftKc, (cuuint32_t)kTcRows};
-    const cuuint32_t estr[2] = {1, 1};
-    const CUresult r = enc(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, (void *)h, dims, strides, box, estr,
-                           CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
-                           CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
-    return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
-}
-
 // launch of fno_rowdft_tc over R rows of n floats at h (n a multiple of 32), with its
 // tensor map and dynamic shared memory (the limit raised once)
 cudaError_t launch_rowdft_tc(const float *h, const __nv_bfloat16 *Bt, float2 *X, long R, int n, int *err,
@@ -443,7 +416,8 @@ cudaError_t launch_rowdft_tc(const float *h, const __nv_bfloat16 *Bt, float2 *X,
         attr = true;
     }
     CUtensorMap m;
-    const cudaError_t e = rows_tensor_map(&m, h, R, n);
+    // R rows of n floats, tiles of 128 rows x 32 floats, zero past the last row
+    const cudaError_t e = fch_tmap_f32_2d(&m, h, (uint64_t)n, (uint64_t)R, (uint64_t)n * 4, kDftKc, kTcRows);
     if (e != cudaSuccess) return e;
     fno_rowdft_tc<<<(unsigned)((R + kTcRows - 1) / kTcRows), 128, kRowdftSmem, s>>>(m, Bt, X, (int)R, n, err);
     return cudaGetLastError();

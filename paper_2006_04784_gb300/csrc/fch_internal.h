@@ -88,6 +88,7 @@ struct fch_kparams {
     int tail_op;                    // < 0: none; else the control op the pass's last block runs
     double tail_arg;
     unsigned int *ticket;           // arrival counter of the blocks of a pass (reset by the last)
+    int *err;                       // set to 1 by a pass whose bounded wait on a bulk copy ran out (may be null)
     fch_consts<float> cf;
     fch_consts<double> cd;
     fch_consts<fch::df> cdf;

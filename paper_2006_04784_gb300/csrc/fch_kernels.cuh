@@ -533,6 +533,62 @@ template <int THREADS, int LOGN, int MODE> constexpr int col_min_blocks()
                : pass_min_blocks<THREADS, LOGN>();
 }
 
+// Pair 0 of a column tile of an N-point transform (columns kx = 0 in slot s0 and
+// kx = N/2 in slot s1 of a tile whose row n sits at skew(n) * nc), work item ky in [0, N/2]: rows ky and -ky of
+// both columns (one row where they coincide). Each of the two columns is the
+// transform of a real pair of its own, so the Hermitian split pairs row ky with row
+// -ky of the same column.
+template <typename T, int MODE>
+__device__ __forceinline__ void pair0_item(const fch_kparams &kp, const fch_consts<T> &K, const fch_coef<T> &co,
+                                           const ColBufs<typename CT<T>::t> &bf, typename CT<T>::t *tile, int N,
+                                           int nc, int s0, int s1, int ky, bool inv, T *red)
+{
+    typedef typename CT<T>::t C;
+    typedef ColTraits<MODE> TR;
+    const int mky = (N - ky) & (N - 1);
+    const int rk = skew(ky) * nc, rm = skew(mky) * nc;
+    const int nrow = (ky == 0 || ky == (N >> 1)) ? 1 : 2;
+    C za[2], zb[2];
+    za[0] = tile[rk + s0];
+    za[1] = tile[rm + s0];
+    zb[0] = tile[rk + s1];
+    zb[1] = tile[rm + s1];
+    C outa[2], outb[2];
+#pragma unroll
+    for (int side = 0; side < 2; side++) {
+        const int kx = side ? (N >> 1) : 0;
+#pragma unroll
+        for (int rr = 0; rr < 2; rr++) {
+            if (rr >= nrow) break;
+            const int kyy = rr ? mky : ky;
+            const C zr = side ? zb[rr] : za[rr];
+            const C zo = side ? zb[rr ^ 1] : za[rr ^ 1];
+            C A = mk<C>(0, 0), B = mk<C>(0, 0);
+            if (TR::FWD) {
+                const C z1 = cconj(zo);
+                A = cscale_p2(cadd(zr, z1), (T)0.5);
+                const C dm = csub(zr, z1);
+                B = mk<C>(mul_p2(dm.y, (T)0.5), mul_p2(dm.x, (T)-0.5));
+            }
+            C Co = mk<C>(0, 0), Do = mk<C>(0, 0);
+            spec_elem<T, MODE>(kp, K, co, bf, kx, kyy, A, B, Co, Do, red);
+            const C o = mk<C>(Co.x - Do.y, Co.y + Do.x);
+            if (side)
+                outb[rr] = o;
+            else
+                outa[rr] = o;
+        }
+    }
+    if (inv) {
+        tile[rk + s0] = outa[0];
+        tile[rk + s1] = outb[0];
+        if (nrow == 2) {
+            tile[rm + s0] = outa[1];
+            tile[rm + s1] = outb[1];
+        }
+    }
+}
+
 // LOGN > 0: the grid size is a compile-time constant (N = 2^LOGN >= 512), so the
 // index arithmetic of the transforms folds into immediates; LOGN = 0 reads N and P
 // from the parameters.
@@ -636,47 +692,7 @@ col_pass(const fch_kparams kp)
             }
         } else {
             if (ky > (N >> 1)) continue;
-            // columns kx = 0 (slot s0) and kx = N/2 (slot s1), rows ky and -ky
-            const int nrow = (ky == 0 || ky == (N >> 1)) ? 1 : 2;
-            C za[2], zb[2];
-            za[0] = tile[rk + s0];
-            za[1] = tile[rm + s0];
-            zb[0] = tile[rk + s1];
-            zb[1] = tile[rm + s1];
-            C outa[2], outb[2];
-#pragma unroll
-            for (int side = 0; side < 2; side++) {
-                const int kx = side ? (N >> 1) : 0;
-#pragma unroll
-                for (int rr = 0; rr < 2; rr++) {
-                    if (rr >= nrow) break;
-                    const int kyy = rr ? mky : ky;
-                    const C zr = side ? zb[rr] : za[rr];
-                    const C zo = side ? zb[rr ^ 1] : za[rr ^ 1];
-                    C A = mk<C>(0, 0), B = mk<C>(0, 0);
-                    if (TR::FWD) {
-                        const C z1 = cconj(zo);
-                        A = cscale_p2(cadd(zr, z1), (T)0.5);
-                        const C dm = csub(zr, z1);
-                        B = mk<C>(mul_p2(dm.y, (T)0.5), mul_p2(dm.x, (T)-0.5));
-                    }
-                    C Co = mk<C>(0, 0), Do = mk<C>(0, 0);
-                    spec_elem<T, MODE>(kp, K, co, bf, kx, kyy, A, B, Co, Do, red);
-                    const C o = mk<C>(Co.x - Do.y, Co.y + Do.x);
-                    if (side)
-                        outb[rr] = o;
-                    else
-                        outa[rr] = o;
-                }
-            }
-            if (inv) {
-                tile[rk + s0] = outa[0];
-                tile[rk + s1] = outb[0];
-                if (nrow == 2) {
-                    tile[rm + s0] = outa[1];
-                    tile[rm + s1] = outb[1];
-                }
-            }
+            pair0_item<T, MODE>(kp, K, co, bf, tile, N, nc, s0, s1, ky, inv, red);
         }
     }
     if (has_red) {

@@ -2,6 +2,8 @@
 // Included once per precision by fch_f64.cu / fch_f32.cu with FCH_T and FCH_SUFFIX set.
 #include "fch_kernels.cuh"
 #include "fch_warpfft.cuh"
+#include "fch_colt.cuh"
+#include "fch_tmap.h"
 
 namespace {
 
@@ -105,8 +107,54 @@ template <typename T, int M> cudaError_t launch_col_cl(const fch_kparams &kp, cu
     return launch_pass(f, dim3(1024, pair_grid(kp)), dim3(128), smem, s, kp);
 }
 
+// N = 1024, single precision, the column passes of standalone transform plans (which
+// carry an error word): the persistent TMA-staged kernel, as many blocks as are
+// resident at once; the inverse needs 16-byte aligned half spectra (bulk copies)
+template <int M> bool col_t_applies(const fch_kparams &kp)
+{
+    if (M != CM_FWD_STORE && M != CM_INV_LOAD) return false;
+    if (!kp.err || kp.npairs < 1 || kp.N != 1024 || kp.tile_col != 0 || (kp.flags & FCH_FL_F64IO)) return false;
+    if (M == CM_INV_LOAD)
+        return kp.in0 && !(((uintptr_t)kp.in0 | (uintptr_t)kp.in1 | (uintptr_t)kp.pstride_in) & 15);
+    return true;
+}
+
+template <int M> cudaError_t launch_col_t(const fch_kparams &kp, cudaStream_t s)
+{
+    if constexpr (M == CM_FWD_STORE || M == CM_INV_LOAD) {
+        static int resident = 0;
+        if (!resident) {
+            int dev = 0, sms = 0, per = 0;
+            cudaError_t e = cudaFuncSetAttribute(fch::col_pass_t<M>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                 fch::kColtSmem);
+            if (e == cudaSuccess) e = cudaGetDevice(&dev);
+            if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+            if (e == cudaSuccess)
+                e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, fch::col_pass_t<M>, fch::kColtThreads,
+                                                                  fch::kColtSmem);
+            if (e != cudaSuccess) return e;
+            if (per < 1) return cudaErrorInvalidConfiguration;
+            resident = sms * per;
+        }
+        const long np = pair_grid(kp), tiles = np * 256;
+        // Z of the launch's pairs: np * N rows of 2N floats, boxes of 256 rows x 8 floats
+        CUtensorMap m;
+        cudaError_t e = fch_tmap_f32_2d(&m, kp.Z, 2048, (uint64_t)np * 1024, 8192, 8, 256);
+        if (e != cudaSuccess) return e;
+        cudaLaunchConfig_t cfg = {};
+        cudaLaunchAttribute at[1];
+        fch_pdl_config(cfg, at, dim3((unsigned)(tiles < resident ? tiles : resident)), dim3(fch::kColtThreads),
+                       fch::kColtSmem, s, kp.pdl != 0);
+        return cudaLaunchKernelEx(&cfg, fch::col_pass_t<M>, kp, m);
+    }
+    return cudaErrorInvalidValue;
+}
+
 template <typename T, int M> cudaError_t launch_col(const fch_kparams &kp, cudaStream_t s)
 {
+    if constexpr (sizeof(T) == 4) {
+        if (col_t_applies<M>(kp)) return launch_col_t<M>(kp, s);
+    }
     if (warp_path<T>() && kp.N == 1024 && kp.tw2 && kp.tile_col == -2) return launch_col_w<M>(kp, s);
     if constexpr (sizeof(T) == 8) {
         if (kp.N == 1024 && kp.tile_col == 0) return launch_col_cl<T, M>(kp, s);

@@ -144,6 +144,12 @@ row_pass_w(const fch_kparams kp)
             const C zn = __ldg(Rn + lane + 32 * n2);
             v[n2] = plain ? zn : cadd(zn, cscale(csub(zn, __ldg(Rm + lane + 32 * n2)), g));
         }
+    } else if (MODE == RM_R2C_LOAD && !f64io && kp.in1) {
+        // two float fields (the common case, without a branch per element)
+        const float *a = (const float *)pair_in(kp.in0, kp) + (long)y * N + lane;
+        const float *b = (const float *)pair_in(kp.in1, kp) + (long)y * N + lane;
+#pragma unroll
+        for (int n2 = 0; n2 < 32; n2++) v[n2] = mk<C>(__ldcs(a + 32 * n2), __ldcs(b + 32 * n2));
     } else if (MODE == RM_R2C_LOAD) {
         const void *in0 = pair_in(kp.in0, kp), *in1 = pair_in(kp.in1, kp);
 #pragma unroll
@@ -181,12 +187,26 @@ row_pass_w(const fch_kparams kp)
         const int slot = kp.src == FCH_SRC_UNEW ? cs->iu_new : (kp.src == 5 ? cs->iu_m : cs->iu_n);
         store = (C *)kp.Rs[slot] + (long)y * N;
     }
+    if (MODE == RM_C2R_STORE && !f64io && kp.out0 && kp.out1) {
+        // two float fields (the common case, without a branch per element)
+        float *o0 = (float *)pair_out(kp.out0, kp) + (long)y * N + lane;
+        float *o1 = (float *)pair_out(kp.out1, kp) + (long)y * N + lane;
+#pragma unroll
+        for (int k1 = 0; k1 < 32; k1++) {
+            __stcs(o0 + 32 * k1, v[k1].x);
+            __stcs(o1 + 32 * k1, v[k1].y);
+        }
+        return;
+    }
+    if (MODE == RM_F && store) {
+#pragma unroll
+        for (int k1 = 0; k1 < 32; k1++) store[lane + 32 * k1] = v[k1];
+    }
     if (MODE != RM_R2C_LOAD) {
         const fch_consts<float> &K = kp.cf;
 #pragma unroll
         for (int k1 = 0; k1 < 32; k1++) {
             const int x = lane + 32 * k1;
-            if (MODE == RM_F && store) store[x] = v[k1];
             const float u = v[k1].x, lu = v[k1].y;
             if (MODE == RM_C2R_STORE) {
                 const long g = (long)y * N + x;

@@ -36,7 +36,7 @@ EXPORTS = ["fch_status_string", "fch_last_cuda_error", "fch_params_default", "fc
            "fch_fno_backward", "fch_fno_adam", "fch_step_psd_from", "fch_run_fixed",
            "fch_adaptive_trial_info", "fch_get_history_device", "fch_adaptive_enqueue_psd_from",
            "fch_ensemble_run_adaptive_each", "fch_autotune_step", "fch_step_from", "fch_fno_set_bf16",
-           "fch_alu_peak", "fch_fno_learned_start", "fch_adaptive_enqueue_from"]
+           "fch_alu_peak", "fch_fno_learned_start", "fch_adaptive_enqueue_from", "fch_fft_plan_status"]
 NCOL, NROW = 10, 8
 NPASS = NCOL + NROW + 1
 PASS_NAMES = (["col_fwd_store", "col_inv_load", "col_start", "col_imex_solve", "col_f_finish",
@@ -161,6 +161,7 @@ def lib():
         L.fch_fft_plan_destroy.argtypes = [vp]
         L.fch_fft_r2c.argtypes = [vp, vp, vp, C.c_int]
         L.fch_fft_c2r.argtypes = [vp, vp, vp, C.c_int]
+        L.fch_fft_plan_status.argtypes = [vp]
         L.fch_adaptive_begin.argtypes = [vp, C.c_int, C.c_double, C.c_double]
         L.fch_adaptive_enqueue.argtypes = [vp, C.c_int]
         L.fch_adaptive_end.argtypes = [vp, C.POINTER(Stats)]
@@ -454,6 +455,11 @@ class FFTPlan:
     def c2r(self, X, x):
         b = x.shape[0] if x.dim() == 3 else 1
         _check(lib().fch_fft_c2r(self._h, _tensor_ptr(X), _tensor_ptr(x), b), "fch_fft_c2r")
+
+    def status(self):
+        """fch_fft_plan_status: synchronizes the plan's stream; raises if a pass's
+        bounded wait on a bulk copy ran out since the last call"""
+        _check(lib().fch_fft_plan_status(self._h), "fch_fft_plan_status")
 
 
 class _Member(Context):

@@ -92,6 +92,7 @@ def test_fft_batched_launches_match_single_fields(n, prec, batch):
     plan.r2c(xt, X)
     back = torch.empty_like(xt)
     plan.c2r(X, back)
+    plan.status()
     for b in sorted({0, 2 * (batch // 4), batch - 3, batch - 1}):
         m = 1 if b == batch - 1 else 2
         X1 = torch.empty((m, n // 2 + 1, n), dtype=cdt, device=DEV)
@@ -112,29 +113,56 @@ def test_fft_batched_launches_match_single_fields(n, prec, batch):
 
 @pytest.mark.parametrize("n,prec", [(1024, 0), (2048, 0), (1024, 1), (2048, 1)])
 def test_fft_full_size_sampled_outputs(n, prec):
+    # three fields: a pair (the Hermitian split into both half spectra) and an odd one
     rng = np.random.default_rng(7)
-    x = rng.standard_normal((n, n))
+    x = rng.standard_normal((3, n, n))
     dt = torch.float64 if prec == 0 else torch.float32
     cdt = torch.complex128 if prec == 0 else torch.complex64
     xt = torch.tensor(x, dtype=dt, device=DEV)
-    X = torch.empty((1, n // 2 + 1, n), dtype=cdt, device=DEV)
+    X = torch.empty((3, n // 2 + 1, n), dtype=cdt, device=DEV)
     plan = fch.FFTPlan(n, prec)
-    plan.r2c(xt[None], X)
-    torch.cuda.synchronize()
-    Xh = X[0].cpu().numpy()
+    plan.r2c(xt, X)
+    plan.status()
+    Xh = X.cpu().numpy()
     idx = np.arange(n)
     scale = math.sqrt(n * n)  # typical |X| of unit white noise
-    for kx, ky in [(0, 0), (1, 0), (0, 1), (n // 2, 0), (n // 2, n // 2), (3, n - 5),
-                   (n // 2 - 1, 17), (200, 999 % n)]:
-        ex = np.exp(-2j * np.pi * kx * idx / n)
-        ey = np.exp(-2j * np.pi * ky * idx / n)
-        ref = ey @ x @ ex  # direct DFT of one output
-        tol = 1e-12 if prec == 0 else 3e-6
-        assert abs(Xh[kx, ky] - ref) <= tol * scale * math.log2(n)
+    tol = 1e-12 if prec == 0 else 3e-6
+    for f in range(3):
+        for kx, ky in [(0, 0), (1, 0), (0, 1), (n // 2, 0), (n // 2, n // 2), (3, n - 5),
+                       (n // 2 - 1, 17), (200, 999 % n), (2, 3), (n // 2 - 2, n - 1)]:
+            ex = np.exp(-2j * np.pi * kx * idx / n)
+            ey = np.exp(-2j * np.pi * ky * idx / n)
+            ref = ey @ x[f] @ ex  # direct DFT of one output
+            assert abs(Xh[f, kx, ky] - ref) <= tol * scale * math.log2(n), (f, kx, ky)
     back = torch.empty_like(xt)
-    plan.c2r(X, back[None])
-    torch.cuda.synchronize()
+    plan.c2r(X, back)
+    plan.status()
     assert np.abs(back.cpu().numpy() - x).max() <= (1e-12 if prec == 0 else 3e-5)
+
+
+def test_fft_fp32_1024_staged_inverse_columns_match_the_plain_kernel():
+    # At N = 1024 in single precision a plan's inverse column pass fetches the half
+    # spectra by bulk copy when they are 16-byte aligned; spectra one complex64 off
+    # that alignment take the plain shared-memory kernel. Both run the same
+    # arithmetic: the fields agree bit for bit (the pairs of a multi-pair launch and
+    # the odd last field), and the plan reports no device-side timeout.
+    n, batch = 1024, 5
+    rng = np.random.default_rng(11)
+    x = torch.tensor(rng.standard_normal((batch, n, n)), dtype=torch.float32, device=DEV)
+    plan = fch.FFTPlan(n, 1)
+    X = torch.empty((batch, n // 2 + 1, n), dtype=torch.complex64, device=DEV)
+    plan.r2c(x, X)
+    store = torch.empty(batch * (n // 2 + 1) * n + 2, dtype=torch.complex64, device=DEV)
+    Xu = store[1:1 + batch * (n // 2 + 1) * n].view(batch, n // 2 + 1, n)
+    Xu.copy_(X)
+    assert Xu.data_ptr() % 16 == 8
+    ya, yu = torch.empty_like(x), torch.empty_like(x)
+    plan.c2r(X, ya)
+    plan.c2r(Xu, yu)
+    plan.status()
+    assert torch.equal(ya, yu)
+    assert (ya - x).abs().max().item() <= 3e-5 * x.abs().max().item()
+    plan.close()
 
 
 # --------------------------------------------------------------------------- F(u)
