@@ -13,8 +13,12 @@
 //    radix-8 stage reads it there (rows t + 128 r of column c: a warp reads 256
 //    contiguous bytes) and writes the skewed tile, after which the stage is free;
 //  - inverse (C2R): the rows kx of the two half spectra (8 KB each, cp.async.bulk)
-//    of the tile's two column pairs; the spectral stage reads them there. The tile of
-//    pair 0 (kx = 0 and N/2 need four rows) reads its spectra from global memory.
+//    of the tile's two column pairs; the first radix-8 stage forms its inputs from
+//    them there (the spectral stage folded into it) and writes the skewed tile. The
+//    tile of pair 0 (kx = 0 and N/2 need four rows) reads its spectra from global
+//    memory and takes the separate spectral stage.
+// The forward spectral stage gives each thread rows ky and -ky of the tile, read as
+// whole 32-byte rows, and the four work items that touch only them.
 // Copies complete in bytes on the block's mbarrier; a wait that runs out of time (1 s)
 // sets *kp.err, and the block stops after waiting (bounded) for the copy it started.
 #pragma once
@@ -180,29 +184,34 @@ __global__ void __launch_bounds__(kColtThreads, 2) col_pass_t(const fch_kparams 
                 }
             }
         } else {
-            // spectral stage: the two half spectra into the four columns. A thread owns
-            // rows ky and -ky of the tile (written whole) and the four work items that
-            // write them; the spectra come from the stage (unit stride in ky).
             if (p0 > 0) {
-                for (int ky = threadIdx.x; ky <= (N >> 1); ky += NT) {
-                    const int mky = (N - ky) & (N - 1);
-                    C rk[4], rm[4];
+                // the spectral stage fused into the first radix-8 stage: thread (c, t)
+                // forms rows t + 128 r of column c straight from the staged spectra. With
+                // (C, D) the two half spectra over N^2, slot 0 (column kx) of a pair holds
+                // C + i D at (kx, ky) and slot 1 (column N - kx) conj(C) + i conj(D) taken
+                // at (kx, -ky).
+                const int pp = c >> 1;
+                const bool odd = c & 1;
+                const C *a = stage + 2 * pp * N, *b = stage + (2 * pp + 1) * N;
+                C v[8];
 #pragma unroll
-                    for (int pp = 0; pp < 2; pp++) {
-                        const C *a = stage + 2 * pp * N, *b = stage + (2 * pp + 1) * N;
-                        const C ck = cscale(a[ky], inv_n2), cm = cscale(a[mky], inv_n2);
-                        const C dk = two ? cscale(b[ky], inv_n2) : mk<C>(0.f, 0.f);
-                        const C dm = two ? cscale(b[mky], inv_n2) : mk<C>(0.f, 0.f);
-                        // item (pp, ky) writes slot 0 of row ky and slot 1 of row -ky; item (pp, -ky)
-                        // slot 0 of row -ky and slot 1 of row ky
-                        rk[2 * pp] = mk<C>(ck.x - dk.y, ck.y + dk.x);
-                        rm[2 * pp + 1] = mk<C>(ck.x + dk.y, dk.x - ck.y);
-                        rm[2 * pp] = mk<C>(cm.x - dm.y, cm.y + dm.x);
-                        rk[2 * pp + 1] = mk<C>(cm.x + dm.y, dm.x - cm.y);
-                    }
-                    store_row4(tile + skew(ky) * NC, rk);
-                    if (mky != ky) store_row4(tile + skew(mky) * NC, rm);
+                for (int r = 0; r < 8; r++) {
+                    const int ky = t + 128 * r, kk = odd ? (N - ky) & (N - 1) : ky;
+                    const C Co = cscale(a[kk], inv_n2);
+                    const C Do = two ? cscale(b[kk], inv_n2) : mk<C>(0.f, 0.f);
+                    v[r] = odd ? mk<C>(Co.x + Do.y, Do.x - Co.y) : mk<C>(Co.x - Do.y, Co.y + Do.x);
                 }
+                bfly8<+1>(v);
+#pragma unroll
+                for (int r = 0; r < 8; r++) tile[skew(8 * t + r) * NC + c] = v[r];
+                __syncthreads(); // stage consumed, tile written
+                if (threadIdx.x == 0) {
+                    fch::tc::fence_async_smem(); // the stage's reads come before the next copy's writes
+                    if (g + gridDim.x < ntiles) fetch(g + gridDim.x);
+                }
+                fft_stage<+1, 3, false>(tile, N, LOGN, NC, c, tw, t, 8, 3);
+                fft_stage<+1, 3, false>(tile, N, LOGN, NC, c, tw, t, 64, 6);
+                fft_stage<+1, 1, false>(tile, N, LOGN, NC, c, tw, t, 512, 9);
             } else {
                 // pair 0 (columns 0 and N/2) and pair 1, item by item from global memory
 #pragma unroll 1
@@ -220,21 +229,20 @@ __global__ void __launch_bounds__(kColtThreads, 2) col_pass_t(const fch_kparams 
                         pair0_item<float, MODE>(kp, K, co, bf, tile, N, NC, s0, s1, ky, true, red);
                     }
                 }
+                __syncthreads();
+                if (threadIdx.x == 0) { // the stage is idle here
+                    fch::tc::fence_async_smem();
+                    if (g + gridDim.x < ntiles) fetch(g + gridDim.x);
+                }
+                fft_smem<+1, false>(tile, N, LOGN, NC, c, tw, t);
             }
-            __syncthreads(); // stage consumed, tile written
-            if (threadIdx.x == 0) {
-                fch::tc::fence_async_smem();
-                if (g + gridDim.x < ntiles) fetch(g + gridDim.x);
-            }
-            fft_smem<+1, false>(tile, N, LOGN, NC, c, tw, t);
             // the four columns back to Z: half a 32-byte row per thread and store
             C *Z = (C *)kp.Z + pr * N * N;
 #pragma unroll
             for (int k = 0; k < 4; k++) {
                 const int i = threadIdx.x + k * NT;
                 const int n = i >> 1, h = i & 1;
-                __stcg((float4 *)(Z + (long)n * N + 2 * p0 + 2 * h),
-                       *(const float4 *)(tile + skew(n) * NC + 2 * h));
+                __stcg((float4 *)(Z + (long)n * N + 2 * p0 + 2 * h), *(const float4 *)(tile + skew(n) * NC + 2 * h));
             }
         }
         __syncthreads(); // the tile is read before the next tile's first writes
