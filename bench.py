@@ -476,11 +476,14 @@ def fno_forward_times(args, sizes=(128, 256, 512, 1024), reps=10):
     net.set_params(T.init_params(net, seed=0))
     out = {"network": "32 channels, 4 layers, 16 modes, 64 projection channels", "unit": "ms per forward pass",
            "modes": {"0": "fp32", "1": "bf16 weights", "2": "bf16 weights, truncated DFTs, tensor cores"}}
+    if args.fno_forward_n:
+        sizes = (args.fno_forward_n,)
+    modes = (args.fno_forward_mode,) if args.fno_forward_mode >= 0 else (0, 1, 2)
     for n in sizes:
         a = torch.randn((1, 2, n, n), device=dev, generator=torch.Generator(device=dev).manual_seed(n))
         y = torch.empty((1, n, n), device=dev)
         row = {}
-        for mode in (0, 1, 2):
+        for mode in modes:
             net.set_bf16(mode)
             for _ in range(3):
                 net.forward(a, y)
@@ -1473,6 +1476,10 @@ def main():
     ap.add_argument("--fno-iters", type=int, default=1500)
     ap.add_argument("--fno-lr", type=float, default=1e-3)
     ap.add_argument("--fno-t-adaptive", type=float, default=2e-2)
+    ap.add_argument("--fno-forward-n", type=int, default=0,
+                    help="--fno-forward: one grid size only (0: 128, 256, 512, 1024)")
+    ap.add_argument("--fno-forward-mode", type=int, default=-1,
+                    help="--fno-forward: one mode only (0 FP32, 1 bf16 weights, 2 tensor cores; -1: all)")
     ap.add_argument("--fno-forward", action="store_true",
                     help="only the FNO forward pass time per grid and mode (FP32, BF16 weights, truncated DFTs)")
     ap.add_argument("--fft-only", action="store_true",

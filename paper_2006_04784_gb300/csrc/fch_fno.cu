@@ -39,6 +39,33 @@ namespace {
 constexpr int kMaxW2 = 128;  // hidden channels of the projection
 
 __device__ __forceinline__ float gelu(float x) { return 0.5f * x * (1.0f + erff(x * 0.70710678118654752f)); }
+
+// GELU for the tensor-core inference kernels, with erf from the rational approximation
+// of Abramowitz and Stegun, Handbook of Mathematical Functions, eq. 7.1.28: for u >= 0,
+// erf(u) = 1 - (1 + a1 u + a2 u^2 + ... + a6 u^6)^-16 with |error| <= 3e-7 (one
+// reciprocal and sixteen multiplies or multiply-adds instead of the library's erff; the
+// sign by symmetry). In float, 1 - p^-16 loses digits near u = 0, so erf comes out
+// within about 2e-6 absolute: GELU within |x| 1e-6. Its outputs feed bfloat16 operands
+// (relative rounding 2^-9) or FP32 sums with bfloat16 weights, whose rounding is larger.
+__device__ __forceinline__ float gelu_as(float x)
+{
+    const float u = fminf(fabsf(x) * 0.70710678118654752f, 8.0f); // erf(8) is 1 in float; p stays finite
+    float p = 0.0000430638f;
+    p = fmaf(p, u, 0.0002765672f);
+    p = fmaf(p, u, 0.0001520143f);
+    p = fmaf(p, u, 0.0092705272f);
+    p = fmaf(p, u, 0.0422820123f);
+    p = fmaf(p, u, 0.0705230784f);
+    p = fmaf(p, u, 1.0f);
+    float r = __fdividef(1.0f, p); // p >= 1
+    r = fmaf(r, fmaf(-p, r, 1.0f), r); // one Newton step: 1/p to about an ulp
+    r = r * r;
+    r = r * r;
+    r = r * r;
+    r = r * r; // p^-16
+    const float e = copysignf(1.0f - r, x);
+    return 0.5f * x * (1.0f + e);
+}
 __device__ __forceinline__ float gelu_grad(float x)
 {
     return 0.5f * (1.0f + erff(x * 0.70710678118654752f)) + x * 0.39894228040143268f * expf(-0.5f * x * x);
@@ -81,6 +108,34 @@ __global__ void fno_lift(const float *__restrict__ a, const WT *__restrict__ P, 
         float acc = bs[c];
         for (int i = 0; i < cin; i++) acc += ps[c * cin + i] * in[i];
         h[((long)b * W + c) * n2 + p] = acc;
+    }
+}
+
+// the same with the channel counts fixed at compile time (the tensor-core forward
+// pass): loops unrolled, each output channel one multiply-add chain and one store at a
+// running pointer
+template <typename WT, int W, int CIN>
+__global__ void __launch_bounds__(256) fno_lift_t(const float *__restrict__ a, const WT *__restrict__ P,
+                                                  const WT *__restrict__ bP, float *__restrict__ h, long pts, int n2)
+{
+    __shared__ float ps[W * CIN], bs[W];
+    for (int i = threadIdx.x; i < W * CIN; i += blockDim.x) ps[i] = wld(P, i);
+    for (int i = threadIdx.x; i < W; i += blockDim.x) bs[i] = wld(bP, i);
+    __syncthreads();
+    const long t = (long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= pts) return;
+    const long b = t / n2, p = t - b * n2;
+    float in[CIN];
+#pragma unroll
+    for (int i = 0; i < CIN; i++) in[i] = __ldcs(a + (b * CIN + i) * n2 + p);
+    float *hp = h + b * W * n2 + p;
+#pragma unroll
+    for (int c = 0; c < W; c++) {
+        float acc = bs[c];
+#pragma unroll
+        for (int i = 0; i < CIN; i++) acc = fmaf(ps[c * CIN + i], in[i], acc);
+        *hp = acc;
+        hp += n2;
     }
 }
 
@@ -423,46 +478,48 @@ cudaError_t launch_rowdft_tc(const float *h, const __nv_bfloat16 *Bt, float2 *X,
     return cudaGetLastError();
 }
 
-// Y[f][kyi][kx] = sum_y X[f][y][kx] e^{-2 pi i ky y / n}: one block per (field f, kx),
-// threads over y, the 2M-1 sums reduced in a fixed order (warp shuffles, then warps)
+// Y[f][kyi][kx] = sum_y X[f][y][kx] e^{-2 pi i ky y / n}: one block per (field f, kx).
+// The column X[f][.][kx] and the twiddle table (cos, sin)(2 pi j / n) go to shared
+// memory; eight threads share each retained ky (thread j of the eight sums the y = j
+// mod 8), then three shuffle levels add the eight partial sums in a fixed order.
+// n a multiple of 128; dynamic shared memory: 2 n float2.
 template <int MM>
 __global__ void __launch_bounds__(256) fno_coldft(const float2 *__restrict__ X, const float2 *__restrict__ tw1,
                                                   float2 *__restrict__ Y, int n)
 {
     constexpr int K2 = 2 * MM - 1;
-    __shared__ float2 part[8][K2];
+    static_assert(K2 <= 32, "eight threads a retained ky in 256 threads");
+    extern __shared__ float2 cd_sm[];
+    float2 *col = cd_sm, *tw = cd_sm + n;
     const int f = blockIdx.x, kx = blockIdx.y, tid = threadIdx.x;
-    float2 acc[K2];
-#pragma unroll
-    for (int k = 0; k < K2; k++) acc[k] = make_float2(0.f, 0.f);
     for (int y = tid; y < n; y += 256) {
-        const float2 v = X[((long)f * n + y) * 16 + kx];
-#pragma unroll
-        for (int k = 0; k < K2; k++) {
-            const int ky = k < MM ? k : n - (k - MM + 1);
-            const float2 w = tw1[(int)(((long)ky * y) & (n - 1))]; // (cos, sin)(2 pi ky y / n)
-            acc[k].x += v.x * w.x + v.y * w.y;
-            acc[k].y += v.y * w.x - v.x * w.y;
-        }
+        col[y] = X[((long)f * n + y) * 16 + kx];
+        tw[y] = tw1[y];
     }
-#pragma unroll
-    for (int k = 0; k < K2; k++)
-        for (int o = 16; o > 0; o >>= 1) {
-            acc[k].x += __shfl_down_sync(0xffffffffu, acc[k].x, o);
-            acc[k].y += __shfl_down_sync(0xffffffffu, acc[k].y, o);
-        }
-    if ((tid & 31) == 0)
-#pragma unroll
-        for (int k = 0; k < K2; k++) part[tid >> 5][k] = acc[k];
     __syncthreads();
-    if (tid < K2) {
-        float2 sum = make_float2(0.f, 0.f);
-        for (int w = 0; w < 8; w++) {
-            sum.x += part[w][tid].x;
-            sum.y += part[w][tid].y;
+    const int k = tid >> 3, j = tid & 7; // k = K2 (the last eight threads) computes nothing kept
+    const int ky = k < MM ? k : n - (k - MM + 1);
+    // the twiddle of y + 8 is the twiddle of y times (cos, sin)(2 pi 8 ky / n): a table
+    // read starts each run of 16 such steps (the reads of a warp would meet bank
+    // conflicts at stride ky in the table; the products stay within ~16 roundings)
+    const float2 step = tw[(8 * ky) & (n - 1)];
+    float2 acc = make_float2(0.f, 0.f);
+    for (int y0 = j; y0 < n; y0 += 128) {
+        float2 w = tw[(ky * y0) & (n - 1)];
+#pragma unroll
+        for (int r = 0; r < 16; r++) {
+            const float2 v = col[y0 + 8 * r];
+            acc.x = fmaf(v.x, w.x, fmaf(v.y, w.y, acc.x));
+            acc.y = fmaf(v.y, w.x, fmaf(-v.x, w.y, acc.y));
+            w = make_float2(fmaf(w.x, step.x, -w.y * step.y), fmaf(w.x, step.y, w.y * step.x));
         }
-        Y[((long)f * K2 + tid) * MM + kx] = sum;
     }
+#pragma unroll
+    for (int o = 4; o > 0; o >>= 1) {
+        acc.x += __shfl_xor_sync(0xffffffffu, acc.x, o);
+        acc.y += __shfl_xor_sync(0xffffffffu, acc.y, o);
+    }
+    if (j == 0 && k < K2) Y[((long)f * K2 + k) * MM + kx] = acc;
 }
 
 // Z[b][o][kyi][kx] = sum_i R[m][o][i] Y[b][i][kyi][kx], m = kx (2M-1) + kyi
@@ -485,28 +542,34 @@ __global__ void fno_mix_modes(const float2 *__restrict__ Y, const WT *__restrict
     Z[(((long)b * W + o) * K2 + kyi) * M + kx] = make_float2(re, im);
 }
 
-// V[f][y][kx] = sum_kyi Z[f][kyi][kx] e^{+2 pi i ky y / n}
+// V[f][y][kx] = sum_kyi Z[f][kyi][kx] e^{+2 pi i ky y / n}: one block per (field f, 64
+// rows y); Z[f] and the twiddle table (cos, sin)(2 pi j / n) in shared memory, thread
+// (y, kx) four outputs. Dynamic shared memory: n float2.
 template <int MM>
-__global__ void fno_icoldft(const float2 *__restrict__ Z, const float2 *__restrict__ tw1, float2 *__restrict__ V,
-                            long nf, int n)
+__global__ void __launch_bounds__(256) fno_icoldft(const float2 *__restrict__ Z, const float2 *__restrict__ tw1,
+                                                   float2 *__restrict__ V, long nf, int n)
 {
-    constexpr int K2 = 2 * MM - 1;
-    const long t = (long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (t >= nf * n * MM) return;
-    const int kx = (int)(t % MM);
-    const long fy = t / MM;
-    const int y = (int)(fy % n);
-    const long f = fy / n;
-    float re = 0.f, im = 0.f;
+    constexpr int K2 = 2 * MM - 1, YB = 64;
+    __shared__ float2 zs[K2 * MM];
+    extern __shared__ float2 ic_tw[];
+    const int nyb = n / YB;
+    const long f = blockIdx.x / nyb;
+    const int y0 = (int)(blockIdx.x % nyb) * YB, tid = threadIdx.x;
+    for (int i = tid; i < K2 * MM; i += 256) zs[i] = Z[f * K2 * MM + i];
+    for (int i = tid; i < n; i += 256) ic_tw[i] = tw1[i];
+    __syncthreads();
+    for (int i = tid; i < YB * MM; i += 256) {
+        const int y = y0 + i / MM, kx = i % MM;
+        float re = 0.f, im = 0.f;
 #pragma unroll
-    for (int k = 0; k < K2; k++) {
-        const int ky = k < MM ? k : n - (k - MM + 1);
-        const float2 z = Z[(f * K2 + k) * MM + kx];
-        const float2 w = tw1[(int)(((long)ky * y) & (n - 1))];
-        re += z.x * w.x - z.y * w.y;
-        im += z.x * w.y + z.y * w.x;
+        for (int k = 0; k < K2; k++) {
+            const int ky = k < MM ? k : n - (k - MM + 1);
+            const float2 z = zs[k * MM + kx], w = ic_tw[(ky * y) & (n - 1)];
+            re = fmaf(z.x, w.x, fmaf(-z.y, w.y, re));
+            im = fmaf(z.x, w.y, fmaf(z.y, w.x, im));
+        }
+        V[(f * n + y) * 16 + kx] = make_float2(re, im);
     }
-    V[fy * 16 + kx] = make_float2(re, im);
 }
 
 // out[b][c][p] = act(sum_j Wl[c][j] h[b][j][p] + bl[c] + S[b][c][p]) with S from V by
@@ -607,10 +670,14 @@ __global__ void __launch_bounds__(128) fno_pw_tc(const float *__restrict__ h, co
         fch::tc::mbar_init_fence();
     }
     float f[8];
+    const float *hp = h + (long)b * W * n2 + p;
 #pragma unroll
     for (int kc = 0; kc < W / 8; kc++) {
 #pragma unroll
-        for (int e = 0; e < 8; e++) f[e] = h[((long)b * W + kc * 8 + e) * n2 + p];
+        for (int e = 0; e < 8; e++) {
+            f[e] = *hp;
+            hp += n2;
+        }
         core_store(sA, tid, kc, pack8_bf16(f));
     }
 #pragma unroll
@@ -664,10 +731,19 @@ __global__ void __launch_bounds__(128) fno_pw_tc(const float *__restrict__ h, co
     if (ok) {
         float v[32];
         fch::tc::tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16), v);
+        float *op = out + (long)b * W * n2 + p;
+        if (act) {
 #pragma unroll
-        for (int o = 0; o < W; o++) {
-            const float z = v[o] + bs[o];
-            out[((long)b * W + o) * n2 + p] = act ? gelu(z) : z;
+            for (int o = 0; o < W; o++) {
+                *op = gelu_as(v[o] + bs[o]);
+                op += n2;
+            }
+        } else {
+#pragma unroll
+            for (int o = 0; o < W; o++) {
+                *op = v[o] + bs[o];
+                op += n2;
+            }
         }
     } else if (tid == 0) {
         atomicExch(err, 1);
@@ -689,7 +765,7 @@ __global__ void __launch_bounds__(128) fno_proj_tc(const float *__restrict__ h, 
 {
     __shared__ __align__(128) unsigned char sA[16 * kTcSBO];
     __shared__ __align__(128) unsigned char sB[(kMaxW2 / 8) * kTcSBO];
-    __shared__ float bq[kMaxW2], q2[kMaxW2];
+    __shared__ __align__(16) float bq[kMaxW2], q2[kMaxW2];
     __shared__ __align__(8) uint64_t bar;
     __shared__ uint32_t tslot;
     const int tid = threadIdx.x, warp = tid >> 5;
@@ -706,10 +782,14 @@ __global__ void __launch_bounds__(128) fno_proj_tc(const float *__restrict__ h, 
         fch::tc::mbar_init_fence();
     }
     float f[8];
+    const float *hp = h + b * W * n2 + p;
 #pragma unroll
     for (int kc = 0; kc < W / 8; kc++) {
 #pragma unroll
-        for (int e = 0; e < 8; e++) f[e] = live ? h[(b * W + kc * 8 + e) * n2 + p] : 0.f;
+        for (int e = 0; e < 8; e++) {
+            f[e] = live ? __ldcs(hp) : 0.f;
+            hp += n2;
+        }
         core_store(sA, tid, kc, pack8_bf16(f));
     }
     for (int i = tid; i < W2 * (W / 8); i += 128) {
@@ -737,13 +817,21 @@ __global__ void __launch_bounds__(128) fno_proj_tc(const float *__restrict__ h, 
     const bool ok = __syncthreads_and(fch::tc::mbar_wait(&bar, 0, kTcBound));
     fch::tc::fence_after_sync();
     if (ok) {
+        // W2 is a multiple of 16: sixteen accumulator columns at a time, the biases and
+        // the second layer's weights four at a time from shared memory
         float acc = __bfloat162float(bQ2[0]);
-        for (int c0 = 0; c0 < W2; c0 += 32) {
-            float v[32];
-            fch::tc::tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0, v);
+        for (int c0 = 0; c0 < W2; c0 += 16) {
+            float v[16];
+            fch::tc::tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0, v);
 #pragma unroll
-            for (int d = 0; d < 32; d++)
-                if (c0 + d < W2) acc += q2[c0 + d] * gelu(v[d] + bq[c0 + d]);
+            for (int d = 0; d < 16; d += 4) {
+                const float4 b4 = *reinterpret_cast<const float4 *>(bq + c0 + d);
+                const float4 q4 = *reinterpret_cast<const float4 *>(q2 + c0 + d);
+                acc = fmaf(q4.x, gelu_as(v[d] + b4.x), acc);
+                acc = fmaf(q4.y, gelu_as(v[d + 1] + b4.y), acc);
+                acc = fmaf(q4.z, gelu_as(v[d + 2] + b4.z), acc);
+                acc = fmaf(q4.w, gelu_as(v[d + 3] + b4.w), acc);
+            }
         }
         if (live) y[g] = acc;
     } else if (tid == 0) {
@@ -1248,16 +1336,25 @@ static fch_status forward_tc(fch_fno *f, int batch, int n, const float *a, float
     const long pts = (long)batch * n2, R = (long)batch * W * n;
     const size_t fld = (size_t)batch * W * n2;
     cudaStream_t s = f->stream;
-    fno_lift<WT><<<grid(pts, 256), 256, 0, s>>>(a, P + offset_of(f, 0, 0), P + offset_of(f, 1, 0), f->h, batch, n2,
-                                                W, f->cin);
+    {
+        const WT *P0 = P + offset_of(f, 0, 0), *P1 = P + offset_of(f, 1, 0);
+        const unsigned gl = grid(pts, 256);
+        switch (f->cin * 64 + W) {
+        case 1 * 64 + 16: fno_lift_t<WT, 16, 1><<<gl, 256, 0, s>>>(a, P0, P1, f->h, pts, n2); break;
+        case 2 * 64 + 16: fno_lift_t<WT, 16, 2><<<gl, 256, 0, s>>>(a, P0, P1, f->h, pts, n2); break;
+        case 1 * 64 + 32: fno_lift_t<WT, 32, 1><<<gl, 256, 0, s>>>(a, P0, P1, f->h, pts, n2); break;
+        case 2 * 64 + 32: fno_lift_t<WT, 32, 2><<<gl, 256, 0, s>>>(a, P0, P1, f->h, pts, n2); break;
+        default: fno_lift<WT><<<gl, 256, 0, s>>>(a, P0, P1, f->h, batch, n2, W, f->cin);
+        }
+    }
     for (int l = 0; l < f->L; l++) {
         float *hin = f->h + l * fld, *hout = f->h + (l + 1) * fld;
         launch_rowdft_tc(hin, f->tc_Bt, f->tc_X, R, n, f->tc_err, s);
-        fno_coldft<16><<<dim3(batch * W, M), 256, 0, s>>>(f->tc_X, f->tc_tw + n, f->tc_Y, n);
+        fno_coldft<16><<<dim3(batch * W, M), 256, 2 * n * sizeof(float2), s>>>(f->tc_X, f->tc_tw + n, f->tc_Y, n);
         fno_mix_modes<WT><<<grid((long)batch * W * f->K, 256), 256, 0, s>>>(f->tc_Y, P + offset_of(f, 4, l),
                                                                            f->tc_Z, batch, W, M);
-        fno_icoldft<16><<<grid((long)batch * W * n * M, 256), 256, 0, s>>>(f->tc_Z, f->tc_tw + n, f->tc_V,
-                                                                          (long)batch * W, n);
+        fno_icoldft<16><<<(unsigned)((long)batch * W * (n / 64)), 256, n * sizeof(float2), s>>>(
+            f->tc_Z, f->tc_tw + n, f->tc_V, (long)batch * W, n);
         // the channel mixing and the inverse x DFT: one MMA chain per 128 points
         const dim3 g((unsigned)(n / 128 * n), (unsigned)batch);
         const int act = l < f->L - 1;
@@ -1410,6 +1507,28 @@ extern "C" fch_status fch_fno_adam(fch_fno *f, float lr, float beta1, float beta
                                                             beta2, eps, c1, c2);
     if (cudaGetLastError() != cudaSuccess) return FCH_ECUDA;
     return refresh_bf16(f);
+}
+
+__global__ void fno_gelu_eval(const float *__restrict__ x, float *__restrict__ y, long cnt, int as)
+{
+    const long t = (long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t < cnt) y[t] = as ? gelu_as(x[t]) : gelu(x[t]);
+}
+
+// test hook (not part of the C ABI of fch.h): the GELU of the inference kernels
+// (as = 1) or of the training path (as = 0) on cnt device floats; 0 or a status
+extern "C" int fch_debug_fno_gelu(const float *x, float *y, long cnt, int as, void *stream)
+{
+    if (!x || !y || cnt < 1) return FCH_EINVAL;
+    cudaStream_t s = (cudaStream_t)stream;
+    fno_gelu_eval<<<grid(cnt, 256), 256, 0, s>>>(x, y, cnt, as);
+    cudaError_t e = cudaGetLastError();
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) {
+        fch_set_thread_error(cudaGetErrorString(e));
+        return FCH_ECUDA;
+    }
+    return FCH_OK;
 }
 
 // test hook (not part of the C ABI of fch.h): the tensor-core row DFT alone,

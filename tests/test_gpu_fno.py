@@ -311,6 +311,32 @@ def test_adaptive_imex_sav_with_learned_extrapolation(small_trained_net, scheme)
     assert rel(out["learned"][1], out["plain"][1]) < 1e-3
 
 
+def test_inference_gelu_vs_erf_and_its_error_bound():
+    # the tensor-core kernels' GELU takes erf from Abramowitz and Stegun 7.1.28
+    # (|error| <= 3e-7); against the training path's GELU (the library erff) and the
+    # exact value, over the range activations take, the tails and the special values
+    import ctypes as C
+
+    f = fch.lib().fch_debug_fno_gelu
+    f.argtypes = [C.c_void_p, C.c_void_p, C.c_long, C.c_int, C.c_void_p]
+    f.restype = C.c_int
+    xs = np.concatenate([np.linspace(-12, 12, 400001), [0.0, -0.0, 1e-30, -1e-30, 40.0, -40.0, 1e30, -1e30]])
+    x = torch.tensor(xs, dtype=torch.float32, device=DEV)
+    ya, ye = torch.empty_like(x), torch.empty_like(x)
+    assert f(x.data_ptr(), ya.data_ptr(), x.numel(), 1, None) == 0
+    assert f(x.data_ptr(), ye.data_ptr(), x.numel(), 0, None) == 0
+    xd = x.double().cpu().numpy()
+    exact = 0.5 * xd * (1 + np.vectorize(math.erf)(xd / math.sqrt(2)))
+    a, e = ya.double().cpu().numpy(), ye.double().cpu().numpy()
+    assert np.isfinite(a).all()
+    # erf within 3e-7 (the approximation) plus the float rounding of p^-16, which
+    # 1 - p^-16 exposes near 0 (2e-6 absolute in all), then the GELU's own rounding
+    bound = 0.5 * np.abs(xd) * 2e-6 + 3e-7 * np.abs(exact) + 1e-37
+    assert (np.abs(a - exact) <= bound).all()
+    assert (np.abs(a - e) <= 1e-6 * np.maximum(1.0, np.abs(xd))).all()
+    assert (a[xd == 0] == 0).all() and a[-2] == xd[-2] and a[-1] == 0.0
+
+
 def _rowdft_fn():
     import ctypes as C
 
