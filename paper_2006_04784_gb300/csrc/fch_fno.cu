@@ -39,36 +39,84 @@ namespace {
 constexpr int kMaxW2 = 128;  // hidden channels of the projection
 
 __device__ __forceinline__ float gelu(float x) { return 0.5f * x * (1.0f + erff(x * 0.70710678118654752f)); }
-
-// GELU for the tensor-core inference kernels, with erf from the rational approximation
-// of Abramowitz and Stegun, Handbook of Mathematical Functions, eq. 7.1.28: for u >= 0,
-// erf(u) = 1 - (1 + a1 u + a2 u^2 + ... + a6 u^6)^-16 with |error| <= 3e-7 (one
-// reciprocal and sixteen multiplies or multiply-adds instead of the library's erff; the
-// sign by symmetry). In float, 1 - p^-16 loses digits near u = 0, so erf comes out
-// within about 2e-6 absolute: GELU within |x| 1e-6. Its outputs feed bfloat16 operands
-// (relative rounding 2^-9) or FP32 sums with bfloat16 weights, whose rounding is larger.
-__device__ __forceinline__ float gelu_as(float x)
-{
-    const float u = fminf(fabsf(x) * 0.70710678118654752f, 8.0f); // erf(8) is 1 in float; p stays finite
-    float p = 0.0000430638f;
-    p = fmaf(p, u, 0.0002765672f);
-    p = fmaf(p, u, 0.0001520143f);
-    p = fmaf(p, u, 0.0092705272f);
-    p = fmaf(p, u, 0.0422820123f);
-    p = fmaf(p, u, 0.0705230784f);
-    p = fmaf(p, u, 1.0f);
-    float r = __fdividef(1.0f, p); // p >= 1
-    r = fmaf(r, fmaf(-p, r, 1.0f), r); // one Newton step: 1/p to about an ulp
-    r = r * r;
-    r = r * r;
-    r = r * r;
-    r = r * r; // p^-16
-    const float e = copysignf(1.0f - r, x);
-    return 0.5f * x * (1.0f + e);
-}
 __device__ __forceinline__ float gelu_grad(float x)
 {
     return 0.5f * (1.0f + erff(x * 0.70710678118654752f)) + x * 0.39894228040143268f * expf(-0.5f * x * x);
+}
+
+// Two floats in one 64-bit register, for the packed FP32 instructions of this GPU
+// (add / mul / fma .rn.f32x2: both lanes in one instruction).
+typedef unsigned long long f32x2;
+__device__ __forceinline__ f32x2 x2(float a, float b)
+{
+    f32x2 r;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(a), "f"(b));
+    return r;
+}
+__device__ __forceinline__ float2 x2_split(f32x2 v)
+{
+    float a, b;
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(a), "=f"(b) : "l"(v));
+    return make_float2(a, b);
+}
+__device__ __forceinline__ f32x2 x2_fma(f32x2 a, f32x2 b, f32x2 c)
+{
+    f32x2 d;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
+    return d;
+}
+__device__ __forceinline__ f32x2 x2_mul(f32x2 a, f32x2 b)
+{
+    f32x2 d;
+    asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
+__device__ __forceinline__ f32x2 x2_add(f32x2 a, f32x2 b)
+{
+    f32x2 d;
+    asm("add.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
+__device__ __forceinline__ float rcp_approx(float x)
+{
+    float r;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
+
+// GELU of two values at once for the tensor-core inference kernels. erf comes from the
+// rational approximation of Abramowitz and Stegun, Handbook of Mathematical Functions,
+// eq. 7.1.28: for u >= 0, 1 - erf(u) = p(u)^-16 with p(u) = 1 + a1 u + ... + a6 u^6,
+// |error| <= 3e-7. With h = x/2 and a = |h| (u = a sqrt 2),
+//   GELU(x) = x/2 (1 + erf(x / sqrt 2)) = (a + h) - a p(u)^-16,
+// which for x < 0 is -a p^-16 itself (no cancellation); a is capped in the last term. One reciprocal per value (with
+// a Newton step), the rest packed: about twelve instructions a value against the
+// library erff's branches. In float, p^-16 carries ~2e-6 relative rounding: GELU
+// within 0.5 |x| 3e-6. Its outputs feed bfloat16 operands (relative rounding 2^-9) or
+// FP32 sums with bfloat16 weights.
+__device__ __forceinline__ f32x2 gelu_as2(f32x2 x)
+{
+    const f32x2 h = x2_mul(x, x2(0.5f, 0.5f));
+    const f32x2 a = h & 0x7FFFFFFF7FFFFFFFull; // |h|
+    // the tail term takes |h| capped at 5.65 (u = |h| sqrt 2 at most 8, where 1 - erf is
+    // 1e-29 and p stays finite for the Newton step)
+    const float2 as = x2_split(a);
+    const f32x2 acn = x2(-fminf(as.x, 5.65f), -fminf(as.y, 5.65f));
+    const f32x2 u = x2_mul(acn, x2(-1.41421356237309505f, -1.41421356237309505f));
+    f32x2 p = x2_fma(x2(0.0000430638f, 0.0000430638f), u, x2(0.0002765672f, 0.0002765672f));
+    p = x2_fma(p, u, x2(0.0001520143f, 0.0001520143f));
+    p = x2_fma(p, u, x2(0.0092705272f, 0.0092705272f));
+    p = x2_fma(p, u, x2(0.0422820123f, 0.0422820123f));
+    p = x2_fma(p, u, x2(0.0705230784f, 0.0705230784f));
+    p = x2_fma(p, u, x2(1.0f, 1.0f)); // in [1, 22]
+    const float2 ps = x2_split(p);
+    f32x2 r = x2(rcp_approx(ps.x), rcp_approx(ps.y));
+    r = x2_fma(r, x2_fma(p ^ 0x8000000080000000ull, r, x2(1.0f, 1.0f)), r); // Newton: r (2 - p r)
+    r = x2_mul(r, r);
+    r = x2_mul(r, r);
+    r = x2_mul(r, r);
+    r = x2_mul(r, r); // p^-16
+    return x2_fma(acn, r, x2_add(a, h));
 }
 
 // ky of retained-mode row kyi
@@ -734,9 +782,11 @@ __global__ void __launch_bounds__(128) fno_pw_tc(const float *__restrict__ h, co
         float *op = out + (long)b * W * n2 + p;
         if (act) {
 #pragma unroll
-            for (int o = 0; o < W; o++) {
-                *op = gelu_as(v[o] + bs[o]);
-                op += n2;
+            for (int o = 0; o < W; o += 2) {
+                const float2 g2 = x2_split(gelu_as2(x2_add(x2(v[o], v[o + 1]), x2(bs[o], bs[o + 1]))));
+                op[0] = g2.x;
+                op[n2] = g2.y;
+                op += 2 * n2;
             }
         } else {
 #pragma unroll
@@ -819,7 +869,7 @@ __global__ void __launch_bounds__(128) fno_proj_tc(const float *__restrict__ h, 
     if (ok) {
         // W2 is a multiple of 16: sixteen accumulator columns at a time, the biases and
         // the second layer's weights four at a time from shared memory
-        float acc = __bfloat162float(bQ2[0]);
+        f32x2 acc = x2(__bfloat162float(bQ2[0]), 0.f); // two partial sums, added at the end
         for (int c0 = 0; c0 < W2; c0 += 16) {
             float v[16];
             fch::tc::tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0, v);
@@ -827,13 +877,12 @@ __global__ void __launch_bounds__(128) fno_proj_tc(const float *__restrict__ h, 
             for (int d = 0; d < 16; d += 4) {
                 const float4 b4 = *reinterpret_cast<const float4 *>(bq + c0 + d);
                 const float4 q4 = *reinterpret_cast<const float4 *>(q2 + c0 + d);
-                acc = fmaf(q4.x, gelu_as(v[d] + b4.x), acc);
-                acc = fmaf(q4.y, gelu_as(v[d + 1] + b4.y), acc);
-                acc = fmaf(q4.z, gelu_as(v[d + 2] + b4.z), acc);
-                acc = fmaf(q4.w, gelu_as(v[d + 3] + b4.w), acc);
+                acc = x2_fma(x2(q4.x, q4.y), gelu_as2(x2_add(x2(v[d], v[d + 1]), x2(b4.x, b4.y))), acc);
+                acc = x2_fma(x2(q4.z, q4.w), gelu_as2(x2_add(x2(v[d + 2], v[d + 3]), x2(b4.z, b4.w))), acc);
             }
         }
-        if (live) y[g] = acc;
+        const float2 a2 = x2_split(acc);
+        if (live) y[g] = a2.x + a2.y;
     } else if (tid == 0) {
         atomicExch(err, 1);
     }
@@ -1512,7 +1561,17 @@ extern "C" fch_status fch_fno_adam(fch_fno *f, float lr, float beta1, float beta
 __global__ void fno_gelu_eval(const float *__restrict__ x, float *__restrict__ y, long cnt, int as)
 {
     const long t = (long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (t < cnt) y[t] = as ? gelu_as(x[t]) : gelu(x[t]);
+    if (!as) {
+        if (t < cnt) y[t] = gelu(x[t]);
+        return;
+    }
+    // the inference GELU works on pairs: elements 2t and 2t + 1 (the last alone twice)
+    const long i = 2 * t;
+    if (i >= cnt) return;
+    const bool pair = i + 1 < cnt;
+    const float2 g = x2_split(gelu_as2(x2(x[i], pair ? x[i + 1] : x[i])));
+    y[i] = g.x;
+    if (pair) y[i + 1] = g.y;
 }
 
 // test hook (not part of the C ABI of fch.h): the GELU of the inference kernels

@@ -312,9 +312,10 @@ def test_adaptive_imex_sav_with_learned_extrapolation(small_trained_net, scheme)
 
 
 def test_inference_gelu_vs_erf_and_its_error_bound():
-    # the tensor-core kernels' GELU takes erf from Abramowitz and Stegun 7.1.28
-    # (|error| <= 3e-7); against the training path's GELU (the library erff) and the
-    # exact value, over the range activations take, the tails and the special values
+    # the tensor-core kernels' GELU (pairs of values, packed FP32) takes erf from
+    # Abramowitz and Stegun 7.1.28 (|error| <= 3e-7); against the training path's GELU
+    # (the library erff) and the exact value, over the range activations take, the
+    # tails and the special values; an odd count leaves the last value alone
     import ctypes as C
 
     f = fch.lib().fch_debug_fno_gelu
@@ -329,12 +330,12 @@ def test_inference_gelu_vs_erf_and_its_error_bound():
     exact = 0.5 * xd * (1 + np.vectorize(math.erf)(xd / math.sqrt(2)))
     a, e = ya.double().cpu().numpy(), ye.double().cpu().numpy()
     assert np.isfinite(a).all()
-    # erf within 3e-7 (the approximation) plus the float rounding of p^-16, which
-    # 1 - p^-16 exposes near 0 (2e-6 absolute in all), then the GELU's own rounding
-    bound = 0.5 * np.abs(xd) * 2e-6 + 3e-7 * np.abs(exact) + 1e-37
+    # 1 - erf within 3e-7 (the approximation) plus the float rounding of p^-16 (about
+    # 2e-6 of it), then the GELU's own rounding
+    bound = 0.5 * np.abs(xd) * 3e-6 + 3e-7 * np.abs(exact) + 1e-37
     assert (np.abs(a - exact) <= bound).all()
     assert (np.abs(a - e) <= 1e-6 * np.maximum(1.0, np.abs(xd))).all()
-    assert (a[xd == 0] == 0).all() and a[-2] == xd[-2] and a[-1] == 0.0
+    assert (a[xd == 0] == 0).all() and a[-2] == xd[-2] and abs(a[-1]) < 1e-20
 
 
 def _rowdft_fn():
