@@ -45,18 +45,22 @@ __device__ __forceinline__ df2 ldg(const df2 *p)
     return r;
 }
 
+// The sums and products of the transformations use the explicitly rounded intrinsics
+// (__fadd_rn, __fsub_rn, __fmul_rn): the compiler never contracts those into fused
+// multiply-adds, which would break the exactness these steps rely on (a product fused
+// into the TwoSum that consumes it counts its rounding error twice).
 __device__ __forceinline__ df two_sum(float a, float b)
 {
-    const float s = a + b;
-    const float bb = s - a;
-    const float e = (a - (s - bb)) + (b - bb);
+    const float s = __fadd_rn(a, b);
+    const float bb = __fsub_rn(s, a);
+    const float e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
     return df(s, e);
 }
 
 __device__ __forceinline__ df fast_two_sum(float a, float b)
 {
-    const float s = a + b;
-    return df(s, b - (s - a));
+    const float s = __fadd_rn(a, b);
+    return df(s, __fsub_rn(b, __fsub_rn(s, a)));
 }
 
 // Sums. The high parts are added exactly (TwoSum), the low parts with one rounding:
@@ -97,11 +101,28 @@ __device__ __forceinline__ df operator-(df a, df b) { return add_norm(a, -b); }
 
 __device__ __forceinline__ df operator*(df a, df b)
 {
-    const float p = a.hi * b.hi;
+    const float p = __fmul_rn(a.hi, b.hi);
     float e = fmaf(a.hi, b.hi, -p);
     e = fmaf(a.hi, b.lo, e);
     e = fmaf(a.lo, b.hi, e);
     return fast_two_sum(p, e);
+}
+
+// Product without the final renormalisation (4 operations instead of 7): the exact
+// product of the high words and, in one error word, its rounding error and the two
+// cross terms. The low word may exceed ulp(hi)/2 by a few units; sums and products
+// take such operands (their error stays a few u^2 relative to the operands' size),
+// and whatever reads only the high word renormalises first. A product neglects
+// lo x lo: an operand whose high word cancelled in an unrenormalised difference (the
+// value then sits in lo) is renormalised before it meets another such operand (a
+// square of a small difference above all).
+__device__ __forceinline__ df mul_lazy(df a, df b)
+{
+    const float p = __fmul_rn(a.hi, b.hi);
+    float e = fmaf(a.hi, b.hi, -p);
+    e = fmaf(a.hi, b.lo, e);
+    e = fmaf(a.lo, b.hi, e);
+    return df(p, e);
 }
 
 // by +-1 (the DIR factors of the butterflies)
@@ -131,7 +152,7 @@ __device__ __forceinline__ df recip(df d)
 {
     d = renorm_exact(d);
     const float r0 = 1.0f / d.hi;
-    const float p = d.hi * r0;
+    const float p = __fmul_rn(d.hi, r0);
     const float pe = fmaf(d.hi, r0, -p);
     const float e = ((1.0f - p) - pe) - d.lo * r0;
     return fast_two_sum(r0, r0 * e);
@@ -152,7 +173,7 @@ __device__ __forceinline__ df2 cmul_lazy(df2 a, df2 w)
 {
     df2 r;
     {
-        const float p1 = a.x.hi * w.x.hi, p2 = a.y.hi * w.y.hi;
+        const float p1 = __fmul_rn(a.x.hi, w.x.hi), p2 = __fmul_rn(a.y.hi, w.y.hi);
         r.x = two_sum(p1, -p2);
         float e = fmaf(a.x.hi, w.x.hi, -p1) - fmaf(a.y.hi, w.y.hi, -p2);
         e = fmaf(a.x.hi, w.x.lo, e);
@@ -162,7 +183,7 @@ __device__ __forceinline__ df2 cmul_lazy(df2 a, df2 w)
         r.x.lo += e;
     }
     {
-        const float p1 = a.x.hi * w.y.hi, p2 = a.y.hi * w.x.hi;
+        const float p1 = __fmul_rn(a.x.hi, w.y.hi), p2 = __fmul_rn(a.y.hi, w.x.hi);
         r.y = two_sum(p1, p2);
         float e = fmaf(a.x.hi, w.y.hi, -p1) + fmaf(a.y.hi, w.x.hi, -p2);
         e = fmaf(a.x.hi, w.y.lo, e);

@@ -81,12 +81,24 @@ template <typename R> __device__ __forceinline__ R rsub(R a, R b) { return a - b
 template <> __device__ __forceinline__ df radd(df a, df b) { return add_lazy(a, b); }
 template <> __device__ __forceinline__ df rsub(df a, df b) { return sub_lazy(a, b); }
 
+template <typename R> __device__ __forceinline__ R rmul(R a, R b) { return a * b; }
+template <> __device__ __forceinline__ df rmul(df a, df b) { return mul_lazy(a, b); }
+
 template <typename C> __device__ __forceinline__ C badd(C a, C b) { return mk<C>(radd(a.x, b.x), radd(a.y, b.y)); }
 template <typename C> __device__ __forceinline__ C bsub(C a, C b) { return mk<C>(rsub(a.x, b.x), rsub(a.y, b.y)); }
 template <typename C> __device__ __forceinline__ C btw(C a, C w) { return cmul(a, w); }
 template <> __device__ __forceinline__ df2 btw(df2 a, df2 w) { return cmul_lazy(a, w); }
 template <typename C> __device__ __forceinline__ C bnorm(C a) { return a; }
 template <> __device__ __forceinline__ df2 bnorm(df2 a) { return mk<df2>(renorm(a.x), renorm(a.y)); }
+// The pointwise and spectral stages use the same unrenormalised arithmetic for
+// double-float (radd, rsub, rmul; lscale below) and renormalise exactly (lnorm) what
+// they store; for float and double these are the plain operations.
+template <typename C, typename S> __device__ __forceinline__ C lscale(C a, S s)
+{
+    return mk<C>(rmul(a.x, s), rmul(a.y, s));
+}
+template <typename C> __device__ __forceinline__ C lnorm(C a) { return a; }
+template <> __device__ __forceinline__ df2 lnorm(df2 a) { return mk<df2>(renorm_exact(a.x), renorm_exact(a.y)); }
 
 // a * (DIR i): DIR = -1 forward (-i), +1 inverse (+i)
 template <int DIR, typename C> __device__ __forceinline__ C rot(C a)
@@ -232,8 +244,8 @@ __device__ __forceinline__ int pair_kx(int q, int N)
 template <typename T>
 __device__ __forceinline__ void well(const fch_consts<T> &k, T u, T &W, T &W1, T &W2)
 {
-    const T v = u - k.bm;
-    T A = mul_p2(v * v, (T)0.5), A1 = v, A2 = (T)1;
+    const T v = rsub(u, k.bm);
+    T A = mul_p2(rmul(v, v), (T)0.5), A1 = v, A2 = (T)1;
     if (k.q != (T)0) {
         const T x = v / k.eps;
         const T e = exp(-fabs(x)); // e^{-|x|} in (0, 1]
@@ -244,12 +256,12 @@ __device__ __forceinline__ void well(const fch_consts<T> &k, T u, T &W, T &W1, T
         A1 += k.q * sech * th;
         A2 += k.qoe * sech * (mul_p2(sech * sech, (T)2) - (T)1);
     }
-    const T w = u - k.bp;
-    const T B = mul_p2(w * w, (T)0.5) + k.g3 * (u - k.c3);
-    const T B1 = w + k.g3;
-    W = A * B;
-    W1 = A1 * B + A * B1;
-    W2 = (k.q != (T)0 ? A2 * B : B) + mul_p2(A1 * B1, (T)2) + A;
+    const T w = rsub(u, k.bp);
+    const T B = radd(mul_p2(rmul(w, w), (T)0.5), rmul(k.g3, rsub(u, k.c3)));
+    const T B1 = radd(w, k.g3);
+    W = rmul(A, B);
+    W1 = radd(rmul(A1, B), rmul(A, B1));
+    W2 = radd(radd(k.q != (T)0 ? rmul(A2, B) : B, mul_p2(rmul(A1, B1), (T)2)), A);
 }
 
 // ---------------------------------------------------------------------------
@@ -384,9 +396,9 @@ __device__ __forceinline__ void spec_elem(const fch_kparams &kp, const fch_const
     const int N = kp.N;
     const long idx = (long)kx * N + ky;
     const int my = ky < (N >> 1) ? ky : ky - N;
-    const T k2 = K.kf2 * (T)(kx * kx + my * my);
-    const T sq = K.e2 * k2 + K.am;
-    const T sk = sq * sq; // symbol of L_IMEX, eq. (e:IMEX-op)
+    const T k2 = rmul(K.kf2, (T)(kx * kx + my * my));
+    const T sq = radd(rmul(K.e2, k2), K.am);
+    const T sk = rmul(sq, sq); // symbol of L_IMEX, eq. (e:IMEX-op)
     const T wgt = (kx == 0 || kx == (N >> 1)) ? (T)1 : (T)2;
     C v = mk<C>(0, 0);
     bool pack = false;
@@ -413,25 +425,28 @@ __device__ __forceinline__ void spec_elem(const fch_kparams &kp, const fch_const
         pack = true;
     } else if (MODE == CM_IMEX_SOLVE) {
         // eq. (IMEX-eq): (a + |k|^2 s) u^{n+1} = -b u^n - c u^{n-1} - |k|^2 N_IMEX(u*)^
-        const C Nh = csub(A, cscale(B, K.e2 * k2));
-        const C rhs = csub(cscale(ldg(bf.Un + idx), -co.b), cadd(cscale(ldg(bf.Um + idx), co.c), cscale(Nh, k2)));
+        const C Nh = bsub(A, lscale(B, rmul(K.e2, k2)));
+        const C rhs = bsub(lscale(ldg(bf.Un + idx), -co.b), badd(lscale(ldg(bf.Um + idx), co.c), lscale(Nh, k2)));
         // the mean mode (k = 0) carries the mass: divide there, where a bias of the
         // one-Newton-step reciprocal would repeat every step and accumulate
-        const T den = co.a + k2 * sk;
-        v = (kx | ky) == 0 ? mk<C>(rhs.x / den, rhs.y / den) : cscale(rhs, recip(den));
-        bf.Unew[idx] = v;
+        const T den = radd(co.a, rmul(k2, sk));
+        v = (kx | ky) == 0 ? mk<C>(rhs.x / den, rhs.y / den) : lscale(rhs, recip(den));
+        bf.Unew[idx] = lnorm(v);
         pack = kp.flags & FCH_FL_PACK_F;
     } else if (MODE == CM_F_FINISH) {
         // mu^ = eps^4 |k|^4 u^ + eps^2 |k|^2 W'^ + (rest)^ ; F^ = -|k|^2 mu^ (eq. sFCH)
         const C u = ldg(bf.src + idx);
-        const C mu = cadd(cadd(cscale(u, K.e4 * k2 * k2), cscale(A, K.e2 * k2)), B);
-        const C F = cscale(mu, -k2);
-        bf.dst[idx] = F;
+        const C mu = badd(badd(lscale(u, rmul(rmul(K.e4, k2), k2)), lscale(A, rmul(K.e2, k2))), B);
+        const C F = lscale(mu, -k2);
+        bf.dst[idx] = lnorm(F);
         if (kp.flags & FCH_FL_AM3) {
             // eq. (Predictor): u_p = u^n + w1 F(u~) + w2 F(u^n) + w3 F(u^{n-1})
-            const C up = cadd(cadd(ldg(bf.Un + idx), cscale(F, co.w1)),
-                              cadd(cscale(ldg(bf.Fn + idx), co.w2), cscale(ldg(bf.Fm + idx), co.w3)));
-            const C df = csub(u, up);
+            const C up = badd(badd(ldg(bf.Un + idx), lscale(F, co.w1)),
+                              badd(lscale(ldg(bf.Fn + idx), co.w2), lscale(ldg(bf.Fm + idx), co.w3)));
+            // the difference cancels the high words where the error is small: it is
+            // renormalised before it is squared (a product drops lo x lo, which then
+            // carries the whole value)
+            const C df = lnorm(bsub(u, up));
             red[0] += wgt * (df.x * df.x + df.y * df.y);
             red[1] += wgt * (up.x * up.x + up.y * up.y);
         }
@@ -503,7 +518,7 @@ __device__ __forceinline__ void spec_elem(const fch_kparams &kp, const fch_const
     }
     if (pack) {
         Co = cscale_p2(v, K.inv_n2);
-        Do = cscale(v, -mul_p2(k2, K.inv_n2));
+        Do = lscale(v, -mul_p2(k2, K.inv_n2));
     }
 }
 
@@ -917,7 +932,7 @@ row_pass(const fch_kparams kp)
             const int r = i / N, x = i - r * N;
             const long gi = (long)(y0 + r) * N + x;
             const C zn = ldg(Rn + gi);
-            rows[r * SL + skew(x)] = plain ? zn : cadd(zn, cscale(csub(zn, ldg(Rm + gi)), g));
+            rows[r * SL + skew(x)] = plain ? zn : badd(zn, lscale(bsub(zn, ldg(Rm + gi)), g));
         }
         __syncthreads();
     } else if (MODE == RM_R2C_LOAD) {
@@ -989,19 +1004,21 @@ row_pass(const fch_kparams kp)
             C o = mk<C>(0, 0);
             if (MODE == RM_NIMEX || MODE == RM_NIMEX_DIRECT) {
                 // N_IMEX = [eps^2 (am - W'' + eta1) Lap u + W''W' - am^2 u - eta2 W'] + eps^2 Lap (am u - W')
-                o.x = K.e2 * (K.am - W2 + K.eta1) * lu + W2 * W1 - K.am2 * u - K.eta2 * W1;
-                o.y = K.am * u - W1;
+                o.x = rsub(rsub(radd(rmul(rmul(K.e2, radd(rsub(K.am, W2), K.eta1)), lu), rmul(W2, W1)),
+                                rmul(K.am2, u)),
+                           rmul(K.eta2, W1));
+                o.y = rsub(rmul(K.am, u), W1);
             } else if (MODE == RM_F || MODE == RM_ENERGY) {
                 // mu = eps^2 Lap w - W'' w + eps^2 eta1 Lap u - eta2 W', w = eps^2 Lap u - W'
-                const T w = K.e2 * lu - W1;
+                const T w = rsub(rmul(K.e2, lu), W1);
                 o.x = W1;
-                o.y = -W2 * w - K.eta2 * W1 + K.e2 * K.eta1 * lu;
+                o.y = radd(rsub(rmul(-W2, w), rmul(K.eta2, W1)), rmul(rmul(K.e2, K.eta1), lu));
                 if (MODE == RM_ENERGY || (kp.flags & FCH_FL_ENERGY))
                     red[0] += (T)0.5 * w * w - K.eta2 * W + (T)0.5 * K.e2 * K.eta1 * u * lu;
             } else if (MODE == RM_SAV || MODE == RM_SAV_DIRECT) {
                 // V = -eps^2 Lap (W' + zeta u) + [-eps^2 (W'' + zeta) Lap u + W' W'' - eta2 W']
-                o.x = W1 + K.zeta * u;
-                o.y = -K.e2 * (W2 + K.zeta) * lu + W1 * W2 - K.eta2 * W1;
+                o.x = radd(W1, rmul(K.zeta, u));
+                o.y = rsub(radd(rmul(rmul(-K.e2, radd(W2, K.zeta)), lu), rmul(W1, W2)), rmul(K.eta2, W1));
                 red[0] += -K.e2 * lu * (W1 + K.zeta * u) + (T)0.5 * W1 * W1 - K.eta2 * W;
             }
             s[skew(x)] = o;
