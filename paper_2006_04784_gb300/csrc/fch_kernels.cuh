@@ -133,11 +133,11 @@ template <int DIR, typename C> __device__ __forceinline__ void bfly8(C *v)
     const C a = v[3], b = v[7];
     C o1, o3;
     if (DIR < 0) {
-        o1 = mk<C>(radd(a.x, a.y) * s, rsub(a.y, a.x) * s);
-        o3 = mk<C>(rsub(b.y, b.x) * s, -(radd(b.x, b.y) * s));
+        o1 = mk<C>(rmul(radd(a.x, a.y), s), rmul(rsub(a.y, a.x), s));
+        o3 = mk<C>(rmul(rsub(b.y, b.x), s), -rmul(radd(b.x, b.y), s));
     } else {
-        o1 = mk<C>(rsub(a.x, a.y) * s, radd(a.x, a.y) * s);
-        o3 = mk<C>(-(radd(b.x, b.y) * s), rsub(b.x, b.y) * s);
+        o1 = mk<C>(rmul(rsub(a.x, a.y), s), rmul(radd(a.x, a.y), s));
+        o3 = mk<C>(-rmul(radd(b.x, b.y), s), rmul(rsub(b.x, b.y), s));
     }
     C o2 = rot<DIR>(v[5]);
     C e0 = v[0], e1 = v[2], e2 = v[4], e3 = v[6], o0 = v[1];
@@ -447,8 +447,10 @@ __device__ __forceinline__ void spec_elem(const fch_kparams &kp, const fch_const
             // renormalised before it is squared (a product drops lo x lo, which then
             // carries the whole value)
             const C df = lnorm(bsub(u, up));
-            red[0] += wgt * (df.x * df.x + df.y * df.y);
-            red[1] += wgt * (up.x * up.x + up.y * up.y);
+            // lazy sums of squares (the weight 1 or 2 scales exactly); |u_p|^2 is a sum of
+            // large terms, where a dropped lo x lo is far below the sum's own rounding
+            red[0] = radd(red[0], mul_p2(radd(rmul(df.x, df.x), rmul(df.y, df.y)), wgt));
+            red[1] = radd(red[1], mul_p2(radd(rmul(up.x, up.x), rmul(up.y, up.y)), wgt));
         }
         return;
     } else if (MODE == CM_SAV_PQ) {
