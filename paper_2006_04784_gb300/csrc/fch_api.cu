@@ -404,6 +404,33 @@ static fch_status upload_twiddles(fch_ctx *ctx, int N, int prec, void *dst, cuda
     return FCH_OK;
 }
 
+// products and sums of polynomials in u (coefficient of u^i at index i)
+static void poly_mul(const double *a, int na, const double *b, int nb, double *c)
+{
+    for (int i = 0; i < na + nb - 1; i++) c[i] = 0.0;
+    for (int i = 0; i < na; i++)
+        for (int j = 0; j < nb; j++) c[i + j] += a[i] * b[j];
+}
+
+// the q = 0 well W(u) = A(u) B(u) and its first two derivatives as polynomials
+static void well_polynomials(double bm, double bp, double g3, double c3, double *wp, double *w1p, double *w2p)
+{
+    const double v[2] = {-bm, 1.0}, w[2] = {-bp, 1.0};
+    double v2[3], w2[3];
+    poly_mul(v, 2, v, 2, v2);
+    poly_mul(w, 2, w, 2, w2);
+    const double A[3] = {0.5 * v2[0], 0.5 * v2[1], 0.5 * v2[2]};
+    const double B[3] = {0.5 * w2[0] - g3 * c3, 0.5 * w2[1] + g3, 0.5 * w2[2]};
+    const double B1[2] = {w[0] + g3, 1.0};
+    poly_mul(A, 3, B, 3, wp);
+    double vB[4], AB1[4], vB1[3];
+    poly_mul(v, 2, B, 3, vB);
+    poly_mul(A, 3, B1, 2, AB1);
+    for (int i = 0; i < 4; i++) w1p[i] = vB[i] + AB1[i];
+    poly_mul(v, 2, B1, 2, vB1);
+    for (int i = 0; i < 3; i++) w2p[i] = B[i] + 2.0 * vB1[i] + A[i];
+}
+
 template <typename T>
 static void fill_consts(fch_consts<T> &k, const fch_params &p, double kf, double am, double inv_n2)
 {
@@ -430,6 +457,14 @@ static void fill_consts(fch_consts<T> &k, const fch_params &p, double kf, double
     k.qoe = (T)(p.q / p.eps);
     k.g3 = (T)(p.gamma / 3.0);
     k.c3 = (T)(0.5 * (3.0 * p.b_plus - p.b_minus));
+    // q = 0: W = A B with A = v^2/2, v = u - b_-, and B = w^2/2 + gamma/3 (u - c3),
+    // w = u - b_+ (eq. e:Wq-def), expanded: W' = v B + A B', W'' = B + 2 v B' + A,
+    // B' = w + gamma/3
+    double wp[5], w1p[4], w2p[3];
+    well_polynomials(p.b_minus, p.b_plus, p.gamma / 3.0, 0.5 * (3.0 * p.b_plus - p.b_minus), wp, w1p, w2p);
+    for (int i = 0; i < 5; i++) k.wp[i] = (T)wp[i];
+    for (int i = 0; i < 4; i++) k.w1p[i] = (T)w1p[i];
+    for (int i = 0; i < 3; i++) k.w2p[i] = (T)w2p[i];
 }
 
 static void fill_kparams_model(fch_kparams &kp, const fch_params &p, int N, double L)

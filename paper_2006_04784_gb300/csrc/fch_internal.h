@@ -22,6 +22,8 @@ template <typename T> struct fch_consts {
     T kappa0, k2e2;   // kappa0, kappa2 eps^2 (ETD)
     T inv_n2;         // 1 / N^2
     T bm, bp, eps, q, qeps, qoe, g3, c3; // well: b_-, b_+, eps, q, q eps, q/eps, gamma/3, (3 b_+ - b_-)/2
+    // q = 0: W, W' and W'' as polynomials in u, coefficients of u^0, u^1, ...
+    T wp[5], w1p[4], w2p[3];
 };
 
 // Per-trial coefficients, mirrored in both precisions by the control kernel.

@@ -240,10 +240,26 @@ __device__ __forceinline__ int pair_kx(int q, int N)
 }
 
 // ---------------------------------------------------------------------------
+// c[0] + c[1] u + ... + c[M-1] u^(M-1) by Horner's rule
+template <typename T, int M> __device__ __forceinline__ T horner(const T *c, T u)
+{
+    T p = c[M - 1];
+#pragma unroll
+    for (int i = M - 2; i >= 0; i--) p = radd(rmul(p, u), c[i]);
+    return p;
+}
+
 // the regularised well W_q, eq. (e:Wq-def), with an overflow-free sech/tanh
 template <typename T>
 __device__ __forceinline__ void well(const fch_consts<T> &k, T u, T &W, T &W1, T &W2)
 {
+    if (k.q == (T)0) {
+        // a quartic: W, W' and W'' by Horner's rule from the host's expansion
+        W = horner<T, 5>(k.wp, u);
+        W1 = horner<T, 4>(k.w1p, u);
+        W2 = horner<T, 3>(k.w2p, u);
+        return;
+    }
     const T v = rsub(u, k.bm);
     T A = mul_p2(rmul(v, v), (T)0.5), A1 = v, A2 = (T)1;
     if (k.q != (T)0) {
