@@ -420,8 +420,8 @@ __device__ __forceinline__ void spec_elem(const fch_kparams &kp, const fch_const
     bool pack = false;
 
     if (MODE == CM_FWD_STORE) {
-        bf.o0[idx] = A;
-        if (bf.o1) bf.o1[idx] = B;
+        bf.o0[idx] = lnorm(A);
+        if (bf.o1) bf.o1[idx] = lnorm(B);
         return;
     }
     if (MODE == CM_INV_LOAD) {
@@ -599,13 +599,13 @@ __device__ __forceinline__ void pair0_item(const fch_kparams &kp, const fch_cons
             C A = mk<C>(0, 0), B = mk<C>(0, 0);
             if (TR::FWD) {
                 const C z1 = cconj(zo);
-                A = cscale_p2(cadd(zr, z1), (T)0.5);
-                const C dm = csub(zr, z1);
+                A = cscale_p2(badd(zr, z1), (T)0.5);
+                const C dm = bsub(zr, z1);
                 B = mk<C>(mul_p2(dm.y, (T)0.5), mul_p2(dm.x, (T)-0.5));
             }
             C Co = mk<C>(0, 0), Do = mk<C>(0, 0);
             spec_elem<T, MODE>(kp, K, co, bf, kx, kyy, A, B, Co, Do, red);
-            const C o = mk<C>(Co.x - Do.y, Co.y + Do.x);
+            const C o = mk<C>(rsub(Co.x, Do.y), radd(Co.y, Do.x));
             if (side)
                 outb[rr] = o;
             else
@@ -713,15 +713,15 @@ col_pass(const fch_kparams kp)
             C A = mk<C>(0, 0), B = mk<C>(0, 0);
             if (TR::FWD) {
                 const C z0 = tile[rk + s0], z1 = cconj(tile[rm + s1]);
-                A = cscale_p2(cadd(z0, z1), (T)0.5);
-                const C dm = csub(z0, z1);
+                A = cscale_p2(badd(z0, z1), (T)0.5);
+                const C dm = bsub(z0, z1);
                 B = mk<C>(mul_p2(dm.y, (T)0.5), mul_p2(dm.x, (T)-0.5));
             }
             C Co = mk<C>(0, 0), Do = mk<C>(0, 0);
             spec_elem<T, MODE>(kp, K, co, bf, p, ky, A, B, Co, Do, red);
             if (inv) {
-                tile[rk + s0] = mk<C>(Co.x - Do.y, Co.y + Do.x);
-                tile[rm + s1] = mk<C>(Co.x + Do.y, Do.x - Co.y);
+                tile[rk + s0] = mk<C>(rsub(Co.x, Do.y), radd(Co.y, Do.x));
+                tile[rm + s1] = mk<C>(radd(Co.x, Do.y), rsub(Do.x, Co.y));
             }
         } else {
             if (ky > (N >> 1)) continue;
@@ -827,15 +827,15 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(128, 7) col_pass_cl(
             C A = mk<C>(0, 0), B = mk<C>(0, 0);
             if (TR::FWD) {
                 const C z0 = s0(ky), z1 = cconj(s1(mky));
-                A = cscale_p2(cadd(z0, z1), (T)0.5);
-                const C dm = csub(z0, z1);
+                A = cscale_p2(badd(z0, z1), (T)0.5);
+                const C dm = bsub(z0, z1);
                 B = mk<C>(mul_p2(dm.y, (T)0.5), mul_p2(dm.x, (T)-0.5));
             }
             C Co = mk<C>(0, 0), Do = mk<C>(0, 0);
             spec_elem<T, MODE>(kp, K, co, bf, p, ky, A, B, Co, Do, red);
             if (inv) {
-                s0(ky) = mk<C>(Co.x - Do.y, Co.y + Do.x);
-                s1(mky) = mk<C>(Co.x + Do.y, Do.x - Co.y);
+                s0(ky) = mk<C>(rsub(Co.x, Do.y), radd(Co.y, Do.x));
+                s1(mky) = mk<C>(radd(Co.x, Do.y), rsub(Do.x, Co.y));
             }
         }
     } else {
@@ -863,13 +863,13 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(128, 7) col_pass_cl(
                     C A = mk<C>(0, 0), B = mk<C>(0, 0);
                     if (TR::FWD) {
                         const C z1 = cconj(zo);
-                        A = cscale_p2(cadd(zr, z1), (T)0.5);
-                        const C dm = csub(zr, z1);
+                        A = cscale_p2(badd(zr, z1), (T)0.5);
+                        const C dm = bsub(zr, z1);
                         B = mk<C>(mul_p2(dm.y, (T)0.5), mul_p2(dm.x, (T)-0.5));
                     }
                     C Co = mk<C>(0, 0), Do = mk<C>(0, 0);
                     spec_elem<T, MODE>(kp, K, co, bf, kx, kyy, A, B, Co, Do, red);
-                    const C o = mk<C>(Co.x - Do.y, Co.y + Do.x);
+                    const C o = mk<C>(rsub(Co.x, Do.y), radd(Co.y, Do.x));
                     if (side)
                         outb[rr] = o;
                     else
