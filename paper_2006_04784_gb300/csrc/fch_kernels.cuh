@@ -250,12 +250,13 @@ template <typename T, int M> __device__ __forceinline__ T horner(const T *c, T u
 }
 
 // the regularised well W_q, eq. (e:Wq-def), with an overflow-free sech/tanh
+// (W itself only where need_w: the energy density and the SAV functional use it)
 template <typename T>
-__device__ __forceinline__ void well(const fch_consts<T> &k, T u, T &W, T &W1, T &W2)
+__device__ __forceinline__ void well(const fch_consts<T> &k, T u, T &W, T &W1, T &W2, bool need_w)
 {
     if (k.q == (T)0) {
         // a quartic: W, W' and W'' by Horner's rule from the host's expansion
-        W = horner<T, 5>(k.wp, u);
+        W = need_w ? horner<T, 5>(k.wp, u) : (T)0;
         W1 = horner<T, 4>(k.w1p, u);
         W2 = horner<T, 3>(k.w2p, u);
         return;
@@ -1018,7 +1019,9 @@ row_pass(const fch_kparams kp)
                 continue;
             }
             T W, W1, W2;
-            well<T>(K, u, W, W1, W2);
+            well<T>(K, u, W, W1, W2,
+                    MODE == RM_SAV || MODE == RM_SAV_DIRECT || MODE == RM_ENERGY ||
+                        (MODE == RM_F && (kp.flags & FCH_FL_ENERGY)));
             C o = mk<C>(0, 0);
             if (MODE == RM_NIMEX || MODE == RM_NIMEX_DIRECT) {
                 // N_IMEX = [eps^2 (am - W'' + eta1) Lap u + W''W' - am^2 u - eta2 W'] + eps^2 Lap (am u - W')

@@ -93,7 +93,9 @@ __device__ __forceinline__ float2 pointwise(const fch_kparams &kp, const fch_con
                                             float lu, float *red)
 {
     float W, W1, W2;
-    well<float>(K, u, W, W1, W2);
+    well<float>(K, u, W, W1, W2,
+                MODE == RM_SAV || MODE == RM_SAV_DIRECT || MODE == RM_ENERGY ||
+                    (MODE == RM_F && (kp.flags & FCH_FL_ENERGY)));
     float2 o = mk<float2>(0.f, 0.f);
     if (MODE == RM_NIMEX || MODE == RM_NIMEX_DIRECT) {
         o.x = K.e2 * (K.am - W2 + K.eta1) * lu + W2 * W1 - K.am2 * u - K.eta2 * W1;
