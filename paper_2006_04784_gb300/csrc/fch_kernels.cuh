@@ -442,12 +442,18 @@ __device__ __forceinline__ void spec_elem(const fch_kparams &kp, const fch_const
         pack = true;
     } else if (MODE == CM_IMEX_SOLVE) {
         // eq. (IMEX-eq): (a + |k|^2 s) u^{n+1} = -b u^n - c u^{n-1} - |k|^2 N_IMEX(u*)^
-        const C Nh = bsub(A, lscale(B, rmul(K.e2, k2)));
-        const C rhs = bsub(lscale(ldg(bf.Un + idx), -co.b), badd(lscale(ldg(bf.Um + idx), co.c), lscale(Nh, k2)));
-        // the mean mode (k = 0) carries the mass: divide there, where a bias of the
-        // one-Newton-step reciprocal would repeat every step and accumulate
-        const T den = radd(co.a, rmul(k2, sk));
-        v = (kx | ky) == 0 ? mk<C>(rhs.x / den, rhs.y / den) : lscale(rhs, recip(den));
+        if ((kx | ky) == 0) {
+            // the mean mode (k = 0) carries the mass: renormalised arithmetic and a
+            // division there, where a bias of the one-Newton-step reciprocal (or the
+            // coarser rounding of unrenormalised low words) would repeat every step
+            const C rhs = csub(cscale(ldg(bf.Un + idx), -co.b), cscale(ldg(bf.Um + idx), co.c));
+            v = mk<C>(rhs.x / co.a, rhs.y / co.a);
+        } else {
+            const C Nh = bsub(A, lscale(B, rmul(K.e2, k2)));
+            const C rhs =
+                bsub(lscale(ldg(bf.Un + idx), -co.b), badd(lscale(ldg(bf.Um + idx), co.c), lscale(Nh, k2)));
+            v = lscale(rhs, recip(radd(co.a, rmul(k2, sk))));
+        }
         bf.Unew[idx] = lnorm(v);
         pack = kp.flags & FCH_FL_PACK_F;
     } else if (MODE == CM_F_FINISH) {
@@ -473,27 +479,33 @@ __device__ __forceinline__ void spec_elem(const fch_kparams &kp, const fch_const
     } else if (MODE == CM_SAV_PQ) {
         // eqs. (4.7)-(4.8): (a + |k|^2 l0) p = -b u^n - c u^{n-1} - |k|^2 l1 u*,
         //                   (a + |k|^2 l0) q = -|k|^2 X,  X = V[u*]/sqrt(E1(u*) + D0)
-        const C X = cscale(cadd(cscale(A, K.e2 * k2), B), co.isq);
+        const C X = lscale(badd(lscale(A, rmul(K.e2, k2)), B), co.isq);
         const C un = ldg(bf.Un + idx), um = ldg(bf.Um + idx);
         const C us = (kp.flags & FCH_FL_USTAR_V) ? ((const C *)kp.Vb)[idx]
-                     : co.gam != (T)0           ? cadd(un, cscale(csub(un, um), co.gam))
+                     : co.gam != (T)0           ? badd(un, lscale(bsub(un, um), co.gam))
                                                 : un;
-        const T l0 = K.e4 * k2 * k2 + K.b1am_e2 * k2 + K.b2am2;
-        const T l1 = -K.l1c * k2 - K.b1am_e2 * k2 - K.b2am2;
-        const T den = co.a + k2 * l0;
+        const T l0 = radd(radd(rmul(rmul(K.e4, k2), k2), rmul(K.b1am_e2, k2)), K.b2am2);
+        const T l1 = rsub(rsub(rmul(-K.l1c, k2), rmul(K.b1am_e2, k2)), K.b2am2);
+        const T den = radd(co.a, rmul(k2, l0));
         const T iden = recip(den);
-        const C pr = csub(cscale(un, -co.b), cadd(cscale(um, co.c), cscale(us, k2 * l1)));
-        const C p = (kx | ky) == 0 ? mk<C>(pr.x / den, pr.y / den) : cscale(pr, iden); // mean mode: as above
-        const C q = cscale(X, -k2 * iden);
+        C p;
+        if ((kx | ky) == 0) { // the mean mode: as in the IMEX solve
+            const C pr = csub(cscale(un, -co.b), cscale(um, co.c));
+            p = mk<C>(pr.x / co.a, pr.y / co.a);
+        } else {
+            p = lnorm(lscale(bsub(lscale(un, -co.b), badd(lscale(um, co.c), lscale(us, rmul(k2, l1)))), iden));
+        }
+        const C q = lnorm(lscale(X, rmul(-k2, iden)));
         ((C *)kp.Pb)[idx] = p;
         ((C *)kp.Qb)[idx] = q;
-        const C rr = cadd(cscale(p, co.a), cadd(cscale(un, co.b), cscale(um, co.c)));
-        red[0] += wgt * (X.x * rr.x + X.y * rr.y);
-        red[1] += wgt * (X.x * q.x + X.y * q.y);
+        // a p + b u^n + c u^{n-1} cancels (a + b + c = 0): renormalised before its product
+        const C rr = lnorm(badd(lscale(p, co.a), badd(lscale(un, co.b), lscale(um, co.c))));
+        red[0] = radd(red[0], mul_p2(radd(rmul(X.x, rr.x), rmul(X.y, rr.y)), wgt));
+        red[1] = radd(red[1], mul_p2(radd(rmul(X.x, q.x), rmul(X.y, q.y)), wgt));
         return;
     } else if (MODE == CM_SAV_COMBINE) {
-        v = cadd(((const C *)kp.Pb)[idx], cscale(((const C *)kp.Qb)[idx], co.r_new));
-        bf.Unew[idx] = v;
+        v = badd(((const C *)kp.Pb)[idx], lscale(((const C *)kp.Qb)[idx], co.r_new));
+        bf.Unew[idx] = lnorm(v);
         pack = kp.flags & FCH_FL_PACK_F;
     } else if (MODE == CM_PSD_ITER) {
         // R = mu(v) + (a v + b u^n + c u^{n-1}) / |k|^2,  d = -R / (s + a/|k|^2)  (k != 0),
@@ -502,36 +514,39 @@ __device__ __forceinline__ void spec_elem(const fch_kparams &kp, const fch_const
         const C vv = Vb[idx];
         C d = mk<C>(0, 0);
         if (k2 > (T)0) {
-            const C mu = cadd(cadd(cscale(vv, K.e4 * k2 * k2), cscale(A, K.e2 * k2)), B);
+            const C mu = badd(badd(lscale(vv, rmul(rmul(K.e4, k2), k2)), lscale(A, rmul(K.e2, k2))), B);
             const T ik2 = recip(k2);
-            const C R = cadd(mu, cscale(cadd(cscale(vv, co.a), cadd(cscale(bf.Un[idx], co.b),
-                                                                    cscale(bf.Um[idx], co.c))), ik2));
-            d = cscale(R, -recip(sk + co.a * ik2));
+            const C R = badd(mu, lscale(badd(lscale(vv, co.a), badd(lscale(bf.Un[idx], co.b),
+                                                                    lscale(bf.Um[idx], co.c))), ik2));
+            // the residual shrinks as the iteration converges: d is renormalised before
+            // its square enters the stopping test
+            d = lnorm(lscale(R, -recip(radd(sk, rmul(co.a, ik2)))));
         }
-        v = cadd(vv, cscale(d, co.lam));
+        v = lnorm(badd(vv, lscale(d, co.lam)));
         Vb[idx] = v;
-        red[0] += wgt * (d.x * d.x + d.y * d.y);
-        red[1] += wgt * (v.x * v.x + v.y * v.y);
+        red[0] = radd(red[0], mul_p2(radd(rmul(d.x, d.x), rmul(d.y, d.y)), wgt));
+        red[1] = radd(red[1], mul_p2(radd(rmul(v.x, v.x), rmul(v.y, v.y)), wgt));
         pack = true;
     } else if (MODE == CM_ETD_STAGE1 || MODE == CM_ETD_STAGE2) {
         // eqs. (ETDRK2), (ETD-L): l = -|k|^2 s - kappa0 - kappa2 eps^2 |k|^2, z = l k
-        const C Nim = csub(A, cscale(B, K.e2 * k2));
-        const T ell = -k2 * sk - K.kappa0 - K.k2e2 * k2;
+        const C Nim = bsub(A, lscale(B, rmul(K.e2, k2)));
+        const T ell = rsub(rsub(rmul(-k2, sk), K.kappa0), rmul(K.k2e2, k2));
         T ez, p1, p2;
-        etd_phi<T>(ell * co.k1, ez, p1, p2);
+        etd_phi<T>(rmul(ell, co.k1), ez, p1, p2);
         C *Nb = (C *)kp.Nb;
+        const T lin = radd(K.kappa0, rmul(K.k2e2, k2));
         if (MODE == CM_ETD_STAGE1) {
             const C un = bf.Un[idx];
-            const C N0 = cadd(cscale(Nim, -k2), cscale(un, K.kappa0 + K.k2e2 * k2));
+            const C N0 = lnorm(badd(lscale(Nim, -k2), lscale(un, lin)));
             Nb[idx] = N0;
-            v = cadd(cscale(un, ez), cscale(N0, co.k1 * p1));
-            bf.Unew[idx] = v;
+            v = badd(lscale(un, ez), lscale(N0, rmul(co.k1, p1)));
+            bf.Unew[idx] = lnorm(v);
             pack = true;
         } else {
             const C ut = bf.Unew[idx];
-            const C N1 = cadd(cscale(Nim, -k2), cscale(ut, K.kappa0 + K.k2e2 * k2));
-            v = cadd(ut, cscale(csub(N1, Nb[idx]), co.k1 * p2));
-            bf.Unew[idx] = v;
+            const C N1 = badd(lscale(Nim, -k2), lscale(ut, lin));
+            v = badd(ut, lscale(bsub(N1, Nb[idx]), rmul(co.k1, p2)));
+            bf.Unew[idx] = lnorm(v);
             pack = kp.flags & FCH_FL_PACK_F;
         }
     }
