@@ -620,51 +620,6 @@ __global__ void __launch_bounds__(256) fno_icoldft(const float2 *__restrict__ Z,
     }
 }
 
-// out[b][c][p] = act(sum_j Wl[c][j] h[b][j][p] + bl[c] + S[b][c][p]) with S from V by
-// the inverse row DFT (one block per row y of one sample, threads over x)
-template <int W, int MM, typename WT>
-__global__ void __launch_bounds__(256) fno_pointwise_idft(const float *__restrict__ h, const float2 *__restrict__ V,
-                                                          const float2 *__restrict__ tw, const WT *__restrict__ Wl,
-                                                          const WT *__restrict__ bl, float *__restrict__ out, int n,
-                                                          int act)
-{
-    __shared__ float ws[W * W];
-    __shared__ float bs[W];
-    __shared__ float2 vs[W * MM];
-    const int b = blockIdx.y, y = blockIdx.x;
-    const long n2 = (long)n * n;
-    for (int i = threadIdx.x; i < W * W; i += blockDim.x) ws[i] = wld(Wl, i);
-    for (int i = threadIdx.x; i < W; i += blockDim.x) bs[i] = wld(bl, i);
-    const float sc = 1.0f / ((float)n * (float)n);
-    for (int i = threadIdx.x; i < W * MM; i += blockDim.x) {
-        const int o = i / MM, kx = i - o * MM;
-        const float2 v = V[(((long)b * W + o) * n + y) * 16 + kx];
-        const float wk = (kx == 0 ? 1.f : 2.f) * sc;
-        vs[i] = make_float2(wk * v.x, wk * v.y);
-    }
-    __syncthreads();
-    for (int x = threadIdx.x; x < n; x += blockDim.x) {
-        const long p = (long)y * n + x;
-        float in[W];
-#pragma unroll
-        for (int j = 0; j < W; j++) in[j] = h[((long)b * W + j) * n2 + p];
-        float2 e[MM];
-#pragma unroll
-        for (int kx = 0; kx < MM; kx++) e[kx] = tw[(long)kx * n + x];
-        for (int c = 0; c < W; c++) {
-            float acc = bs[c];
-#pragma unroll
-            for (int j = 0; j < W; j++) acc += ws[c * W + j] * in[j];
-#pragma unroll
-            for (int kx = 0; kx < MM; kx++) {
-                const float2 v = vs[c * MM + kx];
-                acc += v.x * e[kx].x - v.y * e[kx].y;
-            }
-            out[((long)b * W + c) * n2 + p] = act ? gelu(acc) : acc;
-        }
-    }
-}
-
 // 8 floats rounded to bfloat16 (nearest even), packed as one 16-byte core row
 __device__ __forceinline__ uint4 pack8_bf16(const float *f)
 {
