@@ -163,15 +163,19 @@ fch_status fch_get_state_device(fch_ctx *ctx, void *u_dev, int dtype);
  * with i_tol = psd_itol; ETDRK2 eqs. (ETDRK2), (ETD-L). Enqueued without waiting;
  * PSD enqueues its iterations in chunks of four (as many chunks as the previous
  * solve took, then one at a time) and waits after each batch to read the stopping
- * test; chunks after convergence return at once on the device. */
+ * test; chunks after convergence return at once on the device. (Captured steps --
+ * fch_run_fixed, fch_run_adaptive, ensembles -- iterate PSD on the device instead.) */
 fch_status fch_step(fch_ctx *ctx, fch_scheme scheme, double dt);
 
 /* nsteps fixed steps of size dt, as nsteps fch_step calls, without host work
  * between them: after the first step, one step captured as a CUDA graph is replayed
- * (IMEX, SAV, ETD; PSD, whose stopping test runs on the host, and contexts with
- * per-pass timing on take fch_step calls). Enqueued; a failure inside the steps
- * (non-finite values) shows at the next call that reads the control block
- * (fch_synchronize, fch_get_stats, fch_get_state). */
+ * (contexts with per-pass timing on take fch_step calls). In the graph, PSD's
+ * iterations run in a conditional while node: a one-thread launch after each chunk
+ * of four iterations reads the stopping test on the device and ends the loop once
+ * it holds, the run has failed, or psd_max_iter / 4 + 3 chunks have run. Enqueued; a
+ * failure inside the steps (non-finite values, PSD not converged) shows at the next
+ * call that reads the control block (fch_synchronize, fch_get_stats,
+ * fch_get_state). */
 fch_status fch_run_fixed(fch_ctx *ctx, fch_scheme scheme, double dt, long long nsteps);
 
 /* E(u^n) of eq. (Functional), FP64 accumulation (waits for the stream). */
@@ -202,8 +206,11 @@ fch_status fch_get_stats(fch_ctx *ctx, fch_stats *stats);
  * is needed between trials):
  *  begin   -- sets sigma_tol and t_final, takes the backward-Euler start if the
  *             history is empty and evaluates the F history; does not wait;
- *  enqueue -- enqueues n trial steps (IMEX, SAV, ETD: no wait; PSD waits inside
- *             each solve to test convergence); trials past t_final do nothing;
+ *  enqueue -- enqueues n trial steps without waiting: the first trial of a run
+ *             launches pass by pass (PSD waits inside it to test convergence),
+ *             later ones replay one captured trial (PSD's iterations in a
+ *             conditional while node, as in fch_run_fixed); trials past t_final do
+ *             nothing;
  *  end     -- waits, reports device errors, fills stats (may be NULL). */
 fch_status fch_adaptive_begin(fch_ctx *ctx, fch_scheme scheme, double sigma_tol, double t_final);
 fch_status fch_adaptive_enqueue(fch_ctx *ctx, int n_trials);
@@ -238,8 +245,9 @@ fch_status fch_pass_times(fch_ctx *ctx, double *ms, long long *launches, int n);
  * branches run concurrently), is launched until every member has reached t_final,
  * or a member has failed, or max_launches launches (> 0) have run (FCH_ETIMEOUT).
  * A member that has reached t_final skips its passes in later launches. stats
- * (m entries, may be NULL) receive every member's fch_stats. Schemes: FCH_IMEX,
- * FCH_SAV, FCH_ETD (PSD's convergence test runs on the host: FCH_EINVAL). Members
+ * (m entries, may be NULL) receive every member's fch_stats. Every scheme; a PSD
+ * member iterates in a conditional while node of its branch (as fch_run_fixed), so
+ * members with different iteration counts do not wait for one another. Members
  * with per-pass timing on: FCH_ESTATE. Returns after the members' streams are idle. */
 typedef struct fch_ensemble fch_ensemble;
 #define FCH_ENSEMBLE_MAX 4096

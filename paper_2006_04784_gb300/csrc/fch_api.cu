@@ -259,17 +259,19 @@ struct fch_ctx {
     double *ls_part;
     cudaEvent_t ls_ev[2];
     long long *nfft_dev;
-    unsigned int *ticket;
+    unsigned int *ticket; // [0] the pass-tail ticket, [1] the PSD loop's chunk count
     long long nfft_base;
     bool have_state, failed, have_F;
     fch_scheme ad_scheme;           // scheme of the adaptive run begun last
     bool ad_open;
-    // one trial step (trial + F + decide) of IMEX, SAV, ETD captured as a CUDA graph:
+    // one trial step (trial + F + decide) of each scheme captured as a CUDA graph:
     // every launch reads its per-trial state from the control block, so the same
-    // graph replays any trial; PSD (host convergence test) is not captured
+    // graph replays any trial; PSD's iterations run in a conditional while node
     cudaGraphExec_t trial_graph[4];
     bool trial_warm[4], trial_nograph[4];
-    cudaGraphExec_t psd_graph; // one chunk of PSD iterations
+    bool capturing;            // the stream is being captured: PSD loops on the device
+    cudaStream_t bstream;      // captures the body of the PSD while node (made on first use)
+    cudaGraphExec_t psd_graph; // one chunk of PSD iterations (eager trials)
     bool psd_warm, psd_nograph;
     int psd_hint;              // iterations the last PSD solve took
     // one fixed step (step size fixed_dt[s]) of IMEX, SAV, ETD captured as a CUDA graph
@@ -675,8 +677,8 @@ extern "C" fch_status fch_create(const fch_grid *g, const fch_params *p, void *s
     if (e == cudaSuccess) e = cudaMalloc((void **)&ctx->staging, sizeof(double) * N * N * 2);
     if (e == cudaSuccess) e = cudaMalloc((void **)&ctx->nfft_dev, sizeof(long long));
     if (e == cudaSuccess) e = cudaMemsetAsync(ctx->nfft_dev, 0, sizeof(long long), ctx->stream);
-    if (e == cudaSuccess) e = cudaMalloc((void **)&ctx->ticket, sizeof(unsigned int));
-    if (e == cudaSuccess) e = cudaMemsetAsync(ctx->ticket, 0, sizeof(unsigned int), ctx->stream);
+    if (e == cudaSuccess) e = cudaMalloc((void **)&ctx->ticket, 2 * sizeof(unsigned int));
+    if (e == cudaSuccess) e = cudaMemsetAsync(ctx->ticket, 0, 2 * sizeof(unsigned int), ctx->stream);
     // every state array starts at zero: a backward-Euler start multiplies u^{n-1} by
     // c = 0, which must not meet whatever the memory held before (0 x NaN = NaN)
     for (void **b : bufs)
@@ -754,6 +756,7 @@ extern "C" fch_status fch_destroy(fch_ctx *ctx)
         if (ctx->fixed_graph[i]) cudaGraphExecDestroy(ctx->fixed_graph[i]);
     }
     if (ctx->psd_graph) cudaGraphExecDestroy(ctx->psd_graph);
+    if (ctx->bstream) cudaStreamDestroy(ctx->bstream);
     if (ctx->own_stream && ctx->stream) cudaStreamDestroy(ctx->stream);
     free(ctx);
     return FCH_OK;
@@ -928,6 +931,71 @@ static fch_status psd_iterate(fch_ctx *ctx)
     return FCH_OK;
 }
 
+// The condition of the captured PSD loop (one thread): arm (before the while node)
+// zeroes the chunk count, the body's last launch counts its chunk. The loop goes on
+// while the stopping test has not held, the run has not stopped (done or a failure:
+// OP_PSD_CHECK stops it at psd_max_iter iterations) and fewer than `limit` chunks ran,
+// so it ends after at most `limit` chunks whatever the control block holds.
+__global__ void fch_psd_loop_kernel(cudaGraphConditionalHandle h, const fch_ctrl *c, unsigned int *count, int arm,
+                                    unsigned int limit)
+{
+    const unsigned int n = arm ? 0u : *count + 1u;
+    *count = n;
+    const bool more = !c->done && !c->status && !c->psd_conv && n < limit;
+    cudaGraphSetConditional(h, more ? 1u : 0u);
+}
+
+// PSD iterations inside a stream capture: a while node whose body is one chunk of
+// iterations and the condition launch, then the copy of the converged iterate. The
+// launches next to the node go without programmatic serialization (a programmatic
+// edge joins two kernel nodes only), and so do the body's.
+static fch_status psd_loop_captured(fch_ctx *ctx)
+{
+    if (!ctx->bstream) CKC(ctx, cudaStreamCreateWithFlags(&ctx->bstream, cudaStreamNonBlocking));
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    cudaGraph_t g = nullptr;
+    const cudaGraphNode_t *deps = nullptr;
+    const cudaGraphEdgeData *edata = nullptr;
+    size_t nd = 0;
+    CKC(ctx, cudaStreamGetCaptureInfo(ctx->stream, &cs, nullptr, &g, &deps, &edata, &nd));
+    if (cs != cudaStreamCaptureStatusActive || !g) return FCH_ESTATE;
+    cudaGraphConditionalHandle h;
+    CKC(ctx, cudaGraphConditionalHandleCreate(&h, g, 0, 0));
+    const unsigned int limit = (unsigned int)(ctx->p.psd_max_iter / kPsdChunk + 3);
+    unsigned int *count = ctx->ticket + 1;
+    fch_psd_loop_kernel<<<1, 1, 0, ctx->stream>>>(h, ctx->dctrl, count, 1, limit);
+    CKC(ctx, cudaGetLastError());
+    CKC(ctx, cudaStreamGetCaptureInfo(ctx->stream, &cs, nullptr, &g, &deps, &edata, &nd));
+    cudaGraphNodeParams np = {};
+    np.type = cudaGraphNodeTypeConditional;
+    np.conditional.handle = h;
+    np.conditional.type = cudaGraphCondTypeWhile;
+    np.conditional.size = 1;
+    cudaGraphNode_t node;
+    CKC(ctx, cudaGraphAddNode(&node, g, deps, edata, nd, &np));
+    const cudaGraph_t body = np.conditional.phGraph_out[0];
+    CKC(ctx, cudaStreamBeginCaptureToGraph(ctx->bstream, body, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed));
+    const cudaStream_t outer = ctx->stream;
+    const int pdl = ctx->kp.pdl;
+    ctx->stream = ctx->bstream;
+    ctx->kp.pdl = 0;
+    fch_status s = psd_chunk_eager(ctx);
+    if (s == FCH_OK) {
+        fch_psd_loop_kernel<<<1, 1, 0, ctx->stream>>>(h, ctx->dctrl, count, 0, limit);
+        if (cudaGetLastError() != cudaSuccess) s = FCH_ECUDA;
+    }
+    ctx->stream = outer;
+    cudaGraph_t bg = nullptr;
+    const cudaError_t e = cudaStreamEndCapture(ctx->bstream, &bg);
+    if (s == FCH_OK && e != cudaSuccess) s = FCH_ECUDA;
+    if (s == FCH_OK && cudaStreamUpdateCaptureDependencies(ctx->stream, &node, nullptr, 1,
+                                                           cudaStreamSetCaptureDependencies) != cudaSuccess)
+        s = FCH_ECUDA;
+    if (s == FCH_OK) s = col(ctx, CM_START, FCH_SRC_V, FCH_FL_COPYV);
+    ctx->kp.pdl = pdl;
+    return s;
+}
+
 static fch_status enqueue_trial(fch_ctx *ctx, fch_scheme scheme, bool pack_f)
 {
     const int pf = pack_f ? FCH_FL_PACK_F : 0;
@@ -968,7 +1036,7 @@ static fch_status enqueue_trial(fch_ctx *ctx, fch_scheme scheme, bool pack_f)
         return FCH_OK;
     case FCH_PSD:
         TRY(col(ctx, CM_START, 4, 128));
-        return psd_iterate(ctx);
+        return ctx->capturing ? psd_loop_captured(ctx) : psd_iterate(ctx);
     }
     return FCH_EINVAL;
 }
@@ -1005,8 +1073,8 @@ extern "C" fch_status fch_run_fixed(fch_ctx *ctx, fch_scheme scheme, double dt, 
     if (!ctx || !(dt > 0) || nsteps < 0 || scheme < FCH_IMEX || scheme > FCH_ETD) return FCH_EINVAL;
     if (!ctx->have_state || ctx->failed) return FCH_ESTATE;
     if (nsteps == 0) return FCH_OK;
-    // PSD tests convergence on the host; with per-pass timing every launch is timed
-    if (scheme == FCH_PSD || ctx->timing) {
+    // with per-pass timing every launch is timed
+    if (ctx->timing) {
         for (long long i = 0; i < nsteps; i++) TRY(fch_step(ctx, scheme, dt));
         return FCH_OK;
     }
@@ -1028,7 +1096,9 @@ extern "C" fch_status fch_run_fixed(fch_ctx *ctx, fch_scheme scheme, double dt, 
         cudaGraph_t g = nullptr;
         bool ok = cudaStreamBeginCapture(ctx->stream, cudaStreamCaptureModeRelaxed) == cudaSuccess;
         if (ok) {
+            ctx->capturing = true;
             s = enqueue_fixed_step(ctx, scheme, dt);
+            ctx->capturing = false;
             ok = cudaStreamEndCapture(ctx->stream, &g) == cudaSuccess && g && s == FCH_OK;
         }
         if (ok) ok = cudaGraphInstantiate(&ctx->fixed_graph[scheme], g, 0) == cudaSuccess;
@@ -1400,7 +1470,9 @@ static bool capture_trial(fch_ctx *ctx)
         cudaGetLastError();
         return false;
     }
+    ctx->capturing = true;
     fch_status s = enqueue_adaptive_trial(ctx);
+    ctx->capturing = false;
     cudaGraph_t g = nullptr;
     cudaError_t e = cudaStreamEndCapture(ctx->stream, &g);
     if (s != FCH_OK || e != cudaSuccess || !g) {
@@ -1426,7 +1498,7 @@ extern "C" fch_status fch_adaptive_enqueue(fch_ctx *ctx, int n)
     for (int i = 0; i < n; i++) {
         // the first trial runs eagerly (it also sets the kernels' attributes);
         // later ones replay the captured graph unless per-pass timing is on
-        const bool graph_ok = sc != FCH_PSD && !ctx->timing && ctx->trial_warm[sc] && !ctx->trial_nograph[sc];
+        const bool graph_ok = !ctx->timing && ctx->trial_warm[sc] && !ctx->trial_nograph[sc];
         if (graph_ok && !ctx->trial_graph[sc] && !capture_trial(ctx)) ctx->trial_nograph[sc] = true;
         if (graph_ok && ctx->trial_graph[sc]) {
             ctx->hc_fresh = false;
@@ -1438,7 +1510,7 @@ extern "C" fch_status fch_adaptive_enqueue(fch_ctx *ctx, int n)
             ctx->failed = true;
             return s;
         }
-        if (sc != FCH_PSD) ctx->trial_warm[sc] = true;
+        ctx->trial_warm[sc] = true;
     }
     return FCH_OK;
 }
@@ -1497,7 +1569,7 @@ extern "C" fch_status fch_run_adaptive(fch_ctx *ctx, fch_scheme scheme, double s
             out_of_attempts = true;
             break;
         }
-        long long nb = scheme == FCH_PSD ? 1 : ctx->p.sync_every;
+        long long nb = ctx->p.sync_every;
         if (max_attempts > 0 && nb > max_attempts - used) nb = max_attempts - used;
         const fch_status s = fch_adaptive_enqueue(ctx, (int)nb);
         if (s != FCH_OK) {
@@ -1654,7 +1726,9 @@ static fch_status ensemble_capture(fch_ensemble *e, const fch_scheme *schemes, i
     for (int i = 0; i < e->m && s == FCH_OK; i++) {
         fch_ctx *c = e->ctx[i];
         if (cudaStreamWaitEvent(c->stream, e->fork, 0) != cudaSuccess) s = FCH_ECUDA;
+        c->capturing = true;
         for (int r = 0; r < rounds && s == FCH_OK; r++) s = enqueue_adaptive_trial(c);
+        c->capturing = false;
         if (s == FCH_OK && cudaEventRecord(e->join[i], c->stream) != cudaSuccess) s = FCH_ECUDA;
         if (s == FCH_OK && cudaStreamWaitEvent(e->stream, e->join[i], 0) != cudaSuccess) s = FCH_ECUDA;
     }
@@ -1688,8 +1762,7 @@ extern "C" fch_status fch_ensemble_run_adaptive_each(fch_ensemble *e, const fch_
 {
     if (!e || !schemes || !sigmas || rounds < 1 || rounds > 1024 || max_launches < 0) return FCH_EINVAL;
     for (int i = 0; i < e->m; i++) {
-        if (!(sigmas[i] > 0) || (schemes[i] != FCH_IMEX && schemes[i] != FCH_SAV && schemes[i] != FCH_ETD))
-            return FCH_EINVAL;
+        if (!(sigmas[i] > 0) || schemes[i] < FCH_IMEX || schemes[i] > FCH_ETD) return FCH_EINVAL;
         if (e->ctx[i]->timing) return FCH_ESTATE;
     }
     // every member begins (host checks, backward-Euler start) and runs one trial
@@ -2302,6 +2375,19 @@ extern "C" int fch_debug_tile(int n, int prec, int row, int col, int *out)
     out[6] = g.rpb;
     out[7] = g.P;
     return fch_tile_valid(n, prec, row, col) ? 1 : 0;
+}
+
+// which trials and fixed steps of a context replay a captured graph (tests):
+// out[s] for scheme s: 1 captured, -1 capture failed (eager launches), 0 not yet;
+// out[4 + s]: 1 if a fixed step of scheme s is captured
+extern "C" int fch_debug_graphs(const fch_ctx *ctx, int *out)
+{
+    if (!ctx || !out) return 1;
+    for (int s = 0; s < 4; s++) {
+        out[s] = ctx->trial_graph[s] ? 1 : ctx->trial_nograph[s] ? -1 : 0;
+        out[4 + s] = ctx->fixed_graph[s] ? 1 : 0;
+    }
+    return 0;
 }
 
 // host-side geometry query (used by the CPU tests of the launch configuration)

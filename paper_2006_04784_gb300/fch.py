@@ -168,6 +168,8 @@ def lib():
         L.fch_pass_timing.argtypes = [vp, C.c_int]
         L.fch_pass_times.argtypes = [vp, C.POINTER(C.c_double), C.POINTER(C.c_longlong), C.c_int]
         L.fch_debug_geometry.argtypes = [C.c_int, C.c_int, C.POINTER(C.c_int)]
+        L.fch_debug_graphs.argtypes = [vp, C.POINTER(C.c_int)]
+        L.fch_debug_graphs.restype = C.c_int
         for name in EXPORTS:
             if name not in ("fch_status_string", "fch_last_cuda_error"):
                 getattr(L, name).restype = C.c_int
@@ -414,6 +416,13 @@ class Context:
         st = Stats()
         self._ck(lib().fch_adaptive_end(self._h, C.byref(st)), "fch_adaptive_end")
         return st.as_dict()
+
+    def debug_graphs(self):
+        """per scheme: (trial graph 1 captured / -1 failed / 0 not yet, fixed-step graph 1/0)"""
+        out = (C.c_int * 8)()
+        if lib().fch_debug_graphs(self._h, out):
+            raise ValueError("fch_debug_graphs")
+        return {name: (out[i], out[4 + i]) for name, i in SCHEMES.items()}
 
     def pass_timing(self, on: bool):
         self._ck(lib().fch_pass_timing(self._h, int(bool(on))), "fch_pass_timing")

@@ -39,7 +39,7 @@ def member_init(n, i):
 
 
 @pytest.mark.parametrize("prec", [0, 2])
-@pytest.mark.parametrize("scheme", ["imex", "sav", "etd"])
+@pytest.mark.parametrize("scheme", ["imex", "sav", "etd", "psd"])
 def test_ensemble_members_match_solo_runs(scheme, prec):
     sizes = [64, 128, 64, 32]
     tf = 2e-3
@@ -83,8 +83,6 @@ def test_ensemble_errors_and_budget():
     with fch.Ensemble(sizes, params) as ens:
         for i, n in enumerate(sizes):
             ens[i].set_state(member_init(n, i))
-        with pytest.raises(fch.FchError):
-            ens.run_adaptive("psd", 1e-5, 1e-3)
         st = ens.run_adaptive("imex", 1e-5, 10.0, rounds=2, max_launches=3, raise_on_timeout=False)
         # the backward-Euler start, one trial on the member's stream, then 3 launches
         # of 2 trials each
@@ -102,7 +100,7 @@ def test_ensemble_sweep_members_match_solo_runs(prec):
     # a scheme and a sigma_tol per member: every member equals its solo run, and
     # rerunning the same ensemble with the schemes permuted recaptures the graph
     sizes = [64, 64, 32, 64]
-    schemes = ["imex", "sav", "etd", "imex"]
+    schemes = ["imex", "sav", "etd", "psd"]
     sigmas = [1e-4, 1e-5, 3e-5, 1e-6]
     tf = 2e-3
     params = [member_params(i, prec) for i in range(len(sizes))]
@@ -128,8 +126,23 @@ def test_ensemble_sweep_errors():
         for i, n in enumerate(sizes):
             ens[i].set_state(member_init(n, i))
         with pytest.raises(fch.FchError):
-            ens.run_adaptive_each(["imex", "psd"], [1e-5, 1e-5], 1e-3)
-        with pytest.raises(fch.FchError):
             ens.run_adaptive_each(["imex", "sav"], [1e-5, 0.0], 1e-3)
         st = ens.run_adaptive_each(["sav", "imex"], [1e-5, 1e-4], 1e-3, rounds=2)
         assert all(s["t"] == pytest.approx(1e-3, rel=1e-12) for s in st)
+
+
+def test_ensemble_psd_nonconvergence_is_reported():
+    # a PSD member whose iteration stops at psd_max_iter (4) in a replayed trial
+    # ends the ensemble run with FCH_ENOCONV; the IMEX member is unaffected
+    sizes = [32, 32]
+    params = [member_params(i, 0) for i in range(2)]
+    params[0].psd_max_iter = 4
+    params[0].eta1 = 0.1
+    with fch.Ensemble(sizes, params) as ens:
+        ens[0].set_state(I.multimode_bilayer(32, seed=100))
+        ens[1].set_state(member_init(32, 1))
+        with pytest.raises(fch.FchError) as e:
+            ens.run_adaptive_each(["psd", "imex"], [1e-5, 1e-5], 2e-3, rounds=2)
+        assert e.value.status == 4
+        st = ens[0].stats()
+        assert st["n_steps"] >= 5 and st["t"] < 2e-3 and st["last_psd_iter"] == 4

@@ -372,6 +372,54 @@ def test_errors_are_reported():
         assert e.value.status == 7
 
 
+
+@pytest.mark.parametrize("prec", [0, 2])
+def test_psd_device_loop_matches_host_loop(prec):
+    # captured PSD trials and steps iterate in a conditional while node that reads
+    # the stopping test on the device; with per-pass timing on, the same runs launch
+    # pass by pass and the host reads the test: identical fields and counts
+    n = 64
+    p = lib_params(0.0, zero_stab_cap=1, prec=prec)
+    u0 = I.circle_bilayer(n, noise=1e-3)
+    out = []
+    for timing in (True, False):
+        with fch.Context(n, p) as ctx:
+            ctx.pass_timing(timing)
+            ctx.set_state(u0)
+            st = ctx.run_adaptive("psd", 1e-5, 2e-3)
+            ua = ctx.get_state()
+            ctx.set_state(u0)
+            ctx.run_fixed("psd", 2e-5, 6)
+            out.append((st, ua, ctx.get_state(), ctx.stats()))
+            assert ctx.debug_graphs()["psd"] == ((0, 0) if timing else (1, 1))
+    (s0, a0, f0, c0), (s1, a1, f1, c1) = out
+    for k in ("n_steps", "n_rejects", "n_psd_iter", "last_psd_iter"):
+        assert s0[k] == s1[k], k
+        assert c0[k] == c1[k], k
+    assert s1["n_steps"] > 10 and s1["t"] == pytest.approx(2e-3, rel=1e-13)
+    assert c1["n_steps"] == 6 and c1["n_psd_iter"] > 6
+    assert np.array_equal(a0, a1) and np.array_equal(f0, f1)
+
+
+def test_psd_nonconvergence_inside_captured_trials():
+    # psd_max_iter = 4: the start and the first trials converge in one or two
+    # iterations, a later (replayed) trial does not; the device loop stops there and
+    # the run reports FCH_ENOCONV with the time reached
+    n = 32
+    p = lib_params(0.0, zero_stab_cap=1, psd_max_iter=4)
+    p.eta1 = 0.1
+    with fch.Context(n, p) as ctx:
+        ctx.set_state(I.multimode_bilayer(n, seed=100))
+        with pytest.raises(fch.FchError) as e:
+            ctx.run_adaptive("psd", 1e-5, 2e-3)
+        assert e.value.status == 4
+        st = ctx.stats()
+        assert st["n_steps"] >= 5 and st["t"] < 2e-3 and st["last_psd_iter"] == 4
+        with pytest.raises(fch.FchError) as e:
+            ctx.run_adaptive("psd", 1e-5, 2e-3)
+        assert e.value.status == 7
+
+
 # --------------------------------------------------------------------------- full size (1024^2, mixed)
 def test_mixed_1024_fixed_steps_vs_oracle():
     # the benchmark grid in single precision (warp transforms at N = 1024): a state
