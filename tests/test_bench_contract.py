@@ -32,6 +32,10 @@ def test_reference_arm_line():
     assert d["e2e"]["value"] == d["value"] and d["e2e"]["h2d_bytes_per_step"] == 0
     assert d["cpu_baseline"]["kind"] == "oracle" and d["cpu_baseline"]["cores"] >= 1
     assert "workload" in d["config"]
+    # the reference arm times the GPU arm's own workload (default precision: fp32x2)
+    sys.path.insert(0, ROOT)
+    import bench
+    assert d["config"] == dict(bench.config("fp32x2"), parallelism="single")
 
 
 @pytest.mark.gpu
