@@ -92,7 +92,10 @@ typedef struct {
                           * fch_autotune_step picks; 0: tile_row/tile_col */
     int tile_row, tile_col; /* pass tiles: 0 default (at n = 1024 two-block-cluster
                           * column passes for FCH_FP64 / FCH_FP32X2, warp-level row passes
-                          * for FCH_MIXED; else the kernel built for the grid size); -1 the shared-memory
+                          * for FCH_MIXED; both 0 at n = 128 / 256 in FCH_FP64 and FCH_FP32X2:
+                          * the generic kernels with the step tuner's GB300 tiles, 2 rows and
+                          * 2 (FP64) or 4 pairs at 128, 1 row and 2 (FP64) or the built
+                          * column pairs at 256; else the kernel built for the grid size); -1 the shared-memory
                           * kernels without those; -2 (tile_col, FCH_MIXED at n = 1024) the
                           * warp-level column passes; r > 0 the generic row
                           * kernel with r rows per block / the generic column kernel with

@@ -664,6 +664,20 @@ extern "C" fch_status fch_create(const fch_grid *g, const fch_params *p, void *s
         trow = t.tile_row;
         tcol = t.tile_col;
     }
+    // At 128^2 and 256^2 in double and double-float the compile-time kernels give a
+    // block several rows (column pairs): 8 to 32 blocks for 152 SMs. Unless asked for
+    // other tiles, these grids take the tiles the step tuner (fch_autotune_step,
+    // adaptive IMEX trials) picked on GB300: 1.6-1.7x the trials per second in double,
+    // 1.08-1.14x in double-float.
+    if (!p->autotune && trow == 0 && tcol == 0 && ctx->prec != FCH_MIXED) {
+        if (N == 128) {
+            trow = 2;
+            tcol = ctx->prec == FCH_FP64 ? 2 : 4;
+        } else if (N == 256) {
+            trow = 1;
+            tcol = ctx->prec == FCH_FP64 ? 2 : 0;
+        }
+    }
     ctx->geom = fch_geometry_tiled(N, ctx->prec == FCH_MIXED, trow, tcol);
     void **bufs[] = {&ctx->U[0], &ctx->U[1], &ctx->U[2], &ctx->F[0], &ctx->F[1], &ctx->F[2],
                      &ctx->Pb, &ctx->Qb, &ctx->Vb, &ctx->Nb};
