@@ -92,16 +92,20 @@ typedef struct {
                           * fch_autotune_step picks; 0: tile_row/tile_col */
     int tile_row, tile_col; /* pass tiles: 0 default (at n = 1024 two-block-cluster
                           * column passes for FCH_FP64 / FCH_FP32X2, warp-level row passes
-                          * for FCH_MIXED; both 0 at n = 128 / 256 in FCH_FP64 and FCH_FP32X2:
-                          * the generic kernels with the step tuner's GB300 tiles, 2 rows and
-                          * 2 (FP64) or 4 pairs at 128, 1 row and 2 (FP64) or the built
-                          * column pairs at 256; else the kernel built for the grid size); -1 the shared-memory
-                          * kernels without those; -2 (tile_col, FCH_MIXED at n = 1024) the
-                          * warp-level column passes; r > 0 the generic row
-                          * kernel with r rows per block / the generic column kernel with
-                          * r column pairs per block (powers of two that fit the row
-                          * kernel's 256 threads or the column kernel's 1024 threads a
-                          * block and a block's shared memory; else FCH_EINVAL) */
+                          * for FCH_MIXED; in FCH_FP64 and FCH_FP32X2 at n = 128 / 256 the
+                          * generic kernels with 2 / 1 rows a block and columns as -3, and
+                          * in FCH_FP32X2 at n = 512 columns as -3; else the kernel built
+                          * for the grid size); -1 the shared-memory kernels built for the
+                          * size, without clusters or warp-level rows; -2 (tile_col,
+                          * FCH_MIXED at n = 1024) the warp-level column passes; r > 0 the
+                          * generic row kernel with r rows per block / the generic column
+                          * kernel with r column pairs per block; tile_col = -2 - P
+                          * (-3, -4, -6, ...) the generic column kernel with P pairs per
+                          * block at four points a thread (radix-4 stages, twice the
+                          * threads). Generic tiles are powers of two that fit whole
+                          * warps, the row kernel's 256 threads or the column kernel's
+                          * 1024 threads a block and a block's shared memory; else
+                          * FCH_EINVAL */
 } fch_params;
 
 typedef struct {

@@ -68,6 +68,15 @@ fch_geom fch_geometry_tiled(int N, int prec, int tile_row, int tile_col)
         g.col_blocks = N / (2 * tile_col);
         g.col_smem = (N + 2 * tile_col * SL) * csz;
     }
+    if (tile_col <= -3) {
+        // the generic kernel with P = -2 - tile_col pairs a block and four points a
+        // thread (radix-4 stages): twice the threads of the tile P
+        const int P = -2 - tile_col;
+        g.P = P;
+        g.col_threads = P * N / 2;
+        g.col_blocks = N / (2 * P);
+        g.col_smem = (N + 2 * P * SL) * csz;
+    }
     if (tile_row > 0) {
         g.rpb = tile_row;
         g.row_threads = tile_row * (N / 8);
@@ -77,9 +86,10 @@ fch_geom fch_geometry_tiled(int N, int prec, int tile_row, int tile_col)
     return g;
 }
 
-// generic-kernel tiles: powers of two, whole blocks, at most 256 threads for the row
-// kernel (its launch bound) and 1024 for the column kernel, and the opt-in shared
-// memory of a block (227 KiB, less the kernels' 1 KiB of static arrays)
+// generic-kernel tiles: powers of two, whole blocks, whole warps (the block sums
+// shuffle across all 32 lanes), at most 256 threads for the row kernel (its launch
+// bound) and 1024 for the column kernel, and the opt-in shared memory of a block
+// (227 KiB, less the kernels' 1 KiB of static arrays)
 bool fch_tile_valid(int N, int prec, int tile_row, int tile_col)
 {
     const int smem_max = 227 * 1024 - 1024;
@@ -87,15 +97,16 @@ bool fch_tile_valid(int N, int prec, int tile_row, int tile_col)
     if (tile_row > 0) {
         if ((tile_row & (tile_row - 1)) || tile_row > N) return false;
         const fch_geom g = fch_geometry_tiled(N, prec, tile_row, 0);
-        if (g.row_threads > 256 || g.row_smem > smem_max) return false;
+        if (g.row_threads > 256 || (g.row_threads & 31) || g.row_smem > smem_max) return false;
     } else if (tile_row < -1) {
         return false;
     }
-    if (tile_col > 0) {
-        if ((tile_col & (tile_col - 1)) || tile_col < pmin || tile_col > N / 2) return false;
+    if (tile_col > 0 || tile_col <= -3) {
+        const int P = tile_col > 0 ? tile_col : -2 - tile_col;
+        if ((P & (P - 1)) || P < pmin || P > N / 2) return false;
         const fch_geom g = fch_geometry_tiled(N, prec, 0, tile_col);
-        if (g.col_threads > 1024 || g.col_smem > smem_max) return false;
-    } else if (tile_col < -2 || (tile_col == -2 && !(prec == 1 && N == 1024))) {
+        if (g.col_threads > 1024 || (g.col_threads & 31) || g.col_smem > smem_max) return false;
+    } else if (tile_col == -2 && !(prec == 1 && N == 1024)) {
         return false;
     }
     return true;
@@ -249,7 +260,7 @@ struct fch_ctx {
     bool hc_fresh;       // hc equals the device's block: no launch since the last copy
     fch_ctrl *dctrl;
     double *part;
-    void *U[3], *F[3], *Pb, *Qb, *Vb, *Nb, *Z, *tw, *tw2;
+    void *U[3], *F[3], *Pb, *Qb, *Vb, *Nb, *Z, *tw, *tw4, *tw2;
     void *Rs[3];         // real-space (u, Lap u) of the state slots, kept by adaptive trials
     bool rvalid;         // Rs holds u^n (and u^{n-1} when k_n > 0)
     double *staging;     // N*N doubles for host io
@@ -343,16 +354,18 @@ static int ilog2(int n)
 // read them: the stage with sub-transform length Ns and radix R holds
 // exp(-2 pi i r j / (Ns R)) at Ns - 8 + (r-1) Ns + j, r = 1..R-1, j < Ns.
 // Stages: radix 8 while >= 3 bits remain, then one radix-4 or radix-2 stage.
-template <typename T> static void make_twiddles(int N, T *out)
+// per-stage twiddles of the shared-memory transforms (fft_smem) whose stages have
+// radix 2^lp but the last: lp = 3 (eight points a thread) or 2 (four)
+template <typename T> static void make_twiddles(int N, T *out, int lp = 3)
 {
     for (int m = 0; m < 2 * N; m++) out[m] = 0;
     int Ns = 1, rem = ilog2(N);
     while (rem > 0) {
-        const int lr = rem >= 3 ? 3 : rem, R = 1 << lr;
+        const int lr = rem >= lp ? lp : rem, R = 1 << lr;
         if (Ns > 1)
             for (int r = 1; r < R; r++)
                 for (int j = 0; j < Ns; j++) {
-                    const int m = Ns - 8 + (r - 1) * Ns + j;
+                    const int m = Ns - (1 << lp) + (r - 1) * Ns + j;
                     const double a = -2.0 * M_PI * (double)(r * j) / (double)(Ns * R);
                     out[2 * m] = (T)cos(a);
                     out[2 * m + 1] = (T)sin(a);
@@ -378,25 +391,25 @@ static cudaError_t upload_tw2(void **dst, cudaStream_t s)
     return e;
 }
 
-static fch_status upload_twiddles(fch_ctx *ctx, int N, int prec, void *dst, cudaStream_t s)
+static fch_status upload_twiddles(fch_ctx *ctx, int N, int prec, void *dst, cudaStream_t s, int lp = 3)
 {
     if (prec == FCH_FP32X2) {
         fch::df *h = (fch::df *)malloc(sizeof(fch::df) * 2 * N);
-        make_twiddles(N, h);
+        make_twiddles(N, h, lp);
         cudaError_t e = cudaMemcpyAsync(dst, h, sizeof(fch::df) * 2 * N, cudaMemcpyHostToDevice, s);
         cudaStreamSynchronize(s);
         free(h);
         if (e != cudaSuccess) return FCH_ECUDA;
     } else if (prec) {
         float *h = (float *)malloc(sizeof(float) * 2 * N);
-        make_twiddles(N, h);
+        make_twiddles(N, h, lp);
         cudaError_t e = cudaMemcpyAsync(dst, h, sizeof(float) * 2 * N, cudaMemcpyHostToDevice, s);
         cudaStreamSynchronize(s);
         free(h);
         if (e != cudaSuccess) return FCH_ECUDA;
     } else {
         double *h = (double *)malloc(sizeof(double) * 2 * N);
-        make_twiddles(N, h);
+        make_twiddles(N, h, lp);
         cudaError_t e = cudaMemcpyAsync(dst, h, sizeof(double) * 2 * N, cudaMemcpyHostToDevice, s);
         cudaStreamSynchronize(s);
         free(h);
@@ -665,18 +678,16 @@ extern "C" fch_status fch_create(const fch_grid *g, const fch_params *p, void *s
         tcol = t.tile_col;
     }
     // At 128^2 and 256^2 in double and double-float the compile-time kernels give a
-    // block several rows (column pairs): 8 to 32 blocks for 152 SMs. Unless asked for
-    // other tiles, these grids take the tiles the step tuner (fch_autotune_step,
-    // adaptive IMEX trials) picked on GB300: 1.6-1.7x the trials per second in double,
-    // 1.08-1.14x in double-float.
-    if (!p->autotune && trow == 0 && tcol == 0 && ctx->prec != FCH_MIXED) {
-        if (N == 128) {
-            trow = 2;
-            tcol = ctx->prec == FCH_FP64 ? 2 : 4;
-        } else if (N == 256) {
-            trow = 1;
-            tcol = ctx->prec == FCH_FP64 ? 2 : 0;
-        }
+    // block several rows (column pairs): 8 to 32 blocks for 152 SMs, each pair's chain
+    // of dependent work long. There the default (tile 0, asked for or tuned) is the
+    // row tile the step tuner (fch_autotune_step, adaptive IMEX trials) picked on GB300
+    // and one column pair a block at four points a thread (tile_col -3), and in
+    // double-float at 512^2 the same columns; -1 still asks for the compile-time
+    // kernels. Against those: 2.0x the trials per second in double, 1.3-1.4x in
+    // double-float; 1.09x at 512^2.
+    if (ctx->prec != FCH_MIXED) {
+        if (trow == 0 && (N == 128 || N == 256)) trow = N == 128 ? 2 : 1;
+        if (tcol == 0 && (N == 128 || N == 256 || (N == 512 && ctx->prec == FCH_FP32X2))) tcol = -3;
     }
     ctx->geom = fch_geometry_tiled(N, ctx->prec == FCH_MIXED, trow, tcol);
     void **bufs[] = {&ctx->U[0], &ctx->U[1], &ctx->U[2], &ctx->F[0], &ctx->F[1], &ctx->F[2],
@@ -686,6 +697,7 @@ extern "C" fch_status fch_create(const fch_grid *g, const fch_params *p, void *s
     if (e == cudaSuccess) e = cudaMalloc(&ctx->Z, (size_t)N * N * csz);
     for (int i = 0; i < 3 && e == cudaSuccess; i++) e = cudaMalloc(&ctx->Rs[i], (size_t)N * N * csz);
     if (e == cudaSuccess) e = cudaMalloc(&ctx->tw, (size_t)N * csz);
+    if (e == cudaSuccess) e = cudaMalloc(&ctx->tw4, (size_t)N * csz);
     if (e == cudaSuccess) e = cudaMalloc((void **)&ctx->part, sizeof(double) * FCH_NRED * FCH_MAXBLK);
     if (e == cudaSuccess) e = cudaMalloc((void **)&ctx->dctrl, sizeof(fch_ctrl));
     if (e == cudaSuccess) e = cudaMalloc((void **)&ctx->staging, sizeof(double) * N * N * 2);
@@ -727,12 +739,14 @@ extern "C" fch_status fch_create(const fch_grid *g, const fch_params *p, void *s
     ctx->kp.Z = ctx->Z;
     for (int i = 0; i < 3; i++) ctx->kp.Rs[i] = ctx->Rs[i];
     ctx->kp.tw = ctx->tw;
+    ctx->kp.tw4 = ctx->tw4;
     ctx->kp.part = ctx->part;
     ctx->kp.ctrl = ctx->dctrl;
     ctx->kp.nfft = (unsigned long long *)ctx->nfft_dev;
     ctx->kp.ticket = ctx->ticket;
     ctx->kp.tail_op = -1;
     fch_status s = upload_twiddles(ctx, N, ctx->prec, ctx->tw, ctx->stream);
+    if (s == FCH_OK) s = upload_twiddles(ctx, N, ctx->prec, ctx->tw4, ctx->stream, 2);
     if (s == FCH_OK && ctx->prec == FCH_MIXED && N == 1024 && ctx->p.fft_path != 1) {
         if (upload_tw2(&ctx->tw2, ctx->stream) != cudaSuccess) s = FCH_ECUDA;
         ctx->kp.tw2 = ctx->tw2;
@@ -756,7 +770,7 @@ extern "C" fch_status fch_destroy(fch_ctx *ctx)
     if (!ctx) return FCH_OK;
     if (ctx->stream) cudaStreamSynchronize(ctx->stream);
     void *bufs[] = {ctx->U[0], ctx->U[1], ctx->U[2], ctx->F[0], ctx->F[1], ctx->F[2], ctx->Pb,
-                    ctx->Qb, ctx->Vb, ctx->Nb, ctx->Z, ctx->tw, ctx->part, ctx->dctrl,
+                    ctx->Qb, ctx->Vb, ctx->Nb, ctx->Z, ctx->tw, ctx->tw4, ctx->part, ctx->dctrl,
                     ctx->staging, ctx->nfft_dev, ctx->ticket, ctx->tw2, ctx->Rs[0],
                     ctx->Rs[1], ctx->Rs[2], ctx->ls_a, ctx->ls_y, ctx->ls_part};
     for (void *b : bufs)
@@ -2146,12 +2160,14 @@ extern "C" fch_status fch_autotune_step(int n, int prec, void *stream, fch_tile 
     // rows; another tile replaces the default only if 3 % faster
     fch_tile best;
     memset(&best, 0, sizeof(best));
-    const int cands[] = {0, -1, -2, 1, 2, 4, 8, 16};
+    // (columns also at four points a thread: -3, -4, -6 for 1, 2, 4 pairs a block)
+    const int cands[] = {0, -1, -2, 1, 2, 4, 8, 16, -3, -4, -6};
     for (int is_col = 0; is_col < 2; is_col++) {
         double best_us = 1e30, def_us = 0;
         int best_t = 0;
         for (int c : cands) {
-            if (c < 0 && n != 1024) continue;
+            if ((c == -1 || c == -2) && n != 1024) continue;
+            if (c <= -3 && !is_col) continue;
             const int tr = is_col ? best.tile_row : c, tc = is_col ? c : 0;
             if (!fch_tile_valid(n, single, tr, tc)) continue;
             double us = 0;

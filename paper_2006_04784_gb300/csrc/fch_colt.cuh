@@ -147,9 +147,9 @@ __global__ void __launch_bounds__(kColtThreads, 2) col_pass_t(const fch_kparams 
                 fch::tc::fence_async_smem(); // the stage's reads come before the next copy's writes
                 if (g + gridDim.x < ntiles) fetch(g + gridDim.x);
             }
-            fft_stage<-1, 3, false>(tile, N, LOGN, NC, c, tw, t, 8, 3);
-            fft_stage<-1, 3, false>(tile, N, LOGN, NC, c, tw, t, 64, 6);
-            fft_stage<-1, 1, false>(tile, N, LOGN, NC, c, tw, t, 512, 9);
+            fft_stage<-1, 3, false, 8>(tile, N, LOGN, NC, c, tw, t, 8, 3);
+            fft_stage<-1, 3, false, 8>(tile, N, LOGN, NC, c, tw, t, 64, 6);
+            fft_stage<-1, 1, false, 8>(tile, N, LOGN, NC, c, tw, t, 512, 9);
             // spectral stage: the Hermitian split into the two half spectra. A thread
             // owns rows ky and -ky (both 32-byte rows of the tile, read whole) and all
             // four work items (pair p0 + pp, row ky or -ky) that touch only them.
@@ -209,9 +209,9 @@ __global__ void __launch_bounds__(kColtThreads, 2) col_pass_t(const fch_kparams 
                     fch::tc::fence_async_smem(); // the stage's reads come before the next copy's writes
                     if (g + gridDim.x < ntiles) fetch(g + gridDim.x);
                 }
-                fft_stage<+1, 3, false>(tile, N, LOGN, NC, c, tw, t, 8, 3);
-                fft_stage<+1, 3, false>(tile, N, LOGN, NC, c, tw, t, 64, 6);
-                fft_stage<+1, 1, false>(tile, N, LOGN, NC, c, tw, t, 512, 9);
+                fft_stage<+1, 3, false, 8>(tile, N, LOGN, NC, c, tw, t, 8, 3);
+                fft_stage<+1, 3, false, 8>(tile, N, LOGN, NC, c, tw, t, 64, 6);
+                fft_stage<+1, 1, false, 8>(tile, N, LOGN, NC, c, tw, t, 512, 9);
             } else {
                 // pair 0 (columns 0 and N/2) and pair 1, item by item from global memory
 #pragma unroll 1

@@ -73,7 +73,8 @@ struct fch_kparams {
     void *Pb, *Qb, *Vb, *Nb;        // SAV p/q, PSD iterate, ETD N(u^n)
     void *Rs[3];                    // real-space (u, Lap u) of the three state slots, N x N complex
     void *Z;                        // N x N complex pair-layout work array
-    const void *tw;                 // per-stage Stockham twiddles (see fft_smem)
+    const void *tw;                 // per-stage Stockham twiddles of radix-8 stages (see fft_smem)
+    const void *tw4;                // the same for radix-4 stages (contexts; null in plans)
     const void *tw2;                // N = 1024 warp transform: [k2][n1] exp(-2 pi i n1 k2 / 1024), float
     double *part;                   // [FCH_NRED][FCH_MAXBLK] per-block partial sums
     fch_ctrl *ctrl;

@@ -157,18 +157,20 @@ __device__ __forceinline__ int skew(int n) { return n + (n >> 3); }
 __host__ __device__ inline int skewed_len(int n) { return n + (n >> 3); }
 
 // One Stockham stage of radix R = 2^LR on a length-N sequence at
-// s[skew(n)*stride + off]; thread t of tps = N/8 owns 8/R butterflies.
-template <int DIR, int LR, bool TWG, typename C>
+// s[skew(n)*stride + off]; thread t of tps = N/PPT owns PPT/R butterflies (PPT points a
+// thread: 8 with radix-8 stages, 4 with radix-4 stages).
+template <int DIR, int LR, bool TWG, int PPT, typename C>
 __device__ __forceinline__ void fft_stage(C *s, int N, int logN, int stride, int off, const C *tw,
                                           int t, int Ns, int lNs)
 {
     constexpr int R = 1 << LR;
-    constexpr int NB = 8 / R;
-    const int tps = N >> 3, nb = N >> LR;
+    constexpr int NB = PPT / R;
+    static_assert(NB >= 1 && (PPT == 8 || PPT == 4), "a stage's radix divides the points a thread");
+    const int tps = N / PPT, nb = N >> LR;
     // double-float values stay unrenormalised between stages (the sums and twiddle
     // products take such operands); the last stage renormalises what it stores
     const bool last = (Ns << LR) == N;
-    C v[8];
+    C v[PPT];
 #pragma unroll
     for (int b = 0; b < NB; b++) {
         const int j = t + b * tps;
@@ -180,9 +182,9 @@ __device__ __forceinline__ void fft_stage(C *s, int N, int logN, int stride, int
         const int j = t + b * tps;
         if (Ns > 1) {
             // twiddle exp(DIR 2 pi i r (j mod Ns) / (Ns R)) from the per-stage table
-            // (every stage before the last is radix 8, so this stage starts at Ns - 8;
-            // entry [r-1][j mod Ns]: consecutive lanes read consecutive entries)
-            const C *tws = tw + (Ns - 8) + (j & (Ns - 1));
+            // (every stage before the last has radix PPT, so this stage starts at
+            // Ns - PPT; entry [r-1][j mod Ns]: consecutive lanes read consecutive entries)
+            const C *tws = tw + (Ns - PPT) + (j & (Ns - 1));
 #pragma unroll
             for (int r = 1; r < R; r++) {
                 C tv = TWG ? ldg(tws + (r - 1) * Ns) : tws[(r - 1) * Ns];
@@ -210,25 +212,28 @@ __device__ __forceinline__ void fft_stage(C *s, int N, int logN, int stride, int
 }
 
 // In-place transform of one sequence (all sequences of a block in lockstep);
-// starts and ends with a barrier of the whole block. tw holds the forward
-// twiddles of every stage with Ns > 1 (stage with Ns: entries Ns - 8 + (r-1) Ns + j,
-// value exp(-2 pi i r j / (Ns R)), r = 1..R-1, j < Ns), in shared memory, or in
-// global memory read through the read-only cache when TWG.
-template <int DIR, bool TWG = false, typename C>
+// starts and ends with a barrier of the whole block. PPT points a thread (t < N/PPT):
+// radix-8 stages (PPT 8) or radix-4 stages (PPT 4), then one stage of the remaining
+// radix. tw holds the forward twiddles of every stage with Ns > 1 (stage with Ns:
+// entries Ns - PPT + (r-1) Ns + j, value exp(-2 pi i r j / (Ns R)), r = 1..R-1,
+// j < Ns; a table per PPT), in shared memory, or in global memory read through the
+// read-only cache when TWG.
+template <int DIR, bool TWG = false, int PPT = 8, typename C>
 __device__ void fft_smem(C *s, int N, int logN, int stride, int off, const C *tw, int t)
 {
+    constexpr int LP = PPT == 8 ? 3 : 2;
     int Ns = 1, lNs = 0, rem = logN;
     __syncthreads();
-    while (rem >= 3) {
-        fft_stage<DIR, 3, TWG>(s, N, logN, stride, off, tw, t, Ns, lNs);
-        Ns <<= 3;
-        lNs += 3;
-        rem -= 3;
+    while (rem >= LP) {
+        fft_stage<DIR, LP, TWG, PPT>(s, N, logN, stride, off, tw, t, Ns, lNs);
+        Ns <<= LP;
+        lNs += LP;
+        rem -= LP;
     }
-    if (rem == 2)
-        fft_stage<DIR, 2, TWG>(s, N, logN, stride, off, tw, t, Ns, lNs);
-    else if (rem == 1)
-        fft_stage<DIR, 1, TWG>(s, N, logN, stride, off, tw, t, Ns, lNs);
+    if constexpr (LP == 3) {
+        if (rem == 2) fft_stage<DIR, 2, TWG, PPT>(s, N, logN, stride, off, tw, t, Ns, lNs);
+    }
+    if (rem == 1) fft_stage<DIR, 1, TWG, PPT>(s, N, logN, stride, off, tw, t, Ns, lNs);
 }
 
 // natural kx of slot q of a pair-layout row
@@ -640,12 +645,16 @@ __device__ __forceinline__ void pair0_item(const fch_kparams &kp, const fch_cons
 
 // LOGN > 0: the grid size is a compile-time constant (N = 2^LOGN >= 512), so the
 // index arithmetic of the transforms folds into immediates; LOGN = 0 reads N and P
-// from the parameters.
-template <typename T, int MODE, int LOGN>
+// from the parameters. PPT: points of a column a thread transforms (8: radix-8
+// stages, nc N / 8 threads; 4, generic kernel only: radix-4 stages, twice the threads
+// and half the dependent work a thread, for small grids whose passes are too few
+// warps to fill the GPU; twiddles from kp.tw4).
+template <typename T, int MODE, int LOGN, int PPT = 8>
 __global__ void __launch_bounds__(LOGN ? ((spec_pairs<T, LOGN>() << LOGN) >> 2) : 1024,
                                   col_min_blocks<LOGN ? ((spec_pairs<T, LOGN>() << LOGN) >> 2) : 1024, LOGN, MODE>())
 col_pass(const fch_kparams kp)
 {
+    static_assert(PPT == 8 || (PPT == 4 && LOGN == 0), "four points a thread in the generic kernel only");
     typedef typename CT<T>::t C;
     typedef ColTraits<MODE> TR;
     pdl_begin();
@@ -693,32 +702,33 @@ col_pass(const fch_kparams kp)
         co = fch_coef<T>();
     }
 
-    for (int i = threadIdx.x; i < N; i += nthr) tw[i] = ldg((const C *)kp.tw + i);
+    const C *twsrc = (const C *)(PPT == 8 ? kp.tw : kp.tw4);
+    for (int i = threadIdx.x; i < N; i += nthr) tw[i] = ldg(twsrc + i);
     if (TR::FWD) {
-        // blockDim = nc N / 8: exactly 8 elements of the tile per thread
-        C ld[8];
+        // blockDim = nc N / PPT: exactly PPT elements of the tile per thread
+        C ld[PPT];
 #pragma unroll
-        for (int k = 0; k < 8; k++) {
+        for (int k = 0; k < PPT; k++) {
             const int i = threadIdx.x + k * nthr;
             const int n = i / nc, cc = i - n * nc;
             ld[k] = Z[(long)n * N + 2 * p0 + cc];
         }
 #pragma unroll
-        for (int k = 0; k < 8; k++) {
+        for (int k = 0; k < PPT; k++) {
             const int i = threadIdx.x + k * nthr;
             const int n = i / nc, cc = i - n * nc;
             tile[skew(n) * nc + cc] = ld[k];
         }
-        fft_smem<-1>(tile, N, logN, nc, c, tw, t);
+        fft_smem<-1, false, PPT>(tile, N, logN, nc, c, tw, t);
     } else {
         __syncthreads();
     }
 
     T red[FCH_NRED] = {0, 0, 0, 0};
     // spectral stage: work item (pair p, ky); pair 0 covers columns 0 and N/2
-    // blockDim = P N / 4: exactly 4 work items per thread
+    // blockDim = 2 P N / PPT: exactly PPT / 2 work items per thread
 #pragma unroll 1
-    for (int it = 0; it < 4; it++) {
+    for (int it = 0; it < PPT / 2; it++) {
         const int i = threadIdx.x + it * nthr;
         const int pp = i / N, ky = i - pp * N;
         const int p = p0 + pp;
@@ -749,9 +759,9 @@ col_pass(const fch_kparams kp)
         if (kp.tail_op >= 0) pass_tail(kp);
     }
     if (inv) {
-        fft_smem<+1>(tile, N, logN, nc, c, tw, t);
+        fft_smem<+1, false, PPT>(tile, N, logN, nc, c, tw, t);
 #pragma unroll
-        for (int k = 0; k < 8; k++) {
+        for (int k = 0; k < PPT; k++) {
             const int i = threadIdx.x + k * nthr;
             const int n = i / nc, cc = i - n * nc;
             Z[(long)n * N + 2 * p0 + cc] = tile[skew(n) * nc + cc];

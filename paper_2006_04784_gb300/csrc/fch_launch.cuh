@@ -159,6 +159,17 @@ template <typename T, int M> cudaError_t launch_col(const fch_kparams &kp, cudaS
     if constexpr (sizeof(T) == 8) {
         if (kp.N == 1024 && kp.tile_col == 0) return launch_col_cl<T, M>(kp, s);
     }
+    if (kp.tile_col <= -3) {
+        // the generic kernel at four points a thread: needs the radix-4 twiddle table
+        // (contexts carry one, standalone plans do not)
+        if (!kp.tw4) return cudaErrorInvalidValue;
+        static int attr4 = 0;
+        const fch_geom g = fch_geometry_tiled(kp.N, sizeof(T) == 4, 0, kp.tile_col);
+        pass_fn f = fch::col_pass<T, M, 0, 4>;
+        cudaError_t e = set_smem(f, g.col_smem, 0, attr4);
+        if (e != cudaSuccess) return e;
+        return launch_pass(f, dim3(g.col_blocks, pair_grid(kp)), dim3(g.col_threads), g.col_smem, s, kp);
+    }
     static int attr[12] = {};
     // the warp-level tile without its table (a context made with fft_path = 1) is -1
     const int tc = kp.tile_col == -2 ? -1 : kp.tile_col;

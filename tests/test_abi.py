@@ -74,7 +74,7 @@ def test_tiles_cover_grid(n, prec):
     nvalid = 0
     for t in (1, 2, 4, 8, 16, 32):
         ok_r, g = fch.tile_geometry(n, prec, t, 0)
-        fits_r = t <= n and t * (n // 8) <= 256 and t * sl * csz <= 226 * 1024
+        fits_r = t <= n and t * (n // 8) <= 256 and t * (n // 8) % 32 == 0 and t * sl * csz <= 226 * 1024
         assert ok_r == fits_r, (t, g)
         if ok_r:
             nvalid += 1
@@ -82,7 +82,7 @@ def test_tiles_cover_grid(n, prec):
             assert g["row_threads"] == t * (n // 8) and g["row_smem"] == t * sl * csz
         ok_c, g = fch.tile_geometry(n, prec, 0, t)
         fits_c = (t >= (2 if prec == 1 else 1) and t <= n // 2 and t * n // 4 <= 1024
-                  and (n + 2 * t * sl) * csz <= 226 * 1024)
+                  and t * n // 4 % 32 == 0 and (n + 2 * t * sl) * csz <= 226 * 1024)
         assert ok_c == fits_c, (t, g)
         if ok_c:
             assert g["P"] == t and g["col_blocks"] * t == n // 2
@@ -95,6 +95,17 @@ def test_tiles_cover_grid(n, prec):
     assert ok == (prec == 1 and n == 1024)
     if ok:
         assert g["col_blocks"] == n // 4 and g["col_threads"] == 128
+    # tile_col = -2 - P: the generic column kernel with P pairs a block at four points a
+    # thread (twice the threads of tile P)
+    for t in (1, 2, 4, 8, 16):
+        ok_c, g = fch.tile_geometry(n, prec, 0, -2 - t)
+        fits_c = (t >= (2 if prec == 1 else 1) and t <= n // 2 and t * n // 2 <= 1024
+                  and t * n // 2 % 32 == 0 and (n + 2 * t * sl) * csz <= 226 * 1024)
+        assert ok_c == fits_c, (t, g)
+        if ok_c:
+            assert g["P"] == t and g["col_blocks"] * t == n // 2
+            assert g["col_threads"] == 2 * t * (n // 4) and g["col_smem"] == (n + 2 * t * sl) * csz
+    assert not fch.tile_geometry(n, prec, 0, -5)[0]  # P = 3
 
 
 def test_stockham_index_map_is_a_permutation():

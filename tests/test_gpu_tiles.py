@@ -43,10 +43,12 @@ def lib_params(**kw):
 
 
 @pytest.mark.parametrize("n,prec,tiles", [
-    (256, 0, [(1, 1), (2, 4), (4, 2), (-1, -1)]),
-    (256, 2, [(1, 1), (4, 4), (-1, -1)]),
-    (512, 0, [(1, 2), (2, 1), (-1, -1)]),
-    (1024, 2, [(1, 1), (2, 2)]),
+    (256, 0, [(1, 1), (2, 4), (4, 2), (-1, -1), (1, -3), (1, -4)]),
+    (256, 2, [(1, 1), (4, 4), (-1, -1), (1, -3), (1, -6)]),
+    (128, 2, [(2, -3), (2, -4)]),
+    (64, 0, [(0, -3), (0, -4)]),
+    (512, 0, [(1, 2), (2, 1), (-1, -1), (0, -3)]),
+    (1024, 2, [(1, 1), (2, 2), (0, -3)]),
 ])
 def test_forced_tiles_match_oracle(n, prec, tiles):
     # fixed IMEX and SAV steps under generic-kernel tiles of several shapes
@@ -65,6 +67,28 @@ def test_forced_tiles_match_oracle(n, prec, tiles):
                 for dt in (1e-4, 1e-4, 2e-4):
                     ctx.step(scheme, dt)
                 assert rel(ctx.get_state(), ref[scheme]) < 1e-10, (tr, tc, scheme)
+
+
+def test_four_point_column_tiles_single_precision():
+    # tile_col = -2 - P in single precision (P >= 2): the steps of the default tiles and
+    # of the oracle to single-precision rounding (the bound of the other single-precision
+    # tile test)
+    n = 256
+    u0 = I.circle_bilayer(n, noise=1e-3)
+    o = O.Stepper(n, L, oparams(lib_params(prec=1)))
+    o.set_state(u0)
+    for dt in (1e-4, 1e-4, 2e-4):
+        o.step("imex", dt)
+    out = []
+    for tc in (0, -4, -6):
+        with fch.Context(n, lib_params(prec=1, tile_col=tc)) as ctx:
+            ctx.set_state(u0)
+            for dt in (1e-4, 1e-4, 2e-4):
+                ctx.step("imex", dt)
+            out.append(ctx.get_state())
+    for u in out:
+        assert rel(u, o.state()) < 3e-5
+    assert rel(out[1], out[0]) < 3e-5 and rel(out[2], out[0]) < 3e-5
 
 
 def test_forced_tiles_mixed_1024_warp_and_shared_memory():
