@@ -2407,6 +2407,15 @@ extern "C" int fch_debug_tile(int n, int prec, int row, int col, int *out)
     return fch_tile_valid(n, prec, row, col) ? 1 : 0;
 }
 
+// the per-stage twiddle table of the shared-memory transforms for radix-2^lp stages
+// (lp 3: eight points a thread, 2: four), n complex entries as 2n doubles (CPU tests)
+extern "C" int fch_debug_twiddles(int n, int lp, double *out)
+{
+    if (!pow2_in_range(n) || (lp != 2 && lp != 3) || !out) return 1;
+    make_twiddles(n, out, lp);
+    return 0;
+}
+
 // which trials and fixed steps of a context replay a captured graph (tests):
 // out[s] for scheme s: 1 captured, -1 capture failed (eager launches), 0 not yet;
 // out[4 + s]: 1 if a fixed step of scheme s is captured

@@ -169,6 +169,8 @@ def lib():
         L.fch_pass_times.argtypes = [vp, C.POINTER(C.c_double), C.POINTER(C.c_longlong), C.c_int]
         L.fch_debug_geometry.argtypes = [C.c_int, C.c_int, C.POINTER(C.c_int)]
         L.fch_debug_graphs.argtypes = [vp, C.POINTER(C.c_int)]
+        L.fch_debug_twiddles.argtypes = [C.c_int, C.c_int, C.POINTER(C.c_double)]
+        L.fch_debug_twiddles.restype = C.c_int
         L.fch_debug_graphs.restype = C.c_int
         for name in EXPORTS:
             if name not in ("fch_status_string", "fch_last_cuda_error"):
@@ -232,6 +234,16 @@ def geometry(n: int, prec: int = 0):
     keys = ["col_blocks", "col_threads", "col_smem", "row_blocks", "row_threads", "row_smem",
             "rpb", "P", "ctrl_bytes"]
     return dict(zip(keys, list(out)))
+
+
+def stage_twiddles(n: int, lp: int):
+    """the host's per-stage twiddle table for radix-2^lp shared-memory transforms
+    (n complex entries; host-side query, no device work)"""
+    out = (C.c_double * (2 * n))()
+    if lib().fch_debug_twiddles(n, lp, out):
+        raise ValueError((n, lp))
+    a = np.frombuffer(out, dtype=np.float64)
+    return a[0::2] + 1j * a[1::2]
 
 
 def tile_geometry(n: int, prec: int, tile_row: int, tile_col: int):

@@ -163,3 +163,50 @@ def test_compile_time_pair_rule_matches_geometry():
     for n in (512, 1024, 2048):
         for prec, pmin in ((0, 1), (1, 2)):
             assert fch.geometry(n, prec)["P"] == max(pmin, 1024 // n)
+
+
+def _stockham(x, tw, ppt, sign):
+    """The shared-memory transform's stage schedule and index arithmetic, read from
+    the kernels (fft_smem / fft_stage): radix-ppt stages, then one of the remaining
+    radix; stage Ns reads x[j + r N/R], multiplies by the table's entry
+    Ns - ppt + (r-1) Ns + (j mod Ns) (conjugated for the inverse), takes the R-point
+    DFT and writes output r at ((j >> log Ns) << log(Ns R)) + (j mod Ns) + r Ns."""
+    import numpy as np
+    n = len(x)
+    lp = 3 if ppt == 8 else 2
+    stages, rem = [], int(np.log2(n))
+    while rem >= lp:
+        stages.append(lp)
+        rem -= lp
+    if rem:
+        stages.append(rem)
+    s, ns, lns = np.array(x, dtype=complex), 1, 0
+    for lr in stages:
+        R = 1 << lr
+        nb = n >> lr
+        out = np.full(n, np.nan, dtype=complex)
+        k = np.arange(R)
+        dft = np.exp(sign * 2j * np.pi * np.outer(k, k) / R)
+        for j in range(nb):
+            v = np.array([s[j + r * nb] for r in range(R)])
+            if ns > 1:
+                for r in range(1, R):
+                    t = tw[ns - ppt + (r - 1) * ns + (j & (ns - 1))]
+                    v[r] *= t if sign < 0 else np.conj(t)
+            dst = ((j >> lns) << (lns + lr)) + (j & (ns - 1)) + ns * k
+            assert np.all(np.isnan(out[dst]))
+            out[dst] = dft @ v
+        s, ns, lns = out, ns << lr, lns + lr
+    return s
+
+
+@pytest.mark.parametrize("n", [16, 32, 128, 256, 512, 2048])
+@pytest.mark.parametrize("ppt", [8, 4])
+def test_stage_twiddle_tables_give_the_dft(n, ppt):
+    # the host's twiddle tables for eight and four points a thread, applied with the
+    # kernels' stage indexing, give the DFT and its inverse (numpy's FFT)
+    import numpy as np
+    tw = fch.stage_twiddles(n, 3 if ppt == 8 else 2)
+    x = np.random.default_rng(n + ppt).standard_normal(n) + 1j * np.random.default_rng(1).standard_normal(n)
+    assert np.abs(_stockham(x, tw, ppt, -1) - np.fft.fft(x)).max() < 1e-12 * n
+    assert np.abs(_stockham(x, tw, ppt, +1) - n * np.fft.ifft(x)).max() < 1e-12 * n
