@@ -102,7 +102,8 @@ typedef struct {
                           * kernel with r column pairs per block; tile_col = -2 - P
                           * (-3, -4, -6, ...) the generic column kernel with P pairs per
                           * block at four points a thread (radix-4 stages, twice the
-                          * threads). Generic tiles are powers of two that fit whole
+                          * threads), tile_row = -2 - R the generic row kernel with R
+                          * rows per block at four points a thread. Generic tiles are powers of two that fit whole
                           * warps, the row kernel's 256 threads or the column kernel's
                           * 1024 threads a block and a block's shared memory; else
                           * FCH_EINVAL */

@@ -83,6 +83,14 @@ fch_geom fch_geometry_tiled(int N, int prec, int tile_row, int tile_col)
         g.row_blocks = N / tile_row;
         g.row_smem = tile_row * SL * csz;
     }
+    if (tile_row <= -3) {
+        // the generic row kernel with R = -2 - tile_row rows a block at four points a thread
+        const int R = -2 - tile_row;
+        g.rpb = R;
+        g.row_threads = R * (N / 4);
+        g.row_blocks = N / R;
+        g.row_smem = R * SL * csz;
+    }
     return g;
 }
 
@@ -94,11 +102,12 @@ bool fch_tile_valid(int N, int prec, int tile_row, int tile_col)
 {
     const int smem_max = 227 * 1024 - 1024;
     const int pmin = prec == 1 ? 2 : 1;
-    if (tile_row > 0) {
-        if ((tile_row & (tile_row - 1)) || tile_row > N) return false;
+    if (tile_row > 0 || tile_row <= -3) {
+        const int R = tile_row > 0 ? tile_row : -2 - tile_row;
+        if ((R & (R - 1)) || R > N) return false;
         const fch_geom g = fch_geometry_tiled(N, prec, tile_row, 0);
         if (g.row_threads > 256 || (g.row_threads & 31) || g.row_smem > smem_max) return false;
-    } else if (tile_row < -1) {
+    } else if (tile_row == -2) {
         return false;
     }
     if (tile_col > 0 || tile_col <= -3) {
@@ -2160,7 +2169,8 @@ extern "C" fch_status fch_autotune_step(int n, int prec, void *stream, fch_tile 
     // rows; another tile replaces the default only if 3 % faster
     fch_tile best;
     memset(&best, 0, sizeof(best));
-    // (columns also at four points a thread: -3, -4, -6 for 1, 2, 4 pairs a block)
+    // (columns also at four points a thread: -3, -4, -6 for 1, 2, 4 pairs a block; rows
+    // at four points a thread are tested as fixed-step tiles only, so not candidates)
     const int cands[] = {0, -1, -2, 1, 2, 4, 8, 16, -3, -4, -6};
     for (int is_col = 0; is_col < 2; is_col++) {
         double best_us = 1e30, def_us = 0;

@@ -938,23 +938,26 @@ template <int LOGN> constexpr int row_min_blocks()
     return LOGN == 10 ? 7 : pass_min_blocks<256, LOGN>();
 }
 
-template <typename T, int MODE, int LOGN>
+// PPT: points of a row a thread transforms (8: radix-8 stages; 4, generic kernel only:
+// radix-4 stages and twice the threads, twiddles from kp.tw4), as in col_pass.
+template <typename T, int MODE, int LOGN, int PPT = 8>
 __global__ void __launch_bounds__(LOGN ? row_threads<LOGN>() : 256, LOGN ? row_min_blocks<LOGN>() : 1)
 row_pass(const fch_kparams kp)
 {
+    static_assert(PPT == 8 || (PPT == 4 && LOGN == 0), "four points a thread in the generic kernel only");
     typedef typename CT<T>::t C;
     pdl_begin();
     if (pass_skipped(kp)) return;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ double red_scratch[FCH_NRED * 32];
-    const int N = LOGN ? (1 << LOGN) : kp.N, tps = N >> 3, SL = skewed_len(N);
+    const int N = LOGN ? (1 << LOGN) : kp.N, tps = N / PPT, SL = skewed_len(N);
     const int logN = LOGN ? LOGN : kp.logN;
     const int nthr = LOGN ? row_threads<LOGN>() : (int)blockDim.x;
     if (kp.nfft && blockIdx.x == 0 && threadIdx.x == 0)
         atomicAdd(kp.nfft, (MODE == RM_R2C_LOAD || MODE == RM_C2R_STORE || MODE == RM_ENERGY) ? 2ull : 4ull);
     // twiddles stay in global memory (read-only cache): the shared memory holds
     // only the rows, so more blocks fit an SM
-    const C *tw = (const C *)kp.tw;
+    const C *tw = (const C *)(PPT == 8 ? kp.tw : kp.tw4);
     C *rows = (C *)smem_raw;
     const int rpb = nthr / tps;
     const int rr = threadIdx.x / tps, t = threadIdx.x - rr * tps;
@@ -995,10 +998,10 @@ row_pass(const fch_kparams kp)
             rows[r * SL + skew(x)] = mk<C>(a, b);
         }
     } else {
-        // blockDim = rpb N / 8: each thread moves 4 pairs (kx, N-kx) of its rows
-        C ld[8];
+        // blockDim = rpb N / PPT: each thread moves PPT / 2 pairs (kx, N-kx) of its rows
+        C ld[PPT];
 #pragma unroll
-        for (int k = 0; k < 4; k++) {
+        for (int k = 0; k < PPT / 2; k++) {
             const int i = threadIdx.x + k * nthr;
             const int r = i / (N >> 1), pp = i - r * (N >> 1);
             const C *src = Z + (long)(y0 + r) * N + 2 * pp;
@@ -1006,13 +1009,13 @@ row_pass(const fch_kparams kp)
             ld[2 * k + 1] = src[1];
         }
 #pragma unroll
-        for (int k = 0; k < 4; k++) {
+        for (int k = 0; k < PPT / 2; k++) {
             const int i = threadIdx.x + k * nthr;
             const int r = i / (N >> 1), pp = i - r * (N >> 1);
             rows[r * SL + skew(pp)] = ld[2 * k];
             rows[r * SL + skew(pp ? N - pp : (N >> 1))] = ld[2 * k + 1];
         }
-        fft_smem<+1, true>(rows + rr * SL, N, logN, 1, 0, tw, t);
+        fft_smem<+1, true, PPT>(rows + rr * SL, N, logN, 1, 0, tw, t);
     }
 
     T red[FCH_NRED] = {0, 0, 0, 0};
@@ -1078,9 +1081,9 @@ row_pass(const fch_kparams kp)
     }
     if (MODE == RM_C2R_STORE || MODE == RM_ENERGY) return;
 
-    fft_smem<-1, true>(rows + rr * SL, N, logN, 1, 0, tw, t);
+    fft_smem<-1, true, PPT>(rows + rr * SL, N, logN, 1, 0, tw, t);
 #pragma unroll
-    for (int k = 0; k < 4; k++) {
+    for (int k = 0; k < PPT / 2; k++) {
         const int i = threadIdx.x + k * nthr;
         const int r = i / (N >> 1), pp = i - r * (N >> 1);
         C *dst = Z + (long)(y0 + r) * N + 2 * pp;

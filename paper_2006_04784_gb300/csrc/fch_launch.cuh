@@ -184,6 +184,16 @@ template <typename T, int M> cudaError_t launch_col(const fch_kparams &kp, cudaS
 template <typename T, int M> cudaError_t launch_row(const fch_kparams &kp, cudaStream_t s)
 {
     if (warp_path<T>() && kp.N == 1024 && kp.tw2 && kp.tile_row == 0) return launch_row_w<M>(kp, s);
+    if (kp.tile_row <= -3) {
+        // the generic kernel at four points a thread (radix-4 twiddle table: contexts only)
+        if (!kp.tw4) return cudaErrorInvalidValue;
+        static int attr4 = 0;
+        const fch_geom g = fch_geometry_tiled(kp.N, sizeof(T) == 4, kp.tile_row, 0);
+        pass_fn f = fch::row_pass<T, M, 0, 4>;
+        cudaError_t e = set_smem(f, g.row_smem, 0, attr4);
+        if (e != cudaSuccess) return e;
+        return launch_pass(f, dim3(g.row_blocks, pair_grid(kp)), dim3(g.row_threads), g.row_smem, s, kp);
+    }
     static int attr[12] = {};
     const fch_geom g = fch_geometry_tiled(kp.N, sizeof(T) == 4, kp.tile_row, 0);
     const int li = kp.tile_row <= 0 ? kernel_slot(kp.logN) : 0;

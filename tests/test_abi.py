@@ -106,6 +106,15 @@ def test_tiles_cover_grid(n, prec):
             assert g["P"] == t and g["col_blocks"] * t == n // 2
             assert g["col_threads"] == 2 * t * (n // 4) and g["col_smem"] == (n + 2 * t * sl) * csz
     assert not fch.tile_geometry(n, prec, 0, -5)[0]  # P = 3
+    # tile_row = -2 - R: the generic row kernel with R rows a block at four points a thread
+    for t in (1, 2, 4, 8):
+        ok_r, g = fch.tile_geometry(n, prec, -2 - t, 0)
+        fits_r = t <= n and t * (n // 4) <= 256 and t * (n // 4) % 32 == 0 and t * sl * csz <= 226 * 1024
+        assert ok_r == fits_r, (t, g)
+        if ok_r:
+            assert g["rpb"] == t and g["row_blocks"] * t == n
+            assert g["row_threads"] == t * (n // 4) and g["row_smem"] == t * sl * csz
+    assert not fch.tile_geometry(n, prec, -5, 0)[0]  # R = 3
 
 
 def test_stockham_index_map_is_a_permutation():

@@ -43,12 +43,12 @@ def lib_params(**kw):
 
 
 @pytest.mark.parametrize("n,prec,tiles", [
-    (256, 0, [(1, 1), (2, 4), (4, 2), (-1, -1), (1, -3), (1, -4)]),
-    (256, 2, [(1, 1), (4, 4), (-1, -1), (1, -3), (1, -6)]),
-    (128, 2, [(2, -3), (2, -4)]),
-    (64, 0, [(0, -3), (0, -4)]),
-    (512, 0, [(1, 2), (2, 1), (-1, -1), (0, -3)]),
-    (1024, 2, [(1, 1), (2, 2), (0, -3)]),
+    (256, 0, [(1, 1), (2, 4), (4, 2), (-1, -1), (1, -3), (1, -4), (-3, -3), (-4, 2)]),
+    (256, 2, [(1, 1), (4, 4), (-1, -1), (1, -3), (1, -6), (-3, -3), (-6, -4)]),
+    (128, 2, [(2, -3), (2, -4), (-4, -3)]),
+    (64, 0, [(0, -3), (0, -4), (-4, -3)]),
+    (512, 0, [(1, 2), (2, 1), (-1, -1), (0, -3), (-3, 0)]),
+    (1024, 2, [(1, 1), (2, 2), (0, -3), (-3, 0)]),
 ])
 def test_forced_tiles_match_oracle(n, prec, tiles):
     # fixed IMEX and SAV steps under generic-kernel tiles of several shapes
